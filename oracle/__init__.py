@@ -1,0 +1,177 @@
+"""Oracle tracker (test infrastructure only).
+
+A plain, slow, single-threaded FP64 CPU implementation of the tracking path of
+the Xsuite paper (section "Lattice modelling and single particle tracking"),
+written in ``xtoracle.cpp`` and loaded here through ctypes.  It is the
+independent reference that the CUDA tracker is checked against.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA library
+in ``paper_2310_00317_gb300``; the two meet only through the flat lattice
+table layout (type, order, 48 parameters) and the particle arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SRC = os.path.join(_HERE, "xtoracle.cpp")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# Lattice-table row: the same memory layout the library's public header uses.
+ELEMENT_DTYPE = np.dtype([("type", "<i4"), ("order", "<i4"), ("p", "<f8", (48,))], align=True)
+DRIFT, MULTIPOLE, CAVITY, DIPEDGE, LINEARMAP, APERTURE, MARKER = 1, 2, 3, 4, 5, 6, 0
+
+FLOAT_FIELDS = ("x", "px", "y", "py", "zeta", "delta", "ptau", "rpp", "rvv")
+INT_FIELDS = ("state", "at_turn", "at_element")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (g++, no contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    tmp = _SO + ".tmp%d" % os.getpid()
+    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math",
+           "-shared", "-fPIC", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            P = ctypes.c_void_p
+            i64, i32, u64, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_double
+            L.xo_track.argtypes = [P, i64, P, i32, u64] + [P] * 13 + [i64, i64, i64]
+            L.xo_track.restype = i32
+            L.xo_track_jacobian.argtypes = [P, i64, P, i32, P, i64, P, P, P]
+            L.xo_track_jacobian.restype = i32
+            L.xo_closed_orbit.argtypes = [P, i64, P, i32, i32, P]
+            L.xo_closed_orbit.restype = i32
+            L.xo_sin.argtypes = [dbl]
+            L.xo_sin.restype = dbl
+            L.xo_philox4x64_10.argtypes = [P, P, P]
+            L.xo_philox4x64_10.restype = None
+            L.xo_uniform.argtypes = [u64, u64, u64, u64, i64]
+            L.xo_uniform.restype = dbl
+            L.xo_spectrum_size.restype = i32
+            L.xo_spectrum_table.argtypes = [P, P]
+            L.xo_spectrum_sample.argtypes = [dbl]
+            L.xo_spectrum_sample.restype = dbl
+            L.xo_ref_constants.argtypes = [P, P]
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def _ref_arr(ref) -> np.ndarray:
+    return np.array([ref[0], ref[1], ref[2]], dtype=np.float64)
+
+
+def _elements(elements) -> np.ndarray:
+    el = np.ascontiguousarray(elements)
+    if el.dtype != ELEMENT_DTYPE:
+        el = el.astype(ELEMENT_DTYPE)
+    return el
+
+
+def track(elements, ref, particles: dict, n_turns: int, start_turn: int = 0,
+          rad_mode: int = 0, seed: int = 0) -> dict:
+    """Track a copy of ``particles`` (dict of numpy arrays); returns the new dict."""
+    el = _elements(elements)
+    r = _ref_arr(ref)
+    out = {}
+    for k in FLOAT_FIELDS:
+        out[k] = np.ascontiguousarray(particles[k], dtype=np.float64).copy()
+    for k in INT_FIELDS:
+        out[k] = np.ascontiguousarray(particles[k], dtype=np.int32).copy()
+    out["particle_id"] = np.ascontiguousarray(particles["particle_id"], dtype=np.int64).copy()
+    n = out["x"].shape[0]
+    rc = lib().xo_track(_ptr(el), el.shape[0], _ptr(r), rad_mode, seed,
+                        *[_ptr(out[k]) for k in FLOAT_FIELDS],
+                        *[_ptr(out[k]) for k in INT_FIELDS], _ptr(out["particle_id"]),
+                        n, start_turn, n_turns)
+    if rc != 0:
+        raise ValueError("oracle track rejected its arguments")
+    return out
+
+
+def track_jacobian(elements, ref, z0, n_turns: int = 1, rad_mode: int = 0, along: bool = False):
+    """Final canonical coordinates, the 6x6 Jacobian, and optionally the
+    orbit and cumulative Jacobian after each element of the first turn."""
+    el = _elements(elements)
+    r = _ref_arr(ref)
+    z = np.ascontiguousarray(z0, dtype=np.float64)
+    zo = np.zeros(6)
+    M = np.zeros(36)
+    al = np.zeros(el.shape[0] * 42) if along else None
+    rc = lib().xo_track_jacobian(_ptr(el), el.shape[0], _ptr(r), rad_mode, _ptr(z), n_turns,
+                                 _ptr(zo), _ptr(M), _ptr(al) if along else None)
+    if rc != 0:
+        raise ValueError("oracle jacobian: particle lost or bad input (%d)" % rc)
+    if along:
+        al = al.reshape(el.shape[0], 42)
+        return zo, M.reshape(6, 6), al[:, :6].copy(), al[:, 6:].reshape(-1, 6, 6).copy()
+    return zo, M.reshape(6, 6)
+
+
+def closed_orbit(elements, ref, rad_mode: int = 0, dim: int = 6, guess=None) -> np.ndarray:
+    el = _elements(elements)
+    r = _ref_arr(ref)
+    z = np.zeros(6) if guess is None else np.array(guess, dtype=np.float64)
+    it = lib().xo_closed_orbit(_ptr(el), el.shape[0], _ptr(r), rad_mode, dim, _ptr(z))
+    if it < 0:
+        raise ValueError("closed orbit search failed")
+    return z
+
+
+def sin(x: float) -> float:
+    return lib().xo_sin(float(x))
+
+
+def philox4x64_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    o = np.zeros(4, dtype=np.uint64)
+    lib().xo_philox4x64_10(_ptr(c), _ptr(k), _ptr(o))
+    return o
+
+
+def uniform(seed: int, pid: int, turn: int, elem: int, index: int) -> float:
+    return lib().xo_uniform(seed, pid, turn, elem, index)
+
+
+def spectrum_table():
+    n = lib().xo_spectrum_size()
+    xi = np.zeros(n)
+    F = np.zeros(n)
+    lib().xo_spectrum_table(_ptr(xi), _ptr(F))
+    return xi, F
+
+
+def spectrum_sample(u: float) -> float:
+    return lib().xo_spectrum_sample(float(u))
+
+
+def ref_constants(ref) -> dict:
+    r = _ref_arr(ref)
+    o = np.zeros(6)
+    lib().xo_ref_constants(_ptr(r), _ptr(o))
+    return dict(E0=o[0], beta0=o[1], gamma0=o[2], crad=o[3], kq=o[4], uc15=o[5])

@@ -1,0 +1,671 @@
+// Oracle tracker: plain, slow, single-threaded FP64 CPU implementation of the
+// element-by-element symplectic tracking path of the Xsuite paper (Iadarola et
+// al., "Xsuite: an integrated beam physics simulation framework").
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the independent reference against
+// which the CUDA tracker is checked.  Only the test suite, the smoke check and
+// the CPU-baseline leg of the benchmark may load it.  It shares no code,
+// header, table or constant generator with the CUDA library.
+//
+// The paper prints no formulas; it states that a beam line is a sequence of
+// element objects tracked turn after turn with thin-lens integration
+// (section "Lattice modelling and single particle tracking"), that aperture
+// elements stop tracking of particles found outside ("Particle-matter
+// interaction and collimation studies"), and that synchrotron radiation has a
+// "mean" and a "quantum" model for thin elements ("Synchrotron radiation models
+// and compensation").  The maps below are the textbook thin-lens Hamiltonian
+// maps with MAD-X sign conventions; every operation order and every explicit
+// fma is part of the map definition, so the CUDA path can reproduce the same
+// bits.  Build with -O2 -ffp-contract=off (no implicit contraction).
+//
+// Coordinates: x, px=Px/P0, y, py, zeta=s-beta0*c*t, delta=(P-P0)/P0,
+// ptau=(E-E0)/(P0 c), rpp=1/(1+delta), rvv=beta/beta0.
+//
+// The scalar type is a template parameter so the same map code yields values
+// (double) and exact first derivatives (Dual, forward-mode differentiation)
+// for the one-turn Jacobian, the closed orbit and the optics pins.
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+
+namespace xo {
+
+// ---------------------------------------------------------------------------
+// Physical constants (CODATA 2018).
+static const double C_LIGHT = 299792458.0;          // m/s
+static const double M_ELECTRON = 0.51099895000e6;   // eV
+static const double R_ELECTRON = 2.8179403262e-15;  // m
+static const double ALPHA_FS = 7.2973525693e-3;
+static const double HBAR_C = 197.3269804e-9;        // eV m
+static const double PI = 3.14159265358979323846;
+
+// Element descriptor: the flat lattice-table row (type, order, 48 params).
+struct Element {
+  int32_t type;
+  int32_t order;
+  double p[48];
+};
+enum {
+  T_MARKER = 0, T_DRIFT = 1, T_MULTIPOLE = 2, T_CAVITY = 3,
+  T_DIPEDGE = 4, T_LINEARMAP = 5, T_APERTURE = 6
+};
+struct Reference { double mass0, q0, p0c; };
+
+// ---------------------------------------------------------------------------
+// Dual number with 6 infinitesimal directions (forward-mode derivative).
+struct Dual {
+  double v;
+  double d[6];
+};
+static inline Dual mkd(double v) { Dual r; r.v = v; for (int i = 0; i < 6; i++) r.d[i] = 0; return r; }
+static inline Dual operator+(const Dual& a, const Dual& b) { Dual r; r.v = a.v + b.v; for (int i = 0; i < 6; i++) r.d[i] = a.d[i] + b.d[i]; return r; }
+static inline Dual operator-(const Dual& a, const Dual& b) { Dual r; r.v = a.v - b.v; for (int i = 0; i < 6; i++) r.d[i] = a.d[i] - b.d[i]; return r; }
+static inline Dual operator-(const Dual& a) { Dual r; r.v = -a.v; for (int i = 0; i < 6; i++) r.d[i] = -a.d[i]; return r; }
+static inline Dual operator*(const Dual& a, const Dual& b) { Dual r; r.v = a.v * b.v; for (int i = 0; i < 6; i++) r.d[i] = a.d[i] * b.v + a.v * b.d[i]; return r; }
+static inline Dual operator/(const Dual& a, const Dual& b) { Dual r; r.v = a.v / b.v; for (int i = 0; i < 6; i++) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v; return r; }
+static inline Dual operator+(const Dual& a, double b) { Dual r = a; r.v = a.v + b; return r; }
+static inline Dual operator+(double a, const Dual& b) { Dual r = b; r.v = a + b.v; return r; }
+static inline Dual operator-(const Dual& a, double b) { Dual r = a; r.v = a.v - b; return r; }
+static inline Dual operator-(double a, const Dual& b) { Dual r; r.v = a - b.v; for (int i = 0; i < 6; i++) r.d[i] = -b.d[i]; return r; }
+static inline Dual operator*(const Dual& a, double b) { Dual r; r.v = a.v * b; for (int i = 0; i < 6; i++) r.d[i] = a.d[i] * b; return r; }
+static inline Dual operator*(double a, const Dual& b) { Dual r; r.v = a * b.v; for (int i = 0; i < 6; i++) r.d[i] = a * b.d[i]; return r; }
+static inline Dual operator/(double a, const Dual& b) { Dual r; r.v = a / b.v; for (int i = 0; i < 6; i++) r.d[i] = -r.v * b.d[i] / b.v; return r; }
+
+static inline double val(double a) { return a; }
+static inline double val(const Dual& a) { return a.v; }
+
+// fma: one rounding for the value; exact derivative of a*b+c.
+static inline double FMA(double a, double b, double c) { return std::fma(a, b, c); }
+static inline Dual FMA(const Dual& a, const Dual& b, const Dual& c) {
+  Dual r; r.v = std::fma(a.v, b.v, c.v);
+  for (int i = 0; i < 6; i++) r.d[i] = a.d[i] * b.v + a.v * b.d[i] + c.d[i];
+  return r;
+}
+static inline Dual FMA(double a, const Dual& b, const Dual& c) { return FMA(mkd(a), b, c); }
+static inline Dual FMA(const Dual& a, double b, const Dual& c) { return FMA(a, mkd(b), c); }
+static inline Dual FMA(const Dual& a, const Dual& b, double c) { return FMA(a, b, mkd(c)); }
+static inline Dual FMA(double a, const Dual& b, double c) { return FMA(mkd(a), b, mkd(c)); }
+static inline Dual FMA(const Dual& a, double b, double c) { return FMA(a, mkd(b), mkd(c)); }
+static inline double SQRT(double a) { return std::sqrt(a); }
+static inline Dual SQRT(const Dual& a) { Dual r; r.v = std::sqrt(a.v); for (int i = 0; i < 6; i++) r.d[i] = a.d[i] / (2.0 * r.v); return r; }
+
+// ---------------------------------------------------------------------------
+// sin(x): Cody & Waite (1980) additive range reduction by pi/2 with a
+// three-part constant, then the Taylor series of sin/cos on |r| <= pi/4
+// evaluated by Horner's rule.  Written out so that both implementations of the
+// tracker produce identical bits (library sin routines differ by an ulp).
+// Valid for |x| < 2^40; accuracy about 1 ulp on |x| < 1e6.
+static const double PIO2_1 = 1.5707963267948965579989817342720925807952880859375;
+static const double PIO2_2 = 6.123233995736766035868820147291818682e-17;
+static const double PIO2_3 = -1.4973849048591698329435081771059e-33;
+static const double TWO_OVER_PI = 0.63661977236758134307553505349005744813783858296183;
+static const double RND_MAGIC = 6755399441055744.0;  // 1.5 * 2^52
+
+struct SinCoef {
+  double s[10];  // (-1)^k / (2k+1)!, k = 0..9  (1, -1/3!, ..., -1/19!)
+  double c[11];  // (-1)^k / (2k)!,  k = 0..10 (1, -1/2!, ..., 1/20!)
+  SinCoef() {
+    double f = 1.0;  // running factorial, exact up to 20! as a double
+    for (int n = 1; n <= 21; n++) {
+      f = f * (double)n;
+      if (n % 2 == 1) { int k = (n - 1) / 2; if (k < 10) s[k] = ((k % 2) ? -1.0 : 1.0) / f; }
+      else { int k = n / 2; if (k < 11) c[k] = ((k % 2) ? -1.0 : 1.0) / f; }
+    }
+    s[0] = 1.0; c[0] = 1.0;
+  }
+};
+static const SinCoef SC;
+
+double sin_cw(double x) {
+  double k = (x * TWO_OVER_PI + RND_MAGIC) - RND_MAGIC;  // nearest integer
+  double r = std::fma(-k, PIO2_1, x);
+  r = std::fma(-k, PIO2_2, r);
+  r = std::fma(-k, PIO2_3, r);
+  long long q = (long long)k;
+  int quad = (int)(q & 3);
+  double z = r * r;
+  double res;
+  if (quad & 1) {  // cos r
+    double p = SC.c[10];
+    for (int i = 9; i >= 0; i--) p = std::fma(p, z, SC.c[i]);
+    res = p;
+  } else {  // sin r = r * (s0 + z*(s1 + ...))
+    double p = SC.s[9];
+    for (int i = 8; i >= 1; i--) p = std::fma(p, z, SC.s[i]);
+    res = std::fma(r * z, p, r);
+  }
+  return (quad & 2) ? -res : res;
+}
+static inline double SIN(double a) { return sin_cw(a); }
+static inline Dual SIN(const Dual& a) {
+  Dual r; r.v = sin_cw(a.v); double c = std::cos(a.v);
+  for (int i = 0; i < 6; i++) r.d[i] = c * a.d[i];
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter-based RNG.
+// Counter = (particle id, turn, element index, call index); key = (seed, 0).
+static inline void mulhilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
+  __uint128_t p = (__uint128_t)a * (__uint128_t)b;
+  *hi = (uint64_t)(p >> 64);
+  *lo = (uint64_t)p;
+}
+void philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+  uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint64_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; r++) {
+    uint64_t hi0, lo0, hi1, lo1;
+    mulhilo64(0xD2E7470EE14C6C93ULL, c0, &hi0, &lo0);
+    mulhilo64(0xCA5A826395121157ULL, c2, &hi1, &lo1);
+    uint64_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += 0x9E3779B97F4A7C15ULL;
+    k1 += 0xBB67AE8584CAA73BULL;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+// 53-bit uniform in [0, 1) from a 64-bit word.
+static inline double u01(uint64_t w) { return (double)(w >> 11) * (1.0 / 9007199254740992.0); }
+
+// Stream of uniforms for one (particle, turn, element): four per Philox call.
+struct Uniforms {
+  uint64_t ctr[4], key[2], buf[4];
+  int pos;
+  Uniforms(uint64_t seed, uint64_t pid, uint64_t turn, uint64_t elem) {
+    ctr[0] = pid; ctr[1] = turn; ctr[2] = elem; ctr[3] = 0;
+    key[0] = seed; key[1] = 0; pos = 4;
+  }
+  double next() {
+    if (pos == 4) { philox4x64_10(ctr, key, buf); ctr[3] += 1; pos = 0; }
+    return u01(buf[pos++]);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Photon spectrum for the quantum radiation model.  The number of photons per
+// unit energy fraction xi = u/u_c is proportional to G(xi) = int_xi^inf
+// K_{5/3}(t) dt, normalised by int_0^inf G = 5*pi/3.  Using the integral
+// representation K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt and exchanging
+// the order of integration, the survival function is
+//   S(xi) = int_xi^inf G(s) ds = int_0^inf exp(-xi cosh t) cosh(5t/3)/cosh^2 t dt,
+// and the cumulative distribution is F(xi) = 1 - S(xi)/(5 pi/3).  S is
+// evaluated by the trapezoidal rule in t (the integrand is even and analytic in
+// the strip |Im t| < pi/2, so the rule converges geometrically).
+static const int SPEC_K = 2048;
+static const double SPEC_XI_MIN = 1e-7, SPEC_XI_MAX = 40.0;
+struct Spectrum {
+  double xi[SPEC_K], F[SPEC_K];
+  Spectrum() {
+    const double norm = 5.0 * PI / 3.0, h = 0.05;
+    for (int i = 0; i < SPEC_K; i++) {
+      double e = (double)i / (double)(SPEC_K - 1);
+      double x = SPEC_XI_MIN * std::pow(SPEC_XI_MAX / SPEC_XI_MIN, e);
+      double s = 0.0;
+      for (int j = 0;; j++) {
+        double t = j * h;
+        double ch = std::cosh(t);
+        double g = std::exp(-x * ch) * std::cosh(5.0 * t / 3.0) / (ch * ch);
+        s += (j == 0 ? 0.5 : 1.0) * g;
+        if (x * ch > 60.0 && j > 10) break;
+      }
+      xi[i] = x;
+      F[i] = 1.0 - (h * s) / norm;
+    }
+  }
+  // Inverse CDF: power-law asymptote F ~ xi^(1/3) below the first knot,
+  // linear interpolation between knots, clamp above the last.
+  double sample(double u) const {
+    if (u < F[0]) { double q = u / F[0]; return xi[0] * q * q * q; }
+    if (u >= F[SPEC_K - 1]) return xi[SPEC_K - 1];
+    int lo = 0, hi = SPEC_K - 1;  // F[lo] <= u < F[hi]
+    while (hi - lo > 1) { int mid = (lo + hi) / 2; if (F[mid] <= u) lo = mid; else hi = mid; }
+    double w = (u - F[lo]) / (F[hi] - F[lo]);
+    return xi[lo] + w * (xi[hi] - xi[lo]);
+  }
+};
+static const Spectrum& spectrum() { static Spectrum s; return s; }
+
+// ---------------------------------------------------------------------------
+// Reference-derived constants (computed once per call on the host).
+struct RefConst {
+  double m0, q0, p0c, E0, beta0, gamma0, bg0, ib0, twoib0;
+  // radiation
+  double crad;   // (2/3) r_c m0 / p0c   [m]
+  double kq;     // (5 / (2 sqrt 3)) alpha q0^2  (mean photon count per gamma*h*L)
+  double uc15;   // 1.5 hbar c  [eV m]
+};
+static RefConst ref_const(const Reference& r) {
+  RefConst c;
+  c.m0 = r.mass0; c.q0 = r.q0; c.p0c = r.p0c;
+  c.E0 = std::sqrt(r.p0c * r.p0c + r.mass0 * r.mass0);
+  c.beta0 = r.p0c / c.E0;
+  c.gamma0 = c.E0 / r.mass0;
+  c.bg0 = r.p0c / r.mass0;
+  c.ib0 = c.E0 / r.p0c;
+  c.twoib0 = 2.0 * c.ib0;
+  const double rc = r.q0 * r.q0 * R_ELECTRON * M_ELECTRON / r.mass0;
+  c.crad = 2.0 * rc * r.mass0 / (3.0 * r.p0c);
+  c.kq = 5.0 * ALPHA_FS * r.q0 * r.q0 / (2.0 * std::sqrt(3.0));
+  c.uc15 = 1.5 * HBAR_C;
+  return c;
+}
+
+template <class T> static inline T mkv(double v);
+template <> inline double mkv<double>(double v) { return v; }
+template <> inline Dual mkv<Dual>(double v) { return mkd(v); }
+
+// ---------------------------------------------------------------------------
+// Particle state; opd = 1+delta, rv0v = 1/rvv and ep = opd*rv0v are derived
+// from delta and rvv and recomputed whenever those change (pure functions of
+// the stored state, so recomputation never changes a result).
+template <class T>
+struct Part {
+  T x, px, y, py, zeta, delta, ptau, rpp, rvv;
+  T opd, rv0v, ep;
+  int32_t state, at_turn, at_element;
+  int64_t id;
+};
+template <class T>
+static inline void derive(Part<T>& p) {
+  p.opd = 1.0 + p.delta;
+  p.rv0v = 1.0 / p.rvv;
+  p.ep = p.opd * p.rv0v;
+}
+
+// Energy update from a new ptau, using (1+delta)^2 = 1 + 2 ptau/beta0 + ptau^2
+// written in the cancellation-free form delta = u / (sqrt(1+u) + 1),
+// u = ptau (ptau + 2/beta0); then rpp = 1/(1+delta) and
+// rvv = (1+delta)/(1 + beta0 ptau).
+template <class T>
+static inline void energy_update(Part<T>& p, const RefConst& rc) {
+  T u = p.ptau * (p.ptau + rc.twoib0);
+  T s = SQRT(1.0 + u);
+  p.delta = u / (s + 1.0);
+  p.opd = 1.0 + p.delta;
+  p.rpp = 1.0 / p.opd;
+  p.rvv = p.opd / FMA(rc.beta0, p.ptau, 1.0);
+  p.rv0v = 1.0 / p.rvv;
+  p.ep = p.opd * p.rv0v;
+}
+
+template <class T>
+static inline void mark_lost(Part<T>& p, int code, int turn, int elem) {
+  p.state = code; p.at_turn = turn; p.at_element = elem;
+}
+
+// Exact drift of length L (thin-lens integration: drifts between kicks).
+//   pz = sqrt((1+delta)^2 - px^2 - py^2),  x += px L/pz,  y += py L/pz,
+//   zeta += L - (1+delta)/rvv * L/pz  (path length L(1+delta)/pz at speed beta).
+// A particle with (1+delta)^2 - px^2 - py^2 not in (0, inf) is lost (code -2)
+// with its coordinates unchanged.
+template <class T>
+static inline void drift(Part<T>& p, double L, int turn, int elem) {
+  T pt2 = FMA(p.px, p.px, p.py * p.py);
+  T t = FMA(p.opd, p.opd, -pt2);
+  double tv = val(t);
+  if (!(tv > 0.0 && tv < INFINITY)) { mark_lost(p, -2, turn, elem); return; }
+  T pz = SQRT(t);
+  T lpz = L / pz;
+  p.x = FMA(p.px, lpz, p.x);
+  p.y = FMA(p.py, lpz, p.y);
+  p.zeta = p.zeta + FMA(-p.ep, lpz, mkv<T>(L));
+}
+
+// Energy change by radiation: ptau += dpt, then the energy update; the
+// transverse momenta are scaled by (1+delta_new)/(1+delta_old) so that the
+// angles px/(1+delta), py/(1+delta) are unchanged (emission along the motion).
+template <class T>
+static inline void apply_energy_loss(Part<T>& p, T dpt, const RefConst& rc) {
+  T rpp_old = p.rpp;
+  p.ptau = p.ptau + dpt;
+  energy_update(p, rc);
+  T f = p.opd * rpp_old;
+  p.px = p.px * f;
+  p.py = p.py * f;
+}
+
+// Per-element host constants of a thin multipole: cn = knl_n/n!, sn = ksl_n/n!,
+// k0h = knl0*hxl/L_rad (0 when L_rad == 0), ilr2 = 1/L_rad^2,
+// crl = crad*L_rad, kql = kq*L_rad.
+struct MultConst {
+  int N;
+  double c[11], s[11];
+  double hxl, k0h, lrad, ilr2, crl, kql;
+};
+
+// Quantum model: Poisson number of photons with mean
+// nbar = (5/(2 sqrt 3)) alpha q0^2 gamma h L, energies u = u_c xi with
+// u_c = (3/2) hbar c gamma^3 h and xi drawn from the synchrotron spectrum.
+static const int KMAX_PHOTONS = 200;
+static inline void quantum_kick(Part<double>& p, double br, double bi, const MultConst& m,
+                                const RefConst& rc, uint64_t seed, int turn, int elem) {
+  double kk = std::fma(br, br, bi * bi);
+  double h = std::sqrt(kk * m.ilr2) * p.rpp;
+  double gam = std::fma(rc.bg0, p.ptau, rc.gamma0);
+  double nbar = (m.kql * gam) * h;
+  Uniforms U(seed, (uint64_t)p.id, (uint64_t)turn, (uint64_t)elem);
+  double u0 = U.next();
+  int k = 0;
+  double pk = std::exp(-nbar), F = pk;
+  while (u0 > F && k < KMAX_PHOTONS) { k++; pk = (pk * nbar) / (double)k; F = F + pk; }
+  if (k == 0) return;
+  const Spectrum& S = spectrum();
+  double sxi = 0.0;
+  for (int j = 0; j < k; j++) sxi = sxi + S.sample(U.next());
+  double uc = (rc.uc15 * (gam * gam * gam)) * h;
+  double dpt = -(uc * sxi) / rc.p0c;
+  apply_energy_loss(p, dpt, rc);
+}
+static inline void quantum_kick(Part<Dual>&, const Dual&, const Dual&, const MultConst&,
+                                const RefConst&, uint64_t, int, int) {}
+
+// Thin multipole: b = sum_n (knl_n + i ksl_n) z^n / n!, z = x + i y, by
+// Horner's rule from the highest order; px -= Re b, py += Im b.  With a
+// curvature hxl: px += hxl (1+delta) - knl0 hxl x / L_rad and
+// zeta -= hxl x / rvv (the thin dipole of the curved reference frame).
+// Radiation (mode 1 mean, 2 quantum) is applied once, after the kick, for
+// elements with L_rad > 0, using the field kick (Re b, Im b) only.
+template <class T>
+static inline void multipole(Part<T>& p, const MultConst& m, int rad_mode, const RefConst& rc,
+                             uint64_t seed, int turn, int elem) {
+  T br = mkv<T>(m.c[m.N]);
+  T bi = mkv<T>(m.s[m.N]);
+  for (int n = m.N - 1; n >= 0; n--) {
+    T nr = FMA(br, p.x, FMA(-bi, p.y, mkv<T>(m.c[n])));
+    T ni = FMA(br, p.y, FMA(bi, p.x, mkv<T>(m.s[n])));
+    br = nr; bi = ni;
+  }
+  p.px = p.px - br;
+  p.py = p.py + bi;
+  if (m.hxl != 0.0) {
+    p.px = FMA(m.hxl, p.opd, p.px);
+    p.px = FMA(-m.k0h, p.x, p.px);
+    p.zeta = FMA(-(m.hxl * p.rv0v), p.x, p.zeta);
+  }
+  if (rad_mode == 1 && m.lrad > 0.0) {
+    // Mean model: dE = -(2/3) r_c m0 c^2 beta^3 gamma^4 h^2 L_rad with the local
+    // curvature h = |field kick| / ((1+delta) L_rad).
+    T kk = FMA(br, br, bi * bi);
+    T h2 = (kk * m.ilr2) * (p.rpp * p.rpp);
+    T gam = FMA(rc.bg0, p.ptau, mkv<T>(rc.gamma0));
+    T bet = rc.beta0 * p.rvv;
+    T b3 = bet * bet * bet;
+    T g2 = gam * gam;
+    T g4 = g2 * g2;
+    T dpt = (-m.crl) * b3 * g4 * h2;
+    apply_energy_loss(p, dpt, rc);
+  } else if (rad_mode == 2 && m.lrad > 0.0) {
+    quantum_kick(p, br, bi, m, rc, seed, turn, elem);
+  }
+}
+
+// Prepared element: host constants of each type.
+struct Prep {
+  int type;
+  double L;                              // drift
+  MultConst m;                           // multipole
+  double krf, lagr, qv;                  // cavity
+  double r21, r43;                       // dipole edge
+  double M[36], d[6];                    // linear map in (x,px,y,py,zeta,ptau)
+  double r2;                             // aperture
+};
+
+static Prep prepare(const Element& e, const RefConst& rc) {
+  Prep q;
+  std::memset(&q, 0, sizeof(q));
+  q.type = e.type;
+  switch (e.type) {
+    case T_DRIFT: q.L = e.p[0]; break;
+    case T_MULTIPOLE: {
+      double fact = 1.0;
+      q.m.N = e.order;
+      for (int n = 0; n <= 10; n++) {
+        if (n > 0) fact = fact * (double)n;
+        q.m.c[n] = e.p[n] / fact;
+        q.m.s[n] = e.p[11 + n] / fact;
+      }
+      q.m.hxl = e.p[22];
+      q.m.lrad = e.p[23];
+      q.m.k0h = (q.m.lrad > 0.0) ? (e.p[0] * q.m.hxl) / q.m.lrad : 0.0;
+      q.m.ilr2 = (q.m.lrad > 0.0) ? 1.0 / (q.m.lrad * q.m.lrad) : 0.0;
+      q.m.crl = rc.crad * q.m.lrad;
+      q.m.kql = rc.kq * q.m.lrad;
+      break;
+    }
+    case T_CAVITY: {
+      const double V = e.p[0], f = e.p[1], lag = e.p[2];
+      q.krf = (2.0 * PI * f) / (rc.beta0 * C_LIGHT);
+      q.lagr = lag * PI / 180.0;
+      q.qv = (rc.q0 * V) / rc.p0c;
+      break;
+    }
+    case T_DIPEDGE: {
+      const double h = e.p[0], e1 = e.p[1], hgap = e.p[2], fint = e.p[3];
+      q.r21 = h * std::tan(e1);
+      const double psi = 2.0 * h * hgap * fint * (1.0 + std::sin(e1) * std::sin(e1)) / std::cos(e1);
+      q.r43 = -h * std::tan(e1 - psi);
+      break;
+    }
+    case T_LINEARMAP: {
+      // The table gives M, d on (x,px,y,py,zeta,pzeta), pzeta = ptau/beta0;
+      // convert to (..., ptau): row 5 times beta0, column 5 divided by beta0.
+      for (int i = 0; i < 6; i++) {
+        for (int j = 0; j < 6; j++) {
+          double v = e.p[6 * i + j];
+          if (i == 5 && j != 5) v = v * rc.beta0;
+          else if (j == 5 && i != 5) v = v * rc.ib0;
+          q.M[6 * i + j] = v;
+        }
+        q.d[i] = (i == 5) ? e.p[36 + i] * rc.beta0 : e.p[36 + i];
+      }
+      break;
+    }
+    case T_APERTURE: q.r2 = e.p[0] * e.p[0]; break;
+    default: break;
+  }
+  return q;
+}
+
+// One element.  Returns with p.state != 1 if the particle was lost here.
+template <class T>
+static inline void track_element(Part<T>& p, const Prep& q, int rad_mode, const RefConst& rc,
+                                 uint64_t seed, int turn, int elem) {
+  switch (q.type) {
+    case T_DRIFT: drift(p, q.L, turn, elem); break;
+    case T_MULTIPOLE: multipole(p, q.m, rad_mode, rc, seed, turn, elem); break;
+    case T_CAVITY: {
+      // Thin RF: phase lag - k zeta, k = 2 pi f/(beta0 c); energy gain q0 V sin(phase).
+      T phi = FMA(-q.krf, p.zeta, mkv<T>(q.lagr));
+      p.ptau = FMA(q.qv, SIN(phi), p.ptau);
+      energy_update(p, rc);
+      break;
+    }
+    case T_DIPEDGE:
+      p.px = FMA(q.r21, p.x, p.px);
+      p.py = FMA(q.r43, p.y, p.py);
+      break;
+    case T_LINEARMAP: {
+      T v[6] = {p.x, p.px, p.y, p.py, p.zeta, p.ptau};
+      T o[6];
+      for (int i = 0; i < 6; i++) {
+        T acc = mkv<T>(q.d[i]);
+        for (int j = 0; j < 6; j++) acc = FMA(q.M[6 * i + j], v[j], acc);
+        o[i] = acc;
+      }
+      p.x = o[0]; p.px = o[1]; p.y = o[2]; p.py = o[3]; p.zeta = o[4]; p.ptau = o[5];
+      energy_update(p, rc);
+      break;
+    }
+    case T_APERTURE: {
+      // Circular aperture: lost if x^2 + y^2 > r^2 (a point on the circle
+      // survives) or if x or y is not finite.
+      T rr = FMA(p.x, p.x, p.y * p.y);
+      if (!(val(rr) <= q.r2)) {
+        bool fin = std::isfinite(val(p.x)) && std::isfinite(val(p.y));
+        mark_lost(p, fin ? 0 : -1, turn, elem);
+      }
+      break;
+    }
+    default: break;
+  }
+}
+
+// End-of-turn guard: |x| or |y| above 1 m (or not finite) is lost (code -3)
+// at the last element of the turn.
+template <class T>
+static inline void turn_guard(Part<T>& p, int turn, int n_el) {
+  if (!(std::fabs(val(p.x)) <= 1.0 && std::fabs(val(p.y)) <= 1.0)) mark_lost(p, -3, turn, n_el - 1);
+}
+
+}  // namespace xo
+
+using namespace xo;
+
+extern "C" {
+
+// Tracks n particles (SoA arrays, updated in place) through n_turns turns of
+// the lattice, starting at absolute turn start_turn.  rad_mode: 0 off, 1 mean,
+// 2 quantum (Philox4x64-10 keyed by seed).  Particles with state != 1 on entry
+// are left untouched.  Lost particles keep their coordinates at the loss point
+// and record state, at_turn (absolute, 0-based) and at_element; survivors get
+// at_turn = start_turn + n_turns, at_element = 0.  Returns 0, or -1 on an
+// invalid argument.
+int xo_track(const Element* el, int64_t n_el, const Reference* ref, int rad_mode, uint64_t seed,
+             double* x, double* px, double* y, double* py, double* zeta, double* delta,
+             double* ptau, double* rpp, double* rvv, int32_t* state, int32_t* at_turn,
+             int32_t* at_element, const int64_t* pid, int64_t n, int64_t start_turn,
+             int64_t n_turns) {
+  if (!el || !ref || n_el <= 0 || n < 0 || n_turns < 0 || rad_mode < 0 || rad_mode > 2) return -1;
+  const RefConst rc = ref_const(*ref);
+  std::vector<Prep> prep(n_el);
+  for (int64_t e = 0; e < n_el; e++) {
+    if (el[e].type == T_MULTIPOLE && (el[e].order < 0 || el[e].order > 10)) return -1;
+    prep[e] = prepare(el[e], rc);
+  }
+  for (int64_t i = 0; i < n; i++) {
+    Part<double> p;
+    p.x = x[i]; p.px = px[i]; p.y = y[i]; p.py = py[i]; p.zeta = zeta[i];
+    p.delta = delta[i]; p.ptau = ptau[i]; p.rpp = rpp[i]; p.rvv = rvv[i];
+    p.state = state[i]; p.at_turn = at_turn[i]; p.at_element = at_element[i]; p.id = pid[i];
+    if (p.state != 1) continue;
+    derive(p);
+    for (int64_t t = start_turn; t < start_turn + n_turns && p.state == 1; t++) {
+      for (int64_t e = 0; e < n_el; e++) {
+        track_element(p, prep[e], rad_mode, rc, seed, (int)t, (int)e);
+        if (p.state != 1) break;
+      }
+      if (p.state == 1) turn_guard(p, (int)t, (int)n_el);
+    }
+    if (p.state == 1) { p.at_turn = (int32_t)(start_turn + n_turns); p.at_element = 0; }
+    x[i] = p.x; px[i] = p.px; y[i] = p.y; py[i] = p.py; zeta[i] = p.zeta;
+    delta[i] = p.delta; ptau[i] = p.ptau; rpp[i] = p.rpp; rvv[i] = p.rvv;
+    state[i] = p.state; at_turn[i] = p.at_turn; at_element[i] = p.at_element;
+  }
+  return 0;
+}
+
+// Differentiable tracking of one particle given in canonical coordinates
+// z = (x, px, y, py, zeta, pzeta), pzeta = ptau/beta0, for n_turns turns
+// (radiation 0 or 1).  Writes the final z and the Jacobian dz_out/dz_in
+// (row-major 6x6).  If along != NULL it also receives, after every element of
+// the first turn, 6 coordinates followed by the 36 Jacobian entries
+// (n_el * 42 doubles).  Returns 0, 1 if the particle was lost, -1 on bad input.
+int xo_track_jacobian(const Element* el, int64_t n_el, const Reference* ref, int rad_mode,
+                      const double* z0, int64_t n_turns, double* z_out, double* M_out,
+                      double* along) {
+  if (!el || !ref || n_el <= 0 || rad_mode < 0 || rad_mode > 1) return -1;
+  const RefConst rc = ref_const(*ref);
+  std::vector<Prep> prep(n_el);
+  for (int64_t e = 0; e < n_el; e++) prep[e] = prepare(el[e], rc);
+  Part<Dual> p;
+  Dual* in[6] = {&p.x, &p.px, &p.y, &p.py, &p.zeta, &p.ptau};
+  for (int k = 0; k < 6; k++) { *in[k] = mkd(z0[k]); in[k]->d[k] = 1.0; }
+  p.ptau = p.ptau * rc.beta0;  // pzeta -> ptau
+  p.state = 1; p.at_turn = 0; p.at_element = 0; p.id = 0;
+  energy_update(p, rc);
+  auto out6 = [&](double* zo, double* Mo) {
+    Dual pz = p.ptau * rc.ib0;
+    const Dual* o[6] = {&p.x, &p.px, &p.y, &p.py, &p.zeta, &pz};
+    for (int i = 0; i < 6; i++) {
+      zo[i] = o[i]->v;
+      for (int j = 0; j < 6; j++) Mo[6 * i + j] = o[i]->d[j];
+    }
+  };
+  for (int64_t t = 0; t < n_turns; t++) {
+    for (int64_t e = 0; e < n_el; e++) {
+      track_element(p, prep[e], rad_mode, rc, 0, (int)t, (int)e);
+      if (p.state != 1) return 1;
+      if (along && t == 0) out6(along + 42 * e, along + 42 * e + 6);
+    }
+  }
+  out6(z_out, M_out);
+  return 0;
+}
+
+// Closed orbit by Newton iteration on the one-turn map using the exact
+// Jacobian.  dim = 6: fixed point of all six coordinates (needs RF);
+// dim = 4: fixed point of (x,px,y,py) at the given pzeta (zeta is free).
+// z is the initial guess and receives the orbit.  Returns the iteration count,
+// or -1 on failure.
+int xo_closed_orbit(const Element* el, int64_t n_el, const Reference* ref, int rad_mode, int dim,
+                    double* z) {
+  if (dim != 4 && dim != 6) return -1;
+  for (int it = 0; it < 40; it++) {
+    double zo[6], M[36];
+    if (xo_track_jacobian(el, n_el, ref, rad_mode, z, 1, zo, M, nullptr) != 0) return -1;
+    double A[6][7];
+    double res = 0.0;
+    for (int i = 0; i < dim; i++) {
+      for (int j = 0; j < dim; j++) A[i][j] = M[6 * i + j] - (i == j ? 1.0 : 0.0);
+      A[i][dim] = -(zo[i] - z[i]);
+      res = std::max(res, std::fabs(zo[i] - z[i]));
+    }
+    if (res < 1e-15) return it;
+    // Gaussian elimination with partial pivoting.
+    for (int c = 0; c < dim; c++) {
+      int piv = c;
+      for (int r = c + 1; r < dim; r++) if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+      for (int k = 0; k <= dim; k++) std::swap(A[c][k], A[piv][k]);
+      if (A[c][c] == 0.0) return -1;
+      for (int r = c + 1; r < dim; r++) {
+        double f = A[r][c] / A[c][c];
+        for (int k = c; k <= dim; k++) A[r][k] -= f * A[c][k];
+      }
+    }
+    double dz[6] = {0, 0, 0, 0, 0, 0};
+    for (int r = dim - 1; r >= 0; r--) {
+      double s = A[r][dim];
+      for (int k = r + 1; k < dim; k++) s -= A[r][k] * dz[k];
+      dz[r] = s / A[r][r];
+    }
+    for (int i = 0; i < dim; i++) z[i] += dz[i];
+  }
+  return -1;
+}
+
+// Test hooks for the building blocks.
+double xo_sin(double x) { return sin_cw(x); }
+void xo_philox4x64_10(const uint64_t* ctr, const uint64_t* key, uint64_t* out) { philox4x64_10(ctr, key, out); }
+double xo_uniform(uint64_t seed, uint64_t pid, uint64_t turn, uint64_t elem, int64_t index) {
+  Uniforms U(seed, pid, turn, elem);
+  double u = 0.0;
+  for (int64_t k = 0; k <= index; k++) u = U.next();
+  return u;
+}
+int xo_spectrum_size(void) { return SPEC_K; }
+void xo_spectrum_table(double* xi, double* F) {
+  const Spectrum& S = spectrum();
+  for (int i = 0; i < SPEC_K; i++) { xi[i] = S.xi[i]; F[i] = S.F[i]; }
+}
+double xo_spectrum_sample(double u) { return spectrum().sample(u); }
+// Reference-derived constants, for tests: E0, beta0, gamma0, crad, kq, uc15.
+void xo_ref_constants(const Reference* ref, double* out) {
+  RefConst c = ref_const(*ref);
+  out[0] = c.E0; out[1] = c.beta0; out[2] = c.gamma0; out[3] = c.crad; out[4] = c.kq; out[5] = c.uc15;
+}
+
+}  // extern "C"

@@ -1,0 +1,522 @@
+"""Pins of the oracle tracker against closed forms, invariants, special cases,
+independent libraries and high-precision brute force (CPU only).
+
+Each test checks the oracle against something other than itself, chosen so
+that a dropped term, a wrong sign or index, or a transposed operand in one of
+its maps fails at least one of them.
+"""
+import math
+
+import mpmath
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_00317_gb300 import inputs as I
+
+J6 = np.zeros((6, 6))
+for k in range(3):
+    J6[2 * k, 2 * k + 1] = 1.0
+    J6[2 * k + 1, 2 * k] = -1.0
+
+PROTON = I.proton_reference(450e9)
+
+
+def one(ref, x=0.0, px=0.0, y=0.0, py=0.0, zeta=0.0, delta=0.0):
+    return I.make_particles(ref, [x], [px], [y], [py], [zeta], [delta])
+
+
+def hp_kin(ref, delta):
+    """High-precision kinematics (mpmath) of a particle with momentum deviation delta."""
+    m0, _, p0c = [mpmath.mpf(v) for v in ref]
+    d = mpmath.mpf(delta)
+    E0 = mpmath.sqrt(p0c ** 2 + m0 ** 2)
+    E = mpmath.sqrt((p0c * (1 + d)) ** 2 + m0 ** 2)
+    beta0 = p0c / E0
+    beta = p0c * (1 + d) / E
+    ptau = (E - E0) / p0c
+    return dict(E0=E0, beta0=beta0, beta=beta, ptau=ptau, rvv=beta / beta0)
+
+
+# --------------------------------------------------------------------------
+# Exact drift
+
+def test_drift_closed_form_highprec():
+    """Drift against the straight-line closed form in 40-digit arithmetic."""
+    mpmath.mp.dps = 40
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        x, px, y, py, z = rng.normal(0, [1e-3, 1e-4, 1e-3, 1e-4, 1e-2])
+        d = rng.normal(0, 1e-3)
+        L = float(rng.uniform(0.1, 20.0))
+        p = one(PROTON, x, px, y, py, z, d)
+        el = I.table([I.drift(L)])
+        o = oracle.track(el, PROTON, p, 1)
+        k = hp_kin(PROTON, p["delta"][0])
+        opd = 1 + mpmath.mpf(p["delta"][0])
+        PX, PY = mpmath.mpf(p["px"][0]), mpmath.mpf(p["py"][0])
+        pz = mpmath.sqrt(opd ** 2 - PX ** 2 - PY ** 2)
+        # path length L(1+delta)/pz travelled at beta: zeta += L - beta0/beta * path
+        xe = mpmath.mpf(p["x"][0]) + PX * L / pz
+        ye = mpmath.mpf(p["y"][0]) + PY * L / pz
+        ze = mpmath.mpf(p["zeta"][0]) + L - (k["beta0"] / k["beta"]) * L * opd / pz
+        # rounding bound scales with the operands (the sum may cancel)
+        assert abs(o["x"][0] - float(xe)) <= 4e-16 * (abs(x) + abs(px) * L)
+        assert abs(o["y"][0] - float(ye)) <= 4e-16 * (abs(y) + abs(py) * L)
+        # zeta change is a small difference of O(L) terms: absolute bound
+        assert abs(o["zeta"][0] - float(ze)) <= 8e-16 * L
+        assert o["px"][0] == p["px"][0] and o["delta"][0] == p["delta"][0]
+
+
+def test_drift_reversible():
+    """A drift of -L undoes a drift of +L to rounding."""
+    rng = np.random.default_rng(2)
+    n = 200
+    p = I.make_particles(PROTON, rng.normal(0, 1e-3, n), rng.normal(0, 1e-4, n),
+                         rng.normal(0, 1e-3, n), rng.normal(0, 1e-4, n),
+                         rng.normal(0, 0.1, n), rng.normal(0, 1e-3, n))
+    el = I.table([I.drift(7.3), I.drift(-7.3)])
+    o = oracle.track(el, PROTON, p, 1)
+    for k in ("x", "y"):
+        assert np.max(np.abs(o[k] - p[k])) <= 4e-18 + 4 * np.spacing(np.max(np.abs(p[k])))
+    assert np.max(np.abs(o["zeta"] - p["zeta"])) < 1e-15
+
+
+def test_drift_invalid_momentum_lost():
+    p = one(PROTON, px=0.8, py=0.7)  # px^2 + py^2 > (1+delta)^2
+    o = oracle.track(I.table([I.drift(1.0), I.drift(1.0)]), PROTON, p, 3)
+    assert o["state"][0] == -2 and o["at_turn"][0] == 0 and o["at_element"][0] == 0
+    assert o["x"][0] == p["x"][0] and o["zeta"][0] == p["zeta"][0]
+
+
+# --------------------------------------------------------------------------
+# Thin multipole
+
+@pytest.mark.parametrize("order", list(range(11)))
+def test_multipole_kick_vs_bruteforce(order):
+    """Horner kick vs the term-by-term sum with mpmath powers."""
+    mpmath.mp.dps = 40
+    rng = np.random.default_rng(10 + order)
+    knl = rng.normal(0, 1, order + 1) * 10.0 ** -np.arange(order + 1)
+    ksl = rng.normal(0, 1, order + 1) * 10.0 ** -np.arange(order + 1)
+    el = I.table([I.multipole(knl=knl, ksl=ksl, order=order)])
+    for _ in range(5):
+        x, y = rng.normal(0, 0.01, 2)
+        px, py = rng.normal(0, 1e-4, 2)
+        p = one(PROTON, x, px, y, py, 0.0, 1e-4)
+        o = oracle.track(el, PROTON, p, 1)
+        z = mpmath.mpc(x, y)
+        b = mpmath.mpc(0)
+        scale = mpmath.mpf(0)
+        for n in range(order + 1):
+            term = mpmath.mpc(knl[n], ksl[n]) * z ** n / math.factorial(n)
+            b += term
+            scale += abs(term)
+        tol = 8e-16 * float(scale) + 1e-20
+        assert abs(o["px"][0] - float(px - b.real)) <= tol + 1e-16 * abs(px)
+        assert abs(o["py"][0] - float(py + b.imag)) <= tol + 1e-16 * abs(py)
+        assert o["x"][0] == x and o["y"][0] == y
+
+
+def test_multipole_sign_conventions():
+    """Normal quad focuses x (dpx=-kx, dpy=+ky); skew quad dpx=+ky, dpy=+kx;
+    sextupole dpx=-(k2/2)(x^2-y^2), dpy=k2 x y."""
+    x, y = 3e-3, -2e-3
+    cases = [
+        (I.multipole(knl=[0, 0.1]), -0.1 * x, 0.1 * y),
+        (I.multipole(ksl=[0, 0.1]), 0.1 * y, 0.1 * x),
+        (I.multipole(knl=[0, 0, 0.4]), -0.2 * (x * x - y * y), 0.4 * x * y),
+        (I.multipole(knl=[1e-4]), -1e-4, 0.0),
+        (I.multipole(ksl=[1e-4]), 0.0, 1e-4),
+    ]
+    for row, dpx, dpy in cases:
+        o = oracle.track(I.table([row]), PROTON, one(PROTON, x=x, y=y), 1)
+        assert o["px"][0] == pytest.approx(dpx, rel=1e-14, abs=1e-22)
+        assert o["py"][0] == pytest.approx(dpy, rel=1e-14, abs=1e-22)
+
+
+def test_multipole_curvature_terms():
+    """Thin dipole of the curved frame: px += hxl(1+delta) - knl0 hxl x/L,
+    zeta -= hxl x / rvv (evaluated in high precision)."""
+    mpmath.mpf.dps = 40
+    hxl, L = 1.3e-3, 3.575
+    el = I.table([I.multipole(knl=[hxl], hxl=hxl, lrad=L)])
+    for d in (-2e-3, 0.0, 1.5e-3):
+        x = 4e-3
+        p = one(PROTON, x=x, delta=d)
+        o = oracle.track(el, PROTON, p, 1)
+        k = hp_kin(PROTON, d)
+        px = -hxl + hxl * (1 + mpmath.mpf(p["delta"][0])) - hxl * hxl * x / L
+        zeta = -hxl * x / k["rvv"]
+        assert o["px"][0] == pytest.approx(float(px), rel=1e-12, abs=1e-19)
+        assert o["zeta"][0] == pytest.approx(float(zeta), rel=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Linear optics: FODO phase advance, symplecticity, invariants
+
+def test_fodo_cell_phase_advance():
+    """Thin FODO with f = 5 m and 2 m drifts: cos mu = 1 - L^2/(2 f^2) = 0.92."""
+    cell = I.table([I.multipole(knl=[0, 0.2]), I.drift(2.0), I.multipole(knl=[0, -0.2]), I.drift(2.0)])
+    _, M = oracle.track_jacobian(cell, PROTON, np.zeros(6))
+    assert 0.5 * np.trace(M[:2, :2]) == pytest.approx(0.92, abs=1e-14)
+    assert 0.5 * np.trace(M[2:4, 2:4]) == pytest.approx(0.92, abs=1e-14)
+
+
+def test_fodo10_ring_tune():
+    """The FODO-10 ring (sextupoles off the closed orbit do not act linearly)
+    has Q = 10 arccos(0.92)/(2 pi) = 0.6408..."""
+    el, ref = I.fodo10()
+    co = oracle.closed_orbit(el, ref, dim=6)
+    _, M = oracle.track_jacobian(el, ref, co)
+    # cos(2 pi Q) with Q = 10 arccos(0.92)/(2 pi); the trace fixes Q up to 1-Q
+    assert 0.5 * np.trace(M[:2, :2]) == pytest.approx(math.cos(10 * math.acos(0.92)), abs=1e-12)
+    assert 0.5 * np.trace(M[2:4, 2:4]) == pytest.approx(math.cos(10 * math.acos(0.92)), abs=1e-12)
+    assert np.max(np.abs(co)) < 1e-14
+
+
+@pytest.mark.parametrize("which", ["fodo10", "lhc_cells"])
+def test_symplectic_one_turn(which):
+    """M^T J M = J to 1e-13 for the analytic one-turn Jacobian in canonical
+    (x, px, y, py, zeta, pzeta), radiation off, at an off-axis point."""
+    if which == "fodo10":
+        el, ref = I.fodo10()
+        z0 = np.array([2e-4, 1e-5, -1e-4, 2e-5, 0.05, 2e-4])
+    else:
+        full, ref = I.lhc_ring(n_cells=8)
+        el = full
+        z0 = np.array([1e-3, 1e-5, 1e-3, -1e-5, 0.01, 1e-4])
+    _, M = oracle.track_jacobian(el, ref, z0)
+    E = M.T @ J6 @ M - J6
+    assert np.max(np.abs(E)) < 1e-13 * max(1.0, np.max(np.abs(M)) ** 2)
+
+
+def _rot6(mu, beta=1.0):
+    M = np.eye(6)
+    c, s = math.cos(mu), math.sin(mu)
+    M[0, 0], M[0, 1], M[1, 0], M[1, 1] = c, beta * s, -s / beta, c
+    return M
+
+
+def test_courant_snyder_action_conserved():
+    """Linear lattice (linear-map elements and thin quadrupoles, delta = 0):
+    the Courant-Snyder action from the one-turn matrix is conserved to 1e-13
+    over 1e4 turns.  The linear maps are exact shears (dyadic entries, det = 1
+    exactly) so only the tracker's own rounding can change the action."""
+    S = np.eye(6)
+    S[0, 1] = 2.0
+    S[2, 3] = 2.0
+    el = I.table([I.multipole(knl=[0, 0.25]), I.linear_map(S), I.multipole(knl=[0, -0.25]), I.linear_map(S)])
+    _, M = oracle.track_jacobian(el, PROTON, np.zeros(6))
+    A = M[:2, :2]
+    c = 0.5 * np.trace(A)
+    s = math.copysign(math.sqrt(1 - c * c), A[0, 1])
+    beta, alpha = A[0, 1] / s, (A[0, 0] - A[1, 1]) / (2 * s)
+    gamma = (1 + alpha ** 2) / beta
+    rng = np.random.default_rng(3)
+    n = 16
+    p = I.make_particles(PROTON, rng.normal(0, 1e-3, n), rng.normal(0, 1e-4, n),
+                         np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n))
+    J0 = gamma * p["x"] ** 2 + 2 * alpha * p["x"] * p["px"] + beta * p["px"] ** 2
+    o = oracle.track(el, PROTON, p, 10000)
+    J1 = gamma * o["x"] ** 2 + 2 * alpha * o["x"] * o["px"] + beta * o["px"] ** 2
+    assert np.all(o["state"] == 1)
+    assert np.max(np.abs(J1 / J0 - 1)) < 1e-13
+
+
+def test_henon_map():
+    """Rotation by mu (beta = 1, alpha = 0) + thin sextupole k2 on y = 0 is the
+    Henon map: with X = (k2/2) x, P = (k2/2) px, (X, P) -> R(mu)(X, P - X^2).
+    Iterates agree with a 40-digit evaluation to 1e-12 relative for 1000 turns."""
+    mpmath.mp.dps = 40
+    mu, k2 = 2 * math.pi * 0.2114, 2.0
+    el = I.table([I.multipole(knl=[0, 0, k2]), I.linear_map(_rot6(mu))])
+    starts = [0.05, 0.1, 0.2]
+    p = I.make_particles(PROTON, [s / (k2 / 2) for s in starts], np.zeros(3), np.zeros(3),
+                         np.zeros(3), np.zeros(3), np.zeros(3))
+    o = oracle.track(el, PROTON, p, 1000)
+    c, s = mpmath.cos(mpmath.mpf(mu)), mpmath.sin(mpmath.mpf(mu))
+    for i, X0 in enumerate(starts):
+        X, P = mpmath.mpf(p["x"][i]) * k2 / 2, mpmath.mpf(0)
+        for _ in range(1000):
+            P = P - X * X
+            X, P = c * X + s * P, -s * X + c * P
+        assert o["state"][i] == 1
+        assert o["x"][i] * k2 / 2 == pytest.approx(float(X), rel=1e-12, abs=1e-14)
+        assert o["px"][i] * k2 / 2 == pytest.approx(float(P), rel=1e-12, abs=1e-14)
+
+
+def test_linear_map_element():
+    rng = np.random.default_rng(4)
+    M = np.eye(6) + rng.normal(0, 1e-2, (6, 6))
+    d = rng.normal(0, 1e-6, 6)
+    el = I.table([I.linear_map(M, d)])
+    z0 = np.array([1e-3, 2e-5, -1e-3, 1e-5, 0.02, 3e-4])
+    z1, J = oracle.track_jacobian(el, PROTON, z0)
+    assert np.allclose(z1, M @ z0 + d, rtol=1e-14, atol=1e-19)
+    assert np.allclose(J, M, rtol=1e-13, atol=1e-15)
+
+
+def test_dipedge_matrix():
+    h, e1, hgap, fint = 1 / 500.0, 0.03, 0.02, 0.5
+    el = I.table([I.dipedge(h, e1, hgap, fint)])
+    _, M = oracle.track_jacobian(el, PROTON, np.zeros(6))
+    psi = 2 * h * hgap * fint * (1 + math.sin(e1) ** 2) / math.cos(e1)
+    assert M[1, 0] == pytest.approx(h * math.tan(e1), rel=1e-15)
+    assert M[3, 2] == pytest.approx(-h * math.tan(e1 - psi), rel=1e-15)
+    assert np.linalg.det(M) == pytest.approx(1.0, abs=1e-15)
+    M2 = M.copy(); M2[1, 0] = 0; M2[3, 2] = 0
+    assert np.array_equal(M2, np.eye(6))
+
+
+# --------------------------------------------------------------------------
+# RF cavity and energy variables
+
+def test_rf_energy_identity():
+    """After an RF kick: (1+delta)^2 = 1 + 2 ptau/beta0 + ptau^2, rpp (1+delta) = 1,
+    rvv = beta/beta0 of the particle (high-precision kinematics)."""
+    mpmath.mp.dps = 40
+    el = I.table([I.cavity(5e6, 400e6, 30.0)])
+    rng = np.random.default_rng(5)
+    n = 50
+    p = I.make_particles(PROTON, np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n),
+                         rng.normal(0, 0.2, n), rng.normal(0, 1e-3, n))
+    o = oracle.track(el, PROTON, p, 1)
+    rc = oracle.ref_constants(PROTON)
+    for i in range(n):
+        pt = mpmath.mpf(o["ptau"][i])
+        lhs = (1 + mpmath.mpf(o["delta"][i])) ** 2
+        rhs = 1 + 2 * pt / mpmath.mpf(rc["beta0"]) + pt ** 2
+        assert abs(float(lhs - rhs)) < 4e-16
+        assert o["rpp"][i] * (1 + o["delta"][i]) == pytest.approx(1.0, abs=3e-16)
+        k = hp_kin(PROTON, o["delta"][i])
+        assert o["rvv"][i] == pytest.approx(float(k["rvv"]), rel=2e-15)
+        # energy gain: q V sin(lag - k zeta)
+        phi = math.radians(30.0) - 2 * math.pi * 400e6 / (rc["beta0"] * I.C_LIGHT) * p["zeta"][i]
+        assert o["ptau"][i] - p["ptau"][i] == pytest.approx(5e6 / 450e9 * math.sin(phi), rel=1e-9, abs=1e-18)
+
+
+def test_fodo10_synchrotron_tune():
+    """Small-amplitude synchrotron tune of FODO-10 against
+    cos(2 pi Qs) = 1 + eta C q V omega cos(lag) / (2 beta0^2 p0c c),
+    eta = -1/gamma0^2 (no bends)."""
+    el, ref = I.fodo10()
+    co = oracle.closed_orbit(el, ref, dim=6)
+    _, M = oracle.track_jacobian(el, ref, co)
+    rc = oracle.ref_constants(ref)
+    eta = -1.0 / rc["gamma0"] ** 2
+    C = 40.0
+    omega = 2 * math.pi * 400e6
+    cs = 1 + eta * C * 1e6 * omega * 1.0 / (2 * rc["beta0"] ** 2 * ref[2] * I.C_LIGHT)
+    assert 0.5 * np.trace(M[4:, 4:]) == pytest.approx(cs, abs=1e-13)
+
+
+def test_sin_vs_libm():
+    xs = np.concatenate([np.linspace(-50, 50, 20001), np.random.default_rng(6).uniform(-1e5, 1e5, 5000)])
+    worst = 0.0
+    for x in xs:
+        a, b = oracle.sin(float(x)), math.sin(float(x))
+        worst = max(worst, abs(a - b) / max(np.spacing(abs(b)), 5e-324))
+    assert worst <= 2.0
+
+
+# --------------------------------------------------------------------------
+# Aperture and loss bookkeeping
+
+def test_aperture_and_guard():
+    r = 0.02
+    el = I.table([I.aperture(r), I.drift(1.0)])
+    xs = [0.0, r, 0.019, 0.014, 0.0142, float("nan"), 0.5]
+    ys = [0.0, 0.0, 0.0, 0.014, 0.0142, 0.0, 0.0]
+    p = I.make_particles(PROTON, xs, np.zeros(7), ys, np.zeros(7), np.zeros(7), np.zeros(7))
+    p["state"][:] = 1
+    o = oracle.track(el, PROTON, p, 2, start_turn=5)
+    # on the circle survives; 0.014*sqrt(2) < r survives; 0.0142*sqrt(2) > r lost
+    assert list(o["state"]) == [1, 1, 1, 1, 0, -1, 0]
+    assert list(o["at_turn"]) == [7, 7, 7, 7, 5, 5, 5]
+    assert o["x"][4] == 0.0142 and o["at_element"][4] == 0
+    # end-of-turn guard (|x| > 1 m) with no aperture
+    p2 = one(PROTON, x=1.5)
+    o2 = oracle.track(I.table([I.drift(1.0)]), PROTON, p2, 3)
+    assert o2["state"][0] == -3 and o2["at_turn"][0] == 0 and o2["at_element"][0] == 0
+
+
+def test_segment_resume_bitwise():
+    """track(a) then track(b) from turn a equals track(a+b), radiation included."""
+    el, ref, _ = I.lepton_ring(n_cells=4, E0=5e9, v_total=30e6)
+    p = I.matched_gaussian(el, ref, 20, 1e-3, 1e-3, seed=7)
+    for mode in (0, 1, 2):
+        full = oracle.track(el, ref, p, 30, rad_mode=mode, seed=11)
+        a = oracle.track(el, ref, p, 12, rad_mode=mode, seed=11)
+        b = oracle.track(el, ref, a, 18, start_turn=12, rad_mode=mode, seed=11)
+        for k in oracle.FLOAT_FIELDS + oracle.INT_FIELDS:
+            assert np.array_equal(full[k], b[k]), (mode, k)
+
+
+# --------------------------------------------------------------------------
+# Random numbers and the photon spectrum
+
+def test_philox_vs_numpy():
+    """Philox4x64-10 known answers from numpy's independent implementation
+    (numpy increments the counter before each block)."""
+    for key0, c0, c1 in [(5, 0, 0), (20231001, 123456789, 7), (2 ** 63 + 11, 2 ** 64 - 2, 99)]:
+        bg = np.random.Philox(key=np.array([key0, 0], dtype=np.uint64),
+                              counter=np.array([c0, c1, 0, 0], dtype=np.uint64))
+        ref = bg.random_raw(4)
+        got = oracle.philox4x64_10([c0 + 1, c1, 0, 0], [key0, 0])
+        assert np.array_equal(ref.astype(np.uint64), got)
+
+
+def test_uniforms_statistics():
+    from scipy import stats
+    u = np.array([oracle.uniform(3, pid, 17, 42, j) for pid in range(2000) for j in range(5)])
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+    assert abs(u.mean() - 0.5) < 5 * math.sqrt(1 / 12 / u.size)
+
+
+def test_spectrum_cdf_vs_bessel_quadrature():
+    """The tabulated CDF of xi against scipy's K_{5/3} integrated by quad:
+    F(xi) = (3/(5 pi)) int_0^xi ds int_s^inf K_{5/3}(t) dt
+          = (3/(5 pi)) [xi G(xi) + int_0^xi t K_{5/3}(t) dt]  (integration by parts)."""
+    from scipy import integrate, special
+    xi, F = oracle.spectrum_table()
+    G = lambda s: integrate.quad(lambda t: special.kv(5 / 3, t), s, np.inf, limit=200)[0]
+    for target in (1e-5, 1e-3, 0.05, 0.3, 1.0, 3.0, 8.0):
+        i = int(np.argmin(np.abs(xi - target)))
+        s = xi[i]
+        val = s * G(s) + integrate.quad(lambda t: t * special.kv(5 / 3, t), 0, s, limit=200)[0]
+        assert F[i] == pytest.approx(3 / (5 * math.pi) * val, rel=2e-7, abs=1e-12)
+
+
+def test_spectrum_table_moments():
+    """Mean and second moment of the sampled xi (exactly integrated over the
+    piecewise-linear inverse CDF) against <xi> = 8/(15 sqrt 3), <xi^2> = 11/27."""
+    xi, F = oracle.spectrum_table()
+    # below the first knot xi = xi0 (u/F0)^3: int = xi0 F0/4, int xi^2 = xi0^2 F0/7
+    m1 = xi[0] * F[0] / 4
+    m2 = xi[0] ** 2 * F[0] / 7
+    dF = np.diff(F)
+    a, b = xi[:-1], xi[1:]
+    m1 += np.sum(dF * (a + b) / 2)
+    m2 += np.sum(dF * (a * a + a * b + b * b) / 3)
+    m1 += xi[-1] * (1 - F[-1])
+    m2 += xi[-1] ** 2 * (1 - F[-1])
+    assert m1 == pytest.approx(8 / (15 * math.sqrt(3)), rel=2e-5)
+    assert m2 == pytest.approx(11 / 27, rel=2e-4)
+    # sampled check
+    u = np.random.default_rng(8).random(200000)
+    s = np.array([oracle.spectrum_sample(v) for v in u])
+    assert s.mean() == pytest.approx(8 / (15 * math.sqrt(3)), rel=5 * s.std() / math.sqrt(s.size) / s.mean())
+
+
+# --------------------------------------------------------------------------
+# Synchrotron radiation
+
+def test_radiation_mean_single_slice():
+    """Energy lost in one dipole slice by an on-axis electron:
+    U = C_gamma E^4 h^2 L / (2 pi), C_gamma = 8.846e-5 m/GeV^3 (beta -> 1)."""
+    ref = I.electron_reference(45.6e9)
+    theta, L = 2 * math.pi / 2400, 3.575
+    el = I.table([I.multipole(knl=[theta], hxl=theta, lrad=L)])
+    o = oracle.track(el, ref, one(ref), 1, rad_mode=1)
+    E0 = 45.6
+    U = 8.846e-5 * E0 ** 4 * (theta / L) ** 2 * L / (2 * math.pi) * 1e9
+    assert -o["ptau"][0] * ref[2] == pytest.approx(U, rel=2e-4)
+    # angles kept: px/(1+delta) unchanged by the emission (px = 0 here after
+    # the curvature kick cancels the field kick on axis)
+    assert abs(o["px"][0]) < 1e-18
+
+
+def test_radiation_damping_partition():
+    """Lepton ring with mean radiation: the one-turn eigenvalues at the 6D
+    closed orbit give J_x ~ 1, J_y ~ 1, J_z ~ 2 (separated-function thin ring)
+    and J_x + J_y + J_z = 4 (Robinson) to O(U0/E0)."""
+    el, ref, info = I.lepton_ring(n_cells=20, E0=10e9, v_total=100e6)
+    co = oracle.closed_orbit(el, ref, rad_mode=1, dim=6)
+    _, M = oracle.track_jacobian(el, ref, co, rad_mode=1)
+    lam = np.linalg.eigvals(M)
+    a = -np.log(np.abs(lam))
+    a = np.sort(a)[::-1]
+    rc = oracle.ref_constants(ref)
+    theta = 2 * math.pi / (24 * 20)
+    U0 = 8.846e-5 * (rc["E0"] / 1e9) ** 4 * (24 * 20 * theta ** 2 / 3.575) / (2 * math.pi) * 1e9
+    J = 2 * a * rc["E0"] / U0   # per-turn amplitude decrement alpha = J U0 / (2 E0)
+    pairs = sorted([J[0], J[2], J[4]])
+    assert sum(J) / 2 == pytest.approx(4.0, rel=0.02)
+    assert pairs[0] == pytest.approx(1.0, rel=0.02)
+    assert pairs[1] == pytest.approx(1.0, rel=0.02)
+    assert pairs[2] == pytest.approx(2.0, rel=0.02)
+    assert np.linalg.det(M) == pytest.approx(math.exp(-4 * U0 / rc["E0"]), rel=0.02 * 4 * U0 / rc["E0"])
+
+
+def test_radiation_quantum_statistics():
+    """One dipole slice, many electrons: mean photon number n = (5/(2 sqrt 3))
+    alpha gamma theta, mean loss equal to the mean model, variance of the loss
+    n <u^2> = n (11/27) u_c^2."""
+    ref = I.electron_reference(45.6e9)
+    theta, L = 2 * math.pi / 2400, 3.575
+    el = I.table([I.multipole(knl=[theta], hxl=theta, lrad=L)])
+    n = 100000
+    p = I.make_particles(ref, np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n))
+    oq = oracle.track(el, ref, p, 1, rad_mode=2, seed=99)
+    om = oracle.track(el, ref, one(ref), 1, rad_mode=1)
+    rc = oracle.ref_constants(ref)
+    dE = -oq["ptau"] * ref[2]
+    mean_model = -om["ptau"][0] * ref[2]
+    assert dE.mean() == pytest.approx(mean_model, rel=5 * dE.std() / math.sqrt(n) / dE.mean())
+    g = rc["gamma0"]
+    h = theta / L
+    nbar = 5 / (2 * math.sqrt(3)) * I.C_LIGHT * 0 + 5 / (2 * math.sqrt(3)) * 7.2973525693e-3 * g * h * L
+    uc = 1.5 * 197.3269804e-9 * g ** 3 * h
+    var = nbar * 11 / 27 * uc ** 2
+    assert dE.var() == pytest.approx(var, rel=0.03)
+    assert np.mean(dE == 0) == pytest.approx(math.exp(-nbar), abs=5 * math.sqrt(math.exp(-nbar) / n))
+
+
+# --------------------------------------------------------------------------
+# Brute force: whole-ring tracking in 40-digit arithmetic
+
+def _hp_track(el, ref, p, turns):
+    """The thin maps evaluated in mpmath for a few particles (drift, multipole,
+    cavity only), to bound the oracle's FP64 rounding."""
+    mpmath.mp.dps = 40
+    m0, q0, p0c = [mpmath.mpf(v) for v in ref]
+    E0 = mpmath.sqrt(p0c ** 2 + m0 ** 2)
+    b0 = p0c / E0
+    out = []
+    for i in range(len(p["x"])):
+        x, px, y, py, z = [mpmath.mpf(p[k][i]) for k in ("x", "px", "y", "py", "zeta")]
+        pt = mpmath.mpf(p["ptau"][i])
+        for _ in range(turns):
+            for r in el:
+                t, pp = int(r["type"]), r["p"]
+                d = mpmath.sqrt(1 + 2 * pt / b0 + pt ** 2) - 1
+                if t == I.DRIFT:
+                    L = mpmath.mpf(pp[0])
+                    pz = mpmath.sqrt((1 + d) ** 2 - px ** 2 - py ** 2)
+                    rvv = (1 + d) / (1 + b0 * pt)
+                    x += px * L / pz
+                    y += py * L / pz
+                    z += L - (1 + d) / rvv * L / pz
+                elif t == I.MULTIPOLE:
+                    zz = mpmath.mpc(x, y)
+                    b = sum(mpmath.mpc(pp[n], pp[11 + n]) * zz ** n / math.factorial(n)
+                            for n in range(int(r["order"]) + 1))
+                    px -= b.real
+                    py += b.imag
+                elif t == I.CAVITY:
+                    k = 2 * mpmath.pi * mpmath.mpf(pp[1]) / (b0 * I.C_LIGHT)
+                    pt += q0 * mpmath.mpf(pp[0]) / p0c * mpmath.sin(mpmath.mpf(pp[2]) * mpmath.pi / 180 - k * z)
+        out.append((x, px, y, py, z, pt))
+    return out
+
+
+def test_fodo10_bruteforce_highprec():
+    el, ref = I.fodo10()
+    p = I.subset(I.matched_gaussian(el, ref, 1000, 2.5e-6, 3e-4, seed=I.BASE_SEED), [0, 1, 2])
+    o = oracle.track(el, ref, p, 5)
+    hp = _hp_track(el, ref, p, 5)
+    for i, v in enumerate(hp):
+        for k, ref_v, scale in zip(("x", "px", "y", "py", "zeta", "ptau"), v,
+                                   (1e-3, 1e-4, 1e-3, 1e-4, 1.0, 1e-3)):
+            assert abs(o[k][i] - float(ref_v)) < 1e-14 * scale, (i, k)
