@@ -1,0 +1,243 @@
+/*
+ * xtgb.h -- C ABI of the GB300-native FP64 symplectic tracker.
+ *
+ * Element-by-element single-particle tracking of a particle ensemble through a
+ * circular-accelerator lattice for many turns, the data-parallel hot path of the
+ * Xsuite paper (Iadarola et al., "Xsuite: an integrated beam physics simulation
+ * framework"):
+ *   - a beam line is a sequence of element objects tracked turn after turn with
+ *     thin-lens integration, compiled into one kernel that tracks the whole line
+ *     on the GPU (section "Lattice modelling and single particle tracking");
+ *   - aperture elements stop the tracking of particles found outside and record
+ *     where they were lost (section "Particle-matter interaction and collimation
+ *     studies");
+ *   - synchrotron radiation in a "mean" and a "quantum" model for thin elements
+ *     (section "Synchrotron radiation models and compensation").
+ *
+ * The paper prints no formulas.  The maps are the thin-lens Hamiltonian maps
+ * with MAD-X sign conventions; their exact operation order is fixed (see the
+ * element list below) so that results are reproducible bit for bit.
+ *
+ * Conventions for every function:
+ *   - returns XT_OK (0) or a negative XT_ERR_* code; xt_last_error() gives a
+ *     message for the calling thread.  No C++ exception crosses this ABI.
+ *   - "device pointer" = memory of the current CUDA device (cudaMalloc or a
+ *     PyTorch CUDA tensor); "host pointer" = ordinary or pinned host memory.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls that
+ *     take a stream are asynchronous: the caller synchronises before reading.
+ *   - All floating-point arithmetic of the tracking path is IEEE FP64.
+ */
+#ifndef XTGB_H
+#define XTGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Status codes                                                              */
+#define XT_OK 0
+#define XT_ERR_INVALID -1      /* bad argument (null pointer, size, range)    */
+#define XT_ERR_UNSUPPORTED -2  /* unknown element type or multipole order > 10 */
+#define XT_ERR_CUDA -3         /* a CUDA runtime call failed                   */
+#define XT_ERR_TIMEOUT -4      /* the per-launch cycle budget ran out           */
+#define XT_ERR_CANCELLED -5    /* xt_cancel() was called during tracking         */
+#define XT_ERR_NOMEM -6        /* device or host allocation failed              */
+
+/* ------------------------------------------------------------------------ */
+/* Lattice table                                                             */
+/* Element types (row.type).  Parameters row.p[...]:                         */
+#define XT_MARKER 0     /* no parameters; no effect                           */
+#define XT_DRIFT 1      /* p[0] = length L [m].  Exact drift:
+                           pz = sqrt((1+delta)^2 - px^2 - py^2),
+                           x += px L/pz, y += py L/pz,
+                           zeta += L - (1+delta)/rvv * L/pz;
+                           (1+delta)^2 - px^2 - py^2 outside (0, inf) -> lost
+                           with state -2, coordinates unchanged.               */
+#define XT_MULTIPOLE 2  /* row.order = N (0..10); p[0..10] = knl_n [m^-n],
+                           p[11..21] = ksl_n, p[22] = hxl [rad],
+                           p[23] = L_rad [m] (>= 0).  Thin kick:
+                           b = sum_n (knl_n + i ksl_n)(x + i y)^n / n!,
+                           px -= Re b, py += Im b; if hxl != 0:
+                           px += hxl (1+delta) - knl0 hxl x / L_rad,
+                           zeta -= hxl x / rvv.  Radiation acts after the kick
+                           when enabled and L_rad > 0.                         */
+#define XT_CAVITY 3     /* p[0] = voltage V [V], p[1] = frequency f [Hz],
+                           p[2] = lag [deg].  ptau += q0 V sin(lag - 2 pi f
+                           zeta/(beta0 c)) / p0c, then delta, rpp, rvv.        */
+#define XT_DIPEDGE 4    /* p[0] = h [1/m], p[1] = e1 [rad], p[2] = hgap [m],
+                           p[3] = fint.  Linear edge: px += h tan(e1) x,
+                           py -= h tan(e1 - psi) y,
+                           psi = 2 h hgap fint (1 + sin^2 e1) / cos e1.       */
+#define XT_LINEARMAP 5  /* p[0..35] = M (row-major 6x6), p[36..41] = d, acting
+                           on (x, px, y, py, zeta, pzeta), pzeta = ptau/beta0:
+                           v -> M v + d, then delta, rpp, rvv from ptau.      */
+#define XT_APERTURE 6   /* p[0] = radius r [m].  Circular aperture: lost with
+                           state 0 if x^2 + y^2 > r^2, state -1 if x or y is not
+                           finite.  A point on the circle survives.           */
+
+#define XT_MAX_ORDER 10
+#define XT_NPARAM 48
+
+/* One row of the flat lattice table (392 bytes, 8-byte aligned).            */
+typedef struct {
+  int32_t type;
+  int32_t order;
+  double p[XT_NPARAM];
+} xt_element;
+
+/* Reference particle: rest energy [eV], charge [e], reference momentum
+   p0c [eV].  Derived: E0 = sqrt(p0c^2 + mass0^2), beta0 = p0c/E0.            */
+typedef struct {
+  double mass0;
+  double q0;
+  double p0c;
+} xt_reference;
+
+/* ------------------------------------------------------------------------ */
+/* Particles: structure of arrays, n entries each, all DEVICE pointers,
+   borrowed by the call (the caller owns them).
+   x [m], px = Px/P0, y [m], py, zeta = s - beta0 c t [m],
+   delta = (P-P0)/P0, ptau = (E-E0)/(P0 c), rpp = 1/(1+delta), rvv = beta/beta0
+   (delta, ptau, rpp, rvv must be consistent; they are updated together).
+   state: 1 alive; 0 lost at an aperture; -1 lost with a non-finite x or y;
+   -2 lost in a drift (no longitudinal momentum); -3 lost at the end-of-turn
+   guard (|x| or |y| > 1 m).  Lost particles keep the coordinates they had at
+   the loss; at_turn (absolute, 0-based) and at_element record where.
+   Survivors end with at_turn = start_turn + n_turns, at_element = 0.
+   particle_id keys the quantum-radiation random numbers.                    */
+typedef struct {
+  double *x, *px, *y, *py, *zeta, *delta, *ptau, *rpp, *rvv;
+  int32_t *state, *at_turn, *at_element;
+  const int64_t *particle_id;
+  int64_t n;
+} xt_particles;
+
+/* ------------------------------------------------------------------------ */
+/* Options                                                                   */
+#define XT_RAD_OFF 0
+#define XT_RAD_MEAN 1     /* deterministic energy loss per radiating element   */
+#define XT_RAD_QUANTUM 2  /* Poisson photon emission, Philox4x64-10 keyed by
+                             (seed; particle_id, turn, element, draw)          */
+typedef struct {
+  int32_t radiation;      /* XT_RAD_*                                          */
+  int32_t block;          /* threads per block: 0 = default, else 32..256, %32 */
+  int32_t chunk_bytes;    /* lattice staging chunk: 0 = default, else 1 KiB ..
+                             48 KiB, multiple of 16                             */
+  int32_t segment_turns;  /* turns per launch between compactions of the alive
+                             set: 0 = default                                   */
+  uint64_t seed;          /* quantum-radiation key                              */
+  int64_t max_cycles;     /* per-launch clock64 budget per warp: 0 = none; when
+                             exceeded tracking stops at a turn boundary and
+                             xt_sync_status() returns XT_ERR_TIMEOUT            */
+} xt_options;
+
+/* Fills `opt` with the defaults.                                            */
+void xt_options_default(xt_options* opt);
+
+/* ------------------------------------------------------------------------ */
+/* Tracker                                                                   */
+typedef struct xt_tracker xt_tracker;
+
+/* Compiles the host table (n_elements rows, host pointer, copied; the caller
+   may free it afterwards) into the device lattice of the current device.
+   Errors: XT_ERR_INVALID (null pointer, n_elements < 1 or > 2^24, reference
+   with mass0 <= 0 or p0c <= 0, options out of range), XT_ERR_UNSUPPORTED
+   (unknown type, multipole order outside 0..10), XT_ERR_CUDA/NOMEM.          */
+int xt_tracker_create(const xt_element* table, int64_t n_elements, const xt_reference* ref,
+                      const xt_options* opt, xt_tracker** out);
+
+/* Frees the tracker and its device memory (synchronises the device).        */
+void xt_tracker_destroy(xt_tracker* tr);
+
+/* Replaces the tracker's launch options (radiation mode, block, chunk,
+   segment, seed, budget).  Same range checks as create.                      */
+int xt_tracker_set_options(xt_tracker* tr, const xt_options* opt);
+int xt_tracker_get_options(const xt_tracker* tr, xt_options* opt);
+
+/* Tracks particles p (device pointers, updated in place) for n_turns turns
+   starting at absolute turn start_turn (>= 0, start_turn + n_turns < 2^31).
+   Asynchronous on `stream`.  Particles with state != 1 are not touched.
+   Tracking runs as launches of `segment_turns` turns; between launches the
+   alive particles are compacted into an index list so lost particles cost
+   nothing afterwards.  Results do not depend on the segmentation, block or
+   chunk size: track(a) followed by track(b) from turn a equals track(a+b)
+   bit for bit.  Uses the tracker's own workspace (grown on demand with
+   cudaMalloc, so the first call with a larger n must not be inside a stream
+   capture); calls on one tracker must be ordered on one stream.
+   Errors: XT_ERR_INVALID, XT_ERR_CUDA, XT_ERR_NOMEM.                        */
+int xt_track(xt_tracker* tr, const xt_particles* p, int64_t start_turn, int64_t n_turns,
+             void* stream);
+
+/* Same as xt_track with HOST particle arrays (pointer fields of `p` are host
+   pointers): copies them to the tracker's device buffers, tracks, copies the
+   results back and synchronises `stream` before returning.                  */
+int xt_track_host(xt_tracker* tr, const xt_particles* p, int64_t start_turn, int64_t n_turns,
+                  void* stream);
+
+/* Synchronises `stream` and returns the status of the tracker's launches
+   since the last call: XT_OK, XT_ERR_TIMEOUT or XT_ERR_CANCELLED; clears it. */
+int xt_sync_status(xt_tracker* tr, void* stream);
+
+/* Asks running and future launches of this tracker to stop at the next turn
+   boundary (host-visible flag; thread-safe).  xt_reset_cancel() clears it.   */
+int xt_cancel(xt_tracker* tr);
+int xt_reset_cancel(xt_tracker* tr);
+
+/* Number of tracking launches and the summed FP64 algorithmic flop count per
+   element type, for roofline accounting: flops[t] for t = XT_DRIFT .. XT_APERTURE
+   of one traversal (multipole: of order 10 with curvature, radiation off).   */
+int xt_element_flops(const xt_tracker* tr, int64_t* flops_per_element, int64_t n_elements);
+
+/* Event timing of the tracking kernel launches on their stream: after
+   xt_set_profiling(tr, 1) every tracking launch of this tracker is bracketed
+   by CUDA events; xt_kernel_time() synchronises them and returns the summed
+   duration [ms] and the number of launches since the last query, then
+   restarts the count.  Profiling off (default) records nothing.            */
+int xt_set_profiling(xt_tracker* tr, int enable);
+int xt_kernel_time(xt_tracker* tr, double* total_ms, int64_t* launches);
+
+/* Diagnostic: FP64 fma throughput of the current device [flop/s] measured by a
+   kernel of independent fma chains on `stream` (blocks until done).         */
+int xt_fp64_peak(double* flops_per_s, double* elapsed_ms, void* stream);
+
+/* Picks block size, chunk size and segment length by timing short probe runs
+   on a copy of `probe` (device particles, not modified) for `probe_turns`
+   turns, and stores them in the tracker's options.  Results are cached per
+   (lattice hash, particle count, radiation mode) in the process.           */
+int xt_autotune(xt_tracker* tr, const xt_particles* probe, int64_t probe_turns, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched error seeds: n_seeds trackers (one lattice each, same reference and
+   radiation mode) with their own particle sets, tracked in ONE persistent
+   launch per segment: CTAs pull (seed, 32-particle tile) work items from a
+   queue ordered largest-seed first.  Launch parameters come from trackers[0].
+   When `graph` != 0 the whole multi-segment sequence is captured once into a
+   CUDA graph (cached per argument set) and replayed.  Same result semantics
+   as calling xt_track on each seed.                                         */
+int xt_track_batched(xt_tracker* const* trackers, const xt_particles* particles, int32_t n_seeds,
+                     int64_t start_turn, int64_t n_turns, int32_t graph, void* stream);
+
+/* Synchronises `stream` and returns the status word of the batched launches
+   made with exactly these arguments (XT_OK, XT_ERR_TIMEOUT, XT_ERR_CANCELLED),
+   then clears it.  XT_ERR_INVALID if no such batched launch was made.       */
+int xt_batched_sync_status(xt_tracker* const* trackers, const xt_particles* particles, int32_t n_seeds,
+                           void* stream);
+
+/* Frees the device memory and graphs cached by xt_track_batched (synchronises
+   the device).  Call before destroying trackers used in batched launches.    */
+void xt_batched_release(void);
+
+/* ------------------------------------------------------------------------ */
+/* Message of the last failed call on this thread ("" if none).              */
+const char* xt_last_error(void);
+/* Library version string.                                                   */
+const char* xt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XTGB_H */

@@ -1,0 +1,161 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "xtgb.h"
+
+namespace xt {
+
+// ---------------------------------------------------------------------------
+// Device lattice: a byte stream of 16-byte aligned records, one per non-marker
+// element, in lattice order.  Record = 16-byte header + FP64 parameters padded
+// to a multiple of 16 bytes.  Chunks are contiguous record ranges copied into
+// shared memory by one bulk copy each.
+struct RecHdr {
+  uint16_t type;
+  uint16_t order;
+  uint16_t flags;   // REC_CURV: hxl != 0; REC_RAD: L_rad > 0
+  uint16_t size16;  // record size in 16-byte units
+  uint32_t elem;    // index of the element in the user's table
+  uint32_t pad;
+};
+static_assert(sizeof(RecHdr) == 16, "record header is 16 bytes");
+enum : uint16_t { REC_CURV = 1, REC_RAD = 2 };
+
+// Multipole record parameters (doubles after the header):
+//   [0] hxl  [1] k0h = knl0 hxl / L_rad  [2] crl = crad L_rad  [3] ilr2 = 1/L_rad^2
+//   [4] kql = kq L_rad  [5] L_rad  [6 + 2n] c_n = knl_n/n!  [7 + 2n] s_n = ksl_n/n!
+// Drift: [0] L.  Cavity: [0] krf [1] lag [rad] [2] qv = q0 V/p0c.
+// Edge: [0] r21 [1] r43.  Linear map: [0..35] M in (x,px,y,py,zeta,ptau),
+// [36..41] d.  Aperture: [0] r^2.
+enum { MP_HXL = 0, MP_K0H = 1, MP_CRL = 2, MP_ILR2 = 3, MP_KQL = 4, MP_LRAD = 5, MP_COEF = 6 };
+
+struct Chunk {
+  uint32_t off;    // byte offset in the record stream
+  uint32_t bytes;  // multiple of 16
+  uint32_t nrec;
+  uint32_t pad;
+};
+
+// Reference-derived constants used by the kernels.
+struct RefDev {
+  double beta0, gamma0, bg0, ib0, twoib0, p0c, uc15;
+};
+
+// Coefficients of the sine used by the RF cavity (Taylor series on |r| <= pi/4).
+struct SinTab {
+  double s[10];
+  double c[11];
+};
+
+struct Lattice {
+  std::vector<uint8_t> bytes;     // record stream
+  std::vector<uint32_t> rec_off;  // byte offset of every record
+  std::vector<uint32_t> rec_bytes;
+  int64_t n_el = 0;               // rows in the user's table
+  uint64_t hash = 0;
+  std::vector<int64_t> flops;     // algorithmic FP64 flops of one traversal, per table row
+};
+
+struct Refc {
+  double m0, q0, p0c, E0, beta0, gamma0, bg0, ib0, twoib0, crad, kq, uc15;
+};
+
+// Host-side compilation (xt_lattice.cpp).
+Refc ref_constants(const xt_reference& r);
+int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice* out, std::string* err);
+void build_chunks(const Lattice& lat, uint32_t chunk_bytes, std::vector<Chunk>* out);
+SinTab sin_table();
+// Photon spectrum inverse-CDF table: knots (xi_i, F_i), i = 0..K-1.
+void photon_table(std::vector<double>* xi, std::vector<double>* F);
+int64_t flops_of_row(const xt_element& e, int rad_mode);
+
+// ---------------------------------------------------------------------------
+// Kernel parameter block (passed by value).
+struct TrackArgs {
+  const uint8_t* lat;
+  const Chunk* chunks;
+  int32_t n_chunks;
+  int32_t n_el;
+  int32_t chunk_bytes;  // buffer size per stage
+  int32_t turn0;
+  int32_t n_turns;
+  int32_t pad0;
+  double *x, *px, *y, *py, *zeta, *delta, *ptau, *rpp, *rvv;
+  int32_t *state, *at_turn, *at_element;
+  const int64_t* pid;
+  const int32_t* idx;      // alive index list (compacted)
+  const int32_t* n_alive;  // device scalar
+  int32_t* tile_counter;   // device scalar, zeroed by the compaction
+  int32_t* status;         // device scalar: 0 ok, else XT_ERR_* code
+  const volatile int32_t* cancel;  // host-mapped flag
+  int64_t max_cycles;
+  uint64_t seed;
+  const double* spec_xi;
+  const double* spec_F;
+  int32_t spec_k;
+  int32_t pad1;
+  RefDev ref;
+  SinTab sn;
+};
+
+// Batched-seed variant: per-seed lattice and particle pointers in device arrays.
+struct SeedDev {
+  const uint8_t* lat;
+  const Chunk* chunks;
+  int32_t n_chunks;
+  int32_t n_el;
+  double *x, *px, *y, *py, *zeta, *delta, *ptau, *rpp, *rvv;
+  int32_t *state, *at_turn, *at_element;
+  const int64_t* pid;
+  int64_t n;
+};
+
+struct BatchArgs {
+  const SeedDev* seeds;
+  const int32_t* seed_order;   // seeds sorted by particle count, descending
+  const int64_t* tile_prefix;  // prefix sum of tiles in seed_order (n_seeds+1)
+  const int32_t* idx;          // per-seed compacted alive lists, concatenated
+  const int64_t* idx_base;     // start of each seed's list in idx
+  const int32_t* n_alive;      // per seed
+  int32_t* tile_counter;
+  int32_t* status;
+  const volatile int32_t* cancel;
+  const int32_t* turn_base;    // device scalar: first turn of the call
+  int32_t turn_off;            // this segment's offset from turn_base
+  int32_t n_seeds;
+  int32_t chunk_bytes;
+  int32_t n_turns;
+  int64_t max_cycles;
+  uint64_t seed;
+  const double* spec_xi;
+  const double* spec_F;
+  int32_t spec_k;
+  int32_t pad1;
+  RefDev ref;
+  SinTab sn;
+};
+
+// Launchers (xt_track.cu).  Return a cudaError_t as int.
+int launch_compact(const int32_t* state, int64_t n, int32_t* block_counts, int32_t* idx,
+                   int32_t* n_alive, int32_t* tile_counter, void* stream);
+int launch_track(const TrackArgs& a, int rad_mode, int block, int grid, size_t smem, void* stream);
+int track_occupancy(int rad_mode, int block, size_t smem, int* blocks_per_sm);
+int launch_compact_batched(const SeedDev* seeds_dev, int32_t n_seeds, const int64_t* idx_base_dev,
+                           int32_t* idx, int32_t* n_alive, int32_t* counts, int64_t max_n, void* stream);
+int launch_tile_prefix(const int32_t* n_alive, const int32_t* order, int32_t n_seeds,
+                       int64_t* tile_prefix, int32_t* tile_counter, void* stream);
+int launch_set_int(int32_t* dst, int32_t value, void* stream);
+int launch_track_batched(const BatchArgs& a, int rad_mode, int block, int grid, size_t smem,
+                         void* stream);
+int batched_occupancy(int rad_mode, int block, size_t smem, int* blocks_per_sm);
+int device_sm_count(int* n);
+int device_smem_optin(int* bytes);
+int launch_fp64_probe(double* out, int grid, int block, int iters, void* stream);
+
+size_t track_smem_bytes(int block, int chunk_bytes);
+
+}  // namespace xt

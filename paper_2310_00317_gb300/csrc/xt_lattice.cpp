@@ -1,0 +1,215 @@
+// Host-side lattice compiler: the user's flat table -> device record stream.
+// Compiled with -ffp-contract=off: every host constant is one IEEE operation
+// sequence, so the kernel's results are reproducible bit for bit.
+#include <cmath>
+#include <cstring>
+
+#include "xt_internal.h"
+
+namespace xt {
+
+// CODATA 2018
+static const double CLIGHT = 299792458.0;
+static const double ME_EV = 0.51099895000e6;
+static const double RE_M = 2.8179403262e-15;
+static const double ALPHA = 7.2973525693e-3;
+static const double HBARC_EVM = 197.3269804e-9;
+static const double PI_D = 3.14159265358979323846;
+
+Refc ref_constants(const xt_reference& r) {
+  Refc c;
+  c.m0 = r.mass0;
+  c.q0 = r.q0;
+  c.p0c = r.p0c;
+  c.E0 = std::sqrt(r.p0c * r.p0c + r.mass0 * r.mass0);
+  c.beta0 = r.p0c / c.E0;
+  c.gamma0 = c.E0 / r.mass0;
+  c.bg0 = r.p0c / r.mass0;
+  c.ib0 = c.E0 / r.p0c;
+  c.twoib0 = 2.0 * c.ib0;
+  // classical radius of the tracked species, r_c = q^2 r_e m_e / m
+  const double rc = r.q0 * r.q0 * RE_M * ME_EV / r.mass0;
+  c.crad = 2.0 * rc * r.mass0 / (3.0 * r.p0c);
+  c.kq = 5.0 * ALPHA * r.q0 * r.q0 / (2.0 * std::sqrt(3.0));
+  c.uc15 = 1.5 * HBARC_EVM;
+  return c;
+}
+
+int64_t flops_of_row(const xt_element& e, int rad_mode) {
+  switch (e.type) {
+    case XT_DRIFT: return 14;
+    case XT_MULTIPOLE: {
+      int64_t f = 8 * (int64_t)e.order + 2;
+      if (e.p[22] != 0.0) f += 7;
+      if (rad_mode != XT_RAD_OFF && e.p[23] > 0.0) f += (rad_mode == XT_RAD_MEAN) ? 33 : 34;
+      return f;
+    }
+    case XT_CAVITY: return 18;
+    case XT_DIPEDGE: return 4;
+    case XT_LINEARMAP: return 85;
+    case XT_APERTURE: return 3;
+    default: return 0;
+  }
+}
+
+static void put(std::vector<uint8_t>& b, const void* p, size_t n) {
+  const uint8_t* s = (const uint8_t*)p;
+  b.insert(b.end(), s, s + n);
+}
+
+int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice* out,
+                    std::string* err) {
+  out->bytes.clear();
+  out->rec_off.clear();
+  out->rec_bytes.clear();
+  out->flops.assign((size_t)n, 0);
+  out->n_el = n;
+  for (int64_t i = 0; i < n; i++) {
+    const xt_element& e = table[i];
+    std::vector<double> prm;
+    uint16_t flags = 0;
+    switch (e.type) {
+      case XT_MARKER: continue;
+      case XT_DRIFT: prm = {e.p[0]}; break;
+      case XT_MULTIPOLE: {
+        if (e.order < 0 || e.order > XT_MAX_ORDER) {
+          *err = "element " + std::to_string(i) + ": multipole order outside 0..10";
+          return XT_ERR_UNSUPPORTED;
+        }
+        const double hxl = e.p[22], lrad = e.p[23];
+        if (!(lrad >= 0.0)) {
+          *err = "element " + std::to_string(i) + ": L_rad must be >= 0";
+          return XT_ERR_INVALID;
+        }
+        prm.assign(MP_COEF + 2 * (e.order + 1), 0.0);
+        prm[MP_HXL] = hxl;
+        prm[MP_K0H] = (lrad > 0.0) ? (e.p[0] * hxl) / lrad : 0.0;
+        prm[MP_CRL] = rc.crad * lrad;
+        prm[MP_ILR2] = (lrad > 0.0) ? 1.0 / (lrad * lrad) : 0.0;
+        prm[MP_KQL] = rc.kq * lrad;
+        prm[MP_LRAD] = lrad;
+        double fact = 1.0;
+        for (int k = 0; k <= e.order; k++) {
+          if (k > 0) fact = fact * (double)k;
+          prm[MP_COEF + 2 * k] = e.p[k] / fact;
+          prm[MP_COEF + 2 * k + 1] = e.p[11 + k] / fact;
+        }
+        if (hxl != 0.0) flags |= REC_CURV;
+        if (lrad > 0.0) flags |= REC_RAD;
+        break;
+      }
+      case XT_CAVITY: {
+        const double V = e.p[0], f = e.p[1], lag = e.p[2];
+        prm = {(2.0 * PI_D * f) / (rc.beta0 * CLIGHT), lag * PI_D / 180.0, (rc.q0 * V) / rc.p0c};
+        break;
+      }
+      case XT_DIPEDGE: {
+        const double h = e.p[0], e1 = e.p[1], hgap = e.p[2], fint = e.p[3];
+        const double psi = 2.0 * h * hgap * fint * (1.0 + std::sin(e1) * std::sin(e1)) / std::cos(e1);
+        prm = {h * std::tan(e1), -h * std::tan(e1 - psi)};
+        break;
+      }
+      case XT_LINEARMAP: {
+        // (x,px,y,py,zeta,pzeta) -> (x,px,y,py,zeta,ptau): row 5 times beta0,
+        // column 5 times 1/beta0, d_5 times beta0.
+        prm.assign(42, 0.0);
+        for (int r = 0; r < 6; r++) {
+          for (int c = 0; c < 6; c++) {
+            double v = e.p[6 * r + c];
+            if (r == 5 && c != 5) v = v * rc.beta0;
+            else if (c == 5 && r != 5) v = v * rc.ib0;
+            prm[6 * r + c] = v;
+          }
+          prm[36 + r] = (r == 5) ? e.p[36 + r] * rc.beta0 : e.p[36 + r];
+        }
+        break;
+      }
+      case XT_APERTURE: prm = {e.p[0] * e.p[0]}; break;
+      default:
+        *err = "element " + std::to_string(i) + ": unknown type " + std::to_string(e.type);
+        return XT_ERR_UNSUPPORTED;
+    }
+    if (prm.size() % 2) prm.push_back(0.0);
+    RecHdr h;
+    std::memset(&h, 0, sizeof(h));
+    h.type = (uint16_t)e.type;
+    h.order = (uint16_t)(e.type == XT_MULTIPOLE ? e.order : 0);
+    h.flags = flags;
+    const size_t bytes = sizeof(RecHdr) + prm.size() * sizeof(double);
+    h.size16 = (uint16_t)(bytes / 16);
+    h.elem = (uint32_t)i;
+    out->rec_off.push_back((uint32_t)out->bytes.size());
+    out->rec_bytes.push_back((uint32_t)bytes);
+    put(out->bytes, &h, sizeof(h));
+    put(out->bytes, prm.data(), prm.size() * sizeof(double));
+  }
+  // FNV-1a hash of the record stream (autotune cache key)
+  uint64_t hsh = 1469598103934665603ULL;
+  for (uint8_t b : out->bytes) { hsh ^= b; hsh *= 1099511628211ULL; }
+  out->hash = hsh ^ (uint64_t)n;
+  return XT_OK;
+}
+
+void build_chunks(const Lattice& lat, uint32_t chunk_bytes, std::vector<Chunk>* out) {
+  out->clear();
+  Chunk c = {0, 0, 0, 0};
+  for (size_t r = 0; r < lat.rec_off.size(); r++) {
+    const uint32_t b = lat.rec_bytes[r];
+    if (c.nrec > 0 && c.bytes + b > chunk_bytes) {
+      out->push_back(c);
+      c = {lat.rec_off[r], 0, 0, 0};
+    }
+    if (c.nrec == 0) c.off = lat.rec_off[r];
+    c.bytes += b;
+    c.nrec += 1;
+  }
+  if (c.nrec > 0) out->push_back(c);
+}
+
+SinTab sin_table() {
+  SinTab t;
+  double fact = 1.0;
+  for (int n = 1; n <= 21; n++) {
+    fact = fact * (double)n;
+    const int k = n / 2;
+    if (n & 1) {
+      if (k < 10) t.s[k] = ((k & 1) ? -1.0 : 1.0) / fact;
+    } else if (k < 11) {
+      t.c[k] = ((k & 1) ? -1.0 : 1.0) / fact;
+    }
+  }
+  t.s[0] = 1.0;
+  t.c[0] = 1.0;
+  return t;
+}
+
+// Photon-number spectrum of synchrotron radiation in xi = u/u_c:
+// dN/dxi ~ int_xi^inf K_{5/3}(t) dt, total 5 pi/3.  With
+// K_nu(x) = int_0^inf exp(-x cosh s) cosh(nu s) ds the tail integral is
+// int_xi^inf dN = int_0^inf exp(-xi cosh s) cosh(5s/3) / cosh^2 s ds,
+// evaluated by composite Simpson's rule up to where exp(-xi cosh s) < e^-64.
+void photon_table(std::vector<double>* xi, std::vector<double>* F) {
+  const int K = 2048;
+  const double lo = 1e-7, hi = 40.0, total = 5.0 * PI_D / 3.0;
+  xi->resize(K);
+  F->resize(K);
+  for (int i = 0; i < K; i++) {
+    const double x = lo * std::exp(std::log(hi / lo) * (double)i / (double)(K - 1));
+    const double smax = std::acosh(64.0 / x) + 1.0;
+    int m = (int)(smax / 0.02) + 2;
+    if (m & 1) m++;
+    const double h = smax / m;
+    double acc = 0.0;
+    for (int j = 0; j <= m; j++) {
+      const double s = j * h;
+      const double ch = std::cosh(s);
+      const double g = std::exp(-x * ch) * std::cosh(5.0 * s / 3.0) / (ch * ch);
+      const double w = (j == 0 || j == m) ? 1.0 : ((j & 1) ? 4.0 : 2.0);
+      acc += w * g;
+    }
+    (*xi)[i] = x;
+    (*F)[i] = 1.0 - (acc * h / 3.0) / total;
+  }
+}
+
+}  // namespace xt

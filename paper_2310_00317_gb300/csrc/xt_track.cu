@@ -1,0 +1,854 @@
+// Persistent FP64 tracking kernels for sm_103a.
+//
+// One thread per particle.  Each warp pulls 32-particle tiles from a work
+// counter, loads the tile's state into registers, tracks it for all turns of
+// the launch, and writes it back.  The lattice is a stream of 16-byte aligned
+// records; each warp stages it chunk by chunk into its own pair of shared
+// memory buffers with cp.async.bulk (completion on an mbarrier), so the
+// element parameters are read as warp-uniform shared-memory broadcasts while
+// the next chunk is in flight.  Lost particles are removed between launches by
+// an order-preserving compaction, because on this GPU a masked lane costs the
+// FP64 pipe as much as an active one.
+//
+// Every FP64 operation below follows the fixed operation order of the maps
+// (explicit fma where the map says fma, nothing contracted: -fmad=false), so the
+// results equal those of a plain IEEE implementation of the same maps bit for
+// bit.  Comparisons that only decide a loss are done on the integer pipe with
+// the IEEE bit patterns (monotone for non-negative doubles), keeping the
+// scarce FP64 pipe for arithmetic.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "xt_internal.h"
+
+namespace xt {
+
+#define FULL_MASK 0xffffffffu
+#define XT_MAX_BLOCK 256
+static const int64_t STAGE_WAIT_LIMIT = 4000000000LL;  // clock cycles (~2 s)
+static const int64_t POLL_INTERVAL = 1000000LL;        // cycles between cancel polls
+
+// ---------------------------------------------------------------------------
+// Shared-memory staging primitives (inline PTX).
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Per-warp double buffer.  Lane 0 issues; all lanes wait.
+struct Stage {
+  uint8_t* buf[2];
+  uint64_t* bar[2];
+  uint32_t parity;   // bit b: parity of the next completion of buffer b
+  uint32_t pending;  // bit b: a copy into buffer b is in flight
+};
+
+__device__ __forceinline__ void stage_issue(Stage& s, int b, const uint8_t* src, uint32_t bytes, int lane) {
+  if (lane == 0) {
+    fence_proxy_async();  // order earlier generic reads of the buffer before the async write
+    uint64_t* bar = b ? s.bar[1] : s.bar[0];
+    mbar_expect_tx(bar, bytes);
+    bulk_copy_g2s(b ? s.buf[1] : s.buf[0], src, bytes, bar);
+  }
+  s.pending |= 1u << b;
+}
+
+// Bounded wait; returns false if the copy did not land within the limit.
+__device__ __forceinline__ bool stage_wait(Stage& s, int b) {
+  const uint32_t par = (s.parity >> b) & 1u;
+  uint64_t* bar = b ? s.bar[1] : s.bar[0];
+  bool ok = mbar_try_wait(bar, par);
+  if (!ok) {
+    const int64_t t0 = clock64();
+    while (!(ok = mbar_try_wait(bar, par))) {
+      if (clock64() - t0 > STAGE_WAIT_LIMIT) break;
+    }
+  }
+  ok = __all_sync(FULL_MASK, ok);
+  if (ok) {
+    s.parity ^= 1u << b;
+    s.pending &= ~(1u << b);
+  }
+  return ok;
+}
+
+__device__ __forceinline__ void stage_drain(Stage& s) {
+  for (int b = 0; b < 2; b++)
+    if (s.pending & (1u << b)) stage_wait(s, b);
+}
+
+// ---------------------------------------------------------------------------
+// Integer-pipe classification of IEEE doubles.
+__device__ __forceinline__ uint64_t dbits(double v) { return (uint64_t)__double_as_longlong(v); }
+// 0 < t < inf
+__device__ __forceinline__ bool pos_finite(double t) { return dbits(t) - 1ull < 0x7FEFFFFFFFFFFFFFull; }
+__device__ __forceinline__ bool is_finite(double v) {
+  return (dbits(v) & 0x7FF0000000000000ull) != 0x7FF0000000000000ull;
+}
+// |v| <= 1 (false for NaN)
+__device__ __forceinline__ bool abs_le_one(double v) {
+  return (dbits(v) & 0x7FFFFFFFFFFFFFFFull) <= 0x3FF0000000000000ull;
+}
+
+// ---------------------------------------------------------------------------
+// Particle state in registers.  opd = 1+delta, rv0v = 1/rvv, ep = opd*rv0v are
+// derived from the stored state.
+struct Part {
+  double x, px, y, py, zeta, delta, ptau, rpp, rvv;
+  double opd, rv0v, ep;
+};
+
+__device__ __forceinline__ void derive(Part& p) {
+  p.opd = 1.0 + p.delta;
+  p.rv0v = 1.0 / p.rvv;
+  p.ep = p.opd * p.rv0v;
+}
+
+// (1+delta)^2 = 1 + 2 ptau/beta0 + ptau^2 in the form delta = u/(sqrt(1+u)+1).
+__device__ __forceinline__ void energy_update(Part& p, const RefDev& r) {
+  const double u = p.ptau * (p.ptau + r.twoib0);
+  const double s = sqrt(1.0 + u);
+  p.delta = u / (s + 1.0);
+  p.opd = 1.0 + p.delta;
+  p.rpp = 1.0 / p.opd;
+  p.rvv = p.opd / fma(r.beta0, p.ptau, 1.0);
+  p.rv0v = 1.0 / p.rvv;
+  p.ep = p.opd * p.rv0v;
+}
+
+__device__ __forceinline__ void apply_energy_loss(Part& p, double dpt, const RefDev& r) {
+  const double rpp_old = p.rpp;
+  p.ptau = p.ptau + dpt;
+  energy_update(p, r);
+  const double f = p.opd * rpp_old;
+  p.px = p.px * f;
+  p.py = p.py * f;
+}
+
+// Sine: Cody-Waite reduction by pi/2 (three-part constant, round-to-nearest
+// by the 1.5*2^52 shift) and the Taylor series of sin / cos on |r| <= pi/4.
+__device__ __forceinline__ double sin_cw(double x, const SinTab& t) {
+  const double P1 = 1.5707963267948965579989817342720925807952880859375;
+  const double P2 = 6.123233995736766035868820147291818682e-17;
+  const double P3 = -1.4973849048591698329435081771059e-33;
+  const double TOP = 0.63661977236758134307553505349005744813783858296183;
+  const double SH = 6755399441055744.0;
+  const double k = (x * TOP + SH) - SH;
+  double r = fma(-k, P1, x);
+  r = fma(-k, P2, r);
+  r = fma(-k, P3, r);
+  const int q = (int)((long long)k & 3);
+  const double z = r * r;
+  double res;
+  if (q & 1) {
+    double pc = t.c[10];
+#pragma unroll
+    for (int i = 9; i >= 0; i--) pc = fma(pc, z, t.c[i]);
+    res = pc;
+  } else {
+    double ps = t.s[9];
+#pragma unroll
+    for (int i = 8; i >= 1; i--) ps = fma(ps, z, t.s[i]);
+    res = fma(r * z, ps, r);
+  }
+  return (q & 2) ? -res : res;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon et al., SC'11) and the photon sampler.
+struct Uni {
+  uint64_t c0, c1, c2, c3, key;
+  uint64_t b[4];
+  int pos;
+};
+__device__ __forceinline__ void philox4x64(uint64_t& c0, uint64_t& c1, uint64_t& c2, uint64_t& c3,
+                                           uint64_t k0, uint64_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    const uint64_t m0 = 0xD2E7470EE14C6C93ull, m1 = 0xCA5A826395121157ull;
+    const uint64_t hi0 = __umul64hi(m0, c0), lo0 = m0 * c0;
+    const uint64_t hi1 = __umul64hi(m1, c2), lo1 = m1 * c2;
+    const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B97F4A7C15ull;
+    k1 += 0xBB67AE8584CAA73Bull;
+  }
+}
+__device__ __forceinline__ double uni_next(Uni& u) {
+  if (u.pos == 4) {
+    uint64_t a = u.c0, b = u.c1, c = u.c2, d = u.c3;
+    philox4x64(a, b, c, d, u.key, 0ull);
+    u.b[0] = a; u.b[1] = b; u.b[2] = c; u.b[3] = d;
+    u.c3 += 1;
+    u.pos = 0;
+  }
+  const uint64_t w = u.b[u.pos++];
+  return (double)(w >> 11) * (1.0 / 9007199254740992.0);
+}
+__device__ __forceinline__ double sample_xi(double u, const double* xi, const double* F, int K) {
+  const double F0 = __ldg(F);
+  if (u < F0) {
+    const double q = u / F0;
+    return __ldg(xi) * q * q * q;
+  }
+  if (u >= __ldg(F + K - 1)) return __ldg(xi + K - 1);
+  int lo = 0, hi = K - 1;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(F + mid) <= u) lo = mid; else hi = mid;
+  }
+  const double Fl = __ldg(F + lo), Fh = __ldg(F + hi);
+  const double w = (u - Fl) / (Fh - Fl);
+  const double xl = __ldg(xi + lo);
+  return xl + w * (__ldg(xi + hi) - xl);
+}
+
+struct RadCtx {
+  uint64_t seed;
+  const double* xi;
+  const double* F;
+  int K;
+};
+
+// ---------------------------------------------------------------------------
+// Element maps.  `prm` points to the record's parameters in shared memory.
+
+// Exact drift.  Returns false if the particle is lost (t outside (0, inf)).
+__device__ __forceinline__ bool drift(Part& p, const double* prm) {
+  const double L = prm[0];
+  const double pt2 = fma(p.px, p.px, p.py * p.py);
+  const double t = fma(p.opd, p.opd, -pt2);
+  if (!pos_finite(t)) return false;
+  const double pz = sqrt(t);
+  const double lpz = L / pz;
+  p.x = fma(p.px, lpz, p.x);
+  p.y = fma(p.py, lpz, p.y);
+  p.zeta = p.zeta + fma(-p.ep, lpz, L);
+  return true;
+}
+
+template <int RAD>
+__device__ __forceinline__ void multipole(Part& p, const double* prm, int order, int flags,
+                                          const RefDev& r, const RadCtx& rc, int64_t pid, int turn,
+                                          uint32_t elem) {
+  const double2* cf = (const double2*)(prm + MP_COEF);
+  double2 c = cf[order];
+  double br = c.x, bi = c.y;
+  for (int n = order - 1; n >= 0; n--) {
+    c = cf[n];
+    const double nr = fma(br, p.x, fma(-bi, p.y, c.x));
+    const double ni = fma(br, p.y, fma(bi, p.x, c.y));
+    br = nr;
+    bi = ni;
+  }
+  p.px = p.px - br;
+  p.py = p.py + bi;
+  if (flags & REC_CURV) {
+    const double hxl = prm[MP_HXL];
+    p.px = fma(hxl, p.opd, p.px);
+    p.px = fma(-prm[MP_K0H], p.x, p.px);
+    p.zeta = fma(-(hxl * p.rv0v), p.x, p.zeta);
+  }
+  if (RAD == XT_RAD_MEAN && (flags & REC_RAD)) {
+    const double kk = fma(br, br, bi * bi);
+    const double h2 = (kk * prm[MP_ILR2]) * (p.rpp * p.rpp);
+    const double gam = fma(r.bg0, p.ptau, r.gamma0);
+    const double bet = r.beta0 * p.rvv;
+    const double b3 = bet * bet * bet;
+    const double g2 = gam * gam;
+    const double g4 = g2 * g2;
+    const double dpt = (-prm[MP_CRL]) * b3 * g4 * h2;
+    apply_energy_loss(p, dpt, r);
+  } else if (RAD == XT_RAD_QUANTUM && (flags & REC_RAD)) {
+    const double kk = fma(br, br, bi * bi);
+    const double h = sqrt(kk * prm[MP_ILR2]) * p.rpp;
+    const double gam = fma(r.bg0, p.ptau, r.gamma0);
+    const double nbar = (prm[MP_KQL] * gam) * h;
+    Uni u;
+    u.c0 = (uint64_t)pid; u.c1 = (uint64_t)(uint32_t)turn; u.c2 = elem; u.c3 = 0;
+    u.key = rc.seed; u.pos = 4;
+    const double u0 = uni_next(u);
+    int k = 0;
+    double pk = exp(-nbar), F = pk;
+    while (u0 > F && k < 200) {
+      k++;
+      pk = (pk * nbar) / (double)k;
+      F = F + pk;
+    }
+    if (k > 0) {
+      double sxi = 0.0;
+      for (int j = 0; j < k; j++) sxi = sxi + sample_xi(uni_next(u), rc.xi, rc.F, rc.K);
+      const double uc = (r.uc15 * (gam * gam * gam)) * h;
+      const double dpt = -(uc * sxi) / r.p0c;
+      apply_energy_loss(p, dpt, r);
+    }
+  }
+}
+
+// One record.  Returns the loss code (1 = still alive).
+template <int RAD>
+__device__ __forceinline__ int element(Part& p, uint32_t type, uint32_t order, uint32_t flags,
+                                       uint32_t elem, const double* prm, const RefDev& r,
+                                       const SinTab& sn, const RadCtx& rc, int64_t pid, int turn) {
+  switch (type) {
+    case XT_DRIFT:
+      return drift(p, prm) ? 1 : -2;
+    case XT_MULTIPOLE:
+      multipole<RAD>(p, prm, (int)order, (int)flags, r, rc, pid, turn, elem);
+      return 1;
+    case XT_APERTURE: {
+      const double rr = fma(p.x, p.x, p.y * p.y);
+      if (dbits(rr) > dbits(prm[0])) return (is_finite(p.x) && is_finite(p.y)) ? 0 : -1;
+      return 1;
+    }
+    case XT_CAVITY: {
+      const double phi = fma(-prm[0], p.zeta, prm[1]);
+      p.ptau = fma(prm[2], sin_cw(phi, sn), p.ptau);
+      energy_update(p, r);
+      return 1;
+    }
+    case XT_DIPEDGE:
+      p.px = fma(prm[0], p.x, p.px);
+      p.py = fma(prm[1], p.y, p.py);
+      return 1;
+    case XT_LINEARMAP: {
+      const double v[6] = {p.x, p.px, p.y, p.py, p.zeta, p.ptau};
+      double o[6];
+#pragma unroll
+      for (int i = 0; i < 6; i++) {
+        double acc = prm[36 + i];
+#pragma unroll
+        for (int j = 0; j < 6; j++) acc = fma(prm[6 * i + j], v[j], acc);
+        o[i] = acc;
+      }
+      p.x = o[0]; p.px = o[1]; p.y = o[2]; p.py = o[3]; p.zeta = o[4]; p.ptau = o[5];
+      energy_update(p, r);
+      return 1;
+    }
+    default:
+      return 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The tile body shared by the single-lattice and the batched kernels.
+struct TileLat {
+  const uint8_t* lat;
+  const Chunk* chunks;
+  int nch;
+  int n_el;
+};
+struct TileArrays {
+  double *x, *px, *y, *py, *zeta, *delta, *ptau, *rpp, *rvv;
+  int32_t *state, *at_turn, *at_element;
+  const int64_t* pid;
+};
+struct Ctl {
+  int32_t* status;
+  const volatile int32_t* cancel;
+  int64_t max_cycles;
+  int64_t t_start;
+  int64_t last_poll;
+};
+
+// Returns 0, or an XT_ERR_* code if the launch must stop (cancel, budget, staging).
+template <int RAD>
+__device__ __forceinline__ int track_tile(const TileLat& L, const TileArrays& A, int i, bool active, int turn0,
+                          int n_turns, Stage& st, int& resident_key, int lat_key,
+                          const RefDev& ref, const SinTab& sn, const RadCtx& rc, Ctl& ctl,
+                          int lane) {
+  Part p;
+  int code = 0, lturn = 0;
+  uint32_t lelem = 0;
+  int64_t pid = 0;
+  if (active) {
+    p.x = A.x[i]; p.px = A.px[i]; p.y = A.y[i]; p.py = A.py[i]; p.zeta = A.zeta[i];
+    p.delta = A.delta[i]; p.ptau = A.ptau[i]; p.rpp = A.rpp[i]; p.rvv = A.rvv[i];
+    code = A.state[i];
+    pid = A.pid[i];
+  } else {
+    p.x = p.px = p.y = p.py = p.zeta = p.delta = p.ptau = 0.0;
+    p.rpp = p.rvv = 1.0;
+  }
+  bool alive = active && code == 1;
+  derive(p);
+  int err = 0;
+  int done_turns = 0;
+  const int nch = L.nch;
+  const int64_t total = (int64_t)n_turns * nch;
+  int64_t seq = 0;
+  if (nch > 1) {
+    resident_key = -1;  // buffer 0 is about to be overwritten
+    stage_issue(st, 0, L.lat + L.chunks[0].off, L.chunks[0].bytes, lane);
+    if (total > 1) stage_issue(st, 1, L.lat + L.chunks[1 % nch].off, L.chunks[1 % nch].bytes, lane);
+  }
+  for (int turn = turn0; turn < turn0 + n_turns; ++turn) {
+    for (int c = 0; c < nch; ++c, ++seq) {
+      const uint8_t* buf;
+      const int b = (int)(seq & 1);
+      if (nch == 1) {
+        if (resident_key != lat_key) {
+          stage_issue(st, 0, L.lat + L.chunks[0].off, L.chunks[0].bytes, lane);
+          if (!stage_wait(st, 0)) { err = XT_ERR_CUDA; break; }
+          resident_key = lat_key;
+        }
+        buf = st.buf[0];
+      } else {
+        if (!stage_wait(st, b)) { err = XT_ERR_CUDA; break; }
+        buf = b ? st.buf[1] : st.buf[0];
+      }
+      const uint32_t nrec = __ldg(&L.chunks[c].nrec);
+      const uint8_t* q = buf;
+      for (uint32_t rr = 0; rr < nrec; ++rr) {
+        const uint4 hv = *(const uint4*)q;
+        const uint32_t type = hv.x & 0xFFFFu, order = hv.x >> 16;
+        const uint32_t flags = hv.y & 0xFFFFu, size16 = hv.y >> 16;
+        if (alive) {
+          const int lc = element<RAD>(p, type, order, flags, hv.z, (const double*)(q + 16), ref, sn,
+                                      rc, pid, turn);
+          if (lc != 1) {
+            alive = false;
+            code = lc;
+            lturn = turn;
+            lelem = hv.z;
+          }
+        }
+        q += size16 * 16u;
+      }
+      if (nch > 1) {
+        __syncwarp();
+        if (seq + 2 < total) {
+          const int cn = (int)((seq + 2) % nch);
+          stage_issue(st, b, L.lat + L.chunks[cn].off, L.chunks[cn].bytes, lane);
+        }
+      }
+      if (!__any_sync(FULL_MASK, alive)) break;
+    }
+    if (err) break;
+    if (alive && !(abs_le_one(p.x) && abs_le_one(p.y))) {
+      alive = false;
+      code = -3;
+      lturn = turn;
+      lelem = (uint32_t)(L.n_el - 1);
+    }
+    done_turns = turn - turn0 + 1;
+    if (!__any_sync(FULL_MASK, alive)) break;
+    // cancel flag and cycle budget, checked by lane 0 at most every POLL_INTERVAL
+    int stop = 0;
+    if (lane == 0) {
+      const int64_t now = clock64();
+      if (ctl.max_cycles > 0 && now - ctl.t_start > ctl.max_cycles) stop = XT_ERR_TIMEOUT;
+      else if (now - ctl.last_poll > POLL_INTERVAL) {
+        ctl.last_poll = now;
+        if (*ctl.cancel) stop = XT_ERR_CANCELLED;
+      }
+    }
+    stop = __shfl_sync(FULL_MASK, stop, 0);
+    if (stop && turn + 1 < turn0 + n_turns) { err = stop; break; }
+  }
+  stage_drain(st);
+  if (active) {
+    A.x[i] = p.x; A.px[i] = p.px; A.y[i] = p.y; A.py[i] = p.py; A.zeta[i] = p.zeta;
+    A.delta[i] = p.delta; A.ptau[i] = p.ptau; A.rpp[i] = p.rpp; A.rvv[i] = p.rvv;
+    if (alive) {
+      A.at_turn[i] = turn0 + done_turns;
+      A.at_element[i] = 0;
+    } else if (code != 1) {
+      A.state[i] = code;
+      A.at_turn[i] = lturn;
+      A.at_element[i] = (int32_t)lelem;
+    }
+  }
+  return err;
+}
+
+__device__ __forceinline__ void stage_setup(Stage& st, uint8_t* smem, int chunk_bytes, int lane) {
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  uint64_t* bars = (uint64_t*)smem;
+  uint8_t* bufs = smem + ((nwarps * 16 + 127) & ~127);
+  st.buf[0] = bufs + (size_t)warp * 2 * chunk_bytes;
+  st.buf[1] = st.buf[0] + chunk_bytes;
+  st.bar[0] = bars + 2 * warp;
+  st.bar[1] = bars + 2 * warp + 1;
+  st.parity = 0;
+  st.pending = 0;
+  if (lane == 0) {
+    mbar_init(st.bar[0], 1);
+    mbar_init(st.bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void set_status(int32_t* status, int err) {
+  if (err) atomicCAS(status, 0, err);
+}
+
+template <int RAD>
+__global__ void __launch_bounds__(XT_MAX_BLOCK) track_kernel(const TrackArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int lane = threadIdx.x & 31;
+  Stage st;
+  stage_setup(st, smem, a.chunk_bytes, lane);
+  if (*(volatile int32_t*)a.status != 0) return;
+  const int n_alive = *a.n_alive;
+  const TileLat L = {a.lat, a.chunks, a.n_chunks, a.n_el};
+  const TileArrays A = {a.x, a.px, a.y, a.py, a.zeta, a.delta, a.ptau, a.rpp, a.rvv,
+                        a.state, a.at_turn, a.at_element, a.pid};
+  const RadCtx rc = {a.seed, a.spec_xi, a.spec_F, a.spec_k};
+  Ctl ctl = {a.status, a.cancel, a.max_cycles, clock64(), clock64()};
+  int resident = -1;
+  while (true) {
+    int tile = 0;
+    if (lane == 0) tile = atomicAdd(a.tile_counter, 1);
+    tile = __shfl_sync(FULL_MASK, tile, 0);
+    const int64_t base = (int64_t)tile * 32;
+    if (base >= n_alive) break;
+    const int64_t k = base + lane;
+    const bool active = k < n_alive;
+    const int i = active ? __ldg(a.idx + k) : 0;
+    const int err = track_tile<RAD>(L, A, i, active, a.turn0, a.n_turns, st, resident, 0, a.ref,
+                                    a.sn, rc, ctl, lane);
+    if (err) {
+      if (lane == 0) set_status(a.status, err);
+      break;
+    }
+  }
+}
+
+template <int RAD>
+__global__ void __launch_bounds__(XT_MAX_BLOCK) track_batched_kernel(const BatchArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int lane = threadIdx.x & 31;
+  Stage st;
+  stage_setup(st, smem, a.chunk_bytes, lane);
+  if (*(volatile int32_t*)a.status != 0) return;
+  const int64_t total_tiles = a.tile_prefix[a.n_seeds];
+  const int turn0 = *a.turn_base + a.turn_off;
+  const RadCtx rc = {a.seed, a.spec_xi, a.spec_F, a.spec_k};
+  Ctl ctl = {a.status, a.cancel, a.max_cycles, clock64(), clock64()};
+  int resident = -1;
+  while (true) {
+    int tile = 0;
+    if (lane == 0) tile = atomicAdd(a.tile_counter, 1);
+    tile = __shfl_sync(FULL_MASK, tile, 0);
+    if ((int64_t)tile >= total_tiles) break;
+    // seed j in processing order with tile_prefix[j] <= tile < tile_prefix[j+1]
+    int lo = 0, hi = a.n_seeds;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (a.tile_prefix[mid] <= tile) lo = mid; else hi = mid;
+    }
+    const int s = a.seed_order[lo];
+    const SeedDev& S = a.seeds[s];
+    const int64_t k = ((int64_t)tile - a.tile_prefix[lo]) * 32 + lane;
+    const int nal = a.n_alive[s];
+    const bool active = k < nal;
+    const int i = active ? __ldg(a.idx + a.idx_base[s] + k) : 0;
+    const TileLat L = {S.lat, S.chunks, S.n_chunks, S.n_el};
+    const TileArrays A = {S.x, S.px, S.y, S.py, S.zeta, S.delta, S.ptau, S.rpp, S.rvv,
+                          S.state, S.at_turn, S.at_element, S.pid};
+    const int err = track_tile<RAD>(L, A, i, active, turn0, a.n_turns, st, resident, s, a.ref,
+                                    a.sn, rc, ctl, lane);
+    if (err) {
+      if (lane == 0) set_status(a.status, err);
+      break;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Order-preserving compaction of the alive particles (state == 1).
+static const int CB = 1024;
+
+__global__ void __launch_bounds__(CB) count_alive_kernel(const int32_t* __restrict__ state, int64_t n,
+                                                         int32_t* __restrict__ block_counts) {
+  const int64_t i = (int64_t)blockIdx.x * CB + threadIdx.x;
+  const int v = (i < n) ? (state[i] == 1) : 0;
+  const int c = __syncthreads_count(v);
+  if (threadIdx.x == 0) block_counts[blockIdx.x] = c;
+}
+
+// Exclusive prefix sum of v over the block; *tot (shared) receives the total.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* tot) {
+  __shared__ int warp_sums[CB / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(FULL_MASK, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_sums[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const int x = (lane < nw) ? warp_sums[lane] : 0;
+    int ix = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(FULL_MASK, ix, o);
+      if (lane >= o) ix += t;
+    }
+    if (lane < nw) warp_sums[lane] = ix - x;
+    if (lane == 31) *tot = ix;
+  }
+  __syncthreads();
+  return warp_sums[w] + incl - v;
+}
+
+__global__ void __launch_bounds__(CB) scatter_alive_kernel(const int32_t* __restrict__ state, int64_t n,
+                                                           const int32_t* __restrict__ block_counts,
+                                                           int32_t* __restrict__ idx,
+                                                           int32_t* __restrict__ n_alive,
+                                                           int32_t* __restrict__ tile_counter) {
+  __shared__ int red[CB / 32];
+  __shared__ int total;
+  const int b = blockIdx.x;
+  // offset of this block: sum of the counts of the preceding blocks
+  int s = 0;
+  for (int j = threadIdx.x; j < b; j += CB) s += block_counts[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(FULL_MASK, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  int off = 0;
+  for (int w = 0; w < CB / 32; w++) off += red[w];
+  __syncthreads();
+  const int64_t i = (int64_t)b * CB + threadIdx.x;
+  const int v = (i < n) ? (state[i] == 1) : 0;
+  const int pos = block_exclusive_scan(v, &total);
+  if (v) idx[off + pos] = (int32_t)i;
+  if (threadIdx.x == 0) {
+    if (b == (int)gridDim.x - 1) *n_alive = off + total;
+    if (b == 0) *tile_counter = 0;
+  }
+}
+
+// Batched compaction: grid (blocks, seeds).
+__global__ void __launch_bounds__(CB) count_alive_batched_kernel(const SeedDev* __restrict__ seeds,
+                                                                 int32_t* __restrict__ counts,
+                                                                 int32_t blocks_per_seed) {
+  const int s = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * CB + threadIdx.x;
+  const int64_t n = seeds[s].n;
+  const int v = (i < n) ? (seeds[s].state[i] == 1) : 0;
+  const int c = __syncthreads_count(v);
+  if (threadIdx.x == 0) counts[(int64_t)s * blocks_per_seed + blockIdx.x] = c;
+}
+
+__global__ void __launch_bounds__(CB) scatter_alive_batched_kernel(const SeedDev* __restrict__ seeds,
+                                                                   const int32_t* __restrict__ counts,
+                                                                   int32_t blocks_per_seed,
+                                                                   const int64_t* __restrict__ idx_base,
+                                                                   int32_t* __restrict__ idx,
+                                                                   int32_t* __restrict__ n_alive) {
+  __shared__ int red[CB / 32];
+  __shared__ int total;
+  const int s = blockIdx.y, b = blockIdx.x;
+  const int64_t n = seeds[s].n;
+  const int nb = (int)((n + CB - 1) / CB);
+  if (b >= nb) return;  // whole block exits together
+  const int32_t* cnt = counts + (int64_t)s * blocks_per_seed;
+  int sum = 0;
+  for (int j = threadIdx.x; j < b; j += CB) sum += cnt[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(FULL_MASK, sum, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  int off = 0;
+  for (int w = 0; w < CB / 32; w++) off += red[w];
+  __syncthreads();
+  const int64_t i = (int64_t)b * CB + threadIdx.x;
+  const int v = (i < n) ? (seeds[s].state[i] == 1) : 0;
+  const int pos = block_exclusive_scan(v, &total);
+  if (v) idx[idx_base[s] + off + pos] = (int32_t)i;
+  if (threadIdx.x == 0 && b == nb - 1) n_alive[s] = off + total;
+}
+
+// tile_prefix over the seeds in processing order; also zeroes the work counter.
+__global__ void tile_prefix_kernel(const int32_t* __restrict__ n_alive, const int32_t* __restrict__ order,
+                                   int32_t n_seeds, int64_t* __restrict__ prefix,
+                                   int32_t* __restrict__ tile_counter) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int64_t acc = 0;
+    prefix[0] = 0;
+    for (int j = 0; j < n_seeds; j++) {
+      acc += (n_alive[order[j]] + 31) / 32;
+      prefix[j + 1] = acc;
+    }
+    *tile_counter = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+size_t track_smem_bytes(int block, int chunk_bytes) {
+  const int nw = block / 32;
+  return (size_t)((nw * 16 + 127) & ~127) + (size_t)nw * 2 * (size_t)chunk_bytes;
+}
+
+template <int RAD>
+static int set_smem_attr(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(track_kernel<RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  return (int)cudaFuncSetAttribute(track_batched_kernel<RAD>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+static int smem_attr(int rad, size_t smem) {
+  switch (rad) {
+    case 0: return set_smem_attr<0>(smem);
+    case 1: return set_smem_attr<1>(smem);
+    default: return set_smem_attr<2>(smem);
+  }
+}
+
+int launch_track(const TrackArgs& a, int rad, int block, int grid, size_t smem, void* stream) {
+  int e = smem_attr(rad, smem);
+  if (e) return e;
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (rad) {
+    case 0: track_kernel<0><<<grid, block, smem, s>>>(a); break;
+    case 1: track_kernel<1><<<grid, block, smem, s>>>(a); break;
+    default: track_kernel<2><<<grid, block, smem, s>>>(a); break;
+  }
+  return (int)cudaGetLastError();
+}
+
+int launch_track_batched(const BatchArgs& a, int rad, int block, int grid, size_t smem, void* stream) {
+  int e = smem_attr(rad, smem);
+  if (e) return e;
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (rad) {
+    case 0: track_batched_kernel<0><<<grid, block, smem, s>>>(a); break;
+    case 1: track_batched_kernel<1><<<grid, block, smem, s>>>(a); break;
+    default: track_batched_kernel<2><<<grid, block, smem, s>>>(a); break;
+  }
+  return (int)cudaGetLastError();
+}
+
+int track_occupancy(int rad, int block, size_t smem, int* bps) {
+  int e = smem_attr(rad, smem);
+  if (e) return e;
+  switch (rad) {
+    case 0: return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, track_kernel<0>, block, smem);
+    case 1: return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, track_kernel<1>, block, smem);
+    default: return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, track_kernel<2>, block, smem);
+  }
+}
+
+int batched_occupancy(int rad, int block, size_t smem, int* bps) {
+  int e = smem_attr(rad, smem);
+  if (e) return e;
+  switch (rad) {
+    case 0: return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, track_batched_kernel<0>, block, smem);
+    case 1: return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, track_batched_kernel<1>, block, smem);
+    default: return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, track_batched_kernel<2>, block, smem);
+  }
+}
+
+int launch_compact(const int32_t* state, int64_t n, int32_t* block_counts, int32_t* idx,
+                   int32_t* n_alive, int32_t* tile_counter, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n <= 0) {
+    cudaError_t e = cudaMemsetAsync(n_alive, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaMemsetAsync(tile_counter, 0, sizeof(int32_t), s);
+  }
+  const int nb = (int)((n + CB - 1) / CB);
+  count_alive_kernel<<<nb, CB, 0, s>>>(state, n, block_counts);
+  scatter_alive_kernel<<<nb, CB, 0, s>>>(state, n, block_counts, idx, n_alive, tile_counter);
+  return (int)cudaGetLastError();
+}
+
+int launch_compact_batched(const SeedDev* seeds_dev, int32_t n_seeds, const int64_t* idx_base_dev,
+                           int32_t* idx, int32_t* n_alive, int32_t* counts, int64_t max_n, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int bps = (int)((max_n + CB - 1) / CB);
+  dim3 grid(bps, n_seeds);
+  count_alive_batched_kernel<<<grid, CB, 0, s>>>(seeds_dev, counts, bps);
+  scatter_alive_batched_kernel<<<grid, CB, 0, s>>>(seeds_dev, counts, bps, idx_base_dev, idx, n_alive);
+  return (int)cudaGetLastError();
+}
+
+int launch_tile_prefix(const int32_t* n_alive, const int32_t* order, int32_t n_seeds, int64_t* prefix,
+                       int32_t* tile_counter, void* stream) {
+  tile_prefix_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(n_alive, order, n_seeds, prefix, tile_counter);
+  return (int)cudaGetLastError();
+}
+
+__global__ void set_int_kernel(int32_t* dst, int32_t v) { *dst = v; }
+
+// FP64 throughput probe: 16 independent fma chains per thread.
+__global__ void __launch_bounds__(256) fp64_probe_kernel(double* out, int iters) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  double a[16];
+#pragma unroll
+  for (int j = 0; j < 16; j++) a[j] = 1.0 + 1e-9 * (gid + j);
+  const double m = 0.9999999, c = 1e-7;
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int j = 0; j < 16; j++) a[j] = fma(a[j], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < 16; j++) s += a[j];
+  out[gid] = s;
+}
+
+int launch_fp64_probe(double* out, int grid, int block, int iters, void* stream) {
+  fp64_probe_kernel<<<grid, block, 0, (cudaStream_t)stream>>>(out, iters);
+  return (int)cudaGetLastError();
+}
+
+int launch_set_int(int32_t* dst, int32_t value, void* stream) {
+  set_int_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(dst, value);
+  return (int)cudaGetLastError();
+}
+
+int device_smem_optin(int* bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  return (int)cudaDeviceGetAttribute(bytes, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+}
+
+int device_sm_count(int* n) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  return (int)cudaDeviceGetAttribute(n, cudaDevAttrMultiProcessorCount, dev);
+}
+
+}  // namespace xt

@@ -1,0 +1,295 @@
+"""GPU parity: the CUDA tracker against the oracle, element by element.
+
+The maps have a fixed operation order and every fma is explicit on both
+sides, so coordinates, loss codes, loss turns and loss elements must agree
+bit for bit (the RF sine is the same Cody-Waite/Taylor evaluation on both
+sides).  The quantum radiation model uses each side's own photon table and
+exp, so it is compared in distribution.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_00317_gb300 import inputs as I
+from paper_2310_00317_gb300 import xtgb
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = oracle.FLOAT_FIELDS + oracle.INT_FIELDS
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    xtgb.lib()
+    yield
+    xtgb.batched_release()
+
+
+def gpu_track(el, ref, p, n_turns, start_turn=0, **opt):
+    tr = xtgb.Tracker(el, ref, **opt)
+    P = xtgb.Particles.from_numpy(p)
+    tr.track(P, n_turns, start_turn)
+    assert tr.sync_status() == xtgb.XT_OK
+    out = P.to_numpy()
+    tr.close()
+    return out
+
+
+def assert_same(g, o, where=""):
+    for k in FIELDS:
+        a, b = g[k], o[k]
+        same = (a == b) | (np.isnan(a) & np.isnan(b)) if a.dtype.kind == "f" else (a == b)
+        if not np.all(same):
+            bad = np.flatnonzero(~same)
+            i = bad[0]
+            raise AssertionError("%s%s differs for %d of %d particles; first %d: gpu %r oracle %r"
+                                 % (where, k, bad.size, a.size, i, a[i], b[i]))
+
+
+def random_particles(ref, n, seed, sx=2e-3, spx=1e-4, sz=0.05, sd=1e-3):
+    r = np.random.default_rng(seed)
+    return I.make_particles(ref, r.normal(0, sx, n), r.normal(0, spx, n), r.normal(0, sx, n),
+                            r.normal(0, spx, n), r.normal(0, sz, n), r.normal(0, sd, n))
+
+
+PROTON = I.proton_reference(450e9)
+
+
+# --------------------------------------------------------------------------
+def test_fodo10_full_bitwise():
+    """FODO-10 ring, 1000 matched protons, 1000 turns (the full small config)."""
+    el, ref = I.fodo10()
+    p = I.matched_gaussian(el, ref, 1000, 2.5e-6, 3e-4, seed=I.BASE_SEED)
+    assert_same(gpu_track(el, ref, p, 1000), oracle.track(el, ref, p, 1000))
+
+
+@pytest.mark.parametrize("order", [0, 1, 2, 5, 10])
+def test_multipole_orders_bitwise(order):
+    rng = np.random.default_rng(order)
+    knl = rng.normal(0, 1, order + 1) * 10.0 ** -np.arange(order + 1)
+    ksl = rng.normal(0, 1, order + 1) * 10.0 ** -np.arange(order + 1)
+    el = I.table([I.multipole(knl=knl, ksl=ksl, order=order), I.drift(1.3),
+                  I.multipole(knl=[1e-3] + [0] * order, hxl=1e-3, lrad=2.0, order=order), I.drift(0.7),
+                  I.aperture(0.05)])
+    p = random_particles(PROTON, 333, order)
+    assert_same(gpu_track(el, PROTON, p, 7), oracle.track(el, PROTON, p, 7))
+
+
+def test_every_element_type_bitwise():
+    rng = np.random.default_rng(5)
+    # a focusing linear map (phase advance 0.27 turns, beta 3 m) keeps most particles bounded
+    c, s = math.cos(2 * math.pi * 0.27), math.sin(2 * math.pi * 0.27)
+    M = np.eye(6)
+    for k in (0, 2):
+        M[k, k], M[k, k + 1], M[k + 1, k], M[k + 1, k + 1] = c, 3 * s, -s / 3, c
+    M += rng.normal(0, 1e-4, (6, 6))
+    el = I.table([I.marker(), I.cavity(3e6, 400e6, 170.0), I.drift(2.5), I.dipedge(1 / 300, 0.05, 0.03, 0.5),
+                  I.multipole(knl=[0, 0.05, 0.3], ksl=[0, 0.01]), I.linear_map(M, rng.normal(0, 1e-7, 6)),
+                  I.drift(1.0), I.aperture(0.01), I.dipedge(-1 / 300, 0.05, 0.03, 0.5), I.marker()])
+    p = random_particles(PROTON, 1000, 6, sx=3e-3)
+    g, o = gpu_track(el, PROTON, p, 25), oracle.track(el, PROTON, p, 25)
+    assert_same(g, o)
+    assert np.any(o["state"] == 0) and np.any(o["state"] == 1)
+
+
+def test_lhc_ring_sample_bitwise():
+    """LHC-scale ring (20,000 elements, order-10 errors, RF, apertures):
+    500 DA-grid particles at large amplitude (some are lost), 5 turns."""
+    el, ref = I.lhc_ring()
+    g = I.da_grid(el, ref)
+    idx = np.random.default_rng(1).choice(np.flatnonzero(g["grid"][0] > 14.0), 500, replace=False)
+    p = I.subset(g, np.sort(idx))
+    go, oo = gpu_track(el, ref, p, 5), oracle.track(el, ref, p, 5)
+    assert_same(go, oo)
+
+
+def test_lhc_ring_full_size_sampled():
+    """All 999,990 DA-grid particles in the default launch configuration for
+    2 turns; 200 sampled particles (incl. lost ones) checked bit for bit."""
+    el, ref = I.lhc_ring()
+    g = I.da_grid(el, ref)
+    full = I.subset(g, np.arange(g["x"].shape[0]))
+    out = gpu_track(el, ref, full, 2)
+    lost = np.flatnonzero(out["state"] != 1)
+    rng = np.random.default_rng(2)
+    pick = np.concatenate([rng.choice(lost, min(40, lost.size), replace=False),
+                           rng.choice(out["x"].shape[0], 160, replace=False)])
+    pick = np.unique(pick)
+    o = oracle.track(el, ref, I.subset(full, pick), 2)
+    assert_same({k: out[k][pick] for k in FIELDS}, o)
+
+
+def test_lepton_mean_radiation_bitwise():
+    el, ref, _ = I.lepton_ring()
+    p = I.matched_gaussian(el, ref, 256, 0.0, 1e-3, seed=3, emit_x=2e-9, emit_y=2e-11)
+    g = gpu_track(el, ref, p, 20, radiation=xtgb.RAD_MEAN)
+    o = oracle.track(el, ref, p, 20, rad_mode=1)
+    assert_same(g, o)
+    assert np.all(o["ptau"] != p["ptau"])
+
+
+def test_segmentation_block_chunk_invariance():
+    """Results do not depend on block size, chunk size or segment length, and
+    track(a) + track(b) equals track(a + b)."""
+    el, ref = I.lhc_ring(n_cells=20)
+    p = random_particles(ref, 3000, 9, sx=4e-3, spx=2e-5, sz=0.1, sd=5e-4)
+    base = gpu_track(el, ref, p, 12)
+    for blk, ch, seg in [(32, 1024, 1), (64, 2048, 3), (256, 8192, 12), (96, 8192, 5)]:
+        assert_same(gpu_track(el, ref, p, 12, block=blk, chunk_bytes=ch, segment_turns=seg), base,
+                    "block %d chunk %d seg %d: " % (blk, ch, seg))
+    tr = xtgb.Tracker(el, ref)
+    P = xtgb.Particles.from_numpy(p)
+    tr.track(P, 5, 0)
+    tr.track(P, 7, 5)
+    assert_same(P.to_numpy(), base, "5+7 turns: ")
+    assert_same(base, oracle.track(el, ref, p, 12))
+
+
+def test_edge_cases():
+    el, ref = I.fodo10()
+    # empty ensemble
+    tr = xtgb.Tracker(el, ref)
+    P = xtgb.Particles.from_numpy(I.subset(random_particles(ref, 4, 1), []))
+    tr.track(P, 10)
+    # ragged tail (n not a multiple of 32), particles already lost on entry,
+    # non-finite input, start_turn offset
+    p = random_particles(ref, 1000 + 17, 11, sx=1e-3)
+    p["state"][::7] = 0
+    p["at_turn"][::7] = 3
+    p["x"][5] = np.nan
+    p["px"][6] = 0.9
+    p["py"][6] = 0.9
+    g = gpu_track(el, ref, p, 50, start_turn=123)
+    o = oracle.track(el, ref, p, 50, start_turn=123)
+    assert_same(g, o)
+    assert g["state"][6] == -2 and g["at_turn"][6] == 123
+    assert g["state"][5] == -2  # NaN reaches px at the first quadrupole, then fails the drift
+    assert np.all(g["at_turn"][::7] == 3)
+    # lattice of markers only: only the end-of-turn guard acts
+    mk = I.table([I.marker(), I.marker()])
+    q = random_particles(ref, 64, 12)
+    q["x"][0] = 2.0
+    assert_same(gpu_track(mk, ref, q, 3), oracle.track(mk, ref, q, 3))
+    # zero turns leaves everything untouched
+    assert_same(gpu_track(el, ref, q, 0), q)
+
+
+def test_host_buffer_path_equals_device_path():
+    el, ref = I.fodo10()
+    p = I.matched_gaussian(el, ref, 777, 2.5e-6, 3e-4, seed=4)
+    tr = xtgb.Tracker(el, ref)
+    H = xtgb.HostParticles(p)
+    tr.track_host(H, 100, 0)
+    assert_same(H.a, gpu_track(el, ref, p, 100))
+
+
+def test_batched_seeds_equal_individual():
+    """Uneven particle counts over several error seeds in one persistent
+    launch (graph and plain) equal per-seed tracking and the oracle."""
+    counts = [1000, 37, 400, 2500, 64]
+    trs, ps, ref_out = [], [], []
+    for i, n in enumerate(counts):
+        scales, _ = I.seed_error_scales(i)
+        el, ref = I.lhc_ring(seed=I.BASE_SEED + i, n_cells=4, error_scales=scales)
+        p = I.polar_sample(el, ref, n, seed=100 + i)
+        p = I.subset(p, np.arange(n))
+        trs.append(xtgb.Tracker(el, ref))
+        ps.append(p)
+        ref_out.append(gpu_track(el, ref, p, 30))
+    for graph in (False, True):
+        P = [xtgb.Particles.from_numpy(p) for p in ps]
+        xtgb.track_batched(trs, P, 10, 0, graph=graph)
+        xtgb.track_batched(trs, P, 20, 10, graph=graph)
+        assert xtgb.batched_sync_status(trs, P) == xtgb.XT_OK
+        for i in range(len(counts)):
+            assert_same(P[i].to_numpy(), ref_out[i], "seed %d graph %d: " % (i, graph))
+    el0, ref0 = I.lhc_ring(seed=I.BASE_SEED + 1, n_cells=4, error_scales=I.seed_error_scales(1)[0])
+    assert_same(ref_out[1], oracle.track(el0, ref0, ps[1], 30))
+    xtgb.batched_release()
+    for t in trs:
+        t.close()
+
+
+def test_quantum_radiation_distribution():
+    """Quantum model: reproducible bit for bit on the GPU for a given seed and
+    segmentation-independent; energy spread after emission in one dipole slice
+    matches the oracle's in distribution and the closed-form variance."""
+    ref = I.electron_reference(45.6e9)
+    theta, L = 2 * math.pi / 2400, 3.575
+    el = I.table([I.multipole(knl=[theta], hxl=theta, lrad=L)])
+    n = 200000
+    p = I.make_particles(ref, np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n))
+    g1 = gpu_track(el, ref, p, 1, radiation=xtgb.RAD_QUANTUM, seed=99)
+    g2 = gpu_track(el, ref, p, 1, radiation=xtgb.RAD_QUANTUM, seed=99)
+    assert_same(g1, g2)
+    o = oracle.track(el, ref, I.subset(p, np.arange(50000)), 1, rad_mode=2, seed=99)
+    dg = -g1["ptau"] * ref[2]
+    do = -o["ptau"] * ref[2]
+    from scipy import stats
+    assert stats.ks_2samp(dg, do).pvalue > 1e-3
+    g = ref[2] / ref[0]
+    h = theta / L
+    nbar = 5 / (2 * math.sqrt(3)) * 7.2973525693e-3 * g * h * L
+    uc = 1.5 * 197.3269804e-9 * g ** 3 * h
+    assert dg.var() == pytest.approx(nbar * 11 / 27 * uc ** 2, rel=0.02)
+    # same Philox counters and Poisson inversion: same photon counts; the two
+    # independently built spectrum tables agree closely, so each particle's loss does
+    assert np.mean((dg[:do.size] == 0) == (do == 0)) > 0.9999
+    assert np.allclose(dg[:do.size], do, rtol=1e-6, atol=0)
+    # segment resume on a small ring with quantum radiation
+    el2, ref2, _ = I.lepton_ring(n_cells=4, E0=5e9, v_total=30e6)
+    q = I.matched_gaussian(el2, ref2, 500, 1e-3, 1e-3, seed=7)
+    full = gpu_track(el2, ref2, q, 30, radiation=xtgb.RAD_QUANTUM, seed=5)
+    tr = xtgb.Tracker(el2, ref2, radiation=xtgb.RAD_QUANTUM, seed=5, segment_turns=4)
+    P = xtgb.Particles.from_numpy(q)
+    tr.track(P, 13, 0)
+    tr.track(P, 17, 13)
+    assert_same(P.to_numpy(), full)
+
+
+def test_cycle_budget_and_cancel_return_status():
+    """A launch that runs out of its cycle budget, or is cancelled from the
+    host, stops at a turn boundary and reports it; the context stays usable."""
+    el, ref = I.fodo10()
+    p = I.matched_gaussian(el, ref, 2000, 2.5e-6, 3e-4, seed=8)
+    tr = xtgb.Tracker(el, ref, max_cycles=200000)
+    P = xtgb.Particles.from_numpy(p)
+    tr.track(P, 200000)
+    assert tr.sync_status() == xtgb.XT_ERR_TIMEOUT
+    out = P.to_numpy()
+    assert np.all(out["state"] == 1)
+    stopped = out["at_turn"]
+    assert np.all((stopped > 0) & (stopped < 200000))
+    # resume each particle from its own turn: equal to the oracle
+    first = int(stopped.min())
+    o = oracle.track(el, ref, p, first)
+    sel = np.flatnonzero(stopped == first)
+    assert_same({k: out[k][sel] for k in FIELDS}, {k: o[k][sel] for k in FIELDS})
+    tr.close()
+    tr = xtgb.Tracker(el, ref)
+    tr.cancel()
+    P = xtgb.Particles.from_numpy(p)
+    tr.track(P, 10 ** 6)
+    assert tr.sync_status() == xtgb.XT_ERR_CANCELLED
+    tr.reset_cancel()
+    P = xtgb.Particles.from_numpy(p)
+    tr.track(P, 100)
+    assert tr.sync_status() == xtgb.XT_OK
+    assert_same(P.to_numpy(), oracle.track(el, ref, p, 100))
+
+
+def test_autotune_keeps_results():
+    el, ref = I.lhc_ring(n_cells=10)
+    p = random_particles(ref, 4096, 13, sx=3e-3, spx=2e-5, sz=0.05, sd=3e-4)
+    tr = xtgb.Tracker(el, ref)
+    probe = xtgb.Particles.from_numpy(p)
+    opts = tr.autotune(probe, 2)
+    assert opts["block"] in (64, 128, 256) and opts["chunk_bytes"] in (2048, 4096, 8192, 16384)
+    P = xtgb.Particles.from_numpy(p)
+    tr.track(P, 6)
+    assert_same(P.to_numpy(), oracle.track(el, ref, p, 6))
+    assert_same(probe.to_numpy(), {k: np.asarray(p[k]) for k in FIELDS})
