@@ -293,7 +293,7 @@ def run_ours(args):
     for k in xtgb.ALL_FIELDS:
         v = P.t[k].cpu()
         host[k] = v.pin_memory().numpy()
-    H = xtgb.HostParticles(host)
+    H = xtgb.HostParticles(host, copy=False)
     h2d = n * (9 * 8 + 3 * 4 + 8)
     d2h = n * (9 * 8 + 3 * 4)
     e2e_steps = max(2, args.steps // 3)

@@ -519,6 +519,6 @@ def polar_sample(elements, ref, n: int, seed: int, r_max: float = 20.0, emit_n: 
 
 
 def subset(particles: dict, idx) -> dict:
-    idx = np.asarray(idx)
+    idx = np.asarray(idx, dtype=np.int64)
     return {k: (v[idx].copy() if isinstance(v, np.ndarray) else v)
             for k, v in particles.items() if k not in ("grid", "norm")}

@@ -157,9 +157,12 @@ class Particles:
 class HostParticles:
     """Particle arrays (SoA) as numpy arrays in host memory."""
 
-    def __init__(self, d: dict):
-        self.a = {k: np.ascontiguousarray(d[k], dtype=(np.float64 if k in FLOAT_FIELDS else
-                                                        np.int64 if k == "particle_id" else np.int32))
+    def __init__(self, d: dict, copy: bool = True):
+        """Copies the arrays unless copy=False and they already have the right
+        dtype and layout (then results are written into the caller's arrays)."""
+        self.a = {k: np.array(d[k], dtype=(np.float64 if k in FLOAT_FIELDS else
+                                           np.int64 if k == "particle_id" else np.int32),
+                              copy=copy, order="C")
                   for k in ALL_FIELDS}
         self.n = int(self.a["x"].shape[0])
 
