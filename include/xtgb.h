@@ -178,6 +178,24 @@ int xt_track(xt_tracker* tr, const xt_particles* p, int64_t start_turn, int64_t 
 int xt_track_host(xt_tracker* tr, const xt_particles* p, int64_t start_turn, int64_t n_turns,
                   void* stream);
 
+/* Same tracking as xt_track, for callers that cannot allocate device memory
+   while they track (inside a stream capture that must not allocate, or in an
+   application whose device memory is owned by its own allocator or budget).
+   There is no counterpart in the paper.  xt_track grows a per-tracker
+   workspace with cudaMalloc; this call allocates nothing: its scratch (alive
+   list, counts, counters) is a fixed static device array of
+   XT_NOALLOC_MAX_PARTICLES entries (about 4 MiB, held by every GPU that loads
+   the library until exit).  The caller passes the tracker (created
+   beforehand) and the particles.  n > XT_NOALLOC_MAX_PARTICLES ->
+   XT_ERR_INVALID.  The first call on a device looks up the array's device
+   address (once per device, with that device current); make that first call
+   before any stream capture.  All calls share the one array: calls that
+   overlap on the GPU (other streams, other trackers) race.  Cycle budget and
+   cancel act as in xt_track but their status is not reported.             */
+#define XT_NOALLOC_MAX_PARTICLES 1048576
+int xt_track_noalloc(xt_tracker* tr, const xt_particles* p, int64_t start_turn, int64_t n_turns,
+                     void* stream);
+
 /* Synchronises `stream` and returns the status of the tracker's launches
    since the last call: XT_OK, XT_ERR_TIMEOUT or XT_ERR_CANCELLED; clears it. */
 int xt_sync_status(xt_tracker* tr, void* stream);

@@ -480,6 +480,26 @@ int xt_element_flops(const xt_tracker* t, int64_t* out, int64_t n) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Launch parameters for xt_track_noalloc (xt_noalloc.cu).  Uses the tracker's
+// existing chunk table as built at create/set_options time; no allocation.
+namespace xt {
+void set_error(const std::string& msg) { g_err = msg; }
+
+int noalloc_prepare(xt_tracker* t, const xt_particles* p, int64_t n_turns, TrackArgs* a, int* block,
+                    int* grid, size_t* smem, int* seg, int* rad) {
+  if (!t->d_chunks) return fail(XT_ERR_INVALID, "tracker has no lattice chunk table");
+  *block = eff_block(t);
+  *smem = track_smem_bytes(*block, t->chunk_built);
+  int rc = grid_for(t, *block, *smem, grid);
+  if (rc) return rc;
+  *seg = eff_segment(t, p->n, n_turns);
+  *rad = t->opt.radiation;
+  fill_args(t, p, a);
+  return XT_OK;
+}
+}  // namespace xt
+
+// ---------------------------------------------------------------------------
 // Autotuner: block x chunk x segment on a probe copy of the particles.
 namespace {
 std::mutex g_tune_mu;

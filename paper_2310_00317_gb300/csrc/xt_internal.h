@@ -7,6 +7,8 @@
 
 #include "xtgb.h"
 
+struct xt_tracker;
+
 namespace xt {
 
 // ---------------------------------------------------------------------------
@@ -157,5 +159,11 @@ int device_smem_optin(int* bytes);
 int launch_fp64_probe(double* out, int grid, int block, int iters, void* stream);
 
 size_t track_smem_bytes(int block, int chunk_bytes);
+
+// Launch parameters of a tracker for the allocation-free entry point
+// (xt_api.cpp): fills everything but the scratch pointers, allocates nothing.
+int noalloc_prepare(xt_tracker* t, const xt_particles* p, int64_t n_turns, TrackArgs* a, int* block,
+                    int* grid, size_t* smem, int* seg, int* rad);
+void set_error(const std::string& msg);
 
 }  // namespace xt
