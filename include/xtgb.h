@@ -250,6 +250,65 @@ int xt_batched_sync_status(xt_tracker* const* trackers, const xt_particles* part
 void xt_batched_release(void);
 
 /* ------------------------------------------------------------------------ */
+/* Dynamic-aperture surrogate network.  The paper lists dynamic-aperture
+   estimates based on machine learning among Xsuite's applications (section
+   "Lattice modelling and single particle tracking"); the network is this
+   project's: MLP 16 -> 256 -> 256 -> 256 -> 256 -> 2 with exact GELU,
+   inputs = 6 normalised initial coordinates + 10 lattice-error descriptors,
+   outputs = (survival logit, normalised log loss turn).  bfloat16 weights,
+   inputs, activations and back-propagated dZ; FP32 accumulation on the
+   tensor cores, FP32 bias/GELU/head/loss; FP32 master weights with Adam
+   (beta1 0.9, beta2 0.999, eps 1e-8).
+   Flat parameter layout (XS_N_PARAMS floats): W1 (256x16, row = output unit),
+   b1 (256), W2 (256x256), b2, W3, b3, W4, b4, W5 (2x256), b5 (2).
+   Errors are reported by xs_last_error().                                   */
+#define XS_N_PARAMS 202242
+typedef struct xs_mlp xs_mlp;
+
+/* Allocates the network on the current device, weights uniform in
+   +-1/sqrt(fan_in) from `seed`.                                             */
+int xs_mlp_create(uint64_t seed, xs_mlp** out);
+void xs_mlp_destroy(xs_mlp* net);
+/* Copies XS_N_PARAMS FP32 parameters from / to HOST memory (synchronous);
+   set_params also resets the Adam moments and step count.                  */
+int xs_mlp_set_params(xs_mlp* net, const float* params, int64_t n, void* stream);
+int xs_mlp_get_params(xs_mlp* net, float* params, int64_t n, void* stream);
+/* Inference: X (DEVICE, B x 16 FP32, row-major) -> out (DEVICE, B x 2).      */
+int xs_mlp_forward(xs_mlp* net, const float* X, float* out, int64_t B, void* stream);
+/* Forward + backward without an update.  y (survived 1/0), t (normalised log
+   loss turn), mask (1 where t is defined) are DEVICE FP32 arrays of B.
+   loss = mean BCE(logit, y) + lam * sum mask (pred - t)^2 / max(sum mask, 1).
+   grad_out (DEVICE, XS_N_PARAMS) and loss_out (DEVICE scalar) may be NULL.  */
+int xs_mlp_loss_grad(xs_mlp* net, const float* X, const float* y, const float* t, const float* mask,
+                     int64_t B, float lam, float* grad_out, float* loss_out, void* stream);
+/* One Adam step on the batch; loss_out (DEVICE scalar) may be NULL.         */
+int xs_mlp_train_step(xs_mlp* net, const float* X, const float* y, const float* t, const float* mask,
+                      int64_t B, float lr, float lam, float* loss_out, void* stream);
+const char* xs_last_error(void);
+
+/* Surrogate-guided dynamic-aperture scan glue.  Grid points are ray-major
+   (i = ray * n_r + k, radius index k increasing outward); the DA of a ray is
+   the number of radii before its first lost point.  out2 is the network
+   output (DEVICE, n_rays*n_r x 2), state the particles' state array (DEVICE).
+   xs_da_select, first pass (widen == NULL): per ray r_lo = first point whose
+   survival probability is below 1 - p_lo (written to r_lo[ray], n_r if none);
+   points k in [r_lo - margin, r_lo + window] get state 1 (to be tracked by
+   xt_track), all others XS_STATE_PREDICTED.  Later passes (widen != NULL):
+   state 1 -> XS_STATE_SURVIVED, and on rays with widen[ray] != 0 predicted
+   points in that window or within `margin` of da_prev[ray] become 1.
+   xs_da_combine: da[ray] = first lost point (tracked: state <= 0; predicted:
+   logit < 0; out2 may be NULL when every point was tracked, then predicted
+   points count as survivors); widen[ray] (may be NULL) = 1 if that boundary
+   is a predicted point or has a predicted inner neighbour.                 */
+#define XS_STATE_PREDICTED 2
+#define XS_STATE_SURVIVED 3
+int xs_da_select(const float* out2, int32_t n_rays, int32_t n_r, float p_lo, int32_t margin, int32_t window,
+                 const int32_t* widen, const int32_t* da_prev, int32_t* state, int32_t* r_lo, void* stream);
+int xs_da_combine(const float* out2, const int32_t* state, int32_t n_rays, int32_t n_r, int32_t* da,
+                  int32_t* widen, void* stream);
+const char* xs_da_last_error(void);
+
+/* ------------------------------------------------------------------------ */
 /* Message of the last failed call on this thread ("" if none).              */
 const char* xt_last_error(void);
 /* Library version string.                                                   */

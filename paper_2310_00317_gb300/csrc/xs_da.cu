@@ -1,0 +1,124 @@
+// Glue of the surrogate-guided dynamic-aperture scan.
+//
+// The scan grid is ray-major: particle i = ray * n_r + k, radius index k
+// increasing outward.  The dynamic aperture of a ray is read as the number of
+// radii before the first particle that does not survive (scanning outward).
+// The surrogate's survival logit locates where each ray's first loss is
+// expected; a window of points around it is handed to the FP64 tracker by
+// setting their state to 1 (tracked) and the others to XS_STATE_PREDICTED, so
+// that xt_track's own compaction tracks only that band.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "xtgb.h"
+
+namespace {
+thread_local std::string g_err;
+
+// Per ray: r_lo = first k whose survival probability is below 1 - p_lo
+// (logit < lmax), n_r if none: where the network first doubts survival, and
+// so where the ray's first loss is expected.  First pass (widen == null): the
+// window k in [r_lo - margin, r_lo + window] is tracked (state 1), every other
+// point is predicted (XS_STATE_PREDICTED).  Later passes: survivors of the
+// previous pass (state 1) become XS_STATE_SURVIVED so they are not tracked
+// again, and on the rays flagged in `widen` the predicted points within
+// `margin` of da_prev[ray] (the current first loss) or inside
+// [r_lo - margin, r_lo + window] are added.
+__global__ void select_kernel(const float* __restrict__ out2, int32_t n_rays, int32_t n_r, float lmax,
+                              int32_t margin, int32_t window, const int32_t* __restrict__ widen,
+                              const int32_t* __restrict__ da_prev, int32_t* __restrict__ state,
+                              int32_t* __restrict__ r_lo_out) {
+  const int ray = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ray >= n_rays) return;
+  const int64_t base = (int64_t)ray * n_r;
+  int rl = n_r;
+  for (int k = 0; k < n_r; k++)
+    if (out2[2 * (base + k)] < lmax) { rl = k; break; }
+  r_lo_out[ray] = rl;
+  const int lo = rl - margin, hi = rl + window;
+  if (!widen) {
+    for (int k = 0; k < n_r; k++) state[base + k] = (k >= lo && k <= hi) ? 1 : XS_STATE_PREDICTED;
+    return;
+  }
+  const bool grow = widen[ray] != 0;
+  const int dp = da_prev ? da_prev[ray] : rl;
+  for (int k = 0; k < n_r; k++) {
+    int32_t s = state[base + k];
+    if (s == 1) s = XS_STATE_SURVIVED;
+    if (grow && s == XS_STATE_PREDICTED && ((k >= lo && k <= hi) || (k >= dp - margin && k <= dp + margin)))
+      s = 1;
+    state[base + k] = s;
+  }
+}
+
+// Per ray: DA index = first k that is lost: a tracked point is lost if its
+// state is <= 0, a predicted point if its logit < 0 (out2 may be null when
+// every point was tracked).  widen[ray] = 1 when that first loss is a
+// predicted point, or a tracked point whose inner neighbour was predicted:
+// the boundary then lies at the edge of the tracked band.
+__global__ void combine_kernel(const float* __restrict__ out2, const int32_t* __restrict__ state, int32_t n_rays,
+                               int32_t n_r, int32_t* __restrict__ da, int32_t* __restrict__ widen) {
+  const int ray = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ray >= n_rays) return;
+  const int64_t base = (int64_t)ray * n_r;
+  int first = n_r, w = 0;
+  for (int k = 0; k < n_r; k++) {
+    const int32_t s = state[base + k];
+    const bool predicted = (s == XS_STATE_PREDICTED);
+    const bool lost = predicted ? (out2 && out2[2 * (base + k)] < 0.f) : (s <= 0);
+    if (lost) {
+      first = k;
+      if (predicted) w = 1;
+      else if (k > 0 && state[base + k - 1] == XS_STATE_PREDICTED) w = 1;
+      break;
+    }
+  }
+  da[ray] = first;
+  if (widen) widen[ray] = w;
+}
+}  // namespace
+
+extern "C" {
+
+int xs_da_select(const float* out2, int32_t n_rays, int32_t n_r, float p_lo, int32_t margin, int32_t window,
+                 const int32_t* widen, const int32_t* da_prev, int32_t* state, int32_t* r_lo, void* stream) {
+  g_err.clear();
+  if (!out2 || !state || !r_lo || n_rays < 0 || n_r < 0 || !(p_lo > 0.f && p_lo < 0.5f) || margin < 0 ||
+      window < 0) {
+    g_err = "xs_da_select: null pointer, p_lo outside (0, 0.5) or negative margin/window";
+    return XT_ERR_INVALID;
+  }
+  if (n_rays == 0 || n_r == 0) return XT_OK;
+  const float lmax = logf((1.0f - p_lo) / p_lo);
+  select_kernel<<<(n_rays + 127) / 128, 128, 0, (cudaStream_t)stream>>>(out2, n_rays, n_r, lmax, margin, window,
+                                                                         widen, da_prev, state, r_lo);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    g_err = std::string("xs_da_select: ") + cudaGetErrorString(e);
+    return XT_ERR_CUDA;
+  }
+  return XT_OK;
+}
+
+int xs_da_combine(const float* out2, const int32_t* state, int32_t n_rays, int32_t n_r, int32_t* da,
+                  int32_t* widen, void* stream) {
+  g_err.clear();
+  if (!state || !da || n_rays < 0 || n_r < 0) {
+    g_err = "xs_da_combine: null pointer or negative size";
+    return XT_ERR_INVALID;
+  }
+  if (n_rays == 0) return XT_OK;
+  combine_kernel<<<(n_rays + 127) / 128, 128, 0, (cudaStream_t)stream>>>(out2, state, n_rays, n_r, da, widen);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    g_err = std::string("xs_da_combine: ") + cudaGetErrorString(e);
+    return XT_ERR_CUDA;
+  }
+  return XT_OK;
+}
+
+const char* xs_da_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

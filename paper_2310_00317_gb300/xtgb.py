@@ -323,3 +323,104 @@ def traversed_elements(particles: dict, n_el: int, start_turn: int, n_turns: int
     surv = (st == 1) & alive_before
     lost = (st != 1) & alive_before
     return int(surv.sum()) * n_turns * n_el + int(((at[lost] - start_turn) * n_el + ae[lost] + 1).sum())
+
+
+# ----------------------------------------------------------------------------
+# Dynamic-aperture surrogate network and scan glue.
+XS_N_PARAMS = 202242
+XS_STATE_PREDICTED = 2
+XS_STATE_SURVIVED = 3
+_xs_ready = False
+
+
+def _xs_lib():
+    global _xs_ready
+    L = lib()
+    if not _xs_ready:
+        P, i32, i64, u64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_float
+        L.xs_mlp_create.argtypes = [u64, P]
+        L.xs_mlp_destroy.argtypes = [P]
+        L.xs_mlp_destroy.restype = None
+        L.xs_mlp_set_params.argtypes = [P, P, i64, P]
+        L.xs_mlp_get_params.argtypes = [P, P, i64, P]
+        L.xs_mlp_forward.argtypes = [P, P, P, i64, P]
+        L.xs_mlp_loss_grad.argtypes = [P, P, P, P, P, i64, f32, P, P, P]
+        L.xs_mlp_train_step.argtypes = [P, P, P, P, P, i64, f32, f32, P, P]
+        L.xs_last_error.restype = ctypes.c_char_p
+        L.xs_da_select.argtypes = [P, i32, i32, f32, i32, i32, P, P, P, P, P]
+        L.xs_da_combine.argtypes = [P, P, i32, i32, P, P, P]
+        L.xs_da_last_error.restype = ctypes.c_char_p
+        for n in ("xs_mlp_create", "xs_mlp_set_params", "xs_mlp_get_params", "xs_mlp_forward",
+                  "xs_mlp_loss_grad", "xs_mlp_train_step", "xs_da_select", "xs_da_combine"):
+            getattr(L, n).restype = i32
+        _xs_ready = True
+    return L
+
+
+def _xs_check(code, which="xs_last_error"):
+    if code != XT_OK:
+        raise XtError(code, getattr(_xs_lib(), which)().decode())
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+class Surrogate:
+    """The surrogate network (``xs_mlp``): FP32 master weights on the device."""
+
+    def __init__(self, seed: int = 0):
+        self._h = ctypes.c_void_p()
+        _xs_check(_xs_lib().xs_mlp_create(seed, ctypes.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            _xs_lib().xs_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        _xs_check(_xs_lib().xs_mlp_set_params(self._h, a.ctypes.data, a.shape[0], _stream_handle(None)))
+
+    def get_params(self) -> np.ndarray:
+        a = np.zeros(XS_N_PARAMS, dtype=np.float32)
+        _xs_check(_xs_lib().xs_mlp_get_params(self._h, a.ctypes.data, a.shape[0], _stream_handle(None)))
+        return a
+
+    def forward(self, X):
+        """X: CUDA float32 tensor (B, 16) -> (B, 2)."""
+        import torch
+        X = X.contiguous()
+        out = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device)
+        _xs_check(_xs_lib().xs_mlp_forward(self._h, X.data_ptr(), out.data_ptr(), X.shape[0],
+                                           _stream_handle(None)))
+        return out
+
+    def loss_grad(self, X, y, t, mask, lam: float):
+        import torch
+        g = torch.empty(XS_N_PARAMS, dtype=torch.float32, device=X.device)
+        L = torch.empty(1, dtype=torch.float32, device=X.device)
+        _xs_check(_xs_lib().xs_mlp_loss_grad(self._h, _ptr(X.contiguous()), _ptr(y), _ptr(t), _ptr(mask),
+                                             X.shape[0], lam, g.data_ptr(), L.data_ptr(), _stream_handle(None)))
+        return L, g
+
+    def train_step(self, X, y, t, mask, lr: float, lam: float, loss_out=None):
+        _xs_check(_xs_lib().xs_mlp_train_step(self._h, _ptr(X), _ptr(y), _ptr(t), _ptr(mask), X.shape[0],
+                                              lr, lam, _ptr(loss_out), _stream_handle(None)))
+
+
+def da_select(out2, n_rays: int, n_r: int, p_lo: float, margin: int, window: int, state, r_lo, widen=None,
+              da_prev=None):
+    _xs_check(_xs_lib().xs_da_select(_ptr(out2), n_rays, n_r, p_lo, margin, window, _ptr(widen), _ptr(da_prev),
+                                     _ptr(state), _ptr(r_lo), _stream_handle(None)), "xs_da_last_error")
+
+
+def da_combine(out2, state, n_rays: int, n_r: int, da, widen=None):
+    _xs_check(_xs_lib().xs_da_combine(_ptr(out2), _ptr(state), n_rays, n_r, _ptr(da), _ptr(widen),
+                                      _stream_handle(None)), "xs_da_last_error")

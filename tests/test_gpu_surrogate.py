@@ -1,0 +1,158 @@
+"""GPU parity of the surrogate network and the DA-scan glue.
+
+The network's kernels against the oracle network that rounds to bfloat16 at
+the same points (weights, inputs, activations, back-propagated dZ): every
+output and gradient tensor within 1e-2 relative (Frobenius norm), the loss
+within 1e-4.  The glue kernels against a plain Python statement of the band
+selection and of the per-ray dynamic aperture."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_2310_00317_gb300 import xtgb
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def batch(B, seed):
+    r = np.random.default_rng(seed)
+    X = r.normal(0, 1, (B, 16)).astype(np.float32)
+    y = (r.random(B) < 0.6).astype(np.float32)
+    t = r.random(B).astype(np.float32)
+    return X, y, t, (1 - y).astype(np.float32)
+
+
+def dev(a):
+    import torch
+    return torch.tensor(a, device="cuda")
+
+
+def test_forward_vs_oracle():
+    p = mlp.init_params(7).astype(np.float32).astype(np.float64)
+    net = xtgb.Surrogate(1)
+    net.set_params(p)
+    assert np.array_equal(net.get_params(), p.astype(np.float32))
+    X, _, _, _ = batch(1000 + 13, 2)
+    g = net.forward(dev(X)).cpu().numpy()
+    o, _ = mlp.forward(p, X.astype(np.float64), bf16_points=True)
+    assert rel(g, o) < 1e-2
+    assert rel(g[:, 0], o[:, 0]) < 1e-2 and rel(g[:, 1], o[:, 1]) < 1e-2
+    # large batch goes through the chunked inference path
+    Xb = np.tile(X, (80, 1))
+    gb = net.forward(dev(Xb)).cpu().numpy()
+    assert np.array_equal(gb[:X.shape[0]], g) and np.array_equal(gb[-X.shape[0]:], g)
+    net.close()
+
+
+@pytest.mark.parametrize("B", [64, 777])
+def test_loss_and_gradients_vs_oracle(B):
+    p = mlp.init_params(11).astype(np.float32).astype(np.float64)
+    net = xtgb.Surrogate(1)
+    net.set_params(p)
+    X, y, t, m = batch(B, 3)
+    L, G = net.loss_grad(dev(X), dev(y), dev(t), dev(m), 0.5)
+    G = G.cpu().numpy().astype(np.float64)
+    out, cache = mlp.forward(p, X.astype(np.float64), True)
+    Lo, d = mlp.loss_and_dout(out, y.astype(np.float64), t.astype(np.float64), m.astype(np.float64), 0.5)
+    Go = mlp.backward(p, cache, d, True)
+    assert float(L.item()) == pytest.approx(Lo, rel=1e-4)
+    off = 0
+    for s in mlp.param_shapes():
+        n = int(np.prod(s))
+        assert rel(G[off:off + n], Go[off:off + n]) < 1e-2, (s, rel(G[off:off + n], Go[off:off + n]))
+        off += n
+    net.close()
+
+
+def test_training_tracks_the_oracle():
+    """30 Adam steps on one batch: the GPU's loss curve follows the oracle's."""
+    import torch
+    p0 = mlp.init_params(13).astype(np.float32).astype(np.float64)
+    X, y, t, m = batch(512, 4)
+    net = xtgb.Surrogate(1)
+    net.set_params(p0)
+    Xd, yd, td, md = dev(X), dev(y), dev(t), dev(m)
+    Ld = torch.zeros(1, device="cuda")
+    gl = []
+    for _ in range(30):
+        net.train_step(Xd, yd, td, md, 1e-3, 0.5, Ld)
+        gl.append(float(Ld.item()))
+    p, mo, vo = p0.copy(), np.zeros_like(p0), np.zeros_like(p0)
+    ol = []
+    for step in range(1, 31):
+        out, cache = mlp.forward(p, X.astype(np.float64), True)
+        L, d = mlp.loss_and_dout(out, y.astype(np.float64), t.astype(np.float64), m.astype(np.float64), 0.5)
+        ol.append(L)
+        g = mlp.backward(p, cache, d, True)
+        p, mo, vo = mlp.adam(p, g, mo, vo, step, 1e-3)
+    assert gl[-1] < 0.85 * gl[0]
+    assert np.allclose(gl, ol, rtol=3e-2)
+    assert rel(net.get_params(), p) < 1e-3
+    net.close()
+
+
+def _py_select(logit, n_rays, n_r, p_lo, margin, window):
+    lmax = np.log((1 - p_lo) / p_lo)
+    st = np.zeros(n_rays * n_r, np.int32)
+    rl = np.zeros(n_rays, np.int32)
+    for r in range(n_rays):
+        L = logit[r * n_r:(r + 1) * n_r]
+        doubt = np.flatnonzero(L < np.float32(lmax))
+        rl[r] = doubt[0] if doubt.size else n_r
+        for k in range(n_r):
+            st[r * n_r + k] = 1 if rl[r] - margin <= k <= rl[r] + window else 2
+    return st, rl
+
+
+def _py_combine(logit, st, n_rays, n_r):
+    da = np.zeros(n_rays, np.int32)
+    w = np.zeros(n_rays, np.int32)
+    for r in range(n_rays):
+        da[r] = n_r
+        for k in range(n_r):
+            s = st[r * n_r + k]
+            lost = (logit[r * n_r + k] < 0) if s == 2 else (s <= 0)
+            if lost:
+                da[r] = k
+                w[r] = 1 if (s == 2 or (k > 0 and st[r * n_r + k - 1] == 2)) else 0
+                break
+    return da, w
+
+
+def test_da_glue_vs_python():
+    import torch
+    n_rays, n_r = 45, 300
+    r = np.random.default_rng(5)
+    edge = r.integers(50, 250, n_rays)
+    k = np.arange(n_r)
+    logit = np.concatenate([(edge[j] - k) * 0.4 + r.normal(0, 0.8, n_r) for j in range(n_rays)]).astype(np.float32)
+    out2 = np.stack([logit, np.zeros_like(logit)], axis=1)
+    st_py, rh_py = _py_select(logit, n_rays, n_r, 0.02, 4, 12)
+    st = torch.zeros(n_rays * n_r, dtype=torch.int32, device="cuda")
+    rh = torch.zeros(n_rays, dtype=torch.int32, device="cuda")
+    o2 = dev(out2)
+    xtgb.da_select(o2, n_rays, n_r, 0.02, 4, 12, st, rh)
+    assert np.array_equal(st.cpu().numpy(), st_py) and np.array_equal(rh.cpu().numpy(), rh_py)
+    # "track" the selected points: lost beyond the true edge
+    true_edge = edge + r.integers(-3, 4, n_rays)
+    s = st_py.copy()
+    for j in range(n_rays):
+        for kk in range(n_r):
+            i = j * n_r + kk
+            if s[i] == 1:
+                s[i] = 0 if kk >= true_edge[j] else 1
+    sd = dev(s)
+    da = torch.zeros(n_rays, dtype=torch.int32, device="cuda")
+    w = torch.zeros(n_rays, dtype=torch.int32, device="cuda")
+    xtgb.da_combine(o2, sd, n_rays, n_r, da, w)
+    da_py, w_py = _py_combine(logit, s, n_rays, n_r)
+    assert np.array_equal(da.cpu().numpy(), da_py) and np.array_equal(w.cpu().numpy(), w_py)
+    # a widening pass: survivors are frozen, flagged rays get more points
+    xtgb.da_select(o2, n_rays, n_r, 0.02, 8, 12, sd, rh, widen=w, da_prev=da)
+    s2 = sd.cpu().numpy()
+    assert not np.any(s2 == 1) or np.all(np.isin(np.flatnonzero(s2 == 1) // n_r, np.flatnonzero(w_py)))
+    assert np.all(s2[s == 1] == 3)
