@@ -312,38 +312,43 @@ def fodo10(seed: int = BASE_SEED):
     return table(rows), proton_reference(450e9)
 
 
-def _cell_layout(n_cells: int, kf: float, kd: float, k2f: float, k2d: float, theta: float,
-                 l_quad: float = 3.1, l_dip: float = 14.3, gap: float = 1.49):
-    """One FODO cell as (kind, main strength, drift-after) triples:
-    QF (4 slices), 3 dipoles (4 slices each), SF, QD (4), 3 dipoles, SD.
-    Every multipole slice is followed by a drift; an aperture follows every
-    quadrupole and dipole slice's drift."""
+def _cell_layout(kf: float, kd: float, k2f: float, k2d: float, theta: float, l_quad: float = 3.1,
+                 l_dip: float = 14.3, gap: float = 1.49, quad_slices: int = 4, dip_per_half: int = 3,
+                 dip_slices: int = 4, **_):
+    """One FODO cell as (kind, main strength, drift after) triples: QF,
+    dip_per_half dipoles, SF, QD, dip_per_half dipoles, SD; every magnet split
+    into thin slices at the centres of equal parts, every slice followed by a
+    drift.  LHC-like defaults: 4 quad slices, 3 x 4 dipole slices per half."""
     seq = []
 
-    def magnet(kind, k, length, gap_after):
-        for j in range(4):
-            d = length / 4 if j < 3 else length / 8 + gap_after
+    def magnet(kind, k, length, n, gap_after):
+        for j in range(n):
+            d = length / n if j < n - 1 else length / (2 * n) + gap_after
             seq.append((kind, k, d))
-        # the first drift of the magnet also carries the entry half-slice
-    # half cell 1
-    magnet("QF", kf / 4, l_quad, gap + l_dip / 8)
-    for b in range(3):
-        magnet("MB", theta, l_dip, gap + (l_dip / 8 if b < 2 else 0.0))
-    seq.append(("SF", k2f, gap + l_quad / 8))
-    magnet("QD", kd / 4, l_quad, gap + l_dip / 8)
-    for b in range(3):
-        magnet("MB", theta, l_dip, gap + (l_dip / 8 if b < 2 else 0.0))
-    seq.append(("SD", k2d, gap + l_quad / 8))
+
+    for kq, k2, kq_name, s_name in ((kf, k2f, "QF", "SF"), (kd, k2d, "QD", "SD")):
+        magnet(kq_name, kq / quad_slices, l_quad, quad_slices, gap + l_dip / (2 * dip_slices))
+        for b in range(dip_per_half):
+            last = b == dip_per_half - 1
+            magnet("MB", theta, l_dip, dip_slices, gap + (0.0 if last else l_dip / (2 * dip_slices)))
+        seq.append((s_name, k2, gap + l_quad / (2 * quad_slices)))
     return seq
 
 
 def _ring_rows(n_cells, kf, kd, k2f, k2d, theta, l_dip, rf_cells, rf_v, rf_f, rf_lag,
-               error_rng=None, error_scale=None, aperture_r=0.02, r_ref=0.017):
-    cell = _cell_layout(n_cells, kf, kd, k2f, k2d, theta, l_dip=l_dip)
+               error_rng=None, error_scale=None, aperture_r=0.02, r_ref=0.017, cell=None):
+    """Rows of n_cells cells.  An aperture follows the drift of every
+    quadrupole and dipole slice (or where cell["_ap"](kind, dipole slice index
+    in the half cell) says); the first aperture of the cells in rf_cells is an
+    RF cavity instead."""
+    cell = cell or {}
+    seq = _cell_layout(kf, kd, k2f, k2d, theta, l_dip=l_dip, **cell)
+    ap_rule = cell.get("_ap", None)
     rows = []
     for c in range(n_cells):
         first_ap = True
-        for kind, k, dlen in cell:
+        mb_in_half = 0
+        for kind, k, dlen in seq:
             knl = np.zeros(MAX_ORDER + 1)
             ksl = np.zeros(MAX_ORDER + 1)
             hxl = lrad = 0.0
@@ -353,7 +358,7 @@ def _ring_rows(n_cells, kf, kd, k2f, k2d, theta, l_dip, rf_cells, rf_v, rf_f, rf
             elif kind == "MB":
                 knl[0] = k
                 hxl = k
-                lrad = l_dip / 4
+                lrad = l_dip / cell.get("dip_slices", 4)
                 bref = abs(k)
             else:
                 knl[2] = k
@@ -369,7 +374,12 @@ def _ring_rows(n_cells, kf, kd, k2f, k2d, theta, l_dip, rf_cells, rf_v, rf_f, rf
                 order = MAX_ORDER
             rows.append(multipole(knl=knl, ksl=ksl, hxl=hxl, lrad=lrad, order=order))
             rows.append(drift(dlen))
-            if kind in ("QF", "QD", "MB"):
+            if kind == "MB":
+                mb_in_half += 1
+            elif kind in ("SF", "SD"):
+                mb_in_half = 0
+            want = kind in ("QF", "QD", "MB") if ap_rule is None else ap_rule(kind, mb_in_half)
+            if want:
                 if first_ap and c in rf_cells:
                     rows.append(cavity(rf_v, rf_f, rf_lag))
                 else:
@@ -378,14 +388,14 @@ def _ring_rows(n_cells, kf, kd, k2f, k2d, theta, l_dip, rf_cells, rf_v, rf_f, rf
     return table(rows)
 
 
-def _match_cell(n_cells, qx, qy, theta, l_dip):
+def _match_cell(n_cells, qx, qy, theta, l_dip, cell=None, k0=0.0265):
     """Thin-lens FODO strengths giving the requested tunes (design optics)."""
     ref = proton_reference()
     target = np.array([qx, qy])
-    k = np.array([0.0265, -0.0265])  # integrated per quadrupole, 1/m
+    k = np.array([k0, -k0])  # integrated per quadrupole, 1/m
 
     def tunes(kk):
-        rows = _ring_rows(1, kk[0], kk[1], 0.0, 0.0, theta, l_dip, (), 0, 0, 0)
+        rows = _ring_rows(1, kk[0], kk[1], 0.0, 0.0, theta, l_dip, (), 0, 0, 0, cell=cell)
         o = design_optics(rows, ref)
         return np.array([o["qx"], o["qy"]]) * n_cells
 
@@ -454,24 +464,40 @@ def lhc_ring(seed: int = BASE_SEED, n_cells: int = 200, error_scales=None,
     return rows, ref
 
 
-def lepton_ring(n_cells: int = 100, E0: float = 45.6e9, v_total: float = 500e6):
-    """Lepton ring with radiation: the same 100-element cell as the LHC-scale
-    ring, 100 cells (10,000 elements), 45.6 GeV electrons, no field errors,
-    8 cavities at 400 MHz with V_total = 500 MV phased at
-    180 deg - arcsin(U0/V_total) using the design energy loss
+def _lepton_aperture(kind, dipole_slice):
+    return kind in ("QF", "QD") or (kind == "MB" and dipole_slice == 1)
+
+
+LEPTON_CELL = dict(quad_slices=2, dip_per_half=2, dip_slices=4, l_quad=2.0, gap=1.0, _ap=_lepton_aperture)
+
+
+def lepton_ring(n_cells: int = 200, E0: float = 45.6e9, v_total: float = 500e6):
+    """Lepton ring with radiation: 200 FODO cells of 50 thin elements
+    (10,000): per cell QF and QD in 2 slices, 2 dipoles of 4 slices per half
+    cell (theta = 2 pi/(16 n_cells), L_rad = 10.7/4 m, bending radius 1.36 km),
+    2 sextupoles (linear chromaticity ~ +2), 22 drifts and 6 apertures
+    (r = 20 mm), of which one per cell is an RF cavity.  45.6 GeV electrons,
+    no field errors.  The RF (400 MHz, V_total = 500 MV) is phased at
+    180 deg - arcsin(U0/V_total) with the design energy loss
     U0 = C_gamma E0^4 I2 / (2 pi), C_gamma = 8.846e-5 m/GeV^3,
-    I2 = sum theta^2 / L_rad over the dipole slices."""
+    I2 = sum theta^2 / L_rad.  The ring has no dispersion-free straights, so
+    the RF is spread over every cell: a few lumped stations would make the
+    radiation energy sawtooth jump the dispersive orbit at each station and
+    excite betatron motion."""
     ref = electron_reference(E0)
-    theta = 2 * math.pi / (24 * n_cells)
-    l_dip = 14.3
-    kf, kd = _match_cell(n_cells, 24.31 * n_cells / 100, 24.32 * n_cells / 100, theta, l_dip)
-    cell0 = _ring_rows(1, kf, kd, 1e-9, -1e-9, theta, l_dip, (), 0, 0, 0)
+    theta = 2 * math.pi / (16 * n_cells)
+    l_dip = 10.7
+    cell = LEPTON_CELL
+    mu = 0.2466  # phase advance per cell [2 pi], about 89 degrees
+    base = round(mu * n_cells)
+    kf, kd = _match_cell(n_cells, base + 0.31, base + 0.32, theta, l_dip, cell=cell, k0=0.05)
+    cell0 = _ring_rows(1, kf, kd, 1e-9, -1e-9, theta, l_dip, (), 0, 0, 0, cell=cell)
     k2f, k2d = _match_chroma(cell0, electron_reference(E0), n_cells)
-    I2 = 24 * n_cells * theta ** 2 / (l_dip / 4)
+    I2 = 16 * n_cells * theta ** 2 / (l_dip / 4)
     U0 = 8.846e-5 * (E0 / 1e9) ** 4 * I2 / (2 * math.pi) * 1e9
     lag = 180.0 - math.degrees(math.asin(U0 / v_total))
-    rf_cells = tuple(int(round(i * n_cells / 8)) for i in range(8))
-    rows = _ring_rows(n_cells, kf, kd, k2f, k2d, theta, l_dip, rf_cells, v_total / 8, 400e6, lag)
+    rows = _ring_rows(n_cells, kf, kd, k2f, k2d, theta, l_dip, tuple(range(n_cells)), v_total / n_cells,
+                      400e6, lag, cell=cell)
     return rows, ref, dict(U0=U0, I2=I2, lag=lag)
 
 

@@ -430,23 +430,25 @@ def test_radiation_mean_single_slice():
 def test_radiation_damping_partition():
     """Lepton ring with mean radiation: the one-turn eigenvalues at the 6D
     closed orbit give J_x ~ 1, J_y ~ 1, J_z ~ 2 (separated-function thin ring)
-    and J_x + J_y + J_z = 4 (Robinson) to O(U0/E0)."""
+    and J_x + J_y + J_z = 4 (Robinson) to O(U0/E0); the energy the RF restores
+    on the closed orbit equals C_gamma E^4 I2 / (2 pi) with I2 = sum theta^2/L
+    over the table's dipole slices."""
+    from oracle import optics as O
     el, ref, info = I.lepton_ring(n_cells=20, E0=10e9, v_total=100e6)
-    co = oracle.closed_orbit(el, ref, rad_mode=1, dim=6)
-    _, M = oracle.track_jacobian(el, ref, co, rad_mode=1)
-    lam = np.linalg.eigvals(M)
-    a = -np.log(np.abs(lam))
-    a = np.sort(a)[::-1]
+    d = O.damping(el, ref)
     rc = oracle.ref_constants(ref)
-    theta = 2 * math.pi / (24 * 20)
-    U0 = 8.846e-5 * (rc["E0"] / 1e9) ** 4 * (24 * 20 * theta ** 2 / 3.575) / (2 * math.pi) * 1e9
-    J = 2 * a * rc["E0"] / U0   # per-turn amplitude decrement alpha = J U0 / (2 E0)
-    pairs = sorted([J[0], J[2], J[4]])
-    assert sum(J) / 2 == pytest.approx(4.0, rel=0.02)
-    assert pairs[0] == pytest.approx(1.0, rel=0.02)
-    assert pairs[1] == pytest.approx(1.0, rel=0.02)
-    assert pairs[2] == pytest.approx(2.0, rel=0.02)
-    assert np.linalg.det(M) == pytest.approx(math.exp(-4 * U0 / rc["E0"]), rel=0.02 * 4 * U0 / rc["E0"])
+    mp = el[el["type"] == I.MULTIPOLE]
+    rad = mp[mp["p"][:, 23] > 0]
+    I2 = float(np.sum(rad["p"][:, 0] ** 2 / rad["p"][:, 23]))
+    U0 = 8.846e-5 * (rc["E0"] / 1e9) ** 4 * I2 / (2 * math.pi) * 1e9
+    eps = U0 / rc["E0"]
+    assert d["U0"] == pytest.approx(U0, rel=max(2e-4, 3 * eps))
+    J = d["J"]
+    assert sum(J) == pytest.approx(4.0, rel=3 * eps)
+    assert J[0] == pytest.approx(1.0, abs=10 * eps)
+    assert J[1] == pytest.approx(1.0, abs=10 * eps)
+    assert J[2] == pytest.approx(2.0, abs=10 * eps)
+    assert np.linalg.det(d["M"]) == pytest.approx(math.exp(-4 * d["U0"] / rc["E0"]), rel=0.02 * 4 * eps)
 
 
 def test_radiation_quantum_statistics():
