@@ -153,6 +153,108 @@ def cpu_baseline(seed, n_per_proc, turns):
 
 
 # ----------------------------------------------------------------------------
+# Secondary measurements (N = 1 only).
+def _passes(before, after, start, T, n_el):
+    alive0 = before == 1
+    st, at, ae = after["state"], after["at_turn"].astype(np.int64), after["at_element"].astype(np.int64)
+    surv = alive0 & (st == 1)
+    lost = alive0 & (st != 1)
+    return int(surv.sum()) * T * n_el + int(((at[lost] - start) * n_el + ae[lost] + 1).sum())
+
+
+def measure_batched(T=2, steps=3):
+    """64 error seeds of the LHC-scale ring, uneven particle counts
+    round(10^U(3,5)), one persistent launch per turn; with and without the
+    CUDA graph."""
+    import torch
+    from paper_2310_00317_gb300 import inputs as I
+    from paper_2310_00317_gb300 import xtgb
+    counts = I.batched_seed_counts(64)
+    el0, ref = I.lhc_ring(seed=I.BASE_SEED)
+    optics = I.design_optics(el0, ref)  # errors are orders >= 2: the linear optics are shared
+    trs, ps = [], []
+    for i, n in enumerate(counts):
+        scales, _ = I.seed_error_scales(i)
+        el, _ = I.lhc_ring(seed=I.BASE_SEED + 100 + i, error_scales=scales)
+        p = I.polar_sample(el, ref, int(n), seed=I.BASE_SEED + 200 + i, optics=optics)
+        trs.append(xtgb.Tracker(el, ref))
+        ps.append(xtgb.Particles.from_numpy(I.subset(p, np.arange(int(n)))))
+    n_el = el0.shape[0]
+    out = {"seeds": 64, "particles": int(counts.sum()), "count_min": int(counts.min()),
+           "count_max": int(counts.max()), "n_elements": int(n_el), "turns_per_step": T}
+    turn = 0
+    xtgb.track_batched(trs, ps, T, turn, graph=True)  # capture + warm
+    turn += T
+    for graph in (True, False):
+        ms, units = 0.0, 0
+        for _ in range(steps):
+            before = [P.t["state"].cpu().numpy() for P in ps]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            xtgb.track_batched(trs, ps, T, turn, graph=graph)
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            for b, P in zip(before, ps):
+                units += _passes(b, {k: P.t[k].cpu().numpy() for k in ("state", "at_turn", "at_element")},
+                                 turn, T, n_el)
+            turn += T
+        out["graph" if graph else "no_graph"] = {"value": units / (ms * 1e-3), "ms_per_step": ms / steps}
+    if xtgb.batched_sync_status(trs, ps) != xtgb.XT_OK:
+        raise RuntimeError("batched tracking reported an error status")
+    xtgb.batched_release()
+    for t in trs:
+        t.close()
+    out["unit"] = UNIT
+    return out
+
+
+def measure_lepton(n=200000, turns=10):
+    """Lepton ring (10,000 elements) with mean radiation + quantum excitation."""
+    import torch
+    from paper_2310_00317_gb300 import inputs as I
+    from paper_2310_00317_gb300 import xtgb
+    el, ref, _ = I.lepton_ring()
+    p = I.matched_gaussian(el, ref, n, 0.0, 1.06e-3, seed=5, emit_x=2 * 3.9e-8, emit_y=2 * 3.9e-10)
+    tr = xtgb.Tracker(el, ref, radiation=xtgb.RAD_QUANTUM, seed=1)
+    P = xtgb.Particles.from_numpy(p)
+    tr.track(P, 2, 0)
+    before = P.t["state"].cpu().numpy()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    tr.track(P, turns, 2)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    units = _passes(before, {k: P.t[k].cpu().numpy() for k in ("state", "at_turn", "at_element")}, 2, turns,
+                    el.shape[0])
+    tr.close()
+    return {"workload": "lepton ring 10,000 elements, 45.6 GeV, mean + quantum radiation, %d particles" % n,
+            "turns": turns, "value": units / (ms * 1e-3), "unit": UNIT}
+
+
+def measure_da_scan(n_turns=300):
+    """Surrogate-guided DA scan against the plain FP64 scan at equal turns."""
+    from paper_2310_00317_gb300 import surrogate as S
+    r = S.da_study(train_seeds=48, test_seed=60, mean_count=4000, n_turns=n_turns, epochs=8,
+                   margin_sigma=1.5, window_sigma=1.0)
+    keep = ("n_train", "train_seeds", "label_seconds", "train_seconds", "train_accuracy", "n_turns",
+            "n_elements", "grid_points", "n_rays", "plain_seconds", "surrogate_seconds", "inference_seconds",
+            "speedup", "tracked_fraction", "passes", "da_error_sigma_max", "da_error_sigma_mean",
+            "rays_within_0p2_sigma", "coarse_seconds", "coarse_speedup", "coarse_tracked_fraction",
+            "coarse_da_error_sigma_max")
+    out = {k: r[k] for k in keep}
+    da = np.asarray(r["da_plain_sigma"])
+    out["da_plain_sigma_min_median_max"] = [float(da.min()), float(np.median(da)), float(da.max())]
+    out["workload"] = ("reduced LHC-scale ring (20 cells, 2,000 elements, errors x1.5 x per-seed scales), "
+                       "labels from 48 error seeds by the batched tracker, held-out seed scanned on "
+                       "22,222 radii x 45 angles (999,990 points), %d turns" % n_turns)
+    return out
+
+
+# ----------------------------------------------------------------------------
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -314,6 +416,11 @@ def run_ours(args):
     if rank != 0:
         return 0
 
+    extras = {}
+    if ws == 1 and not args.no_extras:
+        extras["batched_seeds"] = measure_batched()
+        extras["lepton_quantum"] = measure_lepton()
+        extras["da_scan"] = measure_da_scan()
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(seed, args.cpu_particles, args.cpu_turns)
@@ -346,6 +453,7 @@ def run_ours(args):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    line.update(extras)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -364,6 +472,8 @@ def main():
     ap.add_argument("--cpu-turns", type=int, default=10)
     ap.add_argument("--ref-particles", type=int, default=150)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-seed, lepton-ring and DA-scan measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

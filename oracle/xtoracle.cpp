@@ -259,21 +259,24 @@ template <> inline double mkv<double>(double v) { return v; }
 template <> inline Dual mkv<Dual>(double v) { return mkd(v); }
 
 // ---------------------------------------------------------------------------
-// Particle state; opd = 1+delta, rv0v = 1/rvv and ep = opd*rv0v are derived
-// from delta and rvv and recomputed whenever those change (pure functions of
-// the stored state, so recomputation never changes a result).
+// Particle state; opd = 1+delta, dm1 = (1+delta)^2 - 1 = delta (delta + 2),
+// rv0v = 1/rvv, ep = opd*rv0v (= 1 + beta0 ptau) and epm1 = beta0 ptau are
+// derived from delta, rvv and ptau and recomputed whenever those change (pure
+// functions of the stored state, so recomputation never changes a result).
 template <class T>
 struct Part {
   T x, px, y, py, zeta, delta, ptau, rpp, rvv;
-  T opd, rv0v, ep;
+  T opd, dm1, rv0v, ep, epm1;
   int32_t state, at_turn, at_element;
   int64_t id;
 };
 template <class T>
-static inline void derive(Part<T>& p) {
+static inline void derive(Part<T>& p, const RefConst& rc) {
   p.opd = 1.0 + p.delta;
+  p.dm1 = p.delta * (p.delta + 2.0);
   p.rv0v = 1.0 / p.rvv;
   p.ep = p.opd * p.rv0v;
+  p.epm1 = rc.beta0 * p.ptau;
 }
 
 // Energy update from a new ptau, using (1+delta)^2 = 1 + 2 ptau/beta0 + ptau^2
@@ -286,10 +289,12 @@ static inline void energy_update(Part<T>& p, const RefConst& rc) {
   T s = SQRT(1.0 + u);
   p.delta = u / (s + 1.0);
   p.opd = 1.0 + p.delta;
+  p.dm1 = p.delta * (p.delta + 2.0);
   p.rpp = 1.0 / p.opd;
   p.rvv = p.opd / FMA(rc.beta0, p.ptau, 1.0);
   p.rv0v = 1.0 / p.rvv;
   p.ep = p.opd * p.rv0v;
+  p.epm1 = rc.beta0 * p.ptau;
 }
 
 template <class T>
@@ -300,19 +305,33 @@ static inline void mark_lost(Part<T>& p, int code, int turn, int elem) {
 // Exact drift of length L (thin-lens integration: drifts between kicks).
 //   pz = sqrt((1+delta)^2 - px^2 - py^2),  x += px L/pz,  y += py L/pz,
 //   zeta += L - (1+delta)/rvv * L/pz  (path length L(1+delta)/pz at speed beta).
-// A particle with (1+delta)^2 - px^2 - py^2 not in (0, inf) is lost (code -2)
-// with its coordinates unchanged.
+// With u = (1+delta)^2 - 1 - px^2 - py^2 and yh = 1/pz - 1 = (1+u)^(-1/2) - 1:
+//   L/pz = L + L yh,   zeta += -L (beta0 ptau + ep yh)   (ep - 1 = beta0 ptau),
+// so the zeta increment is formed from small quantities without cancellation.
+// yh is the Taylor series of (1+u)^(-1/2) - 1 to order 8 (coefficients
+// binomial(-1/2, n), exact dyadic numbers) for |u| <= 2^-7, where the
+// truncation error is below 2e-17 of yh; otherwise 1/sqrt(1+u) - 1.
+// A particle with u outside (-1, inf) is lost (code -2), coordinates unchanged.
+static const double RS_C[9] = {0.0, -0.5, 0.375, -0.3125, 0.2734375, -0.24609375, 0.2255859375,
+                               -0.20947265625, 0.196380615234375};
 template <class T>
 static inline void drift(Part<T>& p, double L, int turn, int elem) {
   T pt2 = FMA(p.px, p.px, p.py * p.py);
-  T t = FMA(p.opd, p.opd, -pt2);
-  double tv = val(t);
-  if (!(tv > 0.0 && tv < INFINITY)) { mark_lost(p, -2, turn, elem); return; }
-  T pz = SQRT(t);
-  T lpz = L / pz;
+  T u = p.dm1 - pt2;
+  double uv = val(u);
+  if (!(uv > -1.0 && uv < INFINITY)) { mark_lost(p, -2, turn, elem); return; }
+  T yh;
+  if (std::fabs(uv) <= 0.0078125) {
+    T h = mkv<T>(RS_C[8]);
+    for (int n = 7; n >= 1; n--) h = FMA(h, u, mkv<T>(RS_C[n]));
+    yh = h * u;
+  } else {
+    yh = 1.0 / SQRT(1.0 + u) - 1.0;
+  }
+  T lpz = FMA(L, yh, mkv<T>(L));
   p.x = FMA(p.px, lpz, p.x);
   p.y = FMA(p.py, lpz, p.y);
-  p.zeta = p.zeta + FMA(-p.ep, lpz, mkv<T>(L));
+  p.zeta = FMA(-L, FMA(p.ep, yh, p.epm1), p.zeta);
 }
 
 // Energy change by radiation: ptau += dpt, then the energy update; the
@@ -552,7 +571,7 @@ int xo_track(const Element* el, int64_t n_el, const Reference* ref, int rad_mode
     p.delta = delta[i]; p.ptau = ptau[i]; p.rpp = rpp[i]; p.rvv = rvv[i];
     p.state = state[i]; p.at_turn = at_turn[i]; p.at_element = at_element[i]; p.id = pid[i];
     if (p.state != 1) continue;
-    derive(p);
+    derive(p, rc);
     for (int64_t t = start_turn; t < start_turn + n_turns && p.state == 1; t++) {
       for (int64_t e = 0; e < n_el; e++) {
         track_element(p, prep[e], rad_mode, rc, seed, (int)t, (int)e);

@@ -121,17 +121,19 @@ __device__ __forceinline__ bool abs_le_one(double v) {
 }
 
 // ---------------------------------------------------------------------------
-// Particle state in registers.  opd = 1+delta, rv0v = 1/rvv, ep = opd*rv0v are
-// derived from the stored state.
+// Particle state in registers.  opd = 1+delta, dm1 = (1+delta)^2 - 1,
+// rv0v = 1/rvv, ep = opd*rv0v are derived from the stored state.
 struct Part {
   double x, px, y, py, zeta, delta, ptau, rpp, rvv;
-  double opd, rv0v, ep;
+  double opd, dm1, rv0v, ep, epm1;  // epm1 = beta0 ptau (= ep - 1)
 };
 
-__device__ __forceinline__ void derive(Part& p) {
+__device__ __forceinline__ void derive(Part& p, const RefDev& r) {
   p.opd = 1.0 + p.delta;
+  p.dm1 = p.delta * (p.delta + 2.0);
   p.rv0v = 1.0 / p.rvv;
   p.ep = p.opd * p.rv0v;
+  p.epm1 = r.beta0 * p.ptau;
 }
 
 // (1+delta)^2 = 1 + 2 ptau/beta0 + ptau^2 in the form delta = u/(sqrt(1+u)+1).
@@ -140,10 +142,12 @@ __device__ __forceinline__ void energy_update(Part& p, const RefDev& r) {
   const double s = sqrt(1.0 + u);
   p.delta = u / (s + 1.0);
   p.opd = 1.0 + p.delta;
+  p.dm1 = p.delta * (p.delta + 2.0);
   p.rpp = 1.0 / p.opd;
   p.rvv = p.opd / fma(r.beta0, p.ptau, 1.0);
   p.rv0v = 1.0 / p.rvv;
   p.ep = p.opd * p.rv0v;
+  p.epm1 = r.beta0 * p.ptau;
 }
 
 __device__ __forceinline__ void apply_energy_loss(Part& p, double dpt, const RefDev& r) {
@@ -243,17 +247,36 @@ struct RadCtx {
 // ---------------------------------------------------------------------------
 // Element maps.  `prm` points to the record's parameters in shared memory.
 
-// Exact drift.  Returns false if the particle is lost (t outside (0, inf)).
+// Exact drift.  yh = 1/pz - 1 = (1+u)^(-1/2) - 1, u = (1+delta)^2 - 1 - px^2 -
+// py^2: the order-8 Taylor series (Horner, dyadic coefficients) for
+// |u| <= 2^-7, else 1/sqrt(1+u) - 1; then L/pz = L + L yh and
+// zeta += -L (beta0 ptau + ep yh).  No divide or square root on the common
+// path.  Returns false (lost, state unchanged) if u is not in (-1, inf); that
+// test and the branch test run on the integer pipe.
 __device__ __forceinline__ bool drift(Part& p, const double* prm) {
   const double L = prm[0];
   const double pt2 = fma(p.px, p.px, p.py * p.py);
-  const double t = fma(p.opd, p.opd, -pt2);
-  if (!pos_finite(t)) return false;
-  const double pz = sqrt(t);
-  const double lpz = L / pz;
+  const double u = p.dm1 - pt2;
+  const uint64_t ub = dbits(u), ua = ub & 0x7FFFFFFFFFFFFFFFull;
+  const bool valid = (ub >> 63) ? (ua < 0x3FF0000000000000ull) : (ub < 0x7FF0000000000000ull);
+  if (!valid) return false;
+  double yh;
+  if (ua <= 0x3F80000000000000ull) {  // |u| <= 2^-7
+    double h = fma(0.196380615234375, u, -0.20947265625);
+    h = fma(h, u, 0.2255859375);
+    h = fma(h, u, -0.24609375);
+    h = fma(h, u, 0.2734375);
+    h = fma(h, u, -0.3125);
+    h = fma(h, u, 0.375);
+    h = fma(h, u, -0.5);
+    yh = h * u;
+  } else {
+    yh = 1.0 / sqrt(1.0 + u) - 1.0;
+  }
+  const double lpz = fma(L, yh, L);
   p.x = fma(p.px, lpz, p.x);
   p.y = fma(p.py, lpz, p.y);
-  p.zeta = p.zeta + fma(-p.ep, lpz, L);
+  p.zeta = fma(-L, fma(p.ep, yh, p.epm1), p.zeta);
   return true;
 }
 
@@ -401,7 +424,7 @@ __device__ __forceinline__ int track_tile(const TileLat& L, const TileArrays& A,
     p.rpp = p.rvv = 1.0;
   }
   bool alive = active && code == 1;
-  derive(p);
+  derive(p, ref);
   int err = 0;
   int done_turns = 0;
   const int nch = L.nch;

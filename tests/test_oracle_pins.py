@@ -68,6 +68,26 @@ def test_drift_closed_form_highprec():
         assert o["px"][0] == p["px"][0] and o["delta"][0] == p["delta"][0]
 
 
+@pytest.mark.parametrize("d", [0.0, 3e-4, -2e-3, 4e-3, -6e-3, 0.02, -0.05, 0.3])
+def test_drift_both_series_branches(d):
+    """1/pz by the order-8 series (|u| <= 2^-7) and by 1/sqrt(1+u) otherwise:
+    x and the zeta increment against 40-digit arithmetic.  The zeta increment
+    uses ep - 1 = beta0 ptau, which the stored (delta, ptau, rvv) satisfy to
+    rounding, hence the absolute 2e-16 L term."""
+    mpmath.mp.dps = 40
+    L = 3.7
+    x, px, y, py = 1e-3, 2e-4, -1e-3, -1e-4
+    p = one(PROTON, x, px, y, py, 0.0, d)
+    o = oracle.track(I.table([I.drift(L)]), PROTON, p, 1)
+    k = hp_kin(PROTON, p["delta"][0])
+    opd = 1 + mpmath.mpf(p["delta"][0])
+    pz = mpmath.sqrt(opd ** 2 - mpmath.mpf(px) ** 2 - mpmath.mpf(py) ** 2)
+    xe = x + mpmath.mpf(px) * L / pz
+    dz = L - (k["beta0"] / k["beta"]) * L * opd / pz
+    assert abs(o["x"][0] - float(xe)) <= 4e-16 * (abs(x) + abs(px) * L)
+    assert abs(o["zeta"][0] - float(dz)) <= 2e-16 * L + 1e-15 * abs(float(dz))
+
+
 def test_drift_reversible():
     """A drift of -L undoes a drift of +L to rounding."""
     rng = np.random.default_rng(2)
