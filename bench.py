@@ -302,8 +302,9 @@ def run_ours(args):
     from paper_2310_00317_gb300 import inputs as I
     from paper_2310_00317_gb300 import xtgb
 
+    from paper_2310_00317_gb300 import sharding
     # weak scaling: each rank tracks its own error seed of the ring
-    seed = I.BASE_SEED + rank
+    seed = sharding.rank_seed(I.BASE_SEED, rank)
     el, ref = I.lhc_ring(seed=seed)
     n_el = len(el)
     grid = I.da_grid(el, ref)
@@ -375,17 +376,7 @@ def run_ours(args):
     if tr.sync_status() != xtgb.XT_OK:
         raise RuntimeError("tracking reported an error status")
     total_ms = float(sum(step_ms))
-    if ws > 1:
-        t = torch.tensor([total_ms, float(units_all)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        tsum = t.clone()
-        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
-        total_ms_job = float(tmax[0])
-        units_job = float(tsum[1])
-    else:
-        total_ms_job = total_ms
-        units_job = float(units_all)
+    units_job, total_ms_job = sharding.reduce_throughput(units_all, total_ms, device=dev)
     value = units_job / (total_ms_job * 1e-3)
     achieved = flops_all / (kern_ms * 1e-3)
 
