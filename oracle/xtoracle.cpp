@@ -305,7 +305,8 @@ static inline void mark_lost(Part<T>& p, int code, int turn, int elem) {
 // Exact drift of length L (thin-lens integration: drifts between kicks).
 //   pz = sqrt((1+delta)^2 - px^2 - py^2),  x += px L/pz,  y += py L/pz,
 //   zeta += L - (1+delta)/rvv * L/pz  (path length L(1+delta)/pz at speed beta).
-// With u = (1+delta)^2 - 1 - px^2 - py^2 and yh = 1/pz - 1 = (1+u)^(-1/2) - 1:
+// With u = (1+delta)^2 - 1 - px^2 - py^2 (two fused multiply-adds from
+// dm1 = delta (delta + 2)) and yh = 1/pz - 1 = (1+u)^(-1/2) - 1:
 //   L/pz = L + L yh,   zeta += -L (beta0 ptau + ep yh)   (ep - 1 = beta0 ptau),
 // so the zeta increment is formed from small quantities without cancellation.
 // yh is the Taylor series of (1+u)^(-1/2) - 1 to order 8 (coefficients
@@ -316,8 +317,7 @@ static const double RS_C[9] = {0.0, -0.5, 0.375, -0.3125, 0.2734375, -0.24609375
                                -0.20947265625, 0.196380615234375};
 template <class T>
 static inline void drift(Part<T>& p, double L, int turn, int elem) {
-  T pt2 = FMA(p.px, p.px, p.py * p.py);
-  T u = p.dm1 - pt2;
+  T u = FMA(-p.px, p.px, FMA(-p.py, p.py, p.dm1));
   double uv = val(u);
   if (!(uv > -1.0 && uv < INFINITY)) { mark_lost(p, -2, turn, elem); return; }
   T yh;
@@ -354,6 +354,8 @@ struct MultConst {
   int N;
   double c[11], s[11];
   double hxl, k0h, lrad, ilr2, crl, kql;
+  bool pure;    // knl0 == ksl0 == 0 and hxl == 0: no constant term
+  bool bend;    // hxl != 0, hxl == knl0, ksl0 == 0: field and frame curvature cancel on momentum
 };
 
 // Quantum model: Poisson number of photons with mean
@@ -387,10 +389,37 @@ static inline void quantum_kick(Part<Dual>&, const Dual&, const Dual&, const Mul
 // curvature hxl: px += hxl (1+delta) - knl0 hxl x / L_rad and
 // zeta -= hxl x / rvv (the thin dipole of the curved reference frame).
 // Radiation (mode 1 mean, 2 quantum) is applied once, after the kick, for
-// elements with L_rad > 0, using the field kick (Re b, Im b) only.
+// elements with L_rad > 0, using the field kick (Re b, Im b) only.  Without
+// radiation, elements with no constant term, and bends whose curvature equals
+// their dipole field, add the last Horner step straight into px, py.
 template <class T>
 static inline void multipole(Part<T>& p, const MultConst& m, int rad_mode, const RefConst& rc,
                              uint64_t seed, int turn, int elem) {
+  const bool radiates = rad_mode != 0 && m.lrad > 0.0;
+  if (!radiates && (m.pure || m.bend)) {
+    // Folded form: with (ar, ai) the Horner value after the linear-term step,
+    // Re b = ar x - ai y + knl0, Im b = ar y + ai x + ksl0; the constant terms
+    // vanish (pure) or combine with the curvature term as
+    // -knl0 + hxl (1+delta) = hxl delta (bend, hxl == knl0).
+    T pxv = m.bend ? FMA(m.hxl, p.delta, p.px) : p.px;
+    if (m.N >= 1) {
+      T ar = mkv<T>(m.c[m.N]);
+      T ai = mkv<T>(m.s[m.N]);
+      for (int n = m.N - 1; n >= 1; n--) {
+        T nr = FMA(ar, p.x, FMA(-ai, p.y, mkv<T>(m.c[n])));
+        T ni = FMA(ar, p.y, FMA(ai, p.x, mkv<T>(m.s[n])));
+        ar = nr; ai = ni;
+      }
+      pxv = FMA(-ar, p.x, FMA(ai, p.y, pxv));
+      p.py = FMA(ar, p.y, FMA(ai, p.x, p.py));
+    }
+    p.px = pxv;
+    if (m.bend) {
+      p.px = FMA(-m.k0h, p.x, p.px);
+      p.zeta = FMA(-(m.hxl * p.rv0v), p.x, p.zeta);
+    }
+    return;
+  }
   T br = mkv<T>(m.c[m.N]);
   T bi = mkv<T>(m.s[m.N]);
   for (int n = m.N - 1; n >= 0; n--) {
@@ -453,6 +482,8 @@ static Prep prepare(const Element& e, const RefConst& rc) {
       q.m.ilr2 = (q.m.lrad > 0.0) ? 1.0 / (q.m.lrad * q.m.lrad) : 0.0;
       q.m.crl = rc.crad * q.m.lrad;
       q.m.kql = rc.kq * q.m.lrad;
+      q.m.pure = (e.p[0] == 0.0 && e.p[11] == 0.0 && q.m.hxl == 0.0);
+      q.m.bend = (q.m.hxl != 0.0 && q.m.hxl == e.p[0] && e.p[11] == 0.0);
       break;
     }
     case T_CAVITY: {

@@ -25,14 +25,19 @@ struct RecHdr {
   uint32_t pad;
 };
 static_assert(sizeof(RecHdr) == 16, "record header is 16 bytes");
-enum : uint16_t { REC_CURV = 1, REC_RAD = 2 };
+enum : uint16_t { REC_CURV = 1, REC_RAD = 2, REC_PURE = 4, REC_BEND = 8 };
+// REC_PURE: knl0 == ksl0 == 0 and hxl == 0.  REC_BEND: hxl != 0, hxl == knl0,
+// ksl0 == 0.  Without radiation these multipoles add the last Horner step
+// straight into px, py (and a bend's -knl0 + hxl (1+delta) becomes hxl delta).
 
 // Multipole record parameters (doubles after the header):
 //   [0] hxl  [1] k0h = knl0 hxl / L_rad  [2] crl = crad L_rad  [3] ilr2 = 1/L_rad^2
 //   [4] kql = kq L_rad  [5] L_rad  [6 + 2n] c_n = knl_n/n!  [7 + 2n] s_n = ksl_n/n!
 // Drift: [0] L.  Cavity: [0] krf [1] lag [rad] [2] qv = q0 V/p0c.
 // Edge: [0] r21 [1] r43.  Linear map: [0..35] M in (x,px,y,py,zeta,ptau),
-// [36..41] d.  Aperture: [0] r^2.
+// [36..41] d.  Aperture: [0] r^2 [1] half side of a square inside the circle
+// (r (1 - 2^-20) / sqrt 2): |x|, |y| below it means inside, tested on the
+// integer pipe.
 enum { MP_HXL = 0, MP_K0H = 1, MP_CRL = 2, MP_ILR2 = 3, MP_KQL = 4, MP_LRAD = 5, MP_COEF = 6 };
 
 struct Chunk {

@@ -96,6 +96,8 @@ int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice*
         }
         if (hxl != 0.0) flags |= REC_CURV;
         if (lrad > 0.0) flags |= REC_RAD;
+        if (e.p[0] == 0.0 && e.p[11] == 0.0 && hxl == 0.0) flags |= REC_PURE;
+        if (hxl != 0.0 && hxl == e.p[0] && e.p[11] == 0.0) flags |= REC_BEND;
         break;
       }
       case XT_CAVITY: {
@@ -124,7 +126,9 @@ int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice*
         }
         break;
       }
-      case XT_APERTURE: prm = {e.p[0] * e.p[0]}; break;
+      case XT_APERTURE:
+        prm = {e.p[0] * e.p[0], e.p[0] * (1.0 - 9.5367431640625e-07) * 0.70710678118654752};
+        break;
       default:
         *err = "element " + std::to_string(i) + ": unknown type " + std::to_string(e.type);
         return XT_ERR_UNSUPPORTED;

@@ -255,8 +255,7 @@ struct RadCtx {
 // test and the branch test run on the integer pipe.
 __device__ __forceinline__ bool drift(Part& p, const double* prm) {
   const double L = prm[0];
-  const double pt2 = fma(p.px, p.px, p.py * p.py);
-  const double u = p.dm1 - pt2;
+  const double u = fma(-p.px, p.px, fma(-p.py, p.py, p.dm1));
   const uint64_t ub = dbits(u), ua = ub & 0x7FFFFFFFFFFFFFFFull;
   const bool valid = (ub >> 63) ? (ua < 0x3FF0000000000000ull) : (ub < 0x7FF0000000000000ull);
   if (!valid) return false;
@@ -285,6 +284,32 @@ __device__ __forceinline__ void multipole(Part& p, const double* prm, int order,
                                           const RefDev& r, const RadCtx& rc, int64_t pid, int turn,
                                           uint32_t elem) {
   const double2* cf = (const double2*)(prm + MP_COEF);
+  const bool radiates = RAD != XT_RAD_OFF && (flags & REC_RAD);
+  if (!radiates && (flags & (REC_PURE | REC_BEND))) {
+    // last Horner step added straight into px, py; a bend's constant terms
+    // combine to hxl * delta
+    const bool bend = (flags & REC_BEND) != 0;
+    double pxv = bend ? fma(prm[MP_HXL], p.delta, p.px) : p.px;
+    if (order >= 1) {
+      double2 c = cf[order];
+      double ar = c.x, ai = c.y;
+      for (int n = order - 1; n >= 1; n--) {
+        c = cf[n];
+        const double nr = fma(ar, p.x, fma(-ai, p.y, c.x));
+        const double ni = fma(ar, p.y, fma(ai, p.x, c.y));
+        ar = nr;
+        ai = ni;
+      }
+      pxv = fma(-ar, p.x, fma(ai, p.y, pxv));
+      p.py = fma(ar, p.y, fma(ai, p.x, p.py));
+    }
+    p.px = pxv;
+    if (bend) {
+      p.px = fma(-prm[MP_K0H], p.x, p.px);
+      p.zeta = fma(-(prm[MP_HXL] * p.rv0v), p.x, p.zeta);
+    }
+    return;
+  }
   double2 c = cf[order];
   double br = c.x, bi = c.y;
   for (int n = order - 1; n >= 0; n--) {
@@ -456,15 +481,24 @@ __device__ __forceinline__ int track_tile(const TileLat& L, const TileArrays& A,
         const uint4 hv = *(const uint4*)q;
         const uint32_t type = hv.x & 0xFFFFu, order = hv.x >> 16;
         const uint32_t flags = hv.y & 0xFFFFu, size16 = hv.y >> 16;
-        if (alive) {
-          const int lc = element<RAD>(p, type, order, flags, hv.z, (const double*)(q + 16), ref, sn,
-                                      rc, pid, turn);
-          if (lc != 1) {
-            alive = false;
-            code = lc;
-            lturn = turn;
-            lelem = hv.z;
-          }
+        const double* prm = (const double*)(q + 16);
+        int lc = 1;
+        if (type == XT_APERTURE) {
+          // inside the inscribed square (integer pipe) => inside the circle;
+          // the FP64 test runs only if some live lane of the warp is outside
+          const uint64_t box = dbits(prm[1]);
+          const bool in = !alive || ((dbits(p.x) & 0x7FFFFFFFFFFFFFFFull) <= box &&
+                                     (dbits(p.y) & 0x7FFFFFFFFFFFFFFFull) <= box);
+          if (!__all_sync(FULL_MASK, in) && alive) lc = element<RAD>(p, type, order, flags, hv.z, prm, ref,
+                                                                      sn, rc, pid, turn);
+        } else if (alive) {
+          lc = element<RAD>(p, type, order, flags, hv.z, prm, ref, sn, rc, pid, turn);
+        }
+        if (lc != 1) {
+          alive = false;
+          code = lc;
+          lturn = turn;
+          lelem = hv.z;
         }
         q += size16 * 16u;
       }
