@@ -1,7 +1,7 @@
 // Dynamic-aperture surrogate network: MLP 16 -> 256 -> 256 -> 256 -> 256 -> 2
-// (exact GELU), BF16 weights and activations, FP32 accumulation on the tensor
-// cores, FP32 master weights with Adam.  Hand-written forward, backward and
-// optimiser kernels.
+// (exact GELU), BF16 weights and activations, FP32 accumulation in tensor
+// memory on the tcgen05 tensor cores, FP32 master weights with Adam.
+// Hand-written forward, backward and optimiser kernels.
 //
 // Rounding points (the oracle rounds at the same places): the network input,
 // every weight matrix, every hidden activation and every back-propagated
@@ -58,10 +58,17 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
 }
 
 // ---------------------------------------------------------------------------
-// C[M x N] = A[M x K] * B[N x K]^T with A, B bfloat16 (K contiguous), FP32
-// accumulation on the tensor cores (mma.sync m16n8k16), K a multiple of 16.
-// Block tile 64 x 64, 4 warps of 32 x 32.
-enum { EPI_GELU = 0, EPI_DGRAD = 1, EPI_F32 = 2 };
+// C[M x N] = A[M x K] * B[N x K]^T on the 5th-generation tensor cores
+// (tcgen05): A, B bfloat16 with K contiguous, FP32 accumulator in tensor
+// memory.  One CTA of 128 threads per 128-row tile and all N columns
+// (N = 256 or 16); K is processed in chunks of 64 (a multiple of 16).  Each
+// chunk of A (128 x 64) and B (N x 64) is written to shared memory in the
+// K-major, no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix;
+// neighbouring core matrices 128 bytes apart along M/N, one row-group column
+// apart along K), one thread issues the K/16 tcgen05.mma instructions and
+// commits them to an mbarrier; after the last chunk every warp reads its 32
+// rows of the accumulator with tcgen05.ld and applies the epilogue.
+enum { EPI_GELU = 0, EPI_DGRAD = 1, EPI_F32 = 2, EPI_F32ADD = 3 };
 struct Epi {
   const float* bias;    // EPI_GELU
   float* z;             // EPI_GELU: pre-activation out (may be null); EPI_DGRAD: fp32 dZ out
@@ -69,97 +76,182 @@ struct Epi {
   bf16_t* out_b;        // EPI_GELU: activation; EPI_DGRAD: bf16 dZ
   float* out_f;         // EPI_F32
   int ld;               // leading dimension of every output / zprev
+  int* status;          // set to 1 if a tensor-core wait gave up
 };
 
-constexpr int TM = 64, TN = 64, TK = 16, SP = TK + 8;
+constexpr int TC_M = 128, TC_KC = 64;
+constexpr size_t TC_SMEM_LAUNCH = 100 * 1024;  // at most 2 CTAs per SM: 2 x 256 TMEM columns
+constexpr int64_t TC_WAIT_LIMIT = 2000000000LL;
 
-__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+__device__ __forceinline__ uint32_t sm_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride (M/N)
+// byte offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo & 0x3FFFF) >> 4) << 16;
+  d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
 }
 
 template <int EPI>
-__global__ void __launch_bounds__(128) gemm_nt_kernel(const bf16_t* __restrict__ A, int lda,
-                                                      const bf16_t* __restrict__ B, int ldb, int M, int N,
-                                                      int K, Epi e) {
-  __shared__ __align__(16) bf16_t As[TM][SP];
-  __shared__ __align__(16) bf16_t Bs[TN][SP];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp >> 1, wn = warp & 1;
-  const int g = lane >> 2, t = lane & 3;
-  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; i++)
-#pragma unroll
-    for (int j = 0; j < 4; j++)
-#pragma unroll
-      for (int q = 0; q < 4; q++) acc[i][j][q] = 0.f;
-  const int lr = tid >> 1, lc = (tid & 1) * 8;  // 64 rows x 2 halves of 8
-  for (int k0 = 0; k0 < K; k0 += TK) {
-    uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
-    if (m0 + lr < M) va = *(const uint4*)(A + (int64_t)(m0 + lr) * lda + k0 + lc);
-    if (n0 + lr < N) vb = *(const uint4*)(B + (int64_t)(n0 + lr) * ldb + k0 + lc);
-    *(uint4*)&As[lr][lc] = va;
-    *(uint4*)&Bs[lr][lc] = vb;
-    __syncthreads();
-    uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-    for (int i = 0; i < 2; i++) {
-      const int r = wm * 32 + i * 16 + g;
-      af[i][0] = *(const uint32_t*)&As[r][2 * t];
-      af[i][1] = *(const uint32_t*)&As[r + 8][2 * t];
-      af[i][2] = *(const uint32_t*)&As[r][2 * t + 8];
-      af[i][3] = *(const uint32_t*)&As[r + 8][2 * t + 8];
-    }
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-      const int c = wn * 32 + j * 8 + g;
-      bfr[j][0] = *(const uint32_t*)&Bs[c][2 * t];
-      bfr[j][1] = *(const uint32_t*)&Bs[c][2 * t + 8];
-    }
-#pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-      for (int j = 0; j < 4; j++) mma_bf16(acc[i][j], af[i], bfr[j]);
-    __syncthreads();
+__device__ __forceinline__ void epi_store(const Epi& e, int row, int col, float v) {
+  const int64_t o = (int64_t)row * e.ld + col;
+  if (EPI == EPI_GELU) {
+    const float z = v + e.bias[col];
+    if (e.z) e.z[o] = z;
+    e.out_b[o] = f2bf(gelu_f(z));
+  } else if (EPI == EPI_DGRAD) {
+    const float dz = v * gelu_grad_f(e.zprev[o]);
+    e.z[o] = dz;
+    e.out_b[o] = f2bf(dz);
+  } else if (EPI == EPI_F32) {
+    e.out_f[o] = v;
+  } else {
+    atomicAdd(&e.out_f[o], v);  // split-K partial sum
   }
-#pragma unroll
-  for (int i = 0; i < 2; i++) {
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const int row = m0 + wm * 32 + i * 16 + g + ((q & 2) ? 8 : 0);
-        const int col = n0 + wn * 32 + j * 8 + 2 * t + (q & 1);
-        if (row >= M || col >= N) continue;
-        const int64_t o = (int64_t)row * e.ld + col;
-        const float v = acc[i][j][q];
-        if (EPI == EPI_GELU) {
-          const float z = v + e.bias[col];
-          if (e.z) e.z[o] = z;
-          e.out_b[o] = f2bf(gelu_f(z));
-        } else if (EPI == EPI_DGRAD) {
-          const float dz = v * gelu_grad_f(e.zprev[o]);
-          e.z[o] = dz;
-          e.out_b[o] = f2bf(dz);
-        } else {
-          e.out_f[o] = v;
-        }
+}
+
+template <int EPI, int N>
+__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const bf16_t* __restrict__ A, int lda,
+                                                      const bf16_t* __restrict__ B, int ldb, int M, int K, Epi e) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + TC_M * TC_KC * 2;
+  uint64_t* bar = (uint64_t*)(sB + N * TC_KC * 2);
+  uint32_t* tslot = (uint32_t*)(bar + 1);
+  constexpr uint32_t NCOLS = (N <= 32) ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * TC_M;
+  // split-K: this CTA sums K in [kbeg, kend) (gridDim.y slices of multiples of 64)
+  const int kslice = ((K + gridDim.y * TC_KC - 1) / (gridDim.y * TC_KC)) * TC_KC;
+  const int kbeg = blockIdx.y * kslice;
+  const int kend = (kbeg + kslice) < K ? (kbeg + kslice) : K;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_addr(tslot)),
+                 "r"(NCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  // instruction descriptor: D f32, A and B bf16, both K-major, N >> 3, M >> 4
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+                         ((uint32_t)(TC_M >> 4) << 24);
+  uint32_t phase = 0;
+  int ok = 1;
+  for (int k0 = kbeg; k0 < kend; k0 += TC_KC) {
+    const int kc_n = (kend - k0) < TC_KC ? (kend - k0) : TC_KC;
+    const int nvec = kc_n / 8;
+    for (int v = tid; v < TC_M * nvec; v += 128) {
+      const int m = v / nvec, kc = v % nvec;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (m0 + m < M) val = *(const uint4*)(A + (int64_t)(m0 + m) * lda + k0 + kc * 8);
+      *(uint4*)(sA + ((kc * (TC_M / 8)) + (m >> 3)) * 128 + (m & 7) * 16) = val;
+    }
+    for (int v = tid; v < N * nvec; v += 128) {
+      const int n = v / nvec, kc = v % nvec;
+      const uint4 val = *(const uint4*)(B + (int64_t)n * ldb + k0 + kc * 8);
+      *(uint4*)(sB + ((kc * (N / 8)) + (n >> 3)) * 128 + (n & 7) * 16) = val;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int s = 0; s < kc_n / 16; s++) {
+        const uint64_t ad = smem_desc(sm_addr(sA + (2 * s * (TC_M / 8)) * 128), (TC_M / 8) * 128, 128);
+        const uint64_t bd = smem_desc(sm_addr(sB + (2 * s * (N / 8)) * 128), (N / 8) * 128, 128);
+        const uint32_t accumulate = (k0 > kbeg || s > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       sm_addr(bar))
+                   : "memory");
+    }
+    uint32_t done = 0;
+    const long long t0 = clock64();
+    while (!done) {
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(done)
+          : "r"(sm_addr(bar)), "r"(phase)
+          : "memory");
+      if (!done && clock64() - t0 > TC_WAIT_LIMIT) break;
+    }
+    phase ^= 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ok = __syncthreads_and(ok && done);  // the buffers are rewritten only after every MMA read them
+    if (!ok) break;
+  }
+  if (ok && kbeg < kend) {
+    const int row = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < N; c0 += 32) {
+      uint32_t r[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+            "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+            "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+            "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < M) {
+        const int cmax = (N - c0) < 32 ? (N - c0) : 32;
+#pragma unroll 8
+        for (int j = 0; j < cmax; j++) epi_store<EPI>(e, row, c0 + j, __uint_as_float(r[j]));
       }
     }
+  } else if (tid == 0 && e.status) {
+    atomicExch(e.status, 1);
   }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS) : "memory");
 }
 
+template <int EPI, int N>
+int tc_launch(const bf16_t* A, int lda, const bf16_t* B, int ldb, int M, int K, const Epi& e, cudaStream_t s,
+              int ksplit) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t r = cudaFuncSetAttribute(tc_gemm_kernel<EPI, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TC_SMEM_LAUNCH);
+    if (r != cudaSuccess) return (int)r;
+    attr = true;
+  }
+  dim3 grid((M + TC_M - 1) / TC_M, ksplit);
+  tc_gemm_kernel<EPI, N><<<grid, 128, TC_SMEM_LAUNCH, s>>>(A, lda, B, ldb, M, K, e);
+  return (int)cudaGetLastError();
+}
+
+// C = A B^T with N in {16, 256}; K a multiple of 16; lda, ldb multiples of 8.
+// EPI_F32ADD splits K over `ksplit` CTAs per row tile and adds the partial
+// sums into a zeroed output.
 template <int EPI>
 int gemm(const bf16_t* A, int lda, const bf16_t* B, int ldb, int M, int N, int K, const Epi& e,
-         cudaStream_t s) {
-  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
-  gemm_nt_kernel<EPI><<<grid, 128, 0, s>>>(A, lda, B, ldb, M, N, K, e);
-  return (int)cudaGetLastError();
+         cudaStream_t s, int ksplit = 1) {
+  if (M <= 0) return 0;
+  if (K % 16 || lda % 8 || ldb % 8 || ksplit < 1 || (ksplit > 1 && EPI != EPI_F32ADD))
+    return (int)cudaErrorInvalidValue;
+  if (N == 256) return tc_launch<EPI, 256>(A, lda, B, ldb, M, K, e, s, ksplit);
+  if (N == 16) return tc_launch<EPI, 16>(A, lda, B, ldb, M, K, e, s, ksplit);
+  return (int)cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------
@@ -378,6 +470,7 @@ static int forward_layers(xs_mlp* n, int64_t B, bool keep_z, bf16_t** acts, floa
     e.z = keep_z ? n->z[l] : nullptr;
     e.out_b = acts[l + 1];
     e.ld = 256;
+    e.status = (int*)(n->scal + 3);
     int rc = gemm<EPI_GELU>(acts[l], WIDTH[l], n->wb + OFF_W[l], WIDTH[l], (int)B, 256, WIDTH[l], e, s);
     if (rc) return cuda_fail((cudaError_t)rc, "forward gemm");
   }
@@ -396,7 +489,7 @@ static int loss_grad(xs_mlp* n, const float* X, const float* y, const float* t, 
   CK(cudaGetLastError());
   rc = forward_layers(n, B, true, n->a, n->out, s);
   if (rc) return rc;
-  CK(cudaMemsetAsync(n->scal, 0, 2 * sizeof(float), s));
+  CK(cudaMemsetAsync(n->scal, 0, 2 * sizeof(float), s));  // loss, mask count (scal[3]: status)
   mask_count_kernel<<<grid_1d(B, 256), 256, 0, s>>>(mask, B, n->scal + 1);
   loss_kernel<<<grid_1d(B, 256), 256, 0, s>>>(n->out, y, t, mask, B, lam, n->dout, n->scal);
   CK(cudaMemsetAsync(n->grad, 0, NPARAM * sizeof(float), s));
@@ -417,7 +510,10 @@ static int loss_grad(xs_mlp* n, const float* X, const float* y, const float* t, 
     std::memset(&e, 0, sizeof(e));
     e.out_f = n->grad + OFF_W[l];
     e.ld = in;
-    rc = gemm<EPI_F32>(n->dzT, (int)Bp, n->aT, (int)Bp, 256, in, (int)Bp, e, s);
+    e.status = (int*)(n->scal + 3);
+    // split K (the batch) so that about 64 CTAs share the reduction
+    const int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(32, Bp / 128));
+    rc = gemm<EPI_F32ADD>(n->dzT, (int)Bp, n->aT, (int)Bp, 256, in, (int)Bp, e, s, ksplit);
     if (rc) return cuda_fail((cudaError_t)rc, "wgrad gemm");
     colsum_kernel<<<(int)std::min<int64_t>(B, 1024), 256, 0, s>>>(n->dzf[cur], B, 256, n->grad + OFF_B[l]);
     CK(cudaGetLastError());
@@ -429,6 +525,7 @@ static int loss_grad(xs_mlp* n, const float* X, const float* y, const float* t, 
       d.z = n->dzf[1 - cur];
       d.out_b = n->dzb[1 - cur];
       d.ld = 256;
+      d.status = (int*)(n->scal + 3);
       rc = gemm<EPI_DGRAD>(n->dzb[cur], 256, n->wtb + OFF_W[l], 256, (int)B, 256, 256, d, s);
       if (rc) return cuda_fail((cudaError_t)rc, "dgrad gemm");
       cur = 1 - cur;
@@ -456,6 +553,7 @@ int xs_mlp_create(uint64_t seed, xs_mlp** out) {
       cudaMalloc(&n->wtb, NPARAM * sizeof(bf16_t)) != cudaSuccess ||
       cudaMalloc(&n->scal, 4 * sizeof(float)) != cudaSuccess)
     return bail(fail(XT_ERR_NOMEM, "cudaMalloc of the network parameters failed"));
+  if (cudaMemset(n->scal, 0, 4 * sizeof(float)) != cudaSuccess) return bail(fail(XT_ERR_CUDA, "cudaMemset"));
   // uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) initialisation on the host
   std::vector<float> h(NPARAM);
   std::mt19937_64 rng(seed);
@@ -498,7 +596,10 @@ int xs_mlp_get_params(xs_mlp* n, float* params, int64_t count, void* stream) {
   if (!n || !params || count != NPARAM) return fail(XT_ERR_INVALID, "need 202242 parameters");
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaMemcpyAsync(params, n->master, NPARAM * sizeof(float), cudaMemcpyDeviceToHost, s));
+  int32_t st = 0;
+  CK(cudaMemcpyAsync(&st, n->scal + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (st) return fail(XT_ERR_TIMEOUT, "a tensor-core wait gave up in an earlier network kernel");
   return XT_OK;
 }
 
