@@ -7,9 +7,12 @@
 // every weight matrix, every hidden activation and every back-propagated
 // pre-activation gradient dZ are bfloat16; accumulations, biases, GELU and its
 // derivative, the head (256 -> 2), the loss and Adam are FP32.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -60,74 +63,158 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
 // ---------------------------------------------------------------------------
 // C[M x N] = A[M x K] * B[N x K]^T on the 5th-generation tensor cores
 // (tcgen05): A, B bfloat16 with K contiguous, FP32 accumulator in tensor
-// memory.  One CTA of 128 threads per 128-row tile and all N columns
-// (N = 256 or 16); K is processed in chunks of 64 (a multiple of 16).  Each
-// chunk of A (128 x 64) and B (N x 64) is written to shared memory in the
-// K-major, no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix;
-// neighbouring core matrices 128 bytes apart along M/N, one row-group column
-// apart along K), one thread issues the K/16 tcgen05.mma instructions and
-// commits them to an mbarrier; after the last chunk every warp reads its 32
-// rows of the accumulator with tcgen05.ld and applies the epilogue.
-enum { EPI_GELU = 0, EPI_DGRAD = 1, EPI_F32 = 2, EPI_F32ADD = 3 };
+// memory.  A tile is 128 rows x BN columns (BN = 64, or 16 for the narrow
+// first-layer weight gradient) over a K slice of at most 256.  Operands
+// arrive by TMA (cp.async.bulk.tensor) in 64-wide K blocks, one mbarrier per
+// block, in the 128-byte-swizzled K-major layout the tensor cores read
+// directly (rows of 128 bytes, 8-row groups 1024 bytes apart); K positions
+// beyond the tensor are zero-filled by the copy engine, which also covers
+// the 16-wide input layer and ragged tails.  One thread waits for each block
+// and issues its K/16 tcgen05.mma; a commit to an mbarrier signals the
+// accumulator.  CTAs are persistent over tiles (n fastest, so CTAs running
+// together share rows of A); as soon as a tile's MMAs are done the next
+// tile's operands are requested, and the copies overlap the epilogue: 8
+// warps, two per group of 32 accumulator lanes (rows), read the accumulator
+// with tcgen05.ld and apply the fused epilogue with 16-byte stores.  Two
+// CTAs share an SM, so one CTA's MMAs also overlap the other's epilogue.
+enum { EPI_GELU = 0, EPI_DGRAD = 1, EPI_F32ADD = 2 };
 struct Epi {
   const float* bias;    // EPI_GELU
   float* z;             // EPI_GELU: pre-activation out (may be null); EPI_DGRAD: fp32 dZ out
   const float* zprev;   // EPI_DGRAD: pre-activation of this layer's output
   bf16_t* out_b;        // EPI_GELU: activation; EPI_DGRAD: bf16 dZ
-  float* out_f;         // EPI_F32
-  int ld;               // leading dimension of every output / zprev
-  int* status;          // set to 1 if a tensor-core wait gave up
+  float* out_f;         // EPI_F32ADD
+  int ld;               // leading dimension of every output / zprev (a multiple of 4)
+  int* status;          // set to 1 if a tensor-core or copy wait gave up
 };
 
-constexpr int TC_M = 128, TC_KC = 64;
-constexpr size_t TC_SMEM_LAUNCH = 100 * 1024;  // at most 2 CTAs per SM: 2 x 256 TMEM columns
-constexpr int64_t TC_WAIT_LIMIT = 2000000000LL;
+constexpr int TC_M = 128, TC_BK = 64, TC_NST = 4, TC_KSLICE = TC_NST * TC_BK;
+constexpr int64_t TC_WAIT_LIMIT = 2000000000LL;  // clock cycles, about one second
 
 __device__ __forceinline__ uint32_t sm_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Shared-memory matrix descriptor: start address, leading (K) and stride (M/N)
-// byte offsets, descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor for a K-major operand in the 128-byte
+// swizzle layout: start address, 8-row groups 1024 bytes apart (the leading
+// offset is not used by this layout), descriptor version 1, swizzle mode 2.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
-  d |= (uint64_t)((lbo & 0x3FFFF) >> 4) << 16;
-  d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
   d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
   return d;
 }
 
-template <int EPI>
-__device__ __forceinline__ void epi_store(const Epi& e, int row, int col, float v) {
-  const int64_t o = (int64_t)row * e.ld + col;
-  if (EPI == EPI_GELU) {
-    const float z = v + e.bias[col];
-    if (e.z) e.z[o] = z;
-    e.out_b[o] = f2bf(gelu_f(z));
-  } else if (EPI == EPI_DGRAD) {
-    const float dz = v * gelu_grad_f(e.zprev[o]);
-    e.z[o] = dz;
-    e.out_b[o] = f2bf(dz);
-  } else if (EPI == EPI_F32) {
-    e.out_f[o] = v;
-  } else {
-    atomicAdd(&e.out_f[o], v);  // split-K partial sum
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > TC_WAIT_LIMIT) return false;
   }
 }
 
-template <int EPI, int N>
-__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const bf16_t* __restrict__ A, int lda,
-                                                      const bf16_t* __restrict__ B, int ldb, int M, int K, Epi e) {
-  extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + TC_M * TC_KC * 2;
-  uint64_t* bar = (uint64_t*)(sB + N * TC_KC * 2);
-  uint32_t* tslot = (uint32_t*)(bar + 1);
-  constexpr uint32_t NCOLS = (N <= 32) ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(tm), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+template <int CH>
+__device__ __forceinline__ void tmem_load(uint32_t taddr, uint32_t* r);
+template <>
+__device__ __forceinline__ void tmem_load<32>(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+template <>
+__device__ __forceinline__ void tmem_load<16>(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Epilogue of CH accumulator columns [col, col + CH) of one row.
+template <int EPI, int CH>
+__device__ __forceinline__ void epilogue(const Epi& e, int row, int col, const uint32_t* r) {
+  const int64_t o = (int64_t)row * e.ld + col;
+  if (EPI == EPI_F32ADD) {
+#pragma unroll
+    for (int q = 0; q < CH / 4; q++)
+      atomicAdd((float4*)(e.out_f + o + 4 * q),
+                make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]), __uint_as_float(r[4 * q + 2]),
+                            __uint_as_float(r[4 * q + 3])));
+  } else {
+    float v[CH];
+#pragma unroll
+    for (int q = 0; q < CH / 4; q++) {
+      float4 a;
+      if (EPI == EPI_GELU) a = __ldg((const float4*)(e.bias + col) + q);
+      else a = __ldg((const float4*)(e.zprev + o) + q);
+      const float aa[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        const float acc = __uint_as_float(r[4 * q + i]);
+        v[4 * q + i] = (EPI == EPI_GELU) ? acc + aa[i] : acc * gelu_grad_f(aa[i]);
+      }
+    }
+    if (e.z) {
+#pragma unroll
+      for (int q = 0; q < CH / 4; q++)
+        *(float4*)(e.z + o + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+    uint32_t h[CH / 2];
+#pragma unroll
+    for (int i = 0; i < CH / 2; i++) {
+      const float a = (EPI == EPI_GELU) ? gelu_f(v[2 * i]) : v[2 * i];
+      const float b = (EPI == EPI_GELU) ? gelu_f(v[2 * i + 1]) : v[2 * i + 1];
+      h[i] = pack_bf16x2(a, b);
+    }
+#pragma unroll
+    for (int q = 0; q < CH / 8; q++)
+      *(uint4*)(e.out_b + o + 8 * q) = make_uint4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+  }
+}
+
+template <int EPI, int BN>
+__global__ void __launch_bounds__(256) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                      const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
+                                                      Epi e) {
+  constexpr int A_BYTES = TC_M * TC_BK * 2, B_BYTES = BN * TC_BK * 2, STAGE = A_BYTES + B_BYTES;
+  static_assert(STAGE % 1024 == 0, "stages must keep the 1024-byte alignment of the swizzle atoms");
+  constexpr uint32_t NCOLS = BN < 32 ? 32 : BN;
+  constexpr int CH = BN < 32 ? BN : 32;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + TC_NST * STAGE);
+  uint64_t* mma_bar = full + TC_NST;
+  uint32_t* tslot = (uint32_t*)(mma_bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * TC_M;
-  // split-K: this CTA sums K in [kbeg, kend) (gridDim.y slices of multiples of 64)
-  const int kslice = ((K + gridDim.y * TC_KC - 1) / (gridDim.y * TC_KC)) * TC_KC;
-  const int kbeg = blockIdx.y * kslice;
-  const int kend = (kbeg + kslice) < K ? (kbeg + kslice) : K;
+  const int n_mt = (M + TC_M - 1) / TC_M, n_nt = N / BN, n_ks = (K + TC_KSLICE - 1) / TC_KSLICE;
+  const int n_tiles = n_mt * n_nt * n_ks;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_addr(tslot)),
                  "r"(NCOLS)
@@ -135,89 +222,110 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const bf16_t* __restric
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(bar)) : "memory");
+    for (int j = 0; j <= TC_NST; j++)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(full + j)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
   // instruction descriptor: D f32, A and B bf16, both K-major, N >> 3, M >> 4
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                          ((uint32_t)(TC_M >> 4) << 24);
-  uint32_t phase = 0;
-  int ok = 1;
-  for (int k0 = kbeg; k0 < kend; k0 += TC_KC) {
-    const int kc_n = (kend - k0) < TC_KC ? (kend - k0) : TC_KC;
-    const int nvec = kc_n / 8;
-    for (int v = tid; v < TC_M * nvec; v += 128) {
-      const int m = v / nvec, kc = v % nvec;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (m0 + m < M) val = *(const uint4*)(A + (int64_t)(m0 + m) * lda + k0 + kc * 8);
-      *(uint4*)(sA + ((kc * (TC_M / 8)) + (m >> 3)) * 128 + (m & 7) * 16) = val;
+  auto coords = [&](int t, int& m0, int& n0, int& k0, int& k1) {
+    const int nt = t % n_nt, mt = (t / n_nt) % n_mt, ks = t / (n_nt * n_mt);
+    m0 = mt * TC_M;
+    n0 = nt * BN;
+    k0 = ks * TC_KSLICE;
+    k1 = min(K, k0 + TC_KSLICE);
+  };
+  uint32_t pending = 0;  // K blocks with copies in flight (thread 0)
+  auto request = [&](int t) {
+    int m0, n0, k0, k1;
+    coords(t, m0, n0, k0, k1);
+    for (int j = 0; k0 + j * TC_BK < k1; j++) {
+      const uint32_t bar = sm_addr(full + j);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(STAGE) : "memory");
+      tma_load_2d(sm_addr(smem + j * STAGE), &tmA, k0 + j * TC_BK, m0, bar);
+      tma_load_2d(sm_addr(smem + j * STAGE + A_BYTES), &tmB, k0 + j * TC_BK, n0, bar);
+      pending |= 1u << j;
     }
-    for (int v = tid; v < N * nvec; v += 128) {
-      const int n = v / nvec, kc = v % nvec;
-      const uint4 val = *(const uint4*)(B + (int64_t)n * ldb + k0 + kc * 8);
-      *(uint4*)(sB + ((kc * (N / 8)) + (n >> 3)) * 128 + (n & 7) * 16) = val;
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+  };
+  uint32_t fphase = 0, mphase = 0;  // barrier parities (thread 0)
+  int ok = 1, mma_open = 0;
+  int t = blockIdx.x;
+  if (tid == 0 && t < n_tiles) request(t);
+  for (; t < n_tiles; t += gridDim.x) {
+    int m0, n0, k0, k1;
+    coords(t, m0, n0, k0, k1);
     if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int s = 0; s < kc_n / 16; s++) {
-        const uint64_t ad = smem_desc(sm_addr(sA + (2 * s * (TC_M / 8)) * 128), (TC_M / 8) * 128, 128);
-        const uint64_t bd = smem_desc(sm_addr(sB + (2 * s * (N / 8)) * 128), (N / 8) * 128, 128);
-        const uint32_t accumulate = (k0 > kbeg || s > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
-            : "memory");
+      for (int j = 0; k0 + j * TC_BK < k1; j++) {
+        if (!mbar_wait(sm_addr(full + j), (fphase >> j) & 1)) {
+          ok = 0;
+          break;
+        }
+        fphase ^= 1u << j;
+        pending &= ~(1u << j);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int kc = min(TC_BK, k1 - (k0 + j * TC_BK));
+        const uint64_t ad = smem_desc_sw128(sm_addr(smem + j * STAGE));
+        const uint64_t bd = smem_desc_sw128(sm_addr(smem + j * STAGE + A_BYTES));
+        for (int s = 0; s * 16 < kc; s++) {  // K = 16 per instruction: +32 bytes in the swizzled row
+          const uint32_t accumulate = (j > 0 || s > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+              "l"(ad + 2 * s), "l"(bd + 2 * s), "r"(idesc), "r"(accumulate)
+              : "memory");
+          mma_open = 1;
+        }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       sm_addr(bar))
-                   : "memory");
+      if (ok) {
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         sm_addr(mma_bar))
+                     : "memory");
+        if (mbar_wait(sm_addr(mma_bar), mphase)) {
+          mma_open = 0;
+          mphase ^= 1;
+        } else {
+          ok = 0;
+        }
+      }
     }
-    uint32_t done = 0;
-    const long long t0 = clock64();
-    while (!done) {
-      asm volatile(
-          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-          "selp.u32 %0, 1, 0, p;\n\t}"
-          : "=r"(done)
-          : "r"(sm_addr(bar)), "r"(phase)
-          : "memory");
-      if (!done && clock64() - t0 > TC_WAIT_LIMIT) break;
-    }
-    phase ^= 1;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    ok = __syncthreads_and(ok && done);  // the buffers are rewritten only after every MMA read them
+    ok = __syncthreads_and(ok);
     if (!ok) break;
-  }
-  if (ok && kbeg < kend) {
-    const int row = m0 + warp * 32 + lane;
-    for (int c0 = 0; c0 < N; c0 += 32) {
-      uint32_t r[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-            "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-            "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-            "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < M) {
-        const int cmax = (N - c0) < 32 ? (N - c0) : 32;
-#pragma unroll 8
-        for (int j = 0; j < cmax; j++) epi_store<EPI>(e, row, c0 + j, __uint_as_float(r[j]));
-      }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // the MMAs have read the operands: request the next tile's now, so the
+    // copies run under this tile's epilogue
+    if (tid == 0 && t + (int)gridDim.x < n_tiles) request(t + gridDim.x);
+    // warps w and w + 4 share the 32 accumulator lanes (rows) of quadrant
+    // w mod 4 and split the columns
+    const int quad = warp & 3;
+    const int row = m0 + quad * 32 + lane;
+#pragma unroll 1
+    for (int c0 = (warp >> 2) * CH; c0 < BN; c0 += 2 * CH) {
+      uint32_t r[CH];
+      tmem_load<CH>(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, r);
+      if (row < M) epilogue<EPI, CH>(e, row, n0 + c0, r);
     }
-  } else if (tid == 0 && e.status) {
-    atomicExch(e.status, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (!ok && tid == 0) {
+    if (e.status) atomicExch(e.status, 1);
+    // let copies and MMAs still in flight finish (bounded) before the
+    // shared and tensor memory are released
+    for (int j = 0; j < TC_NST; j++)
+      if (pending & (1u << j)) mbar_wait(sm_addr(full + j), (fphase >> j) & 1);
+    if (mma_open) {
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       sm_addr(mma_bar))
+                   : "memory");
+      mbar_wait(sm_addr(mma_bar), mphase);
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -225,33 +333,101 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const bf16_t* __restric
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS) : "memory");
 }
 
-template <int EPI, int N>
-int tc_launch(const bf16_t* A, int lda, const bf16_t* B, int ldb, int M, int K, const Epi& e, cudaStream_t s,
-              int ksplit) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t r = cudaFuncSetAttribute(tc_gemm_kernel<EPI, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)TC_SMEM_LAUNCH);
-    if (r != cudaSuccess) return (int)r;
-    attr = true;
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
   }
-  dim3 grid((M + TC_M - 1) / TC_M, ksplit);
-  tc_gemm_kernel<EPI, N><<<grid, 128, TC_SMEM_LAUNCH, s>>>(A, lda, B, ldb, M, K, e);
-  return (int)cudaGetLastError();
+  return fn;
 }
 
-// C = A B^T with N in {16, 256}; K a multiple of 16; lda, ldb multiples of 8.
-// EPI_F32ADD splits K over `ksplit` CTAs per row tile and adds the partial
-// sums into a zeroed output.
+// rows x cols bfloat16, row stride ld elements; boxes of 64 columns x box_rows
+// rows in the 128-byte swizzle, zero fill outside the tensor.
+int make_tensor_map(CUtensorMap* m, const bf16_t* ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return fail(XT_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  if (((uintptr_t)ptr & 15) || (ld * 2) % 16 || rows < 1 || cols < 1)
+    return fail(XT_ERR_INVALID, "tensor map: base must be 16-byte aligned and the row stride a multiple of 16 bytes");
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)ptr, dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(XT_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return XT_OK;
+}
+
+int sm_count_of_current_device() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (!cache[dev]) cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev);
+  return cache[dev];
+}
+
+template <int EPI, int BN>
+int tc_launch(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, const Epi& e, cudaStream_t s) {
+  constexpr size_t smem = (size_t)TC_NST * (TC_M * TC_BK * 2 + BN * TC_BK * 2) + 1024 + 256;
+  static int occ = 0;
+  if (!occ) {
+    CK(cudaFuncSetAttribute(tc_gemm_kernel<EPI, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CK(cudaFuncSetAttribute(tc_gemm_kernel<EPI, BN>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                            (int)cudaSharedmemCarveoutMaxShared));
+    // CTAs per SM from the shared memory (with the per-block reservation) and
+    // the 512 tensor-memory columns; the CTAs of the persistent grid never wait
+    // on one another, so launching more than fit at once is only slower
+    int dev = 0, per_sm = 0, reserved = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    CK(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    const int by_smem = per_sm / (int)(smem + (size_t)reserved);
+    occ = std::max(1, std::min(by_smem, 512 / (BN < 32 ? 32 : BN)));
+  }
+  const int64_t tiles = (int64_t)((M + TC_M - 1) / TC_M) * (N / BN) * ((K + TC_KSLICE - 1) / TC_KSLICE);
+  const int sms = sm_count_of_current_device();
+  if (sms <= 0) return fail(XT_ERR_CUDA, "device attribute");
+  const int grid = (int)std::min<int64_t>(tiles, (int64_t)occ * sms);
+  tc_gemm_kernel<EPI, BN><<<grid, 256, smem, s>>>(ta, tb, M, N, K, e);
+  CK(cudaGetLastError());
+  return XT_OK;
+}
+
+// C = A B^T: A (M x K, row stride lda), B (N x K, row stride ldb), N = 256 or
+// 16 (16 only for the split-K weight gradient).  K slices of 256 run in
+// separate CTAs; EPI_F32ADD adds their partial sums into a zeroed output,
+// the other epilogues need K <= 256.
 template <int EPI>
-int gemm(const bf16_t* A, int lda, const bf16_t* B, int ldb, int M, int N, int K, const Epi& e,
-         cudaStream_t s, int ksplit = 1) {
-  if (M <= 0) return 0;
-  if (K % 16 || lda % 8 || ldb % 8 || ksplit < 1 || (ksplit > 1 && EPI != EPI_F32ADD))
-    return (int)cudaErrorInvalidValue;
-  if (N == 256) return tc_launch<EPI, 256>(A, lda, B, ldb, M, K, e, s, ksplit);
-  if (N == 16) return tc_launch<EPI, 16>(A, lda, B, ldb, M, K, e, s, ksplit);
-  return (int)cudaErrorInvalidValue;
+int gemm(const bf16_t* A, int lda, const bf16_t* B, int ldb, int M, int N, int K, const Epi& e, cudaStream_t s) {
+  if (M <= 0) return XT_OK;
+  if (K < 1 || (K > TC_KSLICE && EPI != EPI_F32ADD) || e.ld % 4)
+    return fail(XT_ERR_INVALID, "gemm: K must be in 1..256 for this epilogue and ld a multiple of 4");
+  alignas(64) CUtensorMap ta, tb;
+  int rc = make_tensor_map(&ta, A, M, K, lda, TC_M);
+  if (rc) return rc;
+  if (N == 256) {
+    rc = make_tensor_map(&tb, B, N, K, ldb, 64);
+    if (rc) return rc;
+    return tc_launch<EPI, 64>(ta, tb, M, N, K, e, s);
+  }
+  if constexpr (EPI == EPI_F32ADD) {
+    if (N == 16) {
+      rc = make_tensor_map(&tb, B, N, K, ldb, 16);
+      if (rc) return rc;
+      return tc_launch<EPI, 16>(ta, tb, M, N, K, e, s);
+    }
+  }
+  return fail(XT_ERR_INVALID, "gemm: unsupported N");
 }
 
 // ---------------------------------------------------------------------------
@@ -471,8 +647,8 @@ static int forward_layers(xs_mlp* n, int64_t B, bool keep_z, bf16_t** acts, floa
     e.out_b = acts[l + 1];
     e.ld = 256;
     e.status = (int*)(n->scal + 3);
-    int rc = gemm<EPI_GELU>(acts[l], WIDTH[l], n->wb + OFF_W[l], WIDTH[l], (int)B, 256, WIDTH[l], e, s);
-    if (rc) return cuda_fail((cudaError_t)rc, "forward gemm");
+    const int rc = gemm<EPI_GELU>(acts[l], WIDTH[l], n->wb + OFF_W[l], WIDTH[l], (int)B, 256, WIDTH[l], e, s);
+    if (rc) return rc;
   }
   const int64_t threads = B * 32;
   head_forward_kernel<<<(int)((threads + 255) / 256), 256, 0, s>>>(acts[NL - 1], n->wb + OFF_W[NL - 1],
@@ -511,10 +687,9 @@ static int loss_grad(xs_mlp* n, const float* X, const float* y, const float* t, 
     e.out_f = n->grad + OFF_W[l];
     e.ld = in;
     e.status = (int*)(n->scal + 3);
-    // split K (the batch) so that about 64 CTAs share the reduction
-    const int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(32, Bp / 128));
-    rc = gemm<EPI_F32ADD>(n->dzT, (int)Bp, n->aT, (int)Bp, 256, in, (int)Bp, e, s, ksplit);
-    if (rc) return cuda_fail((cudaError_t)rc, "wgrad gemm");
+    // K (the batch) is split in slices of 256 whose partial sums add up in the gradient
+    rc = gemm<EPI_F32ADD>(n->dzT, (int)Bp, n->aT, (int)Bp, 256, in, (int)Bp, e, s);
+    if (rc) return rc;
     colsum_kernel<<<(int)std::min<int64_t>(B, 1024), 256, 0, s>>>(n->dzf[cur], B, 256, n->grad + OFF_B[l]);
     CK(cudaGetLastError());
     if (l > 0) {
@@ -527,7 +702,7 @@ static int loss_grad(xs_mlp* n, const float* X, const float* y, const float* t, 
       d.ld = 256;
       d.status = (int*)(n->scal + 3);
       rc = gemm<EPI_DGRAD>(n->dzb[cur], 256, n->wtb + OFF_W[l], 256, (int)B, 256, 256, d, s);
-      if (rc) return cuda_fail((cudaError_t)rc, "dgrad gemm");
+      if (rc) return rc;
       cur = 1 - cur;
     }
   }
