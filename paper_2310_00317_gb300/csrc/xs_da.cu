@@ -9,6 +9,7 @@
 // that xt_track's own compaction tracks only that band.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cstdint>
 #include <string>
 
@@ -16,6 +17,20 @@
 
 namespace {
 thread_local std::string g_err;
+
+constexpr int DA_BLOCK = 256;  // one block per ray, threads over the radii
+
+__device__ __forceinline__ int block_min(int v) {
+  __shared__ int m;
+  if (threadIdx.x == 0) m = INT_MAX;
+  __syncthreads();
+  v = __reduce_min_sync(0xffffffffu, v);
+  if ((threadIdx.x & 31) == 0) atomicMin(&m, v);
+  __syncthreads();
+  const int r = m;
+  __syncthreads();
+  return r;
+}
 
 // Per ray: r_lo = first k whose survival probability is below 1 - p_lo
 // (logit < lmax), n_r if none: where the network first doubts survival, and
@@ -26,25 +41,31 @@ thread_local std::string g_err;
 // again, and on the rays flagged in `widen` the predicted points within
 // `margin` of da_prev[ray] (the current first loss) or inside
 // [r_lo - margin, r_lo + window] are added.
-__global__ void select_kernel(const float* __restrict__ out2, int32_t n_rays, int32_t n_r, float lmax,
-                              int32_t margin, int32_t window, const int32_t* __restrict__ widen,
-                              const int32_t* __restrict__ da_prev, int32_t* __restrict__ state,
-                              int32_t* __restrict__ r_lo_out) {
-  const int ray = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ray >= n_rays) return;
+__global__ void __launch_bounds__(DA_BLOCK) select_kernel(const float* __restrict__ out2, int32_t n_r, float lmax,
+                                                          int32_t margin, int32_t window,
+                                                          const int32_t* __restrict__ widen,
+                                                          const int32_t* __restrict__ da_prev,
+                                                          int32_t* __restrict__ state,
+                                                          int32_t* __restrict__ r_lo_out) {
+  const int ray = blockIdx.x;
   const int64_t base = (int64_t)ray * n_r;
-  int rl = n_r;
-  for (int k = 0; k < n_r; k++)
-    if (out2[2 * (base + k)] < lmax) { rl = k; break; }
-  r_lo_out[ray] = rl;
+  int first = n_r;
+  for (int k = threadIdx.x; k < n_r; k += DA_BLOCK)
+    if (out2[2 * (base + k)] < lmax) {
+      first = k;
+      break;
+    }
+  const int rl = block_min(first);
+  if (threadIdx.x == 0) r_lo_out[ray] = rl;
   const int lo = rl - margin, hi = rl + window;
   if (!widen) {
-    for (int k = 0; k < n_r; k++) state[base + k] = (k >= lo && k <= hi) ? 1 : XS_STATE_PREDICTED;
+    for (int k = threadIdx.x; k < n_r; k += DA_BLOCK)
+      state[base + k] = (k >= lo && k <= hi) ? 1 : XS_STATE_PREDICTED;
     return;
   }
   const bool grow = widen[ray] != 0;
   const int dp = da_prev ? da_prev[ray] : rl;
-  for (int k = 0; k < n_r; k++) {
+  for (int k = threadIdx.x; k < n_r; k += DA_BLOCK) {
     int32_t s = state[base + k];
     if (s == 1) s = XS_STATE_SURVIVED;
     if (grow && s == XS_STATE_PREDICTED && ((k >= lo && k <= hi) || (k >= dp - margin && k <= dp + margin)))
@@ -58,25 +79,28 @@ __global__ void select_kernel(const float* __restrict__ out2, int32_t n_rays, in
 // every point was tracked).  widen[ray] = 1 when that first loss is a
 // predicted point, or a tracked point whose inner neighbour was predicted:
 // the boundary then lies at the edge of the tracked band.
-__global__ void combine_kernel(const float* __restrict__ out2, const int32_t* __restrict__ state, int32_t n_rays,
-                               int32_t n_r, int32_t* __restrict__ da, int32_t* __restrict__ widen) {
-  const int ray = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ray >= n_rays) return;
+__global__ void __launch_bounds__(DA_BLOCK) combine_kernel(const float* __restrict__ out2,
+                                                           const int32_t* __restrict__ state, int32_t n_r,
+                                                           int32_t* __restrict__ da, int32_t* __restrict__ widen) {
+  const int ray = blockIdx.x;
   const int64_t base = (int64_t)ray * n_r;
-  int first = n_r, w = 0;
-  for (int k = 0; k < n_r; k++) {
+  int first = n_r;
+  for (int k = threadIdx.x; k < n_r; k += DA_BLOCK) {
     const int32_t s = state[base + k];
-    const bool predicted = (s == XS_STATE_PREDICTED);
-    const bool lost = predicted ? (out2 && out2[2 * (base + k)] < 0.f) : (s <= 0);
+    const bool lost = (s == XS_STATE_PREDICTED) ? (out2 && out2[2 * (base + k)] < 0.f) : (s <= 0);
     if (lost) {
       first = k;
-      if (predicted) w = 1;
-      else if (k > 0 && state[base + k - 1] == XS_STATE_PREDICTED) w = 1;
       break;
     }
   }
-  da[ray] = first;
-  if (widen) widen[ray] = w;
+  first = block_min(first);
+  if (threadIdx.x == 0) {
+    int w = 0;
+    if (first < n_r)
+      w = (state[base + first] == XS_STATE_PREDICTED || (first > 0 && state[base + first - 1] == XS_STATE_PREDICTED));
+    da[ray] = first;
+    if (widen) widen[ray] = w;
+  }
 }
 }  // namespace
 
@@ -92,8 +116,8 @@ int xs_da_select(const float* out2, int32_t n_rays, int32_t n_r, float p_lo, int
   }
   if (n_rays == 0 || n_r == 0) return XT_OK;
   const float lmax = logf((1.0f - p_lo) / p_lo);
-  select_kernel<<<(n_rays + 127) / 128, 128, 0, (cudaStream_t)stream>>>(out2, n_rays, n_r, lmax, margin, window,
-                                                                         widen, da_prev, state, r_lo);
+  select_kernel<<<n_rays, DA_BLOCK, 0, (cudaStream_t)stream>>>(out2, n_r, lmax, margin, window, widen, da_prev,
+                                                              state, r_lo);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     g_err = std::string("xs_da_select: ") + cudaGetErrorString(e);
@@ -110,7 +134,17 @@ int xs_da_combine(const float* out2, const int32_t* state, int32_t n_rays, int32
     return XT_ERR_INVALID;
   }
   if (n_rays == 0) return XT_OK;
-  combine_kernel<<<(n_rays + 127) / 128, 128, 0, (cudaStream_t)stream>>>(out2, state, n_rays, n_r, da, widen);
+  if (n_r == 0) {
+    cudaError_t e = cudaMemsetAsync(da, 0, (size_t)n_rays * sizeof(int32_t), (cudaStream_t)stream);
+    if (e == cudaSuccess && widen)
+      e = cudaMemsetAsync(widen, 0, (size_t)n_rays * sizeof(int32_t), (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+      g_err = std::string("xs_da_combine: ") + cudaGetErrorString(e);
+      return XT_ERR_CUDA;
+    }
+    return XT_OK;
+  }
+  combine_kernel<<<n_rays, DA_BLOCK, 0, (cudaStream_t)stream>>>(out2, state, n_r, da, widen);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     g_err = std::string("xs_da_combine: ") + cudaGetErrorString(e);
