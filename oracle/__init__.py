@@ -64,6 +64,8 @@ def lib() -> ctypes.CDLL:
             L.xo_closed_orbit.restype = i32
             L.xo_sin.argtypes = [dbl]
             L.xo_sin.restype = dbl
+            L.xo_inv_pz_m1.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+            L.xo_inv_pz_m1.restype = None
             L.xo_philox4x64_10.argtypes = [P, P, P]
             L.xo_philox4x64_10.restype = None
             L.xo_uniform.argtypes = [u64, u64, u64, u64, i64]
@@ -144,6 +146,14 @@ def closed_orbit(elements, ref, rad_mode: int = 0, dim: int = 6, guess=None) -> 
 
 def sin(x: float) -> float:
     return lib().xo_sin(float(x))
+
+
+def inv_pz_m1(u) -> np.ndarray:
+    """The drift's (1+u)^(-1/2) - 1 as the oracle evaluates it."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.empty_like(u)
+    lib().xo_inv_pz_m1(u.ctypes.data, out.ctypes.data, u.size)
+    return out
 
 
 def philox4x64_10(ctr, key) -> np.ndarray:

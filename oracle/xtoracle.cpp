@@ -313,21 +313,35 @@ static inline void mark_lost(Part<T>& p, int code, int turn, int elem) {
 // binomial(-1/2, n), exact dyadic numbers) for |u| <= 2^-7, where the
 // truncation error is below 2e-17 of yh; otherwise 1/sqrt(1+u) - 1.
 // A particle with u outside (-1, inf) is lost (code -2), coordinates unchanged.
+// Taylor coefficients of (1+u)^(-1/2) - 1: binomial(-1/2, n), exact dyadics.
 static const double RS_C[9] = {0.0, -0.5, 0.375, -0.3125, 0.2734375, -0.24609375, 0.2255859375,
                                -0.20947265625, 0.196380615234375};
+
+// yh = (1+u)^(-1/2) - 1 for u in (-1, inf).  The Taylor series truncated at
+// order n leaves c_{n+1} u^{n+1}, i.e. about 2 |c_{n+1}| |u|^n relative to
+// yh ~ -u/2; the order is the lowest that keeps this below 2^-54 (half an
+// ulp) on its interval: order 3 for |u| <= 2^-18, 6 for |u| <= 2^-9, 8 for
+// |u| <= 2^-7 (Horner from the highest order, then times u); beyond that
+// 1/sqrt(1+u) - 1.
+template <class T>
+static inline T inv_pz_m1(T u) {
+  const double a = std::fabs(val(u));
+  int order = 0;
+  if (a <= 0x1p-18) order = 3;
+  else if (a <= 0x1p-9) order = 6;
+  else if (a <= 0x1p-7) order = 8;
+  if (order == 0) return 1.0 / SQRT(1.0 + u) - 1.0;
+  T h = mkv<T>(RS_C[order]);
+  for (int n = order - 1; n >= 1; n--) h = FMA(h, u, mkv<T>(RS_C[n]));
+  return h * u;
+}
+
 template <class T>
 static inline void drift(Part<T>& p, double L, int turn, int elem) {
   T u = FMA(-p.px, p.px, FMA(-p.py, p.py, p.dm1));
   double uv = val(u);
   if (!(uv > -1.0 && uv < INFINITY)) { mark_lost(p, -2, turn, elem); return; }
-  T yh;
-  if (std::fabs(uv) <= 0.0078125) {
-    T h = mkv<T>(RS_C[8]);
-    for (int n = 7; n >= 1; n--) h = FMA(h, u, mkv<T>(RS_C[n]));
-    yh = h * u;
-  } else {
-    yh = 1.0 / SQRT(1.0 + u) - 1.0;
-  }
+  T yh = inv_pz_m1(u);
   T lpz = FMA(L, yh, mkv<T>(L));
   p.x = FMA(p.px, lpz, p.x);
   p.y = FMA(p.py, lpz, p.y);
@@ -699,6 +713,11 @@ int xo_closed_orbit(const Element* el, int64_t n_el, const Reference* ref, int r
 
 // Test hooks for the building blocks.
 double xo_sin(double x) { return sin_cw(x); }
+
+// The drift's (1+u)^(-1/2) - 1, element-wise (for its pins).
+void xo_inv_pz_m1(const double* u, double* out, int64_t n) {
+  for (int64_t i = 0; i < n; i++) out[i] = inv_pz_m1<double>(u[i]);
+}
 void xo_philox4x64_10(const uint64_t* ctr, const uint64_t* key, uint64_t* out) { philox4x64_10(ctr, key, out); }
 double xo_uniform(uint64_t seed, uint64_t pid, uint64_t turn, uint64_t elem, int64_t index) {
   Uniforms U(seed, pid, turn, elem);

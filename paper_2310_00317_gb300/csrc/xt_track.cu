@@ -247,36 +247,80 @@ struct RadCtx {
 // ---------------------------------------------------------------------------
 // Element maps.  `prm` points to the record's parameters in shared memory.
 
-// Exact drift.  yh = 1/pz - 1 = (1+u)^(-1/2) - 1, u = (1+delta)^2 - 1 - px^2 -
-// py^2: the order-8 Taylor series (Horner, dyadic coefficients) for
-// |u| <= 2^-7, else 1/sqrt(1+u) - 1; then L/pz = L + L yh and
-// zeta += -L (beta0 ptau + ep yh).  No divide or square root on the common
-// path.  Returns false (lost, state unchanged) if u is not in (-1, inf); that
-// test and the branch test run on the integer pipe.
-__device__ __forceinline__ bool drift(Part& p, const double* prm) {
+// (1+u)^(-1/2) - 1 by the Taylor series (Horner, dyadic coefficients) of
+// order 3, 6 or 8, or by 1/sqrt(1+u) - 1.
+__device__ __forceinline__ double inv_pz_m1_order3(double u) {
+  double h = fma(-0.3125, u, 0.375);
+  h = fma(h, u, -0.5);
+  return h * u;
+}
+__device__ __forceinline__ double inv_pz_m1_order6(double u) {
+  double h = fma(0.2255859375, u, -0.24609375);
+  h = fma(h, u, 0.2734375);
+  h = fma(h, u, -0.3125);
+  h = fma(h, u, 0.375);
+  h = fma(h, u, -0.5);
+  return h * u;
+}
+__device__ __forceinline__ double inv_pz_m1_order8(double u) {
+  double h = fma(0.196380615234375, u, -0.20947265625);
+  h = fma(h, u, 0.2255859375);
+  h = fma(h, u, -0.24609375);
+  h = fma(h, u, 0.2734375);
+  h = fma(h, u, -0.3125);
+  h = fma(h, u, 0.375);
+  h = fma(h, u, -0.5);
+  return h * u;
+}
+
+// Exact drift, for the whole warp (dead lanes compute along and keep their
+// coordinates).  yh = 1/pz - 1 = (1+u)^(-1/2) - 1, u = (1+delta)^2 - 1 - px^2
+// - py^2, by the Taylor series of the lowest order whose truncation stays
+// below half an ulp of yh on its interval -- order 3 for |u| <= 2^-18
+// (on-momentum particles), 6 for |u| <= 2^-9, 8 for |u| <= 2^-7 -- else
+// 1/sqrt(1+u) - 1; then L/pz = L + L yh and zeta += -L (beta0 ptau + ep yh).
+// The order is chosen per particle (so the result does not depend on the
+// warp), but when all live lanes of the warp need the same order the warp
+// branches to that series alone: a masked lane costs the FP64 pipe as much
+// as an active one, so per-lane selection would issue every order's
+// instructions.  Returns the loss code: -2 for a live lane whose u is not in
+// (-1, inf), else 1 (dead lanes always 1).  The validity and order tests run
+// on the integer pipe.
+__device__ __forceinline__ int drift_warp(Part& p, const double* prm, bool alive) {
   const double L = prm[0];
   const double u = fma(-p.px, p.px, fma(-p.py, p.py, p.dm1));
   const uint64_t ub = dbits(u), ua = ub & 0x7FFFFFFFFFFFFFFFull;
   const bool valid = (ub >> 63) ? (ua < 0x3FF0000000000000ull) : (ub < 0x7FF0000000000000ull);
-  if (!valid) return false;
+  const bool run = alive && valid;
+  const int tier = (ua <= 0x3ED0000000000000ull)   ? 1   // |u| <= 2^-18
+                   : (ua <= 0x3F60000000000000ull) ? 2   // |u| <= 2^-9
+                   : (ua <= 0x3F80000000000000ull) ? 3   // |u| <= 2^-7
+                                                   : 4;
+  const unsigned present = __reduce_or_sync(FULL_MASK, run ? (1u << tier) : 0u);
+  if (present == 0) return (alive && !valid) ? -2 : 1;
   double yh;
-  if (ua <= 0x3F80000000000000ull) {  // |u| <= 2^-7
-    double h = fma(0.196380615234375, u, -0.20947265625);
-    h = fma(h, u, 0.2255859375);
-    h = fma(h, u, -0.24609375);
-    h = fma(h, u, 0.2734375);
-    h = fma(h, u, -0.3125);
-    h = fma(h, u, 0.375);
-    h = fma(h, u, -0.5);
-    yh = h * u;
+  if (present == 2u) {
+    yh = inv_pz_m1_order3(u);
+  } else if (present == 4u) {
+    yh = inv_pz_m1_order6(u);
+  } else if (present == 8u) {
+    yh = inv_pz_m1_order8(u);
+  } else if (tier == 1) {
+    yh = inv_pz_m1_order3(u);
+  } else if (tier == 2) {
+    yh = inv_pz_m1_order6(u);
+  } else if (tier == 3) {
+    yh = inv_pz_m1_order8(u);
   } else {
     yh = 1.0 / sqrt(1.0 + u) - 1.0;
   }
-  const double lpz = fma(L, yh, L);
-  p.x = fma(p.px, lpz, p.x);
-  p.y = fma(p.py, lpz, p.y);
-  p.zeta = fma(-L, fma(p.ep, yh, p.epm1), p.zeta);
-  return true;
+  if (run) {
+    const double lpz = fma(L, yh, L);
+    p.x = fma(p.px, lpz, p.x);
+    p.y = fma(p.py, lpz, p.y);
+    p.zeta = fma(-L, fma(p.ep, yh, p.epm1), p.zeta);
+  }
+  return (alive && !valid) ? -2 : 1;
 }
 
 template <int RAD>
@@ -369,8 +413,6 @@ __device__ __forceinline__ int element(Part& p, uint32_t type, uint32_t order, u
                                        uint32_t elem, const double* prm, const RefDev& r,
                                        const SinTab& sn, const RadCtx& rc, int64_t pid, int turn) {
   switch (type) {
-    case XT_DRIFT:
-      return drift(p, prm) ? 1 : -2;
     case XT_MULTIPOLE:
       multipole<RAD>(p, prm, (int)order, (int)flags, r, rc, pid, turn, elem);
       return 1;
@@ -483,7 +525,9 @@ __device__ __forceinline__ int track_tile(const TileLat& L, const TileArrays& A,
         const uint32_t flags = hv.y & 0xFFFFu, size16 = hv.y >> 16;
         const double* prm = (const double*)(q + 16);
         int lc = 1;
-        if (type == XT_APERTURE) {
+        if (type == XT_DRIFT) {
+          lc = drift_warp(p, prm, alive);
+        } else if (type == XT_APERTURE) {
           // inside the inscribed square (integer pipe) => inside the circle;
           // the FP64 test runs only if some live lane of the warp is outside
           const uint64_t box = dbits(prm[1]);

@@ -88,6 +88,38 @@ def test_drift_both_series_branches(d):
     assert abs(o["zeta"][0] - float(dz)) <= 2e-16 * L + 1e-15 * abs(float(dz))
 
 
+@pytest.mark.parametrize("bound", [2.0 ** -18, 2.0 ** -9, 2.0 ** -7])
+def test_inv_pz_series_orders_at_their_bounds(bound):
+    """(1+u)^(-1/2) - 1 by the truncated Taylor series, whose order drops with
+    |u| (3 up to 2^-18, 6 up to 2^-9, 8 up to 2^-7): within 2 ulp of the
+    40-digit value at each interval's bound, one ulp either side of it (above
+    2^-7 is the square-root branch, pinned below), and at random u on the
+    interval -- so a dropped term, a wrong coefficient or an interval bound
+    set too wide fails."""
+    mpmath.mp.dps = 40
+    rng = np.random.default_rng(11)
+    edge = [bound, np.nextafter(bound, 0.0)] + ([np.nextafter(bound, 1.0)] if bound < 2.0 ** -7 else [])
+    rand = bound * 2.0 ** -rng.uniform(0.0, 9.0, 200)
+    u = np.concatenate([edge, rand])
+    u = np.concatenate([u, -u])
+    got = oracle.inv_pz_m1(u)
+    for ui, g in zip(u, got):
+        e = 1 / mpmath.sqrt(1 + mpmath.mpf(float(ui))) - 1
+        assert abs(g - float(e)) <= 2 * np.spacing(abs(float(e))), (ui, g, float(e))
+
+
+def test_inv_pz_sqrt_branch_and_tiny_u():
+    """Beyond |u| = 2^-7, 1/sqrt(1+u) - 1 within 2 ulp of 1 + yh (the quantity
+    L/pz = L (1 + yh) uses); u = 0 and subnormal u give yh = -u/2 exactly."""
+    mpmath.mp.dps = 40
+    u = np.array([np.nextafter(2.0 ** -7, 1.0), 0.01, -0.01, 0.3, -0.5, -0.999, 3.0, 1e6])
+    for ui, g in zip(u, oracle.inv_pz_m1(u)):
+        e = 1 / mpmath.sqrt(1 + mpmath.mpf(float(ui))) - 1
+        assert abs(g - float(e)) <= 2 * np.spacing(1.0 + float(e)), (ui, g, float(e))
+    tiny = np.array([0.0, 5e-324, -5e-324, 1e-300, -1e-300])
+    assert np.array_equal(oracle.inv_pz_m1(tiny), -tiny / 2)
+
+
 def test_drift_reversible():
     """A drift of -L undoes a drift of +L to rounding."""
     rng = np.random.default_rng(2)
