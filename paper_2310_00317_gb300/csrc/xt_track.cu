@@ -108,17 +108,19 @@ __device__ __forceinline__ void stage_drain(Stage& s) {
 }
 
 // ---------------------------------------------------------------------------
-// Integer-pipe classification of IEEE doubles.
+// Integer-pipe classification of IEEE doubles.  The bit pattern of |v| is
+// taken in inline PTX: written as a plain mask, the compiler recognises |v|
+// (or a floating-point class test) and issues it on the FP64 pipe, where it
+// costs a full slot.
 __device__ __forceinline__ uint64_t dbits(double v) { return (uint64_t)__double_as_longlong(v); }
-// 0 < t < inf
-__device__ __forceinline__ bool pos_finite(double t) { return dbits(t) - 1ull < 0x7FEFFFFFFFFFFFFFull; }
-__device__ __forceinline__ bool is_finite(double v) {
-  return (dbits(v) & 0x7FF0000000000000ull) != 0x7FF0000000000000ull;
+__device__ __forceinline__ uint64_t abs_bits(double v) {
+  uint64_t r;
+  asm("and.b64 %0, %1, 0x7FFFFFFFFFFFFFFF;" : "=l"(r) : "l"(dbits(v)));
+  return r;
 }
+__device__ __forceinline__ bool is_finite(double v) { return abs_bits(v) < 0x7FF0000000000000ull; }
 // |v| <= 1 (false for NaN)
-__device__ __forceinline__ bool abs_le_one(double v) {
-  return (dbits(v) & 0x7FFFFFFFFFFFFFFFull) <= 0x3FF0000000000000ull;
-}
+__device__ __forceinline__ bool abs_le_one(double v) { return abs_bits(v) <= 0x3FF0000000000000ull; }
 
 // ---------------------------------------------------------------------------
 // Particle state in registers.  opd = 1+delta, dm1 = (1+delta)^2 - 1,
@@ -289,7 +291,7 @@ __device__ __forceinline__ double inv_pz_m1_order8(double u) {
 __device__ __forceinline__ int drift_warp(Part& p, const double* prm, bool alive) {
   const double L = prm[0];
   const double u = fma(-p.px, p.px, fma(-p.py, p.py, p.dm1));
-  const uint64_t ub = dbits(u), ua = ub & 0x7FFFFFFFFFFFFFFFull;
+  const uint64_t ub = dbits(u), ua = abs_bits(u);
   const bool valid = (ub >> 63) ? (ua < 0x3FF0000000000000ull) : (ub < 0x7FF0000000000000ull);
   const bool run = alive && valid;
   const int tier = (ua <= 0x3ED0000000000000ull)   ? 1   // |u| <= 2^-18
@@ -531,8 +533,7 @@ __device__ __forceinline__ int track_tile(const TileLat& L, const TileArrays& A,
           // inside the inscribed square (integer pipe) => inside the circle;
           // the FP64 test runs only if some live lane of the warp is outside
           const uint64_t box = dbits(prm[1]);
-          const bool in = !alive || ((dbits(p.x) & 0x7FFFFFFFFFFFFFFFull) <= box &&
-                                     (dbits(p.y) & 0x7FFFFFFFFFFFFFFFull) <= box);
+          const bool in = !alive || (abs_bits(p.x) <= box && abs_bits(p.y) <= box);
           if (!__all_sync(FULL_MASK, in) && alive) lc = element<RAD>(p, type, order, flags, hv.z, prm, ref,
                                                                       sn, rc, pid, turn);
         } else if (alive) {
