@@ -293,13 +293,21 @@ const char* xs_last_error(void);
    xs_da_select, first pass (widen == NULL): per ray r_lo = first point whose
    survival probability is below 1 - p_lo (written to r_lo[ray], n_r if none);
    points k in [r_lo - margin, r_lo + window] get state 1 (to be tracked by
-   xt_track), all others XS_STATE_PREDICTED.  Later passes (widen != NULL):
-   state 1 -> XS_STATE_SURVIVED, and on rays with widen[ray] != 0 predicted
-   points in that window or within `margin` of da_prev[ray] become 1.
+   xt_track), all others XS_STATE_PREDICTED.  Later passes (widen != NULL,
+   da_prev = the previous pass's da): state 1 -> XS_STATE_SURVIVED; on rays
+   with widen[ray] == XS_WIDEN_INWARD the predicted points in
+   [da_prev - margin, da_prev - 1], on rays with widen[ray] == XS_WIDEN_VERIFY
+   those in [da_prev - margin, da_prev + margin], become 1 (window unused).
    xs_da_combine: da[ray] = first lost point (tracked: state <= 0; predicted:
    logit < 0; out2 may be NULL when every point was tracked, then predicted
-   points count as survivors); widen[ray] (may be NULL) = 1 if that boundary
-   is a predicted point or has a predicted inner neighbour.                 */
+   points count as survivors); widen[ray] (may be NULL) = XS_WIDEN_VERIFY if
+   that point is predicted, XS_WIDEN_INWARD if it is tracked but its inner
+   neighbour is predicted (the boundary may lie further in), else 0.
+   Both return XT_ERR_INVALID for a null required pointer, negative sizes,
+   margin or window, or p_lo outside (0, 0.5); all pointers stay owned by the
+   caller and the calls only enqueue work on `stream`.                      */
+#define XS_WIDEN_INWARD 1
+#define XS_WIDEN_VERIFY 2
 #define XS_STATE_PREDICTED 2
 #define XS_STATE_SURVIVED 3
 int xs_da_select(const float* out2, int32_t n_rays, int32_t n_r, float p_lo, int32_t margin, int32_t window,

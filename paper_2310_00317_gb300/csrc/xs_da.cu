@@ -38,9 +38,10 @@ __device__ __forceinline__ int block_min(int v) {
 // window k in [r_lo - margin, r_lo + window] is tracked (state 1), every other
 // point is predicted (XS_STATE_PREDICTED).  Later passes: survivors of the
 // previous pass (state 1) become XS_STATE_SURVIVED so they are not tracked
-// again, and on the rays flagged in `widen` the predicted points within
-// `margin` of da_prev[ray] (the current first loss) or inside
-// [r_lo - margin, r_lo + window] are added.
+// again, and predicted points are added next to the previous first loss dp:
+// [dp - margin, dp - 1] on rays flagged XS_WIDEN_INWARD (the loss was tracked
+// but its inner neighbour only predicted), [dp - margin, dp + margin] on rays
+// flagged XS_WIDEN_VERIFY (the loss itself was only predicted).
 __global__ void __launch_bounds__(DA_BLOCK) select_kernel(const float* __restrict__ out2, int32_t n_r, float lmax,
                                                           int32_t margin, int32_t window,
                                                           const int32_t* __restrict__ widen,
@@ -57,28 +58,29 @@ __global__ void __launch_bounds__(DA_BLOCK) select_kernel(const float* __restric
     }
   const int rl = block_min(first);
   if (threadIdx.x == 0) r_lo_out[ray] = rl;
-  const int lo = rl - margin, hi = rl + window;
   if (!widen) {
+    const int lo = rl - margin, hi = rl + window;
     for (int k = threadIdx.x; k < n_r; k += DA_BLOCK)
       state[base + k] = (k >= lo && k <= hi) ? 1 : XS_STATE_PREDICTED;
     return;
   }
-  const bool grow = widen[ray] != 0;
+  const int w = widen[ray];
   const int dp = da_prev ? da_prev[ray] : rl;
+  const int a = dp - margin;
+  const int b = (w == XS_WIDEN_VERIFY) ? dp + margin : dp - 1;
   for (int k = threadIdx.x; k < n_r; k += DA_BLOCK) {
     int32_t s = state[base + k];
     if (s == 1) s = XS_STATE_SURVIVED;
-    if (grow && s == XS_STATE_PREDICTED && ((k >= lo && k <= hi) || (k >= dp - margin && k <= dp + margin)))
-      s = 1;
+    if (w != 0 && s == XS_STATE_PREDICTED && k >= a && k <= b) s = 1;
     state[base + k] = s;
   }
 }
 
 // Per ray: DA index = first k that is lost: a tracked point is lost if its
 // state is <= 0, a predicted point if its logit < 0 (out2 may be null when
-// every point was tracked).  widen[ray] = 1 when that first loss is a
-// predicted point, or a tracked point whose inner neighbour was predicted:
-// the boundary then lies at the edge of the tracked band.
+// every point was tracked).  widen[ray] = XS_WIDEN_VERIFY when that first
+// loss is a predicted point, XS_WIDEN_INWARD when it is tracked but its inner
+// neighbour was predicted (the boundary may lie further in), else 0.
 __global__ void __launch_bounds__(DA_BLOCK) combine_kernel(const float* __restrict__ out2,
                                                            const int32_t* __restrict__ state, int32_t n_r,
                                                            int32_t* __restrict__ da, int32_t* __restrict__ widen) {
@@ -96,8 +98,10 @@ __global__ void __launch_bounds__(DA_BLOCK) combine_kernel(const float* __restri
   first = block_min(first);
   if (threadIdx.x == 0) {
     int w = 0;
-    if (first < n_r)
-      w = (state[base + first] == XS_STATE_PREDICTED || (first > 0 && state[base + first - 1] == XS_STATE_PREDICTED));
+    if (first < n_r) {
+      if (state[base + first] == XS_STATE_PREDICTED) w = XS_WIDEN_VERIFY;
+      else if (first > 0 && state[base + first - 1] == XS_STATE_PREDICTED) w = XS_WIDEN_INWARD;
+    }
     da[ray] = first;
     if (widen) widen[ray] = w;
   }

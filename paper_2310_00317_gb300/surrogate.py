@@ -9,8 +9,11 @@ version of it; every computation runs in the library's kernels:
    one batched persistent launch per segment (``xt_track_batched``, CUDA graph);
 2. training: the MLP (``xs_mlp``) learns survival and the normalised log loss
    turn from 6 normalised initial coordinates + 10 lattice-error descriptors;
-3. scan: for a new seed the network predicts the whole polar grid, the glue
-   kernels (``xs_da_select``) hand only the uncertain band to the FP64 tracker
+3. calibration: on a validation seed (neither trained on nor scanned) a plain
+   FP64 scan on a coarser grid sets how far inside and outside the network's
+   first doubtful point the true boundary can lie: the band limits;
+4. scan: for a new seed the network predicts the whole polar grid, the glue
+   kernels (``xs_da_select``) hand only the band to the FP64 tracker
    (``xt_track``), ``xs_da_combine`` forms the per-ray DA and flags rays whose
    boundary touches a predicted point, which are widened and re-tracked.
 
@@ -167,11 +170,14 @@ def plain_scan(tracker, grid: dict, n_rays: int, n_r: int, n_turns: int):
 
 
 def surrogate_scan(tracker, net, grid: dict, X: np.ndarray, n_rays: int, n_r: int, n_turns: int,
-                   p_lo: float = 0.02, margin: int = 500, window: int = 1500, max_passes: int = 4):
-    """Network over the grid, FP64 tracking of a window around where each
-    ray's first loss is expected, widened where the boundary touches a
-    predicted point.  Returns DA index per ray, seconds, tracked points and
-    passes."""
+                   p_lo: float = 0.2, margin: int = 500, window: int = 1500, step: int | None = None,
+                   max_passes: int = 6):
+    """Network over the grid, FP64 tracking of the band [r_lo - margin,
+    r_lo + window] around where each ray's first loss is expected, then, on
+    rays whose first loss is not confirmed by a tracked survivor just inside
+    it, passes that track `step` more points next to it (inward, or on both
+    sides of a loss that was only predicted), the step doubling each pass.
+    Returns DA index per ray, seconds, tracked points and passes."""
     import torch
     P = xtgb.Particles.from_numpy(grid)
     Xd = torch.tensor(X, device="cuda")
@@ -179,13 +185,13 @@ def surrogate_scan(tracker, net, grid: dict, X: np.ndarray, n_rays: int, n_r: in
     da = torch.zeros(n_rays, dtype=torch.int32, device="cuda")
     widen = torch.zeros(n_rays, dtype=torch.int32, device="cuda")
     st = P.t["state"]
+    step = max(1, margin // 2) if step is None else max(1, int(step))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     out2 = net.forward(Xd)
     xtgb.da_select(out2, n_rays, n_r, p_lo, margin, window, st, r_hat)
     tracked = 0
     passes = 0
-    m = margin
     while True:
         tracked += int((st == 1).sum().item())
         tracker.track(P, n_turns)
@@ -193,8 +199,8 @@ def surrogate_scan(tracker, net, grid: dict, X: np.ndarray, n_rays: int, n_r: in
         xtgb.da_combine(out2, st, n_rays, n_r, da, widen)
         if passes >= max_passes or int(widen.sum().item()) == 0:
             break
-        m *= 2
-        xtgb.da_select(out2, n_rays, n_r, p_lo, m, window, st, r_hat, widen=widen, da_prev=da)
+        xtgb.da_select(out2, n_rays, n_r, p_lo, step, 0, st, r_hat, widen=widen, da_prev=da)
+        step *= 2
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     return da.cpu().numpy(), dt, tracked, passes
@@ -231,52 +237,137 @@ def coarse_scan(tracker, grid: dict, n_rays: int, n_r: int, n_turns: int, stride
     return da.cpu().numpy(), dt, tracked
 
 
-def da_study(train_seeds=48, test_seed=60, mean_count=4000, n_turns=1000, n_cells=20, base_mult=1.5,
-             epochs=8, n_r=22222, n_theta=45, deltas=(0,), p_lo=0.02, margin_sigma=0.5, window_sigma=1.5):
-    """Full study: labels, training, and plain / surrogate / coarse scans of a
-    held-out seed.  Returns a dict of the measured quantities."""
+def band_offsets(net, seed: int, n_r: int, n_theta: int, n_turns: int, n_cells: int = 20,
+                 base_mult: float = 1.5, deltas=(0,), p_lo: float = 0.2):
+    """Offsets of the true DA from the network's r_lo (first point it doubts,
+    by ``xs_da_select``) on every ray of one seed, in beam sigmas: a plain
+    FP64 scan of the seed on n_r radii gives the DA.  Returns (offsets,
+    seconds)."""
+    import torch
+    t0 = time.perf_counter()
+    el, ref, desc = seed_ring(seed, n_cells, base_mult)
+    grid, (R, th, dl), n_rays = scan_grid(el, ref, n_r, n_theta, deltas)
+    tr = xtgb.Tracker(el, ref)
+    da, _, _ = plain_scan(tr, grid, n_rays, n_r, n_turns)
+    tr.close()
+    out2 = net.forward(torch.tensor(features(R, th, dl, desc), device="cuda"))
+    st = torch.empty(n_rays * n_r, dtype=torch.int32, device="cuda")
+    r_lo = torch.empty(n_rays, dtype=torch.int32, device="cuda")
+    xtgb.da_select(out2, n_rays, n_r, p_lo, 0, 0, st, r_lo)
+    return (da - r_lo.cpu().numpy()) * (R_MAX / n_r), time.perf_counter() - t0
+
+
+def calibrate_band(net, seeds, n_r: int, n_theta: int, n_turns: int, n_cells: int = 20,
+                   base_mult: float = 1.5, deltas=(0,), p_lo: float = 0.2, pad_sigma: float = 0.1):
+    """Band limits from validation seeds (labelled with the family but neither
+    the scanned seed): the band [r_lo - margin, r_lo + window] should hold the
+    first loss, so margin and window are the largest inward and outward
+    offsets of the DA from r_lo over all their rays, in beam sigmas, plus
+    pad_sigma.  Returns (margin_sigma, window_sigma, seconds, offsets)."""
+    offs, secs = [], 0.0
+    for sd in seeds:
+        off, t = band_offsets(net, sd, n_r, n_theta, n_turns, n_cells, base_mult, deltas, p_lo)
+        offs.append(off)
+        secs += t
+    off = np.concatenate(offs)
+    return max(0.0, -float(off.min())) + pad_sigma, max(0.0, float(off.max())) + pad_sigma, secs, off
+
+
+def _stats(off):
+    return None if off is None else [float(off.min()), float(np.median(off)), float(off.max())]
+
+
+def da_study(family=(13, 61), test_seeds=(60, 13, 30, 45), val_seeds=(59, 41, 20), unseen_seed=200,
+             mean_count=16000, n_turns=300, n_cells=20, base_mult=1.5, epochs=16, n_r=22222, n_theta=45, deltas=(0,),
+             p_lo=0.2, margin_sigma=None, window_sigma=None, pad_sigma=0.1, step_sigma=0.25):
+    """The surrogate workflow on a family of error seeds (seeds family[0] ..
+    family[1]-1): random-amplitude labels of every seed tracked together in
+    one batched launch per segment, the network trained on them, the band
+    limits calibrated on validation seeds of the family (unless given), then
+    plain / surrogate-guided / coarse scans of the test seeds of the family.
+    The network's offsets on a seed outside the family measure how far it
+    generalises.  Returns a dict of the measured quantities; `per_seed` holds
+    one entry per test seed and the totals are summed over them."""
+    import torch
+    seeds = list(range(family[0], family[1]))
+    if (any(t not in seeds for t in test_seeds) or any(v not in seeds for v in val_seeds)
+            or set(test_seeds) & set(val_seeds)):
+        raise ValueError("test and validation seeds must be distinct members of the family")
     rng = np.random.default_rng(I.BASE_SEED + 77)
     lo, hi = math.log10(mean_count) - 0.75, math.log10(mean_count) + 0.75
-    counts = np.round(10.0 ** rng.uniform(lo, hi, train_seeds)).astype(np.int64)
-    data, t_label, label_passes = make_training_set(list(range(train_seeds)), counts, n_turns, n_cells, base_mult)
+    counts = np.round(10.0 ** rng.uniform(lo, hi, len(seeds))).astype(np.int64)
+    data, t_label, label_passes = make_training_set(seeds, counts, n_turns, n_cells, base_mult)
     net = xtgb.Surrogate(seed=7)
     hist, t_train = train(net, data, epochs=epochs)
     acc_train = accuracy(net, data)
-    el, ref, desc = seed_ring(test_seed, n_cells, base_mult)
-    grid, (R, th, dl), n_rays = scan_grid(el, ref, n_r, n_theta, deltas)
-    X = features(R, th, dl, desc)
-    tr = xtgb.Tracker(el, ref)
-    # Run every scan once on a small grid of the same ring first: the first use
-    # of a device kernel (ours or torch's) loads its module, which can take
-    # seconds and must not land inside the timed scans.
-    n_r_w = 256
-    grid_w, (R_w, th_w, dl_w), _ = scan_grid(el, ref, n_r_w, n_theta, deltas)
-    X_w = features(R_w, th_w, dl_w, desc)
-    plain_scan(tr, grid_w, n_rays, n_r_w, 2)
-    surrogate_scan(tr, net, grid_w, X_w, n_rays, n_r_w, 2, p_lo, 4, 8)
-    coarse_scan(tr, grid_w, n_rays, n_r_w, 2)
-    da_p, t_plain, n_plain = plain_scan(tr, grid, n_rays, n_r, n_turns)
+    n_r_cal = max(n_r // 10, 64)
+    t_cal, off = 0.0, None
+    if margin_sigma is None or window_sigma is None:
+        margin_sigma, window_sigma, t_cal, off = calibrate_band(net, val_seeds, n_r_cal, n_theta, n_turns, n_cells,
+                                                                base_mult, deltas, p_lo, pad_sigma)
+    off_unseen = None
+    if unseen_seed is not None:
+        off_unseen, _ = band_offsets(net, unseen_seed, n_r_cal, n_theta, n_turns, n_cells, base_mult, deltas, p_lo)
     dr = R_MAX / n_r
-    t0 = time.perf_counter()
-    net.forward(__import__("torch").tensor(X, device="cuda"))
-    __import__("torch").cuda.synchronize()
-    t_inf = time.perf_counter() - t0
-    da_s, t_sur, n_sur, passes = surrogate_scan(tr, net, grid, X, n_rays, n_r, n_turns, p_lo,
-                                                int(round(margin_sigma / dr)), int(round(window_sigma / dr)))
-    da_c, t_coarse, n_coarse = coarse_scan(tr, grid, n_rays, n_r, n_turns)
-    err_s = np.abs(da_s - da_p) * dr
-    err_c = np.abs(da_c - da_p) * dr
+    margin, window = int(round(margin_sigma / dr)), int(round(window_sigma / dr))
+    step = max(1, int(round(step_sigma / dr)))
+    per_seed = []
+    for ts in test_seeds:
+        el, ref, desc = seed_ring(ts, n_cells, base_mult)
+        grid, (R, th, dl), n_rays = scan_grid(el, ref, n_r, n_theta, deltas)
+        X = features(R, th, dl, desc)
+        tr = xtgb.Tracker(el, ref)
+        # Run every scan once on a small grid of the same ring first: the first
+        # use of a device kernel (ours or torch's) loads its module, which can
+        # take seconds and must not land inside the timed scans.
+        n_r_w = 256
+        grid_w, (R_w, th_w, dl_w), _ = scan_grid(el, ref, n_r_w, n_theta, deltas)
+        X_w = features(R_w, th_w, dl_w, desc)
+        plain_scan(tr, grid_w, n_rays, n_r_w, 2)
+        surrogate_scan(tr, net, grid_w, X_w, n_rays, n_r_w, 2, p_lo, 4, 8, 2)
+        coarse_scan(tr, grid_w, n_rays, n_r_w, 2)
+        da_p, t_plain, _ = plain_scan(tr, grid, n_rays, n_r, n_turns)
+        t0 = time.perf_counter()
+        net.forward(torch.tensor(X, device="cuda"))
+        torch.cuda.synchronize()
+        t_inf = time.perf_counter() - t0
+        da_s, t_sur, n_sur, passes = surrogate_scan(tr, net, grid, X, n_rays, n_r, n_turns, p_lo, margin, window,
+                                                    step)
+        da_c, t_coarse, n_coarse = coarse_scan(tr, grid, n_rays, n_r, n_turns)
+        tr.close()
+        err_s = np.abs(da_s - da_p) * dr
+        err_c = np.abs(da_c - da_p) * dr
+        per_seed.append(dict(
+            seed=int(ts), labels=int(counts[seeds.index(ts)]), n_elements=int(el.shape[0]),
+            da_plain_sigma_min_median_max=_stats(da_p * dr), plain_seconds=t_plain, surrogate_seconds=t_sur,
+            inference_seconds=t_inf, speedup=t_plain / t_sur, tracked_fraction=n_sur / (n_rays * n_r),
+            passes=passes, da_error_sigma_max=float(err_s.max()), da_error_sigma_mean=float(err_s.mean()),
+            rays_within_0p2_sigma=float(np.mean(err_s <= 0.2 + 1e-9)), coarse_seconds=t_coarse,
+            coarse_speedup=t_plain / t_coarse, coarse_tracked_fraction=n_coarse / (n_rays * n_r),
+            coarse_da_error_sigma_max=float(err_c.max()),
+            coarse_rays_within_0p2_sigma=float(np.mean(err_c <= 0.2 + 1e-9))))
     net.close()
-    tr.close()
+    tp = sum(r["plain_seconds"] for r in per_seed)
+    tsur = sum(r["surrogate_seconds"] for r in per_seed)
+    tco = sum(r["coarse_seconds"] for r in per_seed)
+    overhead = (t_label + t_train + t_cal) / len(seeds)
     return dict(
-        n_train=int(data["X"].shape[0]), train_seeds=int(train_seeds), label_seconds=t_label,
-        label_passes=label_passes, train_seconds=t_train, epochs=epochs, loss_history=hist,
-        train_accuracy=acc_train, n_turns=n_turns, n_elements=int(el.shape[0]), grid_points=int(n_rays * n_r),
-        n_rays=int(n_rays), n_r=int(n_r), plain_seconds=t_plain, surrogate_seconds=t_sur,
-        coarse_seconds=t_coarse, inference_seconds=t_inf, speedup=t_plain / t_sur, coarse_speedup=t_plain / t_coarse,
-        tracked_fraction=n_sur / (n_rays * n_r), coarse_tracked_fraction=n_coarse / (n_rays * n_r),
-        passes=passes, da_plain_sigma=(da_p * dr).tolist(),
-        da_error_sigma_max=float(err_s.max()), da_error_sigma_mean=float(err_s.mean()),
-        rays_within_0p2_sigma=float(np.mean(err_s <= 0.2 + 1e-9)),
-        coarse_da_error_sigma_max=float(err_c.max()),
+        family_seeds=len(seeds), test_seeds=[int(t) for t in test_seeds], val_seeds=[int(v) for v in val_seeds],
+        n_train=int(data["X"].shape[0]), label_seconds=t_label, label_passes=label_passes, train_seconds=t_train,
+        epochs=epochs, loss_history=hist, train_accuracy=acc_train,
+        p_lo=p_lo, margin_sigma=float(margin_sigma), window_sigma=float(window_sigma), pad_sigma=pad_sigma,
+        step_sigma=step_sigma, calibration_seconds=t_cal, calibration_offsets_sigma=_stats(off),
+        unseen_seed=unseen_seed, unseen_offsets_sigma=_stats(off_unseen),
+        n_turns=n_turns, grid_points=int(n_theta * len(deltas) * n_r), n_rays=int(n_theta * len(deltas)),
+        n_r=int(n_r), plain_seconds_total=tp, surrogate_seconds_total=tsur, coarse_seconds_total=tco,
+        speedup=tp / tsur, speedup_min=min(r["speedup"] for r in per_seed),
+        speedup_max=max(r["speedup"] for r in per_seed),
+        family_overhead_seconds_per_seed=overhead,
+        speedup_with_overhead=tp / (tsur + overhead * len(per_seed)),
+        da_error_sigma_max=max(r["da_error_sigma_max"] for r in per_seed),
+        rays_within_0p2_sigma=float(np.mean([r["rays_within_0p2_sigma"] for r in per_seed])),
+        max_passes_used=max(r["passes"] for r in per_seed),
+        coarse_speedup=tp / tco, coarse_da_error_sigma_max=max(r["coarse_da_error_sigma_max"] for r in per_seed),
+        coarse_rays_within_0p2_sigma=float(np.mean([r["coarse_rays_within_0p2_sigma"] for r in per_seed])),
+        per_seed=per_seed,
     )

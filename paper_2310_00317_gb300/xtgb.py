@@ -330,6 +330,8 @@ def traversed_elements(particles: dict, n_el: int, start_turn: int, n_turns: int
 XS_N_PARAMS = 202242
 XS_STATE_PREDICTED = 2
 XS_STATE_SURVIVED = 3
+XS_WIDEN_INWARD = 1
+XS_WIDEN_VERIFY = 2
 _xs_ready = False
 
 

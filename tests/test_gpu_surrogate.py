@@ -108,6 +108,22 @@ def _py_select(logit, n_rays, n_r, p_lo, margin, window):
     return st, rl
 
 
+def _py_widen(st, w, da_prev, n_rays, n_r, margin):
+    """A later pass: survivors frozen; points next to the previous first loss
+    added, inward only (1) or on both sides (2)."""
+    s = st.copy()
+    s[s == 1] = 3
+    for r in range(n_rays):
+        if w[r] == 0:
+            continue
+        lo = da_prev[r] - margin
+        hi = da_prev[r] + margin if w[r] == 2 else da_prev[r] - 1
+        for k in range(max(lo, 0), min(hi, n_r - 1) + 1):
+            if s[r * n_r + k] == 2:
+                s[r * n_r + k] = 1
+    return s
+
+
 def _py_combine(logit, st, n_rays, n_r):
     da = np.zeros(n_rays, np.int32)
     w = np.zeros(n_rays, np.int32)
@@ -118,7 +134,10 @@ def _py_combine(logit, st, n_rays, n_r):
             lost = (logit[r * n_r + k] < 0) if s == 2 else (s <= 0)
             if lost:
                 da[r] = k
-                w[r] = 1 if (s == 2 or (k > 0 and st[r * n_r + k - 1] == 2)) else 0
+                if s == 2:
+                    w[r] = 2
+                elif k > 0 and st[r * n_r + k - 1] == 2:
+                    w[r] = 1
                 break
     return da, w
 
@@ -137,8 +156,10 @@ def test_da_glue_vs_python():
     o2 = dev(out2)
     xtgb.da_select(o2, n_rays, n_r, 0.02, 4, 12, st, rh)
     assert np.array_equal(st.cpu().numpy(), st_py) and np.array_equal(rh.cpu().numpy(), rh_py)
-    # "track" the selected points: lost beyond the true edge
+    # "track" the selected points: lost beyond the true edge, which on every
+    # fifth ray lies inside the band's start (an inward flag)
     true_edge = edge + r.integers(-3, 4, n_rays)
+    true_edge[::5] = edge[::5] - 20
     s = st_py.copy()
     for j in range(n_rays):
         for kk in range(n_r):
@@ -151,8 +172,9 @@ def test_da_glue_vs_python():
     xtgb.da_combine(o2, sd, n_rays, n_r, da, w)
     da_py, w_py = _py_combine(logit, s, n_rays, n_r)
     assert np.array_equal(da.cpu().numpy(), da_py) and np.array_equal(w.cpu().numpy(), w_py)
-    # a widening pass: survivors are frozen, flagged rays get more points
+    # both kinds of flag occur in this case
+    assert np.any(w_py == 1) and np.any(w_py == 2)
+    # a widening pass: survivors are frozen, flagged rays get the points next
+    # to their previous first loss
     xtgb.da_select(o2, n_rays, n_r, 0.02, 8, 12, sd, rh, widen=w, da_prev=da)
-    s2 = sd.cpu().numpy()
-    assert not np.any(s2 == 1) or np.all(np.isin(np.flatnonzero(s2 == 1) // n_r, np.flatnonzero(w_py)))
-    assert np.all(s2[s == 1] == 3)
+    assert np.array_equal(sd.cpu().numpy(), _py_widen(s, w_py, da_py, n_rays, n_r, 8))
