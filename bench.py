@@ -187,6 +187,20 @@ def measure_batched(T=2, steps=3):
     n_el = el0.shape[0]
     out = {"seeds": 64, "particles": int(counts.sum()), "count_min": int(counts.min()),
            "count_max": int(counts.max()), "n_elements": int(n_el), "turns_per_step": T}
+    # block, lattice-chunk and segment sizes from the autotuner on a probe of
+    # 65,536 particles of seed 0 over 2 turns; the batched launch takes tracker
+    # 0's options for every seed
+    scales0, _ = I.seed_error_scales(0)
+    el_p, _ = I.lhc_ring(seed=I.BASE_SEED + 100, error_scales=scales0)
+    pr = I.polar_sample(el_p, ref, 65536, seed=I.BASE_SEED + 300, optics=optics)
+    probe = xtgb.Particles.from_numpy(I.subset(pr, np.arange(65536)))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    opt = trs[0].autotune(probe, 2)
+    torch.cuda.synchronize()
+    out["autotune"] = {"block": int(opt["block"]), "chunk_bytes": int(opt["chunk_bytes"]),
+                       "segment_turns": int(opt["segment_turns"]), "seconds": time.perf_counter() - t0,
+                       "probe": "65,536 particles of seed 0, 2 turns, 3 blocks x 4 chunks x 3 segments"}
     turn = 0
     xtgb.track_batched(trs, ps, T, turn, graph=True)  # capture + warm
     turn += T
