@@ -78,6 +78,23 @@ extern "C" {
 #define XT_APERTURE 6   /* p[0] = radius r [m].  Circular aperture: lost with
                            state 0 if x^2 + y^2 > r^2, state -1 if x or y is not
                            finite.  A point on the circle survives.           */
+/* Misalignments and tilts are changes of the reference system (section
+   "Lattice modelling and single particle tracking" of the paper): a shifted or
+   tilted element is wrapped in a shift/rotation and its inverse.            */
+#define XT_XYSHIFT 7    /* p[0] = dx, p[1] = dy [m].  x -= dx, y -= dy.        */
+#define XT_SROTATION 8  /* p[0] = angle theta [rad] about the reference orbit:
+                           x' = x cos + y sin, y' = -x sin + y cos, and the same
+                           for (px, py); cos and sin of theta are taken once on
+                           the host.                                           */
+#define XT_APERTURE_RECT 9     /* p[0] = x_min, p[1] = x_max, p[2] = y_min,
+                           p[3] = y_max [m] (x_min <= x_max, y_min <= y_max):
+                           lost with state 0 unless x_min <= x <= x_max and
+                           y_min <= y <= y_max, state -1 if x or y is not
+                           finite.  The boundary survives.                     */
+#define XT_APERTURE_ELLIPSE 10 /* p[0] = a, p[1] = b [m] (> 0): lost with state 0
+                           if x^2 (1/a^2) + y^2 (1/b^2) > 1 (1/a^2, 1/b^2 taken
+                           once on the host), state -1 if x or y is not
+                           finite.                                             */
 
 #define XT_MAX_ORDER 10
 #define XT_NPARAM 48
@@ -205,9 +222,10 @@ int xt_sync_status(xt_tracker* tr, void* stream);
 int xt_cancel(xt_tracker* tr);
 int xt_reset_cancel(xt_tracker* tr);
 
-/* Number of tracking launches and the summed FP64 algorithmic flop count per
-   element type, for roofline accounting: flops[t] for t = XT_DRIFT .. XT_APERTURE
-   of one traversal (multipole: of order 10 with curvature, radiation off).   */
+/* Algorithmic FP64 flops of one traversal of every table row, for roofline
+   accounting (FMA = 2, add or multiply = 1, square root, divide and sine = 1,
+   compares 0), under the tracker's radiation mode: flops_per_element[i] for
+   row i, n_elements = the table's length (else XT_ERR_INVALID).  Host only. */
 int xt_element_flops(const xt_tracker* tr, int64_t* flops_per_element, int64_t n_elements);
 
 /* Event timing of the tracking kernel launches on their stream: after

@@ -29,6 +29,7 @@ _lib = None
 # Lattice-table row: the same memory layout the library's public header uses.
 ELEMENT_DTYPE = np.dtype([("type", "<i4"), ("order", "<i4"), ("p", "<f8", (48,))], align=True)
 DRIFT, MULTIPOLE, CAVITY, DIPEDGE, LINEARMAP, APERTURE, MARKER = 1, 2, 3, 4, 5, 6, 0
+XYSHIFT, SROTATION, APERTURE_RECT, APERTURE_ELLIPSE = 7, 8, 9, 10
 
 FLOAT_FIELDS = ("x", "px", "y", "py", "zeta", "delta", "ptau", "rpp", "rvv")
 INT_FIELDS = ("state", "at_turn", "at_element")

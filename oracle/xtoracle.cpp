@@ -50,7 +50,8 @@ struct Element {
 };
 enum {
   T_MARKER = 0, T_DRIFT = 1, T_MULTIPOLE = 2, T_CAVITY = 3,
-  T_DIPEDGE = 4, T_LINEARMAP = 5, T_APERTURE = 6
+  T_DIPEDGE = 4, T_LINEARMAP = 5, T_APERTURE = 6, T_XYSHIFT = 7, T_SROTATION = 8,
+  T_APERTURE_RECT = 9, T_APERTURE_ELLIPSE = 10
 };
 struct Reference { double mass0, q0, p0c; };
 
@@ -474,6 +475,10 @@ struct Prep {
   double r21, r43;                       // dipole edge
   double M[36], d[6];                    // linear map in (x,px,y,py,zeta,ptau)
   double r2;                             // aperture
+  double dx, dy;                         // reference-frame shift
+  double cs, sn;                         // reference-frame rotation about s
+  double xmin, xmax, ymin, ymax;         // rectangular aperture
+  double ia2, ib2;                       // elliptic aperture: 1/a^2, 1/b^2
 };
 
 static Prep prepare(const Element& e, const RefConst& rc) {
@@ -529,6 +534,10 @@ static Prep prepare(const Element& e, const RefConst& rc) {
       break;
     }
     case T_APERTURE: q.r2 = e.p[0] * e.p[0]; break;
+    case T_XYSHIFT: q.dx = e.p[0]; q.dy = e.p[1]; break;
+    case T_SROTATION: q.cs = std::cos(e.p[0]); q.sn = std::sin(e.p[0]); break;
+    case T_APERTURE_RECT: q.xmin = e.p[0]; q.xmax = e.p[1]; q.ymin = e.p[2]; q.ymax = e.p[3]; break;
+    case T_APERTURE_ELLIPSE: q.ia2 = 1.0 / (e.p[0] * e.p[0]); q.ib2 = 1.0 / (e.p[1] * e.p[1]); break;
     default: break;
   }
   return q;
@@ -574,6 +583,43 @@ static inline void track_element(Part<T>& p, const Prep& q, int rad_mode, const 
       }
       break;
     }
+    // Misalignments and tilts as changes of the reference system (section
+    // "Lattice modelling and single particle tracking"): the new frame is
+    // displaced by (dx, dy), or rotated by theta about the reference orbit,
+    // x' = x cos + y sin, y' = -x sin + y cos, the same for (px, py).
+    case T_XYSHIFT:
+      p.x = p.x - q.dx;
+      p.y = p.y - q.dy;
+      break;
+    case T_SROTATION: {
+      const T x = p.x, y = p.y, px = p.px, py = p.py;
+      p.x = FMA(q.cs, x, q.sn * y);
+      p.y = FMA(q.cs, y, -(q.sn * x));
+      p.px = FMA(q.cs, px, q.sn * py);
+      p.py = FMA(q.cs, py, -(q.sn * px));
+      break;
+    }
+    // Rectangular aperture: lost unless xmin <= x <= xmax and ymin <= y <= ymax
+    // (the boundary survives); a non-finite x or y is lost with state -1.
+    case T_APERTURE_RECT: {
+      const double x = val(p.x), y = val(p.y);
+      if (!(x >= q.xmin && x <= q.xmax && y >= q.ymin && y <= q.ymax)) {
+        bool fin = std::isfinite(x) && std::isfinite(y);
+        mark_lost(p, fin ? 0 : -1, turn, elem);
+      }
+      break;
+    }
+    // Elliptic aperture with semi-axes a, b: lost if (x/a)^2 + (y/b)^2 > 1,
+    // evaluated as x^2 (1/a^2) + y^2 (1/b^2).
+    case T_APERTURE_ELLIPSE: {
+      const double x = val(p.x), y = val(p.y);
+      const double t = std::fma(x * x, q.ia2, (y * y) * q.ib2);
+      if (!(t <= 1.0)) {
+        bool fin = std::isfinite(x) && std::isfinite(y);
+        mark_lost(p, fin ? 0 : -1, turn, elem);
+      }
+      break;
+    }
     default: break;
   }
 }
@@ -607,6 +653,7 @@ int xo_track(const Element* el, int64_t n_el, const Reference* ref, int rad_mode
   const RefConst rc = ref_const(*ref);
   std::vector<Prep> prep(n_el);
   for (int64_t e = 0; e < n_el; e++) {
+    if (el[e].type < 0 || el[e].type > T_APERTURE_ELLIPSE) return -1;
     if (el[e].type == T_MULTIPOLE && (el[e].order < 0 || el[e].order > 10)) return -1;
     prep[e] = prepare(el[e], rc);
   }

@@ -48,6 +48,10 @@ int64_t flops_of_row(const xt_element& e, int rad_mode) {
     case XT_DIPEDGE: return 4;
     case XT_LINEARMAP: return 85;
     case XT_APERTURE: return 3;
+    case XT_XYSHIFT: return 2;
+    case XT_SROTATION: return 12;
+    case XT_APERTURE_RECT: return 0;
+    case XT_APERTURE_ELLIPSE: return 5;
     default: return 0;
   }
 }
@@ -128,6 +132,22 @@ int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice*
       }
       case XT_APERTURE:
         prm = {e.p[0] * e.p[0], e.p[0] * (1.0 - 9.5367431640625e-07) * 0.70710678118654752};
+        break;
+      case XT_XYSHIFT: prm = {e.p[0], e.p[1]}; break;
+      case XT_SROTATION: prm = {std::cos(e.p[0]), std::sin(e.p[0])}; break;
+      case XT_APERTURE_RECT:
+        if (!(e.p[0] <= e.p[1] && e.p[2] <= e.p[3])) {
+          *err = "element " + std::to_string(i) + ": rectangular aperture needs x_min <= x_max, y_min <= y_max";
+          return XT_ERR_INVALID;
+        }
+        prm = {e.p[0], e.p[1], e.p[2], e.p[3]};
+        break;
+      case XT_APERTURE_ELLIPSE:
+        if (!(e.p[0] > 0.0 && e.p[1] > 0.0)) {
+          *err = "element " + std::to_string(i) + ": elliptic aperture needs a > 0 and b > 0";
+          return XT_ERR_INVALID;
+        }
+        prm = {1.0 / (e.p[0] * e.p[0]), 1.0 / (e.p[1] * e.p[1])};
         break;
       default:
         *err = "element " + std::to_string(i) + ": unknown type " + std::to_string(e.type);

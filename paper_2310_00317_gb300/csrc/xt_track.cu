@@ -423,6 +423,30 @@ __device__ __forceinline__ int element(Part& p, uint32_t type, uint32_t order, u
       if (dbits(rr) > dbits(prm[0])) return (is_finite(p.x) && is_finite(p.y)) ? 0 : -1;
       return 1;
     }
+    case XT_XYSHIFT:  // change of reference frame: displaced by (dx, dy)
+      p.x = p.x - prm[0];
+      p.y = p.y - prm[1];
+      return 1;
+    case XT_SROTATION: {  // change of reference frame: rotated about s (cos, sin)
+      const double c = prm[0], sn = prm[1];
+      const double x = p.x, y = p.y, px = p.px, py = p.py;
+      p.x = fma(c, x, sn * y);
+      p.y = fma(c, y, -(sn * x));
+      p.px = fma(c, px, sn * py);
+      p.py = fma(c, py, -(sn * px));
+      return 1;
+    }
+    case XT_APERTURE_RECT: {
+      const double x = p.x, y = p.y;
+      if (!(x >= prm[0] && x <= prm[1] && y >= prm[2] && y <= prm[3]))
+        return (is_finite(x) && is_finite(y)) ? 0 : -1;
+      return 1;
+    }
+    case XT_APERTURE_ELLIPSE: {  // prm = 1/a^2, 1/b^2; t >= 0 or NaN, so its bits order it
+      const double t = fma(p.x * p.x, prm[0], (p.y * p.y) * prm[1]);
+      if (dbits(t) > 0x3FF0000000000000ull) return (is_finite(p.x) && is_finite(p.y)) ? 0 : -1;
+      return 1;
+    }
     case XT_CAVITY: {
       const double phi = fma(-prm[0], p.zeta, prm[1]);
       p.ptau = fma(prm[2], sin_cw(phi, sn), p.ptau);

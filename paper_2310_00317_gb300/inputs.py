@@ -25,6 +25,7 @@ import numpy as np
 
 ELEMENT_DTYPE = np.dtype([("type", "<i4"), ("order", "<i4"), ("p", "<f8", (48,))], align=True)
 MARKER, DRIFT, MULTIPOLE, CAVITY, DIPEDGE, LINEARMAP, APERTURE = 0, 1, 2, 3, 4, 5, 6
+XYSHIFT, SROTATION, APERTURE_RECT, APERTURE_ELLIPSE = 7, 8, 9, 10
 MAX_ORDER = 10
 
 C_LIGHT = 299792458.0
@@ -80,6 +81,32 @@ def aperture(radius: float):
 
 def marker():
     return _row(MARKER)
+
+
+def xy_shift(dx: float, dy: float):
+    """Change of reference frame: displaced by (dx, dy)."""
+    return _row(XYSHIFT, 0, [dx, dy])
+
+
+def s_rotation(angle: float):
+    """Change of reference frame: rotated by `angle` [rad] about the orbit."""
+    return _row(SROTATION, 0, [angle])
+
+
+def aperture_rect(x_min: float, x_max: float, y_min: float, y_max: float):
+    return _row(APERTURE_RECT, 0, [x_min, x_max, y_min, y_max])
+
+
+def aperture_ellipse(a: float, b: float):
+    return _row(APERTURE_ELLIPSE, 0, [a, b])
+
+
+def misaligned(rows, dx: float = 0.0, dy: float = 0.0, tilt: float = 0.0):
+    """Rows of one element seen from a frame displaced by (dx, dy) and then
+    rotated by `tilt`: shift, rotation, the element, and the inverse
+    rotation and shift."""
+    rows = list(rows) if isinstance(rows, (list, tuple)) else [rows]
+    return ([xy_shift(dx, dy), s_rotation(tilt)] + rows + [s_rotation(-tilt), xy_shift(-dx, -dy)])
 
 
 def table(rows) -> np.ndarray:

@@ -96,6 +96,36 @@ def test_every_element_type_bitwise():
     assert np.any(o["state"] == 0) and np.any(o["state"] == 1)
 
 
+def test_misaligned_elements_and_aperture_shapes_bitwise():
+    """Misaligned and tilted quadrupoles and sextupoles (shift + rotation
+    frames), and the paper's loss-location setting: a rectangular aperture
+    followed by an elliptic one, shifted and tilted with respect to each
+    other.  2,000 particles (a ragged last warp), 150 turns, bit for bit."""
+    qf = I.multipole(knl=[0.0, 0.2])
+    qd = I.multipole(knl=[0.0, -0.2])
+    sx = I.multipole(knl=[0.0, 0.0, 0.05], ksl=[0.0, 0.0, 0.01])
+    rows = [I.cavity(2e6, 400e6, 180.0)]
+    for c in range(10):
+        rows += I.misaligned([qf], dx=1e-4 * (c - 4.5), dy=-3e-5 * c, tilt=1e-3 * (c % 3))
+        rows += [I.drift(2.0)]
+        rows += I.misaligned([sx], dx=2e-4, tilt=0.2 * (c % 2))
+        rows += [I.drift(2.0)]
+        rows += I.misaligned([qd], dx=-1e-4, dy=5e-5, tilt=-2e-3)
+        rows += [I.drift(2.0), I.drift(2.0)]
+    rows += I.misaligned([I.aperture_rect(-4e-3, 4.5e-3, -2.5e-3, 2.8e-3)], dx=2e-4, dy=-1e-4, tilt=0.1)
+    rows += [I.drift(0.5)]
+    rows += I.misaligned([I.aperture_ellipse(4.6e-3, 3.1e-3)], dx=-1.5e-4, dy=1e-4, tilt=-0.07)
+    el = I.table(rows)
+    p = random_particles(PROTON, 2000, 31, sx=1.6e-3, spx=8e-5, sd=2e-4)
+    g, o = gpu_track(el, PROTON, p, 150), oracle.track(el, PROTON, p, 150)
+    assert_same(g, o)
+    rect_at = len(rows) - 9  # [shift, rotation, aperture, rotation, shift] x 2 with a drift between
+    ell_at = len(rows) - 3
+    lost = o["state"] == 0
+    assert np.any(lost & (o["at_element"] == rect_at)) and np.any(lost & (o["at_element"] == ell_at))
+    assert np.sum(o["state"] == 1) > 500
+
+
 def test_lhc_ring_sample_bitwise():
     """LHC-scale ring (20,000 elements, order-10 errors, RF, apertures):
     500 DA-grid particles at large amplitude (some are lost), 5 turns."""

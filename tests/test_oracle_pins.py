@@ -393,6 +393,117 @@ def test_aperture_and_guard():
     assert o2["state"][0] == -3 and o2["at_turn"][0] == 0 and o2["at_element"][0] == 0
 
 
+# --------------------------------------------------------------------------
+# Misalignments and tilts (changes of reference frame) and aperture shapes
+
+def _track_xy(elements, xs, ys, pxs=None, pys=None, n_turns=1):
+    n = len(xs)
+    pxs = np.zeros(n) if pxs is None else np.asarray(pxs, float)
+    pys = np.zeros(n) if pys is None else np.asarray(pys, float)
+    p = I.make_particles(PROTON, np.asarray(xs, float), pxs, np.asarray(ys, float), pys, np.zeros(n), np.zeros(n))
+    return oracle.track(I.table(elements), PROTON, p, n_turns)
+
+
+def test_srotation_identities():
+    """A rotation about s keeps x^2 + y^2 and px^2 + py^2, rotations compose
+    additively, theta then -theta returns to the start, a quarter turn maps
+    (x, y) to (y, -x), and the map is symplectic."""
+    rng = np.random.default_rng(21)
+    n = 50
+    xs, ys, pxs, pys = (rng.normal(0, s, n) for s in (1e-3, 1e-3, 1e-4, 1e-4))
+    th1, th2 = 0.37, -1.21
+    a = _track_xy([I.s_rotation(th1), I.s_rotation(th2)], xs, ys, pxs, pys)
+    b = _track_xy([I.s_rotation(th1 + th2)], xs, ys, pxs, pys)
+    for k, sc in (("x", 1e-3), ("y", 1e-3), ("px", 1e-4), ("py", 1e-4)):
+        assert np.max(np.abs(a[k] - b[k])) < 8e-16 * sc * 10
+    np.testing.assert_allclose(a["x"] ** 2 + a["y"] ** 2, xs ** 2 + ys ** 2, rtol=1e-14)
+    np.testing.assert_allclose(a["px"] ** 2 + a["py"] ** 2, pxs ** 2 + pys ** 2, rtol=1e-14)
+    c = _track_xy([I.s_rotation(th1), I.s_rotation(-th1)], xs, ys, pxs, pys)
+    assert np.max(np.abs(c["x"] - xs)) < 1e-18 and np.max(np.abs(c["py"] - pys)) < 1e-19
+    q = _track_xy([I.s_rotation(math.pi / 2)], xs, ys, pxs, pys)
+    assert np.max(np.abs(q["x"] - ys)) < 1e-18 and np.max(np.abs(q["y"] + xs)) < 1e-18
+    _, M = oracle.track_jacobian(I.table([I.s_rotation(th1), I.drift(2.0), I.s_rotation(th2)]), PROTON,
+                                 np.array([1e-3, 1e-5, -2e-3, 3e-5, 0.0, 1e-4]))
+    assert np.max(np.abs(M.T @ J6 @ M - J6)) < 1e-14
+
+
+def test_xyshift_round_trip():
+    rng = np.random.default_rng(22)
+    xs, ys = rng.normal(0, 1e-3, 40), rng.normal(0, 1e-3, 40)
+    o = _track_xy([I.xy_shift(2.5e-3, -1.25e-3), I.xy_shift(-2.5e-3, 1.25e-3)], xs, ys)
+    assert np.max(np.abs(o["x"] - xs)) <= np.max(np.spacing(np.abs(xs) + 2.5e-3))
+    assert np.max(np.abs(o["y"] - ys)) <= np.max(np.spacing(np.abs(ys) + 1.25e-3))
+    o1 = _track_xy([I.xy_shift(2.5e-3, -1.25e-3)], [2.5e-3], [-1.25e-3])
+    assert o1["x"][0] == 0.0 and o1["y"][0] == 0.0
+
+
+def test_rect_aperture_edges():
+    """One ulp inside each edge survives, one ulp outside is lost, corners and
+    edges survive, a non-finite coordinate is lost with state -1."""
+    x0, x1, y0, y1 = -0.01, 0.02, -0.004, 0.006
+    el = [I.aperture_rect(x0, x1, y0, y1)]
+    up, dn = (lambda v: np.nextafter(v, np.inf)), (lambda v: np.nextafter(v, -np.inf))
+    xs = [x0, x1, x0, x1, dn(x0), up(x1), 0.0, 0.0, up(x0), dn(x1), 0.0, float("nan")]
+    ys = [y0, y1, y1, y0, 0.0, 0.0, dn(y0), up(y1), 0.0, 0.0, float("inf"), 0.0]
+    o = _track_xy(el + [I.drift(0.5)], xs, ys)
+    assert list(o["state"]) == [1, 1, 1, 1, 0, 0, 0, 0, 1, 1, -1, -1]
+
+
+def test_ellipse_aperture_boundary():
+    a, b = 0.03, 0.012
+    t = np.linspace(0.0, 2 * math.pi, 37)[:-1]
+    xs, ys = a * np.cos(t), b * np.sin(t)
+    inside = _track_xy([I.aperture_ellipse(a, b)], xs * (1 - 1e-12), ys * (1 - 1e-12))
+    outside = _track_xy([I.aperture_ellipse(a, b)], xs * (1 + 1e-12), ys * (1 + 1e-12))
+    assert np.all(inside["state"] == 1) and np.all(outside["state"] == 0)
+
+
+def test_tilted_shifted_apertures_geometry():
+    """A rectangle and an ellipse displaced by (dx, dy) and tilted by theta
+    (the aperture transition of the paper's loss-location figure): the loss
+    decision of random points away from the boundary equals a half-plane test
+    against the rectangle's corners in the laboratory frame, and the
+    laboratory-frame quadratic form (p - d)^T Q (p - d) <= 1 of the ellipse."""
+    rng = np.random.default_rng(23)
+    dx, dy, th = 1.5e-3, -0.8e-3, 0.35
+    x0, x1, y0, y1 = -0.012, 0.010, -0.006, 0.007
+    n = 4000
+    xs, ys = rng.uniform(-0.02, 0.02, n), rng.uniform(-0.015, 0.015, n)
+    o = _track_xy(I.misaligned([I.aperture_rect(x0, x1, y0, y1)], dx, dy, th), xs, ys)
+    # corners in the lab frame: d + R(-theta) (u, v), counter-clockwise
+    c, s = math.cos(th), math.sin(th)
+    corners = [(dx + c * u - s * v, dy + s * u + c * v) for u, v in ((x0, y0), (x1, y0), (x1, y1), (x0, y1))]
+    cross = np.stack([(bx - ax) * (ys - ay) - (by - ay) * (xs - ax)
+                      for (ax, ay), (bx, by) in zip(corners, corners[1:] + corners[:1])])
+    sure_in = np.all(cross > 1e-12, axis=0)
+    sure_out = np.any(cross < -1e-12, axis=0)
+    assert sure_in.sum() > 500 and sure_out.sum() > 500
+    assert np.all(o["state"][sure_in] == 1) and np.all(o["state"][sure_out] == 0)
+    a, b = 0.011, 0.006
+    o = _track_xy(I.misaligned([I.aperture_ellipse(a, b)], dx, dy, th), xs, ys)
+    R = np.array([[c, s], [-s, c]])
+    Q = R.T @ np.diag([1 / a ** 2, 1 / b ** 2]) @ R
+    d = np.stack([xs - dx, ys - dy])
+    f = np.einsum("in,ij,jn->n", d, Q, d)
+    assert np.all(o["state"][f < 1 - 1e-9] == 1) and np.all(o["state"][f > 1 + 1e-9] == 0)
+
+
+def test_misaligned_quadrupole_is_a_dipole_kick():
+    """A thin quadrupole displaced by dx kicks a particle on the axis by
+    px = k1 L dx (feed-down).  Tilted by +pi/4 (frame x' = x cos + y sin,
+    y' = -x sin + y cos) it kicks a particle at (0, y) by px = -k1 L y,
+    py = 0, worked out by hand: the skew quadrupole ksl1 = -k1 L of the
+    multipole convention (b = (knl + i ksl)(x + i y), px -= Re b)."""
+    k1l, dx = 0.05, 2e-3
+    o = _track_xy(I.misaligned([I.multipole(knl=[0.0, k1l])], dx=dx), [0.0], [0.0])
+    assert o["px"][0] == pytest.approx(k1l * dx, rel=1e-15) and o["x"][0] == pytest.approx(0.0, abs=1e-19)
+    y = 1e-3
+    o = _track_xy(I.misaligned([I.multipole(knl=[0.0, k1l])], tilt=math.pi / 4), [0.0], [y])
+    assert o["px"][0] == pytest.approx(-k1l * y, rel=1e-14) and abs(o["py"][0]) < 1e-19
+    sk = _track_xy([I.multipole(ksl=[0.0, -k1l])], [0.0], [y])
+    assert o["px"][0] == pytest.approx(sk["px"][0], rel=1e-14)
+
+
 def test_segment_resume_bitwise():
     """track(a) then track(b) from turn a equals track(a+b), radiation included."""
     el, ref, _ = I.lepton_ring(n_cells=4, E0=5e9, v_total=30e6)
