@@ -268,6 +268,37 @@ int xt_batched_sync_status(xt_tracker* const* trackers, const xt_particles* part
 void xt_batched_release(void);
 
 /* ------------------------------------------------------------------------ */
+/* Loss-location refinement (section "Particle-matter interaction and
+   collimation studies" of the paper: backtracking and a polygonal
+   interpolation of the aperture).
+   For every particle with state 0 lost at an aperture row e (XT_APERTURE,
+   XT_APERTURE_RECT, XT_APERTURE_ELLIPSE), s_loss[i] receives the position
+   [m from the start of the table, the loss turn not included] where its
+   trajectory first leaves the aperture between the previous aperture row q
+   and e, to within ds [m]:
+   - the aperture between q and e is the polygon interpolated linearly in s
+     between the two apertures' polygons; each polygon joins the boundary
+     points met by n_angles rays at angles 2 pi k / n_angles from the
+     aperture's own frame origin (which must lie inside it), taken to the
+     laboratory frame through the shift and rotation rows before the row;
+   - the particle is backtracked from its loss coordinates to the exit of q
+     with the inverse maps (drift of -L, kicks and frame changes undone),
+     then tracked forward again with every drift cut into steps of at most
+     ds; s_loss is the first step end found outside the interpolated
+     polygon, or the position of e if none is;
+   - radiation is not reversed (the maps between two apertures are taken
+     without it), and a linear-map row between q and e makes the particle's
+     result NaN.
+   Other particles get NaN.  Particles are DEVICE arrays as for xt_track and
+   are not modified; s_loss is a DEVICE array of n doubles.  Errors:
+   XT_ERR_INVALID (null pointer, ds <= 0, n_angles outside 8..1024, no
+   aperture row in the table).  The tables are built on the first call (and
+   when n_angles changes) and kept by the tracker; the call is asynchronous
+   on `stream` afterwards.                                                   */
+int xt_refine_losses(xt_tracker* tr, const xt_particles* particles, double ds, int32_t n_angles,
+                     double* s_loss, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Dynamic-aperture surrogate network.  The paper lists dynamic-aperture
    estimates based on machine learning among Xsuite's applications (section
    "Lattice modelling and single particle tracking"); the network is this

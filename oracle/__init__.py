@@ -76,6 +76,8 @@ def lib() -> ctypes.CDLL:
             L.xo_spectrum_sample.argtypes = [dbl]
             L.xo_spectrum_sample.restype = dbl
             L.xo_ref_constants.argtypes = [P, P]
+            L.xo_refine_losses.argtypes = [P, i64, P] + [P] * 11 + [i64, dbl, i32, P]
+            L.xo_refine_losses.restype = i32
             _lib = L
     return _lib
 
@@ -93,6 +95,23 @@ def _elements(elements) -> np.ndarray:
     if el.dtype != ELEMENT_DTYPE:
         el = el.astype(ELEMENT_DTYPE)
     return el
+
+
+def refine_losses(elements, ref, particles: dict, ds: float, n_angles: int = 128) -> np.ndarray:
+    """Loss positions [m] of the particles lost at apertures (state 0), NaN
+    for the others; see xo_refine_losses."""
+    el = _elements(elements)
+    r = _ref_arr(ref)
+    a = {k: np.ascontiguousarray(particles[k], dtype=np.float64) for k in FLOAT_FIELDS}
+    st = np.ascontiguousarray(particles["state"], dtype=np.int32)
+    ae = np.ascontiguousarray(particles["at_element"], dtype=np.int32)
+    n = st.shape[0]
+    out = np.empty(n)
+    rc = lib().xo_refine_losses(_ptr(el), el.shape[0], _ptr(r), *[_ptr(a[k]) for k in FLOAT_FIELDS], _ptr(st),
+                                _ptr(ae), n, float(ds), int(n_angles), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle refine_losses rejected its arguments")
+    return out
 
 
 def track(elements, ref, particles: dict, n_turns: int, start_turn: int = 0,

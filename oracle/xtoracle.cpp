@@ -631,6 +631,107 @@ static inline void turn_guard(Part<T>& p, int turn, int n_el) {
   if (!(std::fabs(val(p.x)) <= 1.0 && std::fabs(val(p.y)) <= 1.0)) mark_lost(p, -3, turn, n_el - 1);
 }
 
+
+// ---------------------------------------------------------------------------
+// Loss-location refinement (section "Particle-matter interaction and
+// collimation studies": backtracking plus a polygonal interpolation of the
+// aperture between two aperture elements).
+
+// Reference frame at the entrance of a row: local = R(th) (lab - d), with
+// R(th) (x, y) = (x cos + y sin, -x sin + y cos); built up from the shift and
+// rotation rows before it.
+struct Frame { double th, dx, dy; };
+
+static bool is_aperture(int t) { return t == T_APERTURE || t == T_APERTURE_RECT || t == T_APERTURE_ELLIPSE; }
+
+// Distance from the aperture's frame origin to its boundary along the ray at
+// angle phi; negative if the origin is not strictly inside.
+static double ray_to_boundary(const Element& e, double phi) {
+  const double c = std::cos(phi), s = std::sin(phi);
+  if (e.type == T_APERTURE) return e.p[0];
+  if (e.type == T_APERTURE_ELLIPSE) {
+    const double a = e.p[0], b = e.p[1];
+    return 1.0 / std::sqrt(c * c / (a * a) + s * s / (b * b));
+  }
+  const double x0 = e.p[0], x1 = e.p[1], y0 = e.p[2], y1 = e.p[3];
+  if (!(x0 < 0.0 && 0.0 < x1 && y0 < 0.0 && 0.0 < y1)) return -1.0;
+  double t = INFINITY;
+  if (c > 0.0) t = std::min(t, x1 / c);
+  if (c < 0.0) t = std::min(t, x0 / c);
+  if (s > 0.0) t = std::min(t, y1 / s);
+  if (s < 0.0) t = std::min(t, y0 / s);
+  return t;
+}
+
+// Crossing-number test of (x, y) against the polygon interpolated at weight
+// w between polygons A and B (n vertices each, x then y per vertex).
+static bool inside_polygon(double x, double y, const double* A, const double* B, double w, int n) {
+  bool in = false;
+  for (int k = 0; k < n; k++) {
+    const int k2 = (k + 1 == n) ? 0 : k + 1;
+    const double ax = std::fma(w, B[2 * k] - A[2 * k], A[2 * k]);
+    const double ay = std::fma(w, B[2 * k + 1] - A[2 * k + 1], A[2 * k + 1]);
+    const double bx = std::fma(w, B[2 * k2] - A[2 * k2], A[2 * k2]);
+    const double by = std::fma(w, B[2 * k2 + 1] - A[2 * k2 + 1], A[2 * k2 + 1]);
+    if ((ay > y) != (by > y)) {
+      const double xi = ax + (y - ay) * (bx - ax) / (by - ay);
+      if (x < xi) in = !in;
+    }
+  }
+  return in;
+}
+
+// Inverse of one row's map (radiation off).  Returns false if the row has
+// no inverse here (linear map) or the backward drift is not defined.
+static bool inverse_row(Part<double>& p, const Prep& q, const RefConst& rc) {
+  switch (q.type) {
+    case T_DRIFT:
+      drift(p, -q.L, 0, 0);
+      return p.state == 1;
+    case T_MULTIPOLE: {
+      // the kick leaves x, y unchanged: recompute the field and take it back
+      double br = q.m.c[q.m.N], bi = q.m.s[q.m.N];
+      for (int n = q.m.N - 1; n >= 0; n--) {
+        const double nr = std::fma(br, p.x, std::fma(-bi, p.y, q.m.c[n]));
+        const double ni = std::fma(br, p.y, std::fma(bi, p.x, q.m.s[n]));
+        br = nr;
+        bi = ni;
+      }
+      p.px = p.px + br;
+      p.py = p.py - bi;
+      if (q.m.hxl != 0.0) {
+        p.px = std::fma(-q.m.hxl, p.opd, p.px);
+        p.px = std::fma(q.m.k0h, p.x, p.px);
+        p.zeta = std::fma(q.m.hxl * p.rv0v, p.x, p.zeta);
+      }
+      return true;
+    }
+    case T_CAVITY: {
+      const double phi = std::fma(-q.krf, p.zeta, q.lagr);
+      p.ptau = std::fma(-q.qv, SIN(phi), p.ptau);
+      energy_update(p, rc);
+      return true;
+    }
+    case T_DIPEDGE:
+      p.px = std::fma(-q.r21, p.x, p.px);
+      p.py = std::fma(-q.r43, p.y, p.py);
+      return true;
+    case T_LINEARMAP: return false;
+    case T_XYSHIFT:
+      p.x = p.x + q.dx;
+      p.y = p.y + q.dy;
+      return true;
+    case T_SROTATION: {
+      const double x = p.x, y = p.y, px = p.px, py = p.py;
+      p.x = std::fma(q.cs, x, -(q.sn * y));
+      p.y = std::fma(q.cs, y, q.sn * x);
+      p.px = std::fma(q.cs, px, -(q.sn * py));
+      p.py = std::fma(q.cs, py, q.sn * px);
+      return true;
+    }
+    default: return true;  // markers, apertures
+  }
+}
 }  // namespace xo
 
 using namespace xo;
@@ -675,6 +776,120 @@ int xo_track(const Element* el, int64_t n_el, const Reference* ref, int rad_mode
     x[i] = p.x; px[i] = p.px; y[i] = p.y; py[i] = p.py; zeta[i] = p.zeta;
     delta[i] = p.delta; ptau[i] = p.ptau; rpp[i] = p.rpp; rvv[i] = p.rvv;
     state[i] = p.state; at_turn[i] = p.at_turn; at_element[i] = p.at_element;
+  }
+  return 0;
+}
+
+// Loss-location refinement of the particles with state 0 lost at an aperture
+// row (see the helpers above): s_loss[i] = position [m from the start of the
+// table] where the trajectory first leaves the polygon interpolated between
+// the previous aperture and the losing one, found by backtracking to the
+// previous aperture and re-tracking with drifts cut into steps <= ds; the
+// aperture's own position if no step is outside; NaN for other particles, a
+// linear map in between, or an aperture whose frame origin is not inside it.
+// Returns 0, or -1 on bad input.
+int xo_refine_losses(const Element* el, int64_t n_el, const Reference* ref, const double* x, const double* px,
+                     const double* y, const double* py, const double* zeta, const double* delta,
+                     const double* ptau, const double* rpp, const double* rvv, const int32_t* state,
+                     const int32_t* at_element, int64_t n, double ds, int n_angles, double* s_loss) {
+  if (!el || !ref || n_el <= 0 || n < 0 || !(ds > 0.0) || n_angles < 8 || n_angles > 1024) return -1;
+  const RefConst rc = ref_const(*ref);
+  std::vector<Prep> prep(n_el);
+  std::vector<double> spos(n_el + 1, 0.0);
+  std::vector<Frame> fr(n_el);
+  Frame f = {0.0, 0.0, 0.0};
+  int64_t n_ap = 0;
+  for (int64_t e = 0; e < n_el; e++) {
+    if (el[e].type < 0 || el[e].type > T_APERTURE_ELLIPSE) return -1;
+    if (el[e].type == T_MULTIPOLE && (el[e].order < 0 || el[e].order > 10)) return -1;
+    prep[e] = prepare(el[e], rc);
+    fr[e] = f;
+    spos[e + 1] = spos[e] + (el[e].type == T_DRIFT ? el[e].p[0] : 0.0);
+    if (el[e].type == T_XYSHIFT) {
+      const double c = std::cos(f.th), sn = std::sin(f.th);
+      f.dx = f.dx + (c * el[e].p[0] - sn * el[e].p[1]);
+      f.dy = f.dy + (sn * el[e].p[0] + c * el[e].p[1]);
+    } else if (el[e].type == T_SROTATION) {
+      f.th = f.th + el[e].p[0];
+    }
+    if (is_aperture(el[e].type)) n_ap++;
+  }
+  if (n_ap == 0) return -1;
+  const double C = spos[n_el];
+  // laboratory-frame polygons of the apertures; previous aperture of each
+  std::vector<std::vector<double>> poly(n_el);
+  std::vector<int64_t> prev(n_el, -1);
+  std::vector<char> ok(n_el, 0);
+  const double two_pi = 6.283185307179586;
+  int64_t last = -1;
+  for (int64_t e = 0; e < n_el; e++)
+    if (is_aperture(el[e].type)) last = e;
+  for (int64_t e = 0; e < n_el; e++) {
+    if (!is_aperture(el[e].type)) continue;
+    prev[e] = last;
+    last = e;
+    poly[e].resize(2 * (size_t)n_angles);
+    const double c = std::cos(fr[e].th), sn = std::sin(fr[e].th);
+    ok[e] = 1;
+    for (int k = 0; k < n_angles; k++) {
+      const double phi = two_pi * (double)k / (double)n_angles;
+      const double r = ray_to_boundary(el[e], phi);
+      if (!(r > 0.0)) ok[e] = 0;
+      const double lx = r * std::cos(phi), ly = r * std::sin(phi);
+      poly[e][2 * k] = (c * lx - sn * ly) + fr[e].dx;
+      poly[e][2 * k + 1] = (sn * lx + c * ly) + fr[e].dy;
+    }
+  }
+  for (int64_t i = 0; i < n; i++) {
+    s_loss[i] = NAN;
+    const int64_t e = at_element[i];
+    if (state[i] != 0 || e < 0 || e >= n_el || !is_aperture(el[e].type)) continue;
+    const int64_t q = prev[e];
+    if (!ok[e] || !ok[q]) continue;
+    Part<double> p;
+    p.x = x[i]; p.px = px[i]; p.y = y[i]; p.py = py[i]; p.zeta = zeta[i];
+    p.delta = delta[i]; p.ptau = ptau[i]; p.rpp = rpp[i]; p.rvv = rvv[i];
+    p.state = 1; p.at_turn = 0; p.at_element = 0; p.id = 0;
+    derive(p, rc);
+    // back to the exit of q
+    bool good = true;
+    for (int64_t j = e;;) {
+      j = (j == 0) ? n_el - 1 : j - 1;
+      if (j == q) break;
+      if (!inverse_row(p, prep[j], rc)) { good = false; break; }
+    }
+    if (!good) continue;
+    // forward again, drifts in steps, against the interpolated polygon
+    const double s_q = spos[q];
+    const double seg = (e > q) ? spos[e] - s_q : spos[e] + C - s_q;
+    double pos = s_q;
+    double found = NAN;
+    for (int64_t j = q;;) {
+      j = (j + 1 == n_el) ? 0 : j + 1;
+      if (j == e) break;
+      if (prep[j].type == T_DRIFT && prep[j].L > 0.0) {
+        const double L = prep[j].L;
+        const int64_t ns = (int64_t)std::ceil(L / ds);
+        const double h = L / (double)ns;
+        const double c = std::cos(fr[j].th), sn = std::sin(fr[j].th);
+        for (int64_t k = 1; k <= ns; k++) {
+          drift(p, h, 0, 0);
+          const double at = std::fma((double)k, h, pos);
+          if (p.state != 1) { found = at; break; }
+          const double lx = (c * p.x - sn * p.y) + fr[j].dx;
+          const double ly = (sn * p.x + c * p.y) + fr[j].dy;
+          const double w = (at - s_q) / seg;
+          if (!inside_polygon(lx, ly, poly[q].data(), poly[e].data(), w, n_angles)) { found = at; break; }
+        }
+        if (found == found) break;
+        pos = pos + L;
+      } else {
+        track_element(p, prep[j], 0, rc, 0, 0, 0);
+        if (p.state != 1) { found = pos; break; }
+      }
+    }
+    if (!(found == found)) found = spos[e];
+    s_loss[i] = (found >= C) ? found - C : found;
   }
   return 0;
 }

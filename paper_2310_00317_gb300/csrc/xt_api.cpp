@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -107,6 +108,10 @@ struct xt_tracker {
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
   size_t ev_used = 0;
+  // loss-location refinement tables (one device buffer), built on first use
+  int refine_angles = 0;
+  uint8_t* d_refine = nullptr;
+  RefineArgs refine_tab;  // table pointers into d_refine
 };
 
 static int prof_pair(xt_tracker* t, cudaEvent_t* a, cudaEvent_t* b) {
@@ -310,6 +315,7 @@ void xt_tracker_destroy(xt_tracker* t) {
   cudaFree(t->d_idx);
   cudaFree(t->d_counts);
   cudaFree(t->d_stage);
+  cudaFree(t->d_refine);
   if (t->h_cancel) cudaFreeHost(t->h_cancel);
   for (auto& pr : t->ev) {
     cudaEventDestroy(pr.first);
@@ -468,6 +474,151 @@ int xt_fp64_peak(double* flops_per_s, double* elapsed_ms, void* stream) {
   // 16 independent fma chains per thread per iteration, 2 flops each
   *flops_per_s = 2.0 * 16.0 * (double)iters * (double)grid * (double)block / (ms * 1e-3);
   *elapsed_ms = ms;
+  return XT_OK;
+}
+
+// Loss-location refinement tables (see xt_refine_losses in xtgb.h): entrance
+// position and reference frame of every row, record offsets, previous
+// aperture, and the laboratory-frame polygon of every aperture from rays at
+// n_angles angles about its frame origin.
+static bool is_aperture_type(int t) {
+  return t == XT_APERTURE || t == XT_APERTURE_RECT || t == XT_APERTURE_ELLIPSE;
+}
+
+// distance from the aperture's frame origin to its boundary along angle phi;
+// negative if the origin is not strictly inside
+static double boundary_distance(const xt_element& e, double phi) {
+  const double c = std::cos(phi), s = std::sin(phi);
+  if (e.type == XT_APERTURE) return e.p[0];
+  if (e.type == XT_APERTURE_ELLIPSE) {
+    const double a = e.p[0], b = e.p[1];
+    return 1.0 / std::sqrt(c * c / (a * a) + s * s / (b * b));
+  }
+  const double x0 = e.p[0], x1 = e.p[1], y0 = e.p[2], y1 = e.p[3];
+  if (!(x0 < 0.0 && 0.0 < x1 && y0 < 0.0 && 0.0 < y1)) return -1.0;
+  double t = INFINITY;
+  if (c > 0.0) t = std::min(t, x1 / c);
+  if (c < 0.0) t = std::min(t, x0 / c);
+  if (s > 0.0) t = std::min(t, y1 / s);
+  if (s < 0.0) t = std::min(t, y0 / s);
+  return t;
+}
+
+static int build_refine_tables(xt_tracker* t, int n_angles) {
+  const int64_t n = t->lat.n_el;
+  std::vector<int32_t> row_off(n, -1), prev(n, -1), pidx(n, -1);
+  std::vector<double> spos(n + 1, 0.0), frame(4 * n, 0.0);
+  double th = 0.0, fdx = 0.0, fdy = 0.0;
+  size_t k = 0;
+  int64_t last = -1;
+  for (int64_t i = 0; i < n; i++) {
+    const xt_element& e = t->table[i];
+    if (e.type != XT_MARKER) row_off[i] = (int32_t)t->lat.rec_off[k++];
+    frame[4 * i] = std::cos(th);
+    frame[4 * i + 1] = std::sin(th);
+    frame[4 * i + 2] = fdx;
+    frame[4 * i + 3] = fdy;
+    spos[i + 1] = spos[i] + (e.type == XT_DRIFT ? e.p[0] : 0.0);
+    if (e.type == XT_XYSHIFT) {
+      const double c = std::cos(th), sn = std::sin(th);
+      fdx = fdx + (c * e.p[0] - sn * e.p[1]);
+      fdy = fdy + (sn * e.p[0] + c * e.p[1]);
+    } else if (e.type == XT_SROTATION) {
+      th = th + e.p[0];
+    }
+    if (is_aperture_type(e.type)) last = i;
+  }
+  if (last < 0) return fail(XT_ERR_INVALID, "refinement needs an aperture row in the table");
+  const double two_pi = 6.283185307179586;
+  std::vector<double> polys;
+  int32_t np = 0;
+  for (int64_t i = 0; i < n; i++) {
+    const xt_element& e = t->table[i];
+    if (!is_aperture_type(e.type)) continue;
+    prev[i] = (int32_t)last;
+    last = i;
+    const double c = frame[4 * i], sn = frame[4 * i + 1];
+    std::vector<double> v(2 * (size_t)n_angles);
+    bool ok = true;
+    for (int kk = 0; kk < n_angles; kk++) {
+      const double phi = two_pi * (double)kk / (double)n_angles;
+      const double r = boundary_distance(e, phi);
+      if (!(r > 0.0)) ok = false;
+      const double lx = r * std::cos(phi), ly = r * std::sin(phi);
+      v[2 * kk] = (c * lx - sn * ly) + frame[4 * i + 2];
+      v[2 * kk + 1] = (sn * lx + c * ly) + frame[4 * i + 3];
+    }
+    if (!ok) continue;
+    pidx[i] = np++;
+    polys.insert(polys.end(), v.begin(), v.end());
+  }
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t b_off = al(n * 4), b_prev = al(n * 4), b_pidx = al(n * 4), b_spos = al((n + 1) * 8),
+               b_frame = al(4 * n * 8), b_poly = al(std::max<size_t>(polys.size(), 1) * 8);
+  const size_t total = b_off + b_prev + b_pidx + b_spos + b_frame + b_poly;
+  std::vector<uint8_t> h(total, 0);
+  size_t o = 0;
+  std::memcpy(h.data() + o, row_off.data(), n * 4);
+  const size_t o_off = o;
+  o += b_off;
+  std::memcpy(h.data() + o, prev.data(), n * 4);
+  const size_t o_prev = o;
+  o += b_prev;
+  std::memcpy(h.data() + o, pidx.data(), n * 4);
+  const size_t o_pidx = o;
+  o += b_pidx;
+  std::memcpy(h.data() + o, spos.data(), (n + 1) * 8);
+  const size_t o_spos = o;
+  o += b_spos;
+  std::memcpy(h.data() + o, frame.data(), 4 * n * 8);
+  const size_t o_frame = o;
+  o += b_frame;
+  if (!polys.empty()) std::memcpy(h.data() + o, polys.data(), polys.size() * 8);
+  const size_t o_poly = o;
+  if (t->d_refine) cudaFree(t->d_refine);
+  t->d_refine = nullptr;
+  t->refine_angles = 0;
+  int rc = dev_alloc(&t->d_refine, total);
+  if (rc) return rc;
+  CK(cudaMemcpy(t->d_refine, h.data(), total, cudaMemcpyHostToDevice));
+  RefineArgs& a = t->refine_tab;
+  std::memset(&a, 0, sizeof(a));
+  a.lat = t->d_lat;
+  a.row_off = (const int32_t*)(t->d_refine + o_off);
+  a.prev_ap = (const int32_t*)(t->d_refine + o_prev);
+  a.poly_idx = (const int32_t*)(t->d_refine + o_pidx);
+  a.spos = (const double*)(t->d_refine + o_spos);
+  a.frame = (const double*)(t->d_refine + o_frame);
+  a.polys = (const double*)(t->d_refine + o_poly);
+  a.n_el = (int32_t)n;
+  a.n_angles = n_angles;
+  a.ref = t->ref;
+  a.sn = t->sn;
+  t->refine_angles = n_angles;
+  return XT_OK;
+}
+
+int xt_refine_losses(xt_tracker* t, const xt_particles* p, double ds, int32_t n_angles, double* s_loss,
+                     void* stream) {
+  g_err.clear();
+  if (!t || !particles_ok(p) || !s_loss) return fail(XT_ERR_INVALID, "null tracker, particles or s_loss");
+  if (!(ds > 0.0) || n_angles < 8 || n_angles > 1024)
+    return fail(XT_ERR_INVALID, "refinement needs ds > 0 and 8 <= n_angles <= 1024");
+  if (t->refine_angles != n_angles) {
+    int rc = build_refine_tables(t, n_angles);
+    if (rc) return rc;
+  }
+  if (p->n == 0) return XT_OK;
+  RefineArgs a = t->refine_tab;
+  a.ds = ds;
+  a.x = p->x; a.px = p->px; a.y = p->y; a.py = p->py; a.zeta = p->zeta;
+  a.delta = p->delta; a.ptau = p->ptau; a.rpp = p->rpp; a.rvv = p->rvv;
+  a.state = p->state;
+  a.at_element = p->at_element;
+  a.s_loss = s_loss;
+  a.n = p->n;
+  int e = launch_refine(a, stream);
+  if (e) return cuda_fail((cudaError_t)e, "refinement launch");
   return XT_OK;
 }
 

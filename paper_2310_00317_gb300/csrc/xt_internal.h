@@ -109,6 +109,32 @@ struct TrackArgs {
   SinTab sn;
 };
 
+// Loss-location refinement (one thread per particle).  Tables built on the
+// host per tracker: for every table row its record offset in `lat` (-1 for a
+// marker), its entrance position and reference frame (cos, sin, dx, dy:
+// lab = R(-th) local + d), the previous aperture row and the index of its
+// laboratory-frame polygon (-1 if none or unusable).
+struct RefineArgs {
+  const uint8_t* lat;
+  const int32_t* row_off;
+  const double* spos;      // n_el + 1 entries (the last is the table length)
+  const double* frame;     // 4 per row
+  const int32_t* prev_ap;
+  const int32_t* poly_idx;
+  const double* polys;     // n_angles x (x, y) per polygon
+  int32_t n_el;
+  int32_t n_angles;
+  double ds;
+  const double *x, *px, *y, *py, *zeta, *delta, *ptau, *rpp, *rvv;
+  const int32_t *state, *at_element;
+  double* s_loss;
+  int64_t n;
+  RefDev ref;
+  SinTab sn;
+};
+
+int launch_refine(const RefineArgs& a, void* stream);
+
 // Batched-seed variant: per-seed lattice and particle pointers in device arrays.
 struct SeedDev {
   const uint8_t* lat;

@@ -714,6 +714,171 @@ __global__ void __launch_bounds__(XT_MAX_BLOCK) track_batched_kernel(const Batch
 }
 
 // ---------------------------------------------------------------------------
+// Loss-location refinement (section "Particle-matter interaction and
+// collimation studies"): one thread per lost particle, backtracking to the
+// previous aperture with the inverse maps, then re-tracking with drifts cut
+// into steps and each step end tested against the aperture polygon
+// interpolated in s.  Particles sit at different places, so there are no
+// warp votes here: the series order of the drift is chosen per lane.
+
+__device__ __forceinline__ bool drift_lane(Part& p, double L) {
+  const double u = fma(-p.px, p.px, fma(-p.py, p.py, p.dm1));
+  const uint64_t ub = dbits(u), ua = abs_bits(u);
+  const bool valid = (ub >> 63) ? (ua < 0x3FF0000000000000ull) : (ub < 0x7FF0000000000000ull);
+  if (!valid) return false;
+  double yh;
+  if (ua <= 0x3ED0000000000000ull) yh = inv_pz_m1_order3(u);
+  else if (ua <= 0x3F60000000000000ull) yh = inv_pz_m1_order6(u);
+  else if (ua <= 0x3F80000000000000ull) yh = inv_pz_m1_order8(u);
+  else yh = 1.0 / sqrt(1.0 + u) - 1.0;
+  const double lpz = fma(L, yh, L);
+  p.x = fma(p.px, lpz, p.x);
+  p.y = fma(p.py, lpz, p.y);
+  p.zeta = fma(-L, fma(p.ep, yh, p.epm1), p.zeta);
+  return true;
+}
+
+// Inverse of one record's map, radiation off.  False if there is none here
+// (linear map) or the backward drift is not defined.
+__device__ __forceinline__ bool inverse_record(Part& p, uint32_t type, uint32_t order, uint32_t flags,
+                                               const double* prm, const RefDev& r, const SinTab& sn) {
+  switch (type) {
+    case XT_DRIFT: return drift_lane(p, -prm[0]);
+    case XT_MULTIPOLE: {  // x, y are unchanged by the kick: recompute the field, take it back
+      const double2* cf = (const double2*)(prm + MP_COEF);
+      double2 c = cf[order];
+      double br = c.x, bi = c.y;
+      for (int n = (int)order - 1; n >= 0; n--) {
+        c = cf[n];
+        const double nr = fma(br, p.x, fma(-bi, p.y, c.x));
+        const double ni = fma(br, p.y, fma(bi, p.x, c.y));
+        br = nr;
+        bi = ni;
+      }
+      p.px = p.px + br;
+      p.py = p.py - bi;
+      if (flags & REC_CURV) {
+        p.px = fma(-prm[MP_HXL], p.opd, p.px);
+        p.px = fma(prm[MP_K0H], p.x, p.px);
+        p.zeta = fma(prm[MP_HXL] * p.rv0v, p.x, p.zeta);
+      }
+      return true;
+    }
+    case XT_CAVITY: {
+      const double phi = fma(-prm[0], p.zeta, prm[1]);
+      p.ptau = fma(-prm[2], sin_cw(phi, sn), p.ptau);
+      energy_update(p, r);
+      return true;
+    }
+    case XT_DIPEDGE:
+      p.px = fma(-prm[0], p.x, p.px);
+      p.py = fma(-prm[1], p.y, p.py);
+      return true;
+    case XT_LINEARMAP: return false;
+    case XT_XYSHIFT:
+      p.x = p.x + prm[0];
+      p.y = p.y + prm[1];
+      return true;
+    case XT_SROTATION: {
+      const double c = prm[0], s = prm[1];
+      const double x = p.x, y = p.y, px = p.px, py = p.py;
+      p.x = fma(c, x, -(s * y));
+      p.y = fma(c, y, s * x);
+      p.px = fma(c, px, -(s * py));
+      p.py = fma(c, py, s * px);
+      return true;
+    }
+    default: return true;  // apertures
+  }
+}
+
+// Crossing-number test of (x, y) against the polygon interpolated at weight
+// w between polygons A and B (n vertices, x then y per vertex).
+__device__ __forceinline__ bool inside_polygon(double x, double y, const double* A, const double* B, double w,
+                                               int n) {
+  bool in = false;
+  for (int k = 0; k < n; k++) {
+    const int k2 = (k + 1 == n) ? 0 : k + 1;
+    const double ax = fma(w, B[2 * k] - A[2 * k], A[2 * k]);
+    const double ay = fma(w, B[2 * k + 1] - A[2 * k + 1], A[2 * k + 1]);
+    const double bx = fma(w, B[2 * k2] - A[2 * k2], A[2 * k2]);
+    const double by = fma(w, B[2 * k2 + 1] - A[2 * k2 + 1], A[2 * k2 + 1]);
+    if ((ay > y) != (by > y)) {
+      const double xi = ax + (y - ay) * (bx - ax) / (by - ay);
+      if (x < xi) in = !in;
+    }
+  }
+  return in;
+}
+
+__global__ void __launch_bounds__(128) refine_kernel(RefineArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const double nan = __longlong_as_double(0x7FF8000000000000ll);
+  a.s_loss[i] = nan;
+  const int e = a.at_element[i];
+  if (a.state[i] != 0 || e < 0 || e >= a.n_el) return;
+  const int q = a.prev_ap[e];
+  if (q < 0 || a.poly_idx[e] < 0 || a.poly_idx[q] < 0) return;
+  Part p;
+  p.x = a.x[i]; p.px = a.px[i]; p.y = a.y[i]; p.py = a.py[i]; p.zeta = a.zeta[i];
+  p.delta = a.delta[i]; p.ptau = a.ptau[i]; p.rpp = a.rpp[i]; p.rvv = a.rvv[i];
+  derive(p, a.ref);
+  for (int j = e;;) {  // back to the exit of q
+    j = (j == 0) ? a.n_el - 1 : j - 1;
+    if (j == q) break;
+    const int off = a.row_off[j];
+    if (off < 0) continue;
+    const uint4 hv = *(const uint4*)(a.lat + off);
+    if (!inverse_record(p, hv.x & 0xFFFFu, hv.x >> 16, hv.y & 0xFFFFu, (const double*)(a.lat + off + 16), a.ref,
+                        a.sn))
+      return;
+  }
+  const double* PA = a.polys + (int64_t)a.poly_idx[q] * 2 * a.n_angles;
+  const double* PB = a.polys + (int64_t)a.poly_idx[e] * 2 * a.n_angles;
+  const double s_q = a.spos[q];
+  const double C = a.spos[a.n_el];
+  const double seg = (e > q) ? a.spos[e] - s_q : a.spos[e] + C - s_q;
+  double pos = s_q;
+  double found = nan;
+  bool hit = false;
+  RadCtx rc;
+  rc.seed = 0; rc.xi = nullptr; rc.F = nullptr; rc.K = 0;
+  for (int j = q;;) {
+    j = (j + 1 == a.n_el) ? 0 : j + 1;
+    if (j == e) break;
+    const int off = a.row_off[j];
+    if (off < 0) continue;
+    const uint4 hv = *(const uint4*)(a.lat + off);
+    const uint32_t type = hv.x & 0xFFFFu;
+    const double* prm = (const double*)(a.lat + off + 16);
+    if (type == XT_DRIFT && prm[0] > 0.0) {
+      const double L = prm[0];
+      const int64_t ns = (int64_t)ceil(L / a.ds);
+      const double h = L / (double)ns;
+      const double c = a.frame[4 * j], sn = a.frame[4 * j + 1], dx = a.frame[4 * j + 2], dy = a.frame[4 * j + 3];
+      for (int64_t k = 1; k <= ns; k++) {
+        const bool ok = drift_lane(p, h);
+        const double at = fma((double)k, h, pos);
+        if (!ok) { found = at; hit = true; break; }
+        const double lx = (c * p.x - sn * p.y) + dx;
+        const double ly = (sn * p.x + c * p.y) + dy;
+        const double w = (at - s_q) / seg;
+        if (!inside_polygon(lx, ly, PA, PB, w, a.n_angles)) { found = at; hit = true; break; }
+      }
+      if (hit) break;
+      pos = pos + L;
+    } else if (type == XT_DRIFT) {
+      if (!drift_lane(p, prm[0])) { found = pos; hit = true; break; }
+    } else {
+      element<XT_RAD_OFF>(p, type, hv.x >> 16, hv.y & 0xFFFFu, hv.z, prm, a.ref, a.sn, rc, 0, 0);
+    }
+  }
+  if (!hit) found = a.spos[e];
+  a.s_loss[i] = (found >= C) ? found - C : found;
+}
+
+// ---------------------------------------------------------------------------
 // Order-preserving compaction of the alive particles (state == 1).
 static const int CB = 1024;
 
@@ -955,6 +1120,12 @@ __global__ void __launch_bounds__(256) fp64_probe_kernel(double* out, int iters)
 
 int launch_fp64_probe(double* out, int grid, int block, int iters, void* stream) {
   fp64_probe_kernel<<<grid, block, 0, (cudaStream_t)stream>>>(out, iters);
+  return (int)cudaGetLastError();
+}
+
+int launch_refine(const RefineArgs& a, void* stream) {
+  if (a.n <= 0) return 0;
+  refine_kernel<<<(unsigned)((a.n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(a);
   return (int)cudaGetLastError();
 }
 

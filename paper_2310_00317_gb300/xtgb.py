@@ -80,6 +80,7 @@ def lib() -> ctypes.CDLL:
             L.xt_reset_cancel.argtypes = [P]
             L.xt_element_flops.argtypes = [P, P, i64]
             L.xt_autotune.argtypes = [P, P, i64, P]
+            L.xt_refine_losses.argtypes = [P, P, ctypes.c_double, ctypes.c_int32, P, P]
             L.xt_track_batched.argtypes = [P, P, i32, i64, i64, i32, P]
             L.xt_batched_sync_status.argtypes = [P, P, i32, P]
             L.xt_set_profiling.argtypes = [P, i32]
@@ -90,7 +91,7 @@ def lib() -> ctypes.CDLL:
             for name in ("xt_tracker_create", "xt_tracker_set_options", "xt_tracker_get_options",
                          "xt_track", "xt_track_host", "xt_sync_status", "xt_cancel", "xt_reset_cancel",
                          "xt_element_flops", "xt_autotune", "xt_track_batched", "xt_batched_sync_status",
-                         "xt_set_profiling", "xt_kernel_time", "xt_fp64_peak"):
+                         "xt_set_profiling", "xt_kernel_time", "xt_fp64_peak", "xt_refine_losses"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -253,6 +254,17 @@ class Tracker:
         n = ctypes.c_int64()
         _check(lib().xt_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+    def refine_losses(self, particles: Particles, ds: float, n_angles: int = 128, stream=None):
+        """Loss positions [m from the start of the table] of the particles
+        lost at apertures, to within ds, as a CUDA float64 tensor (NaN for the
+        others); see xt_refine_losses."""
+        import torch
+        out = torch.empty(particles.n, dtype=torch.float64, device=particles.t["x"].device)
+        s = particles.c_struct()
+        _check(lib().xt_refine_losses(self._h, ctypes.byref(s), float(ds), int(n_angles), out.data_ptr(),
+                                      _stream_handle(stream)))
+        return out
 
     def autotune(self, probe: Particles, probe_turns: int, stream=None) -> dict:
         s = probe.c_struct()

@@ -126,6 +126,47 @@ def test_misaligned_elements_and_aperture_shapes_bitwise():
     assert np.sum(o["state"] == 1) > 500
 
 
+def test_refine_losses_bitwise():
+    """Loss-location refinement on the GPU against the oracle, bit for bit:
+    a misaligned FODO ring with a rectangular then an elliptic aperture
+    (shifted and tilted with respect to each other) and circular apertures
+    in the cells, particles lost over 40 turns, refined to 1 cm with
+    128-gon apertures; NaN for survivors and for a ring with a linear map
+    between two apertures."""
+    rows = [I.cavity(2e6, 400e6, 180.0), I.aperture(0.006)]
+    for c in range(6):
+        rows += I.misaligned([I.multipole(knl=[0.0, 0.2])], dx=1e-4 * (c - 2.5), tilt=1e-3 * c)
+        rows += [I.drift(2.0), I.multipole(knl=[0.0, 0.0, 0.05]), I.drift(2.0)]
+        rows += I.misaligned([I.multipole(knl=[0.0, -0.2])], dy=5e-5 * c)
+        rows += [I.drift(2.0), I.aperture(0.0055), I.drift(2.0)]
+    rows += I.misaligned([I.aperture_rect(-4e-3, 4.5e-3, -2.5e-3, 2.8e-3)], dx=2e-4, dy=-1e-4, tilt=0.1)
+    rows += [I.drift(1.5), I.drift(1.0)]
+    rows += I.misaligned([I.aperture_ellipse(4.6e-3, 3.1e-3)], dx=-1.5e-4, dy=1e-4, tilt=-0.07)
+    el = I.table(rows)
+    p = random_particles(PROTON, 3000, 37, sx=1.6e-3, spx=8e-5, sd=2e-4)
+    o = oracle.track(el, PROTON, p, 40)
+    assert np.sum(o["state"] == 0) > 500
+    s_o = oracle.refine_losses(el, PROTON, o, 0.01, 128)
+    import torch
+    tr = xtgb.Tracker(el, PROTON)
+    P = xtgb.Particles.from_numpy(o)
+    s_g = tr.refine_losses(P, 0.01, 128).cpu().numpy()
+    tr.close()
+    same = (s_g == s_o) | (np.isnan(s_g) & np.isnan(s_o))
+    assert np.all(same), np.flatnonzero(~same)[:5]
+    assert np.all(np.isnan(s_o[o["state"] != 0])) and not np.any(np.isnan(s_o[o["state"] == 0]))
+    # a linear map between two apertures: no inverse, NaN on both sides
+    el2 = I.table([I.aperture(0.01), I.drift(1.0), I.linear_map(np.eye(6)), I.drift(1.0), I.aperture(0.01)])
+    q = I.make_particles(PROTON, np.array([0.009]), np.array([2e-3]), np.zeros(1), np.zeros(1), np.zeros(1),
+                         np.zeros(1))
+    oq = oracle.track(el2, PROTON, q, 1)
+    assert oq["state"][0] == 0
+    tr2 = xtgb.Tracker(el2, PROTON)
+    assert np.isnan(tr2.refine_losses(xtgb.Particles.from_numpy(oq), 0.01).cpu().numpy()[0])
+    assert np.isnan(oracle.refine_losses(el2, PROTON, oq, 0.01)[0])
+    tr2.close()
+
+
 def test_lhc_ring_sample_bitwise():
     """LHC-scale ring (20,000 elements, order-10 errors, RF, apertures):
     500 DA-grid particles at large amplitude (some are lost), 5 turns."""

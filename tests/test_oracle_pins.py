@@ -504,6 +504,138 @@ def test_misaligned_quadrupole_is_a_dipole_kick():
     assert o["px"][0] == pytest.approx(sk["px"][0], rel=1e-14)
 
 
+# --------------------------------------------------------------------------
+# Loss-location refinement
+
+def _lost_at(el, xs, pxs, ys=None, pys=None):
+    n = len(xs)
+    ys = np.zeros(n) if ys is None else np.asarray(ys, float)
+    pys = np.zeros(n) if pys is None else np.asarray(pys, float)
+    p = I.make_particles(PROTON, np.asarray(xs, float), np.asarray(pxs, float), ys, pys, np.zeros(n), np.zeros(n))
+    return oracle.track(I.table(el), PROTON, p, 1)
+
+
+def _first_root(a2, a1, a0):
+    """Smallest positive root of a2 s^2 + a1 s + a0 = 0."""
+    r = np.roots([a2, a1, a0])
+    r = np.real(r[np.isreal(r)])
+    return float(np.min(r[r > 0]))
+
+
+@pytest.mark.parametrize("r2", [0.01, 0.006])
+def test_refine_straight_line_through_cylinder_and_cone(r2):
+    """Circular apertures r1 = 10 mm at s = 0 and r2 at s = 20 m with drifts
+    between: the interpolated polygon is a regular polygon of circumradius
+    r1 + (r2 - r1) s / 20 m, so a straight trajectory leaves it where
+    |x0 + a s, y0 + b s| = r(s) (a quadratic, a = px/pz, b = py/pz), less the
+    polygon's sag; the refined position lies within one step after that."""
+    r1, Ls, ds, n_ang = 0.01, 20.0, 0.01, 1024
+    el = [I.aperture(r1), I.drift(7.0), I.drift(13.0), I.aperture(r2)]
+    rng = np.random.default_rng(41)
+    n = 60
+    phi = rng.uniform(0, 2 * math.pi, n)
+    rad = rng.uniform(0.0, 0.6 * min(r1, r2), n)
+    xs, ys = rad * np.cos(phi), rad * np.sin(phi)
+    th = rng.uniform(0, 2 * math.pi, n)
+    ang = rng.uniform(6e-4, 1.2e-3, n)
+    pxs, pys = ang * np.cos(th), ang * np.sin(th)
+    o = _lost_at(el, xs, pxs, ys, pys)
+    lost = o["state"] == 0
+    assert lost.sum() > 40 and np.all(o["at_element"][lost] == 3)
+    s = oracle.refine_losses(I.table(el), PROTON, o, ds, n_ang)
+    assert np.all(np.isnan(s[~lost]))
+    sag = 1 - math.cos(math.pi / n_ang)
+    for i in np.flatnonzero(lost):
+        pz = math.sqrt(1 - pxs[i] ** 2 - pys[i] ** 2)
+        a, b = pxs[i] / pz, pys[i] / pz
+        k = (r2 - r1) / Ls
+        # (x0 + a s)^2 + (y0 + b s)^2 - (r1 + k s)^2 = 0
+        s_star = _first_root(a * a + b * b - k * k, 2 * (xs[i] * a + ys[i] * b) - 2 * r1 * k,
+                             xs[i] ** 2 + ys[i] ** 2 - r1 ** 2)
+        if s_star >= Ls:
+            continue
+        v_r = (xs[i] + a * s_star) * a + (ys[i] + b * s_star) * b
+        v_r = v_r / (r1 + k * s_star) - k
+        early = sag * r1 / max(v_r, 1e-12)
+        assert s_star - early - 1e-9 <= s[i] <= s_star + ds + 1e-9, (i, s[i], s_star)
+
+
+def test_refine_backtracks_through_a_kick():
+    """A thin quadrupole halfway between two circular apertures: the particle
+    lost at the second aperture is backtracked through the drift, the inverse
+    kick and the first drift, then re-tracked; the crossing on the second
+    straight segment is x1 + (px1 / pz1)(s - 10) = r, worked out by hand."""
+    r, k = 0.01, 0.02
+    el = [I.aperture(r), I.drift(10.0), I.multipole(knl=[0.0, -k]), I.drift(10.0), I.aperture(r)]
+    xs = np.array([0.002, 0.004, -0.003, 0.0])
+    pxs = np.array([6e-4, 4e-4, -6e-4, 7e-4])
+    o = _lost_at(el, xs, pxs)
+    s = oracle.refine_losses(I.table(el), PROTON, o, 0.005, 1024)
+    for i in range(len(xs)):
+        pz = math.sqrt(1 - pxs[i] ** 2)
+        x1 = xs[i] + pxs[i] / pz * 10.0
+        assert abs(x1) < r
+        px1 = pxs[i] + k * x1
+        pz1 = math.sqrt(1 - px1 ** 2)
+        x2 = x1 + px1 / pz1 * 10.0
+        assert o["state"][i] == 0 and abs(x2) > r
+        s_star = 10.0 + (math.copysign(r, px1) - x1) * pz1 / px1
+        early = (1 - math.cos(math.pi / 1024)) * r * pz1 / abs(px1)
+        assert s_star - early - 1e-9 <= s[i] <= s_star + 0.005 + 1e-9, (i, s[i], s_star)
+
+
+def _winding_inside(px, py, vx, vy):
+    """Winding number of the closed polygon (vx, vy) about (px, py) != 0."""
+    ang = np.arctan2(vy - py, vx - px)
+    d = np.diff(np.append(ang, ang[0]))
+    d = (d + np.pi) % (2 * np.pi) - np.pi
+    return abs(np.sum(d)) > np.pi
+
+
+def test_refine_rect_to_ellipse_transition_bruteforce():
+    """The paper's loss-location example: a rectangular aperture, then 5 m
+    further an elliptic one, shifted and tilted with respect to each other.
+    Straight trajectories scanned every 1 mm against the interpolated polygon
+    (built here from the two shapes and tested by winding number): the
+    refined position is the first outside point to within the step."""
+    n_ang, ds = 256, 0.01
+    dx, dy, th = 1.2e-3, -0.7e-3, 0.25
+    el = (I.misaligned([I.aperture_rect(-0.010, 0.012, -0.006, 0.005)], 0.0, 0.0, 0.0) + [I.drift(2.0), I.drift(3.0)]
+          + I.misaligned([I.aperture_ellipse(0.009, 0.0045)], dx, dy, th))
+    ap_e = len(el) - 3
+    rng = np.random.default_rng(43)
+    n = 40
+    xs, ys = rng.uniform(-0.004, 0.004, n), rng.uniform(-0.002, 0.002, n)
+    t = rng.uniform(0, 2 * math.pi, n)
+    pxs, pys = 1.6e-3 * np.cos(t), 1.6e-3 * np.sin(t)
+    o = _lost_at(el, xs, pxs, ys, pys)
+    lost = (o["state"] == 0) & (o["at_element"] == ap_e)
+    assert lost.sum() > 10
+    s = oracle.refine_losses(I.table(el), PROTON, o, ds, n_ang)
+    phis = 2 * np.pi * np.arange(n_ang) / n_ang
+    c, sn = np.cos(phis), np.sin(phis)
+    with np.errstate(divide="ignore"):
+        tx = np.where(c > 0, 0.012 / c, np.where(c < 0, -0.010 / c, np.inf))
+        ty = np.where(sn > 0, 0.005 / sn, np.where(sn < 0, -0.006 / sn, np.inf))
+    rr = np.minimum(tx, ty)
+    A = np.stack([rr * c, rr * sn], 1)
+    re = 1 / np.sqrt(c ** 2 / 0.009 ** 2 + sn ** 2 / 0.0045 ** 2)
+    loc = np.stack([re * c, re * sn], 1)
+    B = np.stack([math.cos(th) * loc[:, 0] - math.sin(th) * loc[:, 1] + dx,
+                  math.sin(th) * loc[:, 0] + math.cos(th) * loc[:, 1] + dy], 1)
+    for i in np.flatnonzero(lost):
+        pz = math.sqrt(1 - pxs[i] ** 2 - pys[i] ** 2)
+        first = None
+        for sv in np.arange(0.001, 5.0 + 1e-9, 0.001):
+            w = sv / 5.0
+            V = A + w * (B - A)
+            if not _winding_inside(xs[i] + pxs[i] / pz * sv, ys[i] + pys[i] / pz * sv, V[:, 0], V[:, 1]):
+                first = sv
+                break
+        first = 5.0 if first is None else first
+        assert first - 0.001 - 1e-9 <= s[i] <= first + ds + 1e-9, (i, s[i], first)
+
+
 def test_segment_resume_bitwise():
     """track(a) then track(b) from turn a equals track(a+b), radiation included."""
     el, ref, _ = I.lepton_ring(n_cells=4, E0=5e9, v_total=30e6)
