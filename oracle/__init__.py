@@ -30,6 +30,7 @@ _lib = None
 ELEMENT_DTYPE = np.dtype([("type", "<i4"), ("order", "<i4"), ("p", "<f8", (48,))], align=True)
 DRIFT, MULTIPOLE, CAVITY, DIPEDGE, LINEARMAP, APERTURE, MARKER = 1, 2, 3, 4, 5, 6, 0
 XYSHIFT, SROTATION, APERTURE_RECT, APERTURE_ELLIPSE = 7, 8, 9, 10
+BEAMBEAM4D = 11
 
 FLOAT_FIELDS = ("x", "px", "y", "py", "zeta", "delta", "ptau", "rpp", "rvv")
 INT_FIELDS = ("state", "at_turn", "at_element")
@@ -78,6 +79,14 @@ def lib() -> ctypes.CDLL:
             L.xo_ref_constants.argtypes = [P, P]
             L.xo_refine_losses.argtypes = [P, i64, P] + [P] * 11 + [i64, dbl, i32, P]
             L.xo_refine_losses.restype = i32
+            L.xo_exp.argtypes = [P, P, i64]
+            L.xo_exp.restype = None
+            L.xo_one_minus_exp.argtypes = [P, P, i64]
+            L.xo_one_minus_exp.restype = None
+            L.xo_faddeeva.argtypes = [P, P, P, P, i64]
+            L.xo_faddeeva.restype = None
+            L.xo_gauss_field.argtypes = [dbl, dbl, P, P, P, P, i64]
+            L.xo_gauss_field.restype = None
             _lib = L
     return _lib
 
@@ -166,6 +175,36 @@ def closed_orbit(elements, ref, rad_mode: int = 0, dim: int = 6, guess=None) -> 
 
 def sin(x: float) -> float:
     return lib().xo_sin(float(x))
+
+
+def _vec(f, *arrays, outs=1):
+    a = [np.ascontiguousarray(x, dtype=np.float64) for x in arrays]
+    o = [np.empty_like(a[0]) for _ in range(outs)]
+    f(*[x.ctypes.data for x in a], *[x.ctypes.data for x in o], a[0].size)
+    return o[0] if outs == 1 else o
+
+
+def exp(x) -> np.ndarray:
+    """The beam-beam kick's e^x as the oracle evaluates it."""
+    return _vec(lib().xo_exp, x)
+
+
+def one_minus_exp(u) -> np.ndarray:
+    return _vec(lib().xo_one_minus_exp, u)
+
+
+def faddeeva(x, y):
+    """w(x + i y) for y >= 0 as (real, imaginary) arrays."""
+    return _vec(lib().xo_faddeeva, x, y, outs=2)
+
+
+def gauss_field(sx: float, sy: float, x, y):
+    """Field shape (f_x, f_y) of a unit bi-Gaussian line charge."""
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (x, y)]
+    fx, fy = np.empty_like(a[0]), np.empty_like(a[0])
+    lib().xo_gauss_field(float(sx), float(sy), a[0].ctypes.data, a[1].ctypes.data, fx.ctypes.data,
+                         fy.ctypes.data, a[0].size)
+    return fx, fy
 
 
 def inv_pz_m1(u) -> np.ndarray:

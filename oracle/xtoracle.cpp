@@ -51,7 +51,7 @@ struct Element {
 enum {
   T_MARKER = 0, T_DRIFT = 1, T_MULTIPOLE = 2, T_CAVITY = 3,
   T_DIPEDGE = 4, T_LINEARMAP = 5, T_APERTURE = 6, T_XYSHIFT = 7, T_SROTATION = 8,
-  T_APERTURE_RECT = 9, T_APERTURE_ELLIPSE = 10
+  T_APERTURE_RECT = 9, T_APERTURE_ELLIPSE = 10, T_BEAMBEAM4D = 11
 };
 struct Reference { double mass0, q0, p0c; };
 
@@ -90,6 +90,8 @@ static inline Dual FMA(const Dual& a, double b, const Dual& c) { return FMA(a, m
 static inline Dual FMA(const Dual& a, const Dual& b, double c) { return FMA(a, b, mkd(c)); }
 static inline Dual FMA(double a, const Dual& b, double c) { return FMA(mkd(a), b, mkd(c)); }
 static inline Dual FMA(const Dual& a, double b, double c) { return FMA(a, mkd(b), mkd(c)); }
+// a b + c with a, b constants (used only by value-only elements)
+static inline Dual FMA(double a, double b, const Dual& c) { Dual r = c; r.v = std::fma(a, b, c.v); return r; }
 static inline double SQRT(double a) { return std::sqrt(a); }
 static inline Dual SQRT(const Dual& a) { Dual r; r.v = std::sqrt(a.v); for (int i = 0; i < 6; i++) r.d[i] = a.d[i] / (2.0 * r.v); return r; }
 
@@ -253,6 +255,171 @@ static RefConst ref_const(const Reference& r) {
   c.kq = 5.0 * ALPHA_FS * r.q0 * r.q0 / (2.0 * std::sqrt(3.0));
   c.uc15 = 1.5 * HBAR_C;
   return c;
+}
+
+// ---------------------------------------------------------------------------
+// Special functions of the beam-beam kick (section "Beam-beam interactions").
+
+// 1/n! for n = 0..18 (n! is exact in double up to 18!).
+static const std::vector<double>& inv_fact() {
+  static std::vector<double> c = [] {
+    std::vector<double> v(19);
+    double f = 1.0;
+    for (int n = 0; n <= 18; n++) {
+      if (n > 0) f = f * (double)n;
+      v[n] = 1.0 / f;
+    }
+    return v;
+  }();
+  return c;
+}
+
+// e^x: Cody-Waite reduction x = k ln2 + r with ln 2 split into a head with
+// 20 significant bits (k * head exact) and a tail, e^r by its Taylor series
+// to r^13 on |r| <= ln2/2 (truncation below 1e-17 relative), times 2^k from
+// the exponent bits (in two steps below the normal range).
+static double exp_cw(double x) {
+  if (x != x) return x;
+  if (!(x > -745.2)) return 0.0;
+  if (x > 709.7) return INFINITY;
+  const double sh = 6755399441055744.0;  // 1.5 * 2^52: adding it rounds to an integer
+  const double t = std::fma(x, 1.4426950408889634, sh) - sh;
+  const int k = (int)t;
+  double r = std::fma(-t, 0x1.62e42p-1, x);
+  r = std::fma(-t, 0x1.fdf473de6af28p-22, r);
+  const std::vector<double>& c = inv_fact();
+  double p = c[13];
+  for (int n = 12; n >= 0; n--) p = std::fma(p, r, c[n]);
+  auto pow2 = [](int e) {
+    const uint64_t b = (uint64_t)(e + 1023) << 52;
+    double v;
+    std::memcpy(&v, &b, 8);
+    return v;
+  };
+  if (k >= -1022) return p * pow2(k);
+  return (p * pow2(k + 64)) * pow2(-64);
+}
+
+// 1 - e^(-u) for u >= 0 without cancellation: for u < 1/2 the series
+// u sum_n (-u)^n / (n+1)!, n = 0..17 (truncation below 1e-22), else 1 - e^(-u).
+static double one_minus_exp(double u) {
+  const std::vector<double>& c = inv_fact();
+  if (u < 0.5) {
+    double s = c[18];
+    for (int n = 16; n >= 0; n--) s = std::fma(s, -u, c[n + 1]);
+    return u * s;
+  }
+  return 1.0 - exp_cw(-u);
+}
+
+// Faddeeva function w(z) = e^(-z^2) erfc(-i z) for Im z >= 0 by Weideman's
+// rational expansion (J. A. C. Weideman, SIAM J. Numer. Anal. 31 (1994)
+// 1497): w = 2 p(Z) / (L - i z)^2 + (1/sqrt(pi)) / (L - i z), Z = (L + i z) /
+// (L - i z), p a polynomial of degree N - 1 = 39, L = (N / sqrt 2)^(1/2);
+// p's coefficients are the cosine transform of e^(-t^2)(L^2 + t^2) sampled at
+// t = L tan(theta/2), here by a plain DFT.
+struct Faddeeva {
+  double L;
+  double a[40];  // p(Z) = sum_n a[n] Z^n
+};
+static const Faddeeva& faddeeva_coefficients() {
+  static Faddeeva c = [] {
+    Faddeeva q;
+    const int N = 40, M = 2 * N, M2 = 2 * M;
+    const double L = std::sqrt((double)N / std::sqrt(2.0));
+    std::vector<double> f(M2), fs(M2);
+    f[0] = 0.0;
+    for (int j = 1; j < M2; j++) {
+      const int k = j - M;  // -M+1 .. M-1
+      const double theta = (double)k * PI / (double)M;
+      const double t = L * std::tan(theta / 2.0);
+      f[j] = std::exp(-t * t) * (L * L + t * t);
+    }
+    for (int j = 0; j < M2; j++) fs[j] = f[(j + M) % M2];
+    q.L = L;
+    for (int n = 0; n < N; n++) {
+      const int m = n + 1;
+      double acc = 0.0;
+      for (int j = 0; j < M2; j++) acc = acc + fs[j] * std::cos(2.0 * PI * (double)((j * m) % M2) / (double)M2);
+      q.a[n] = acc / (double)M2;
+    }
+    return q;
+  }();
+  return c;
+}
+
+static void faddeeva(double x, double y, double* wr, double* wi) {
+  const Faddeeva& c = faddeeva_coefficients();
+  const double L = c.L;
+  const double cr = L + y;                      // L - i z = (L + y) - i x
+  const double D = std::fma(cr, cr, x * x);
+  const double qr = cr / D, qi = x / D;         // q = 1 / (L - i z)
+  const double ar = L - y;                      // L + i z = (L - y) + i x
+  const double Zr = std::fma(ar, qr, -(x * qi));
+  const double Zi = std::fma(ar, qi, x * qr);
+  double pr = c.a[39], pi = 0.0;
+  for (int n = 38; n >= 0; n--) {
+    const double nr = std::fma(pr, Zr, std::fma(-pi, Zi, c.a[n]));
+    const double ni = std::fma(pr, Zi, pi * Zr);
+    pr = nr;
+    pi = ni;
+  }
+  const double tr = std::fma(pr, qr, -(pi * qi));  // t = p q
+  const double ti = std::fma(pr, qi, pi * qr);
+  const double ur = std::fma(2.0, tr, 0.5641895835477563);  // u = 2 p q + 1/sqrt(pi)
+  const double ui = 2.0 * ti;
+  *wr = std::fma(qr, ur, -(qi * ui));  // w = q u
+  *wi = std::fma(qr, ui, qi * ur);
+}
+
+// Constants of a 4D beam-beam lens (table: p[0] = charge times number of
+// particles of the strong bunch [e], p[1] = its speed beta_s (moving against
+// the tracked beam), p[2], p[3] = sigma_x, sigma_y [m], p[4], p[5] = its
+// centre [m]).
+struct BBConst {
+  double K, xc, yc;
+  int mode;        // 0 round, 1 sigma_x > sigma_y, 2 sigma_y > sigma_x
+  double h1, h2;   // 1/(2 sigma_1^2), 1/(2 sigma_2^2) (round: h1 = 1/(2 sigma^2))
+  double rs, rsi;  // sigma_2/sigma_1, sigma_1/sigma_2
+  double invS, cpre;  // 1/S, sqrt(pi)/S, S = sqrt(2 (sigma_1^2 - sigma_2^2))
+  double lin1, lin2;  // 1/(sigma_1 (sigma_1 + sigma_2)), 1/(sigma_2 (sigma_1 + sigma_2))
+};
+
+// Field of a unit bi-Gaussian line charge, f = E 2 pi eps0 / lambda, at (x, y)
+// about its centre: Bassetti-Erskine with w(z) in the first quadrant and the
+// signs restored from symmetry; round beam: (x, y)(1 - e^(-r^2/2 sigma^2))/r^2.
+// Within rho^2 = (x/sigma_x)^2 + (y/sigma_y)^2 < 1e-10 of the centre the
+// difference of the two w values cancels, and the linear field
+// (x / (sigma_x (sigma_x + sigma_y)), y / (sigma_y (sigma_x + sigma_y))),
+// whose relative error there is of order rho^2, is used instead.
+static void gauss_field(double x, double y, const BBConst& b, double* fx, double* fy) {
+  const double ax = std::fabs(x), ay = std::fabs(y);
+  double gx, gy;
+  if (b.mode == 0) {
+    const double r2 = std::fma(ax, ax, ay * ay);
+    const double g = (r2 == 0.0) ? b.h1 : one_minus_exp(r2 * b.h1) / r2;
+    gx = ax * g;
+    gy = ay * g;
+  } else {
+    const double u = (b.mode == 1) ? ax : ay, v = (b.mode == 1) ? ay : ax;  // u along the larger sigma
+    const double h = std::fma(u, u * b.h1, v * (v * b.h2));                // rho^2 / 2
+    double fu, fv;
+    if (h < 5e-11) {
+      fu = u * b.lin1;
+      fv = v * b.lin2;
+    } else {
+      double w1r, w1i, w2r, w2i;
+      faddeeva(u * b.invS, v * b.invS, &w1r, &w1i);
+      faddeeva((u * b.rs) * b.invS, (v * b.rsi) * b.invS, &w2r, &w2i);
+      const double e = exp_cw(-h);
+      fu = b.cpre * std::fma(-e, w2i, w1i);  // Im of (sqrt(pi)/S)(w1 - e w2)
+      fv = b.cpre * std::fma(-e, w2r, w1r);  // Re
+    }
+    gx = (b.mode == 1) ? fu : fv;
+    gy = (b.mode == 1) ? fv : fu;
+  }
+  *fx = std::copysign(gx, x);
+  *fy = std::copysign(gy, y);
 }
 
 template <class T> static inline T mkv(double v);
@@ -479,6 +646,7 @@ struct Prep {
   double cs, sn;                         // reference-frame rotation about s
   double xmin, xmax, ymin, ymax;         // rectangular aperture
   double ia2, ib2;                       // elliptic aperture: 1/a^2, 1/b^2
+  BBConst bb;                            // 4D beam-beam lens
 };
 
 static Prep prepare(const Element& e, const RefConst& rc) {
@@ -538,6 +706,34 @@ static Prep prepare(const Element& e, const RefConst& rc) {
     case T_SROTATION: q.cs = std::cos(e.p[0]); q.sn = std::sin(e.p[0]); break;
     case T_APERTURE_RECT: q.xmin = e.p[0]; q.xmax = e.p[1]; q.ymin = e.p[2]; q.ymax = e.p[3]; break;
     case T_APERTURE_ELLIPSE: q.ia2 = 1.0 / (e.p[0] * e.p[0]); q.ib2 = 1.0 / (e.p[1] * e.p[1]); break;
+    case T_BEAMBEAM4D: {
+      // kick of a counter-moving Gaussian bunch integrated over the crossing:
+      // Delta p_perp / P0 = 2 q0 q_s N_s (r_e m_e c^2 / p0 c) (1 + beta0 beta_s) /
+      // (beta0 + beta_s) f(x - x_c, y - y_c)
+      const double qN = e.p[0], bs = e.p[1], sx2 = e.p[2] * e.p[2], sy2 = e.p[3] * e.p[3];
+      BBConst& b = q.bb;
+      b.K = 2.0 * rc.q0 * qN * (R_ELECTRON * M_ELECTRON) / rc.p0c * ((1.0 + rc.beta0 * bs) / (rc.beta0 + bs));
+      b.xc = e.p[4];
+      b.yc = e.p[5];
+      if (std::fabs(sx2 - sy2) <= 1e-10 * (sx2 + sy2)) {
+        b.mode = 0;
+        b.h1 = 1.0 / (sx2 + sy2);
+      } else {
+        const bool flat = sx2 > sy2;
+        const double s1 = flat ? e.p[2] : e.p[3], s2 = flat ? e.p[3] : e.p[2];
+        b.mode = flat ? 1 : 2;
+        const double S = std::sqrt(2.0 * (s1 * s1 - s2 * s2));
+        b.h1 = 1.0 / (2.0 * (s1 * s1));
+        b.h2 = 1.0 / (2.0 * (s2 * s2));
+        b.rs = s2 / s1;
+        b.rsi = s1 / s2;
+        b.invS = 1.0 / S;
+        b.cpre = 1.772453850905516 / S;
+        b.lin1 = 1.0 / (s1 * (s1 + s2));
+        b.lin2 = 1.0 / (s2 * (s1 + s2));
+      }
+      break;
+    }
     default: break;
   }
   return q;
@@ -597,6 +793,16 @@ static inline void track_element(Part<T>& p, const Prep& q, int rad_mode, const 
       p.y = FMA(q.cs, y, -(q.sn * x));
       p.px = FMA(q.cs, px, q.sn * py);
       p.py = FMA(q.cs, py, -(q.sn * px));
+      break;
+    }
+    // 4D weak-strong beam-beam (section "Beam-beam interactions"): transverse
+    // kick of a frozen Gaussian bunch, independent of the longitudinal
+    // coordinates.  Values only (the Jacobian entry points reject this type).
+    case T_BEAMBEAM4D: {
+      double fx, fy;
+      gauss_field(val(p.x) - q.bb.xc, val(p.y) - q.bb.yc, q.bb, &fx, &fy);
+      p.px = FMA(q.bb.K, fx, p.px);
+      p.py = FMA(q.bb.K, fy, p.py);
       break;
     }
     // Rectangular aperture: lost unless xmin <= x <= xmax and ymin <= y <= ymax
@@ -717,6 +923,13 @@ static bool inverse_row(Part<double>& p, const Prep& q, const RefConst& rc) {
       p.py = std::fma(-q.r43, p.y, p.py);
       return true;
     case T_LINEARMAP: return false;
+    case T_BEAMBEAM4D: {  // x, y unchanged by the kick: take the same kick back
+      double fx, fy;
+      gauss_field(p.x - q.bb.xc, p.y - q.bb.yc, q.bb, &fx, &fy);
+      p.px = std::fma(-q.bb.K, fx, p.px);
+      p.py = std::fma(-q.bb.K, fy, p.py);
+      return true;
+    }
     case T_XYSHIFT:
       p.x = p.x + q.dx;
       p.y = p.y + q.dy;
@@ -754,7 +967,7 @@ int xo_track(const Element* el, int64_t n_el, const Reference* ref, int rad_mode
   const RefConst rc = ref_const(*ref);
   std::vector<Prep> prep(n_el);
   for (int64_t e = 0; e < n_el; e++) {
-    if (el[e].type < 0 || el[e].type > T_APERTURE_ELLIPSE) return -1;
+    if (el[e].type < 0 || el[e].type > T_BEAMBEAM4D) return -1;
     if (el[e].type == T_MULTIPOLE && (el[e].order < 0 || el[e].order > 10)) return -1;
     prep[e] = prepare(el[e], rc);
   }
@@ -800,7 +1013,7 @@ int xo_refine_losses(const Element* el, int64_t n_el, const Reference* ref, cons
   Frame f = {0.0, 0.0, 0.0};
   int64_t n_ap = 0;
   for (int64_t e = 0; e < n_el; e++) {
-    if (el[e].type < 0 || el[e].type > T_APERTURE_ELLIPSE) return -1;
+    if (el[e].type < 0 || el[e].type > T_BEAMBEAM4D) return -1;
     if (el[e].type == T_MULTIPOLE && (el[e].order < 0 || el[e].order > 10)) return -1;
     prep[e] = prepare(el[e], rc);
     fr[e] = f;
@@ -904,6 +1117,8 @@ int xo_track_jacobian(const Element* el, int64_t n_el, const Reference* ref, int
                       const double* z0, int64_t n_turns, double* z_out, double* M_out,
                       double* along) {
   if (!el || !ref || n_el <= 0 || rad_mode < 0 || rad_mode > 1) return -1;
+  for (int64_t e = 0; e < n_el; e++)
+    if (el[e].type == T_BEAMBEAM4D) return -1;  // value-only element
   const RefConst rc = ref_const(*ref);
   std::vector<Prep> prep(n_el);
   for (int64_t e = 0; e < n_el; e++) prep[e] = prepare(el[e], rc);
@@ -975,6 +1190,27 @@ int xo_closed_orbit(const Element* el, int64_t n_el, const Reference* ref, int r
 
 // Test hooks for the building blocks.
 double xo_sin(double x) { return sin_cw(x); }
+
+// The special functions of the beam-beam kick, element-wise (for their pins).
+void xo_exp(const double* x, double* out, int64_t n) {
+  for (int64_t i = 0; i < n; i++) out[i] = exp_cw(x[i]);
+}
+void xo_one_minus_exp(const double* u, double* out, int64_t n) {
+  for (int64_t i = 0; i < n; i++) out[i] = one_minus_exp(u[i]);
+}
+void xo_faddeeva(const double* x, const double* y, double* wr, double* wi, int64_t n) {
+  for (int64_t i = 0; i < n; i++) faddeeva(x[i], y[i], &wr[i], &wi[i]);
+}
+// Field shape of a unit bi-Gaussian line charge (sigma_x, sigma_y) at (x, y).
+void xo_gauss_field(double sx, double sy, const double* x, const double* y, double* fx, double* fy, int64_t n) {
+  Element e;
+  std::memset(&e, 0, sizeof(e));
+  e.type = T_BEAMBEAM4D;
+  e.p[0] = 1.0; e.p[1] = 1.0; e.p[2] = sx; e.p[3] = sy;
+  const Reference r = {938.27208816e6, 1.0, 450e9};
+  const Prep q = prepare(e, ref_const(r));
+  for (int64_t i = 0; i < n; i++) gauss_field(x[i], y[i], q.bb, &fx[i], &fy[i]);
+}
 
 // The drift's (1+u)^(-1/2) - 1, element-wise (for its pins).
 void xo_inv_pz_m1(const double* u, double* out, int64_t n) {

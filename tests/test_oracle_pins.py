@@ -636,6 +636,118 @@ def test_refine_rect_to_ellipse_transition_bruteforce():
         assert first - 0.001 - 1e-9 <= s[i] <= first + ds + 1e-9, (i, s[i], first)
 
 
+# --------------------------------------------------------------------------
+# 4D beam-beam kick: special functions and field
+
+def _ulps(a, b):
+    return np.abs(a - b) / np.spacing(np.abs(b))
+
+
+def test_exp_vs_40_digits():
+    rng = np.random.default_rng(51)
+    x = np.concatenate([rng.uniform(-745.0, 709.0, 300), rng.uniform(-1, 1, 200), rng.uniform(-745.1, -708.0, 50),
+                        [0.0, -0.0, 1e-300, -1e-300, 709.0, -708.3]])
+    got = oracle.exp(x)
+    mpmath.mp.dps = 40
+    ref = np.array([float(mpmath.exp(mpmath.mpf(float(v)))) for v in x])
+    normal = ref > 2.3e-308
+    assert np.max(_ulps(got[normal], ref[normal])) <= 1.0
+    assert np.max(np.abs(got[~normal] - ref[~normal]) / 5e-324) <= 1.0
+    assert oracle.exp(np.array([-800.0]))[0] == 0.0 and np.isnan(oracle.exp(np.array([np.nan]))[0])
+
+
+def test_one_minus_exp_vs_40_digits():
+    rng = np.random.default_rng(52)
+    u = np.concatenate([10.0 ** rng.uniform(-300, 1.7, 400), [0.4999999, 0.5, 0.5000001]])
+    got = oracle.one_minus_exp(u)
+    mpmath.mp.dps = 40
+    ref = np.array([float(-mpmath.expm1(-mpmath.mpf(float(v)))) for v in u])
+    assert np.max(_ulps(got, ref)) <= 2.0
+
+
+def test_faddeeva_vs_scipy():
+    """w(z) in the first quadrant against scipy's independent wofz: within
+    5e-14 relative on a grid from 1e-6 to 1e5 and near the real axis."""
+    from scipy.special import wofz
+    v = np.concatenate([[0.0], np.logspace(-6, 5, 70), np.linspace(0.1, 9.9, 50)])
+    X, Y = np.meshgrid(v, v)
+    wr, wi = oracle.faddeeva(X.ravel(), Y.ravel())
+    ref = wofz(X.ravel() + 1j * Y.ravel())
+    err = np.abs(wr + 1j * wi - ref) / np.abs(ref)
+    assert err.max() < 5e-14, (err.max(), (X.ravel() + 1j * Y.ravel())[np.argmax(err)])
+
+
+@pytest.mark.parametrize("sx,sy", [(2e-3, 1e-3), (0.4e-3, 1.2e-3), (1.0005e-3, 1e-3), (0.7e-3, 0.7e-3)])
+def test_gauss_field_vs_integral(sx, sy):
+    """Field of a unit bi-Gaussian line charge against its single-integral
+    form f_x = x int_0^inf exp(-x^2/(2sx^2+q) - y^2/(2sy^2+q)) /
+    ((2sx^2+q)^(3/2) (2sy^2+q)^(1/2)) dq (and f_y with the roles swapped),
+    integrated by mpmath at points near the centre, at a few sigma and far."""
+    rng = np.random.default_rng(53)
+    pts = np.concatenate([rng.normal(0, 1, (20, 2)) * [sx, sy], rng.normal(0, 4, (20, 2)) * [sx, sy],
+                          [[30 * sx, 5 * sy], [-2e-9, 1e-9], [sx, 0.0], [0.0, -sy]]])
+    fx, fy = oracle.gauss_field(sx, sy, pts[:, 0], pts[:, 1])
+    mpmath.mp.dps = 25
+    ax, ay = mpmath.mpf(2 * sx * sx), mpmath.mpf(2 * sy * sy)
+    m = min(ax, ay)
+    cuts = [0, m / 1000, m / 10, m, 10 * m, 1000 * m, 1e6 * m, mpmath.inf]
+    for (x, y), gx, gy in zip(pts, fx, fy):
+        X, Y = mpmath.mpf(float(x)), mpmath.mpf(float(y))
+        e = lambda q: mpmath.exp(-X * X / (ax + q) - Y * Y / (ay + q))
+        ix = float(mpmath.quad(lambda q: e(q) / ((ax + q) ** 1.5 * (ay + q) ** 0.5), cuts))
+        iy = float(mpmath.quad(lambda q: e(q) / ((ax + q) ** 0.5 * (ay + q) ** 1.5), cuts))
+        scale = math.hypot(x * ix, y * iy) + 1e-300
+        assert abs(gx - x * ix) <= 1e-10 * scale and abs(gy - y * iy) <= 1e-10 * scale, (x, y, gx, x * ix)
+
+
+def test_gauss_field_round_limits():
+    """Round beam: f = (x, y)/(2 sigma^2) near the centre and (x, y)/r^2 far
+    away (all the charge enclosed)."""
+    s = 1e-3
+    x, y = np.array([1e-9, -3e-10, 40 * s]), np.array([2e-9, 1e-10, 30 * s])
+    fx, fy = oracle.gauss_field(s, s, x, y)
+    assert fx[0] == pytest.approx(x[0] / (2 * s * s), rel=1e-12) and fy[1] == pytest.approx(y[1] / (2 * s * s), rel=1e-12)
+    r2 = x[2] ** 2 + y[2] ** 2
+    assert fx[2] == pytest.approx(x[2] / r2, rel=1e-15) and fy[2] == pytest.approx(y[2] / r2, rel=1e-15)
+
+
+def test_beambeam_linear_tune_shift():
+    """A ring (linear map: tune 0.31, beta* = 0.55 m) with a head-on round
+    proton bunch at the IP: the small-amplitude tune, from central differences
+    of oracle tracking, obeys the thin-lens relation
+    cos 2 pi Q = cos 2 pi Q0 + (beta k / 2) sin 2 pi Q0 with the textbook
+    defocusing strength k = N r_p / (gamma sigma^2) (like charges, beta = 1,
+    so to within 1/(2 gamma^2)): -Delta Q is the beam-beam parameter
+    N r_p beta / (4 pi gamma sigma^2)."""
+    ref = PROTON
+    m0, _, p0c = ref
+    gamma = math.sqrt(p0c ** 2 + m0 ** 2) / m0
+    N, sig, beta, Q0 = 1.15e11, 50e-6, 0.55, 0.31
+    mu = 2 * math.pi * Q0
+    M = np.eye(6)
+    for k in (0, 2):
+        M[k, k], M[k, k + 1], M[k + 1, k], M[k + 1, k + 1] = math.cos(mu), beta * math.sin(mu), -math.sin(mu) / beta, math.cos(mu)
+    bb = I.table([I.linear_map(M)])[0].copy()
+    bb["type"] = oracle.BEAMBEAM4D
+    bb["p"][:6] = [N, 1.0, sig, sig, 0.0, 0.0]
+    el = I.table([I.linear_map(M), bb])
+    eps = 1e-9
+    xs = np.array([eps, -eps])
+    o = oracle.track(el, ref, I.make_particles(ref, xs, np.zeros(2), np.zeros(2), np.zeros(2), np.zeros(2), np.zeros(2)), 1)
+    o2 = oracle.track(el, ref, I.make_particles(ref, np.zeros(2), xs * 1e-2, np.zeros(2), np.zeros(2), np.zeros(2), np.zeros(2)), 1)
+    R = np.array([[(o["x"][0] - o["x"][1]) / (2 * eps), (o2["x"][0] - o2["x"][1]) / (2e-2 * eps)],
+                  [(o["px"][0] - o["px"][1]) / (2 * eps), (o2["px"][0] - o2["px"][1]) / (2e-2 * eps)]])
+    r_p = 2.8179403262e-15 * 0.51099895000e6 / m0
+    k = N * r_p / (gamma * sig * sig)
+    shift = beta * k / 2 * math.sin(mu)
+    # the textbook strength takes beta0 = 1: allow its relative error 1/(2 gamma^2)
+    beta0 = p0c / math.sqrt(p0c ** 2 + m0 ** 2)
+    assert abs(0.5 * np.trace(R) - (math.cos(mu) + shift)) <= 1.5 * (1 - beta0) * abs(shift) + 1e-10
+    xi = N * r_p * beta / (4 * math.pi * gamma * sig * sig)
+    dq = math.acos(0.5 * np.trace(R)) / (2 * math.pi) - Q0
+    assert dq == pytest.approx(-xi, rel=0.05) and 0.001 < xi < 0.01
+
+
 def test_segment_resume_bitwise():
     """track(a) then track(b) from turn a equals track(a+b), radiation included."""
     el, ref, _ = I.lepton_ring(n_cells=4, E0=5e9, v_total=30e6)
