@@ -95,6 +95,21 @@ extern "C" {
                            if x^2 (1/a^2) + y^2 (1/b^2) > 1 (1/a^2, 1/b^2 taken
                            once on the host), state -1 if x or y is not
                            finite.                                             */
+#define XT_BEAMBEAM4D 11 /* 4D weak-strong beam-beam lens (section "Beam-beam
+                           interactions"): p[0] = q_s N_s, the charge [e] times
+                           the number of particles of the strong bunch, p[1] =
+                           its speed beta_s (0 < beta_s <= 1, moving against
+                           the tracked beam), p[2], p[3] = sigma_x, sigma_y
+                           [m] (> 0), p[4], p[5] = its centre x_c, y_c [m].
+                           px += K f_x, py += K f_y with
+                           K = 2 q0 q_s N_s (r_e m_e c^2 / p0 c)
+                               (1 + beta0 beta_s) / (beta0 + beta_s)
+                           and f the field shape of a unit bi-Gaussian line
+                           charge at (x - x_c, y - y_c): Bassetti-Erskine with
+                           the Faddeeva function (round-beam closed form when
+                           sigma_x^2, sigma_y^2 agree to 1e-10; the linear
+                           field within (dx/sigma_x)^2 + (dy/sigma_y)^2 < 1e-10
+                           of the centre).  Independent of zeta and delta.   */
 
 #define XT_MAX_ORDER 10
 #define XT_NPARAM 48

@@ -279,6 +279,12 @@ int xt_tracker_create(const xt_element* table, int64_t n, const xt_reference* re
   if (e) return cuda_fail((cudaError_t)e, "device attribute");
   e = device_smem_optin(&t->smem_max);
   if (e) return cuda_fail((cudaError_t)e, "device attribute");
+  {
+    double tab[60];
+    special_table(tab);
+    e = upload_special_table(tab);
+    if (e) return cuda_fail((cudaError_t)e, "beam-beam constant table");
+  }
   rc = dev_alloc(&t->d_lat, t->lat.bytes.size());
   if (rc) return rc;
   if (!t->lat.bytes.empty())

@@ -135,6 +135,11 @@ struct RefineArgs {
 
 int launch_refine(const RefineArgs& a, void* stream);
 
+// Beam-beam constant table (60 doubles, see special_table) for the current
+// device's constant memory.
+void special_table(double* out);
+int upload_special_table(const double* tab);
+
 // Batched-seed variant: per-seed lattice and particle pointers in device arrays.
 struct SeedDev {
   const uint8_t* lat;

@@ -3,6 +3,7 @@
 // sequence, so the kernel's results are reproducible bit for bit.
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "xt_internal.h"
 
@@ -52,6 +53,11 @@ int64_t flops_of_row(const xt_element& e, int rad_mode) {
     case XT_SROTATION: return 12;
     case XT_APERTURE_RECT: return 0;
     case XT_APERTURE_ELLIPSE: return 5;
+    case XT_BEAMBEAM4D: {
+      // round: the field and the kick; else two 40-term w(z) (~300 each), e^x and the rest
+      const double sx2 = e.p[2] * e.p[2], sy2 = e.p[3] * e.p[3];
+      return (std::fabs(sx2 - sy2) <= 1e-10 * (sx2 + sy2)) ? 20 : 650;
+    }
     default: return 0;
   }
 }
@@ -142,6 +148,38 @@ int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice*
         }
         prm = {e.p[0], e.p[1], e.p[2], e.p[3]};
         break;
+      case XT_BEAMBEAM4D: {
+        const double qN = e.p[0], bs = e.p[1], sx = e.p[2], sy = e.p[3];
+        if (!(sx > 0.0 && sy > 0.0 && bs > 0.0 && bs <= 1.0)) {
+          *err = "element " + std::to_string(i) + ": beam-beam lens needs sigma_x, sigma_y > 0 and 0 < beta_s <= 1";
+          return XT_ERR_INVALID;
+        }
+        const double sx2 = sx * sx, sy2 = sy * sy;
+        // kick of a counter-moving Gaussian bunch integrated over the crossing
+        const double K = 2.0 * rc.q0 * qN * (RE_M * ME_EV) / rc.p0c * ((1.0 + rc.beta0 * bs) / (rc.beta0 + bs));
+        prm.assign(12, 0.0);
+        prm[0] = K;
+        prm[1] = e.p[4];
+        prm[2] = e.p[5];
+        if (std::fabs(sx2 - sy2) <= 1e-10 * (sx2 + sy2)) {
+          prm[3] = 0.0;  // round
+          prm[4] = 1.0 / (sx2 + sy2);
+        } else {
+          const bool flat = sx2 > sy2;
+          const double s1 = flat ? sx : sy, s2 = flat ? sy : sx;
+          const double S = std::sqrt(2.0 * (s1 * s1 - s2 * s2));
+          prm[3] = flat ? 1.0 : 2.0;
+          prm[4] = 1.0 / (2.0 * (s1 * s1));
+          prm[5] = 1.0 / (2.0 * (s2 * s2));
+          prm[6] = s2 / s1;
+          prm[7] = s1 / s2;
+          prm[8] = 1.0 / S;
+          prm[9] = 1.772453850905516 / S;
+          prm[10] = 1.0 / (s1 * (s1 + s2));
+          prm[11] = 1.0 / (s2 * (s1 + s2));
+        }
+        break;
+      }
       case XT_APERTURE_ELLIPSE:
         if (!(e.p[0] > 0.0 && e.p[1] > 0.0)) {
           *err = "element " + std::to_string(i) + ": elliptic aperture needs a > 0 and b > 0";
@@ -205,6 +243,37 @@ SinTab sin_table() {
   t.s[0] = 1.0;
   t.c[0] = 1.0;
   return t;
+}
+
+// Constant table of the beam-beam kick: [0] L, [1..40] the coefficients of
+// p(Z) in Weideman's rational expansion of the Faddeeva function
+// (J. A. C. Weideman, SIAM J. Numer. Anal. 31 (1994) 1497; N = 40 terms,
+// L = (N / sqrt 2)^(1/2), the cosine transform of e^(-t^2)(L^2 + t^2) at
+// t = L tan(theta/2) by a plain DFT), [41..59] 1/n! for n = 0..18.
+void special_table(double* out) {
+  const int N = 40, M = 2 * N, M2 = 2 * M;
+  const double L = std::sqrt((double)N / std::sqrt(2.0));
+  std::vector<double> f(M2), fs(M2);
+  f[0] = 0.0;
+  for (int j = 1; j < M2; j++) {
+    const int k = j - M;
+    const double theta = (double)k * PI_D / (double)M;
+    const double t = L * std::tan(theta / 2.0);
+    f[j] = std::exp(-t * t) * (L * L + t * t);
+  }
+  for (int j = 0; j < M2; j++) fs[j] = f[(j + M) % M2];
+  out[0] = L;
+  for (int n = 0; n < N; n++) {
+    const int m = n + 1;
+    double acc = 0.0;
+    for (int j = 0; j < M2; j++) acc = acc + fs[j] * std::cos(2.0 * PI_D * (double)((j * m) % M2) / (double)M2);
+    out[1 + n] = acc / (double)M2;
+  }
+  double fact = 1.0;
+  for (int n = 0; n <= 18; n++) {
+    if (n > 0) fact = fact * (double)n;
+    out[41 + n] = 1.0 / fact;
+  }
 }
 
 // Photon-number spectrum of synchrotron radiation in xi = u/u_c:

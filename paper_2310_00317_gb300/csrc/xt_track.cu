@@ -325,6 +325,100 @@ __device__ __forceinline__ int drift_warp(Part& p, const double* prm, bool alive
   return (alive && !valid) ? -2 : 1;
 }
 
+// ---------------------------------------------------------------------------
+// 4D beam-beam lens (section "Beam-beam interactions"): the transverse kick of
+// a frozen Gaussian bunch.  Constant table from the host: [0] L, [1..40]
+// Weideman's coefficients of the Faddeeva expansion, [41..59] 1/n!.
+__constant__ double c_special[60];
+
+// e^x: Cody-Waite reduction x = k ln2 + r (ln 2 as a 20-bit head, so that
+// k * head is exact, plus a tail), e^r by its Taylor series to r^13 on
+// |r| <= ln2/2, times 2^k from the exponent bits (two steps below the
+// normal range).
+__device__ __forceinline__ double exp_cw(double x) {
+  if (x != x) return x;
+  if (!(x > -745.2)) return 0.0;
+  if (x > 709.7) return __longlong_as_double(0x7FF0000000000000ll);
+  const double sh = 6755399441055744.0;  // 1.5 * 2^52: adding it rounds to an integer
+  const double t = fma(x, 1.4426950408889634, sh) - sh;
+  const int k = (int)t;
+  double r = fma(-t, 0x1.62e42p-1, x);
+  r = fma(-t, 0x1.fdf473de6af28p-22, r);
+  double p = c_special[41 + 13];
+  for (int n = 12; n >= 0; n--) p = fma(p, r, c_special[41 + n]);
+  if (k >= -1022) return p * __longlong_as_double((long long)(k + 1023) << 52);
+  return (p * __longlong_as_double((long long)(k + 64 + 1023) << 52)) * __longlong_as_double((long long)(1023 - 64) << 52);
+}
+
+// 1 - e^(-u), u >= 0: the series u sum_n (-u)^n/(n+1)! below u = 1/2.
+__device__ __forceinline__ double one_minus_exp(double u) {
+  if (u < 0.5) {
+    double s = c_special[41 + 18];
+    for (int n = 16; n >= 0; n--) s = fma(s, -u, c_special[41 + n + 1]);
+    return u * s;
+  }
+  return 1.0 - exp_cw(-u);
+}
+
+// w(x + i y), y >= 0: 2 p(Z) q^2 + q / sqrt(pi), q = 1/(L - i z),
+// Z = (L + i z) q.
+__device__ __forceinline__ void faddeeva(double x, double y, double* wr, double* wi) {
+  const double L = c_special[0];
+  const double cr = L + y;
+  const double D = fma(cr, cr, x * x);
+  const double qr = cr / D, qi = x / D;
+  const double ar = L - y;
+  const double Zr = fma(ar, qr, -(x * qi));
+  const double Zi = fma(ar, qi, x * qr);
+  double pr = c_special[1 + 39], pi = 0.0;
+  for (int n = 38; n >= 0; n--) {
+    const double nr = fma(pr, Zr, fma(-pi, Zi, c_special[1 + n]));
+    const double ni = fma(pr, Zi, pi * Zr);
+    pr = nr;
+    pi = ni;
+  }
+  const double tr = fma(pr, qr, -(pi * qi));
+  const double ti = fma(pr, qi, pi * qr);
+  const double ur = fma(2.0, tr, 0.5641895835477563);
+  const double ui = 2.0 * ti;
+  *wr = fma(qr, ur, -(qi * ui));
+  *wi = fma(qr, ui, qi * ur);
+}
+
+// Field shape of the unit bi-Gaussian line charge of record prm (K, x_c, y_c,
+// mode, h1, h2, rs, rsi, 1/S, sqrt(pi)/S, lin1, lin2) at (x, y) about its
+// centre.
+__device__ __forceinline__ void bb_field(double x, double y, const double* prm, double* fx, double* fy) {
+  const double ax = fabs(x), ay = fabs(y);
+  const int mode = (int)prm[3];
+  double gx, gy;
+  if (mode == 0) {
+    const double r2 = fma(ax, ax, ay * ay);
+    const double g = (r2 == 0.0) ? prm[4] : one_minus_exp(r2 * prm[4]) / r2;
+    gx = ax * g;
+    gy = ay * g;
+  } else {
+    const double u = (mode == 1) ? ax : ay, v = (mode == 1) ? ay : ax;
+    const double h = fma(u, u * prm[4], v * (v * prm[5]));
+    double fu, fv;
+    if (h < 5e-11) {
+      fu = u * prm[10];
+      fv = v * prm[11];
+    } else {
+      double w1r, w1i, w2r, w2i;
+      faddeeva(u * prm[8], v * prm[8], &w1r, &w1i);
+      faddeeva((u * prm[6]) * prm[8], (v * prm[7]) * prm[8], &w2r, &w2i);
+      const double e = exp_cw(-h);
+      fu = prm[9] * fma(-e, w2i, w1i);
+      fv = prm[9] * fma(-e, w2r, w1r);
+    }
+    gx = (mode == 1) ? fu : fv;
+    gy = (mode == 1) ? fv : fu;
+  }
+  *fx = copysign(gx, x);
+  *fy = copysign(gy, y);
+}
+
 template <int RAD>
 __device__ __forceinline__ void multipole(Part& p, const double* prm, int order, int flags,
                                           const RefDev& r, const RadCtx& rc, int64_t pid, int turn,
@@ -421,6 +515,13 @@ __device__ __forceinline__ int element(Part& p, uint32_t type, uint32_t order, u
     case XT_APERTURE: {
       const double rr = fma(p.x, p.x, p.y * p.y);
       if (dbits(rr) > dbits(prm[0])) return (is_finite(p.x) && is_finite(p.y)) ? 0 : -1;
+      return 1;
+    }
+    case XT_BEAMBEAM4D: {
+      double fx, fy;
+      bb_field(p.x - prm[1], p.y - prm[2], prm, &fx, &fy);
+      p.px = fma(prm[0], fx, p.px);
+      p.py = fma(prm[0], fy, p.py);
       return 1;
     }
     case XT_XYSHIFT:  // change of reference frame: displaced by (dx, dy)
@@ -641,7 +742,9 @@ __device__ __forceinline__ void set_status(int32_t* status, int err) {
 }
 
 template <int RAD>
-__global__ void __launch_bounds__(XT_MAX_BLOCK) track_kernel(const TrackArgs a) {
+// At least 3 blocks of XT_MAX_BLOCK per SM caps the registers at 80: the
+// rare beam-beam lens alone would otherwise raise the whole kernel's count.
+__global__ void __launch_bounds__(XT_MAX_BLOCK, 3) track_kernel(const TrackArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
   Stage st;
@@ -673,7 +776,7 @@ __global__ void __launch_bounds__(XT_MAX_BLOCK) track_kernel(const TrackArgs a) 
 }
 
 template <int RAD>
-__global__ void __launch_bounds__(XT_MAX_BLOCK) track_batched_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(XT_MAX_BLOCK, 3) track_batched_kernel(const BatchArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
   Stage st;
@@ -775,6 +878,13 @@ __device__ __forceinline__ bool inverse_record(Part& p, uint32_t type, uint32_t 
       p.py = fma(-prm[1], p.y, p.py);
       return true;
     case XT_LINEARMAP: return false;
+    case XT_BEAMBEAM4D: {  // x, y unchanged by the kick: take the same kick back
+      double fx, fy;
+      bb_field(p.x - prm[1], p.y - prm[2], prm, &fx, &fy);
+      p.px = fma(-prm[0], fx, p.px);
+      p.py = fma(-prm[0], fy, p.py);
+      return true;
+    }
     case XT_XYSHIFT:
       p.x = p.x + prm[0];
       p.y = p.y + prm[1];
@@ -1127,6 +1237,10 @@ int launch_refine(const RefineArgs& a, void* stream) {
   if (a.n <= 0) return 0;
   refine_kernel<<<(unsigned)((a.n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(a);
   return (int)cudaGetLastError();
+}
+
+int upload_special_table(const double* tab) {
+  return (int)cudaMemcpyToSymbol(c_special, tab, 60 * sizeof(double));
 }
 
 int launch_set_int(int32_t* dst, int32_t value, void* stream) {

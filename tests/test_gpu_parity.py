@@ -167,6 +167,35 @@ def test_refine_losses_bitwise():
     tr2.close()
 
 
+def bb_lens(qN, beta_s, sx, sy, xc=0.0, yc=0.0):
+    r = I.marker().copy()
+    r["type"] = oracle.BEAMBEAM4D
+    r["p"][:6] = [qN, beta_s, sx, sy, xc, yc]
+    return r
+
+
+def test_beambeam_lenses_bitwise():
+    """4D beam-beam lenses (round, flat and tall strong bunches, one off
+    centre) in a FODO ring with sextupoles: 1,500 particles spanning the
+    lenses' linear cores and tails, 300 turns, bit for bit (the Faddeeva
+    function and the exponential are the same evaluation on both sides)."""
+    rows = [I.cavity(2e6, 400e6, 180.0)]
+    lenses = [bb_lens(1.5e11, 1.0, 0.4e-3, 0.4e-3), bb_lens(1.5e11, 1.0, 0.8e-3, 0.25e-3, 5e-5, -2e-5),
+              bb_lens(-1.0e11, 0.9999, 0.3e-3, 0.9e-3, -1e-4, 3e-5)]
+    for c in range(6):
+        rows += I.misaligned([I.multipole(knl=[0.0, 0.2])], dx=1e-5 * c)
+        rows += [I.drift(2.0), I.multipole(knl=[0.0, 0.0, 0.03]), I.drift(2.0)]
+        rows += [I.multipole(knl=[0.0, -0.2]), I.drift(2.0)]
+        if c % 2 == 0:
+            rows += [lenses[c // 2]]
+        rows += [I.drift(2.0), I.aperture(0.01)]
+    el = I.table(rows)
+    p = random_particles(PROTON, 1500, 43, sx=8e-4, spx=5e-5, sd=2e-4)
+    g, o = gpu_track(el, PROTON, p, 300), oracle.track(el, PROTON, p, 300)
+    assert_same(g, o)
+    assert np.sum(o["state"] == 1) > 300
+
+
 def test_lhc_ring_sample_bitwise():
     """LHC-scale ring (20,000 elements, order-10 errors, RF, apertures):
     500 DA-grid particles at large amplitude (some are lost), 5 turns."""

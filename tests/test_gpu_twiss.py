@@ -80,3 +80,26 @@ def test_damping_decrements_of_the_lepton_ring():
     d = O.damping(el, ref)
     np.testing.assert_allclose(g["alpha"], d["alpha"], rtol=1e-5)
     assert np.max(np.abs(g["closed_orbit"] - d["closed_orbit"])) < 1e-10
+
+
+def test_beambeam_tune_shift_by_tracking():
+    """A linear ring with a head-on round proton lens at the IP: the tune
+    from Twiss by tracking on the GPU obeys the thin-lens relation
+    cos 2 pi Q = cos 2 pi Q0 + (beta k / 2) sin 2 pi Q0 with the lens's
+    linear strength k = K / (2 sigma^2), K = 2 N r_e m_e c^2 / p0 c."""
+    ref = I.proton_reference(450e9)
+    m0, _, p0c = ref
+    N, sig, beta, Q0 = 1.15e11, 50e-6, 0.55, 0.31
+    mu = 2 * math.pi * Q0
+    M = np.eye(6)
+    for k in (0, 2):
+        M[k, k], M[k, k + 1], M[k + 1, k], M[k + 1, k + 1] = math.cos(mu), beta * math.sin(mu), -math.sin(mu) / beta, math.cos(mu)
+    lens = I.marker().copy()
+    lens["type"] = oracle.BEAMBEAM4D
+    lens["p"][:6] = [N, 1.0, sig, sig, 0.0, 0.0]
+    el = I.table([I.linear_map(M), lens])
+    t = T.twiss(el, ref)
+    k = 2 * N * 2.8179403262e-15 * 0.51099895000e6 / p0c / (2 * sig * sig)
+    assert math.cos(2 * math.pi * t["qx"]) == pytest.approx(math.cos(mu) + beta * k / 2 * math.sin(mu), abs=1e-8)
+    assert math.cos(2 * math.pi * t["qy"]) == pytest.approx(math.cos(mu) + beta * k / 2 * math.sin(mu), abs=1e-8)
+    assert t["qx"] < Q0 - 0.004
