@@ -254,6 +254,40 @@ def measure_refinement(tr, host, ds=0.01, n_angles=128, reps=5):
             "workload": "particles lost at the 20 mm circular apertures of the LHC-scale ring in the headline run"}
 
 
+def measure_beambeam(n=1000000, n_lens=1000, turns=2):
+    """Throughput of the 4D beam-beam lens: a line of flat lenses (two w(z)
+    evaluations per pass), CUDA-event time, FP64 fraction from the library's
+    flop count per lens."""
+    import torch
+    from paper_2310_00317_gb300 import inputs as I
+    from paper_2310_00317_gb300 import xtgb
+    ref = I.proton_reference(450e9)
+    lens = I.marker().copy()
+    lens["type"] = 11  # XT_BEAMBEAM4D
+    lens["p"][:6] = [1.5e11, 1.0, 0.8e-3, 0.25e-3, 0.0, 0.0]
+    el = I.table([lens] * n_lens)
+    rng = np.random.default_rng(I.BASE_SEED + 11)
+    p = I.make_particles(ref, rng.normal(0, 1e-3, n), rng.normal(0, 1e-6, n), rng.normal(0, 0.4e-3, n),
+                         rng.normal(0, 1e-6, n), np.zeros(n), np.zeros(n))
+    tr = xtgb.Tracker(el, ref)
+    P = xtgb.Particles.from_numpy(p)
+    tr.track(P, 1)
+    tr.set_profiling(True)
+    tr.kernel_time()
+    tr.track(P, turns, 1)
+    ms, nl = tr.kernel_time()
+    per_pass = float(tr.element_flops().sum()) / n_lens
+    alive = int((P.t["state"] == 1).sum())
+    tr.close()
+    passes = alive * n_lens * turns
+    achieved = passes * per_pass / (ms * 1e-3)
+    return {"workload": "%d particles through %d flat 4D beam-beam lenses (sigma 0.8 x 0.25 mm), %d turns"
+                        % (n, n_lens, turns),
+            "value": passes / (ms * 1e-3), "unit": "particle*lens passes/s", "kernel_ms": ms,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": NOMINAL_FP64 / 1e12, "unit": "TFLOP/s",
+                         "frac": achieved / NOMINAL_FP64, "algorithmic_flops_per_pass": per_pass}}
+
+
 def measure_lepton(n=200000, turns=10):
     """Lepton ring (10,000 elements) with mean radiation + quantum excitation."""
     import torch
@@ -457,6 +491,7 @@ def run_ours(args):
     extras = {}
     if ws == 1 and not args.no_extras:
         extras["loss_refinement"] = measure_refinement(tr, H.a)
+        extras["beambeam_lens"] = measure_beambeam()
         extras["batched_seeds"] = measure_batched()
         extras["lepton_quantum"] = measure_lepton()
         extras["da_scan"] = measure_da_scan()
