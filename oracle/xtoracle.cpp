@@ -198,10 +198,11 @@ struct Uniforms {
 // and the cumulative distribution is F(xi) = 1 - S(xi)/(5 pi/3).  S is
 // evaluated by the trapezoidal rule in t (the integrand is even and analytic in
 // the strip |Im t| < pi/2, so the rule converges geometrically).
-static const int SPEC_K = 2048;
+static const int SPEC_K = 2048, SPEC_GUIDE = 4096;
 static const double SPEC_XI_MIN = 1e-7, SPEC_XI_MAX = 40.0;
 struct Spectrum {
   double xi[SPEC_K], F[SPEC_K];
+  int guide[SPEC_GUIDE];  // guide[j] = max{i : F[i] <= j / SPEC_GUIDE} (Chen and Asau, 1974)
   Spectrum() {
     const double norm = 5.0 * PI / 3.0, h = 0.05;
     for (int i = 0; i < SPEC_K; i++) {
@@ -218,14 +219,23 @@ struct Spectrum {
       xi[i] = x;
       F[i] = 1.0 - (h * s) / norm;
     }
+    int i = 0;
+    for (int j = 0; j < SPEC_GUIDE; j++) {
+      const double t = (double)j / (double)SPEC_GUIDE;
+      while (i + 1 < SPEC_K && F[i + 1] <= t) i++;
+      guide[j] = i;
+    }
   }
   // Inverse CDF: power-law asymptote F ~ xi^(1/3) below the first knot,
-  // linear interpolation between knots, clamp above the last.
+  // linear interpolation between knots lo and lo + 1 with
+  // lo = max{i : F[i] <= u} (walked up from the guide entry of u's cell),
+  // clamp above the last knot.
   double sample(double u) const {
     if (u < F[0]) { double q = u / F[0]; return xi[0] * q * q * q; }
     if (u >= F[SPEC_K - 1]) return xi[SPEC_K - 1];
-    int lo = 0, hi = SPEC_K - 1;  // F[lo] <= u < F[hi]
-    while (hi - lo > 1) { int mid = (lo + hi) / 2; if (F[mid] <= u) lo = mid; else hi = mid; }
+    int lo = guide[(int)(u * (double)SPEC_GUIDE)];
+    while (F[lo + 1] <= u) lo++;
+    const int hi = lo + 1;
     double w = (u - F[lo]) / (F[hi] - F[lo]);
     return xi[lo] + w * (xi[hi] - xi[lo]);
   }
@@ -553,7 +563,7 @@ static inline void quantum_kick(Part<double>& p, double br, double bi, const Mul
   Uniforms U(seed, (uint64_t)p.id, (uint64_t)turn, (uint64_t)elem);
   double u0 = U.next();
   int k = 0;
-  double pk = std::exp(-nbar), F = pk;
+  double pk = exp_cw(-nbar), F = pk;
   while (u0 > F && k < KMAX_PHOTONS) { k++; pk = (pk * nbar) / (double)k; F = F + pk; }
   if (k == 0) return;
   const Spectrum& S = spectrum();

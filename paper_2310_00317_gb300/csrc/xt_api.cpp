@@ -93,6 +93,7 @@ struct xt_tracker {
   int chunk_built = 0;  // chunk size the table was built for
   double* d_spec_xi = nullptr;
   double* d_spec_F = nullptr;
+  int32_t* d_spec_guide = nullptr;
   int spec_k = 0;
   int32_t* d_scal = nullptr;  // [0] status [1] n_alive [2] tile_counter [3] turn base
   int32_t* h_cancel = nullptr;
@@ -189,6 +190,7 @@ static void fill_args(const xt_tracker* t, const xt_particles* p, TrackArgs* a) 
   a->seed = t->opt.seed;
   a->spec_xi = t->d_spec_xi;
   a->spec_F = t->d_spec_F;
+  a->spec_guide = t->d_spec_guide;
   a->spec_k = t->spec_k;
   a->ref = t->ref;
   a->sn = t->sn;
@@ -290,14 +292,18 @@ int xt_tracker_create(const xt_element* table, int64_t n, const xt_reference* re
   if (!t->lat.bytes.empty())
     CK(cudaMemcpy(t->d_lat, t->lat.bytes.data(), t->lat.bytes.size(), cudaMemcpyHostToDevice));
   std::vector<double> xi, F;
-  photon_table(&xi, &F);
+  std::vector<int32_t> guide;
+  photon_table(&xi, &F, &guide);
   t->spec_k = (int)xi.size();
   rc = dev_alloc(&t->d_spec_xi, xi.size());
   if (rc) return rc;
   rc = dev_alloc(&t->d_spec_F, F.size());
   if (rc) return rc;
+  rc = dev_alloc(&t->d_spec_guide, guide.size());
+  if (rc) return rc;
   CK(cudaMemcpy(t->d_spec_xi, xi.data(), xi.size() * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(t->d_spec_F, F.data(), F.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(t->d_spec_guide, guide.data(), guide.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   rc = dev_alloc(&t->d_scal, 8);
   if (rc) return rc;
   CK(cudaMemset(t->d_scal, 0, 8 * sizeof(int32_t)));
@@ -317,6 +323,7 @@ void xt_tracker_destroy(xt_tracker* t) {
   cudaFree(t->d_chunks);
   cudaFree(t->d_spec_xi);
   cudaFree(t->d_spec_F);
+  cudaFree(t->d_spec_guide);
   cudaFree(t->d_scal);
   cudaFree(t->d_idx);
   cudaFree(t->d_counts);
@@ -853,6 +860,7 @@ int enqueue_batched(xt_tracker* t0, BatchPlan* pl, int64_t n_turns, int seg, int
   a.seed = t0->opt.seed;
   a.spec_xi = t0->d_spec_xi;
   a.spec_F = t0->d_spec_F;
+  a.spec_guide = t0->d_spec_guide;
   a.spec_k = t0->spec_k;
   a.ref = t0->ref;
   a.sn = t0->sn;

@@ -77,7 +77,8 @@ int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice*
 void build_chunks(const Lattice& lat, uint32_t chunk_bytes, std::vector<Chunk>* out);
 SinTab sin_table();
 // Photon spectrum inverse-CDF table: knots (xi_i, F_i), i = 0..K-1.
-void photon_table(std::vector<double>* xi, std::vector<double>* F);
+void photon_table(std::vector<double>* xi, std::vector<double>* F, std::vector<int32_t>* guide);
+constexpr int XT_SPEC_GUIDE = 4096;  // guide-table entries (uniform cells in the CDF)
 int64_t flops_of_row(const xt_element& e, int rad_mode);
 
 // ---------------------------------------------------------------------------
@@ -103,6 +104,7 @@ struct TrackArgs {
   uint64_t seed;
   const double* spec_xi;
   const double* spec_F;
+  const int32_t* spec_guide;
   int32_t spec_k;
   int32_t pad1;
   RefDev ref;
@@ -171,6 +173,7 @@ struct BatchArgs {
   uint64_t seed;
   const double* spec_xi;
   const double* spec_F;
+  const int32_t* spec_guide;
   int32_t spec_k;
   int32_t pad1;
   RefDev ref;

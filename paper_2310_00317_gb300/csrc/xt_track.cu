@@ -221,28 +221,31 @@ __device__ __forceinline__ double uni_next(Uni& u) {
   const uint64_t w = u.b[u.pos++];
   return (double)(w >> 11) * (1.0 / 9007199254740992.0);
 }
-__device__ __forceinline__ double sample_xi(double u, const double* xi, const double* F, int K) {
+// Inverse CDF of the photon spectrum: power-law asymptote F ~ xi^(1/3) below
+// the first knot, clamp above the last, else linear interpolation on the
+// knot interval [lo, lo+1] with lo = max{i : F[i] <= u}, found by walking up
+// from the guide table's entry for u's cell of width 1/XT_SPEC_GUIDE.
+__device__ __forceinline__ double sample_xi(double u, const double* xi, const double* F, const int32_t* guide,
+                                            int K) {
   const double F0 = __ldg(F);
   if (u < F0) {
     const double q = u / F0;
     return __ldg(xi) * q * q * q;
   }
   if (u >= __ldg(F + K - 1)) return __ldg(xi + K - 1);
-  int lo = 0, hi = K - 1;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (__ldg(F + mid) <= u) lo = mid; else hi = mid;
-  }
-  const double Fl = __ldg(F + lo), Fh = __ldg(F + hi);
+  int lo = __ldg(guide + (int)(u * (double)XT_SPEC_GUIDE));
+  while (__ldg(F + lo + 1) <= u) lo++;
+  const double Fl = __ldg(F + lo), Fh = __ldg(F + lo + 1);
   const double w = (u - Fl) / (Fh - Fl);
   const double xl = __ldg(xi + lo);
-  return xl + w * (__ldg(xi + hi) - xl);
+  return xl + w * (__ldg(xi + lo + 1) - xl);
 }
 
 struct RadCtx {
   uint64_t seed;
   const double* xi;
   const double* F;
+  const int32_t* guide;
   int K;
 };
 
@@ -487,7 +490,7 @@ __device__ __forceinline__ void multipole(Part& p, const double* prm, int order,
     u.key = rc.seed; u.pos = 4;
     const double u0 = uni_next(u);
     int k = 0;
-    double pk = exp(-nbar), F = pk;
+    double pk = exp_cw(-nbar), F = pk;
     while (u0 > F && k < 200) {
       k++;
       pk = (pk * nbar) / (double)k;
@@ -495,7 +498,7 @@ __device__ __forceinline__ void multipole(Part& p, const double* prm, int order,
     }
     if (k > 0) {
       double sxi = 0.0;
-      for (int j = 0; j < k; j++) sxi = sxi + sample_xi(uni_next(u), rc.xi, rc.F, rc.K);
+      for (int j = 0; j < k; j++) sxi = sxi + sample_xi(uni_next(u), rc.xi, rc.F, rc.guide, rc.K);
       const double uc = (r.uc15 * (gam * gam * gam)) * h;
       const double dpt = -(uc * sxi) / r.p0c;
       apply_energy_loss(p, dpt, r);
@@ -754,7 +757,7 @@ __global__ void __launch_bounds__(XT_MAX_BLOCK, 3) track_kernel(const TrackArgs 
   const TileLat L = {a.lat, a.chunks, a.n_chunks, a.n_el};
   const TileArrays A = {a.x, a.px, a.y, a.py, a.zeta, a.delta, a.ptau, a.rpp, a.rvv,
                         a.state, a.at_turn, a.at_element, a.pid};
-  const RadCtx rc = {a.seed, a.spec_xi, a.spec_F, a.spec_k};
+  const RadCtx rc = {a.seed, a.spec_xi, a.spec_F, a.spec_guide, a.spec_k};
   Ctl ctl = {a.status, a.cancel, a.max_cycles, clock64(), clock64()};
   int resident = -1;
   while (true) {
@@ -784,7 +787,7 @@ __global__ void __launch_bounds__(XT_MAX_BLOCK, 3) track_batched_kernel(const Ba
   if (*(volatile int32_t*)a.status != 0) return;
   const int64_t total_tiles = a.tile_prefix[a.n_seeds];
   const int turn0 = *a.turn_base + a.turn_off;
-  const RadCtx rc = {a.seed, a.spec_xi, a.spec_F, a.spec_k};
+  const RadCtx rc = {a.seed, a.spec_xi, a.spec_F, a.spec_guide, a.spec_k};
   Ctl ctl = {a.status, a.cancel, a.max_cycles, clock64(), clock64()};
   int resident = -1;
   while (true) {
@@ -953,7 +956,7 @@ __global__ void __launch_bounds__(128) refine_kernel(RefineArgs a) {
   double found = nan;
   bool hit = false;
   RadCtx rc;
-  rc.seed = 0; rc.xi = nullptr; rc.F = nullptr; rc.K = 0;
+  rc.seed = 0; rc.xi = nullptr; rc.F = nullptr; rc.guide = nullptr; rc.K = 0;
   for (int j = q;;) {
     j = (j + 1 == a.n_el) ? 0 : j + 1;
     if (j == e) break;
