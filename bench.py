@@ -537,6 +537,49 @@ def run_ours(args):
     return 0
 
 
+def run_mlp(args):
+    """Surrogate network alone (not part of the default run): CUDA-event time
+    of a forward pass over args.mlp_forward samples, or of args.mlp_train
+    training steps of batch 4096, on random inputs."""
+    import torch
+    from paper_2310_00317_gb300 import xtgb
+    net = xtgb.Surrogate(seed=7)
+    g = torch.Generator(device="cpu")
+    g.manual_seed(0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.mlp_forward:
+        X = torch.randn(args.mlp_forward, 16, generator=g).cuda()
+        net.forward(X)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            net.forward(X)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        flops = 2.0 * args.mlp_forward * (16 * 256 + 3 * 256 * 256 + 256 * 2)
+        out = {"mlp_forward_samples": args.mlp_forward, "ms": ms, "tflops": flops / (ms * 1e-3) / 1e12}
+    else:
+        B = 4096
+        X = torch.randn(B, 16, generator=g).cuda()
+        y = (torch.rand(B, generator=g) > 0.5).float().cuda()
+        t = torch.rand(B, generator=g).cuda()
+        m = (torch.rand(B, generator=g) > 0.5).float().cuda()
+        L = torch.zeros(1, device="cuda")
+        for _ in range(3):
+            net.train_step(X, y, t, m, 1e-3, 0.5, L)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.mlp_train):
+            net.train_step(X, y, t, m, 1e-3, 0.5, L)
+        e1.record()
+        torch.cuda.synchronize()
+        out = {"mlp_train_steps": args.mlp_train, "batch": B, "ms_per_step": e0.elapsed_time(e1) / args.mlp_train}
+    net.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -551,9 +594,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-seed, lepton-ring and DA-scan measurements")
+    ap.add_argument("--mlp-forward", type=int, default=0,
+                    help="time only the surrogate's forward pass over this many samples (--steps repeats)")
+    ap.add_argument("--mlp-train", type=int, default=0,
+                    help="time only this many surrogate training steps (batch 4096)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mlp_forward or args.mlp_train:
+        return run_mlp(args)
     return run_ours(args)
 
 
