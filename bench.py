@@ -262,9 +262,7 @@ def measure_beambeam(n=1000000, n_lens=1000, turns=2):
     from paper_2310_00317_gb300 import inputs as I
     from paper_2310_00317_gb300 import xtgb
     ref = I.proton_reference(450e9)
-    lens = I.marker().copy()
-    lens["type"] = 11  # XT_BEAMBEAM4D
-    lens["p"][:6] = [1.5e11, 1.0, 0.8e-3, 0.25e-3, 0.0, 0.0]
+    lens = I.beambeam4d(1.5e11, 1.0, 0.8e-3, 0.25e-3)
     el = I.table([lens] * n_lens)
     rng = np.random.default_rng(I.BASE_SEED + 11)
     p = I.make_particles(ref, rng.normal(0, 1e-3, n), rng.normal(0, 1e-6, n), rng.normal(0, 0.4e-3, n),

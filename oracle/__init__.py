@@ -31,6 +31,7 @@ ELEMENT_DTYPE = np.dtype([("type", "<i4"), ("order", "<i4"), ("p", "<f8", (48,))
 DRIFT, MULTIPOLE, CAVITY, DIPEDGE, LINEARMAP, APERTURE, MARKER = 1, 2, 3, 4, 5, 6, 0
 XYSHIFT, SROTATION, APERTURE_RECT, APERTURE_ELLIPSE = 7, 8, 9, 10
 BEAMBEAM4D = 11
+QUAD = 12
 
 FLOAT_FIELDS = ("x", "px", "y", "py", "zeta", "delta", "ptau", "rpp", "rvv")
 INT_FIELDS = ("state", "at_turn", "at_element")

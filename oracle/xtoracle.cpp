@@ -51,7 +51,7 @@ struct Element {
 enum {
   T_MARKER = 0, T_DRIFT = 1, T_MULTIPOLE = 2, T_CAVITY = 3,
   T_DIPEDGE = 4, T_LINEARMAP = 5, T_APERTURE = 6, T_XYSHIFT = 7, T_SROTATION = 8,
-  T_APERTURE_RECT = 9, T_APERTURE_ELLIPSE = 10, T_BEAMBEAM4D = 11
+  T_APERTURE_RECT = 9, T_APERTURE_ELLIPSE = 10, T_BEAMBEAM4D = 11, T_QUAD = 12
 };
 struct Reference { double mass0, q0, p0c; };
 
@@ -142,7 +142,34 @@ double sin_cw(double x) {
   }
   return (quad & 2) ? -res : res;
 }
+// cos x: the same reduction as sin_cw with the quadrant advanced by one.
+double cos_cw(double x) {
+  double k = (x * TWO_OVER_PI + RND_MAGIC) - RND_MAGIC;
+  double r = std::fma(-k, PIO2_1, x);
+  r = std::fma(-k, PIO2_2, r);
+  r = std::fma(-k, PIO2_3, r);
+  long long q = (long long)k;
+  int quad = (int)((q + 1) & 3);
+  double z = r * r;
+  double res;
+  if (quad & 1) {
+    double p = SC.c[10];
+    for (int i = 9; i >= 0; i--) p = std::fma(p, z, SC.c[i]);
+    res = p;
+  } else {
+    double p = SC.s[9];
+    for (int i = 8; i >= 1; i--) p = std::fma(p, z, SC.s[i]);
+    res = std::fma(r * z, p, r);
+  }
+  return (quad & 2) ? -res : res;
+}
 static inline double SIN(double a) { return sin_cw(a); }
+static inline double COS(double a) { return cos_cw(a); }
+static inline Dual COS(const Dual& a) {
+  Dual r; r.v = cos_cw(a.v); double sn = std::sin(a.v);
+  for (int i = 0; i < 6; i++) r.d[i] = -sn * a.d[i];
+  return r;
+}
 static inline Dual SIN(const Dual& a) {
   Dual r; r.v = sin_cw(a.v); double c = std::cos(a.v);
   for (int i = 0; i < 6; i++) r.d[i] = c * a.d[i];
@@ -320,6 +347,16 @@ static double one_minus_exp(double u) {
     return u * s;
   }
   return 1.0 - exp_cw(-u);
+}
+
+// cos a and sin(a)/a, cosh a and sinh(a)/a for a >= 0: series in a^2 below
+// a = 1/2 (to a^16 / 17!, truncation below 1e-19), else from sin_cw/cos_cw and
+// two exponentials.
+static inline double EXPC(double a) { return exp_cw(a); }
+static inline Dual EXPC(const Dual& a) {
+  Dual r; r.v = exp_cw(a.v);
+  for (int i = 0; i < 6; i++) r.d[i] = r.v * a.d[i];
+  return r;
 }
 
 // Faddeeva function w(z) = e^(-z^2) erfc(-i z) for Im z >= 0 by Weideman's
@@ -657,6 +694,7 @@ struct Prep {
   double xmin, xmax, ymin, ymax;         // rectangular aperture
   double ia2, ib2;                       // elliptic aperture: 1/a^2, 1/b^2
   BBConst bb;                            // 4D beam-beam lens
+  double k1, Lq;                         // thick quadrupole
 };
 
 static Prep prepare(const Element& e, const RefConst& rc) {
@@ -716,6 +754,7 @@ static Prep prepare(const Element& e, const RefConst& rc) {
     case T_SROTATION: q.cs = std::cos(e.p[0]); q.sn = std::sin(e.p[0]); break;
     case T_APERTURE_RECT: q.xmin = e.p[0]; q.xmax = e.p[1]; q.ymin = e.p[2]; q.ymax = e.p[3]; break;
     case T_APERTURE_ELLIPSE: q.ia2 = 1.0 / (e.p[0] * e.p[0]); q.ib2 = 1.0 / (e.p[1] * e.p[1]); break;
+    case T_QUAD: q.k1 = e.p[0]; q.Lq = e.p[1]; break;
     case T_BEAMBEAM4D: {
       // kick of a counter-moving Gaussian bunch integrated over the crossing:
       // Delta p_perp / P0 = 2 q0 q_s N_s (r_e m_e c^2 / p0 c) (1 + beta0 beta_s) /
@@ -805,6 +844,7 @@ static inline void track_element(Part<T>& p, const Prep& q, int rad_mode, const 
       p.py = FMA(q.cs, py, -(q.sn * px));
       break;
     }
+    case T_QUAD: thick_quad(p, q.k1, q.Lq); break;
     // 4D weak-strong beam-beam (section "Beam-beam interactions"): transverse
     // kick of a frozen Gaussian bunch, independent of the longitudinal
     // coordinates.  Values only (the Jacobian entry points reject this type).
@@ -847,6 +887,81 @@ static inline void turn_guard(Part<T>& p, int turn, int n_el) {
   if (!(std::fabs(val(p.x)) <= 1.0 && std::fabs(val(p.y)) <= 1.0)) mark_lost(p, -3, turn, n_el - 1);
 }
 
+
+// ---------------------------------------------------------------------------
+// Thick quadrupole: the exact flow over L of the expanded Hamiltonian
+// H = pzeta - (1+delta) + (px^2 + py^2) / (2 (1+delta)) + k1 (x^2 - y^2) / 2
+// (the paraxial form of the drift's square root plus the quadrupole field;
+// section "Lattice modelling and single particle tracking" names thick
+// quadrupoles).  Transverse motion is harmonic with w^2 = |k1| / (1+delta):
+// cos/sin in the focusing plane, cosh/sinh in the other; zeta gains
+// dzeta/ds = 1 - (1/rvv)(1 + (px^2 + py^2) / (2 (1+delta)^2)) integrated in
+// closed form.  Evaluated at a = w |L| with the sign of L carried through, so
+// that the same map with -L is its inverse.
+template <class T>
+static inline void trig_sa(const T& a, T* C, T* Sa) {
+  const std::vector<double>& c = inv_fact();
+  *C = COS(a);
+  if (val(a) < 0.5) {
+    const T z = a * a;
+    T p = mkv<T>(c[17]);
+    for (int n = 7; n >= 0; n--) p = FMA(p, -z, mkv<T>(c[2 * n + 1]));
+    *Sa = p;
+  } else {
+    *Sa = SIN(a) / a;
+  }
+}
+template <class T>
+static inline void hyp_sa(const T& a, T* Ch, T* Sha) {
+  const std::vector<double>& c = inv_fact();
+  if (val(a) < 0.5) {
+    const T z = a * a;
+    T p = mkv<T>(c[17]);
+    for (int n = 7; n >= 0; n--) p = FMA(p, z, mkv<T>(c[2 * n + 1]));
+    *Sha = p;
+    T q = mkv<T>(c[18]);
+    for (int n = 8; n >= 0; n--) q = FMA(q, z, mkv<T>(c[2 * n]));
+    *Ch = q;
+  } else {
+    const T e = EXPC(a), ei = EXPC(-a);
+    *Ch = 0.5 * (e + ei);
+    *Sha = (0.5 * (e - ei)) / a;
+  }
+}
+template <class T>
+static inline void thick_quad(Part<T>& p, double k1, double L) {
+  if (L == 0.0) return;
+  const T aK = (k1 >= 0.0) ? k1 * p.rpp : (-k1) * p.rpp;  // |k1| / (1+delta)
+  const T w = SQRT(aK);
+  const T a = w * std::fabs(L);
+  T C, Sa, Ch, Sha;
+  trig_sa(a, &C, &Sa);
+  hyp_sa(a, &Ch, &Sha);
+  T* u = (k1 >= 0.0) ? &p.x : &p.y;   // focusing plane
+  T* pu = (k1 >= 0.0) ? &p.px : &p.py;
+  T* v = (k1 >= 0.0) ? &p.y : &p.x;
+  T* pv = (k1 >= 0.0) ? &p.py : &p.px;
+  const T u0 = *u, pu0 = *pu, v0 = *v, pv0 = *pv;
+  const T g = (aK * L) * Sa;    // w sin(w L)
+  const T gh = (aK * L) * Sha;  // w sinh(w L)
+  *u = FMA(C, u0, ((L * Sa) * p.rpp) * pu0);
+  *pu = FMA(-(g * p.opd), u0, C * pu0);
+  *v = FMA(Ch, v0, ((L * Sha) * p.rpp) * pv0);
+  *pv = FMA(gh * p.opd, v0, Ch * pv0);
+  // I = integral over the element of px^2 + py^2
+  const T o2 = p.opd * p.opd;
+  const T A2 = pu0 * pu0, B2 = (aK * o2) * (u0 * u0);
+  const T Ah2 = pv0 * pv0, Bh2 = (aK * o2) * (v0 * v0);
+  const double hL = 0.5 * L;
+  T I = hL * (A2 + B2);
+  I = FMA(hL * (Sa * C), A2 - B2, I);
+  I = FMA(-((p.opd * L) * (Sa * g)), pu0 * u0, I);
+  I = FMA(mkv<T>(hL), Ah2 - Bh2, I);
+  I = FMA(hL * (Sha * Ch), Ah2 + Bh2, I);
+  I = FMA((p.opd * L) * (Sha * gh), pv0 * v0, I);
+  // L (1 - 1/rvv) - I / (2 rvv (1+delta)^2), with 1 - 1/rvv = (delta - beta0 ptau) / (1+delta)
+  p.zeta = p.zeta + FMA(L * (p.delta - p.epm1), p.rpp, -(((0.5 * p.rv0v) * (p.rpp * p.rpp)) * I));
+}
 
 // ---------------------------------------------------------------------------
 // Loss-location refinement (section "Particle-matter interaction and
@@ -933,6 +1048,7 @@ static bool inverse_row(Part<double>& p, const Prep& q, const RefConst& rc) {
       p.py = std::fma(-q.r43, p.y, p.py);
       return true;
     case T_LINEARMAP: return false;
+    case T_QUAD: thick_quad(p, q.k1, -q.Lq); return true;
     case T_BEAMBEAM4D: {  // x, y unchanged by the kick: take the same kick back
       double fx, fy;
       gauss_field(p.x - q.bb.xc, p.y - q.bb.yc, q.bb, &fx, &fy);
@@ -977,7 +1093,7 @@ int xo_track(const Element* el, int64_t n_el, const Reference* ref, int rad_mode
   const RefConst rc = ref_const(*ref);
   std::vector<Prep> prep(n_el);
   for (int64_t e = 0; e < n_el; e++) {
-    if (el[e].type < 0 || el[e].type > T_BEAMBEAM4D) return -1;
+    if (el[e].type < 0 || el[e].type > T_QUAD) return -1;
     if (el[e].type == T_MULTIPOLE && (el[e].order < 0 || el[e].order > 10)) return -1;
     prep[e] = prepare(el[e], rc);
   }
@@ -1023,11 +1139,11 @@ int xo_refine_losses(const Element* el, int64_t n_el, const Reference* ref, cons
   Frame f = {0.0, 0.0, 0.0};
   int64_t n_ap = 0;
   for (int64_t e = 0; e < n_el; e++) {
-    if (el[e].type < 0 || el[e].type > T_BEAMBEAM4D) return -1;
+    if (el[e].type < 0 || el[e].type > T_QUAD) return -1;
     if (el[e].type == T_MULTIPOLE && (el[e].order < 0 || el[e].order > 10)) return -1;
     prep[e] = prepare(el[e], rc);
     fr[e] = f;
-    spos[e + 1] = spos[e] + (el[e].type == T_DRIFT ? el[e].p[0] : 0.0);
+    spos[e + 1] = spos[e] + (el[e].type == T_DRIFT ? el[e].p[0] : (el[e].type == T_QUAD ? el[e].p[1] : 0.0));
     if (el[e].type == T_XYSHIFT) {
       const double c = std::cos(f.th), sn = std::sin(f.th);
       f.dx = f.dx + (c * el[e].p[0] - sn * el[e].p[1]);
@@ -1109,6 +1225,7 @@ int xo_refine_losses(const Element* el, int64_t n_el, const Reference* ref, cons
       } else {
         track_element(p, prep[j], 0, rc, 0, 0, 0);
         if (p.state != 1) { found = pos; break; }
+        if (prep[j].type == T_QUAD) pos = pos + prep[j].Lq;  // a loss inside is placed at its exit
       }
     }
     if (!(found == found)) found = spos[e];

@@ -26,6 +26,7 @@ import numpy as np
 ELEMENT_DTYPE = np.dtype([("type", "<i4"), ("order", "<i4"), ("p", "<f8", (48,))], align=True)
 MARKER, DRIFT, MULTIPOLE, CAVITY, DIPEDGE, LINEARMAP, APERTURE = 0, 1, 2, 3, 4, 5, 6
 XYSHIFT, SROTATION, APERTURE_RECT, APERTURE_ELLIPSE = 7, 8, 9, 10
+BEAMBEAM4D, QUAD = 11, 12
 MAX_ORDER = 10
 
 C_LIGHT = 299792458.0
@@ -91,6 +92,17 @@ def xy_shift(dx: float, dy: float):
 def s_rotation(angle: float):
     """Change of reference frame: rotated by `angle` [rad] about the orbit."""
     return _row(SROTATION, 0, [angle])
+
+
+def quadrupole(k1: float, length: float):
+    """Thick quadrupole: k1 [m^-2] (> 0 focuses x), length [m]."""
+    return _row(QUAD, 0, [k1, length])
+
+
+def beambeam4d(q_n: float, beta_s: float, sigma_x: float, sigma_y: float, x_c: float = 0.0, y_c: float = 0.0):
+    """4D weak-strong beam-beam lens: strong bunch of q_n = charge x particles
+    [e] at speed beta_s against the beam, Gaussian sigma_x, sigma_y, centre."""
+    return _row(BEAMBEAM4D, 0, [q_n, beta_s, sigma_x, sigma_y, x_c, y_c])
 
 
 def aperture_rect(x_min: float, x_max: float, y_min: float, y_max: float):

@@ -169,10 +169,7 @@ def test_refine_losses_bitwise():
 
 
 def bb_lens(qN, beta_s, sx, sy, xc=0.0, yc=0.0):
-    r = I.marker().copy()
-    r["type"] = oracle.BEAMBEAM4D
-    r["p"][:6] = [qN, beta_s, sx, sy, xc, yc]
-    return r
+    return I.beambeam4d(qN, beta_s, sx, sy, xc, yc)
 
 
 def test_beambeam_lenses_bitwise():

@@ -94,9 +94,7 @@ def test_beambeam_tune_shift_by_tracking():
     M = np.eye(6)
     for k in (0, 2):
         M[k, k], M[k, k + 1], M[k + 1, k], M[k + 1, k + 1] = math.cos(mu), beta * math.sin(mu), -math.sin(mu) / beta, math.cos(mu)
-    lens = I.marker().copy()
-    lens["type"] = oracle.BEAMBEAM4D
-    lens["p"][:6] = [N, 1.0, sig, sig, 0.0, 0.0]
+    lens = I.beambeam4d(N, 1.0, sig, sig)
     el = I.table([I.linear_map(M), lens])
     t = T.twiss(el, ref)
     k = 2 * N * 2.8179403262e-15 * 0.51099895000e6 / p0c / (2 * sig * sig)
