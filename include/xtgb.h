@@ -110,6 +110,17 @@ extern "C" {
                            sigma_x^2, sigma_y^2 agree to 1e-10; the linear
                            field within (dx/sigma_x)^2 + (dy/sigma_y)^2 < 1e-10
                            of the centre).  Independent of zeta and delta.   */
+#define XT_QUAD 12       /* p[0] = k1 [m^-2] (> 0 focuses in x), p[1] = length
+                           L [m] (finite, >= 0; L = 0 has no effect).  Thick
+                           quadrupole (section "Lattice modelling and single
+                           particle tracking"): the exact flow of
+                           (px^2 + py^2) / (2 (1+delta)) + k1 (x^2 - y^2) / 2,
+                           harmonic with w^2 = |k1| / (1+delta) (cos/sin in
+                           the focusing plane, cosh/sinh in the other); zeta
+                           gains L (1 - 1/rvv) minus the integral of
+                           (px^2 + py^2) / (2 rvv (1+delta)^2) over the body,
+                           in closed form.  Delta and ptau are unchanged.
+                           Loss refinement steps through it like a drift.    */
 
 #define XT_MAX_ORDER 10
 #define XT_NPARAM 48

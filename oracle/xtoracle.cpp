@@ -932,7 +932,10 @@ template <class T>
 static inline void thick_quad(Part<T>& p, double k1, double L) {
   if (L == 0.0) return;
   const T aK = (k1 >= 0.0) ? k1 * p.rpp : (-k1) * p.rpp;  // |k1| / (1+delta)
-  const T w = SQRT(aK);
+  // aK vanishes only for k1 = 0, where the map depends on a^2 alone: there w
+  // takes aK itself (same value, sqrt(+-0) = +-0) so that dual numbers carry a
+  // zero derivative instead of 0 * inf.
+  const T w = (k1 == 0.0) ? aK : SQRT(aK);
   const T a = w * std::fabs(L);
   T C, Sa, Ch, Sha;
   trig_sa(a, &C, &Sa);
@@ -1206,13 +1209,17 @@ int xo_refine_losses(const Element* el, int64_t n_el, const Reference* ref, cons
     for (int64_t j = q;;) {
       j = (j + 1 == n_el) ? 0 : j + 1;
       if (j == e) break;
-      if (prep[j].type == T_DRIFT && prep[j].L > 0.0) {
-        const double L = prep[j].L;
+      // drifts and thick quadrupoles in steps of at most ds (the quadrupole's
+      // flow composes exactly, so its steps give the same map as one pass)
+      const bool quad = prep[j].type == T_QUAD && prep[j].Lq > 0.0;
+      if ((prep[j].type == T_DRIFT && prep[j].L > 0.0) || quad) {
+        const double L = quad ? prep[j].Lq : prep[j].L;
         const int64_t ns = (int64_t)std::ceil(L / ds);
         const double h = L / (double)ns;
         const double c = std::cos(fr[j].th), sn = std::sin(fr[j].th);
         for (int64_t k = 1; k <= ns; k++) {
-          drift(p, h, 0, 0);
+          if (quad) thick_quad(p, prep[j].k1, h);
+          else drift(p, h, 0, 0);
           const double at = std::fma((double)k, h, pos);
           if (p.state != 1) { found = at; break; }
           const double lx = (c * p.x - sn * p.y) + fr[j].dx;
@@ -1225,7 +1232,6 @@ int xo_refine_losses(const Element* el, int64_t n_el, const Reference* ref, cons
       } else {
         track_element(p, prep[j], 0, rc, 0, 0, 0);
         if (p.state != 1) { found = pos; break; }
-        if (prep[j].type == T_QUAD) pos = pos + prep[j].Lq;  // a loss inside is placed at its exit
       }
     }
     if (!(found == found)) found = spos[e];

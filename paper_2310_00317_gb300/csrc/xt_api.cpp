@@ -531,7 +531,7 @@ static int build_refine_tables(xt_tracker* t, int n_angles) {
     frame[4 * i + 1] = std::sin(th);
     frame[4 * i + 2] = fdx;
     frame[4 * i + 3] = fdy;
-    spos[i + 1] = spos[i] + (e.type == XT_DRIFT ? e.p[0] : 0.0);
+    spos[i + 1] = spos[i] + (e.type == XT_DRIFT ? e.p[0] : (e.type == XT_QUAD ? e.p[1] : 0.0));
     if (e.type == XT_XYSHIFT) {
       const double c = std::cos(th), sn = std::sin(th);
       fdx = fdx + (c * e.p[0] - sn * e.p[1]);

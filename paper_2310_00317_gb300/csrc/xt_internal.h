@@ -26,6 +26,8 @@ struct RecHdr {
 };
 static_assert(sizeof(RecHdr) == 16, "record header is 16 bytes");
 enum : uint16_t { REC_CURV = 1, REC_RAD = 2, REC_PURE = 4, REC_BEND = 8 };
+// thick quadrupole: x is the focusing plane (k1 >= 0)
+enum : uint16_t { REC_QF = 1 };
 // REC_PURE: knl0 == ksl0 == 0 and hxl == 0.  REC_BEND: hxl != 0, hxl == knl0,
 // ksl0 == 0.  Without radiation these multipoles add the last Horner step
 // straight into px, py (and a bend's -knl0 + hxl (1+delta) becomes hxl delta).

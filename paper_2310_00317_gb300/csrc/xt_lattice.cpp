@@ -53,6 +53,9 @@ int64_t flops_of_row(const xt_element& e, int rad_mode) {
     case XT_SROTATION: return 12;
     case XT_APERTURE_RECT: return 0;
     case XT_APERTURE_ELLIPSE: return 5;
+    // |k1|/(1+delta), a, cos, sin(a)/a, cosh and sinh(a)/a (13); the 4x4 map (18);
+    // the path-length integral (36) and zeta (9)
+    case XT_QUAD: return (e.p[1] == 0.0) ? 0 : 76;
     case XT_BEAMBEAM4D: {
       // round: the field and the kick; else two 40-term w(z) (~300 each), e^x and the rest
       const double sx2 = e.p[2] * e.p[2], sy2 = e.p[3] * e.p[3];
@@ -178,6 +181,17 @@ int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice*
           prm[10] = 1.0 / (s1 * (s1 + s2));
           prm[11] = 1.0 / (s2 * (s1 + s2));
         }
+        break;
+      }
+      case XT_QUAD: {
+        const double k1 = e.p[0], L = e.p[1];
+        if (!(L >= 0.0) || !std::isfinite(L) || !std::isfinite(k1)) {
+          *err = "element " + std::to_string(i) + ": thick quadrupole needs a finite k1 and a finite length L >= 0";
+          return XT_ERR_INVALID;
+        }
+        if (L == 0.0) continue;  // no effect
+        prm = {(k1 >= 0.0) ? k1 : -k1, L};
+        if (k1 >= 0.0) flags |= REC_QF;
         break;
       }
       case XT_APERTURE_ELLIPSE:

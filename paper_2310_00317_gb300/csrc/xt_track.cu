@@ -161,9 +161,10 @@ __device__ __forceinline__ void apply_energy_loss(Part& p, double dpt, const Ref
   p.py = p.py * f;
 }
 
-// Sine: Cody-Waite reduction by pi/2 (three-part constant, round-to-nearest
-// by the 1.5*2^52 shift) and the Taylor series of sin / cos on |r| <= pi/4.
-__device__ __forceinline__ double sin_cw(double x, const SinTab& t) {
+// Sine (shift 0) or cosine (shift 1): Cody-Waite reduction by pi/2 (three-part
+// constant, round-to-nearest by the 1.5*2^52 shift), the quadrant advanced by
+// `shift`, and the Taylor series of sin / cos on |r| <= pi/4.
+__device__ __forceinline__ double trig_cw(double x, const SinTab& t, int shift) {
   const double P1 = 1.5707963267948965579989817342720925807952880859375;
   const double P2 = 6.123233995736766035868820147291818682e-17;
   const double P3 = -1.4973849048591698329435081771059e-33;
@@ -173,7 +174,7 @@ __device__ __forceinline__ double sin_cw(double x, const SinTab& t) {
   double r = fma(-k, P1, x);
   r = fma(-k, P2, r);
   r = fma(-k, P3, r);
-  const int q = (int)((long long)k & 3);
+  const int q = (int)(((long long)k + shift) & 3);
   const double z = r * r;
   double res;
   if (q & 1) {
@@ -189,6 +190,7 @@ __device__ __forceinline__ double sin_cw(double x, const SinTab& t) {
   }
   return (q & 2) ? -res : res;
 }
+__device__ __forceinline__ double sin_cw(double x, const SinTab& t) { return trig_cw(x, t, 0); }
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon et al., SC'11) and the photon sampler.
@@ -422,6 +424,65 @@ __device__ __forceinline__ void bb_field(double x, double y, const double* prm, 
   *fy = copysign(gy, y);
 }
 
+// Thick quadrupole (section "Lattice modelling and single particle tracking"):
+// the exact flow, over a length L of either sign, of the expanded Hamiltonian
+// (px^2 + py^2) / (2 (1+delta)) + k1 (x^2 - y^2) / 2.  Transverse motion is
+// harmonic with w^2 = |k1| / (1+delta), cos / sin in the focusing plane (x when
+// fx) and cosh / sinh in the other; zeta gains
+// L (1 - 1/rvv) - (1 / (2 rvv (1+delta)^2)) * integral of (px^2 + py^2) ds,
+// the integral in closed form.  C = cos a, Sa = sin(a)/a, Ch = cosh a and
+// Sha = sinh(a)/a at a = w |L|: series in a^2 (1/n! from the special table)
+// below a = 1/2, else from trig_cw and two exponentials.
+__device__ __forceinline__ void thick_quad(Part& p, double absk1, double L, bool fx, const SinTab& sn) {
+  const double aK = absk1 * p.rpp;
+  const double a = sqrt(aK) * fabs(L);
+  const double C = trig_cw(a, sn, 1);
+  double Sa, Ch, Sha;
+  if (a < 0.5) {
+    const double z = a * a;
+    double ps = c_special[41 + 17], ph = c_special[41 + 17], pc = c_special[41 + 18];
+#pragma unroll
+    for (int n = 7; n >= 0; n--) {
+      ps = fma(ps, -z, c_special[41 + 2 * n + 1]);
+      ph = fma(ph, z, c_special[41 + 2 * n + 1]);
+    }
+#pragma unroll
+    for (int n = 8; n >= 0; n--) pc = fma(pc, z, c_special[41 + 2 * n]);
+    Sa = ps;
+    Sha = ph;
+    Ch = pc;
+  } else {
+    Sa = trig_cw(a, sn, 0) / a;
+    const double e = exp_cw(a), ei = exp_cw(-a);
+    Ch = 0.5 * (e + ei);
+    Sha = (0.5 * (e - ei)) / a;
+  }
+  const double u0 = fx ? p.x : p.y, pu0 = fx ? p.px : p.py;
+  const double v0 = fx ? p.y : p.x, pv0 = fx ? p.py : p.px;
+  const double g = (aK * L) * Sa;    // w sin(w L)
+  const double gh = (aK * L) * Sha;  // w sinh(w L)
+  const double u1 = fma(C, u0, ((L * Sa) * p.rpp) * pu0);
+  const double pu1 = fma(-(g * p.opd), u0, C * pu0);
+  const double v1 = fma(Ch, v0, ((L * Sha) * p.rpp) * pv0);
+  const double pv1 = fma(gh * p.opd, v0, Ch * pv0);
+  const double o2 = p.opd * p.opd;
+  const double A2 = pu0 * pu0, B2 = (aK * o2) * (u0 * u0);
+  const double Ah2 = pv0 * pv0, Bh2 = (aK * o2) * (v0 * v0);
+  const double hL = 0.5 * L;
+  double I = hL * (A2 + B2);
+  I = fma(hL * (Sa * C), A2 - B2, I);
+  I = fma(-((p.opd * L) * (Sa * g)), pu0 * u0, I);
+  I = fma(hL, Ah2 - Bh2, I);
+  I = fma(hL * (Sha * Ch), Ah2 + Bh2, I);
+  I = fma((p.opd * L) * (Sha * gh), pv0 * v0, I);
+  // 1 - 1/rvv = (delta - beta0 ptau) / (1+delta)
+  p.zeta = p.zeta + fma(L * (p.delta - p.epm1), p.rpp, -(((0.5 * p.rv0v) * (p.rpp * p.rpp)) * I));
+  p.x = fx ? u1 : v1;
+  p.px = fx ? pu1 : pv1;
+  p.y = fx ? v1 : u1;
+  p.py = fx ? pv1 : pu1;
+}
+
 template <int RAD>
 __device__ __forceinline__ void multipole(Part& p, const double* prm, int order, int flags,
                                           const RefDev& r, const RadCtx& rc, int64_t pid, int turn,
@@ -560,6 +621,9 @@ __device__ __forceinline__ int element(Part& p, uint32_t type, uint32_t order, u
     case XT_DIPEDGE:
       p.px = fma(prm[0], p.x, p.px);
       p.py = fma(prm[1], p.y, p.py);
+      return 1;
+    case XT_QUAD:  // prm = |k1|, L; flags = REC_QF when x is the focusing plane
+      thick_quad(p, prm[0], prm[1], (flags & REC_QF) != 0, sn);
       return 1;
     case XT_LINEARMAP: {
       const double v[6] = {p.x, p.px, p.y, p.py, p.zeta, p.ptau};
@@ -880,6 +944,9 @@ __device__ __forceinline__ bool inverse_record(Part& p, uint32_t type, uint32_t 
       p.px = fma(-prm[0], p.x, p.px);
       p.py = fma(-prm[1], p.y, p.py);
       return true;
+    case XT_QUAD:
+      thick_quad(p, prm[0], -prm[1], (flags & REC_QF) != 0, sn);
+      return true;
     case XT_LINEARMAP: return false;
     case XT_BEAMBEAM4D: {  // x, y unchanged by the kick: take the same kick back
       double fx, fy;
@@ -965,13 +1032,19 @@ __global__ void __launch_bounds__(128) refine_kernel(RefineArgs a) {
     const uint4 hv = *(const uint4*)(a.lat + off);
     const uint32_t type = hv.x & 0xFFFFu;
     const double* prm = (const double*)(a.lat + off + 16);
-    if (type == XT_DRIFT && prm[0] > 0.0) {
-      const double L = prm[0];
+    // drifts and thick quadrupoles in steps of at most ds (the quadrupole's
+    // flow composes exactly, so its steps give the same map as one pass)
+    const bool quad = type == XT_QUAD && prm[1] > 0.0;
+    if ((type == XT_DRIFT && prm[0] > 0.0) || quad) {
+      const double L = quad ? prm[1] : prm[0];
       const int64_t ns = (int64_t)ceil(L / a.ds);
       const double h = L / (double)ns;
       const double c = a.frame[4 * j], sn = a.frame[4 * j + 1], dx = a.frame[4 * j + 2], dy = a.frame[4 * j + 3];
+      const bool qf = (hv.y & REC_QF) != 0;
       for (int64_t k = 1; k <= ns; k++) {
-        const bool ok = drift_lane(p, h);
+        bool ok = true;
+        if (quad) thick_quad(p, prm[0], h, qf, a.sn);
+        else ok = drift_lane(p, h);
         const double at = fma((double)k, h, pos);
         if (!ok) { found = at; hit = true; break; }
         const double lx = (c * p.x - sn * p.y) + dx;

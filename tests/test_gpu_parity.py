@@ -168,6 +168,59 @@ def test_refine_losses_bitwise():
     tr2.close()
 
 
+def thick_quad_ring(n_cells=8, aperture=0.006):
+    """FODO cells of thick quadrupoles (a = w L about 0.67: the exponential
+    branch) with weak thick trims (a < 1/2: the series branch), k1 of both
+    signs and zero, a zero-length quadrupole, a misaligned and tilted one,
+    sextupoles, RF and circular apertures."""
+    rows = [I.cavity(2e6, 400e6, 180.0)]
+    for c in range(n_cells):
+        rows += I.misaligned([I.quadrupole(0.05, 3.0)], dx=1e-4 * (c - 3.5), dy=2e-5 * c, tilt=1e-3 * (c % 3))
+        rows += [I.drift(2.0), I.multipole(knl=[0.0, 0.0, 0.05]), I.drift(2.0)]
+        rows += [I.quadrupole(-0.05, 3.0)]
+        rows += [I.drift(1.5), I.quadrupole(0.004, 0.8), I.quadrupole(0.1, 0.0), I.quadrupole(0.0, 0.5),
+                 I.quadrupole(-0.004, 0.8), I.drift(1.5), I.aperture(aperture)]
+    return rows
+
+
+def test_thick_quadrupole_ring_bitwise():
+    """2,000 particles (5e-4 momentum spread, so a crosses 1/2 differently
+    per particle), 120 turns through a ring of thick quadrupoles, bit for bit
+    with the oracle, losses included."""
+    el = I.table(thick_quad_ring())
+    p = random_particles(PROTON, 2000, 47, sx=1.5e-3, spx=8e-5, sd=5e-4)
+    g, o = gpu_track(el, PROTON, p, 120), oracle.track(el, PROTON, p, 120)
+    assert_same(g, o)
+    assert 200 < np.sum(o["state"] == 1) < 1800
+
+
+def test_refine_losses_through_thick_quadrupoles_bitwise():
+    """Loss refinement that steps through thick quadrupole bodies (the
+    quadrupole's flow in steps of ds) and backtracks through them (the flow
+    with -L), GPU against oracle bit for bit; some refined losses lie inside
+    a quadrupole."""
+    rows = thick_quad_ring(n_cells=6, aperture=0.0055)
+    el = I.table(rows)
+    p = random_particles(PROTON, 3000, 53, sx=1.6e-3, spx=8e-5, sd=3e-4)
+    o = oracle.track(el, PROTON, p, 30)
+    assert np.sum(o["state"] == 0) > 500
+    s_o = oracle.refine_losses(el, PROTON, o, 0.01, 128)
+    tr = xtgb.Tracker(el, PROTON)
+    s_g = tr.refine_losses(xtgb.Particles.from_numpy(o), 0.01, 128).cpu().numpy()
+    tr.close()
+    same = (s_g == s_o) | (np.isnan(s_g) & np.isnan(s_o))
+    assert np.all(same), np.flatnonzero(~same)[:5]
+    pos, body = 0.0, []
+    for r in rows:
+        L = float(r["p"][0]) if int(r["type"]) == I.DRIFT else (float(r["p"][1]) if int(r["type"]) == I.QUAD else 0.0)
+        if int(r["type"]) == I.QUAD and L > 0:
+            body.append((pos, pos + L))
+        pos += L
+    lost = s_o[o["state"] == 0]
+    inside = sum(np.sum((lost > a + 1e-9) & (lost < b - 1e-9)) for a, b in body)
+    assert inside > 20
+
+
 def bb_lens(qN, beta_s, sx, sy, xc=0.0, yc=0.0):
     return I.beambeam4d(qN, beta_s, sx, sy, xc, yc)
 

@@ -584,6 +584,35 @@ def test_refine_backtracks_through_a_kick():
         assert s_star - early - 1e-9 <= s[i] <= s_star + 0.005 + 1e-9, (i, s[i], s_star)
 
 
+def test_refine_steps_through_a_thick_quadrupole():
+    """A defocusing thick quadrupole (k1 = -0.05 m^-2 over 6 m) between 1 m
+    drifts and two circular apertures: inside the magnet x(t) = x1 cosh(w t)
+    + (px1 / w) sinh(w t), w = sqrt(0.05), t = s - 1 m (on momentum).  The
+    refined loss lies within one step after the crossing x(s) = r found here
+    by bisection, less the 1024-gon's sag."""
+    r, k1, Lq, ds = 0.01, -0.05, 6.0, 0.005
+    el = [I.aperture(r), I.drift(1.0), I.quadrupole(k1, Lq), I.drift(1.0), I.aperture(r)]
+    xs = np.array([0.006, 0.007, -0.008, 0.0065, -0.0062])
+    pxs = np.array([1e-4, -2e-4, 3e-4, 0.0, -1e-4])
+    o = _lost_at(el, xs, pxs)
+    assert np.all(o["state"] == 0) and np.all(o["at_element"] == 4)
+    s = oracle.refine_losses(I.table(el), PROTON, o, ds, 1024)
+    w = math.sqrt(-k1)
+    for i in range(len(xs)):
+        pz = math.sqrt(1 - pxs[i] ** 2)
+        x1, px1 = xs[i] + pxs[i] / pz, pxs[i]
+        xq = lambda t: x1 * math.cosh(w * t) + px1 / w * math.sinh(w * t)
+        def cross(rr):
+            lo, hi = 0.0, Lq
+            assert abs(xq(lo)) < rr < abs(xq(hi))
+            for _ in range(200):
+                mid = 0.5 * (lo + hi)
+                lo, hi = (mid, hi) if abs(xq(mid)) < rr else (lo, mid)
+            return 1.0 + hi
+        s_star, s_early = cross(r), cross(r * math.cos(math.pi / 1024))
+        assert s_early - 1e-9 <= s[i] <= s_star + ds + 1e-9, (i, s[i], s_star)
+
+
 def _winding_inside(px, py, vx, vy):
     """Winding number of the closed polygon (vx, vy) about (px, py) != 0."""
     ang = np.arctan2(vy - py, vx - px)
@@ -761,6 +790,22 @@ def test_thick_quad_linear_matrix(k1):
     dfo = np.array([[math.cosh(w * L), math.sinh(w * L) / w], [w * math.sinh(w * L), math.cosh(w * L)]])
     fx, fy = (foc, dfo) if k1 > 0 else (dfo, foc)
     assert np.max(np.abs(M[:2, :2] - fx)) < 1e-14 and np.max(np.abs(M[2:4, 2:4] - fy)) < 1e-14
+
+
+def test_thick_quad_without_gradient_is_the_expanded_drift():
+    """k1 = 0: x += L px / (1+delta) in both planes, with finite derivatives."""
+    L, d = 1.7, 2e-3
+    z0 = np.array([1e-3, 2e-4, -5e-4, 1e-4, 0.0, d])
+    zo, M = oracle.track_jacobian(I.table([I.quadrupole(0.0, L)]), PROTON, z0)
+    p = oracle.track(I.table([I.quadrupole(0.0, L)]), PROTON,
+                     I.make_particles(PROTON, [1e-3], [2e-4], [-5e-4], [1e-4], [0.0], [d]), 1)
+    opd = 1.0 + p["delta"][0]
+    assert abs(p["x"][0] - (1e-3 + L * 2e-4 / opd)) < 1e-18 and abs(p["y"][0] - (-5e-4 + L * 1e-4 / opd)) < 1e-18
+    assert np.all(np.isfinite(M))
+    b0 = PROTON[2] / math.hypot(PROTON[0], PROTON[2])
+    pt = b0 * d  # z0[5] is pzeta = ptau / beta0
+    opd_z = math.sqrt(1.0 + 2.0 * pt / b0 + pt * pt)
+    assert abs(M[0, 1] - L / opd_z) < 1e-15 and abs(M[2, 3] - L / opd_z) < 1e-15 and M[1, 0] == 0.0
 
 
 def test_thick_quad_symplectic_and_reversible():
