@@ -522,11 +522,10 @@ static int build_refine_tables(xt_tracker* t, int n_angles) {
   std::vector<int32_t> row_off(n, -1), prev(n, -1), pidx(n, -1);
   std::vector<double> spos(n + 1, 0.0), frame(4 * n, 0.0);
   double th = 0.0, fdx = 0.0, fdy = 0.0;
-  size_t k = 0;
   int64_t last = -1;
   for (int64_t i = 0; i < n; i++) {
     const xt_element& e = t->table[i];
-    if (e.type != XT_MARKER) row_off[i] = (int32_t)t->lat.rec_off[k++];
+    row_off[i] = t->lat.row_rec[(size_t)i];
     frame[4 * i] = std::cos(th);
     frame[4 * i + 1] = std::sin(th);
     frame[4 * i + 2] = fdx;

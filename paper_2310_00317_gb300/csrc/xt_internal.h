@@ -64,6 +64,7 @@ struct Lattice {
   std::vector<uint8_t> bytes;     // record stream
   std::vector<uint32_t> rec_off;  // byte offset of every record
   std::vector<uint32_t> rec_bytes;
+  std::vector<int32_t> row_rec;   // per table row: its record's byte offset, -1 if it has none
   int64_t n_el = 0;               // rows in the user's table
   uint64_t hash = 0;
   std::vector<int64_t> flops;     // algorithmic FP64 flops of one traversal, per table row

@@ -74,6 +74,7 @@ int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice*
                     std::string* err) {
   out->bytes.clear();
   out->rec_off.clear();
+  out->row_rec.assign((size_t)n, -1);
   out->rec_bytes.clear();
   out->flops.assign((size_t)n, 0);
   out->n_el = n;
@@ -214,6 +215,7 @@ int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice*
     const size_t bytes = sizeof(RecHdr) + prm.size() * sizeof(double);
     h.size16 = (uint16_t)(bytes / 16);
     h.elem = (uint32_t)i;
+    out->row_rec[(size_t)i] = (int32_t)out->bytes.size();
     out->rec_off.push_back((uint32_t)out->bytes.size());
     out->rec_bytes.push_back((uint32_t)bytes);
     put(out->bytes, &h, sizeof(h));
