@@ -51,7 +51,8 @@ struct Element {
 enum {
   T_MARKER = 0, T_DRIFT = 1, T_MULTIPOLE = 2, T_CAVITY = 3,
   T_DIPEDGE = 4, T_LINEARMAP = 5, T_APERTURE = 6, T_XYSHIFT = 7, T_SROTATION = 8,
-  T_APERTURE_RECT = 9, T_APERTURE_ELLIPSE = 10, T_BEAMBEAM4D = 11, T_QUAD = 12
+  T_APERTURE_RECT = 9, T_APERTURE_ELLIPSE = 10, T_BEAMBEAM4D = 11, T_QUAD = 12,
+  T_BEND = 13
 };
 struct Reference { double mass0, q0, p0c; };
 
@@ -73,6 +74,7 @@ static inline Dual operator-(const Dual& a, double b) { Dual r = a; r.v = a.v - 
 static inline Dual operator-(double a, const Dual& b) { Dual r; r.v = a - b.v; for (int i = 0; i < 6; i++) r.d[i] = -b.d[i]; return r; }
 static inline Dual operator*(const Dual& a, double b) { Dual r; r.v = a.v * b; for (int i = 0; i < 6; i++) r.d[i] = a.d[i] * b; return r; }
 static inline Dual operator*(double a, const Dual& b) { Dual r; r.v = a * b.v; for (int i = 0; i < 6; i++) r.d[i] = a * b.d[i]; return r; }
+static inline Dual operator/(const Dual& a, double b) { Dual r; r.v = a.v / b; for (int i = 0; i < 6; i++) r.d[i] = a.d[i] / b; return r; }
 static inline Dual operator/(double a, const Dual& b) { Dual r; r.v = a / b.v; for (int i = 0; i < 6; i++) r.d[i] = -r.v * b.d[i] / b.v; return r; }
 
 static inline double val(double a) { return a; }
@@ -695,6 +697,8 @@ struct Prep {
   double ia2, ib2;                       // elliptic aperture: 1/a^2, 1/b^2
   BBConst bb;                            // 4D beam-beam lens
   double k1, Lq;                         // thick quadrupole
+  double bk0, bh, bL, bk1;               // thick bend: field, curvature, length, gradient
+  int bfull;                             // thick bend: 1 = full model, 0 = expanded
 };
 
 static Prep prepare(const Element& e, const RefConst& rc) {
@@ -755,6 +759,7 @@ static Prep prepare(const Element& e, const RefConst& rc) {
     case T_APERTURE_RECT: q.xmin = e.p[0]; q.xmax = e.p[1]; q.ymin = e.p[2]; q.ymax = e.p[3]; break;
     case T_APERTURE_ELLIPSE: q.ia2 = 1.0 / (e.p[0] * e.p[0]); q.ib2 = 1.0 / (e.p[1] * e.p[1]); break;
     case T_QUAD: q.k1 = e.p[0]; q.Lq = e.p[1]; break;
+    case T_BEND: q.bk0 = e.p[0]; q.bh = e.p[1]; q.bL = e.p[2]; q.bk1 = e.p[3]; q.bfull = (e.p[4] != 0.0); break;
     case T_BEAMBEAM4D: {
       // kick of a counter-moving Gaussian bunch integrated over the crossing:
       // Delta p_perp / P0 = 2 q0 q_s N_s (r_e m_e c^2 / p0 c) (1 + beta0 beta_s) /
@@ -845,6 +850,10 @@ static inline void track_element(Part<T>& p, const Prep& q, int rad_mode, const 
       break;
     }
     case T_QUAD: thick_quad(p, q.k1, q.Lq); break;
+    case T_BEND:
+      if (q.bfull) bend_full(p, q.bk0, q.bh, q.bL, turn, elem);
+      else bend_expanded(p, q.bk0, q.bh, q.bL, q.bk1);
+      break;
     // 4D weak-strong beam-beam (section "Beam-beam interactions"): transverse
     // kick of a frozen Gaussian bunch, independent of the longitudinal
     // coordinates.  Values only (the Jacobian entry points reject this type).
@@ -966,6 +975,168 @@ static inline void thick_quad(Part<T>& p, double k1, double L) {
   p.zeta = p.zeta + FMA(L * (p.delta - p.epm1), p.rpp, -(((0.5 * p.rv0v) * (p.rpp * p.rpp)) * I));
 }
 
+// Entire functions of z (either sign) with a = sqrt|z|: C = cos a,
+// S = sin(a)/a, S2 = (1 - C)/z, S3 = (1 - S)/z for z > 0 (cosh and sinh for
+// z < 0).  Series in z below |z| = 1/4 (C and S to z^8, S2 and S3 to z^7:
+// truncation below 1e-18), else from sin_cw/cos_cw or two exponentials.
+template <class T>
+static inline void osc_funcs(const T& z, T* C, T* S, T* S2, T* S3) {
+  const std::vector<double>& f = inv_fact();
+  if (std::fabs(val(z)) < 0.25) {
+    const T mz = -z;
+    T c = mkv<T>(f[16]), s = mkv<T>(f[17]), s2 = mkv<T>(f[16]), s3 = mkv<T>(f[17]);
+    for (int n = 7; n >= 0; n--) {
+      c = FMA(c, mz, mkv<T>(f[2 * n]));
+      s = FMA(s, mz, mkv<T>(f[2 * n + 1]));
+    }
+    for (int n = 6; n >= 0; n--) {
+      s2 = FMA(s2, mz, mkv<T>(f[2 * n + 2]));
+      s3 = FMA(s3, mz, mkv<T>(f[2 * n + 3]));
+    }
+    *C = c; *S = s; *S2 = s2; *S3 = s3;
+    return;
+  }
+  if (val(z) > 0.0) {
+    const T a = SQRT(z);
+    *C = COS(a);
+    *S = SIN(a) / a;
+  } else {
+    const T a = SQRT(-z);
+    const T e = EXPC(a), ei = EXPC(-a);
+    *C = 0.5 * (e + ei);
+    *S = (0.5 * (e - ei)) / a;
+  }
+  *S2 = (1.0 - *C) / z;
+  *S3 = (1.0 - *S) / z;
+}
+
+// asin(v)/v = sum_n a_n v^(2n), a_n = (2n)! / (4^n n!^2 (2n+1)), n = 0..13
+// (a running product t_n = t_(n-1) (2n-1) / (2n), then a_n = t_n / (2n+1)).
+static const std::vector<double>& asin_coef() {
+  static std::vector<double> c = [] {
+    std::vector<double> v(14);
+    double t = 1.0;
+    for (int n = 0; n < 14; n++) {
+      if (n > 0) t = (t * (double)(2 * n - 1)) / (double)(2 * n);
+      v[n] = t / (double)(2 * n + 1);
+    }
+    return v;
+  }();
+  return c;
+}
+
+// asin(u)/u for |u| <= 1: the angle is halved, asin u = 2 asin v with
+// v = u / sqrt(2 (1 + sqrt(1 - u^2))), until |v| < 1/4 (at most three times),
+// then the series (truncation below 3e-18 there).
+template <class T>
+static inline T asin_over(const T& u) {
+  const std::vector<double>& a = asin_coef();
+  T v = u;
+  double m = 1.0;
+  for (int k = 0; k < 4 && std::fabs(val(v)) >= 0.25; k++) {
+    v = v / SQRT(2.0 * (1.0 + SQRT(1.0 - v * v)));
+    m = m + m;
+  }
+  const T z = v * v;
+  T s = mkv<T>(a[13]);
+  for (int n = 12; n >= 0; n--) s = FMA(s, z, mkv<T>(a[n]));
+  if (m == 1.0) return s;
+  return (m * (v / u)) * s;
+}
+
+// Thick bend, expanded model (section "Lattice modelling and single particle
+// tracking": the model for large machines and small bending angles): the
+// exact flow of
+//   (px^2 + py^2) / (2 (1+delta)) - h x (1+delta) + k0 (x + h x^2 / 2) + k1 (x^2 - y^2) / 2,
+// the Hamiltonian in the frame of curvature h with its square root expanded
+// to second order in px, py and the factor (1 + h x) kept on the leading term
+// only.  x is a driven oscillator, px' = F - Kx x with F = h (1+delta) - k0
+// and Kx = k0 h + k1; y has py' = k1 y; and
+//   zeta' = 1 - (1/rvv) (1 + h x + (px^2 + py^2) / (2 (1+delta)^2)),
+// integrated in closed form with the functions of osc_funcs at
+// z = K L^2 / (1+delta).  The sign of L is carried through (-L inverts).
+template <class T>
+static inline void bend_expanded(Part<T>& p, double k0, double h, double L, double k1) {
+  const double Kx = k0 * h + k1, L2 = L * L;
+  const T zx = (Kx * p.rpp) * L2;
+  const T zy = ((-k1) * p.rpp) * L2;
+  T C, S, S2, S3, Cy, Sy, S2y, S3y;
+  osc_funcs(zx, &C, &S, &S2, &S3);
+  osc_funcs(zy, &Cy, &Sy, &S2y, &S3y);
+  const T x0 = p.x, px0 = p.px, y0 = p.y, py0 = p.py;
+  const T F = FMA(h, p.delta, mkv<T>(h - k0));  // h (1+delta) - k0
+  const T G = FMA(-Kx, x0, F);                   // px' at the entrance
+  const T Gy = k1 * y0;
+  const T Lr = L * p.rpp;
+  p.x = FMA(C, x0, FMA(Lr * S, px0, ((L * Lr) * S2) * F));
+  p.px = FMA(C, px0, (L * S) * G);
+  p.y = FMA(Cy, y0, (Lr * Sy) * py0);
+  p.py = FMA(Cy, py0, (L * Sy) * Gy);
+  // integrals over the body of x and of px^2 + py^2, with px(s) = px0 c(s) + G s1(s):
+  // int c^2 = (L/2)(1 + C S), int c s1 = (L S)^2 / 2, int s1^2 = (L^3/2)(1 - C S)/z
+  // and (1 - C S)/z = S3 + S S2
+  const T Ix = FMA(L * S, x0, FMA((L * Lr) * S2, px0, ((L2 * Lr) * S3) * F));
+  const double hL = 0.5 * L, hL3 = 0.5 * (L2 * L);
+  T I = (hL * FMA(C, S, mkv<T>(1.0))) * (px0 * px0);
+  I = FMA(L2 * (S * S), px0 * G, I);
+  I = FMA(hL3 * FMA(S, S2, S3), G * G, I);
+  I = FMA(hL * FMA(Cy, Sy, mkv<T>(1.0)), py0 * py0, I);
+  I = FMA(L2 * (Sy * Sy), py0 * Gy, I);
+  I = FMA(hL3 * FMA(Sy, S2y, S3y), Gy * Gy, I);
+  // L (1 - 1/rvv) = L (delta - beta0 ptau) / (1+delta)
+  p.zeta = p.zeta + FMA(L * (p.delta - p.epm1), p.rpp, -(p.rv0v * FMA(h, Ix, (0.5 * (p.rpp * p.rpp)) * I)));
+}
+
+// Thick bend, full model (section "Lattice modelling and single particle
+// tracking": the model for small machines): the exact motion in a uniform
+// vertical field k0 = B / (B rho) through a sector of curvature h and
+// reference length L.  In the horizontal plane the particle runs on a circle
+// of radius p_h / k0, p_h^2 = (1+delta)^2 - py^2, along which pX + k0 Z and
+// pZ - k0 X are constant (X, Z laboratory coordinates about the sector's
+// centre, X along the entrance x axis).  At the exit plane, turned by
+// theta = h L, this gives
+//   px' = B - k0 (1/h + x) sin(theta),   B = px cos + pz sin,  Q = pz cos - px sin,
+//   x'  = x cos - (1 - cos)/h + (1/h + x) sin (px' + B) / (pz' + Q),
+// with sin/h = L S, (1 - cos)/h = h L^2 S2 (functions of z = theta^2), so that
+// h = 0 is the straight dipole.  The arc length in the horizontal plane is
+// l_h = chord asin(u)/u, u = k0 chord / (2 p_h), with
+// chord^2 = (x' - x)^2 + (1 + h x)(1 + h x') 2 L^2 S2; then y += py l_h / p_h
+// and zeta += L - (1/rvv)(1+delta) l_h / p_h.  The sign of L is carried
+// through (-L inverts).  Lost with code -2 if pz or pz' is not real or the
+// particle cannot reach the exit plane.
+template <class T>
+static inline void bend_full(Part<T>& p, double k0, double h, double L, int turn, int elem) {
+  const double th = h * L, L2 = L * L;
+  double C, S, S2, S3;
+  osc_funcs(th * th, &C, &S, &S2, &S3);
+  const double sn = th * S, Sh = L * S, Ch = (h * L2) * S2, D2 = 2.0 * (L2 * S2);
+  const T u = FMA(-p.px, p.px, FMA(-p.py, p.py, p.dm1));  // pz^2 - 1
+  if (!(val(u) > -1.0 && val(u) < INFINITY)) { mark_lost(p, -2, turn, elem); return; }
+  const T pz = SQRT(1.0 + u);
+  const T ph2 = 1.0 + FMA(-p.py, p.py, p.dm1);
+  const T B = FMA(p.px, C, pz * sn);
+  const T Q = FMA(pz, C, -(p.px * sn));
+  const T r0s = FMA(p.x, sn, Sh);          // (1/h + x) sin(theta)
+  const T A = FMA(-k0, r0s, B);            // px at the exit plane
+  const T pzf2 = FMA(-A, A, ph2);
+  if (!(val(pzf2) > 0.0)) { mark_lost(p, -2, turn, elem); return; }
+  const T pzf = SQRT(pzf2);
+  const T den = pzf + Q;
+  if (!(val(den) > 0.0)) { mark_lost(p, -2, turn, elem); return; }
+  const T xf = FMA(p.x, C, mkv<T>(-Ch)) + r0s * ((A + B) / den);
+  const T dxf = xf - p.x;
+  const T chord = SQRT(FMA(dxf, dxf, (FMA(h, p.x, mkv<T>(1.0)) * FMA(h, xf, mkv<T>(1.0))) * D2));
+  const T ph = SQRT(ph2);
+  const T uu = (k0 * chord) / (ph + ph);
+  if (!(std::fabs(val(uu)) <= 1.0)) { mark_lost(p, -2, turn, elem); return; }
+  const T lh = ((L >= 0.0) ? chord : -chord) * asin_over(uu);
+  const T lr = lh / ph;
+  p.x = xf;
+  p.px = A;
+  p.y = FMA(p.py, lr, p.y);
+  p.zeta = p.zeta + FMA(-p.ep, lr, mkv<T>(L));
+}
+
 // ---------------------------------------------------------------------------
 // Loss-location refinement (section "Particle-matter interaction and
 // collimation studies": backtracking plus a polygonal interpolation of the
@@ -1052,6 +1223,10 @@ static bool inverse_row(Part<double>& p, const Prep& q, const RefConst& rc) {
       return true;
     case T_LINEARMAP: return false;
     case T_QUAD: thick_quad(p, q.k1, -q.Lq); return true;
+    case T_BEND:
+      if (q.bfull) bend_full(p, q.bk0, q.bh, -q.bL, 0, 0);
+      else bend_expanded(p, q.bk0, q.bh, -q.bL, q.bk1);
+      return p.state == 1;
     case T_BEAMBEAM4D: {  // x, y unchanged by the kick: take the same kick back
       double fx, fy;
       gauss_field(p.x - q.bb.xc, p.y - q.bb.yc, q.bb, &fx, &fy);
@@ -1080,6 +1255,23 @@ using namespace xo;
 
 extern "C" {
 
+// A table row the oracle accepts: a known type, a multipole order 0..10, a
+// bend model 0 (expanded) or 1 (full, without gradient).
+static bool row_ok(const Element& e) {
+  if (e.type < 0 || e.type > T_BEND) return false;
+  if (e.type == T_MULTIPOLE && (e.order < 0 || e.order > 10)) return false;
+  if (e.type == T_BEND && !(e.p[4] == 0.0 || (e.p[4] == 1.0 && e.p[3] == 0.0))) return false;
+  return true;
+}
+
+// Reference length of a row (drift, thick quadrupole and thick bend).
+static double row_length(const Element& e) {
+  if (e.type == T_DRIFT) return e.p[0];
+  if (e.type == T_QUAD) return e.p[1];
+  if (e.type == T_BEND) return e.p[2];
+  return 0.0;
+}
+
 // Tracks n particles (SoA arrays, updated in place) through n_turns turns of
 // the lattice, starting at absolute turn start_turn.  rad_mode: 0 off, 1 mean,
 // 2 quantum (Philox4x64-10 keyed by seed).  Particles with state != 1 on entry
@@ -1096,8 +1288,7 @@ int xo_track(const Element* el, int64_t n_el, const Reference* ref, int rad_mode
   const RefConst rc = ref_const(*ref);
   std::vector<Prep> prep(n_el);
   for (int64_t e = 0; e < n_el; e++) {
-    if (el[e].type < 0 || el[e].type > T_QUAD) return -1;
-    if (el[e].type == T_MULTIPOLE && (el[e].order < 0 || el[e].order > 10)) return -1;
+    if (!row_ok(el[e])) return -1;
     prep[e] = prepare(el[e], rc);
   }
   for (int64_t i = 0; i < n; i++) {
@@ -1142,11 +1333,10 @@ int xo_refine_losses(const Element* el, int64_t n_el, const Reference* ref, cons
   Frame f = {0.0, 0.0, 0.0};
   int64_t n_ap = 0;
   for (int64_t e = 0; e < n_el; e++) {
-    if (el[e].type < 0 || el[e].type > T_QUAD) return -1;
-    if (el[e].type == T_MULTIPOLE && (el[e].order < 0 || el[e].order > 10)) return -1;
+    if (!row_ok(el[e])) return -1;
     prep[e] = prepare(el[e], rc);
     fr[e] = f;
-    spos[e + 1] = spos[e] + (el[e].type == T_DRIFT ? el[e].p[0] : (el[e].type == T_QUAD ? el[e].p[1] : 0.0));
+    spos[e + 1] = spos[e] + row_length(el[e]);
     if (el[e].type == T_XYSHIFT) {
       const double c = std::cos(f.th), sn = std::sin(f.th);
       f.dx = f.dx + (c * el[e].p[0] - sn * el[e].p[1]);
@@ -1209,16 +1399,18 @@ int xo_refine_losses(const Element* el, int64_t n_el, const Reference* ref, cons
     for (int64_t j = q;;) {
       j = (j + 1 == n_el) ? 0 : j + 1;
       if (j == e) break;
-      // drifts and thick quadrupoles in steps of at most ds (the quadrupole's
-      // flow composes exactly, so its steps give the same map as one pass)
-      const bool quad = prep[j].type == T_QUAD && prep[j].Lq > 0.0;
-      if ((prep[j].type == T_DRIFT && prep[j].L > 0.0) || quad) {
-        const double L = quad ? prep[j].Lq : prep[j].L;
+      // drifts, thick quadrupoles and thick bends in steps of at most ds (the
+      // thick maps are flows: their steps compose to the same map as one pass)
+      const int ty = prep[j].type;
+      const double L = row_length(el[j]);
+      if ((ty == T_DRIFT || ty == T_QUAD || ty == T_BEND) && L > 0.0) {
         const int64_t ns = (int64_t)std::ceil(L / ds);
         const double h = L / (double)ns;
         const double c = std::cos(fr[j].th), sn = std::sin(fr[j].th);
         for (int64_t k = 1; k <= ns; k++) {
-          if (quad) thick_quad(p, prep[j].k1, h);
+          if (ty == T_QUAD) thick_quad(p, prep[j].k1, h);
+          else if (ty == T_BEND && prep[j].bfull) bend_full(p, prep[j].bk0, prep[j].bh, h, 0, 0);
+          else if (ty == T_BEND) bend_expanded(p, prep[j].bk0, prep[j].bh, h, prep[j].bk1);
           else drift(p, h, 0, 0);
           const double at = std::fma((double)k, h, pos);
           if (p.state != 1) { found = at; break; }
@@ -1251,7 +1443,7 @@ int xo_track_jacobian(const Element* el, int64_t n_el, const Reference* ref, int
                       double* along) {
   if (!el || !ref || n_el <= 0 || rad_mode < 0 || rad_mode > 1) return -1;
   for (int64_t e = 0; e < n_el; e++)
-    if (el[e].type == T_BEAMBEAM4D) return -1;  // value-only element
+    if (!row_ok(el[e]) || el[e].type == T_BEAMBEAM4D) return -1;  // value-only element
   const RefConst rc = ref_const(*ref);
   std::vector<Prep> prep(n_el);
   for (int64_t e = 0; e < n_el; e++) prep[e] = prepare(el[e], rc);

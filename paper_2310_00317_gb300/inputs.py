@@ -26,7 +26,7 @@ import numpy as np
 ELEMENT_DTYPE = np.dtype([("type", "<i4"), ("order", "<i4"), ("p", "<f8", (48,))], align=True)
 MARKER, DRIFT, MULTIPOLE, CAVITY, DIPEDGE, LINEARMAP, APERTURE = 0, 1, 2, 3, 4, 5, 6
 XYSHIFT, SROTATION, APERTURE_RECT, APERTURE_ELLIPSE = 7, 8, 9, 10
-BEAMBEAM4D, QUAD = 11, 12
+BEAMBEAM4D, QUAD, BEND = 11, 12, 13
 MAX_ORDER = 10
 
 C_LIGHT = 299792458.0
@@ -97,6 +97,13 @@ def s_rotation(angle: float):
 def quadrupole(k1: float, length: float):
     """Thick quadrupole: k1 [m^-2] (> 0 focuses x), length [m]."""
     return _row(QUAD, 0, [k1, length])
+
+
+def bend(k0: float, h: float, length: float, k1: float = 0.0, full: bool = False):
+    """Thick sector bend: field k0 = B / (B rho) [1/m], frame curvature h
+    [1/m] (k0 = h on the design orbit), reference length [m], gradient k1
+    [m^-2] (expanded model only); full=True selects the exact model."""
+    return _row(BEND, 0, [k0, h, length, k1, 1.0 if full else 0.0])
 
 
 def beambeam4d(q_n: float, beta_s: float, sigma_x: float, sigma_y: float, x_c: float = 0.0, y_c: float = 0.0):

@@ -844,6 +844,183 @@ def test_thick_quad_is_the_limit_of_thin_slices(delta):
     assert 3.5 < gaps[0] / gaps[1] < 4.5
 
 
+# --------------------------------------------------------------------------
+# Thick bends
+
+def _bend_matrix_want(h, L, Md56):
+    mp = mpmath.mp
+    mp.dps = 40
+    th = mpmath.mpf(h) * L
+    c, s = mpmath.cos(th), mpmath.sin(th)
+    omc = 2 * mpmath.sin(th / 2) ** 2
+    W = np.eye(6)
+    W[0, 0], W[0, 1], W[1, 0], W[1, 1] = float(c), float(s / h), float(-h * s), float(c)
+    W[0, 5], W[1, 5], W[4, 0], W[4, 1] = float(omc / h), float(s), float(-s), float(-omc / h)
+    W[2, 3] = L
+    W[4, 5] = Md56 - float(L - s / h)
+    return W
+
+
+@pytest.mark.parametrize("full", [False, True])
+@pytest.mark.parametrize("h,L", [(1 / 1.5, 1.2), (1 / 2800.0, 14.3)])
+def test_sector_bend_linear_matrix(full, h, L):
+    """On the design orbit (k0 = h) both models have the textbook sector-bend
+    matrix: cos, sin(theta)/h, -h sin in x; R16 = (1 - cos)/h, R26 = sin,
+    R51 = -sin, R52 = -(1 - cos)/h; R34 = L; and R56 = the drift's R56 less
+    L - sin(theta)/h, the path length saved by the dispersive orbit."""
+    _, M = oracle.track_jacobian(I.table([I.bend(h, h, L, full=full)]), PROTON, np.zeros(6))
+    _, Md = oracle.track_jacobian(I.table([I.drift(L)]), PROTON, np.zeros(6))
+    W = _bend_matrix_want(h, L, Md[4, 5])
+    assert np.max(np.abs(M - W)) < 1e-12, np.max(np.abs(M - W))
+
+
+def test_combined_function_bend_matrix():
+    """Expanded model with a gradient on the design orbit: Kx = h^2 + k1 in
+    x, R11 = cos(w L), R12 = sin(w L)/w, R16 = h (1 - cos)/Kx, R26 = h
+    sin(w L)/w; y defocused by k1 > 0: cosh and sinh."""
+    h, L, k1 = 0.2, 1.5, 0.3
+    _, M = oracle.track_jacobian(I.table([I.bend(h, h, L, k1=k1)]), PROTON, np.zeros(6))
+    w, wy = math.sqrt(h * h + k1), math.sqrt(k1)
+    c, s = math.cos(w * L), math.sin(w * L)
+    want = {(0, 0): c, (0, 1): s / w, (1, 0): -w * s, (1, 1): c, (0, 5): h * (1 - c) / (w * w), (1, 5): h * s / w,
+            (2, 2): math.cosh(wy * L), (2, 3): math.sinh(wy * L) / wy, (3, 2): wy * math.sinh(wy * L),
+            (3, 3): math.cosh(wy * L)}
+    for (i, j), v in want.items():
+        assert abs(M[i, j] - v) < 1e-13, (i, j, M[i, j], v)
+
+
+@pytest.mark.parametrize("full", [False, True])
+def test_bend_symplectic_and_reversible(full):
+    """Field and frame curvature mismatched (k0 != h), off axis and off
+    momentum: M^T J M = J, and the same bend with -L brings the particle back."""
+    k1 = 0.0 if full else 0.12
+    b = I.bend(0.55, 0.5, 1.3, k1=k1, full=full)
+    z0 = np.array([2e-3, 1e-3, -1.5e-3, -2e-4, 0.02, 3e-3])
+    _, M = oracle.track_jacobian(I.table([b]), PROTON, z0)
+    assert np.max(np.abs(M.T @ J6 @ M - J6)) < 1e-12
+    p = I.make_particles(PROTON, [2e-3], [1e-3], [-1.5e-3], [-2e-4], [0.02], [3e-3])
+    o = oracle.track(I.table([b, I.bend(0.55, 0.5, -1.3, k1=k1, full=full)]), PROTON, p, 1)
+    for k, sc in (("x", 2e-3), ("px", 1e-3), ("y", 1.5e-3), ("py", 2e-4), ("zeta", 0.02)):
+        assert abs(o[k][0] - p[k][0]) < 1e-13 * sc + 1e-15, k
+
+
+@pytest.mark.parametrize("delta", [0.0, 1e-5])
+def test_expanded_bend_is_the_limit_of_thin_slices(delta):
+    """N drift-kick-drift slices (exact drifts; thin kicks with knl = (k0, k1)
+    L/N and frame curvature hxl = h L/N) converge to the expanded bend at
+    second order (field and curvature mismatched, with a gradient): the gap
+    falls four-fold from N = 400 to N = 800, zeta included.  Orbits stay at
+    the micron level, where the exact drift's terms beyond the expansion are
+    far below the slicing gap."""
+    k0, h, k1, L = 0.050002, 0.05, 0.03, 2.0
+    rng = np.random.default_rng(67)
+    n = 20
+    p = I.make_particles(PROTON, rng.normal(0, 1e-5, n), rng.normal(0, 5e-7, n), rng.normal(0, 1e-5, n),
+                         rng.normal(0, 5e-7, n), np.zeros(n), np.full(n, delta))
+    a = oracle.track(I.table([I.bend(k0, h, L, k1=k1)]), PROTON, p, 1)
+    gaps = []
+    for N in (400, 800):
+        ds = L / N
+        kick = I.multipole(knl=[k0 * ds, k1 * ds], hxl=h * ds, lrad=ds)
+        b = oracle.track(I.table([I.drift(ds / 2), kick, I.drift(ds / 2)] * N), PROTON, p, 1)
+        dz = np.max(np.abs(b["zeta"] - p["zeta"]))
+        sc = {k: np.max(np.abs(b[k] - p[k])) + np.max(np.abs(p[k])) for k in ("x", "px", "y", "py")}
+        sc["zeta"] = dz
+        gaps.append(max(np.max(np.abs(a[k] - b[k])) / sc[k] for k in sc))
+    assert gaps[1] < 1e-5
+    assert 3.5 < gaps[0] / gaps[1] < 4.5
+
+
+def _bend_by_geometry(k0, h, L, x, px, y, py, delta, zeta):
+    """Exit coordinates of the full bend by plane geometry in 40 digits: the
+    particle's circle (centre P0 + (1/k0) (-pz, px), radius p_h / k0) is cut
+    with the exit ray of the sector, the exit momentum is the circle's
+    tangent there, and the arc length is radius times the swept angle."""
+    mp = mpmath.mp
+    mp.dps = 40
+    m0, _, p0c = PROTON
+    b0 = mpmath.mpf(p0c) / mpmath.sqrt(mpmath.mpf(p0c) ** 2 + mpmath.mpf(m0) ** 2)
+    opd = 1 + mpmath.mpf(delta)
+    g0 = 1 / mpmath.sqrt(1 - b0 * b0)
+    E = mpmath.sqrt((opd * p0c) ** 2 + mpmath.mpf(m0) ** 2)
+    beta = opd * p0c / E
+    rv0v = b0 / beta
+    k0, h, L, x, px, y, py = [mpmath.mpf(v) for v in (k0, h, L, x, px, y, py)]
+    pz = mpmath.sqrt(opd ** 2 - px ** 2 - py ** 2)
+    ph = mpmath.sqrt(px ** 2 + pz ** 2)
+    R = 1 / h
+    P0 = mpmath.matrix([R + x, 0])
+    th = h * L
+    e = mpmath.matrix([mpmath.cos(th), mpmath.sin(th)])
+    et = mpmath.matrix([-mpmath.sin(th), mpmath.cos(th)])
+    Cp = P0 + mpmath.matrix([-pz, px]) / k0
+    rho = ph / k0
+    ec = e[0] * Cp[0] + e[1] * Cp[1]
+    disc = mpmath.sqrt(ec ** 2 - (Cp[0] ** 2 + Cp[1] ** 2) + rho ** 2)
+    r = min((ec - disc, ec + disc), key=lambda v: abs(v - (R + x)))
+    P1 = r * e
+    a0, a1 = P0 - Cp, P1 - Cp
+    v1 = mpmath.matrix([-a1[1], a1[0]]) * (ph / rho)  # counter-clockwise tangent
+    phi = mpmath.atan2(a0[0] * a1[1] - a0[1] * a1[0], a0[0] * a1[0] + a0[1] * a1[1])
+    lh = rho * phi
+    out = dict(x=r - R, px=v1[0] * e[0] + v1[1] * e[1], y=y + py * lh / ph,
+               zeta=mpmath.mpf(zeta) + L - rv0v * opd * lh / ph, pzf=v1[0] * et[0] + v1[1] * et[1])
+    return {k: float(v) for k, v in out.items()}
+
+
+@pytest.mark.parametrize("h,L,k0", [(1 / 1.5, 1.2, 1 / 1.5), (1 / 1.5, 1.2, 1.1 / 1.5), (0.05, 2.0, 0.04),
+                                    (1 / 2800.0, 14.3, 1 / 2800.0)])
+def test_full_bend_against_plane_geometry(h, L, k0):
+    """The full model against the circle-and-ray construction: a small-ring
+    dipole (theta = 0.8: the trigonometric branch and two halvings in
+    asin(u)/u), a mismatched field, a weak field in a curved frame and an
+    LHC-like dipole, over random particles off axis and off momentum."""
+    rng = np.random.default_rng(71)
+    n = 12
+    xs, pxs = rng.normal(0, 2e-3, n), rng.normal(0, 1e-3, n)
+    ys, pys = rng.normal(0, 2e-3, n), rng.normal(0, 1e-3, n)
+    ds_ = rng.normal(0, 2e-3, n)
+    p = I.make_particles(PROTON, xs, pxs, ys, pys, np.full(n, 0.01), ds_)
+    o = oracle.track(I.table([I.bend(k0, h, L, full=True)]), PROTON, p, 1)
+    assert np.all(o["state"] == 1)
+    for i in range(n):
+        g = _bend_by_geometry(k0, h, L, xs[i], pxs[i], ys[i], pys[i], p["delta"][i], 0.01)
+        for k in ("x", "px", "y"):
+            assert abs(o[k][i] - g[k]) < 2e-15 * L + 1e-15 * abs(g[k]), (k, i, o[k][i], g[k])
+        assert abs(o["zeta"][i] - g["zeta"]) < 1e-14 * L, (i, o["zeta"][i], g["zeta"])
+
+
+def test_full_bend_without_field_or_curvature_is_the_exact_drift():
+    rng = np.random.default_rng(73)
+    n = 10
+    p = I.make_particles(PROTON, rng.normal(0, 2e-3, n), rng.normal(0, 1e-3, n), rng.normal(0, 2e-3, n),
+                         rng.normal(0, 1e-3, n), np.zeros(n), rng.normal(0, 1e-3, n))
+    a = oracle.track(I.table([I.bend(0.0, 0.0, 3.0, full=True)]), PROTON, p, 1)
+    b = oracle.track(I.table([I.drift(3.0)]), PROTON, p, 1)
+    for k in ("x", "px", "y", "py"):
+        assert np.max(np.abs(a[k] - b[k])) < 1e-17 + 1e-15 * np.max(np.abs(b[k]))
+    assert np.max(np.abs(a["zeta"] - b["zeta"])) < 1e-15
+
+
+def test_full_and_expanded_bends_agree_to_first_order():
+    """The models differ by the Hamiltonian terms the expansion drops, the
+    leading one h x (px^2 + py^2) / (2 (1+delta)), of third order: the maps
+    then differ at second order in the amplitudes, and halving them cuts the
+    gap four-fold."""
+    h, L = 0.5, 1.0
+    gaps = []
+    for amp in (2e-3, 1e-3):
+        rng = np.random.default_rng(79)
+        n = 20
+        p = I.make_particles(PROTON, rng.normal(0, amp, n), rng.normal(0, amp, n), rng.normal(0, amp, n),
+                             rng.normal(0, amp, n), np.zeros(n), rng.normal(0, amp, n))
+        a = oracle.track(I.table([I.bend(h, h, L, full=True)]), PROTON, p, 1)
+        b = oracle.track(I.table([I.bend(h, h, L)]), PROTON, p, 1)
+        gaps.append(max(np.max(np.abs(a[k] - b[k])) for k in ("x", "px", "y", "py")))
+    assert gaps[0] < 1e-5
+    assert 3.6 < gaps[0] / gaps[1] < 4.4
+
+
 def test_segment_resume_bitwise():
     """track(a) then track(b) from turn a equals track(a+b), radiation included."""
     el, ref, _ = I.lepton_ring(n_cells=4, E0=5e9, v_total=30e6)
