@@ -121,6 +121,25 @@ extern "C" {
                            (px^2 + py^2) / (2 rvv (1+delta)^2) over the body,
                            in closed form.  Delta and ptau are unchanged.
                            Loss refinement steps through it like a drift.    */
+#define XT_BEND 13       /* Thick sector bend (section "Lattice modelling and
+                           single particle tracking": a full map for small
+                           machines, an expanded one for large machines and
+                           small bending angles).  p[0] = k0 = B / (B rho)
+                           [1/m], p[1] = frame curvature h [1/m] (k0 = h on
+                           the design orbit; h = 0 is a straight frame),
+                           p[2] = reference length L [m] (finite, >= 0),
+                           p[3] = gradient k1 [m^-2] (expanded model only),
+                           p[4] = model: 0 expanded, 1 full (k1 must be 0).
+                           Expanded: the exact flow of
+                           (px^2 + py^2) / (2 (1+delta)) - h x (1+delta)
+                           + k0 (x + h x^2 / 2) + k1 (x^2 - y^2) / 2, with
+                           zeta' = 1 - (1/rvv)(1 + h x + (px^2 + py^2) /
+                           (2 (1+delta)^2)).  Full: the exact motion in the
+                           uniform field through the sector (arc of a circle
+                           in the horizontal plane, straight in y); lost with
+                           state -2 if the particle cannot reach the exit
+                           plane.  Delta and ptau are unchanged.  Loss
+                           refinement steps through it like a drift.        */
 
 #define XT_MAX_ORDER 10
 #define XT_NPARAM 48

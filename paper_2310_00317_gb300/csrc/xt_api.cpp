@@ -282,7 +282,7 @@ int xt_tracker_create(const xt_element* table, int64_t n, const xt_reference* re
   e = device_smem_optin(&t->smem_max);
   if (e) return cuda_fail((cudaError_t)e, "device attribute");
   {
-    double tab[60];
+    double tab[XT_SPECIAL_N];
     special_table(tab);
     e = upload_special_table(tab);
     if (e) return cuda_fail((cudaError_t)e, "beam-beam constant table");
@@ -530,7 +530,8 @@ static int build_refine_tables(xt_tracker* t, int n_angles) {
     frame[4 * i + 1] = std::sin(th);
     frame[4 * i + 2] = fdx;
     frame[4 * i + 3] = fdy;
-    spos[i + 1] = spos[i] + (e.type == XT_DRIFT ? e.p[0] : (e.type == XT_QUAD ? e.p[1] : 0.0));
+    spos[i + 1] = spos[i] + (e.type == XT_DRIFT ? e.p[0]
+                             : (e.type == XT_QUAD ? e.p[1] : (e.type == XT_BEND ? e.p[2] : 0.0)));
     if (e.type == XT_XYSHIFT) {
       const double c = std::cos(th), sn = std::sin(th);
       fdx = fdx + (c * e.p[0] - sn * e.p[1]);

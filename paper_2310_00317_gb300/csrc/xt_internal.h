@@ -28,6 +28,8 @@ static_assert(sizeof(RecHdr) == 16, "record header is 16 bytes");
 enum : uint16_t { REC_CURV = 1, REC_RAD = 2, REC_PURE = 4, REC_BEND = 8 };
 // thick quadrupole: x is the focusing plane (k1 >= 0)
 enum : uint16_t { REC_QF = 1 };
+// thick bend: the full (exact) model
+enum : uint16_t { REC_BFULL = 1 };
 // REC_PURE: knl0 == ksl0 == 0 and hxl == 0.  REC_BEND: hxl != 0, hxl == knl0,
 // ksl0 == 0.  Without radiation these multipoles add the last Horner step
 // straight into px, py (and a bend's -knl0 + hxl (1+delta) becomes hxl delta).
@@ -140,8 +142,12 @@ struct RefineArgs {
 
 int launch_refine(const RefineArgs& a, void* stream);
 
-// Beam-beam constant table (60 doubles, see special_table) for the current
-// device's constant memory.
+// Constant table of the special functions (beam-beam kick, thick elements;
+// XT_SPECIAL_N doubles, see special_table) for the current device's
+// constant memory.
+#define XT_SPECIAL_N 74
+#define XT_SPECIAL_FACT 41  // 1/n!, n = 0..18
+#define XT_SPECIAL_ASIN 60  // asin(v)/v series coefficients, n = 0..13
 void special_table(double* out);
 int upload_special_table(const double* tab);
 

@@ -56,6 +56,11 @@ int64_t flops_of_row(const xt_element& e, int rad_mode) {
     // |k1|/(1+delta), a, cos, sin(a)/a, cosh and sinh(a)/a (13); the 4x4 map (18);
     // the path-length integral (36) and zeta (9)
     case XT_QUAD: return (e.p[1] == 0.0) ? 0 : 76;
+    // expanded: two sets of oscillator functions (20), the 4x4 map (18), the
+    // integrals (50) and zeta (10); full: the sector functions (10), pz and
+    // the exit momentum (20), x (10), the chord and the arc length (45), y and
+    // zeta (8)
+    case XT_BEND: return (e.p[4] != 0.0) ? 93 : 98;
     case XT_BEAMBEAM4D: {
       // round: the field and the kick; else two 40-term w(z) (~300 each), e^x and the rest
       const double sx2 = e.p[2] * e.p[2], sy2 = e.p[3] * e.p[3];
@@ -195,6 +200,20 @@ int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice*
         if (k1 >= 0.0) flags |= REC_QF;
         break;
       }
+      case XT_BEND: {
+        const double k0 = e.p[0], h = e.p[1], L = e.p[2], k1 = e.p[3], model = e.p[4];
+        if (!std::isfinite(k0) || !std::isfinite(h) || !std::isfinite(k1) || !std::isfinite(L) || !(L >= 0.0)) {
+          *err = "element " + std::to_string(i) + ": thick bend needs finite k0, h, k1 and a length L >= 0";
+          return XT_ERR_INVALID;
+        }
+        if (!(model == 0.0 || (model == 1.0 && k1 == 0.0))) {
+          *err = "element " + std::to_string(i) + ": thick bend model must be 0 (expanded) or 1 (full, k1 = 0)";
+          return XT_ERR_INVALID;
+        }
+        prm = {k0, h, L, k1};
+        if (model == 1.0) flags |= REC_BFULL;
+        break;
+      }
       case XT_APERTURE_ELLIPSE:
         if (!(e.p[0] > 0.0 && e.p[1] > 0.0)) {
           *err = "element " + std::to_string(i) + ": elliptic aperture needs a > 0 and b > 0";
@@ -265,7 +284,10 @@ SinTab sin_table() {
 // p(Z) in Weideman's rational expansion of the Faddeeva function
 // (J. A. C. Weideman, SIAM J. Numer. Anal. 31 (1994) 1497; N = 40 terms,
 // L = (N / sqrt 2)^(1/2), the cosine transform of e^(-t^2)(L^2 + t^2) at
-// t = L tan(theta/2) by a plain DFT), [41..59] 1/n! for n = 0..18.
+// t = L tan(theta/2) by a plain DFT), [41..59] 1/n! for n = 0..18; and for
+// the thick bend's arc length [60..73] the coefficients a_n of
+// asin(v)/v = sum a_n v^(2n), a_n = (2n)! / (4^n n!^2 (2n+1)) from the
+// running product t_n = t_(n-1) (2n-1) / (2n), a_n = t_n / (2n+1).
 void special_table(double* out) {
   const int N = 40, M = 2 * N, M2 = 2 * M;
   const double L = std::sqrt((double)N / std::sqrt(2.0));
@@ -288,7 +310,12 @@ void special_table(double* out) {
   double fact = 1.0;
   for (int n = 0; n <= 18; n++) {
     if (n > 0) fact = fact * (double)n;
-    out[41 + n] = 1.0 / fact;
+    out[XT_SPECIAL_FACT + n] = 1.0 / fact;
+  }
+  double t = 1.0;
+  for (int n = 0; n < 14; n++) {
+    if (n > 0) t = (t * (double)(2 * n - 1)) / (double)(2 * n);
+    out[XT_SPECIAL_ASIN + n] = t / (double)(2 * n + 1);
   }
 }
 

@@ -333,8 +333,9 @@ __device__ __forceinline__ int drift_warp(Part& p, const double* prm, bool alive
 // ---------------------------------------------------------------------------
 // 4D beam-beam lens (section "Beam-beam interactions"): the transverse kick of
 // a frozen Gaussian bunch.  Constant table from the host: [0] L, [1..40]
-// Weideman's coefficients of the Faddeeva expansion, [41..59] 1/n!.
-__constant__ double c_special[60];
+// Weideman's coefficients of the Faddeeva expansion, [41..59] 1/n!, and
+// [60..73] the series coefficients of asin(v)/v (thick bend).
+__constant__ double c_special[XT_SPECIAL_N];
 
 // e^x: Cody-Waite reduction x = k ln2 + r (ln 2 as a 20-bit head, so that
 // k * head is exact, plus a tail), e^r by its Taylor series to r^13 on
@@ -422,6 +423,141 @@ __device__ __forceinline__ void bb_field(double x, double y, const double* prm, 
   }
   *fx = copysign(gx, x);
   *fy = copysign(gy, y);
+}
+
+// Entire functions of z (either sign) with a = sqrt|z|: C = cos a,
+// S = sin(a)/a, S2 = (1 - C)/z, S3 = (1 - S)/z for z > 0 (cosh and sinh for
+// z < 0).  Series in z below |z| = 1/4 (1/n! from the special table), else
+// from trig_cw or two exponentials.
+__device__ __forceinline__ void osc_funcs(double z, const SinTab& sn, double* C, double* S, double* S2,
+                                          double* S3) {
+  if (fabs(z) < 0.25) {
+    const double mz = -z;
+    const double* f = c_special + XT_SPECIAL_FACT;
+    double c = f[16], s = f[17], s2 = f[16], s3 = f[17];
+#pragma unroll
+    for (int n = 7; n >= 0; n--) {
+      c = fma(c, mz, f[2 * n]);
+      s = fma(s, mz, f[2 * n + 1]);
+    }
+#pragma unroll
+    for (int n = 6; n >= 0; n--) {
+      s2 = fma(s2, mz, f[2 * n + 2]);
+      s3 = fma(s3, mz, f[2 * n + 3]);
+    }
+    *C = c; *S = s; *S2 = s2; *S3 = s3;
+    return;
+  }
+  if (z > 0.0) {
+    const double a = sqrt(z);
+    *C = trig_cw(a, sn, 1);
+    *S = trig_cw(a, sn, 0) / a;
+  } else {
+    const double a = sqrt(-z);
+    const double e = exp_cw(a), ei = exp_cw(-a);
+    *C = 0.5 * (e + ei);
+    *S = (0.5 * (e - ei)) / a;
+  }
+  *S2 = (1.0 - *C) / z;
+  *S3 = (1.0 - *S) / z;
+}
+
+// asin(u)/u for |u| <= 1: the angle is halved, asin u = 2 asin v with
+// v = u / sqrt(2 (1 + sqrt(1 - u^2))), until |v| < 1/4 (at most three times
+// for |u| <= 1; the loop stops at four), then the series from the table.
+__device__ __forceinline__ double asin_over(double u) {
+  double v = u, m = 1.0;
+  for (int k = 0; k < 4 && fabs(v) >= 0.25; k++) {
+    v = v / sqrt(2.0 * (1.0 + sqrt(1.0 - v * v)));
+    m = m + m;
+  }
+  const double* a = c_special + XT_SPECIAL_ASIN;
+  const double z = v * v;
+  double s = a[13];
+#pragma unroll
+  for (int n = 12; n >= 0; n--) s = fma(s, z, a[n]);
+  if (m == 1.0) return s;
+  return (m * (v / u)) * s;
+}
+
+// Thick bend, expanded model (section "Lattice modelling and single particle
+// tracking": the model for large machines and small bending angles): the
+// exact flow of
+//   (px^2 + py^2) / (2 (1+delta)) - h x (1+delta) + k0 (x + h x^2 / 2) + k1 (x^2 - y^2) / 2,
+// the curved-frame Hamiltonian with its square root expanded to second order
+// in px, py.  x is a driven oscillator, px' = F - Kx x, F = h (1+delta) - k0,
+// Kx = k0 h + k1; py' = k1 y; zeta' = 1 - (1/rvv)(1 + h x + (px^2 + py^2) /
+// (2 (1+delta)^2)), integrated in closed form.  L of either sign.
+__device__ __forceinline__ void bend_expanded(Part& p, double k0, double h, double L, double k1,
+                                              const SinTab& sn) {
+  const double Kx = k0 * h + k1, L2 = L * L;
+  const double zx = (Kx * p.rpp) * L2;
+  const double zy = ((-k1) * p.rpp) * L2;
+  double C, S, S2, S3, Cy, Sy, S2y, S3y;
+  osc_funcs(zx, sn, &C, &S, &S2, &S3);
+  osc_funcs(zy, sn, &Cy, &Sy, &S2y, &S3y);
+  const double x0 = p.x, px0 = p.px, y0 = p.y, py0 = p.py;
+  const double F = fma(h, p.delta, h - k0);  // h (1+delta) - k0
+  const double G = fma(-Kx, x0, F);
+  const double Gy = k1 * y0;
+  const double Lr = L * p.rpp;
+  p.x = fma(C, x0, fma(Lr * S, px0, ((L * Lr) * S2) * F));
+  p.px = fma(C, px0, (L * S) * G);
+  p.y = fma(Cy, y0, (Lr * Sy) * py0);
+  p.py = fma(Cy, py0, (L * Sy) * Gy);
+  // integrals of x and of px^2 + py^2 over the body; (1 - C S)/z = S3 + S S2
+  const double Ix = fma(L * S, x0, fma((L * Lr) * S2, px0, ((L2 * Lr) * S3) * F));
+  const double hL = 0.5 * L, hL3 = 0.5 * (L2 * L);
+  double I = (hL * fma(C, S, 1.0)) * (px0 * px0);
+  I = fma(L2 * (S * S), px0 * G, I);
+  I = fma(hL3 * fma(S, S2, S3), G * G, I);
+  I = fma(hL * fma(Cy, Sy, 1.0), py0 * py0, I);
+  I = fma(L2 * (Sy * Sy), py0 * Gy, I);
+  I = fma(hL3 * fma(Sy, S2y, S3y), Gy * Gy, I);
+  p.zeta = p.zeta + fma(L * (p.delta - p.epm1), p.rpp, -(p.rv0v * fma(h, Ix, (0.5 * (p.rpp * p.rpp)) * I)));
+}
+
+// Thick bend, full model (section "Lattice modelling and single particle
+// tracking": the model for small machines): exact motion in a uniform field
+// k0 through a sector of curvature h and length L (either sign).  From the
+// invariants pX + k0 Z and pZ - k0 X of circular motion: at the exit plane
+// px' = B - k0 (1/h + x) sin, x' = x cos - (1 - cos)/h + (1/h + x) sin
+// (px' + B)/(pz' + Q), B = px cos + pz sin, Q = pz cos - px sin, with
+// sin/h = L S and (1 - cos)/h = h L^2 S2 at z = (h L)^2; the horizontal arc
+// length is chord * asin(u)/u, u = k0 chord / (2 p_h), and y, zeta follow it.
+// Returns 1, or -2 (lost) if pz or pz' is not real or the exit plane is not
+// reached.
+__device__ __forceinline__ int bend_full(Part& p, double k0, double h, double L, const SinTab& sn) {
+  const double th = h * L, L2 = L * L;
+  double C, S, S2, S3;
+  osc_funcs(th * th, sn, &C, &S, &S2, &S3);
+  const double snt = th * S, Sh = L * S, Ch = (h * L2) * S2, D2 = 2.0 * (L2 * S2);
+  const double u = fma(-p.px, p.px, fma(-p.py, p.py, p.dm1));  // pz^2 - 1
+  if (!(u > -1.0 && u < INFINITY)) return -2;
+  const double pz = sqrt(1.0 + u);
+  const double ph2 = 1.0 + fma(-p.py, p.py, p.dm1);
+  const double B = fma(p.px, C, pz * snt);
+  const double Q = fma(pz, C, -(p.px * snt));
+  const double r0s = fma(p.x, snt, Sh);  // (1/h + x) sin(theta)
+  const double A = fma(-k0, r0s, B);     // px at the exit plane
+  const double pzf2 = fma(-A, A, ph2);
+  if (!(pzf2 > 0.0)) return -2;
+  const double pzf = sqrt(pzf2);
+  const double den = pzf + Q;
+  if (!(den > 0.0)) return -2;
+  const double xf = fma(p.x, C, -Ch) + r0s * ((A + B) / den);
+  const double dxf = xf - p.x;
+  const double chord = sqrt(fma(dxf, dxf, (fma(h, p.x, 1.0) * fma(h, xf, 1.0)) * D2));
+  const double ph = sqrt(ph2);
+  const double uu = (k0 * chord) / (ph + ph);
+  if (!(fabs(uu) <= 1.0)) return -2;
+  const double lh = ((L >= 0.0) ? chord : -chord) * asin_over(uu);
+  const double lr = lh / ph;
+  p.x = xf;
+  p.px = A;
+  p.y = fma(p.py, lr, p.y);
+  p.zeta = p.zeta + fma(-p.ep, lr, L);
+  return 1;
 }
 
 // Thick quadrupole (section "Lattice modelling and single particle tracking"):
@@ -624,6 +760,10 @@ __device__ __forceinline__ int element(Part& p, uint32_t type, uint32_t order, u
       return 1;
     case XT_QUAD:  // prm = |k1|, L; flags = REC_QF when x is the focusing plane
       thick_quad(p, prm[0], prm[1], (flags & REC_QF) != 0, sn);
+      return 1;
+    case XT_BEND:  // prm = k0, h, L, k1; flags = REC_BFULL for the full model
+      if (flags & REC_BFULL) return bend_full(p, prm[0], prm[1], prm[2], sn);
+      bend_expanded(p, prm[0], prm[1], prm[2], prm[3], sn);
       return 1;
     case XT_LINEARMAP: {
       const double v[6] = {p.x, p.px, p.y, p.py, p.zeta, p.ptau};
@@ -947,6 +1087,10 @@ __device__ __forceinline__ bool inverse_record(Part& p, uint32_t type, uint32_t 
     case XT_QUAD:
       thick_quad(p, prm[0], -prm[1], (flags & REC_QF) != 0, sn);
       return true;
+    case XT_BEND:
+      if (flags & REC_BFULL) return bend_full(p, prm[0], prm[1], -prm[2], sn) == 1;
+      bend_expanded(p, prm[0], prm[1], -prm[2], prm[3], sn);
+      return true;
     case XT_LINEARMAP: return false;
     case XT_BEAMBEAM4D: {  // x, y unchanged by the kick: take the same kick back
       double fx, fy;
@@ -1032,18 +1176,19 @@ __global__ void __launch_bounds__(128) refine_kernel(RefineArgs a) {
     const uint4 hv = *(const uint4*)(a.lat + off);
     const uint32_t type = hv.x & 0xFFFFu;
     const double* prm = (const double*)(a.lat + off + 16);
-    // drifts and thick quadrupoles in steps of at most ds (the quadrupole's
-    // flow composes exactly, so its steps give the same map as one pass)
-    const bool quad = type == XT_QUAD && prm[1] > 0.0;
-    if ((type == XT_DRIFT && prm[0] > 0.0) || quad) {
-      const double L = quad ? prm[1] : prm[0];
+    // drifts, thick quadrupoles and thick bends in steps of at most ds (the
+    // thick maps are flows: their steps compose to the same map as one pass)
+    const double L = (type == XT_DRIFT) ? prm[0] : (type == XT_QUAD) ? prm[1] : (type == XT_BEND) ? prm[2] : 0.0;
+    if ((type == XT_DRIFT || type == XT_QUAD || type == XT_BEND) && L > 0.0) {
       const int64_t ns = (int64_t)ceil(L / a.ds);
       const double h = L / (double)ns;
       const double c = a.frame[4 * j], sn = a.frame[4 * j + 1], dx = a.frame[4 * j + 2], dy = a.frame[4 * j + 3];
-      const bool qf = (hv.y & REC_QF) != 0;
+      const uint32_t fl = hv.y & 0xFFFFu;
       for (int64_t k = 1; k <= ns; k++) {
         bool ok = true;
-        if (quad) thick_quad(p, prm[0], h, qf, a.sn);
+        if (type == XT_QUAD) thick_quad(p, prm[0], h, (fl & REC_QF) != 0, a.sn);
+        else if (type == XT_BEND && (fl & REC_BFULL)) ok = bend_full(p, prm[0], prm[1], h, a.sn) == 1;
+        else if (type == XT_BEND) bend_expanded(p, prm[0], prm[1], h, prm[3], a.sn);
         else ok = drift_lane(p, h);
         const double at = fma((double)k, h, pos);
         if (!ok) { found = at; hit = true; break; }
@@ -1056,8 +1201,10 @@ __global__ void __launch_bounds__(128) refine_kernel(RefineArgs a) {
       pos = pos + L;
     } else if (type == XT_DRIFT) {
       if (!drift_lane(p, prm[0])) { found = pos; hit = true; break; }
-    } else {
-      element<XT_RAD_OFF>(p, type, hv.x >> 16, hv.y & 0xFFFFu, hv.z, prm, a.ref, a.sn, rc, 0, 0);
+    } else if (element<XT_RAD_OFF>(p, type, hv.x >> 16, hv.y & 0xFFFFu, hv.z, prm, a.ref, a.sn, rc, 0, 0) != 1) {
+      found = pos;
+      hit = true;
+      break;
     }
   }
   if (!hit) found = a.spos[e];
@@ -1316,7 +1463,7 @@ int launch_refine(const RefineArgs& a, void* stream) {
 }
 
 int upload_special_table(const double* tab) {
-  return (int)cudaMemcpyToSymbol(c_special, tab, 60 * sizeof(double));
+  return (int)cudaMemcpyToSymbol(c_special, tab, XT_SPECIAL_N * sizeof(double));
 }
 
 int launch_set_int(int32_t* dst, int32_t value, void* stream) {

@@ -221,6 +221,59 @@ def test_refine_losses_through_thick_quadrupoles_bitwise():
     assert inside > 20
 
 
+def bend_ring(n_cells=8, aperture=0.02):
+    """A small ring (bending radius 1.5 m): full-model sector bends of 0.6 rad
+    (the trigonometric branch and angle halvings in the arc length), expanded
+    combined-function bends with the field 0.2 % off the frame curvature,
+    thick quadrupoles, sextupoles, RF and circular apertures."""
+    h = 1 / 1.5
+    rows = [I.cavity(2e6, 400e6, 180.0)]
+    for c in range(n_cells):
+        rows += [I.quadrupole(0.8, 0.3), I.drift(0.3), I.bend(h, h, 0.9, full=True), I.drift(0.3)]
+        rows += [I.multipole(knl=[0.0, 0.0, 0.5])]
+        rows += [I.quadrupole(-0.8, 0.3), I.drift(0.3), I.bend(h * 1.002, h, 0.9, k1=-0.05), I.drift(0.3),
+                 I.aperture(aperture)]
+    return rows
+
+
+def test_thick_bend_ring_bitwise():
+    """2,000 particles (plus a few at steep angles) for 100 turns through
+    full and expanded bends, bit for bit with the oracle, losses included."""
+    el = I.table(bend_ring())
+    p = random_particles(PROTON, 2000, 59, sx=5e-3, spx=2.5e-3, sd=1e-3)
+    for i, (px, py) in enumerate([(0.9, 0.0), (-0.9, 0.1), (0.3, 0.95), (0.99, 0.0)]):
+        p["px"][i], p["py"][i] = px, py
+    g, o = gpu_track(el, PROTON, p, 100), oracle.track(el, PROTON, p, 100)
+    assert_same(g, o)
+    assert 200 < np.sum(o["state"] == 1) < 1900
+
+
+def test_refine_losses_through_thick_bends_bitwise():
+    """Refinement stepping through full and expanded bend bodies and
+    backtracking through them with -L, GPU against oracle bit for bit; some
+    refined losses lie inside a bend."""
+    rows = bend_ring(n_cells=6, aperture=0.012)
+    el = I.table(rows)
+    p = random_particles(PROTON, 3000, 61, sx=5e-3, spx=2.5e-3, sd=1e-3)
+    o = oracle.track(el, PROTON, p, 20)
+    assert np.sum(o["state"] == 0) > 500
+    s_o = oracle.refine_losses(el, PROTON, o, 0.01, 128)
+    tr = xtgb.Tracker(el, PROTON)
+    s_g = tr.refine_losses(xtgb.Particles.from_numpy(o), 0.01, 128).cpu().numpy()
+    tr.close()
+    same = (s_g == s_o) | (np.isnan(s_g) & np.isnan(s_o))
+    assert np.all(same), np.flatnonzero(~same)[:5]
+    pos, body = 0.0, []
+    for r in rows:
+        t = int(r["type"])
+        L = float(r["p"][0]) if t == I.DRIFT else float(r["p"][1]) if t == I.QUAD else float(r["p"][2]) if t == I.BEND else 0.0
+        if t == I.BEND:
+            body.append((pos, pos + L))
+        pos += L
+    lost = s_o[o["state"] == 0]
+    assert sum(np.sum((lost > a + 1e-9) & (lost < b - 1e-9)) for a, b in body) > 20
+
+
 def bb_lens(qN, beta_s, sx, sy, xc=0.0, yc=0.0):
     return I.beambeam4d(qN, beta_s, sx, sy, xc, yc)
 
