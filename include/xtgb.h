@@ -267,6 +267,20 @@ int xt_sync_status(xt_tracker* tr, void* stream);
 int xt_cancel(xt_tracker* tr);
 int xt_reset_cancel(xt_tracker* tr);
 
+/* Monitor: one pass of the table (turn number `turn`, which keys the quantum
+   radiation's random numbers) for the particles in device buffers, with their
+   state written after every table row: out (device, n_elements * 8 * n
+   doubles, caller-owned) receives for row i, coordinate c of (x, px, y, py,
+   zeta, ptau, delta, state) and particle j the value out[(i * 8 + c) * n + j]
+   (the state as a double: 1 alive, else the loss code).  The particles are
+   advanced exactly as one turn of xt_track would advance them (bit for bit),
+   under the tracker's radiation mode.  It serves the lattice functions along
+   the line and the energy-loss compensation of section "Twiss module"; at
+   most XT_MONITOR_MAX_PARTICLES particles (else XT_ERR_INVALID).  Async on
+   `stream`.                                                                */
+#define XT_MONITOR_MAX_PARTICLES 4096
+int xt_track_monitor(xt_tracker* tr, const xt_particles* particles, int64_t turn, double* out, void* stream);
+
 /* Algorithmic FP64 flops of one traversal of every table row, for roofline
    accounting (FMA = 2, add or multiply = 1, square root, divide and sine = 1,
    compares 0), under the tracker's radiation mode: flops_per_element[i] for

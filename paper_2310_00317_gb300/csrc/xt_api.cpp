@@ -113,6 +113,8 @@ struct xt_tracker {
   int refine_angles = 0;
   uint8_t* d_refine = nullptr;
   RefineArgs refine_tab;  // table pointers into d_refine
+  // per-row record offsets for the monitor, uploaded on first use
+  int32_t* d_rowoff = nullptr;
 };
 
 static int prof_pair(xt_tracker* t, cudaEvent_t* a, cudaEvent_t* b) {
@@ -329,6 +331,7 @@ void xt_tracker_destroy(xt_tracker* t) {
   cudaFree(t->d_counts);
   cudaFree(t->d_stage);
   cudaFree(t->d_refine);
+  cudaFree(t->d_rowoff);
   if (t->h_cancel) cudaFreeHost(t->h_cancel);
   for (auto& pr : t->ev) {
     cudaEventDestroy(pr.first);
@@ -632,6 +635,42 @@ int xt_refine_losses(xt_tracker* t, const xt_particles* p, double ds, int32_t n_
   a.n = p->n;
   int e = launch_refine(a, stream);
   if (e) return cuda_fail((cudaError_t)e, "refinement launch");
+  return XT_OK;
+}
+
+int xt_track_monitor(xt_tracker* t, const xt_particles* p, int64_t turn, double* out, void* stream) {
+  g_err.clear();
+  if (!t || !particles_ok(p) || !out) return fail(XT_ERR_INVALID, "null tracker, particles or out");
+  if (turn < 0 || turn > 0x7ffffffe) return fail(XT_ERR_INVALID, "turn outside 0..2^31-2");
+  if (p->n > XT_MONITOR_MAX_PARTICLES) return fail(XT_ERR_INVALID, "the monitor takes at most 4096 particles");
+  const int64_t n_el = t->lat.n_el;
+  if (!t->d_rowoff) {
+    int rc = dev_alloc(&t->d_rowoff, (size_t)n_el);
+    if (rc) return rc;
+    CK(cudaMemcpy(t->d_rowoff, t->lat.row_rec.data(), (size_t)n_el * 4, cudaMemcpyHostToDevice));
+  }
+  if (p->n == 0) return XT_OK;
+  MonitorArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.lat = t->d_lat;
+  a.row_off = t->d_rowoff;
+  a.n_el = (int32_t)n_el;
+  a.turn = (int32_t)turn;
+  a.n = p->n;
+  a.x = p->x; a.px = p->px; a.y = p->y; a.py = p->py; a.zeta = p->zeta;
+  a.delta = p->delta; a.ptau = p->ptau; a.rpp = p->rpp; a.rvv = p->rvv;
+  a.state = p->state; a.at_turn = p->at_turn; a.at_element = p->at_element;
+  a.pid = p->particle_id;
+  a.out = out;
+  a.seed = t->opt.seed;
+  a.spec_xi = t->d_spec_xi;
+  a.spec_F = t->d_spec_F;
+  a.spec_guide = t->d_spec_guide;
+  a.spec_k = t->spec_k;
+  a.ref = t->ref;
+  a.sn = t->sn;
+  int e = launch_monitor(a, t->opt.radiation, stream);
+  if (e) return cuda_fail((cudaError_t)e, "monitor launch");
   return XT_OK;
 }
 

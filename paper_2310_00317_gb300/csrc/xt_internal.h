@@ -116,6 +116,29 @@ struct TrackArgs {
   SinTab sn;
 };
 
+// One pass of the table for a few particles with their state recorded after
+// every table row (one thread per particle; records read from global memory).
+struct MonitorArgs {
+  const uint8_t* lat;
+  const int32_t* row_off;  // per table row: record offset in lat, -1 if none
+  int32_t n_el;
+  int32_t turn;
+  int64_t n;
+  double *x, *px, *y, *py, *zeta, *delta, *ptau, *rpp, *rvv;
+  int32_t *state, *at_turn, *at_element;
+  const int64_t* pid;
+  double* out;  // [row][8][n]: x, px, y, py, zeta, ptau, delta, state
+  uint64_t seed;
+  const double* spec_xi;
+  const double* spec_F;
+  const int32_t* spec_guide;
+  int32_t spec_k;
+  int32_t pad0;
+  RefDev ref;
+  SinTab sn;
+};
+int launch_monitor(const MonitorArgs& a, int rad, void* stream);
+
 // Loss-location refinement (one thread per particle).  Tables built on the
 // host per tracker: for every table row its record offset in `lat` (-1 for a
 // marker), its entrance position and reference frame (cos, sin, dx, dy:

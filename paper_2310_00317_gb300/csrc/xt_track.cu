@@ -1212,6 +1212,74 @@ __global__ void __launch_bounds__(128) refine_kernel(RefineArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Monitor: one pass of the table with the particle state written after every
+// row (for lattice functions along the line and the tapering loop).  The maps,
+// the loss rules and the end-of-turn guard are those of the tracking kernel,
+// so the final state equals one turn of xt_track bit for bit.
+template <int RAD>
+__global__ void __launch_bounds__(128) monitor_kernel(const MonitorArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  Part p;
+  p.x = a.x[i]; p.px = a.px[i]; p.y = a.y[i]; p.py = a.py[i]; p.zeta = a.zeta[i];
+  p.delta = a.delta[i]; p.ptau = a.ptau[i]; p.rpp = a.rpp[i]; p.rvv = a.rvv[i];
+  int code = a.state[i];
+  const int64_t pid = a.pid[i];
+  bool alive = code == 1;
+  int lturn = a.at_turn[i];
+  int lelem = a.at_element[i];
+  derive(p, a.ref);
+  const RadCtx rc = {a.seed, a.spec_xi, a.spec_F, a.spec_guide, a.spec_k};
+  const int64_t n = a.n;
+  for (int r = 0; r < a.n_el; r++) {
+    const int off = a.row_off[r];
+    if (off >= 0 && alive) {
+      const uint4 hv = *(const uint4*)(a.lat + off);
+      const uint32_t type = hv.x & 0xFFFFu;
+      const double* prm = (const double*)(a.lat + off + 16);
+      int lc;
+      if (type == XT_DRIFT) lc = drift_lane(p, prm[0]) ? 1 : -2;
+      else lc = element<RAD>(p, type, hv.x >> 16, hv.y & 0xFFFFu, hv.z, prm, a.ref, a.sn, rc, pid, a.turn);
+      if (lc != 1) {
+        alive = false;
+        code = lc;
+        lturn = a.turn;
+        lelem = (int)hv.z;
+      }
+    }
+    if (r == a.n_el - 1 && alive && !(abs_le_one(p.x) && abs_le_one(p.y))) {
+      alive = false;
+      code = -3;
+      lturn = a.turn;
+      lelem = a.n_el - 1;
+    }
+    double* o = a.out + (int64_t)r * 8 * n + i;
+    o[0] = p.x; o[n] = p.px; o[2 * n] = p.y; o[3 * n] = p.py;
+    o[4 * n] = p.zeta; o[5 * n] = p.ptau; o[6 * n] = p.delta; o[7 * n] = (double)code;
+  }
+  a.x[i] = p.x; a.px[i] = p.px; a.y[i] = p.y; a.py[i] = p.py; a.zeta[i] = p.zeta;
+  a.delta[i] = p.delta; a.ptau[i] = p.ptau; a.rpp[i] = p.rpp; a.rvv[i] = p.rvv;
+  if (alive) {  // survivors: the turn count advances, as in the tracking kernel
+    lturn = a.turn + 1;
+    lelem = 0;
+  }
+  a.state[i] = code;
+  a.at_turn[i] = lturn;
+  a.at_element[i] = lelem;
+}
+
+int launch_monitor(const MonitorArgs& a, int rad, void* stream) {
+  if (a.n == 0 || a.n_el == 0) return 0;
+  const int block = 128;
+  const int grid = (int)((a.n + block - 1) / block);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (rad == XT_RAD_MEAN) monitor_kernel<XT_RAD_MEAN><<<grid, block, 0, s>>>(a);
+  else if (rad == XT_RAD_QUANTUM) monitor_kernel<XT_RAD_QUANTUM><<<grid, block, 0, s>>>(a);
+  else monitor_kernel<XT_RAD_OFF><<<grid, block, 0, s>>>(a);
+  return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Order-preserving compaction of the alive particles (state == 1).
 static const int CB = 1024;
 

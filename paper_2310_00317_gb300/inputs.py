@@ -517,7 +517,7 @@ def _lepton_aperture(kind, dipole_slice):
 LEPTON_CELL = dict(quad_slices=2, dip_per_half=2, dip_slices=4, l_quad=2.0, gap=1.0, _ap=_lepton_aperture)
 
 
-def lepton_ring(n_cells: int = 200, E0: float = 45.6e9, v_total: float = 500e6):
+def lepton_ring(n_cells: int = 200, E0: float = 45.6e9, v_total: float = 500e6, rf_every: int = 1):
     """Lepton ring with radiation: 200 FODO cells of 50 thin elements
     (10,000): per cell QF and QD in 2 slices, 2 dipoles of 4 slices per half
     cell (theta = 2 pi/(16 n_cells), L_rad = 10.7/4 m, bending radius 1.36 km),
@@ -529,7 +529,8 @@ def lepton_ring(n_cells: int = 200, E0: float = 45.6e9, v_total: float = 500e6):
     I2 = sum theta^2 / L_rad.  The ring has no dispersion-free straights, so
     the RF is spread over every cell: a few lumped stations would make the
     radiation energy sawtooth jump the dispersive orbit at each station and
-    excite betatron motion."""
+    excite betatron motion; rf_every > 1 lumps the RF into stations every
+    rf_every cells (the case that energy-loss compensation addresses)."""
     ref = electron_reference(E0)
     theta = 2 * math.pi / (16 * n_cells)
     l_dip = 10.7
@@ -542,7 +543,8 @@ def lepton_ring(n_cells: int = 200, E0: float = 45.6e9, v_total: float = 500e6):
     I2 = 16 * n_cells * theta ** 2 / (l_dip / 4)
     U0 = 8.846e-5 * (E0 / 1e9) ** 4 * I2 / (2 * math.pi) * 1e9
     lag = 180.0 - math.degrees(math.asin(U0 / v_total))
-    rows = _ring_rows(n_cells, kf, kd, k2f, k2d, theta, l_dip, tuple(range(n_cells)), v_total / n_cells,
+    rf_cells = tuple(range(0, n_cells, rf_every))
+    rows = _ring_rows(n_cells, kf, kd, k2f, k2d, theta, l_dip, rf_cells, v_total / len(rf_cells),
                       400e6, lag, cell=cell)
     return rows, ref, dict(U0=U0, I2=I2, lag=lag)
 

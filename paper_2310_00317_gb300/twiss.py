@@ -125,6 +125,112 @@ def twiss(table, ref, dim: int = 4, delta0: float = 0.0, radiation: int = 0) -> 
                 bety=M[2, 3] / sy, alfy=(M[2, 2] - M[3, 3]) / (2 * sy), dx=D[0], dpx=D[1], dy=D[2], dpy=D[3])
 
 
+def row_lengths(table) -> np.ndarray:
+    """Reference length of every table row (drifts, thick quadrupoles, bends)."""
+    t = np.asarray(table)
+    L = np.zeros(t.shape[0])
+    for i in range(t.shape[0]):
+        ty = int(t[i]["type"])
+        if ty == I.DRIFT:
+            L[i] = t[i]["p"][0]
+        elif ty == I.QUAD:
+            L[i] = t[i]["p"][1]
+        elif ty == I.BEND:
+            L[i] = t[i]["p"][2]
+    return L
+
+
+def _symplectic_form(n: int) -> np.ndarray:
+    S = np.zeros((n, n))
+    for k in range(0, n, 2):
+        S[k, k + 1], S[k + 1, k] = 1.0, -1.0
+    return S
+
+
+def normal_modes(M: np.ndarray) -> np.ndarray:
+    """Eigenvectors of a stable one-turn matrix (n x n, n = 4 or 6), one per
+    mode as columns (mode I mostly in x, II in y, III in zeta), each chosen
+    from its conjugate pair and scaled so that v^H S v = i (S the symplectic
+    form).  For an uncoupled plane this is v = (sqrt(beta), (i - alpha) /
+    sqrt(beta)) / sqrt(2) times a phase."""
+    n = M.shape[0]
+    S = _symplectic_form(n)
+    w, V = np.linalg.eig(M)
+    modes = []
+    for k in range(n):
+        v = V[:, k]
+        nv = np.vdot(v, S @ v)  # purely imaginary for a symplectic M
+        if nv.imag > 0:
+            modes.append(v / math.sqrt(nv.imag))
+    if len(modes) != n // 2:
+        raise RuntimeError("one-turn matrix is not stable (eigenvalues off the unit circle)")
+    planes = [int(np.argmax([abs(v[2 * j]) ** 2 + abs(v[2 * j + 1]) ** 2 for j in range(n // 2)])) for v in modes]
+    if sorted(planes) != list(range(n // 2)):
+        raise RuntimeError("modes cannot be assigned to planes (strong coupling)")
+    return np.stack([modes[planes.index(j)] for j in range(n // 2)], 1)
+
+
+def twiss_along(table, ref, dim: int = 4, delta0: float = 0.0, radiation: int = 0) -> dict:
+    """Lattice functions at the exit of every table row (section "Twiss
+    module"): the closed orbit and one-turn Jacobian as in twiss(); the
+    13-particle central-difference stencil about the closed orbit is then
+    tracked once through the line by the monitor (xt_track_monitor), which
+    gives the orbit and the Jacobian M_i from the start to the exit of every
+    row; the eigenvectors of the one-turn matrix (normal_modes) are carried
+    along as M_i v, and the Mais-Ripken functions are read from them:
+    beta_x^I = 2 |v_I,x|^2, alpha_x^I = -2 Re(conj(v_I,x) v_I,px), the phase
+    advance from arg v_I,x, likewise for y and mode II; the cross terms
+    beta_x^II, beta_y^I measure linear coupling.  The dispersion (per unit
+    pzeta, as in twiss()) is M_i (D_0, 1) with D_0 periodic."""
+    m0, _, p0c = ref
+    beta0 = p0c / math.sqrt(p0c * p0c + m0 * m0)
+    el = without_cavities(table) if dim == 4 else np.asarray(table)
+    tr = xtgb.Tracker(el, ref, radiation=radiation)
+    try:
+        E0 = math.sqrt(p0c * p0c + m0 * m0)
+        E = math.sqrt((p0c * (1 + delta0)) ** 2 + m0 * m0)
+        guess = np.zeros(6)
+        guess[5] = (E - E0) / p0c / beta0
+        z = closed_orbit(tr, ref, dim=dim, guess=guess)
+        Z = np.tile(z, (13, 1))
+        for i in range(6):
+            Z[1 + 2 * i, i] += EPS[i]
+            Z[2 + 2 * i, i] -= EPS[i]
+        P = xtgb.Particles.from_numpy(particles_from_z(ref, Z))
+        out = tr.monitor(P).cpu().numpy()
+    finally:
+        tr.close()
+    if np.any(out[:, 7, :] != 1.0):
+        raise RuntimeError("a particle of the stencil was lost along the line")
+    zs = out[:, :6, :].copy()
+    zs[:, 5, :] /= beta0  # ptau -> pzeta
+    orbit = zs[:, :, 0]
+    Ms = np.empty((zs.shape[0], 6, 6))
+    for k in range(6):
+        Ms[:, :, k] = (zs[:, :, 1 + 2 * k] - zs[:, :, 2 + 2 * k]) / (2.0 * EPS[k])
+    M = Ms[-1]
+    n = 4 if dim == 4 else 6
+    Vm = normal_modes(M[:n, :n])
+    V = np.einsum("eij,jk->eik", Ms[:, :n, :n], Vm)
+    V = np.concatenate([Vm[None], V], 0)  # row -1: the start of the line
+    bx1, by2 = 2 * np.abs(V[:, 0, 0]) ** 2, 2 * np.abs(V[:, 2, 1]) ** 2
+    ax1 = -2 * np.real(np.conj(V[:, 0, 0]) * V[:, 1, 0])
+    ay2 = -2 * np.real(np.conj(V[:, 2, 1]) * V[:, 3, 1])
+    mux = np.unwrap(np.angle(V[:, 0, 0]))
+    muy = np.unwrap(np.angle(V[:, 2, 1]))
+    D0 = np.linalg.solve(np.eye(4) - M[:4, :4], M[:4, 5])
+    D = np.einsum("eij,j->ei", Ms[:, :4, :4], D0) + Ms[:, :4, 5]
+    D = np.concatenate([D0[None], D], 0)
+    s = np.concatenate([[0.0], np.cumsum(row_lengths(el))])
+    orb = np.concatenate([z[None], orbit], 0)
+    return dict(s=s, x=orb[:, 0], px=orb[:, 1], y=orb[:, 2], py=orb[:, 3], zeta=orb[:, 4], pzeta=orb[:, 5],
+                betx=bx1, bety=by2, alfx=ax1, alfy=ay2, mux=(mux - mux[0]) / (2 * math.pi),
+                muy=(muy - muy[0]) / (2 * math.pi), betx2=2 * np.abs(V[:, 0, 1]) ** 2,
+                bety1=2 * np.abs(V[:, 2, 0]) ** 2, dx=D[:, 0], dpx=D[:, 1], dy=D[:, 2], dpy=D[:, 3],
+                M=M, modes=Vm, qx=((mux[-1] - mux[0]) / (2 * math.pi)) % 1.0,
+                qy=((muy[-1] - muy[0]) / (2 * math.pi)) % 1.0)
+
+
 def chromaticity(table, ref, d: float = 1e-5) -> tuple:
     """dQ/ddelta from the tunes at delta = +d and -d (RF off)."""
     a, b = twiss(table, ref, 4, d), twiss(table, ref, 4, -d)
@@ -142,3 +248,97 @@ def damping(table, ref) -> dict:
     planes = np.argmax(np.abs(V[[0, 2, 4], :]) ** 2 + np.abs(V[[1, 3, 5], :]) ** 2, axis=0)
     alpha = np.array([np.mean(-np.log(np.abs(w[planes == k]))) for k in range(3)])
     return dict(alpha=alpha, closed_orbit=t["closed_orbit"], M=t["M"])
+
+
+# --------------------------------------------------------------------------
+# Energy-loss compensation ("tapering", section "Twiss module")
+
+def scale_magnets(table, scale) -> np.ndarray:
+    """A copy of the table with the field strengths of every magnet row i
+    scaled by scale[i]: thin multipole knl and ksl (not the frame curvature
+    hxl nor L_rad), thick quadrupole k1, bend k0 and k1 (not h), dipole-edge
+    h.  Other rows are unchanged."""
+    el = np.array(table, copy=True)
+    for i in range(el.shape[0]):
+        t, f = int(el[i]["type"]), float(scale[i])
+        if t == I.MULTIPOLE:
+            el[i]["p"][:22] = el[i]["p"][:22] * f
+        elif t == I.QUAD:
+            el[i]["p"][0] = el[i]["p"][0] * f
+        elif t == I.BEND:
+            el[i]["p"][0] = el[i]["p"][0] * f
+            el[i]["p"][3] = el[i]["p"][3] * f
+        elif t == I.DIPEDGE:
+            el[i]["p"][0] = el[i]["p"][0] * f
+    return el
+
+
+def compensate_energy_loss(table, ref, max_iter: int = 40, tol: float = 1e-13) -> dict:
+    """The paper's iteration for lepton rings with strong radiation:
+    (1) the 4D closed orbit without radiation, energy frozen; (2) with mean
+    radiation, one particle from that orbit tracked once around by the
+    monitor while every magnet's strength is scaled to the energy
+    (1 + delta) of the particle entering it, which measures the energy lost
+    along the ring while keeping the orbit and optics; (3) the RF phases set
+    so that the cavities restore that loss, shared in proportion to their
+    voltages: every cavity runs at the phase phi with
+    q V_total sin(phi) = U0, on the side of 90 degrees its lag had, and
+    lag = phi + k_rf zeta at the particle's zeta; (4) steps 2-3 repeated,
+    the scaling taken from the previous pass, until scaling, lags and the
+    energy after one turn settle.  Every turn is tracked on the GPU."""
+    m0, q0, p0c = ref
+    beta0 = p0c / math.sqrt(p0c * p0c + m0 * m0)
+    el0 = np.array(table, copy=True)
+    n = el0.shape[0]
+    cav = np.array([i for i in range(n) if int(el0[i]["type"]) == I.CAVITY and el0[i]["p"][0] != 0.0])
+    if cav.size == 0:
+        raise ValueError("no RF cavity to compensate the energy loss")
+    volts = np.array([el0[i]["p"][0] for i in cav])
+    krf = np.array([2 * math.pi * el0[i]["p"][1] / (beta0 * 2.99792458e8) for i in cav])
+    above = np.array([el0[i]["p"][2] > 90.0 for i in cav])
+    tr = xtgb.Tracker(without_cavities(el0), ref)
+    try:
+        z4 = closed_orbit(tr, ref, dim=4)
+    finally:
+        tr.close()
+    scale = np.ones(n)
+    lags = np.array([el0[i]["p"][2] for i in cav])
+    last = None
+    for it in range(1, max_iter + 1):
+        el = scale_magnets(el0, scale)
+        for j, i in enumerate(cav):
+            el[i]["p"][2] = lags[j]
+        tr = xtgb.Tracker(el, ref, radiation=xtgb.RAD_MEAN)
+        try:
+            P = xtgb.Particles.from_numpy(particles_from_z(ref, z4[None]))
+            start = P.to_numpy()
+            out = tr.monitor(P).cpu().numpy()[:, :, 0]
+        finally:
+            tr.close()
+        if np.any(out[:, 7] != 1.0):
+            raise RuntimeError("the closed-orbit particle was lost during compensation")
+        delta_in = np.concatenate([[start["delta"][0]], out[:-1, 6]])
+        ptau_in = np.concatenate([[start["ptau"][0]], out[:-1, 5]])
+        zeta_in = np.concatenate([[start["zeta"][0]], out[:-1, 4]])
+        dpt = out[:, 5] - ptau_in
+        radiated = -(np.sum(dpt) - np.sum(dpt[cav]))  # in units of p0 c
+        u = radiated * p0c / (q0 * np.sum(volts))
+        if not abs(u) < 1.0:
+            raise RuntimeError("the RF voltage cannot restore the energy loss")
+        phi = np.where(above, math.pi - math.asin(u), math.asin(u))
+        new_lags = np.degrees(phi + krf * zeta_in[cav])
+        new_scale = 1.0 + delta_in
+        d_end = out[-1, 6] - start["delta"][0]
+        done = (np.max(np.abs(new_scale - scale)) < tol and np.max(np.abs(new_lags - lags)) < 1e-9
+                and abs(d_end) < tol)
+        scale, lags = new_scale, new_lags
+        last = dict(delta=delta_in, x=np.concatenate([[z4[0]], out[:-1, 0]]),
+                    y=np.concatenate([[z4[2]], out[:-1, 2]]), delta_end=d_end)
+        if done:
+            break
+    el = scale_magnets(el0, scale)
+    for j, i in enumerate(cav):
+        el[i]["p"][2] = lags[j]
+    return dict(table=el, scale=scale, lags=lags, energy_loss=radiated * p0c, iterations=it,
+                converged=done, **last)
+

@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
             L.xt_element_flops.argtypes = [P, P, i64]
             L.xt_autotune.argtypes = [P, P, i64, P]
             L.xt_refine_losses.argtypes = [P, P, ctypes.c_double, ctypes.c_int32, P, P]
+            L.xt_track_monitor.argtypes = [P, P, ctypes.c_int64, P, P]
             L.xt_track_batched.argtypes = [P, P, i32, i64, i64, i32, P]
             L.xt_batched_sync_status.argtypes = [P, P, i32, P]
             L.xt_set_profiling.argtypes = [P, i32]
@@ -264,6 +265,16 @@ class Tracker:
         s = particles.c_struct()
         _check(lib().xt_refine_losses(self._h, ctypes.byref(s), float(ds), int(n_angles), out.data_ptr(),
                                       _stream_handle(stream)))
+        return out
+
+    def monitor(self, particles: Particles, turn: int = 0, stream=None):
+        """One pass of the table with the particles' state after every row:
+        a CUDA float64 tensor [n_elements, 8, n] of (x, px, y, py, zeta, ptau,
+        delta, state); the particles advance by one turn as in track()."""
+        import torch
+        out = torch.empty((self.table.shape[0], 8, particles.n), dtype=torch.float64, device=particles.t["x"].device)
+        s = particles.c_struct()
+        _check(lib().xt_track_monitor(self._h, ctypes.byref(s), int(turn), out.data_ptr(), _stream_handle(stream)))
         return out
 
     def autotune(self, probe: Particles, probe_turns: int, stream=None) -> dict:

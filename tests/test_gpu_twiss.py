@@ -101,3 +101,141 @@ def test_beambeam_tune_shift_by_tracking():
     assert math.cos(2 * math.pi * t["qx"]) == pytest.approx(math.cos(mu) + beta * k / 2 * math.sin(mu), abs=1e-8)
     assert math.cos(2 * math.pi * t["qy"]) == pytest.approx(math.cos(mu) + beta * k / 2 * math.sin(mu), abs=1e-8)
     assert t["qx"] < Q0 - 0.004
+
+
+# --------------------------------------------------------------------------
+# Lattice functions along the line (eigenvectors propagated by tracking)
+
+def _mixed_lepton_line():
+    """Thin and thick elements with mean radiation on: radiating thin dipole
+    slices, full and expanded bends, thick quadrupoles, sextupoles, an RF
+    cavity and an aperture."""
+    h = 1.0 / 30.0
+    rows = [I.cavity(50e6, 400e6, 175.0)]
+    for c in range(6):
+        rows += [I.quadrupole(0.35, 0.5), I.drift(0.4), I.bend(h, h, 1.5, full=True), I.drift(0.3)]
+        rows += [I.multipole(knl=[h * 1.0, 0.0, 0.3], hxl=h * 1.0, lrad=1.0), I.drift(0.3)]
+        rows += [I.quadrupole(-0.35, 0.5), I.drift(0.4), I.bend(h, h, 1.5, k1=-0.02), I.drift(0.5),
+                 I.aperture(0.008)]
+    return I.table(rows)
+
+
+def test_monitor_equals_the_oracle_after_every_row():
+    """The monitor's state after every row equals the oracle tracking the
+    same particles through that prefix of the table, bit for bit, with mean
+    radiation; the final state equals one turn of xt_track."""
+    import torch
+    from paper_2310_00317_gb300 import xtgb
+    el = _mixed_lepton_line()
+    ref = I.electron_reference(3e9)
+    rng = np.random.default_rng(83)
+    n = 64
+    p = I.make_particles(ref, rng.normal(0, 3e-3, n), rng.normal(0, 1e-3, n), rng.normal(0, 1e-3, n),
+                         rng.normal(0, 1e-4, n), rng.normal(0, 1e-3, n), rng.normal(0, 2e-3, n))
+    tr = xtgb.Tracker(el, ref, radiation=xtgb.RAD_MEAN)
+    P = xtgb.Particles.from_numpy(p)
+    out = tr.monitor(P).cpu().numpy()
+    Q = xtgb.Particles.from_numpy(p)
+    tr.track(Q, 1)
+    tr.close()
+    fin, one = P.to_numpy(), Q.to_numpy()
+    for k in oracle.FLOAT_FIELDS + oracle.INT_FIELDS:
+        a, b = fin[k], one[k]
+        assert np.all((a == b) | (np.isnan(a) & np.isnan(b))), k
+    names = ("x", "px", "y", "py", "zeta", "ptau", "delta")
+    for i in range(el.shape[0]):
+        o = oracle.track(el[:i + 1], ref, p, 1, rad_mode=1)
+        for c, k in enumerate(names):
+            a = out[i, c]
+            assert np.all((a == o[k]) | (np.isnan(a) & np.isnan(o[k]))), (i, k)
+        assert np.all(out[i, 7] == o["state"]), i
+    assert np.any(out[-1, 7] != 1.0) and np.any(out[-1, 7] == 1.0)
+
+
+def _cs_along(Ms, b0, a0):
+    m11, m12, m21, m22 = Ms[:, 0, 0], Ms[:, 0, 1], Ms[:, 1, 0], Ms[:, 1, 1]
+    u, v = m11 * b0 - m12 * a0, m21 * b0 - m22 * a0
+    return (u * u + m12 * m12) / b0, -(u * v + m12 * m22) / b0
+
+
+def test_twiss_along_thin_fodo():
+    """FODO-10 (thin quadrupoles f = 5 m, 4 m cells): beta at the quadrupoles
+    equals the closed forms Lc (1 +- sin(mu/2)) / sin(mu) with
+    sin(mu/2) = Lc / (4 f), the phase advance per cell is mu, and beta and
+    alpha at every row agree with Courant-Snyder propagation through the
+    oracle's exact per-row Jacobians."""
+    el, ref = I.fodo10()
+    t = T.twiss_along(el, ref)
+    mu = 2 * math.asin(0.2)
+    bp, bm = 4 * 1.2 / math.sin(mu), 4 * 0.8 / math.sin(mu)
+    rows = list(el)
+    qf = np.array([i for i, r in enumerate(rows) if int(r["type"]) == I.MULTIPOLE and r["p"][1] > 0])
+    qd = np.array([i for i, r in enumerate(rows) if int(r["type"]) == I.MULTIPOLE and r["p"][1] < 0])
+    assert np.allclose(t["betx"][qf + 1], bp, rtol=1e-7) and np.allclose(t["bety"][qf + 1], bm, rtol=1e-7)
+    assert np.allclose(t["betx"][qd + 1], bm, rtol=1e-7) and np.allclose(t["bety"][qd + 1], bp, rtol=1e-7)
+    assert np.allclose(np.diff(t["mux"][qf + 1]), mu / (2 * math.pi), atol=1e-9)
+    assert abs(t["qx"] - (10 * mu / (2 * math.pi)) % 1.0) < 1e-9
+    assert np.max(t["betx2"]) < 1e-12 and np.max(t["bety1"]) < 1e-12
+    elo = T.without_cavities(el)
+    _, M, _, Ms = oracle.track_jacobian(elo, ref, np.zeros(6), along=True)
+    sx = math.sqrt(1 - (0.5 * np.trace(M[:2, :2])) ** 2)
+    bx0, ax0 = M[0, 1] / sx, (M[0, 0] - M[1, 1]) / (2 * sx)
+    bx, ax = _cs_along(Ms, bx0, ax0)
+    assert np.max(np.abs(t["betx"][1:] / bx - 1)) < 1e-7
+    assert np.max(np.abs(t["alfx"][1:] - ax)) < 1e-6
+
+
+def test_twiss_along_coupled_ring_with_thick_elements():
+    """A misaligned FODO ring with a skew quadrupole, thick quadrupoles and
+    expanded bends: the GPU's eigenvectors propagated along the line agree
+    with those propagated through the oracle's exact per-row Jacobians
+    (beta of both modes in both planes, the dispersion), and the coupling
+    terms are non-zero."""
+    el0, ref = misaligned_fodo()
+    h = 0.01
+    rows = list(el0)[:26] + [I.multipole(ksl=[0.0, 0.02]), I.quadrupole(0.1, 0.6), I.bend(h, h, 2.0),
+                              I.quadrupole(-0.01, 0.6)] + list(el0)[26:]
+    el = I.table(rows)
+    t = T.twiss_along(el, ref)
+    elo = T.without_cavities(el)
+    co = oracle.closed_orbit(elo, ref, rad_mode=0, dim=4)
+    _, M, _, Ms = oracle.track_jacobian(elo, ref, co, along=True)
+    V0 = T.normal_modes(M[:4, :4])
+    V = np.einsum("eij,jk->eik", Ms[:, :4, :4], V0)
+    for name, j, k in (("betx", 0, 0), ("bety", 2, 1), ("betx2", 0, 1), ("bety1", 2, 0)):
+        want = 2 * np.abs(V[:, j, k]) ** 2
+        assert np.max(np.abs(t[name][1:] - want)) < 1e-7 * np.max(want), name
+    D0 = np.linalg.solve(np.eye(4) - M[:4, :4], M[:4, 5])
+    D = np.einsum("eij,j->ei", Ms[:, :4, :4], D0) + Ms[:, :4, 5]
+    assert np.max(np.abs(t["dx"][1:] - D[:, 0])) < 1e-6 * np.max(np.abs(D[:, 0]))
+    assert np.max(t["betx2"]) > 1e-3 and np.max(t["bety1"]) > 1e-3
+
+
+# --------------------------------------------------------------------------
+# Energy-loss compensation (tapering)
+
+def test_energy_loss_compensation_keeps_the_design_orbit():
+    """The 45.6 GeV lepton ring (10,000 rows) with its RF lumped into 4
+    stations, so that the radiation energy sawtooth spans about 1.5e-3.
+    After the compensation loop the closed-orbit particle comes back with
+    the energy it started with, stays on the design orbit while its energy
+    follows the sawtooth, and the energy lost per turn is the design
+    C_gamma E0^4 I2 / (2 pi) within 0.5 %.  With the same RF phases and
+    untapered magnets the orbit strays by millimetres."""
+    from paper_2310_00317_gb300 import xtgb
+    rows, ref, info = I.lepton_ring(rf_every=50)
+    el = I.table(rows)
+    c = T.compensate_energy_loss(el, ref)
+    assert c["converged"] and c["iterations"] < 40
+    assert abs(c["delta_end"]) < 1e-12
+    assert np.max(np.abs(c["x"])) < 1e-9 and np.max(np.abs(c["y"])) < 1e-12
+    assert 1e-3 < np.ptp(c["delta"]) < 2e-3
+    assert abs(c["energy_loss"] / info["U0"] - 1) < 5e-3
+    # untapered magnets, compensated RF phases: the sawtooth moves the orbit
+    el_u = np.array(c["table"], copy=True)
+    el_u = T.scale_magnets(el_u, 1.0 / c["scale"])
+    tr = xtgb.Tracker(el_u, ref, radiation=xtgb.RAD_MEAN)
+    P = xtgb.Particles.from_numpy(T.particles_from_z(ref, np.zeros((1, 6))))
+    out = tr.monitor(P).cpu().numpy()[:, :, 0]
+    tr.close()
+    assert np.max(np.abs(out[:, 0])) > 1e-4

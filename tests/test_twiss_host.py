@@ -1,0 +1,63 @@
+"""Host logic of the lattice functions (no GPU): the normal modes of a
+one-turn matrix and their normalisation."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2310_00317_gb300 import twiss as T
+
+
+def cs_block(beta, alpha, mu):
+    g = (1 + alpha * alpha) / beta
+    c, s = math.cos(mu), math.sin(mu)
+    return np.array([[c + alpha * s, beta * s], [-g * s, c - alpha * s]])
+
+
+@pytest.mark.parametrize("n", [4, 6])
+def test_uncoupled_modes_give_courant_snyder_parameters(n):
+    """Block-diagonal one-turn matrices: 2 |v_x|^2 = beta and
+    -2 Re(conj(v_x) v_px) = alpha in each plane, v^H S v = i."""
+    pars = [(12.3, -1.7, 2 * math.pi * 0.31), (4.1, 0.6, 2 * math.pi * 0.27), (900.0, 0.0, 2 * math.pi * 0.004)]
+    M = np.zeros((n, n))
+    for k in range(n // 2):
+        M[2 * k:2 * k + 2, 2 * k:2 * k + 2] = cs_block(*pars[k])
+    V = T.normal_modes(M)
+    S = T._symplectic_form(n)
+    for k in range(n // 2):
+        v = V[:, k]
+        assert abs(np.vdot(v, S @ v) - 1j) < 1e-12
+        b, a, _ = pars[k]
+        assert abs(2 * abs(v[2 * k]) ** 2 - b) < 1e-12 * b
+        assert abs(-2 * np.real(np.conj(v[2 * k]) * v[2 * k + 1]) - a) < 1e-12
+        # the other planes carry nothing
+        assert all(abs(v[2 * j]) < 1e-12 for j in range(n // 2) if j != k)
+
+
+def test_coupled_modes_are_normalised_and_propagate_with_the_map():
+    """A symplectic coupling rotation R applied to an uncoupled matrix:
+    the modes of R M R^-1 are R times those of M (up to a phase), each with
+    v^H S v = i."""
+    M = np.zeros((4, 4))
+    M[:2, :2] = cs_block(10.0, 0.5, 2 * math.pi * 0.31)
+    M[2:, 2:] = cs_block(6.0, -0.3, 2 * math.pi * 0.18)
+    th = 0.2
+    c, s = math.cos(th), math.sin(th)
+    R = np.array([[c, 0, s, 0], [0, c, 0, s], [-s, 0, c, 0], [0, -s, 0, c]])
+    Mc = R @ M @ np.linalg.inv(R)
+    V0, V = T.normal_modes(M), T.normal_modes(Mc)
+    S = T._symplectic_form(4)
+    for k in range(2):
+        assert abs(np.vdot(V[:, k], S @ V[:, k]) - 1j) < 1e-12
+        w = R @ V0[:, k]
+        ph = np.vdot(w, V[:, k]) / np.vdot(w, w)
+        assert abs(abs(ph) - 1) < 1e-12 and np.max(np.abs(V[:, k] - ph * w)) < 1e-12
+    assert 2 * abs(V[0, 1]) ** 2 > 0.1  # mode II has an x part: coupling
+
+
+def test_unstable_matrix_is_rejected():
+    M = np.eye(4)
+    M[:2, :2] = [[2.0, 1.0], [1.0, 1.0]]  # hyperbolic
+    M[2:, 2:] = cs_block(6.0, 0.0, 1.0)
+    with pytest.raises(RuntimeError):
+        T.normal_modes(M)
