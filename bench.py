@@ -286,6 +286,71 @@ def measure_beambeam(n=1000000, n_lens=1000, turns=2):
                          "frac": achieved / NOMINAL_FP64, "algorithmic_flops_per_pass": per_pass}}
 
 
+def measure_thick(n=1000000, turns=4):
+    """Throughput of the thick elements: a small ring (bending radius 1.5 m,
+    50 cells) of full-model sector bends, expanded combined-function bends,
+    thick quadrupoles, sextupoles, drifts and apertures; CUDA-event time of
+    the tracking kernel, FP64 fraction from the library's flop counts."""
+    from paper_2310_00317_gb300 import inputs as I
+    from paper_2310_00317_gb300 import xtgb
+    ref = I.proton_reference(450e9)
+    h = 1 / 1.5
+    rows = []
+    for c in range(50):
+        rows += [I.quadrupole(0.8, 0.3), I.drift(0.3), I.bend(h, h, 0.9, full=True), I.drift(0.3),
+                 I.multipole(knl=[0.0, 0.0, 0.5]), I.quadrupole(-0.8, 0.3), I.drift(0.3),
+                 I.bend(h, h, 0.9, k1=-0.05), I.drift(0.3), I.aperture(0.02)]
+    el = I.table(rows)
+    rng = np.random.default_rng(I.BASE_SEED + 13)
+    p = I.make_particles(ref, rng.normal(0, 1e-3, n), rng.normal(0, 5e-4, n), rng.normal(0, 1e-3, n),
+                         rng.normal(0, 5e-4, n), np.zeros(n), rng.normal(0, 5e-4, n))
+    tr = xtgb.Tracker(el, ref)
+    P = xtgb.Particles.from_numpy(p)
+    tr.track(P, 1)
+    tr.set_profiling(True)
+    tr.kernel_time()
+    alive0 = int((P.t["state"] == 1).sum())
+    tr.track(P, turns, 1)
+    ms, nl = tr.kernel_time()
+    alive1 = int((P.t["state"] == 1).sum())
+    per_turn = float(tr.element_flops().sum())
+    tr.close()
+    units = 0.5 * (alive0 + alive1) * len(rows) * turns
+    achieved = 0.5 * (alive0 + alive1) * per_turn * turns / (ms * 1e-3)
+    return {"workload": "%d particles, %d turns of a 500-row ring of full and expanded thick bends, thick "
+                        "quadrupoles, sextupoles and drifts" % (n, turns),
+            "value": units / (ms * 1e-3), "unit": "particle*element*turns/s", "kernel_ms": ms,
+            "alive": [alive0, alive1],
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": NOMINAL_FP64 / 1e12, "unit": "TFLOP/s",
+                         "frac": achieved / NOMINAL_FP64, "algorithmic_flops_per_turn": per_turn}}
+
+
+def measure_twiss():
+    """Wall time of the lattice functions along the LHC-scale ring (closed
+    orbit, one-turn Jacobian, eigenvectors carried along 20,000 rows by the
+    monitor) and of the energy-loss compensation loop on the 45.6 GeV lepton
+    ring with its RF in 4 stations (each pass one monitor launch)."""
+    import time
+    from paper_2310_00317_gb300 import inputs as I
+    from paper_2310_00317_gb300 import twiss as T
+    el, ref = I.lhc_ring(seed=I.BASE_SEED)
+    T.twiss_along(el, ref)  # warm-up (first-use costs)
+    t0 = time.perf_counter()
+    tw = T.twiss_along(el, ref)
+    t_tw = time.perf_counter() - t0
+    rows, lref, info = I.lepton_ring(rf_every=50)
+    t0 = time.perf_counter()
+    c = T.compensate_energy_loss(I.table(rows), lref)
+    t_c = time.perf_counter() - t0
+    return {"twiss_along": {"workload": "LHC-scale ring, %d rows" % el.shape[0], "seconds": t_tw,
+                            "qx": tw["qx"], "qy": tw["qy"], "betx_max": float(np.max(tw["betx"]))},
+            "energy_loss_compensation": {"workload": "45.6 GeV lepton ring, %d rows, 4 RF stations" % len(rows),
+                                         "seconds": t_c, "iterations": c["iterations"],
+                                         "converged": bool(c["converged"]),
+                                         "energy_loss_eV": c["energy_loss"], "design_U0_eV": info["U0"],
+                                         "max_abs_x_m": float(np.max(np.abs(c["x"])))}}
+
+
 def measure_lepton(n=200000, turns=10):
     """Lepton ring (10,000 elements) with mean radiation + quantum excitation."""
     import torch
@@ -490,6 +555,8 @@ def run_ours(args):
     if ws == 1 and not args.no_extras:
         extras["loss_refinement"] = measure_refinement(tr, H.a)
         extras["beambeam_lens"] = measure_beambeam()
+        extras["thick_elements"] = measure_thick()
+        extras["twiss"] = measure_twiss()
         extras["batched_seeds"] = measure_batched()
         extras["lepton_quantum"] = measure_lepton()
         extras["da_scan"] = measure_da_scan()

@@ -178,7 +178,7 @@ def test_twiss_along_thin_fodo():
     assert np.max(t["betx2"]) < 1e-12 and np.max(t["bety1"]) < 1e-12
     elo = T.without_cavities(el)
     _, M, _, Ms = oracle.track_jacobian(elo, ref, np.zeros(6), along=True)
-    sx = math.sqrt(1 - (0.5 * np.trace(M[:2, :2])) ** 2)
+    sx = math.copysign(math.sqrt(1 - (0.5 * np.trace(M[:2, :2])) ** 2), M[0, 1])  # sin(mu)
     bx0, ax0 = M[0, 1] / sx, (M[0, 0] - M[1, 1]) / (2 * sx)
     bx, ax = _cs_along(Ms, bx0, ax0)
     assert np.max(np.abs(t["betx"][1:] / bx - 1)) < 1e-7
