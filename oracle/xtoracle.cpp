@@ -688,7 +688,10 @@ struct Prep {
   double L;                              // drift
   MultConst m;                           // multipole
   double krf, lagr, qv;                  // cavity
-  double r21, r43;                       // dipole edge
+  double r21, r43;                       // dipole edge (linear model)
+  int enl;                               // dipole edge: 1 = non-linear model
+  double ek0, et, esg, ecorr;            // non-linear edge: field, tan(e1), +1 entrance / -1 exit,
+                                         // finite-extent vertical correction
   double M[36], d[6];                    // linear map in (x,px,y,py,zeta,ptau)
   double r2;                             // aperture
   double dx, dy;                         // reference-frame shift
@@ -737,6 +740,11 @@ static Prep prepare(const Element& e, const RefConst& rc) {
       q.r21 = h * std::tan(e1);
       const double psi = 2.0 * h * hgap * fint * (1.0 + std::sin(e1) * std::sin(e1)) / std::cos(e1);
       q.r43 = -h * std::tan(e1 - psi);
+      q.enl = (e.p[4] != 0.0);
+      q.ek0 = h;
+      q.et = std::tan(e1);
+      q.esg = (e.p[5] != 0.0) ? -1.0 : 1.0;
+      q.ecorr = q.r21 + q.r43;  // h tan(e1) - h tan(e1 - psi)
       break;
     }
     case T_LINEARMAP: {
@@ -808,8 +816,12 @@ static inline void track_element(Part<T>& p, const Prep& q, int rad_mode, const 
       break;
     }
     case T_DIPEDGE:
-      p.px = FMA(q.r21, p.x, p.px);
-      p.py = FMA(q.r43, p.y, p.py);
+      if (q.enl) {
+        edge_nonlinear(p, q.ek0, q.et, q.esg, q.r21, q.ecorr, turn, elem);
+      } else {
+        p.px = FMA(q.r21, p.x, p.px);
+        p.py = FMA(q.r43, p.y, p.py);
+      }
       break;
     case T_LINEARMAP: {
       T v[6] = {p.x, p.px, p.y, p.py, p.zeta, p.ptau};
@@ -973,6 +985,53 @@ static inline void thick_quad(Part<T>& p, double k1, double L) {
   I = FMA((p.opd * L) * (Sha * gh), pv0 * v0, I);
   // L (1 - 1/rvv) - I / (2 rvv (1+delta)^2), with 1 - 1/rvv = (delta - beta0 ptau) / (1+delta)
   p.zeta = p.zeta + FMA(L * (p.delta - p.epm1), p.rpp, -(((0.5 * p.rv0v) * (p.rpp * p.rpp)) * I));
+}
+
+// Dipole edge, non-linear model (section "Lattice modelling and single
+// particle tracking": edge effects as full non-linear maps).  A hard edge of
+// the field k0 whose face makes the angle e with the normal to the reference
+// orbit; to first order in the field gradient the fields that Maxwell's
+// equations attach to the edge (B_s = y dB_y/ds, B_x = -tan(e) y dB_y/ds)
+// kick the particle by py -= k0 y T with T = tan(e + s atan(px/pz)) (s = +1
+// at the entrance, -1 at the exit: the angle between the trajectory and the
+// face normal), and the field missing from (or added to) the wedge between
+// the face and the normal plane gives px += k0 tan(e) x.  The map is the
+// canonical transformation of the generating function
+//   x X' + y Y' + zeta Z' + (k0/2) y^2 T(px, py', delta) - (k0/2) tan(e) x^2
+// (fringe part: py' = py - k0 y T(px, py') solved by three fixed-point
+// steps; then x, y, zeta shifted by (k0/2) y^2 dT/d(px, py, pzeta)), with
+//   dT/dpx = s (1 + t^2)(pz^2 + px^2) / (pz D^2),  dT/dpy = s (1 + t^2) px py / (pz D^2),
+//   dT/ddelta = -s (1 + t^2) px (1+delta) / (pz D^2),  D = pz - s t px,  t = tan(e),
+// and the wedge kick after it at the entrance, before it at the exit.  The
+// finite extent of the fringe (fint, hgap) enters as in the linear model: a
+// further py += (h tan(e) - h tan(e - psi)) y, so that the linearisation at
+// the origin is the linear edge.  Lost with code -2 if pz is not real.
+template <class T>
+static inline void edge_nonlinear(Part<T>& p, double k0, double t, double sgn, double r21, double corr,
+                                  int turn, int elem) {
+  if (sgn < 0.0) p.px = FMA(r21, p.x, p.px);
+  const T px = p.px, y = p.y, py = p.py;
+  const T base = FMA(-px, px, p.dm1);  // (1+delta)^2 - 1 - px^2
+  if (!(val(FMA(-py, py, base)) > -1.0)) { mark_lost(p, -2, turn, elem); return; }
+  const T ky = k0 * y;
+  const double st = sgn * t;
+  T pyn = py;
+  for (int k = 0; k < 3; k++) {
+    const T pz = SQRT(1.0 + FMA(-pyn, pyn, base));
+    const T Tv = FMA(t, pz, sgn * px) / FMA(-st, px, pz);
+    pyn = FMA(-ky, Tv, py);
+  }
+  const T u = FMA(-pyn, pyn, base);
+  if (!(val(u) > -1.0)) { mark_lost(p, -2, turn, elem); return; }
+  const T pz = SQRT(1.0 + u);
+  const T D = FMA(-st, px, pz);
+  const T c = (sgn * (1.0 + t * t)) / (pz * (D * D));
+  const T g = ((0.5 * k0) * (y * y)) * c;
+  p.x = FMA(g, FMA(pz, pz, px * px), p.x);
+  p.y = FMA(g, px * pyn, p.y);
+  p.zeta = FMA(-(g * (px * p.opd)), p.rv0v, p.zeta);
+  p.py = FMA(corr, p.y, pyn);
+  if (sgn > 0.0) p.px = FMA(r21, p.x, p.px);
 }
 
 // Entire functions of z (either sign) with a = sqrt|z|: C = cos a,
@@ -1218,6 +1277,7 @@ static bool inverse_row(Part<double>& p, const Prep& q, const RefConst& rc) {
       return true;
     }
     case T_DIPEDGE:
+      if (q.enl) return false;  // no inverse formed for the non-linear edge
       p.px = std::fma(-q.r21, p.x, p.px);
       p.py = std::fma(-q.r43, p.y, p.py);
       return true;
