@@ -30,6 +30,8 @@ enum : uint16_t { REC_CURV = 1, REC_RAD = 2, REC_PURE = 4, REC_BEND = 8 };
 enum : uint16_t { REC_QF = 1 };
 // thick bend: the full (exact) model
 enum : uint16_t { REC_BFULL = 1 };
+// dipole edge: the non-linear model
+enum : uint16_t { REC_ENL = 1 };
 // REC_PURE: knl0 == ksl0 == 0 and hxl == 0.  REC_BEND: hxl != 0, hxl == knl0,
 // ksl0 == 0.  Without radiation these multipoles add the last Horner step
 // straight into px, py (and a bend's -knl0 + hxl (1+delta) becomes hxl delta).

@@ -703,6 +703,44 @@ __device__ __forceinline__ void multipole(Part& p, const double* prm, int order,
   }
 }
 
+// Dipole edge, non-linear model (section "Lattice modelling and single
+// particle tracking": edge effects as full non-linear maps); prm = r21, r43,
+// k0, t = tan(e), s (+1 entrance, -1 exit), corr.  The canonical map of the
+// generating function x X' + y Y' + zeta Z' + (k0/2) y^2 T(px, py', delta)
+// - (k0/2) t x^2 with T = tan(e + s atan(px/pz)) (the vertical kick of the
+// fields a hard edge carries to first order in the field gradient): py' from
+// three fixed-point steps, then x, y, zeta shifted by (k0/2) y^2 dT/d(px,
+// py, pzeta); the wedge kick px += r21 x after it at the entrance, before it
+// at the exit; the finite-extent correction py += corr y, corr = r21 + r43,
+// so that the linearisation is the linear edge.  Returns -2 if pz is not real.
+__device__ __forceinline__ int edge_nonlinear(Part& p, const double* prm) {
+  const double r21 = prm[0], k0 = prm[2], t = prm[3], sgn = prm[4], corr = prm[5];
+  if (sgn < 0.0) p.px = fma(r21, p.x, p.px);
+  const double px = p.px, y = p.y, py = p.py;
+  const double base = fma(-px, px, p.dm1);  // (1+delta)^2 - 1 - px^2
+  if (!(fma(-py, py, base) > -1.0)) return -2;
+  const double ky = k0 * y;
+  const double st = sgn * t;
+  double pyn = py;
+  for (int k = 0; k < 3; k++) {
+    const double pz = sqrt(1.0 + fma(-pyn, pyn, base));
+    const double Tv = fma(t, pz, sgn * px) / fma(-st, px, pz);
+    pyn = fma(-ky, Tv, py);
+  }
+  const double u = fma(-pyn, pyn, base);
+  if (!(u > -1.0)) return -2;
+  const double pz = sqrt(1.0 + u);
+  const double D = fma(-st, px, pz);
+  const double c = (sgn * (1.0 + t * t)) / (pz * (D * D));
+  const double g = ((0.5 * k0) * (y * y)) * c;
+  p.x = fma(g, fma(pz, pz, px * px), p.x);
+  p.y = fma(g, px * pyn, p.y);
+  p.zeta = fma(-(g * (px * p.opd)), p.rv0v, p.zeta);
+  p.py = fma(corr, p.y, pyn);
+  if (sgn > 0.0) p.px = fma(r21, p.x, p.px);
+  return 1;
+}
+
 // One record.  Returns the loss code (1 = still alive).
 template <int RAD>
 __device__ __forceinline__ int element(Part& p, uint32_t type, uint32_t order, uint32_t flags,
@@ -755,6 +793,7 @@ __device__ __forceinline__ int element(Part& p, uint32_t type, uint32_t order, u
       return 1;
     }
     case XT_DIPEDGE:
+      if (flags & REC_ENL) return edge_nonlinear(p, prm);
       p.px = fma(prm[0], p.x, p.px);
       p.py = fma(prm[1], p.y, p.py);
       return 1;
@@ -1081,6 +1120,7 @@ __device__ __forceinline__ bool inverse_record(Part& p, uint32_t type, uint32_t 
       return true;
     }
     case XT_DIPEDGE:
+      if (flags & REC_ENL) return false;  // no inverse formed for the non-linear edge
       p.px = fma(-prm[0], p.x, p.px);
       p.py = fma(-prm[1], p.y, p.py);
       return true;

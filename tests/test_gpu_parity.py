@@ -274,6 +274,31 @@ def test_refine_losses_through_thick_bends_bitwise():
     assert sum(np.sum((lost > a + 1e-9) & (lost < b - 1e-9)) for a, b in body) > 20
 
 
+def test_nonlinear_dipole_edges_bitwise():
+    """Rectangular bends: non-linear entrance and exit edges (face angle
+    theta/2, fint * hgap set) around full-model bends, linear edges around
+    the expanded ones, in the small ring; 2,000 particles at up to 5 mrad
+    plus a few steep ones, 100 turns, bit for bit."""
+    h = 1 / 1.5
+    th = h * 0.9
+    rows = [I.cavity(2e6, 400e6, 180.0)]
+    for c in range(8):
+        rows += [I.quadrupole(0.8, 0.3), I.drift(0.3),
+                 I.dipedge(h, th / 2, hgap=0.02, fint=0.5, nonlinear=True),
+                 I.bend(h, h, 0.9, full=True),
+                 I.dipedge(h, th / 2, hgap=0.02, fint=0.5, nonlinear=True, exit=True), I.drift(0.3),
+                 I.multipole(knl=[0.0, 0.0, 0.5]), I.quadrupole(-0.8, 0.3), I.drift(0.3),
+                 I.dipedge(h, 0.05), I.bend(h, h, 0.9, k1=-0.05), I.dipedge(h, 0.05), I.drift(0.3),
+                 I.aperture(0.02)]
+    el = I.table(rows)
+    p = random_particles(PROTON, 2000, 97, sx=4e-3, spx=2e-3, sd=1e-3)
+    for i, (px, py) in enumerate([(0.3, 0.2), (-0.5, 0.1), (0.05, 0.9)]):
+        p["px"][i], p["py"][i] = px, py
+    g, o = gpu_track(el, PROTON, p, 100), oracle.track(el, PROTON, p, 100)
+    assert_same(g, o)
+    assert 100 < np.sum(o["state"] == 1) < 1950
+
+
 def bb_lens(qN, beta_s, sx, sy, xc=0.0, yc=0.0):
     return I.beambeam4d(qN, beta_s, sx, sy, xc, yc)
 
