@@ -170,65 +170,145 @@ def normal_modes(M: np.ndarray) -> np.ndarray:
     return np.stack([modes[planes.index(j)] for j in range(n // 2)], 1)
 
 
-def twiss_along(table, ref, dim: int = 4, delta0: float = 0.0, radiation: int = 0) -> dict:
-    """Lattice functions at the exit of every table row (section "Twiss
-    module"): the closed orbit and one-turn Jacobian as in twiss(); the
-    13-particle central-difference stencil about the closed orbit is then
-    tracked once through the line by the monitor (xt_track_monitor), which
-    gives the orbit and the Jacobian M_i from the start to the exit of every
-    row; the eigenvectors of the one-turn matrix (normal_modes) are carried
-    along as M_i v, and the Mais-Ripken functions are read from them:
-    beta_x^I = 2 |v_I,x|^2, alpha_x^I = -2 Re(conj(v_I,x) v_I,px), the phase
-    advance from arg v_I,x, likewise for y and mode II; the cross terms
-    beta_x^II, beta_y^I measure linear coupling.  The dispersion (per unit
-    pzeta, as in twiss()) is M_i (D_0, 1) with D_0 periodic."""
+def _stencil_along(tr, ref, z):
+    """Orbit and Jacobians from the start to the exit of every row: the
+    13-particle central-difference stencil about z tracked once through the
+    table by the monitor.  Returns (orbit [n, 6], M [n, 6, 6]) in canonical
+    coordinates (pzeta = ptau / beta0)."""
     m0, _, p0c = ref
     beta0 = p0c / math.sqrt(p0c * p0c + m0 * m0)
-    el = without_cavities(table) if dim == 4 else np.asarray(table)
-    tr = xtgb.Tracker(el, ref, radiation=radiation)
-    try:
-        E0 = math.sqrt(p0c * p0c + m0 * m0)
-        E = math.sqrt((p0c * (1 + delta0)) ** 2 + m0 * m0)
-        guess = np.zeros(6)
-        guess[5] = (E - E0) / p0c / beta0
-        z = closed_orbit(tr, ref, dim=dim, guess=guess)
-        Z = np.tile(z, (13, 1))
-        for i in range(6):
-            Z[1 + 2 * i, i] += EPS[i]
-            Z[2 + 2 * i, i] -= EPS[i]
-        P = xtgb.Particles.from_numpy(particles_from_z(ref, Z))
-        out = tr.monitor(P).cpu().numpy()
-    finally:
-        tr.close()
+    Z = np.tile(z, (13, 1))
+    for i in range(6):
+        Z[1 + 2 * i, i] += EPS[i]
+        Z[2 + 2 * i, i] -= EPS[i]
+    P = xtgb.Particles.from_numpy(particles_from_z(ref, Z))
+    out = tr.monitor(P).cpu().numpy()
     if np.any(out[:, 7, :] != 1.0):
         raise RuntimeError("a particle of the stencil was lost along the line")
     zs = out[:, :6, :].copy()
     zs[:, 5, :] /= beta0  # ptau -> pzeta
-    orbit = zs[:, :, 0]
     Ms = np.empty((zs.shape[0], 6, 6))
     for k in range(6):
         Ms[:, :, k] = (zs[:, :, 1 + 2 * k] - zs[:, :, 2 + 2 * k]) / (2.0 * EPS[k])
-    M = Ms[-1]
-    n = 4 if dim == 4 else 6
-    Vm = normal_modes(M[:n, :n])
+    return zs[:, :, 0], Ms
+
+
+def _functions_along(el, z, orbit, Ms, Vm, D0) -> dict:
+    """Mais-Ripken functions at the start (row -1 of the arrays: index 0)
+    and at the exit of every row from the modes Vm at the start carried as
+    M_i v: beta_x^I = 2 |v_I,x|^2, alpha_x^I = -2 Re(conj(v_I,x) v_I,px),
+    the phase from arg v_I,x (likewise y, mode II), the cross terms
+    beta_x^II and beta_y^I, and the dispersion M_i (D_0, 1)."""
+    n = Vm.shape[0]
     V = np.einsum("eij,jk->eik", Ms[:, :n, :n], Vm)
-    V = np.concatenate([Vm[None], V], 0)  # row -1: the start of the line
-    bx1, by2 = 2 * np.abs(V[:, 0, 0]) ** 2, 2 * np.abs(V[:, 2, 1]) ** 2
-    ax1 = -2 * np.real(np.conj(V[:, 0, 0]) * V[:, 1, 0])
-    ay2 = -2 * np.real(np.conj(V[:, 2, 1]) * V[:, 3, 1])
+    V = np.concatenate([Vm[None], V], 0)
     mux = np.unwrap(np.angle(V[:, 0, 0]))
     muy = np.unwrap(np.angle(V[:, 2, 1]))
-    D0 = np.linalg.solve(np.eye(4) - M[:4, :4], M[:4, 5])
     D = np.einsum("eij,j->ei", Ms[:, :4, :4], D0) + Ms[:, :4, 5]
     D = np.concatenate([D0[None], D], 0)
     s = np.concatenate([[0.0], np.cumsum(row_lengths(el))])
     orb = np.concatenate([z[None], orbit], 0)
     return dict(s=s, x=orb[:, 0], px=orb[:, 1], y=orb[:, 2], py=orb[:, 3], zeta=orb[:, 4], pzeta=orb[:, 5],
-                betx=bx1, bety=by2, alfx=ax1, alfy=ay2, mux=(mux - mux[0]) / (2 * math.pi),
-                muy=(muy - muy[0]) / (2 * math.pi), betx2=2 * np.abs(V[:, 0, 1]) ** 2,
-                bety1=2 * np.abs(V[:, 2, 0]) ** 2, dx=D[:, 0], dpx=D[:, 1], dy=D[:, 2], dpy=D[:, 3],
-                M=M, modes=Vm, qx=((mux[-1] - mux[0]) / (2 * math.pi)) % 1.0,
-                qy=((muy[-1] - muy[0]) / (2 * math.pi)) % 1.0)
+                betx=2 * np.abs(V[:, 0, 0]) ** 2, bety=2 * np.abs(V[:, 2, 1]) ** 2,
+                alfx=-2 * np.real(np.conj(V[:, 0, 0]) * V[:, 1, 0]), alfy=-2 * np.real(np.conj(V[:, 2, 1]) * V[:, 3, 1]),
+                mux=(mux - mux[0]) / (2 * math.pi), muy=(muy - muy[0]) / (2 * math.pi),
+                betx2=2 * np.abs(V[:, 0, 1]) ** 2, bety1=2 * np.abs(V[:, 2, 0]) ** 2,
+                dx=D[:, 0], dpx=D[:, 1], dy=D[:, 2], dpy=D[:, 3], modes_along=V)
+
+
+def _pzeta_of_delta(ref, delta0):
+    m0, _, p0c = ref
+    beta0 = p0c / math.sqrt(p0c * p0c + m0 * m0)
+    E0 = math.sqrt(p0c * p0c + m0 * m0)
+    E = math.sqrt((p0c * (1 + delta0)) ** 2 + m0 * m0)
+    return (E - E0) / p0c / beta0
+
+
+def twiss_along(table, ref, dim: int = 4, delta0: float = 0.0, radiation: int = 0) -> dict:
+    """Lattice functions at the exit of every table row of a ring (section
+    "Twiss module"): the closed orbit and one-turn Jacobian as in twiss();
+    the stencil about the closed orbit tracked once through the line by the
+    monitor gives the Jacobian M_i to the exit of every row; the modes of
+    the one-turn matrix (normal_modes) are carried along as M_i v and the
+    Mais-Ripken functions read from them (_functions_along).  The dispersion
+    (per unit pzeta, as in twiss()) is M_i (D_0, 1) with D_0 periodic.
+    dim=6 keeps the RF and gives three modes (the third longitudinal)."""
+    el = without_cavities(table) if dim == 4 else np.asarray(table)
+    tr = xtgb.Tracker(el, ref, radiation=radiation)
+    try:
+        guess = np.zeros(6)
+        guess[5] = _pzeta_of_delta(ref, delta0)
+        z = closed_orbit(tr, ref, dim=dim, guess=guess)
+        orbit, Ms = _stencil_along(tr, ref, z)
+    finally:
+        tr.close()
+    M = Ms[-1]
+    n = 4 if dim == 4 else 6
+    Vm = normal_modes(M[:n, :n])
+    D0 = np.linalg.solve(np.eye(4) - M[:4, :4], M[:4, 5])
+    out = _functions_along(el, z, orbit, Ms, Vm, D0)
+    out.update(M=M, modes=Vm, qx=float(out["mux"][-1]) % 1.0, qy=float(out["muy"][-1]) % 1.0)
+    return out
+
+
+def twiss_open(table, ref, betx: float, alfx: float, bety: float, alfy: float, dx: float = 0.0, dpx: float = 0.0,
+               dy: float = 0.0, dpy: float = 0.0, orbit=None, delta0: float = 0.0, radiation: int = 0) -> dict:
+    """Lattice functions along a line, or a portion of a ring, from given
+    initial conditions (section "Twiss module": Twiss on part of a line with
+    assigned initial conditions and momentum): uncoupled modes built from
+    (beta, alpha) at the start, v_I = (sqrt(betx), (i - alfx)/sqrt(betx), 0, 0)
+    / sqrt(2) and likewise v_II, carried through the monitor's per-row
+    Jacobians about the given orbit (zeros, at momentum delta0, by default)."""
+    z = np.zeros(6) if orbit is None else np.array(orbit, dtype=np.float64)
+    if orbit is None:
+        z[5] = _pzeta_of_delta(ref, delta0)
+    el = np.asarray(table)
+    tr = xtgb.Tracker(el, ref, radiation=radiation)
+    try:
+        orb, Ms = _stencil_along(tr, ref, z)
+    finally:
+        tr.close()
+    Vm = np.zeros((4, 2), dtype=complex)
+    Vm[0, 0], Vm[1, 0] = math.sqrt(betx), (1j - alfx) / math.sqrt(betx)
+    Vm[2, 1], Vm[3, 1] = math.sqrt(bety), (1j - alfy) / math.sqrt(bety)
+    Vm /= math.sqrt(2.0)
+    return _functions_along(el, z, orb, Ms, Vm, np.array([dx, dpx, dy, dpy], dtype=np.float64))
+
+
+R_ELECTRON = 2.8179403262e-15        # classical electron radius [m]
+LAMBDA_C_ELECTRON = 3.8615926796e-13  # reduced Compton wavelength hbar / (m_e c) [m]
+
+
+def equilibrium_emittances(table, ref) -> dict:
+    """Equilibrium emittances from the linear normal form (section "Twiss
+    module", after Chao): the modes of the 6D one-turn matrix without
+    radiation are carried along the ring (twiss_along, dim=6); a quantum
+    kick of variance s2_i in pzeta at radiating element i raises the action
+    of mode k by |v_k,zeta(i)|^2 s2_i (the action of z is |v^H S z|^2), and
+    the mode damps at 2 alpha_k per turn (damping()), so
+    eps_k = sum_i |v_k,zeta(i)|^2 s2_i / (2 alpha_k).  The energy diffusion
+    of a thin radiating slice of curvature h = knl0 / L_rad is
+    s2 = 55 / (48 sqrt 3) r_e (hbar / m_e c) gamma0^5 |h|^3 L_rad (electrons;
+    pzeta = delta for beta0 -> 1).  Also returns the momentum spread
+    2 sum_k eps_k |v_k,pzeta|^2 at the start."""
+    m0, _, p0c = ref
+    gamma0 = math.sqrt(p0c * p0c + m0 * m0) / m0
+    t6 = twiss_along(table, ref, dim=6)
+    dmp = damping(table, ref)
+    el = np.asarray(table)
+    V = t6["modes_along"]  # [row + 1, 6, 3]
+    c = 55.0 / (48.0 * math.sqrt(3.0)) * R_ELECTRON * LAMBDA_C_ELECTRON * gamma0 ** 5
+    growth = np.zeros(3)
+    for i in range(el.shape[0]):
+        r = el[i]
+        if int(r["type"]) != I.MULTIPOLE or r["p"][23] <= 0.0 or r["p"][0] == 0.0:
+            continue
+        L = r["p"][23]
+        h = r["p"][0] / L
+        growth += np.abs(V[i + 1, 4, :]) ** 2 * (c * abs(h) ** 3 * L)
+    eps = growth / (2.0 * dmp["alpha"])
+    sigma_delta = math.sqrt(2.0 * float(np.sum(eps * np.abs(t6["modes"][5, :]) ** 2)))
+    return dict(eps=eps, sigma_delta=sigma_delta, alpha=dmp["alpha"], twiss=t6)
 
 
 def chromaticity(table, ref, d: float = 1e-5) -> tuple:

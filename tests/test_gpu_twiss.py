@@ -239,3 +239,35 @@ def test_energy_loss_compensation_keeps_the_design_orbit():
     out = tr.monitor(P).cpu().numpy()[:, :, 0]
     tr.close()
     assert np.max(np.abs(out[:, 0])) > 1e-4
+
+
+def test_twiss_open_line_with_periodic_initial_conditions():
+    """One cell of FODO-10 as an open line from the ring's periodic
+    functions at its start reproduces the ring's beta, alpha and phase
+    along the cell; from other initial conditions beta follows
+    Courant-Snyder propagation through the oracle's per-row Jacobians."""
+    el, ref = I.fodo10()
+    ring = T.twiss_along(el, ref)
+    cell = T.without_cavities(el)[1:6]
+    t = T.twiss_open(cell, ref, ring["betx"][1], ring["alfx"][1], ring["bety"][1], ring["alfy"][1])
+    assert np.max(np.abs(t["betx"] - ring["betx"][1:7])) < 1e-7 * np.max(ring["betx"])
+    assert np.max(np.abs(t["alfy"] - ring["alfy"][1:7])) < 1e-7
+    assert np.max(np.abs(t["mux"] - (ring["mux"][1:7] - ring["mux"][1]))) < 1e-9
+    t2 = T.twiss_open(T.without_cavities(el), ref, 20.0, -1.5, 5.0, 0.4)
+    _, _, _, Ms = oracle.track_jacobian(T.without_cavities(el), ref, np.zeros(6), along=True)
+    bx, ax = _cs_along(Ms, 20.0, -1.5)
+    assert np.max(np.abs(t2["betx"][1:] / bx - 1)) < 1e-7 and np.max(np.abs(t2["alfx"][1:] - ax)) < 1e-6
+
+
+def test_equilibrium_emittances_from_the_normal_form():
+    """The 45.6 GeV lepton ring: horizontal emittance and momentum spread
+    from the normal form (quantum diffusion carried by the 6D modes, damping
+    from the one-turn eigenvalues) agree with the synchrotron-integral values
+    C_q gamma^2 I5 / (J_x I2) and C_q gamma^2 I3 / (J_z I2) of the oracle's
+    optics within 2 %; the vertical emittance of the uncoupled ring vanishes."""
+    el, ref, _ = I.lepton_ring()
+    e = T.equilibrium_emittances(el, ref)
+    eq = O.equilibrium(el, ref)
+    assert abs(e["eps"][0] / eq["eps_x"] - 1) < 0.02, (e["eps"], eq["eps_x"])
+    assert abs(e["sigma_delta"] / eq["sigma_delta"] - 1) < 0.02, (e["sigma_delta"], eq["sigma_delta"])
+    assert e["eps"][1] < 1e-6 * e["eps"][0]
