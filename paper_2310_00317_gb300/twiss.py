@@ -275,6 +275,47 @@ def twiss_open(table, ref, betx: float, alfx: float, bety: float, alfy: float, d
     return _functions_along(el, z, orb, Ms, Vm, np.array([dx, dpx, dy, dpy], dtype=np.float64))
 
 
+def kick_as_closed_orbit(table, ref) -> tuple:
+    """The "kick as closed orbit" line of section "Twiss module": with mean
+    radiation the 6D closed orbit is found and one particle on it is
+    tracked once around by the monitor; at every radiating multipole the
+    radiation's share of the change is read off the monitor (the energy step
+    dpzeta, and px, py times 1 - 1/f where f = (1+delta_after)/(1+delta_before)
+    is the scaling that keeps the angles), and the returned table carries
+    those constant kicks as identity linear maps with offsets right after
+    each radiating row.  Tracked with radiation off, it gives every particle
+    the closed orbit's radiation kicks: a symplectic one-turn matrix that
+    includes the energy loss to first order.  Returns (table, closed orbit,
+    the position of every original row in the new table)."""
+    m0, _, p0c = ref
+    beta0 = p0c / math.sqrt(p0c * p0c + m0 * m0)
+    el0 = np.asarray(table)
+    tr = xtgb.Tracker(el0, ref, radiation=xtgb.RAD_MEAN)
+    try:
+        co = closed_orbit(tr, ref, dim=6)
+        P = xtgb.Particles.from_numpy(particles_from_z(ref, co[None]))
+        start = P.to_numpy()
+        out = tr.monitor(P).cpu().numpy()[:, :, 0]
+    finally:
+        tr.close()
+    before = np.concatenate([[[start[k][0] for k in ("x", "px", "y", "py", "zeta", "ptau")] + [start["delta"][0]]],
+                             out[:-1, :7]], 0)
+    rows, index = [], []
+    for i in range(el0.shape[0]):
+        r = el0[i]
+        index.append(len(rows))
+        rows.append(r)
+        if int(r["type"]) != I.MULTIPOLE or r["p"][23] <= 0.0:
+            continue
+        f = (1.0 + out[i, 6]) / (1.0 + before[i, 6])
+        d = np.zeros(6)
+        d[1] = out[i, 1] * (1.0 - 1.0 / f)
+        d[3] = out[i, 3] * (1.0 - 1.0 / f)
+        d[5] = (out[i, 5] - before[i, 5]) / beta0
+        rows.append(I.linear_map(np.eye(6), d))
+    return I.table(rows), co, np.array(index)
+
+
 R_ELECTRON = 2.8179403262e-15        # classical electron radius [m]
 LAMBDA_C_ELECTRON = 3.8615926796e-13  # reduced Compton wavelength hbar / (m_e c) [m]
 
@@ -287,8 +328,9 @@ def equilibrium_emittances(table, ref) -> dict:
     of mode k by |v_k,zeta(i)|^2 s2_i (the action of z is |v^H S z|^2), and
     the mode damps at 2 alpha_k per turn (damping()), so
     eps_k = sum_i |v_k,zeta(i)|^2 s2_i / (2 alpha_k).  The energy diffusion
-    of a thin radiating slice of curvature h = knl0 / L_rad is
-    s2 = 55 / (48 sqrt 3) r_e (hbar / m_e c) gamma0^5 |h|^3 L_rad (electrons;
+    of a thin radiating slice of curvature h = knl0 / L_rad is the variance of
+    its relative energy kick per passage,
+    s2 = 55 / (24 sqrt 3) r_e (hbar / m_e c) gamma0^5 |h|^3 L_rad (electrons;
     pzeta = delta for beta0 -> 1).  Also returns the momentum spread
     2 sum_k eps_k |v_k,pzeta|^2 at the start."""
     m0, _, p0c = ref
@@ -297,7 +339,7 @@ def equilibrium_emittances(table, ref) -> dict:
     dmp = damping(table, ref)
     el = np.asarray(table)
     V = t6["modes_along"]  # [row + 1, 6, 3]
-    c = 55.0 / (48.0 * math.sqrt(3.0)) * R_ELECTRON * LAMBDA_C_ELECTRON * gamma0 ** 5
+    c = 55.0 / (24.0 * math.sqrt(3.0)) * R_ELECTRON * LAMBDA_C_ELECTRON * gamma0 ** 5
     growth = np.zeros(3)
     for i in range(el.shape[0]):
         r = el[i]

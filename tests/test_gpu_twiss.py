@@ -271,3 +271,33 @@ def test_equilibrium_emittances_from_the_normal_form():
     assert abs(e["eps"][0] / eq["eps_x"] - 1) < 0.02, (e["eps"], eq["eps_x"])
     assert abs(e["sigma_delta"] / eq["sigma_delta"] - 1) < 0.02, (e["sigma_delta"], eq["sigma_delta"])
     assert e["eps"][1] < 1e-6 * e["eps"][0]
+
+
+def test_kick_as_closed_orbit_lattice_functions():
+    """The 45.6 GeV lepton ring with mean radiation, by the kick-as-closed-
+    orbit line (radiation kicks of the closed orbit applied to every
+    particle as constant translations): tracked without radiation it keeps
+    the radiation closed orbit, its one-turn matrix is symplectic, its tunes
+    equal the eigen-tunes of the non-symplectic one-turn matrix with
+    radiation, and its beta functions differ from those without radiation
+    by the small amount the energy sawtooth causes."""
+    from paper_2310_00317_gb300 import xtgb
+    el, ref, _ = I.lepton_ring()
+    kt, co, index = T.kick_as_closed_orbit(el, ref)
+    tr = xtgb.Tracker(kt, ref)
+    z1 = T.track_z(tr, ref, co[None])[0]
+    tr.close()
+    assert np.max(np.abs(z1 - co)) < 1e-11
+    t = T.twiss_along(kt, ref, dim=6)
+    S6 = T._symplectic_form(6)
+    assert np.max(np.abs(t["M"].T @ S6 @ t["M"] - S6)) < 1e-8
+    rad = T.twiss(el, ref, dim=6, radiation=xtgb.RAD_MEAN)
+    w = np.linalg.eigvals(rad["M"])
+    q_rad = np.sort(np.abs(np.angle(w)) / (2 * math.pi))[[2, 4]]  # the two transverse pairs
+    w0 = np.linalg.eigvals(t["M"])
+    q_kc = np.sort(np.abs(np.angle(w0)) / (2 * math.pi))[[2, 4]]
+    assert np.max(np.abs(q_rad - q_kc)) < 1e-4, (q_rad, q_kc)
+    t0 = T.twiss_along(el, ref, dim=6)
+    rel = np.abs(t["betx"][index + 1] / t0["betx"][1:] - 1)
+    print("max relative beta-x change from radiation: %.2e" % np.max(rel))
+    assert np.max(rel) < 1e-2
