@@ -288,18 +288,22 @@ def measure_beambeam(n=1000000, n_lens=1000, turns=2):
 
 def measure_thick(n=1000000, turns=4):
     """Throughput of the thick elements: a small ring (bending radius 1.5 m,
-    50 cells) of full-model sector bends, expanded combined-function bends,
-    thick quadrupoles, sextupoles, drifts and apertures; CUDA-event time of
-    the tracking kernel, FP64 fraction from the library's flop counts."""
+    50 cells) of full-model sector bends between non-linear edges, expanded
+    combined-function bends between linear edges, thick quadrupoles,
+    sextupoles, drifts and apertures; CUDA-event time of the tracking
+    kernel, FP64 fraction from the library's flop counts."""
     from paper_2310_00317_gb300 import inputs as I
     from paper_2310_00317_gb300 import xtgb
     ref = I.proton_reference(450e9)
     h = 1 / 1.5
     rows = []
+    th = h * 0.9
     for c in range(50):
-        rows += [I.quadrupole(0.8, 0.3), I.drift(0.3), I.bend(h, h, 0.9, full=True), I.drift(0.3),
-                 I.multipole(knl=[0.0, 0.0, 0.5]), I.quadrupole(-0.8, 0.3), I.drift(0.3),
-                 I.bend(h, h, 0.9, k1=-0.05), I.drift(0.3), I.aperture(0.02)]
+        rows += [I.quadrupole(0.8, 0.3), I.drift(0.3), I.dipedge(h, th / 2, hgap=0.02, fint=0.5, nonlinear=True),
+                 I.bend(h, h, 0.9, full=True), I.dipedge(h, th / 2, hgap=0.02, fint=0.5, nonlinear=True, exit=True),
+                 I.drift(0.3), I.multipole(knl=[0.0, 0.0, 0.5]), I.quadrupole(-0.8, 0.3), I.drift(0.3),
+                 I.dipedge(h, 0.05), I.bend(h, h, 0.9, k1=-0.05), I.dipedge(h, 0.05), I.drift(0.3),
+                 I.aperture(0.02)]
     el = I.table(rows)
     rng = np.random.default_rng(I.BASE_SEED + 13)
     p = I.make_particles(ref, rng.normal(0, 1e-3, n), rng.normal(0, 5e-4, n), rng.normal(0, 1e-3, n),
@@ -317,8 +321,9 @@ def measure_thick(n=1000000, turns=4):
     tr.close()
     units = 0.5 * (alive0 + alive1) * len(rows) * turns
     achieved = 0.5 * (alive0 + alive1) * per_turn * turns / (ms * 1e-3)
-    return {"workload": "%d particles, %d turns of a 500-row ring of full and expanded thick bends, thick "
-                        "quadrupoles, sextupoles and drifts" % (n, turns),
+    return {"workload": "%d particles, %d turns of a %d-row ring of full thick bends between non-linear edges, "
+                        "expanded bends between linear edges, thick quadrupoles, sextupoles and drifts"
+                        % (n, turns, len(rows)),
             "value": units / (ms * 1e-3), "unit": "particle*element*turns/s", "kernel_ms": ms,
             "alive": [alive0, alive1],
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": NOMINAL_FP64 / 1e12, "unit": "TFLOP/s",
@@ -663,12 +668,32 @@ def main():
                     help="time only the surrogate's forward pass over this many samples (--steps repeats)")
     ap.add_argument("--mlp-train", type=int, default=0,
                     help="time only this many surrogate training steps (batch 4096)")
+    ap.add_argument("--only", default="",
+                    help="run one extra measurement alone and print its JSON: thick_elements[:n[:turns]], "
+                         "beambeam_lens[:n[:turns]] or twiss")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.mlp_forward or args.mlp_train:
         return run_mlp(args)
+    if args.only:
+        return run_only(args.only)
     return run_ours(args)
+
+
+def run_only(spec: str) -> int:
+    """One extra measurement on its own (for profiling its kernel)."""
+    name, *nums = spec.split(":")
+    kw = {}
+    if nums:
+        kw["n"] = int(nums[0])
+    if len(nums) > 1:
+        kw["turns"] = int(nums[1])
+    fn = {"thick_elements": measure_thick, "beambeam_lens": measure_beambeam, "twiss": measure_twiss}.get(name)
+    if fn is None:
+        raise SystemExit("--only: unknown measurement %r" % name)
+    print(json.dumps({name: fn(**kw)}))
+    return 0
 
 
 if __name__ == "__main__":
