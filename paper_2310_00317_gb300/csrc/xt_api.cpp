@@ -117,6 +117,10 @@ struct xt_tracker {
   int32_t* d_rowoff = nullptr;
 };
 
+// Kernel instantiation for a tracker: radiation mode + 3 if its table has
+// thick rows (the thin-only instantiation leaves their code out of the loop).
+static int kind_of(const xt_tracker* t) { return t->opt.radiation + (t->lat.thick ? 3 : 0); }
+
 static int prof_pair(xt_tracker* t, cudaEvent_t* a, cudaEvent_t* b) {
   if (t->ev_used == t->ev.size()) {
     cudaEvent_t x, y;
@@ -203,7 +207,7 @@ static int grid_for(xt_tracker* t, int block, size_t smem, int* grid) {
     return fail(XT_ERR_INVALID, "block x 2 x chunk_bytes exceeds the shared memory of one block (" +
                                     std::to_string(smem) + " > " + std::to_string(t->smem_max) + ")");
   int bps = 0;
-  int e = track_occupancy(t->opt.radiation, block, smem, &bps);
+  int e = track_occupancy(kind_of(t), block, smem, &bps);
   if (e) return cuda_fail((cudaError_t)e, "occupancy");
   if (bps < 1) return fail(XT_ERR_INVALID, "launch configuration does not fit on an SM");
   *grid = bps * t->sm_count;
@@ -237,7 +241,7 @@ static int track_device(xt_tracker* t, const xt_particles* p, int64_t start_turn
       if (rc) return rc;
       CK(cudaEventRecord(ea, (cudaStream_t)stream));
     }
-    e = launch_track(a, t->opt.radiation, block, grid, smem, stream);
+    e = launch_track(a, kind_of(t), block, grid, smem, stream);
     if (e) return cuda_fail((cudaError_t)e, "tracking launch");
     if (t->prof) CK(cudaEventRecord(eb, (cudaStream_t)stream));
   }
@@ -696,7 +700,7 @@ int noalloc_prepare(xt_tracker* t, const xt_particles* p, int64_t n_turns, Track
   int rc = grid_for(t, *block, *smem, grid);
   if (rc) return rc;
   *seg = eff_segment(t, p->n, n_turns);
-  *rad = t->opt.radiation;
+  *rad = kind_of(t);
   fill_args(t, p, a);
   return XT_OK;
 }
@@ -769,7 +773,7 @@ extern "C" int xt_autotune(xt_tracker* t, const xt_particles* probe, int64_t pro
         if (xt_tracker_set_options(t, &o) != XT_OK) continue;
         int bps = 0;
         const size_t sm = track_smem_bytes(blk, t->chunk_built);
-        if (sm > (size_t)t->smem_max || track_occupancy(o.radiation, blk, sm, &bps) || bps < 1) continue;
+        if (sm > (size_t)t->smem_max || track_occupancy(o.radiation + (t->lat.thick ? 3 : 0), blk, sm, &bps) || bps < 1) continue;
         if ((rc = restore())) break;
         CK(cudaEventRecord(e0, s));
         rc = track_device(t, &w, 0, probe_turns, stream);
@@ -879,7 +883,7 @@ int make_plan(xt_tracker* const* trs, const xt_particles* ps, int32_t ns, BatchP
   return XT_OK;
 }
 
-int enqueue_batched(xt_tracker* t0, BatchPlan* pl, int64_t n_turns, int seg, int block, size_t smem,
+int enqueue_batched(xt_tracker* t0, BatchPlan* pl, int kind, int64_t n_turns, int seg, int block, size_t smem,
                     int grid, void* stream) {
   BatchArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -912,7 +916,7 @@ int enqueue_batched(xt_tracker* t0, BatchPlan* pl, int64_t n_turns, int seg, int
     if (e) return cuda_fail((cudaError_t)e, "tile prefix");
     a.turn_off = (int32_t)done;
     a.n_turns = nt;
-    e = launch_track_batched(a, t0->opt.radiation, block, grid, smem, stream);
+    e = launch_track_batched(a, kind, block, grid, smem, stream);
     if (e) return cuda_fail((cudaError_t)e, "batched tracking launch");
   }
   return XT_OK;
@@ -939,6 +943,9 @@ extern "C" int xt_track_batched(xt_tracker* const* trs, const xt_particles* ps, 
   }
   if (total > 0x7fffffff) return fail(XT_ERR_INVALID, "too many particles in the batch");
   if (n_turns == 0 || total == 0) return XT_OK;
+  bool thick = false;
+  for (int i = 0; i < ns; i++) thick = thick || trs[i]->lat.thick;
+  const int kind = t0->opt.radiation + (thick ? 3 : 0);
   const int block = eff_block(t0);
   const int chunk = eff_chunk(t0);
   for (int i = 0; i < ns; i++) {
@@ -949,7 +956,7 @@ extern "C" int xt_track_batched(xt_tracker* const* trs, const xt_particles* ps, 
   if (smem > (size_t)t0->smem_max)
     return fail(XT_ERR_INVALID, "block x 2 x chunk_bytes exceeds the shared memory of one block");
   int bpsm = 0;
-  int e = batched_occupancy(t0->opt.radiation, block, smem, &bpsm);
+  int e = batched_occupancy(kind, block, smem, &bpsm);
   if (e) return cuda_fail((cudaError_t)e, "occupancy");
   if (bpsm < 1) return fail(XT_ERR_INVALID, "launch configuration does not fit on an SM");
   const int grid = bpsm * t0->sm_count;
@@ -967,17 +974,17 @@ extern "C" int xt_track_batched(xt_tracker* const* trs, const xt_particles* ps, 
   const int seg = eff_segment(t0, total / ns, n_turns);
   e = launch_set_int(pl->d_scal + 2, (int32_t)start_turn, stream);
   if (e) return cuda_fail((cudaError_t)e, "turn base");
-  if (!graph) return enqueue_batched(t0, pl, n_turns, seg, block, smem, grid, stream);
-  const auto gk = std::make_tuple(n_turns, seg, block, chunk, t0->opt.radiation);
+  if (!graph) return enqueue_batched(t0, pl, kind, n_turns, seg, block, smem, grid, stream);
+  const auto gk = std::make_tuple(n_turns, seg, block, chunk, kind);
   auto gi = pl->graphs.find(gk);
   if (gi == pl->graphs.end()) {
     cudaStream_t cs;
     CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     // make sure kernel attributes are set before capture
     int dummy = 0;
-    batched_occupancy(t0->opt.radiation, block, smem, &dummy);
+    batched_occupancy(kind, block, smem, &dummy);
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_batched(t0, pl, n_turns, seg, block, smem, grid, cs);
+    int rc = enqueue_batched(t0, pl, kind, n_turns, seg, block, smem, grid, cs);
     cudaGraph_t gr;
     cudaError_t ce = cudaStreamEndCapture(cs, &gr);
     cudaStreamDestroy(cs);

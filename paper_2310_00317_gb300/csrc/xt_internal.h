@@ -69,6 +69,7 @@ struct Lattice {
   std::vector<uint32_t> rec_off;  // byte offset of every record
   std::vector<uint32_t> rec_bytes;
   std::vector<int32_t> row_rec;   // per table row: its record's byte offset, -1 if it has none
+  bool thick = false;             // a beam-beam, thick-quadrupole, bend or non-linear-edge record
   int64_t n_el = 0;               // rows in the user's table
   uint64_t hash = 0;
   std::vector<int64_t> flops;     // algorithmic FP64 flops of one traversal, per table row
@@ -217,16 +218,18 @@ struct BatchArgs {
 // Launchers (xt_track.cu).  Return a cudaError_t as int.
 int launch_compact(const int32_t* state, int64_t n, int32_t* block_counts, int32_t* idx,
                    int32_t* n_alive, int32_t* tile_counter, void* stream);
-int launch_track(const TrackArgs& a, int rad_mode, int block, int grid, size_t smem, void* stream);
-int track_occupancy(int rad_mode, int block, size_t smem, int* blocks_per_sm);
+// kind = radiation mode (XT_RAD_*) + 3 when the table has thick rows
+// (Lattice::thick): it picks the kernel instantiation.
+int launch_track(const TrackArgs& a, int kind, int block, int grid, size_t smem, void* stream);
+int track_occupancy(int kind, int block, size_t smem, int* blocks_per_sm);
 int launch_compact_batched(const SeedDev* seeds_dev, int32_t n_seeds, const int64_t* idx_base_dev,
                            int32_t* idx, int32_t* n_alive, int32_t* counts, int64_t max_n, void* stream);
 int launch_tile_prefix(const int32_t* n_alive, const int32_t* order, int32_t n_seeds,
                        int64_t* tile_prefix, int32_t* tile_counter, void* stream);
 int launch_set_int(int32_t* dst, int32_t value, void* stream);
-int launch_track_batched(const BatchArgs& a, int rad_mode, int block, int grid, size_t smem,
+int launch_track_batched(const BatchArgs& a, int kind, int block, int grid, size_t smem,
                          void* stream);
-int batched_occupancy(int rad_mode, int block, size_t smem, int* blocks_per_sm);
+int batched_occupancy(int kind, int block, size_t smem, int* blocks_per_sm);
 int device_sm_count(int* n);
 int device_smem_optin(int* bytes);
 int launch_fp64_probe(double* out, int grid, int block, int iters, void* stream);

@@ -81,6 +81,7 @@ int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice*
   out->bytes.clear();
   out->rec_off.clear();
   out->row_rec.assign((size_t)n, -1);
+  out->thick = false;
   out->rec_bytes.clear();
   out->flops.assign((size_t)n, 0);
   out->n_el = n;
@@ -246,6 +247,9 @@ int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice*
     h.size16 = (uint16_t)(bytes / 16);
     h.elem = (uint32_t)i;
     out->row_rec[(size_t)i] = (int32_t)out->bytes.size();
+    if (e.type == XT_BEAMBEAM4D || e.type == XT_QUAD || e.type == XT_BEND ||
+        (e.type == XT_DIPEDGE && (flags & REC_ENL)))
+      out->thick = true;
     out->rec_off.push_back((uint32_t)out->bytes.size());
     out->rec_bytes.push_back((uint32_t)bytes);
     put(out->bytes, &h, sizeof(h));

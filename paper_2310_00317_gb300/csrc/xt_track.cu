@@ -741,8 +741,11 @@ __device__ __forceinline__ int edge_nonlinear(Part& p, const double* prm) {
   return 1;
 }
 
-// One record.  Returns the loss code (1 = still alive).
-template <int RAD>
+// One record.  Returns the loss code (1 = still alive).  THICK = false is the
+// instantiation for tables without beam-beam lenses, thick quadrupoles,
+// bends or non-linear edges (the host chooses it only for such tables): their
+// bodies then stay out of the thin-element tracking loop.
+template <int RAD, bool THICK = true>
 __device__ __forceinline__ int element(Part& p, uint32_t type, uint32_t order, uint32_t flags,
                                        uint32_t elem, const double* prm, const RefDev& r,
                                        const SinTab& sn, const RadCtx& rc, int64_t pid, int turn) {
@@ -756,10 +759,12 @@ __device__ __forceinline__ int element(Part& p, uint32_t type, uint32_t order, u
       return 1;
     }
     case XT_BEAMBEAM4D: {
-      double fx, fy;
-      bb_field(p.x - prm[1], p.y - prm[2], prm, &fx, &fy);
-      p.px = fma(prm[0], fx, p.px);
-      p.py = fma(prm[0], fy, p.py);
+      if constexpr (THICK) {
+        double fx, fy;
+        bb_field(p.x - prm[1], p.y - prm[2], prm, &fx, &fy);
+        p.px = fma(prm[0], fx, p.px);
+        p.py = fma(prm[0], fy, p.py);
+      }
       return 1;
     }
     case XT_XYSHIFT:  // change of reference frame: displaced by (dx, dy)
@@ -793,16 +798,20 @@ __device__ __forceinline__ int element(Part& p, uint32_t type, uint32_t order, u
       return 1;
     }
     case XT_DIPEDGE:
-      if (flags & REC_ENL) return edge_nonlinear(p, prm);
+      if constexpr (THICK) {
+        if (flags & REC_ENL) return edge_nonlinear(p, prm);
+      }
       p.px = fma(prm[0], p.x, p.px);
       p.py = fma(prm[1], p.y, p.py);
       return 1;
     case XT_QUAD:  // prm = |k1|, L; flags = REC_QF when x is the focusing plane
-      thick_quad(p, prm[0], prm[1], (flags & REC_QF) != 0, sn);
+      if constexpr (THICK) thick_quad(p, prm[0], prm[1], (flags & REC_QF) != 0, sn);
       return 1;
     case XT_BEND:  // prm = k0, h, L, k1; flags = REC_BFULL for the full model
-      if (flags & REC_BFULL) return bend_full(p, prm[0], prm[1], prm[2], sn);
-      bend_expanded(p, prm[0], prm[1], prm[2], prm[3], sn);
+      if constexpr (THICK) {
+        if (flags & REC_BFULL) return bend_full(p, prm[0], prm[1], prm[2], sn);
+        bend_expanded(p, prm[0], prm[1], prm[2], prm[3], sn);
+      }
       return 1;
     case XT_LINEARMAP: {
       const double v[6] = {p.x, p.px, p.y, p.py, p.zeta, p.ptau};
@@ -845,7 +854,7 @@ struct Ctl {
 };
 
 // Returns 0, or an XT_ERR_* code if the launch must stop (cancel, budget, staging).
-template <int RAD>
+template <int RAD, bool THICK>
 __device__ __forceinline__ int track_tile(const TileLat& L, const TileArrays& A, int i, bool active, int turn0,
                           int n_turns, Stage& st, int& resident_key, int lat_key,
                           const RefDev& ref, const SinTab& sn, const RadCtx& rc, Ctl& ctl,
@@ -905,10 +914,10 @@ __device__ __forceinline__ int track_tile(const TileLat& L, const TileArrays& A,
           // the FP64 test runs only if some live lane of the warp is outside
           const uint64_t box = dbits(prm[1]);
           const bool in = !alive || (abs_bits(p.x) <= box && abs_bits(p.y) <= box);
-          if (!__all_sync(FULL_MASK, in) && alive) lc = element<RAD>(p, type, order, flags, hv.z, prm, ref,
+          if (!__all_sync(FULL_MASK, in) && alive) lc = element<RAD, THICK>(p, type, order, flags, hv.z, prm, ref,
                                                                       sn, rc, pid, turn);
         } else if (alive) {
-          lc = element<RAD>(p, type, order, flags, hv.z, prm, ref, sn, rc, pid, turn);
+          lc = element<RAD, THICK>(p, type, order, flags, hv.z, prm, ref, sn, rc, pid, turn);
         }
         if (lc != 1) {
           alive = false;
@@ -987,9 +996,10 @@ __device__ __forceinline__ void set_status(int32_t* status, int err) {
   if (err) atomicCAS(status, 0, err);
 }
 
-template <int RAD>
+// KIND = radiation mode + 3 if the table has thick rows (see element()).
 // At least 3 blocks of XT_MAX_BLOCK per SM caps the registers at 80: the
 // rare beam-beam lens alone would otherwise raise the whole kernel's count.
+template <int KIND>
 __global__ void __launch_bounds__(XT_MAX_BLOCK, 3) track_kernel(const TrackArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
@@ -1012,8 +1022,8 @@ __global__ void __launch_bounds__(XT_MAX_BLOCK, 3) track_kernel(const TrackArgs 
     const int64_t k = base + lane;
     const bool active = k < n_alive;
     const int i = active ? __ldg(a.idx + k) : 0;
-    const int err = track_tile<RAD>(L, A, i, active, a.turn0, a.n_turns, st, resident, 0, a.ref,
-                                    a.sn, rc, ctl, lane);
+    const int err = track_tile<KIND % 3, (KIND >= 3)>(L, A, i, active, a.turn0, a.n_turns, st, resident, 0,
+                                                     a.ref, a.sn, rc, ctl, lane);
     if (err) {
       if (lane == 0) set_status(a.status, err);
       break;
@@ -1021,7 +1031,7 @@ __global__ void __launch_bounds__(XT_MAX_BLOCK, 3) track_kernel(const TrackArgs 
   }
 }
 
-template <int RAD>
+template <int KIND>
 __global__ void __launch_bounds__(XT_MAX_BLOCK, 3) track_batched_kernel(const BatchArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
@@ -1053,8 +1063,8 @@ __global__ void __launch_bounds__(XT_MAX_BLOCK, 3) track_batched_kernel(const Ba
     const TileLat L = {S.lat, S.chunks, S.n_chunks, S.n_el};
     const TileArrays A = {S.x, S.px, S.y, S.py, S.zeta, S.delta, S.ptau, S.rpp, S.rvv,
                           S.state, S.at_turn, S.at_element, S.pid};
-    const int err = track_tile<RAD>(L, A, i, active, turn0, a.n_turns, st, resident, s, a.ref,
-                                    a.sn, rc, ctl, lane);
+    const int err = track_tile<KIND % 3, (KIND >= 3)>(L, A, i, active, turn0, a.n_turns, st, resident, s,
+                                                     a.ref, a.sn, rc, ctl, lane);
     if (err) {
       if (lane == 0) set_status(a.status, err);
       break;
@@ -1449,66 +1459,79 @@ size_t track_smem_bytes(int block, int chunk_bytes) {
   return (size_t)((nw * 16 + 127) & ~127) + (size_t)nw * 2 * (size_t)chunk_bytes;
 }
 
-template <int RAD>
+template <int KIND>
 static int set_smem_attr(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(track_kernel<RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(track_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return (int)e;
-  return (int)cudaFuncSetAttribute(track_batched_kernel<RAD>,
+  return (int)cudaFuncSetAttribute(track_batched_kernel<KIND>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-static int smem_attr(int rad, size_t smem) {
-  switch (rad) {
+// kind = radiation mode (0..2) + 3 for tables with thick rows
+static int smem_attr(int kind, size_t smem) {
+  switch (kind) {
     case 0: return set_smem_attr<0>(smem);
     case 1: return set_smem_attr<1>(smem);
-    default: return set_smem_attr<2>(smem);
+    case 2: return set_smem_attr<2>(smem);
+    case 3: return set_smem_attr<3>(smem);
+    case 4: return set_smem_attr<4>(smem);
+    default: return set_smem_attr<5>(smem);
   }
 }
 
-int launch_track(const TrackArgs& a, int rad, int block, int grid, size_t smem, void* stream) {
-  int e = smem_attr(rad, smem);
+int launch_track(const TrackArgs& a, int kind, int block, int grid, size_t smem, void* stream) {
+  int e = smem_attr(kind, smem);
   if (e) return e;
   cudaStream_t s = (cudaStream_t)stream;
-  switch (rad) {
+  switch (kind) {
     case 0: track_kernel<0><<<grid, block, smem, s>>>(a); break;
     case 1: track_kernel<1><<<grid, block, smem, s>>>(a); break;
-    default: track_kernel<2><<<grid, block, smem, s>>>(a); break;
+    case 2: track_kernel<2><<<grid, block, smem, s>>>(a); break;
+    case 3: track_kernel<3><<<grid, block, smem, s>>>(a); break;
+    case 4: track_kernel<4><<<grid, block, smem, s>>>(a); break;
+    default: track_kernel<5><<<grid, block, smem, s>>>(a); break;
   }
   return (int)cudaGetLastError();
 }
 
-int launch_track_batched(const BatchArgs& a, int rad, int block, int grid, size_t smem, void* stream) {
-  int e = smem_attr(rad, smem);
+int launch_track_batched(const BatchArgs& a, int kind, int block, int grid, size_t smem, void* stream) {
+  int e = smem_attr(kind, smem);
   if (e) return e;
   cudaStream_t s = (cudaStream_t)stream;
-  switch (rad) {
+  switch (kind) {
     case 0: track_batched_kernel<0><<<grid, block, smem, s>>>(a); break;
     case 1: track_batched_kernel<1><<<grid, block, smem, s>>>(a); break;
-    default: track_batched_kernel<2><<<grid, block, smem, s>>>(a); break;
+    case 2: track_batched_kernel<2><<<grid, block, smem, s>>>(a); break;
+    case 3: track_batched_kernel<3><<<grid, block, smem, s>>>(a); break;
+    case 4: track_batched_kernel<4><<<grid, block, smem, s>>>(a); break;
+    default: track_batched_kernel<5><<<grid, block, smem, s>>>(a); break;
   }
   return (int)cudaGetLastError();
 }
 
-int track_occupancy(int rad, int block, size_t smem, int* bps) {
-  int e = smem_attr(rad, smem);
+template <int KIND>
+static int occ(int* bps, int block, size_t smem, bool batched) {
+  if (batched) return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, track_batched_kernel<KIND>, block, smem);
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, track_kernel<KIND>, block, smem);
+}
+
+static int occupancy(int kind, int block, size_t smem, int* bps, bool batched) {
+  int e = smem_attr(kind, smem);
   if (e) return e;
-  switch (rad) {
-    case 0: return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, track_kernel<0>, block, smem);
-    case 1: return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, track_kernel<1>, block, smem);
-    default: return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, track_kernel<2>, block, smem);
+  switch (kind) {
+    case 0: return occ<0>(bps, block, smem, batched);
+    case 1: return occ<1>(bps, block, smem, batched);
+    case 2: return occ<2>(bps, block, smem, batched);
+    case 3: return occ<3>(bps, block, smem, batched);
+    case 4: return occ<4>(bps, block, smem, batched);
+    default: return occ<5>(bps, block, smem, batched);
   }
 }
 
-int batched_occupancy(int rad, int block, size_t smem, int* bps) {
-  int e = smem_attr(rad, smem);
-  if (e) return e;
-  switch (rad) {
-    case 0: return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, track_batched_kernel<0>, block, smem);
-    case 1: return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, track_batched_kernel<1>, block, smem);
-    default: return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, track_batched_kernel<2>, block, smem);
-  }
-}
+int track_occupancy(int kind, int block, size_t smem, int* bps) { return occupancy(kind, block, smem, bps, false); }
+
+int batched_occupancy(int kind, int block, size_t smem, int* bps) { return occupancy(kind, block, smem, bps, true); }
 
 int launch_compact(const int32_t* state, int64_t n, int32_t* block_counts, int32_t* idx,
                    int32_t* n_alive, int32_t* tile_counter, void* stream) {
