@@ -33,6 +33,7 @@ XYSHIFT, SROTATION, APERTURE_RECT, APERTURE_ELLIPSE = 7, 8, 9, 10
 BEAMBEAM4D = 11
 QUAD = 12
 BEND = 13
+SPACECHARGE = 14
 
 FLOAT_FIELDS = ("x", "px", "y", "py", "zeta", "delta", "ptau", "rpp", "rvv")
 INT_FIELDS = ("state", "at_turn", "at_element")

@@ -52,7 +52,7 @@ enum {
   T_MARKER = 0, T_DRIFT = 1, T_MULTIPOLE = 2, T_CAVITY = 3,
   T_DIPEDGE = 4, T_LINEARMAP = 5, T_APERTURE = 6, T_XYSHIFT = 7, T_SROTATION = 8,
   T_APERTURE_RECT = 9, T_APERTURE_ELLIPSE = 10, T_BEAMBEAM4D = 11, T_QUAD = 12,
-  T_BEND = 13
+  T_BEND = 13, T_SPACECHARGE = 14
 };
 struct Reference { double mass0, q0, p0c; };
 
@@ -698,11 +698,36 @@ struct Prep {
   double cs, sn;                         // reference-frame rotation about s
   double xmin, xmax, ymin, ymax;         // rectangular aperture
   double ia2, ib2;                       // elliptic aperture: 1/a^2, 1/b^2
-  BBConst bb;                            // 4D beam-beam lens
+  BBConst bb;                            // 4D beam-beam lens; frozen space charge (shape and K)
+  double sc_i2sz2;                       // frozen space charge: 1/(2 sigma_z^2), 0 for a coasting beam
   double k1, Lq;                         // thick quadrupole
   double bk0, bh, bL, bk1;               // thick bend: field, curvature, length, gradient
   int bfull;                             // thick bend: 1 = full model, 0 = expanded
 };
+
+// Field-shape constants of a bi-Gaussian line charge with sigma_x, sigma_y
+// (gauss_field): round when the two squares agree to 1e-10, else the
+// Bassetti-Erskine constants with sigma_1 the larger.
+static void gauss_shape(BBConst& b, double sx, double sy) {
+  const double sx2 = sx * sx, sy2 = sy * sy;
+  if (std::fabs(sx2 - sy2) <= 1e-10 * (sx2 + sy2)) {
+    b.mode = 0;
+    b.h1 = 1.0 / (sx2 + sy2);
+  } else {
+    const bool flat = sx2 > sy2;
+    const double s1 = flat ? sx : sy, s2 = flat ? sy : sx;
+    b.mode = flat ? 1 : 2;
+    const double S = std::sqrt(2.0 * (s1 * s1 - s2 * s2));
+    b.h1 = 1.0 / (2.0 * (s1 * s1));
+    b.h2 = 1.0 / (2.0 * (s2 * s2));
+    b.rs = s2 / s1;
+    b.rsi = s1 / s2;
+    b.invS = 1.0 / S;
+    b.cpre = 1.772453850905516 / S;
+    b.lin1 = 1.0 / (s1 * (s1 + s2));
+    b.lin2 = 1.0 / (s2 * (s1 + s2));
+  }
+}
 
 static Prep prepare(const Element& e, const RefConst& rc) {
   Prep q;
@@ -772,28 +797,29 @@ static Prep prepare(const Element& e, const RefConst& rc) {
       // kick of a counter-moving Gaussian bunch integrated over the crossing:
       // Delta p_perp / P0 = 2 q0 q_s N_s (r_e m_e c^2 / p0 c) (1 + beta0 beta_s) /
       // (beta0 + beta_s) f(x - x_c, y - y_c)
-      const double qN = e.p[0], bs = e.p[1], sx2 = e.p[2] * e.p[2], sy2 = e.p[3] * e.p[3];
+      const double qN = e.p[0], bs = e.p[1];
       BBConst& b = q.bb;
       b.K = 2.0 * rc.q0 * qN * (R_ELECTRON * M_ELECTRON) / rc.p0c * ((1.0 + rc.beta0 * bs) / (rc.beta0 + bs));
       b.xc = e.p[4];
       b.yc = e.p[5];
-      if (std::fabs(sx2 - sy2) <= 1e-10 * (sx2 + sy2)) {
-        b.mode = 0;
-        b.h1 = 1.0 / (sx2 + sy2);
-      } else {
-        const bool flat = sx2 > sy2;
-        const double s1 = flat ? e.p[2] : e.p[3], s2 = flat ? e.p[3] : e.p[2];
-        b.mode = flat ? 1 : 2;
-        const double S = std::sqrt(2.0 * (s1 * s1 - s2 * s2));
-        b.h1 = 1.0 / (2.0 * (s1 * s1));
-        b.h2 = 1.0 / (2.0 * (s2 * s2));
-        b.rs = s2 / s1;
-        b.rsi = s1 / s2;
-        b.invS = 1.0 / S;
-        b.cpre = 1.772453850905516 / S;
-        b.lin1 = 1.0 / (s1 * (s1 + s2));
-        b.lin2 = 1.0 / (s2 * (s1 + s2));
-      }
+      gauss_shape(b, e.p[2], e.p[3]);
+      break;
+    }
+    case T_SPACECHARGE: {
+      // frozen space charge (section "Space charge", frozen model): the beam's
+      // own Gaussian line charge of peak density lambda0 [1/m], electric and
+      // magnetic forces cancelling to 1/gamma^2, integrated over the length L
+      // the lumped element stands for:
+      // Delta p_perp / P0 = 2 r_c lambda0 L / (beta0^2 gamma0^3) g(zeta) f(x - x_c, y - y_c),
+      // r_c = q0^2 r_e m_e / m0, g = exp(-zeta^2 / (2 sigma_z^2)) (1 when sigma_z = 0)
+      const double lam0 = e.p[0], sz = e.p[1], L = e.p[4];
+      const double rcl = rc.q0 * rc.q0 * R_ELECTRON * M_ELECTRON / rc.m0;
+      BBConst& b = q.bb;
+      b.K = 2.0 * rcl * lam0 * L / (rc.beta0 * rc.beta0 * rc.gamma0 * rc.gamma0 * rc.gamma0);
+      b.xc = e.p[5];
+      b.yc = e.p[6];
+      gauss_shape(b, e.p[2], e.p[3]);
+      q.sc_i2sz2 = (sz > 0.0) ? 1.0 / (2.0 * (sz * sz)) : 0.0;
       break;
     }
     default: break;
@@ -874,6 +900,16 @@ static inline void track_element(Part<T>& p, const Prep& q, int rad_mode, const 
       gauss_field(val(p.x) - q.bb.xc, val(p.y) - q.bb.yc, q.bb, &fx, &fy);
       p.px = FMA(q.bb.K, fx, p.px);
       p.py = FMA(q.bb.K, fy, p.py);
+      break;
+    }
+    case T_SPACECHARGE: {  // values only, like the beam-beam lens
+      double fx, fy;
+      gauss_field(val(p.x) - q.bb.xc, val(p.y) - q.bb.yc, q.bb, &fx, &fy);
+      const double zt = val(p.zeta);
+      const double g = (q.sc_i2sz2 > 0.0) ? exp_cw(-((zt * zt) * q.sc_i2sz2)) : 1.0;
+      const double Kg = q.bb.K * g;
+      p.px = FMA(Kg, fx, p.px);
+      p.py = FMA(Kg, fy, p.py);
       break;
     }
     // Rectangular aperture: lost unless xmin <= x <= xmax and ymin <= y <= ymax
@@ -1294,6 +1330,15 @@ static bool inverse_row(Part<double>& p, const Prep& q, const RefConst& rc) {
       p.py = std::fma(-q.bb.K, fy, p.py);
       return true;
     }
+    case T_SPACECHARGE: {  // x, y, zeta unchanged by the kick: take the same kick back
+      double fx, fy;
+      gauss_field(p.x - q.bb.xc, p.y - q.bb.yc, q.bb, &fx, &fy);
+      const double g = (q.sc_i2sz2 > 0.0) ? exp_cw(-((p.zeta * p.zeta) * q.sc_i2sz2)) : 1.0;
+      const double Kg = q.bb.K * g;
+      p.px = std::fma(-Kg, fx, p.px);
+      p.py = std::fma(-Kg, fy, p.py);
+      return true;
+    }
     case T_XYSHIFT:
       p.x = p.x + q.dx;
       p.y = p.y + q.dy;
@@ -1318,7 +1363,7 @@ extern "C" {
 // A table row the oracle accepts: a known type, a multipole order 0..10, a
 // bend model 0 (expanded) or 1 (full, without gradient).
 static bool row_ok(const Element& e) {
-  if (e.type < 0 || e.type > T_BEND) return false;
+  if (e.type < 0 || e.type > T_SPACECHARGE) return false;
   if (e.type == T_MULTIPOLE && (e.order < 0 || e.order > 10)) return false;
   if (e.type == T_BEND && !(e.p[4] == 0.0 || (e.p[4] == 1.0 && e.p[3] == 0.0))) return false;
   return true;
@@ -1503,7 +1548,7 @@ int xo_track_jacobian(const Element* el, int64_t n_el, const Reference* ref, int
                       double* along) {
   if (!el || !ref || n_el <= 0 || rad_mode < 0 || rad_mode > 1) return -1;
   for (int64_t e = 0; e < n_el; e++)
-    if (!row_ok(el[e]) || el[e].type == T_BEAMBEAM4D) return -1;  // value-only element
+    if (!row_ok(el[e]) || el[e].type == T_BEAMBEAM4D || el[e].type == T_SPACECHARGE) return -1;  // value-only
   const RefConst rc = ref_const(*ref);
   std::vector<Prep> prep(n_el);
   for (int64_t e = 0; e < n_el; e++) prep[e] = prepare(el[e], rc);

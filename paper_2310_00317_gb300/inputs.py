@@ -26,7 +26,7 @@ import numpy as np
 ELEMENT_DTYPE = np.dtype([("type", "<i4"), ("order", "<i4"), ("p", "<f8", (48,))], align=True)
 MARKER, DRIFT, MULTIPOLE, CAVITY, DIPEDGE, LINEARMAP, APERTURE = 0, 1, 2, 3, 4, 5, 6
 XYSHIFT, SROTATION, APERTURE_RECT, APERTURE_ELLIPSE = 7, 8, 9, 10
-BEAMBEAM4D, QUAD, BEND = 11, 12, 13
+BEAMBEAM4D, QUAD, BEND, SPACECHARGE = 11, 12, 13, 14
 MAX_ORDER = 10
 
 C_LIGHT = 299792458.0
@@ -114,6 +114,14 @@ def beambeam4d(q_n: float, beta_s: float, sigma_x: float, sigma_y: float, x_c: f
     """4D weak-strong beam-beam lens: strong bunch of q_n = charge x particles
     [e] at speed beta_s against the beam, Gaussian sigma_x, sigma_y, centre."""
     return _row(BEAMBEAM4D, 0, [q_n, beta_s, sigma_x, sigma_y, x_c, y_c])
+
+
+def spacecharge(line_density: float, sigma_z: float, sigma_x: float, sigma_y: float, length: float,
+                x_c: float = 0.0, y_c: float = 0.0):
+    """Frozen space-charge lens: the beam's own Gaussian charge, peak line
+    density [particles/m], bunch length sigma_z [m] (0: coasting beam),
+    transverse sigma_x, sigma_y [m], for `length` [m] of ring, centre."""
+    return _row(SPACECHARGE, 0, [line_density, sigma_z, sigma_x, sigma_y, length, x_c, y_c])
 
 
 def aperture_rect(x_min: float, x_max: float, y_min: float, y_max: float):

@@ -1113,6 +1113,86 @@ def test_nonlinear_edge_against_soft_fringe_integration(exit_face):
     assert gn_e[2] < 0.2 * gl_e[2] and gn_e[3] < 0.02 * gl_e[3]
 
 
+# --------------------------------------------------------------------------
+# Frozen space charge
+
+def test_space_charge_kick_from_the_fields_of_the_beam():
+    """A round coasting beam: the kick equals the Lorentz force of the
+    beam's own fields integrated over the lens length, worked out in SI
+    units here (Gauss's law for the radial field of the Gaussian line
+    charge, B = beta E / c, so the force is q E / gamma^2; time L / (beta c);
+    momentum gamma m beta c), in 40-digit arithmetic."""
+    mp = mpmath.mp
+    mp.dps = 40
+    lam, sig, L = 5e10, 1.2e-3, 3.0
+    ref = PROTON
+    el = I.table([I.spacecharge(lam, 0.0, sig, sig, L)])
+    xs = np.array([3e-4, -1.1e-3, 2.5e-3, 4e-6])
+    ys = np.array([1e-4, 7e-4, -1.9e-3, -2e-6])
+    n = len(xs)
+    p = I.make_particles(ref, xs, np.zeros(n), ys, np.zeros(n), np.zeros(n), np.zeros(n))
+    o = oracle.track(el, ref, p, 1)
+    e, eps0, c = mpmath.mpf("1.602176634e-19"), mpmath.mpf("8.8541878128e-12"), mpmath.mpf(299792458)
+    m_kg = mpmath.mpf(ref[0]) * e / c ** 2
+    E0 = mpmath.sqrt(mpmath.mpf(ref[2]) ** 2 + mpmath.mpf(ref[0]) ** 2)
+    gamma, beta = E0 / ref[0], mpmath.mpf(ref[2]) / E0
+    p0 = gamma * m_kg * beta * c
+    for i in range(n):
+        x, y = mpmath.mpf(xs[i]), mpmath.mpf(ys[i])
+        r2 = x * x + y * y
+        Er = lam * e / (2 * mpmath.pi * eps0) * (1 - mpmath.exp(-r2 / (2 * sig ** 2))) / r2  # E_x / x
+        kick = e * Er * (1 - beta ** 2) * (L / (beta * c)) / p0
+        # r_e m_e c^2 and e^2 / (4 pi eps0) from rounded CODATA values agree to ~1e-11
+        assert abs(o["px"][i] - float(kick * x)) < 1e-10 * abs(float(kick * x))
+        assert abs(o["py"][i] - float(kick * y)) < 1e-10 * abs(float(kick * y))
+
+
+def test_space_charge_longitudinal_profile():
+    """Bunched: the kick at zeta = sigma_z is e^(-1/2) times the kick at the
+    bunch centre, at 2 sigma_z e^(-2); coasting (sigma_z = 0): no zeta
+    dependence."""
+    sz = 0.3
+    xs = np.full(3, 1e-3)
+    p = I.make_particles(PROTON, xs, np.zeros(3), np.full(3, 5e-4), np.zeros(3), np.array([0.0, sz, -2 * sz]),
+                         np.zeros(3))
+    o = oracle.track(I.table([I.spacecharge(4e10, sz, 1e-3, 6e-4, 2.0)]), PROTON, p, 1)
+    assert abs(o["px"][1] / o["px"][0] - math.exp(-0.5)) < 1e-15
+    assert abs(o["px"][2] / o["px"][0] - math.exp(-2.0)) < 1e-15
+    assert abs(o["py"][1] / o["py"][0] - math.exp(-0.5)) < 1e-15
+    oc = oracle.track(I.table([I.spacecharge(4e10, 0.0, 1e-3, 6e-4, 2.0)]), PROTON, p, 1)
+    assert oc["px"][0] == oc["px"][1] == oc["px"][2] and oc["px"][0] == o["px"][0]
+
+
+def test_space_charge_linear_tune_shift():
+    """A 2 GeV/c proton ring (linear, tune Q0) with one round space-charge
+    lens: the small-amplitude one-turn matrix (by differences of tracked
+    particles) has cos(2 pi Q) = cos(mu0) + (beta k / 2) sin(mu0) with the
+    defocusing k = K / (2 sigma^2), K = 2 r_c lambda L / (beta0^2 gamma0^3)."""
+    ref = I.proton_reference(2e9)
+    lam, sig, L, beta, Q0 = 3e9, 8e-4, 50.0, 12.0, 0.27
+    mu = 2 * math.pi * Q0
+    M = np.eye(6)
+    for k in (0, 2):
+        M[k, k], M[k, k + 1], M[k + 1, k], M[k + 1, k + 1] = (math.cos(mu), beta * math.sin(mu),
+                                                              -math.sin(mu) / beta, math.cos(mu))
+    el = I.table([I.linear_map(M), I.spacecharge(lam, 0.0, sig, sig, L)])
+    m0, _, p0c = ref
+    E0 = math.hypot(p0c, m0)
+    b0, g0 = p0c / E0, E0 / m0
+    rc = 2.8179403262e-15 * 0.51099895000e6 / m0
+    K = 2 * rc * lam * L / (b0 * b0 * g0 ** 3)
+    kdef = K / (2 * sig * sig)
+    eps = 1e-9
+    p = I.make_particles(ref, [eps, -eps, 0.0, 0.0], [0.0, 0.0, eps / beta, -eps / beta], np.zeros(4),
+                         np.zeros(4), np.zeros(4), np.zeros(4))
+    o = oracle.track(el, ref, p, 1)
+    m11 = (o["x"][0] - o["x"][1]) / (2 * eps)
+    m22 = (o["px"][2] - o["px"][3]) / (2 * eps / beta)
+    want = math.cos(mu) + beta * kdef / 2 * math.sin(mu)
+    assert abs(0.5 * (m11 + m22) - want) < 1e-7
+    assert want > math.cos(mu) + 0.05  # defocusing: the tune moves well away
+
+
 def test_segment_resume_bitwise():
     """track(a) then track(b) from turn a equals track(a+b), radiation included."""
     el, ref, _ = I.lepton_ring(n_cells=4, E0=5e9, v_total=30e6)
