@@ -153,6 +153,18 @@ extern "C" {
                            state -2 if the particle cannot reach the exit
                            plane.  Delta and ptau are unchanged.  Loss
                            refinement steps through it like a drift.        */
+#define XT_SPACECHARGE 14 /* Frozen space-charge lens (section "Space charge",
+                           frozen model): p[0] = peak line density lambda0
+                           [particles/m], p[1] = sigma_z [m] (> 0 a Gaussian
+                           bunch; 0 a coasting beam), p[2], p[3] = sigma_x,
+                           sigma_y [m] (> 0), p[4] = length L [m] of ring the
+                           lumped lens stands for, p[5], p[6] = beam centre.
+                           px += K g f_x, py += K g f_y with
+                           K = 2 r_c lambda0 L / (beta0^2 gamma0^3),
+                           r_c = q0^2 r_e m_e / m0, g = exp(-zeta^2 /
+                           (2 sigma_z^2)) (1 when coasting) and f the field
+                           shape of XT_BEAMBEAM4D at (x - x_c, y - y_c).
+                           Independent of delta.                            */
 
 #define XT_MAX_ORDER 10
 #define XT_NPARAM 48

@@ -67,8 +67,38 @@ int64_t flops_of_row(const xt_element& e, int rad_mode) {
       const double sx2 = e.p[2] * e.p[2], sy2 = e.p[3] * e.p[3];
       return (std::fabs(sx2 - sy2) <= 1e-10 * (sx2 + sy2)) ? 20 : 650;
     }
+    case XT_SPACECHARGE: {  // the same field, plus the longitudinal profile of a bunch (5)
+      const double sx2 = e.p[2] * e.p[2], sy2 = e.p[3] * e.p[3];
+      return ((std::fabs(sx2 - sy2) <= 1e-10 * (sx2 + sy2)) ? 20 : 650) + ((e.p[1] > 0.0) ? 5 : 0);
+    }
     default: return 0;
   }
+}
+
+// Field-shape constants of a bi-Gaussian line charge into prm[3..11]: [3]
+// mode (0 round when the squares agree to 1e-10, 1 sigma_x > sigma_y, 2
+// otherwise), then 1/(2 s1^2), 1/(2 s2^2), s2/s1, s1/s2, 1/S, sqrt(pi)/S,
+// 1/(s1 (s1 + s2)), 1/(s2 (s1 + s2)) with s1 the larger sigma and
+// S = sqrt(2 (s1^2 - s2^2)); round: [4] = 1/(sigma_x^2 + sigma_y^2).
+static void gauss_shape(double* prm, double sx, double sy) {
+  const double sx2 = sx * sx, sy2 = sy * sy;
+  if (std::fabs(sx2 - sy2) <= 1e-10 * (sx2 + sy2)) {
+    prm[3] = 0.0;
+    prm[4] = 1.0 / (sx2 + sy2);
+    return;
+  }
+  const bool flat = sx2 > sy2;
+  const double s1 = flat ? sx : sy, s2 = flat ? sy : sx;
+  const double S = std::sqrt(2.0 * (s1 * s1 - s2 * s2));
+  prm[3] = flat ? 1.0 : 2.0;
+  prm[4] = 1.0 / (2.0 * (s1 * s1));
+  prm[5] = 1.0 / (2.0 * (s2 * s2));
+  prm[6] = s2 / s1;
+  prm[7] = s1 / s2;
+  prm[8] = 1.0 / S;
+  prm[9] = 1.772453850905516 / S;
+  prm[10] = 1.0 / (s1 * (s1 + s2));
+  prm[11] = 1.0 / (s2 * (s1 + s2));
 }
 
 static void put(std::vector<uint8_t>& b, const void* p, size_t n) {
@@ -175,30 +205,31 @@ int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice*
           *err = "element " + std::to_string(i) + ": beam-beam lens needs sigma_x, sigma_y > 0 and 0 < beta_s <= 1";
           return XT_ERR_INVALID;
         }
-        const double sx2 = sx * sx, sy2 = sy * sy;
         // kick of a counter-moving Gaussian bunch integrated over the crossing
         const double K = 2.0 * rc.q0 * qN * (RE_M * ME_EV) / rc.p0c * ((1.0 + rc.beta0 * bs) / (rc.beta0 + bs));
         prm.assign(12, 0.0);
         prm[0] = K;
         prm[1] = e.p[4];
         prm[2] = e.p[5];
-        if (std::fabs(sx2 - sy2) <= 1e-10 * (sx2 + sy2)) {
-          prm[3] = 0.0;  // round
-          prm[4] = 1.0 / (sx2 + sy2);
-        } else {
-          const bool flat = sx2 > sy2;
-          const double s1 = flat ? sx : sy, s2 = flat ? sy : sx;
-          const double S = std::sqrt(2.0 * (s1 * s1 - s2 * s2));
-          prm[3] = flat ? 1.0 : 2.0;
-          prm[4] = 1.0 / (2.0 * (s1 * s1));
-          prm[5] = 1.0 / (2.0 * (s2 * s2));
-          prm[6] = s2 / s1;
-          prm[7] = s1 / s2;
-          prm[8] = 1.0 / S;
-          prm[9] = 1.772453850905516 / S;
-          prm[10] = 1.0 / (s1 * (s1 + s2));
-          prm[11] = 1.0 / (s2 * (s1 + s2));
+        gauss_shape(prm.data(), sx, sy);
+        break;
+      }
+      case XT_SPACECHARGE: {
+        const double lam0 = e.p[0], sz = e.p[1], sx = e.p[2], sy = e.p[3], L = e.p[4];
+        if (!(sx > 0.0 && sy > 0.0 && sz >= 0.0 && lam0 >= 0.0 && L >= 0.0) || !std::isfinite(lam0) ||
+            !std::isfinite(L) || !std::isfinite(sz)) {
+          *err = "element " + std::to_string(i) +
+                 ": space-charge lens needs sigma_x, sigma_y > 0, sigma_z >= 0, a line density >= 0 and L >= 0";
+          return XT_ERR_INVALID;
         }
+        // the beam's own field, electric and magnetic forces cancelling to 1/gamma^2
+        const double rcl = rc.q0 * rc.q0 * RE_M * ME_EV / rc.m0;
+        prm.assign(13, 0.0);
+        prm[0] = 2.0 * rcl * lam0 * L / (rc.beta0 * rc.beta0 * rc.gamma0 * rc.gamma0 * rc.gamma0);
+        prm[1] = e.p[5];
+        prm[2] = e.p[6];
+        gauss_shape(prm.data(), sx, sy);
+        prm[12] = (sz > 0.0) ? 1.0 / (2.0 * (sz * sz)) : 0.0;
         break;
       }
       case XT_QUAD: {
@@ -247,7 +278,7 @@ int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice*
     h.size16 = (uint16_t)(bytes / 16);
     h.elem = (uint32_t)i;
     out->row_rec[(size_t)i] = (int32_t)out->bytes.size();
-    if (e.type == XT_BEAMBEAM4D || e.type == XT_QUAD || e.type == XT_BEND ||
+    if (e.type == XT_BEAMBEAM4D || e.type == XT_SPACECHARGE || e.type == XT_QUAD || e.type == XT_BEND ||
         (e.type == XT_DIPEDGE && (flags & REC_ENL)))
       out->thick = true;
     out->rec_off.push_back((uint32_t)out->bytes.size());

@@ -767,6 +767,17 @@ __device__ __forceinline__ int element(Part& p, uint32_t type, uint32_t order, u
       }
       return 1;
     }
+    case XT_SPACECHARGE: {  // prm: K, centre, field constants, 1/(2 sigma_z^2) (0: coasting)
+      if constexpr (THICK) {
+        double fx, fy;
+        bb_field(p.x - prm[1], p.y - prm[2], prm, &fx, &fy);
+        const double g = (prm[12] > 0.0) ? exp_cw(-((p.zeta * p.zeta) * prm[12])) : 1.0;
+        const double Kg = prm[0] * g;
+        p.px = fma(Kg, fx, p.px);
+        p.py = fma(Kg, fy, p.py);
+      }
+      return 1;
+    }
     case XT_XYSHIFT:  // change of reference frame: displaced by (dx, dy)
       p.x = p.x - prm[0];
       p.y = p.y - prm[1];
@@ -1147,6 +1158,15 @@ __device__ __forceinline__ bool inverse_record(Part& p, uint32_t type, uint32_t 
       bb_field(p.x - prm[1], p.y - prm[2], prm, &fx, &fy);
       p.px = fma(-prm[0], fx, p.px);
       p.py = fma(-prm[0], fy, p.py);
+      return true;
+    }
+    case XT_SPACECHARGE: {  // x, y, zeta unchanged by the kick: take the same kick back
+      double fx, fy;
+      bb_field(p.x - prm[1], p.y - prm[2], prm, &fx, &fy);
+      const double g = (prm[12] > 0.0) ? exp_cw(-((p.zeta * p.zeta) * prm[12])) : 1.0;
+      const double Kg = prm[0] * g;
+      p.px = fma(-Kg, fx, p.px);
+      p.py = fma(-Kg, fy, p.py);
       return true;
     }
     case XT_XYSHIFT:
