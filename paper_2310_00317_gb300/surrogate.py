@@ -17,7 +17,7 @@ version of it; every computation runs in the library's kernels:
    (``xt_track``), ``xs_da_combine`` forms the per-ray DA and flags rays whose
    boundary touches a predicted point, which are widened and re-tracked.
 
-The plain FP64 scan tracks every grid point and is the judge of the
+The plain FP64 scan tracks every grid point and is the arbiter of the
 surrogate's DA error, stated in beam sigmas.  A non-learned baseline places the
 band from a coarse FP64 grid instead.
 """
