@@ -464,6 +464,50 @@ def test_batched_seeds_equal_individual():
         t.close()
 
 
+def test_batched_mixed_thin_and_thick_seeds():
+    """A batch mixing a thin-lattice seed with thick-element seeds runs the
+    thick instantiation of the batched kernel for all of them: plain and
+    graph launches equal per-seed tracking and the oracle, bit for bit."""
+    seeds = [(I.table(bend_ring(n_cells=4)), PROTON, 700, 3e-3),
+             (I.table(thick_quad_ring(n_cells=5)), PROTON, 1300, 1.2e-3),
+             (I.fodo10()[0], PROTON, 250, 3e-3)]
+    trs, ps, ref_out = [], [], []
+    for i, (el, ref, n, sx) in enumerate(seeds):
+        p = random_particles(ref, n, 200 + i, sx=sx, spx=sx / 3, sd=5e-4)
+        trs.append(xtgb.Tracker(el, ref))
+        ps.append(p)
+        ref_out.append(oracle.track(el, ref, p, 40))
+    for graph in (False, True):
+        P = [xtgb.Particles.from_numpy(p) for p in ps]
+        xtgb.track_batched(trs, P, 15, 0, graph=graph)
+        xtgb.track_batched(trs, P, 25, 15, graph=graph)
+        assert xtgb.batched_sync_status(trs, P) == xtgb.XT_OK
+        for i in range(len(seeds)):
+            assert_same(P[i].to_numpy(), ref_out[i], "seed %d graph %d: " % (i, graph))
+    xtgb.batched_release()
+    for t in trs:
+        t.close()
+
+
+@pytest.mark.parametrize("rad", [1, 2])
+def test_radiation_with_thick_elements_bitwise(rad):
+    """A small lepton ring with thick quadrupoles, a full bend between
+    non-linear edges and a beam-beam lens added, mean and quantum radiation
+    (the radiating instantiations of the thick kernel): bit for bit."""
+    el0, ref, _ = I.lepton_ring(n_cells=4, E0=5e9, v_total=30e6)
+    rows = list(el0)
+    h = 0.01
+    extra = [I.quadrupole(0.02, 0.5), I.dipedge(h, 0.02, nonlinear=True), I.bend(h, h, 1.0, full=True),
+             I.dipedge(h, 0.02, nonlinear=True, exit=True), I.quadrupole(-0.02, 0.5),
+             I.beambeam4d(5e9, 1.0, 3e-4, 1e-4)]
+    rows = rows[:len(rows) // 2] + extra + rows[len(rows) // 2:]
+    el = I.table(rows)
+    q = I.matched_gaussian(el0, ref, 800, 1e-3, 1e-3, seed=11)
+    g = gpu_track(el, ref, q, 25, radiation=rad, seed=3)
+    o = oracle.track(el, ref, q, 25, rad_mode=rad, seed=3)
+    assert_same(g, o)
+
+
 def test_quantum_radiation_bitwise_and_distribution():
     """Quantum model: reproducible bit for bit on the GPU for a given seed,
     segmentation-independent, equal to the oracle bit for bit, and the energy
