@@ -44,9 +44,9 @@ SM_MAX_MHZ = 2070.0
 NOMINAL_FP64 = FP64_FLOP_PER_CLK_SM * N_SM * SM_MAX_MHZ * 1e6
 # DRAM bytes (read + write) of a tracking launch per particle and turn: ncu
 # capture of the current kernel on a 60,000-particle subset of this workload
-# over one turn (6,918,144 B read, 0 B written).  The per-launch traffic is the
+# over one turn (7,375,616 B read, 0 B written).  The per-launch traffic is the
 # particle state, so it scales with the particle count.
-TRACK_DRAM_BYTES_PER_PARTICLE_TURN = 6918144.0 / 60000.0
+TRACK_DRAM_BYTES_PER_PARTICLE_TURN = 7375616.0 / 60000.0
 
 
 def dist_env():
