@@ -299,12 +299,13 @@ static RefConst ref_const(const Reference& r) {
 // ---------------------------------------------------------------------------
 // Special functions of the beam-beam kick (section "Beam-beam interactions").
 
-// 1/n! for n = 0..18 (n! is exact in double up to 18!).
+// 1/n! for n = 0..21 (n! is exact in double up to 18!; beyond, the running
+// product rounds, far below what the series that use these terms resolve).
 static const std::vector<double>& inv_fact() {
   static std::vector<double> c = [] {
-    std::vector<double> v(19);
+    std::vector<double> v(22);
     double f = 1.0;
-    for (int n = 0; n <= 18; n++) {
+    for (int n = 0; n <= 21; n++) {
       if (n > 0) f = f * (double)n;
       v[n] = 1.0 / f;
     }
@@ -351,9 +352,8 @@ static double one_minus_exp(double u) {
   return 1.0 - exp_cw(-u);
 }
 
-// cos a and sin(a)/a, cosh a and sinh(a)/a for a >= 0: series in a^2 below
-// a = 1/2 (to a^16 / 17!, truncation below 1e-19), else from sin_cw/cos_cw and
-// two exponentials.
+// e^a for scalars and dual numbers (the hyperbolic branch of the oscillator
+// functions of the thick elements).
 static inline double EXPC(double a) { return exp_cw(a); }
 static inline Dual EXPC(const Dual& a) {
   Dual r; r.v = exp_cw(a.v);
@@ -953,50 +953,19 @@ static inline void turn_guard(Part<T>& p, int turn, int n_el) {
 // quadrupoles).  Transverse motion is harmonic with w^2 = |k1| / (1+delta):
 // cos/sin in the focusing plane, cosh/sinh in the other; zeta gains
 // dzeta/ds = 1 - (1/rvv)(1 + (px^2 + py^2) / (2 (1+delta)^2)) integrated in
-// closed form.  Evaluated at a = w |L| with the sign of L carried through, so
-// that the same map with -L is its inverse.
+// closed form.  cos a, sin(a)/a, cosh a and sinh(a)/a at a = w |L| are the
+// oscillator functions (osc_funcs) at z = |k1| L^2 / (1+delta) and -z; the
+// sign of L is carried through, so that the same map with -L is its inverse.
 template <class T>
-static inline void trig_sa(const T& a, T* C, T* Sa) {
-  const std::vector<double>& c = inv_fact();
-  *C = COS(a);
-  if (val(a) < 0.5) {
-    const T z = a * a;
-    T p = mkv<T>(c[17]);
-    for (int n = 7; n >= 0; n--) p = FMA(p, -z, mkv<T>(c[2 * n + 1]));
-    *Sa = p;
-  } else {
-    *Sa = SIN(a) / a;
-  }
-}
-template <class T>
-static inline void hyp_sa(const T& a, T* Ch, T* Sha) {
-  const std::vector<double>& c = inv_fact();
-  if (val(a) < 0.5) {
-    const T z = a * a;
-    T p = mkv<T>(c[17]);
-    for (int n = 7; n >= 0; n--) p = FMA(p, z, mkv<T>(c[2 * n + 1]));
-    *Sha = p;
-    T q = mkv<T>(c[18]);
-    for (int n = 8; n >= 0; n--) q = FMA(q, z, mkv<T>(c[2 * n]));
-    *Ch = q;
-  } else {
-    const T e = EXPC(a), ei = EXPC(-a);
-    *Ch = 0.5 * (e + ei);
-    *Sha = (0.5 * (e - ei)) / a;
-  }
-}
+static inline void osc_funcs(const T& z, T* C, T* S, T* S2, T* S3);
 template <class T>
 static inline void thick_quad(Part<T>& p, double k1, double L) {
   if (L == 0.0) return;
   const T aK = (k1 >= 0.0) ? k1 * p.rpp : (-k1) * p.rpp;  // |k1| / (1+delta)
-  // aK vanishes only for k1 = 0, where the map depends on a^2 alone: there w
-  // takes aK itself (same value, sqrt(+-0) = +-0) so that dual numbers carry a
-  // zero derivative instead of 0 * inf.
-  const T w = (k1 == 0.0) ? aK : SQRT(aK);
-  const T a = w * std::fabs(L);
-  T C, Sa, Ch, Sha;
-  trig_sa(a, &C, &Sa);
-  hyp_sa(a, &Ch, &Sha);
+  const T z = aK * (L * L);
+  T C, Sa, Ch, Sha, u2, u3;
+  osc_funcs(z, &C, &Sa, &u2, &u3);     // cos a, sin(a)/a
+  osc_funcs(-z, &Ch, &Sha, &u2, &u3);  // cosh a, sinh(a)/a
   T* u = (k1 >= 0.0) ? &p.x : &p.y;   // focusing plane
   T* pu = (k1 >= 0.0) ? &p.px : &p.py;
   T* v = (k1 >= 0.0) ? &p.y : &p.x;
@@ -1072,19 +1041,17 @@ static inline void edge_nonlinear(Part<T>& p, double k0, double t, double sgn, d
 
 // Entire functions of z (either sign) with a = sqrt|z|: C = cos a,
 // S = sin(a)/a, S2 = (1 - C)/z, S3 = (1 - S)/z for z > 0 (cosh and sinh for
-// z < 0).  Series in z below |z| = 1/4 (C and S to z^8, S2 and S3 to z^7:
-// truncation below 1e-18), else from sin_cw/cos_cw or two exponentials.
+// z < 0).  Series in z below |z| = 1 (each to z^9: truncation below 1e-21),
+// else from sin_cw/cos_cw or two exponentials.
 template <class T>
 static inline void osc_funcs(const T& z, T* C, T* S, T* S2, T* S3) {
   const std::vector<double>& f = inv_fact();
-  if (std::fabs(val(z)) < 0.25) {
+  if (std::fabs(val(z)) < 1.0) {
     const T mz = -z;
-    T c = mkv<T>(f[16]), s = mkv<T>(f[17]), s2 = mkv<T>(f[16]), s3 = mkv<T>(f[17]);
-    for (int n = 7; n >= 0; n--) {
+    T c = mkv<T>(f[18]), s = mkv<T>(f[19]), s2 = mkv<T>(f[20]), s3 = mkv<T>(f[21]);
+    for (int n = 8; n >= 0; n--) {
       c = FMA(c, mz, mkv<T>(f[2 * n]));
       s = FMA(s, mz, mkv<T>(f[2 * n + 1]));
-    }
-    for (int n = 6; n >= 0; n--) {
       s2 = FMA(s2, mz, mkv<T>(f[2 * n + 2]));
       s3 = FMA(s3, mz, mkv<T>(f[2 * n + 3]));
     }

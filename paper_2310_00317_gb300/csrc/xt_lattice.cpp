@@ -58,10 +58,10 @@ int64_t flops_of_row(const xt_element& e, int rad_mode) {
     // the path-length integral (36) and zeta (9)
     case XT_QUAD: return (e.p[1] == 0.0) ? 0 : 76;
     // expanded: two sets of oscillator functions (20), the 4x4 map (18), the
-    // integrals (50) and zeta (10); full: the sector functions (10), pz and
-    // the exit momentum (20), x (10), the chord and the arc length (45), y and
-    // zeta (8)
-    case XT_BEND: return (e.p[4] != 0.0) ? 93 : 98;
+    // integrals (50) and zeta (10); full (the sector functions are per-element
+    // constants): pz and the exit momentum (20), x (10), the chord and the arc
+    // length (45), y and zeta (8)
+    case XT_BEND: return (e.p[4] != 0.0) ? 83 : 98;
     case XT_BEAMBEAM4D: {
       // round: the field and the kick; else two 40-term w(z) (~300 each), e^x and the rest
       const double sx2 = e.p[2] * e.p[2], sy2 = e.p[3] * e.p[3];
@@ -99,6 +99,63 @@ static void gauss_shape(double* prm, double sx, double sy) {
   prm[9] = 1.772453850905516 / S;
   prm[10] = 1.0 / (s1 * (s1 + s2));
   prm[11] = 1.0 / (s2 * (s1 + s2));
+}
+
+// The device's sine/cosine (trig_cw: Cody-Waite reduction by pi/2, Taylor
+// series on |r| <= pi/4 with the coefficients of sin_table), on the host, for
+// per-element constants that the device would otherwise recompute for every
+// particle.  shift 0: sine, 1: cosine.
+static double host_trig_cw(double x, const SinTab& t, int shift) {
+  const double P1 = 1.5707963267948965579989817342720925807952880859375;
+  const double P2 = 6.123233995736766035868820147291818682e-17;
+  const double P3 = -1.4973849048591698329435081771059e-33;
+  const double TOP = 0.63661977236758134307553505349005744813783858296183;
+  const double SH = 6755399441055744.0;
+  const double k = (x * TOP + SH) - SH;
+  double r = std::fma(-k, P1, x);
+  r = std::fma(-k, P2, r);
+  r = std::fma(-k, P3, r);
+  const int q = (int)(((long long)k + shift) & 3);
+  const double z = r * r;
+  double res;
+  if (q & 1) {
+    double pc = t.c[10];
+    for (int i = 9; i >= 0; i--) pc = std::fma(pc, z, t.c[i]);
+    res = pc;
+  } else {
+    double ps = t.s[9];
+    for (int i = 8; i >= 1; i--) ps = std::fma(ps, z, t.s[i]);
+    res = std::fma(r * z, ps, r);
+  }
+  return (q & 2) ? -res : res;
+}
+
+// C = cos a, S = sin(a)/a, S2 = (1 - C)/z at z = a^2 >= 0, by the device's
+// oscillator-function steps (series in z below 1 with 1/n! from the special
+// table, else host_trig_cw): the full bend's sector constants at z = (h L)^2.
+static void sector_funcs(double z, double* C, double* S, double* S2) {
+  double f[22];
+  double fact = 1.0;
+  for (int n = 0; n <= 21; n++) {
+    if (n > 0) fact = fact * (double)n;
+    f[n] = 1.0 / fact;
+  }
+  if (std::fabs(z) < 1.0) {
+    const double mz = -z;
+    double c = f[18], s = f[19], s2 = f[20];
+    for (int n = 8; n >= 0; n--) {
+      c = std::fma(c, mz, f[2 * n]);
+      s = std::fma(s, mz, f[2 * n + 1]);
+      s2 = std::fma(s2, mz, f[2 * n + 2]);
+    }
+    *C = c; *S = s; *S2 = s2;
+    return;
+  }
+  const SinTab t = sin_table();
+  const double a = std::sqrt(z);
+  *C = host_trig_cw(a, t, 1);
+  *S = host_trig_cw(a, t, 0) / a;
+  *S2 = (1.0 - *C) / z;
 }
 
 static void put(std::vector<uint8_t>& b, const void* p, size_t n) {
@@ -254,7 +311,15 @@ int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice*
           return XT_ERR_INVALID;
         }
         prm = {k0, h, L, k1};
-        if (model == 1.0) flags |= REC_BFULL;
+        if (model == 1.0) {  // the sector's constants once: C, S, S2 at z = (h L)^2
+          flags |= REC_BFULL;
+          const double th = h * L;
+          double C, S, S2;
+          sector_funcs(th * th, &C, &S, &S2);
+          prm.push_back(C);
+          prm.push_back(S);
+          prm.push_back(S2);
+        }
         break;
       }
       case XT_APERTURE_ELLIPSE:
@@ -330,8 +395,9 @@ SinTab sin_table() {
 // p(Z) in Weideman's rational expansion of the Faddeeva function
 // (J. A. C. Weideman, SIAM J. Numer. Anal. 31 (1994) 1497; N = 40 terms,
 // L = (N / sqrt 2)^(1/2), the cosine transform of e^(-t^2)(L^2 + t^2) at
-// t = L tan(theta/2) by a plain DFT), [41..59] 1/n! for n = 0..18; and for
-// the thick bend's arc length [60..73] the coefficients a_n of
+// t = L tan(theta/2) by a plain DFT), [41..62] 1/n! for n = 0..21 (the running
+// product n! rounds beyond 18!); and for the thick bend's arc length [63..76]
+// the coefficients a_n of
 // asin(v)/v = sum a_n v^(2n), a_n = (2n)! / (4^n n!^2 (2n+1)) from the
 // running product t_n = t_(n-1) (2n-1) / (2n), a_n = t_n / (2n+1).
 void special_table(double* out) {
@@ -354,7 +420,7 @@ void special_table(double* out) {
     out[1 + n] = acc / (double)M2;
   }
   double fact = 1.0;
-  for (int n = 0; n <= 18; n++) {
+  for (int n = 0; n <= 21; n++) {
     if (n > 0) fact = fact * (double)n;
     out[XT_SPECIAL_FACT + n] = 1.0 / fact;
   }

@@ -427,21 +427,18 @@ __device__ __forceinline__ void bb_field(double x, double y, const double* prm, 
 
 // Entire functions of z (either sign) with a = sqrt|z|: C = cos a,
 // S = sin(a)/a, S2 = (1 - C)/z, S3 = (1 - S)/z for z > 0 (cosh and sinh for
-// z < 0).  Series in z below |z| = 1/4 (1/n! from the special table), else
-// from trig_cw or two exponentials.
+// z < 0).  Series in z below |z| = 1, each to z^9 (1/n! from the special
+// table), else from trig_cw or two exponentials.
 __device__ __forceinline__ void osc_funcs(double z, const SinTab& sn, double* C, double* S, double* S2,
                                           double* S3) {
-  if (fabs(z) < 0.25) {
+  if (fabs(z) < 1.0) {
     const double mz = -z;
     const double* f = c_special + XT_SPECIAL_FACT;
-    double c = f[16], s = f[17], s2 = f[16], s3 = f[17];
+    double c = f[18], s = f[19], s2 = f[20], s3 = f[21];
 #pragma unroll
-    for (int n = 7; n >= 0; n--) {
+    for (int n = 8; n >= 0; n--) {
       c = fma(c, mz, f[2 * n]);
       s = fma(s, mz, f[2 * n + 1]);
-    }
-#pragma unroll
-    for (int n = 6; n >= 0; n--) {
       s2 = fma(s2, mz, f[2 * n + 2]);
       s3 = fma(s3, mz, f[2 * n + 3]);
     }
@@ -527,10 +524,11 @@ __device__ __forceinline__ void bend_expanded(Part& p, double k0, double h, doub
 // length is chord * asin(u)/u, u = k0 chord / (2 p_h), and y, zeta follow it.
 // Returns 1, or -2 (lost) if pz or pz' is not real or the exit plane is not
 // reached.
-__device__ __forceinline__ int bend_full(Part& p, double k0, double h, double L, const SinTab& sn) {
+// C, S, S2: the oscillator functions at z = (h L)^2 (from the record, or
+// bend_full below for other lengths).
+__device__ __forceinline__ int bend_full_c(Part& p, double k0, double h, double L, double C, double S,
+                                           double S2) {
   const double th = h * L, L2 = L * L;
-  double C, S, S2, S3;
-  osc_funcs(th * th, sn, &C, &S, &S2, &S3);
   const double snt = th * S, Sh = L * S, Ch = (h * L2) * S2, D2 = 2.0 * (L2 * S2);
   const double u = fma(-p.px, p.px, fma(-p.py, p.py, p.dm1));  // pz^2 - 1
   if (!(u > -1.0 && u < INFINITY)) return -2;
@@ -559,6 +557,12 @@ __device__ __forceinline__ int bend_full(Part& p, double k0, double h, double L,
   p.zeta = p.zeta + fma(-p.ep, lr, L);
   return 1;
 }
+__device__ __forceinline__ int bend_full(Part& p, double k0, double h, double L, const SinTab& sn) {
+  const double th = h * L;
+  double C, S, S2, S3;
+  osc_funcs(th * th, sn, &C, &S, &S2, &S3);
+  return bend_full_c(p, k0, h, L, C, S, S2);
+}
 
 // Thick quadrupole (section "Lattice modelling and single particle tracking"):
 // the exact flow, over a length L of either sign, of the expanded Hamiltonian
@@ -567,32 +571,14 @@ __device__ __forceinline__ int bend_full(Part& p, double k0, double h, double L,
 // fx) and cosh / sinh in the other; zeta gains
 // L (1 - 1/rvv) - (1 / (2 rvv (1+delta)^2)) * integral of (px^2 + py^2) ds,
 // the integral in closed form.  C = cos a, Sa = sin(a)/a, Ch = cosh a and
-// Sha = sinh(a)/a at a = w |L|: series in a^2 (1/n! from the special table)
-// below a = 1/2, else from trig_cw and two exponentials.
+// Sha = sinh(a)/a at a = w |L| are the oscillator functions at
+// z = |k1| L^2 / (1+delta) and -z.
 __device__ __forceinline__ void thick_quad(Part& p, double absk1, double L, bool fx, const SinTab& sn) {
   const double aK = absk1 * p.rpp;
-  const double a = sqrt(aK) * fabs(L);
-  const double C = trig_cw(a, sn, 1);
-  double Sa, Ch, Sha;
-  if (a < 0.5) {
-    const double z = a * a;
-    double ps = c_special[41 + 17], ph = c_special[41 + 17], pc = c_special[41 + 18];
-#pragma unroll
-    for (int n = 7; n >= 0; n--) {
-      ps = fma(ps, -z, c_special[41 + 2 * n + 1]);
-      ph = fma(ph, z, c_special[41 + 2 * n + 1]);
-    }
-#pragma unroll
-    for (int n = 8; n >= 0; n--) pc = fma(pc, z, c_special[41 + 2 * n]);
-    Sa = ps;
-    Sha = ph;
-    Ch = pc;
-  } else {
-    Sa = trig_cw(a, sn, 0) / a;
-    const double e = exp_cw(a), ei = exp_cw(-a);
-    Ch = 0.5 * (e + ei);
-    Sha = (0.5 * (e - ei)) / a;
-  }
+  const double z = aK * (L * L);
+  double C, Sa, Ch, Sha, u2, u3;
+  osc_funcs(z, sn, &C, &Sa, &u2, &u3);
+  osc_funcs(-z, sn, &Ch, &Sha, &u2, &u3);
   const double u0 = fx ? p.x : p.y, pu0 = fx ? p.px : p.py;
   const double v0 = fx ? p.y : p.x, pv0 = fx ? p.py : p.px;
   const double g = (aK * L) * Sa;    // w sin(w L)
@@ -820,7 +806,7 @@ __device__ __forceinline__ int element(Part& p, uint32_t type, uint32_t order, u
       return 1;
     case XT_BEND:  // prm = k0, h, L, k1; flags = REC_BFULL for the full model
       if constexpr (THICK) {
-        if (flags & REC_BFULL) return bend_full(p, prm[0], prm[1], prm[2], sn);
+        if (flags & REC_BFULL) return bend_full_c(p, prm[0], prm[1], prm[2], prm[4], prm[5], prm[6]);
         bend_expanded(p, prm[0], prm[1], prm[2], prm[3], sn);
       }
       return 1;
@@ -1149,7 +1135,7 @@ __device__ __forceinline__ bool inverse_record(Part& p, uint32_t type, uint32_t 
       thick_quad(p, prm[0], -prm[1], (flags & REC_QF) != 0, sn);
       return true;
     case XT_BEND:
-      if (flags & REC_BFULL) return bend_full(p, prm[0], prm[1], -prm[2], sn) == 1;
+      if (flags & REC_BFULL) return bend_full_c(p, prm[0], prm[1], -prm[2], prm[4], prm[5], prm[6]) == 1;
       bend_expanded(p, prm[0], prm[1], -prm[2], prm[3], sn);
       return true;
     case XT_LINEARMAP: return false;
