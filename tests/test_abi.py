@@ -82,3 +82,33 @@ def test_traversed_element_count():
     before = np.array([1, 1, 1, 0], np.int32)
     # survivor: 2 turns x 20; lost at (5,10): 0*20+11; lost at (6,0): 20+1; not alive before: 0
     assert xtgb.traversed_elements(p, 20, 5, 2, before) == 40 + 11 + 21
+
+
+def test_create_rejects_bad_element_parameters_before_cuda(L):
+    """Every parameter rule of the element rows is checked by the lattice
+    compiler before any CUDA call: XT_ERR_INVALID, with the row named."""
+    el, ref = I.fodo10()
+    r = xtgb._Reference(*ref)
+    bad_rows = [
+        I.quadrupole(0.1, -1.0),                      # negative length
+        I.quadrupole(float("nan"), 1.0),              # non-finite gradient
+        I._row(I.BEND, 0, [0.1, 0.1, 1.0, 0.0, 2.0]),  # unknown model
+        I.bend(0.1, 0.1, 1.0, k1=0.2, full=True),     # gradient in the full model
+        I.bend(0.1, 0.1, -1.0),                       # negative length
+        I.bend(0.1, float("inf"), 1.0),               # non-finite curvature
+        I._row(I.DIPEDGE, 0, [0.1, 0.1, 0.0, 0.0, 2.0, 0.0]),  # unknown edge model
+        I._row(I.DIPEDGE, 0, [0.1, 0.1, 0.0, 0.0, 1.0, 3.0]),  # unknown face
+        I.spacecharge(1e10, 0.0, 0.0, 1e-3, 1.0),     # zero sigma_x
+        I.spacecharge(-1e10, 0.0, 1e-3, 1e-3, 1.0),   # negative line density
+        I.spacecharge(1e10, -0.1, 1e-3, 1e-3, 1.0),   # negative sigma_z
+        I.beambeam4d(1e11, 1.5, 1e-3, 1e-3),          # beta_s > 1
+        I.aperture_ellipse(0.0, 0.01),                # zero semi-axis
+        I.aperture_rect(0.01, -0.01, -0.01, 0.01),    # x_min > x_max
+    ]
+    for row in bad_rows:
+        t = I.table(list(el)[:3] + [row] + list(el)[3:])
+        h = ctypes.c_void_p()
+        rc = L.xt_tracker_create(t.ctypes.data, t.shape[0], ctypes.byref(r), None, ctypes.byref(h))
+        assert rc == xtgb.XT_ERR_INVALID, (row, rc)
+        assert "element 3" in xtgb.last_error(), xtgb.last_error()
+        assert not h.value

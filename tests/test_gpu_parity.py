@@ -320,6 +320,36 @@ def test_space_charge_lenses_bitwise():
     assert_same(g, o)
 
 
+def test_thick_element_edge_cases_bitwise():
+    """Degenerate and extreme thick rows, bit for bit: a quadrupole without
+    gradient, one of zero length, strong ones past |z| = 1 (trigonometric
+    and exponential branches); full bends without field (a curved drift),
+    without curvature (a straight dipole), with the field reversed, of
+    1.5 rad (host trigonometry for the sector constants, two angle
+    halvings), of zero length; expanded bends of zero length and with a
+    strong gradient; non-linear edges at zero and negative angles;
+    space-charge lenses with no charge and of zero length."""
+    rows = [I.cavity(2e6, 400e6, 180.0), I.quadrupole(0.0, 0.7), I.quadrupole(-0.3, 0.0), I.drift(0.4),
+            I.quadrupole(5.0, 0.6), I.drift(0.3), I.quadrupole(-5.0, 0.6), I.drift(0.3),
+            I.dipedge(0.3, 0.0, nonlinear=True), I.bend(0.3, 0.3, 5.0, full=True),
+            I.dipedge(-0.3, -0.1, nonlinear=True, exit=True),
+            # each off-design bend followed by one that takes the orbit back
+            I.bend(0.0, 0.05, 1.0, full=True), I.bend(0.1, 0.05, 1.0, full=True),
+            I.bend(0.05, 0.0, 1.0, full=True), I.bend(-0.05, 0.0, 1.0, full=True),
+            I.bend(-0.05, 0.05, 1.0, full=True), I.bend(0.15, 0.05, 1.0, full=True),
+            I.bend(0.05, 0.05, 0.0), I.bend(0.05, 0.05, 0.0, full=True), I.bend(0.0, 0.0, 1.0),
+            I.bend(0.04, 0.05, 1.0, k1=-1.2), I.spacecharge(0.0, 0.3, 1e-3, 1e-3, 1.0),
+            I.spacecharge(1e10, 0.2, 2e-3, 1e-3, 0.0), I.aperture(0.5)]
+    el = I.table(rows)
+    p = random_particles(PROTON, 1200, 103, sx=1e-4, spx=5e-5, sd=1e-3)
+    # one pass keeps every particle; as a ring the line is unstable, and the
+    # second pass loses them all in the full bend (code -2)
+    for turns, want in ((1, 1), (2, -2)):
+        g, o = gpu_track(el, PROTON, p, turns), oracle.track(el, PROTON, p, turns)
+        assert_same(g, o)
+        assert np.all(o["state"] == want)
+
+
 def bb_lens(qN, beta_s, sx, sy, xc=0.0, yc=0.0):
     return I.beambeam4d(qN, beta_s, sx, sy, xc, yc)
 
