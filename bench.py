@@ -670,7 +670,7 @@ def main():
                     help="time only this many surrogate training steps (batch 4096)")
     ap.add_argument("--only", default="",
                     help="run one extra measurement alone and print its JSON: thick_elements[:n[:turns]], "
-                         "beambeam_lens[:n[:turns]] or twiss")
+                         "beambeam_lens[:n[:turns]], lepton_quantum[:n[:turns]] or twiss")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -689,7 +689,8 @@ def run_only(spec: str) -> int:
         kw["n"] = int(nums[0])
     if len(nums) > 1:
         kw["turns"] = int(nums[1])
-    fn = {"thick_elements": measure_thick, "beambeam_lens": measure_beambeam, "twiss": measure_twiss}.get(name)
+    fn = {"thick_elements": measure_thick, "beambeam_lens": measure_beambeam, "twiss": measure_twiss,
+          "lepton_quantum": measure_lepton}.get(name)
     if fn is None:
         raise SystemExit("--only: unknown measurement %r" % name)
     print(json.dumps({name: fn(**kw)}))
