@@ -232,6 +232,8 @@ static const double SPEC_XI_MIN = 1e-7, SPEC_XI_MAX = 40.0;
 struct Spectrum {
   double xi[SPEC_K], F[SPEC_K];
   int guide[SPEC_GUIDE];  // guide[j] = max{i : F[i] <= j / SPEC_GUIDE} (Chen and Asau, 1974)
+  double idF[SPEC_K];     // 1 / (F[i+1] - F[i]): the interpolation multiplies instead of dividing
+  double iF0;             // 1 / F[0]
   Spectrum() {
     const double norm = 5.0 * PI / 3.0, h = 0.05;
     for (int i = 0; i < SPEC_K; i++) {
@@ -254,18 +256,21 @@ struct Spectrum {
       while (i + 1 < SPEC_K && F[i + 1] <= t) i++;
       guide[j] = i;
     }
+    for (int k = 0; k + 1 < SPEC_K; k++) idF[k] = 1.0 / (F[k + 1] - F[k]);
+    idF[SPEC_K - 1] = 0.0;
+    iF0 = 1.0 / F[0];
   }
   // Inverse CDF: power-law asymptote F ~ xi^(1/3) below the first knot,
   // linear interpolation between knots lo and lo + 1 with
   // lo = max{i : F[i] <= u} (walked up from the guide entry of u's cell),
   // clamp above the last knot.
   double sample(double u) const {
-    if (u < F[0]) { double q = u / F[0]; return xi[0] * q * q * q; }
+    if (u < F[0]) { double q = u * iF0; return xi[0] * q * q * q; }
     if (u >= F[SPEC_K - 1]) return xi[SPEC_K - 1];
     int lo = guide[(int)(u * (double)SPEC_GUIDE)];
     while (F[lo + 1] <= u) lo++;
     const int hi = lo + 1;
-    double w = (u - F[lo]) / (F[hi] - F[lo]);
+    double w = (u - F[lo]) * idF[lo];
     return xi[lo] + w * (xi[hi] - xi[lo]);
   }
 };
@@ -593,6 +598,16 @@ struct MultConst {
 // nbar = (5/(2 sqrt 3)) alpha q0^2 gamma h L, energies u = u_c xi with
 // u_c = (3/2) hbar c gamma^3 h and xi drawn from the synchrotron spectrum.
 static const int KMAX_PHOTONS = 200;
+// 1/k for k = 0..KMAX_PHOTONS (entry 0 unused): the Poisson recurrence
+// pk = pk nbar / k multiplies by it.
+static const std::vector<double>& recip_k() {
+  static std::vector<double> r = [] {
+    std::vector<double> v(KMAX_PHOTONS + 1, 0.0);
+    for (int k = 1; k <= KMAX_PHOTONS; k++) v[k] = 1.0 / (double)k;
+    return v;
+  }();
+  return r;
+}
 static inline void quantum_kick(Part<double>& p, double br, double bi, const MultConst& m,
                                 const RefConst& rc, uint64_t seed, int turn, int elem) {
   double kk = std::fma(br, br, bi * bi);
@@ -603,7 +618,8 @@ static inline void quantum_kick(Part<double>& p, double br, double bi, const Mul
   double u0 = U.next();
   int k = 0;
   double pk = exp_cw(-nbar), F = pk;
-  while (u0 > F && k < KMAX_PHOTONS) { k++; pk = (pk * nbar) / (double)k; F = F + pk; }
+  const std::vector<double>& rk = recip_k();
+  while (u0 > F && k < KMAX_PHOTONS) { k++; pk = (pk * nbar) * rk[k]; F = F + pk; }
   if (k == 0) return;
   const Spectrum& S = spectrum();
   double sxi = 0.0;

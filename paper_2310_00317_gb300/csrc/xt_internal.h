@@ -171,9 +171,10 @@ int launch_refine(const RefineArgs& a, void* stream);
 // Constant table of the special functions (beam-beam kick, thick elements;
 // XT_SPECIAL_N doubles, see special_table) for the current device's
 // constant memory.
-#define XT_SPECIAL_N 77
-#define XT_SPECIAL_FACT 41  // 1/n!, n = 0..21
-#define XT_SPECIAL_ASIN 63  // asin(v)/v series coefficients, n = 0..13
+#define XT_SPECIAL_N 278
+#define XT_SPECIAL_FACT 41    // 1/n!, n = 0..21
+#define XT_SPECIAL_ASIN 63    // asin(v)/v series coefficients, n = 0..13
+#define XT_SPECIAL_RECIP 77   // 1/k, k = 0..200 (entry 0 unused): the photon-count recurrence
 void special_table(double* out);
 int upload_special_table(const double* tab);
 

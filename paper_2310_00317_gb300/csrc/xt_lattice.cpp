@@ -400,6 +400,7 @@ SinTab sin_table() {
 // the coefficients a_n of
 // asin(v)/v = sum a_n v^(2n), a_n = (2n)! / (4^n n!^2 (2n+1)) from the
 // running product t_n = t_(n-1) (2n-1) / (2n), a_n = t_n / (2n+1).
+// [77..277] 1/k for k = 0..200 (the photon-count recurrence; entry 0 unused).
 void special_table(double* out) {
   const int N = 40, M = 2 * N, M2 = 2 * M;
   const double L = std::sqrt((double)N / std::sqrt(2.0));
@@ -429,6 +430,8 @@ void special_table(double* out) {
     if (n > 0) t = (t * (double)(2 * n - 1)) / (double)(2 * n);
     out[XT_SPECIAL_ASIN + n] = t / (double)(2 * n + 1);
   }
+  out[XT_SPECIAL_RECIP] = 0.0;
+  for (int k = 1; k <= 200; k++) out[XT_SPECIAL_RECIP + k] = 1.0 / (double)k;
 }
 
 // Photon-number spectrum of synchrotron radiation in xi = u/u_c:
@@ -471,6 +474,12 @@ void photon_table(std::vector<double>* xi, std::vector<double>* F, std::vector<i
     while (i + 1 < K && (*F)[i + 1] <= t) i++;
     (*guide)[j] = i;
   }
+  // after the K knots: 1 / (F[k+1] - F[k]) for each interval (0 for the last
+  // knot), then 1 / F[0], so that the sampler multiplies instead of dividing
+  F->resize(2 * K + 1);
+  for (int k = 0; k + 1 < K; k++) (*F)[K + k] = 1.0 / ((*F)[k + 1] - (*F)[k]);
+  (*F)[2 * K - 1] = 0.0;
+  (*F)[2 * K] = 1.0 / (*F)[0];
 }
 
 }  // namespace xt

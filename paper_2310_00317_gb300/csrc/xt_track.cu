@@ -226,19 +226,19 @@ __device__ __forceinline__ double uni_next(Uni& u) {
 // Inverse CDF of the photon spectrum: power-law asymptote F ~ xi^(1/3) below
 // the first knot, clamp above the last, else linear interpolation on the
 // knot interval [lo, lo+1] with lo = max{i : F[i] <= u}, found by walking up
-// from the guide table's entry for u's cell of width 1/XT_SPEC_GUIDE.
+// from the guide table's entry for u's cell of width 1/XT_SPEC_GUIDE.  F
+// holds the K knots, then 1/(F[k+1] - F[k]) per interval and 1/F[0].
 __device__ __forceinline__ double sample_xi(double u, const double* xi, const double* F, const int32_t* guide,
                                             int K) {
   const double F0 = __ldg(F);
   if (u < F0) {
-    const double q = u / F0;
+    const double q = u * __ldg(F + 2 * K);
     return __ldg(xi) * q * q * q;
   }
   if (u >= __ldg(F + K - 1)) return __ldg(xi + K - 1);
   int lo = __ldg(guide + (int)(u * (double)XT_SPEC_GUIDE));
   while (__ldg(F + lo + 1) <= u) lo++;
-  const double Fl = __ldg(F + lo), Fh = __ldg(F + lo + 1);
-  const double w = (u - Fl) / (Fh - Fl);
+  const double w = (u - __ldg(F + lo)) * __ldg(F + K + lo);
   const double xl = __ldg(xi + lo);
   return xl + w * (__ldg(xi + lo + 1) - xl);
 }
@@ -676,7 +676,7 @@ __device__ __forceinline__ void multipole(Part& p, const double* prm, int order,
     double pk = exp_cw(-nbar), F = pk;
     while (u0 > F && k < 200) {
       k++;
-      pk = (pk * nbar) / (double)k;
+      pk = (pk * nbar) * c_special[XT_SPECIAL_RECIP + k];
       F = F + pk;
     }
     if (k > 0) {
