@@ -482,9 +482,10 @@ template <> inline Dual mkv<Dual>(double v) { return mkd(v); }
 
 // ---------------------------------------------------------------------------
 // Particle state; opd = 1+delta, dm1 = (1+delta)^2 - 1 = delta (delta + 2),
-// rv0v = 1/rvv, ep = opd*rv0v (= 1 + beta0 ptau) and epm1 = beta0 ptau are
-// derived from delta, rvv and ptau and recomputed whenever those change (pure
-// functions of the stored state, so recomputation never changes a result).
+// ep = 1 + beta0 ptau (= opd / rvv), rv0v = 1/rvv = ep rpp and
+// epm1 = beta0 ptau are derived from delta, rpp and ptau and recomputed
+// whenever those change (pure functions of the stored state, so
+// recomputation never changes a result).
 template <class T>
 struct Part {
   T x, px, y, py, zeta, delta, ptau, rpp, rvv;
@@ -496,15 +497,15 @@ template <class T>
 static inline void derive(Part<T>& p, const RefConst& rc) {
   p.opd = 1.0 + p.delta;
   p.dm1 = p.delta * (p.delta + 2.0);
-  p.rv0v = 1.0 / p.rvv;
-  p.ep = p.opd * p.rv0v;
+  p.ep = FMA(rc.beta0, p.ptau, 1.0);
+  p.rv0v = p.ep * p.rpp;
   p.epm1 = rc.beta0 * p.ptau;
 }
 
 // Energy update from a new ptau, using (1+delta)^2 = 1 + 2 ptau/beta0 + ptau^2
 // written in the cancellation-free form delta = u / (sqrt(1+u) + 1),
-// u = ptau (ptau + 2/beta0); then rpp = 1/(1+delta) and
-// rvv = (1+delta)/(1 + beta0 ptau).
+// u = ptau (ptau + 2/beta0); then rpp = 1/(1+delta),
+// rvv = (1+delta)/(1 + beta0 ptau) and 1/rvv = (1 + beta0 ptau) rpp.
 template <class T>
 static inline void energy_update(Part<T>& p, const RefConst& rc) {
   T u = p.ptau * (p.ptau + rc.twoib0);
@@ -513,9 +514,9 @@ static inline void energy_update(Part<T>& p, const RefConst& rc) {
   p.opd = 1.0 + p.delta;
   p.dm1 = p.delta * (p.delta + 2.0);
   p.rpp = 1.0 / p.opd;
-  p.rvv = p.opd / FMA(rc.beta0, p.ptau, 1.0);
-  p.rv0v = 1.0 / p.rvv;
-  p.ep = p.opd * p.rv0v;
+  p.ep = FMA(rc.beta0, p.ptau, 1.0);
+  p.rvv = p.opd / p.ep;
+  p.rv0v = p.ep * p.rpp;
   p.epm1 = rc.beta0 * p.ptau;
 }
 

@@ -124,17 +124,18 @@ __device__ __forceinline__ bool abs_le_one(double v) { return abs_bits(v) <= 0x3
 
 // ---------------------------------------------------------------------------
 // Particle state in registers.  opd = 1+delta, dm1 = (1+delta)^2 - 1,
-// rv0v = 1/rvv, ep = opd*rv0v are derived from the stored state.
+// rv0v = 1/rvv and ep = 1 + beta0 ptau are derived from the stored state.
 struct Part {
   double x, px, y, py, zeta, delta, ptau, rpp, rvv;
   double opd, dm1, rv0v, ep, epm1;  // epm1 = beta0 ptau (= ep - 1)
 };
 
+// ep = 1 + beta0 ptau (= opd / rvv), rv0v = 1/rvv = ep rpp
 __device__ __forceinline__ void derive(Part& p, const RefDev& r) {
   p.opd = 1.0 + p.delta;
   p.dm1 = p.delta * (p.delta + 2.0);
-  p.rv0v = 1.0 / p.rvv;
-  p.ep = p.opd * p.rv0v;
+  p.ep = fma(r.beta0, p.ptau, 1.0);
+  p.rv0v = p.ep * p.rpp;
   p.epm1 = r.beta0 * p.ptau;
 }
 
@@ -146,9 +147,9 @@ __device__ __forceinline__ void energy_update(Part& p, const RefDev& r) {
   p.opd = 1.0 + p.delta;
   p.dm1 = p.delta * (p.delta + 2.0);
   p.rpp = 1.0 / p.opd;
-  p.rvv = p.opd / fma(r.beta0, p.ptau, 1.0);
-  p.rv0v = 1.0 / p.rvv;
-  p.ep = p.opd * p.rv0v;
+  p.ep = fma(r.beta0, p.ptau, 1.0);
+  p.rvv = p.opd / p.ep;
+  p.rv0v = p.ep * p.rpp;
   p.epm1 = r.beta0 * p.ptau;
 }
 
