@@ -519,6 +519,32 @@ def test_batched_mixed_thin_and_thick_seeds():
         t.close()
 
 
+def test_batched_seeds_with_quantum_radiation():
+    """Quantum radiation in a batch of two lepton rings, one with thick rows
+    (so the batch runs the radiating thick instantiation): plain and graph
+    launches equal per-seed tracking and the oracle, bit for bit."""
+    el0, ref, _ = I.lepton_ring(n_cells=4, E0=5e9, v_total=30e6)
+    rows = list(el0)
+    thick = I.table(rows[:20] + [I.quadrupole(0.02, 0.5), I.quadrupole(-0.02, 0.5)] + rows[20:])
+    seeds = [(el0, 600), (thick, 900)]
+    trs, ps, ref_out = [], [], []
+    for i, (el, n) in enumerate(seeds):
+        q = I.matched_gaussian(el0, ref, n, 1e-3, 1e-3, seed=300 + i)
+        trs.append(xtgb.Tracker(el, ref, radiation=xtgb.RAD_QUANTUM, seed=17))
+        ps.append(q)
+        ref_out.append(oracle.track(el, ref, q, 20, rad_mode=2, seed=17))
+    for graph in (False, True):
+        P = [xtgb.Particles.from_numpy(q) for q in ps]
+        xtgb.track_batched(trs, P, 8, 0, graph=graph)
+        xtgb.track_batched(trs, P, 12, 8, graph=graph)
+        assert xtgb.batched_sync_status(trs, P) == xtgb.XT_OK
+        for i in range(len(seeds)):
+            assert_same(P[i].to_numpy(), ref_out[i], "seed %d graph %d: " % (i, graph))
+    xtgb.batched_release()
+    for t in trs:
+        t.close()
+
+
 @pytest.mark.parametrize("rad", [1, 2])
 def test_radiation_with_thick_elements_bitwise(rad):
     """A small lepton ring with thick quadrupoles, a full bend between
