@@ -61,3 +61,31 @@ def test_unstable_matrix_is_rejected():
     M[2:, 2:] = cs_block(6.0, 0.0, 1.0)
     with pytest.raises(RuntimeError):
         T.normal_modes(M)
+
+
+def test_scale_magnets_scales_fields_not_geometry():
+    """Tapering scales field strengths only: thin multipole knl and ksl,
+    quadrupole k1, bend k0 and k1, edge h; never the frame curvature hxl,
+    L_rad, the bend's h and length, nor other rows."""
+    from paper_2310_00317_gb300 import inputs as I
+    rows = [I.multipole(knl=[0.01, 0.2, 0.3], ksl=[0.0, 0.05], hxl=0.01, lrad=2.0), I.quadrupole(0.1, 0.5),
+            I.bend(0.02, 0.02, 1.0, k1=-0.1), I.dipedge(0.02, 0.1, hgap=0.03, fint=0.5), I.drift(1.0),
+            I.cavity(1e6, 4e8, 180.0)]
+    el = I.table(rows)
+    f = np.array([1.01, 1.02, 1.03, 1.04, 1.05, 1.06])
+    sc = T.scale_magnets(el, f)
+    assert np.array_equal(sc[0]["p"][:22], el[0]["p"][:22] * 1.01)
+    assert sc[0]["p"][22] == el[0]["p"][22] and sc[0]["p"][23] == el[0]["p"][23]
+    assert sc[1]["p"][0] == el[1]["p"][0] * 1.02 and sc[1]["p"][1] == el[1]["p"][1]
+    assert sc[2]["p"][0] == el[2]["p"][0] * 1.03 and sc[2]["p"][3] == el[2]["p"][3] * 1.03
+    assert sc[2]["p"][1] == el[2]["p"][1] and sc[2]["p"][2] == el[2]["p"][2]
+    assert sc[3]["p"][0] == el[3]["p"][0] * 1.04 and np.array_equal(sc[3]["p"][1:], el[3]["p"][1:])
+    assert np.array_equal(sc[4]["p"], el[4]["p"]) and np.array_equal(sc[5]["p"], el[5]["p"])
+    assert np.array_equal(el[1]["p"][:2], [0.1, 0.5])  # the input table is not modified
+
+
+def test_row_lengths():
+    from paper_2310_00317_gb300 import inputs as I
+    el = I.table([I.drift(1.5), I.quadrupole(0.1, 0.4), I.bend(0.01, 0.01, 2.5), I.multipole(knl=[0, 0.1]),
+                  I.aperture(0.02), I.spacecharge(1e10, 0.0, 1e-3, 1e-3, 3.0)])
+    assert np.array_equal(T.row_lengths(el), [1.5, 0.4, 2.5, 0.0, 0.0, 0.0])
