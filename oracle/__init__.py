@@ -90,6 +90,8 @@ def lib() -> ctypes.CDLL:
             L.xo_faddeeva.restype = None
             L.xo_gauss_field.argtypes = [dbl, dbl, P, P, P, P, i64]
             L.xo_gauss_field.restype = None
+            L.xo_lyapunov.argtypes = [P, i64, P, i32, P, P, P, i64, i64, i64, P, P, P]
+            L.xo_lyapunov.restype = i32
             _lib = L
     return _lib
 
@@ -174,6 +176,88 @@ def closed_orbit(elements, ref, rad_mode: int = 0, dim: int = 6, guess=None) -> 
     if it < 0:
         raise ValueError("closed orbit search failed")
     return z
+
+
+def lyapunov(elements, ref, z0, dz0, n_turns: int, every: int = 10, metric=None,
+             rad_mode: int = 0, growth: float = 1e3) -> dict:
+    """Chaos marker (twin-particle finite-time Lyapunov estimate, xo_lyapunov).
+
+    z0: (n, 6) canonical starts (x, px, y, py, zeta, pzeta); dz0: the twin's
+    offset (6,); metric: 6x6 matrix A of the distance |A dz| (identity if
+    None).  Returns sum_log, turns, lost (0 both survived, 1 only one lost or
+    lost at different turns, 2 both lost in the same turn), lam = sum_log /
+    turns, and chaotic: the twin was lost alone, or the separation grew by
+    more than ``growth`` times the turn count, sum_log > ln(growth * turns).
+    A regular orbit separates at most linearly in the turn count, so the
+    default leaves it three orders of magnitude of room."""
+    el = _elements(elements)
+    r = _ref_arr(ref)
+    z = np.ascontiguousarray(np.asarray(z0, dtype=np.float64).reshape(-1, 6))
+    d = np.ascontiguousarray(np.asarray(dz0, dtype=np.float64).reshape(6))
+    A = None if metric is None else np.ascontiguousarray(np.asarray(metric, dtype=np.float64).reshape(36))
+    n = z.shape[0]
+    S = np.zeros(n)
+    T = np.zeros(n, dtype=np.int32)
+    L = np.zeros(n, dtype=np.int32)
+    rc = lib().xo_lyapunov(_ptr(el), el.shape[0], _ptr(r), rad_mode, _ptr(z), _ptr(d),
+                           None if A is None else _ptr(A), n, int(n_turns), int(every),
+                           _ptr(S), _ptr(T), _ptr(L))
+    if rc != 0:
+        raise ValueError("oracle lyapunov rejected its arguments")
+    lam = S / np.maximum(T, 1)
+    chaotic = (L == 1) | (S > np.log(growth * np.maximum(T, 1)))
+    return dict(sum_log=S, turns=T, lost=L, lam=lam, chaotic=chaotic)
+
+
+def _track_job(args):
+    elements, ref, particles, n_turns = args
+    return track(elements, ref, particles, n_turns)
+
+
+def _lyapunov_job(args):
+    elements, ref, z0, dz0, n_turns, every, metric = args
+    return lyapunov(elements, ref, z0, dz0, n_turns, every=every, metric=metric)
+
+
+def _chunks(n: int, procs: int):
+    k = max(1, min(procs, n))
+    return [c for c in np.array_split(np.arange(n), k) if c.size]
+
+
+def track_parallel(elements, ref, particles: dict, n_turns: int, procs: int | None = None) -> dict:
+    """``track`` split over ``procs`` spawned processes (one particle slice
+    each; the particles are independent, so the result is the same)."""
+    import multiprocessing as mp
+    lib()  # built once here, not by every worker
+    n = np.asarray(particles["x"]).shape[0]
+    procs = procs or os.cpu_count() or 1
+    parts = _chunks(n, procs)
+    jobs = [(elements, ref, {k: np.asarray(particles[k])[c] for k in FLOAT_FIELDS + INT_FIELDS + ("particle_id",)},
+             n_turns) for c in parts]
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        res = pool.map(_track_job, jobs)
+    return {k: np.concatenate([r[k] for r in res]) for k in res[0]}
+
+
+def lyapunov_parallel(elements, ref, z0, dz0, n_turns: int, every: int = 10, metric=None,
+                      procs: int | None = None) -> dict:
+    """``lyapunov`` split over ``procs`` spawned processes."""
+    import multiprocessing as mp
+    lib()
+    z = np.asarray(z0, dtype=np.float64).reshape(-1, 6)
+    procs = procs or os.cpu_count() or 1
+    parts = _chunks(z.shape[0], procs)
+    jobs = [(elements, ref, z[c], dz0, n_turns, every, metric) for c in parts]
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        res = pool.map(_lyapunov_job, jobs)
+    return {k: np.concatenate([r[k] for r in res]) for k in res[0]}
+
+
+def canonical(particles: dict, ref) -> np.ndarray:
+    """(n, 6) canonical coordinates (x, px, y, py, zeta, pzeta = ptau/beta0)."""
+    beta0 = ref_constants(ref)["beta0"]
+    return np.stack([np.asarray(particles[k], dtype=np.float64) for k in ("x", "px", "y", "py", "zeta")]
+                    + [np.asarray(particles["ptau"], dtype=np.float64) / beta0], axis=1)
 
 
 def sin(x: float) -> float:

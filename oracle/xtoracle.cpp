@@ -1602,6 +1602,97 @@ int xo_closed_orbit(const Element* el, int64_t n_el, const Reference* ref, int r
   return -1;
 }
 
+// Chaos marker: finite-time Lyapunov estimate by the twin-particle method of
+// Benettin, Galgani and Strelcyn (Phys. Rev. A 14, 2338 (1976)).  It tells
+// regular orbits, whose neighbours separate at most linearly in the number of
+// turns, from chaotic ones, where a separation grows exponentially and any
+// rounding difference reaches the loss turn.
+//
+// Particle i starts at canonical z = (x, px, y, py, zeta, pzeta) (row i of
+// z0, n x 6; pzeta = ptau/beta0), its twin at z + dz0.  Both are tracked turn
+// by turn with the maps and loss checks of xo_track (radiation 0 or 1).
+// After every `every` turns, and after the last one, the separation
+// d = |A (z_twin - z)| is measured in the metric A (6 x 6 row-major, the
+// identity if NULL); ln(d / d0), d0 = |A dz0|, is added to sum_log[i] and the
+// twin is moved back to distance d0 along the current separation.
+// turns[i] = turns completed by both; lost[i] = 0 if both survived, 2 if
+// both were lost in the same turn, 1 if only one of them was lost (or the
+// separation stopped being finite and positive).  The estimate is
+// lambda = sum_log / turns per turn.  Returns 0, or -1 on bad input.
+int xo_lyapunov(const Element* el, int64_t n_el, const Reference* ref, int rad_mode,
+                const double* z0, const double* dz0, const double* metric, int64_t n,
+                int64_t n_turns, int64_t every, double* sum_log, int32_t* turns, int32_t* lost) {
+  if (!el || !ref || !z0 || !dz0 || n_el <= 0 || n < 0 || n_turns < 0 || every < 1 ||
+      rad_mode < 0 || rad_mode > 1)
+    return -1;
+  const RefConst rc = ref_const(*ref);
+  std::vector<Prep> prep(n_el);
+  for (int64_t e = 0; e < n_el; e++) {
+    if (!row_ok(el[e])) return -1;
+    prep[e] = prepare(el[e], rc);
+  }
+  double A[36];
+  for (int k = 0; k < 36; k++) A[k] = metric ? metric[k] : (k % 7 == 0 ? 1.0 : 0.0);
+  auto norm = [&](const double* v) {
+    double s = 0.0;
+    for (int r = 0; r < 6; r++) {
+      double w = 0.0;
+      for (int c = 0; c < 6; c++) w += A[6 * r + c] * v[c];
+      s += w * w;
+    }
+    return std::sqrt(s);
+  };
+  auto set = [&](Part<double>& p, const double* z, int64_t id) {
+    p.x = z[0]; p.px = z[1]; p.y = z[2]; p.py = z[3]; p.zeta = z[4];
+    p.ptau = z[5] * rc.beta0;
+    p.state = 1; p.at_turn = 0; p.at_element = 0; p.id = id;
+    energy_update(p, rc);
+  };
+  auto get = [&](const Part<double>& p, double* z) {
+    z[0] = p.x; z[1] = p.px; z[2] = p.y; z[3] = p.py; z[4] = p.zeta; z[5] = p.ptau * rc.ib0;
+  };
+  auto one_turn = [&](Part<double>& p, int64_t t) {
+    for (int64_t e = 0; e < n_el && p.state == 1; e++) track_element(p, prep[e], rad_mode, rc, 0, (int)t, (int)e);
+    if (p.state == 1) turn_guard(p, (int)t, (int)n_el);
+  };
+  const double d0 = norm(dz0);
+  if (!(d0 > 0.0) || !std::isfinite(d0)) return -1;
+  for (int64_t i = 0; i < n; i++) {
+    double zp[6], zq[6];
+    for (int k = 0; k < 6; k++) { zp[k] = z0[6 * i + k]; zq[k] = zp[k] + dz0[k]; }
+    Part<double> p, q;
+    set(p, zp, i);
+    set(q, zq, i);
+    double S = 0.0;
+    int64_t t = 0;
+    int32_t code = 0;
+    while (t < n_turns) {
+      one_turn(p, t);
+      one_turn(q, t);
+      if (p.state != 1 || q.state != 1) {
+        code = (p.state != 1 && q.state != 1) ? 2 : 1;
+        break;
+      }
+      t++;
+      if (t % every == 0 || t == n_turns) {
+        get(p, zp);
+        get(q, zq);
+        double dv[6];
+        for (int k = 0; k < 6; k++) dv[k] = zq[k] - zp[k];
+        const double d = norm(dv);
+        if (!(d > 0.0) || !std::isfinite(d)) { code = 1; break; }
+        S += std::log(d / d0);
+        for (int k = 0; k < 6; k++) zq[k] = zp[k] + dv[k] * (d0 / d);
+        set(q, zq, i);
+      }
+    }
+    sum_log[i] = S;
+    turns[i] = (int32_t)t;
+    lost[i] = code;
+  }
+  return 0;
+}
+
 // Test hooks for the building blocks.
 double xo_sin(double x) { return sin_cw(x); }
 
