@@ -195,9 +195,12 @@ __device__ __forceinline__ double sin_cw(double x, const SinTab& t) { return tri
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon et al., SC'11) and the photon sampler.
+// The four words of the current Philox block wait in b0..b3 and are handed
+// out in that order by shifting the queue, so that every index is static and
+// the block stays in registers (an indexed array would live in local memory).
 struct Uni {
   uint64_t c0, c1, c2, c3, key;
-  uint64_t b[4];
+  uint64_t b0, b1, b2, b3;
   int pos;
 };
 __device__ __forceinline__ void philox4x64(uint64_t& c0, uint64_t& c1, uint64_t& c2, uint64_t& c3,
@@ -213,35 +216,53 @@ __device__ __forceinline__ void philox4x64(uint64_t& c0, uint64_t& c1, uint64_t&
     k1 += 0xBB67AE8584CAA73Bull;
   }
 }
-__device__ __forceinline__ double uni_next(Uni& u) {
+// The next 64-bit Philox word; its uniform is (w >> 11) 2^-53 (unit53).
+__device__ __forceinline__ uint64_t uni_word(Uni& u) {
   if (u.pos == 4) {
     uint64_t a = u.c0, b = u.c1, c = u.c2, d = u.c3;
     philox4x64(a, b, c, d, u.key, 0ull);
-    u.b[0] = a; u.b[1] = b; u.b[2] = c; u.b[3] = d;
+    u.b0 = a; u.b1 = b; u.b2 = c; u.b3 = d;
     u.c3 += 1;
     u.pos = 0;
   }
-  const uint64_t w = u.b[u.pos++];
-  return (double)(w >> 11) * (1.0 / 9007199254740992.0);
+  const uint64_t w = u.b0;
+  u.b0 = u.b1;
+  u.b1 = u.b2;
+  u.b2 = u.b3;
+  u.pos++;
+  return w;
+}
+// m 2^-53 for m < 2^53, assembled from its bits: the value is exact, the same
+// as converting m and multiplying by 2^-53, but takes no FP64 instruction.
+__device__ __forceinline__ double unit53(uint64_t m) {
+  if (m == 0) return 0.0;
+  const int e = 63 - __clzll((long long)m);  // leading bit, 0..52
+  const uint64_t mant = (m << (52 - e)) & 0x000FFFFFFFFFFFFFull;
+  return __longlong_as_double((long long)(((uint64_t)(e + 970) << 52) | mant));  // exponent e - 53
 }
 // Inverse CDF of the photon spectrum: power-law asymptote F ~ xi^(1/3) below
 // the first knot, clamp above the last, else linear interpolation on the
 // knot interval [lo, lo+1] with lo = max{i : F[i] <= u}, found by walking up
 // from the guide table's entry for u's cell of width 1/XT_SPEC_GUIDE.  F
 // holds the K knots, then 1/(F[k+1] - F[k]) per interval and 1/F[0].
-__device__ __forceinline__ double sample_xi(double u, const double* xi, const double* F, const int32_t* guide,
+// u = (w >> 11) 2^-53 from the Philox word w.  u and the knots F are
+// non-negative, so their order is the order of their bit patterns, and the
+// comparisons run on the integer pipe; u's guide cell floor(u 4096) is w >> 52.
+static_assert(XT_SPEC_GUIDE == 4096, "the guide cell is the top 12 bits of the Philox word");
+__device__ __forceinline__ double sample_xi(uint64_t w, const double* xi, const double* F, const int32_t* guide,
                                             int K) {
-  const double F0 = __ldg(F);
-  if (u < F0) {
+  const double u = unit53(w >> 11);
+  const uint64_t ub = dbits(u);
+  if (ub < dbits(__ldg(F))) {
     const double q = u * __ldg(F + 2 * K);
     return __ldg(xi) * q * q * q;
   }
-  if (u >= __ldg(F + K - 1)) return __ldg(xi + K - 1);
-  int lo = __ldg(guide + (int)(u * (double)XT_SPEC_GUIDE));
-  while (__ldg(F + lo + 1) <= u) lo++;
-  const double w = (u - __ldg(F + lo)) * __ldg(F + K + lo);
+  if (ub >= dbits(__ldg(F + K - 1))) return __ldg(xi + K - 1);
+  int lo = __ldg(guide + (int)(w >> 52));
+  while (dbits(__ldg(F + lo + 1)) <= ub) lo++;
+  const double f = (u - __ldg(F + lo)) * __ldg(F + K + lo);
   const double xl = __ldg(xi + lo);
-  return xl + w * (__ldg(xi + lo + 1) - xl);
+  return xl + f * (__ldg(xi + lo + 1) - xl);
 }
 
 struct RadCtx {
@@ -342,13 +363,21 @@ __constant__ double c_special[XT_SPECIAL_N];
 // k * head is exact, plus a tail), e^r by its Taylor series to r^13 on
 // |r| <= ln2/2, times 2^k from the exponent bits (two steps below the
 // normal range).
+// The range tests compare bit patterns on the integer pipe (745.2 and 709.7
+// are 0x408749999999999A and 0x40862D999999999A); in range, s = x/ln2 + sh
+// lies in [2^52, 2^53), where the integer k is the difference of the bits.
 __device__ __forceinline__ double exp_cw(double x) {
-  if (x != x) return x;
-  if (!(x > -745.2)) return 0.0;
-  if (x > 709.7) return __longlong_as_double(0x7FF0000000000000ll);
+  const uint64_t xb = dbits(x), xa = abs_bits(x);
+  if (xa > 0x7FF0000000000000ull) return x;                          // NaN
+  if (xb >> 63) {
+    if (xa >= 0x408749999999999Aull) return 0.0;                       // x <= -745.2
+  } else if (xa > 0x40862D999999999Aull) {
+    return __longlong_as_double(0x7FF0000000000000ll);                 // x > 709.7
+  }
   const double sh = 6755399441055744.0;  // 1.5 * 2^52: adding it rounds to an integer
-  const double t = fma(x, 1.4426950408889634, sh) - sh;
-  const int k = (int)t;
+  const double s = fma(x, 1.4426950408889634, sh);
+  const double t = s - sh;
+  const int k = (int)(dbits(s) - dbits(sh));
   double r = fma(-t, 0x1.62e42p-1, x);
   r = fma(-t, 0x1.fdf473de6af28p-22, r);
   double p = c_special[41 + 13];
@@ -672,17 +701,19 @@ __device__ __forceinline__ void multipole(Part& p, const double* prm, int order,
     Uni u;
     u.c0 = (uint64_t)pid; u.c1 = (uint64_t)(uint32_t)turn; u.c2 = elem; u.c3 = 0;
     u.key = rc.seed; u.pos = 4;
-    const double u0 = uni_next(u);
+    // u0 and the partial sums F are non-negative (F is NaN only if nbar
+    // is): the test u0 > F compares their bit patterns
+    const uint64_t u0b = dbits(unit53(uni_word(u) >> 11));
     int k = 0;
     double pk = exp_cw(-nbar), F = pk;
-    while (u0 > F && k < 200) {
+    while (u0b > dbits(F) && k < 200) {
       k++;
       pk = (pk * nbar) * c_special[XT_SPECIAL_RECIP + k];
       F = F + pk;
     }
     if (k > 0) {
       double sxi = 0.0;
-      for (int j = 0; j < k; j++) sxi = sxi + sample_xi(uni_next(u), rc.xi, rc.F, rc.guide, rc.K);
+      for (int j = 0; j < k; j++) sxi = sxi + sample_xi(uni_word(u), rc.xi, rc.F, rc.guide, rc.K);
       const double uc = (r.uc15 * (gam * gam * gam)) * h;
       const double dpt = -(uc * sxi) / r.p0c;
       apply_energy_loss(p, dpt, r);
