@@ -121,6 +121,26 @@ __device__ __forceinline__ uint64_t abs_bits(double v) {
 __device__ __forceinline__ bool is_finite(double v) { return abs_bits(v) < 0x7FF0000000000000ull; }
 // |v| <= 1 (false for NaN)
 __device__ __forceinline__ bool abs_le_one(double v) { return abs_bits(v) <= 0x3FF0000000000000ull; }
+// The same answers as the floating-point comparisons in their comments, NaN
+// included, from the bit patterns (on the integer pipe).
+// v > 0
+__device__ __forceinline__ bool is_positive(double v) { return dbits(v) - 1ull < 0x7FF0000000000000ull; }
+// v > -1
+__device__ __forceinline__ bool gt_minus_one(double v) {
+  const uint64_t b = dbits(v);
+  return (b >> 63) ? (abs_bits(v) < 0x3FF0000000000000ull) : (b <= 0x7FF0000000000000ull);
+}
+// v > -1 && v < inf
+__device__ __forceinline__ bool in_minus_one_inf(double v) {
+  const uint64_t b = dbits(v);
+  return (b >> 63) ? (abs_bits(v) < 0x3FF0000000000000ull) : (b < 0x7FF0000000000000ull);
+}
+// |v| < 1
+__device__ __forceinline__ bool abs_lt_one(double v) { return abs_bits(v) < 0x3FF0000000000000ull; }
+// |v| >= 1/4
+__device__ __forceinline__ bool abs_ge_quarter(double v) {
+  return abs_bits(v) - 0x3FD0000000000000ull <= 0x7FF0000000000000ull - 0x3FD0000000000000ull;
+}
 
 // ---------------------------------------------------------------------------
 // Particle state in registers.  opd = 1+delta, dm1 = (1+delta)^2 - 1,
@@ -461,7 +481,7 @@ __device__ __forceinline__ void bb_field(double x, double y, const double* prm, 
 // table), else from trig_cw or two exponentials.
 __device__ __forceinline__ void osc_funcs(double z, const SinTab& sn, double* C, double* S, double* S2,
                                           double* S3) {
-  if (fabs(z) < 1.0) {
+  if (abs_lt_one(z)) {
     const double mz = -z;
     const double* f = c_special + XT_SPECIAL_FACT;
     double c = f[18], s = f[19], s2 = f[20], s3 = f[21];
@@ -475,7 +495,7 @@ __device__ __forceinline__ void osc_funcs(double z, const SinTab& sn, double* C,
     *C = c; *S = s; *S2 = s2; *S3 = s3;
     return;
   }
-  if (z > 0.0) {
+  if (is_positive(z)) {
     const double a = sqrt(z);
     *C = trig_cw(a, sn, 1);
     *S = trig_cw(a, sn, 0) / a;
@@ -494,7 +514,8 @@ __device__ __forceinline__ void osc_funcs(double z, const SinTab& sn, double* C,
 // for |u| <= 1; the loop stops at four), then the series from the table.
 __device__ __forceinline__ double asin_over(double u) {
   double v = u, m = 1.0;
-  for (int k = 0; k < 4 && fabs(v) >= 0.25; k++) {
+  int halved = 0;
+  for (; halved < 4 && abs_ge_quarter(v); halved++) {
     v = v / sqrt(2.0 * (1.0 + sqrt(1.0 - v * v)));
     m = m + m;
   }
@@ -503,7 +524,7 @@ __device__ __forceinline__ double asin_over(double u) {
   double s = a[13];
 #pragma unroll
   for (int n = 12; n >= 0; n--) s = fma(s, z, a[n]);
-  if (m == 1.0) return s;
+  if (halved == 0) return s;
   return (m * (v / u)) * s;
 }
 
@@ -561,7 +582,7 @@ __device__ __forceinline__ int bend_full_c(Part& p, double k0, double h, double 
   const double th = h * L, L2 = L * L;
   const double snt = th * S, Sh = L * S, Ch = (h * L2) * S2, D2 = 2.0 * (L2 * S2);
   const double u = fma(-p.px, p.px, fma(-p.py, p.py, p.dm1));  // pz^2 - 1
-  if (!(u > -1.0 && u < INFINITY)) return -2;
+  if (!in_minus_one_inf(u)) return -2;
   const double pz = sqrt(1.0 + u);
   const double ph2 = 1.0 + fma(-p.py, p.py, p.dm1);
   const double B = fma(p.px, C, pz * snt);
@@ -569,16 +590,16 @@ __device__ __forceinline__ int bend_full_c(Part& p, double k0, double h, double 
   const double r0s = fma(p.x, snt, Sh);  // (1/h + x) sin(theta)
   const double A = fma(-k0, r0s, B);     // px at the exit plane
   const double pzf2 = fma(-A, A, ph2);
-  if (!(pzf2 > 0.0)) return -2;
+  if (!is_positive(pzf2)) return -2;
   const double pzf = sqrt(pzf2);
   const double den = pzf + Q;
-  if (!(den > 0.0)) return -2;
+  if (!is_positive(den)) return -2;
   const double xf = fma(p.x, C, -Ch) + r0s * ((A + B) / den);
   const double dxf = xf - p.x;
   const double chord = sqrt(fma(dxf, dxf, (fma(h, p.x, 1.0) * fma(h, xf, 1.0)) * D2));
   const double ph = sqrt(ph2);
   const double uu = (k0 * chord) / (ph + ph);
-  if (!(fabs(uu) <= 1.0)) return -2;
+  if (!abs_le_one(uu)) return -2;
   const double lh = ((L >= 0.0) ? chord : -chord) * asin_over(uu);
   const double lr = lh / ph;
   p.x = xf;
@@ -736,7 +757,7 @@ __device__ __forceinline__ int edge_nonlinear(Part& p, const double* prm) {
   if (sgn < 0.0) p.px = fma(r21, p.x, p.px);
   const double px = p.px, y = p.y, py = p.py;
   const double base = fma(-px, px, p.dm1);  // (1+delta)^2 - 1 - px^2
-  if (!(fma(-py, py, base) > -1.0)) return -2;
+  if (!gt_minus_one(fma(-py, py, base))) return -2;
   const double ky = k0 * y;
   const double st = sgn * t;
   double pyn = py;
@@ -746,7 +767,7 @@ __device__ __forceinline__ int edge_nonlinear(Part& p, const double* prm) {
     pyn = fma(-ky, Tv, py);
   }
   const double u = fma(-pyn, pyn, base);
-  if (!(u > -1.0)) return -2;
+  if (!gt_minus_one(u)) return -2;
   const double pz = sqrt(1.0 + u);
   const double D = fma(-st, px, pz);
   const double c = (sgn * (1.0 + t * t)) / (pz * (D * D));
