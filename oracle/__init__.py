@@ -230,6 +230,8 @@ def track_parallel(elements, ref, particles: dict, n_turns: int, procs: int | No
     import multiprocessing as mp
     lib()  # built once here, not by every worker
     n = np.asarray(particles["x"]).shape[0]
+    if n == 0:
+        return track(elements, ref, particles, n_turns)
     procs = procs or os.cpu_count() or 1
     parts = _chunks(n, procs)
     jobs = [(elements, ref, {k: np.asarray(particles[k])[c] for k in FLOAT_FIELDS + INT_FIELDS + ("particle_id",)},
@@ -245,6 +247,8 @@ def lyapunov_parallel(elements, ref, z0, dz0, n_turns: int, every: int = 10, met
     import multiprocessing as mp
     lib()
     z = np.asarray(z0, dtype=np.float64).reshape(-1, 6)
+    if z.shape[0] == 0:
+        return lyapunov(elements, ref, z, dz0, n_turns, every=every, metric=metric)
     procs = procs or os.cpu_count() or 1
     parts = _chunks(z.shape[0], procs)
     jobs = [(elements, ref, z[c], dz0, n_turns, every, metric) for c in parts]

@@ -132,3 +132,22 @@ def test_rejects_bad_arguments():
         oracle.lyapunov(el, PROTON, z, np.array([1e-9, 0, 0, 0, 0, 0]), 10, every=0)
     with pytest.raises(ValueError):
         oracle.lyapunov(el, PROTON, z, np.array([1e-9, 0, 0, 0, 0, 0]), 10, rad_mode=2)
+
+
+def test_parallel_helpers_equal_the_single_process_calls():
+    """The spawned-process helpers split the particles into slices; the
+    particles are independent, so the results are the same bit for bit."""
+    el = _henon()
+    X0 = np.linspace(0.05, 0.66, 7)
+    z = np.zeros((X0.size, 6))
+    z[:, 0] = X0
+    dz = np.array([1e-9, 0, 0, 0, 0, 0])
+    a = oracle.lyapunov(el, PROTON, z, dz, 300)
+    b = oracle.lyapunov_parallel(el, PROTON, z, dz, 300, procs=3)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    p = I.make_particles(PROTON, X0, np.zeros(7), np.zeros(7), np.zeros(7), np.zeros(7), np.zeros(7))
+    ta, tb = oracle.track(el, PROTON, p, 300), oracle.track_parallel(el, PROTON, p, 300, procs=3)
+    for k in ta:
+        assert np.array_equal(ta[k], tb[k]), k
+    assert oracle.lyapunov_parallel(el, PROTON, np.zeros((0, 6)), dz, 10)["sum_log"].shape == (0,)
