@@ -642,3 +642,58 @@ def test_autotune_keeps_results():
     tr.track(P, 6)
     assert_same(P.to_numpy(), oracle.track(el, ref, p, 6))
     assert_same(probe.to_numpy(), {k: np.asarray(p[k]) for k in FIELDS})
+
+
+def test_lepton_quantum_full_size_sampled():
+    """The 45.6 GeV lepton ring (10,000 rows) with mean radiation and quantum
+    excitation: 200,000 matched particles for 2 turns in the default launch
+    configuration, as the benchmark times it; about 120 sampled particles
+    (lost ones included) checked bit for bit against the oracle."""
+    el, ref, _ = I.lepton_ring()
+    n = 200000
+    p = I.matched_gaussian(el, ref, n, 0.0, 1.06e-3, seed=5, emit_x=2 * 3.9e-8, emit_y=2 * 3.9e-10)
+    out = gpu_track(el, ref, p, 2, radiation=xtgb.RAD_QUANTUM, seed=1)
+    rng = np.random.default_rng(11)
+    lost = np.flatnonzero(out["state"] != 1)
+    pick = np.unique(np.concatenate([rng.choice(lost, min(20, lost.size), replace=False),
+                                     rng.choice(n, 100, replace=False)]))
+    o = oracle.track(el, ref, I.subset(p, pick), 2, rad_mode=2, seed=1)
+    assert_same({k: out[k][pick] for k in FIELDS}, o)
+    assert np.all(o["ptau"][o["state"] == 1] != p["ptau"][pick][o["state"] == 1])
+
+
+def test_batched_seeds_full_size_sampled():
+    """64 error seeds of the LHC-scale ring (20,000 rows each) with uneven
+    counts round(10^U(3,5)), 1.74e6 particles: the autotuned options on a
+    65,536-particle probe, then one batched launch of 2 turns in a CUDA graph,
+    as the benchmark times it; per seed a lost particle (if any) and a random
+    one checked bit for bit against the oracle."""
+    counts = I.batched_seed_counts(64)
+    el0, ref = I.lhc_ring(seed=I.BASE_SEED)
+    optics = I.design_optics(el0, ref)
+    els, trs, ps, P = [], [], [], []
+    for i, n in enumerate(counts):
+        scales, _ = I.seed_error_scales(i)
+        el, _ = I.lhc_ring(seed=I.BASE_SEED + 100 + i, error_scales=scales)
+        p = I.subset(I.polar_sample(el, ref, int(n), seed=I.BASE_SEED + 200 + i, optics=optics), np.arange(int(n)))
+        els.append(el)
+        ps.append(p)
+        trs.append(xtgb.Tracker(el, ref))
+        P.append(xtgb.Particles.from_numpy(p))
+    pr = I.polar_sample(els[0], ref, 65536, seed=I.BASE_SEED + 300, optics=optics)
+    trs[0].autotune(xtgb.Particles.from_numpy(I.subset(pr, np.arange(65536))), 2)
+    xtgb.track_batched(trs, P, 2, 0, graph=True)
+    assert xtgb.batched_sync_status(trs, P) == xtgb.XT_OK
+    rng = np.random.default_rng(12)
+    n_lost = 0
+    for i in range(len(counts)):
+        g = P[i].to_numpy()
+        lost = np.flatnonzero(g["state"] != 1)
+        n_lost += lost.size
+        pick = np.unique(np.concatenate([lost[:1], rng.choice(int(counts[i]), 1)]))
+        o = oracle.track(els[i], ref, I.subset(ps[i], pick), 2)
+        assert_same({k: g[k][pick] for k in FIELDS}, o, "seed %d: " % i)
+    assert n_lost > 0
+    xtgb.batched_release()
+    for t in trs:
+        t.close()
