@@ -1374,3 +1374,81 @@ def test_fodo10_bruteforce_highprec():
         for k, ref_v, scale in zip(("x", "px", "y", "py", "zeta", "ptau"), v,
                                    (1e-3, 1e-4, 1e-3, 1e-4, 1.0, 1e-3)):
             assert abs(o[k][i] - float(ref_v)) < 1e-14 * scale, (i, k)
+
+
+# --------------------------------------------------------------------------
+# The optics helpers of the oracle (oracle/optics.py)
+
+def test_twiss_uncoupled_fodo_closed_forms():
+    """FODO-10 (thin f = +-5 m, 2 m drifts, sin(mu/2) = L/(2f) = 0.2): at the
+    entry of every thin QF, beta_x = L_c (1 + sin(mu/2))/sin(mu) with the cell
+    length L_c = 4 m and alpha_x = -beta_x/(2f) (symmetric point of the thin
+    lens); at every QD, beta_x = L_c (1 - sin(mu/2))/sin(mu) and
+    alpha_x = +beta_x/(2f); y swaps the two; no bends, so no dispersion."""
+    from oracle import optics as O
+    el, ref = I.fodo10()
+    tw = O.twiss_uncoupled(el, ref)
+    f, Lc = 5.0, 4.0
+    s2 = Lc / (4 * f)
+    mu = 2 * math.asin(s2)
+    bmax = Lc * (1 + s2) / math.sin(mu)
+    bmin = Lc * (1 - s2) / math.sin(mu)
+    qf = [i for i in range(el.shape[0]) if int(el[i]["type"]) == I.MULTIPOLE and el[i]["p"][1] > 0]
+    qd = [i for i in range(el.shape[0]) if int(el[i]["type"]) == I.MULTIPOLE and el[i]["p"][1] < 0]
+    assert len(qf) == 10 and len(qd) == 10
+    for i in qf:
+        assert tw["betx"][i] == pytest.approx(bmax, rel=1e-12)
+        assert tw["alfx"][i] == pytest.approx(-bmax / (2 * f), rel=1e-12)
+        assert tw["bety"][i] == pytest.approx(bmin, rel=1e-12)
+        assert tw["alfy"][i] == pytest.approx(bmin / (2 * f), rel=1e-12)
+    for i in qd:
+        assert tw["betx"][i] == pytest.approx(bmin, rel=1e-12)
+        assert tw["alfx"][i] == pytest.approx(bmin / (2 * f), rel=1e-12)
+        assert tw["bety"][i] == pytest.approx(bmax, rel=1e-12)
+        assert tw["alfy"][i] == pytest.approx(-bmax / (2 * f), rel=1e-12)
+    assert np.max(np.abs(tw["dx"])) == 0.0 and np.max(np.abs(tw["dpx"])) == 0.0
+
+
+def test_radiation_integrals_isomagnetic_and_H_from_local_one_turn_matrices():
+    """Lepton ring of 20 cells, every dipole slice of the same curvature
+    1/rho: I2 = 2 pi/rho and I3 = 2 pi/rho^2 (isomagnetic ring).  I5 sums
+    H |h|^3 L with H = gamma D^2 + 2 alpha D D' + beta D'^2 from lattice
+    functions propagated along the line; here H is recomputed at every dipole
+    slice from that slice's own one-turn matrix A_i = M_i A M_i^-1 (beta,
+    alpha, gamma from its entries, D from (1 - A_i) D = the slice's
+    dispersion column), and the two I5 agree.  The constants are the
+    textbook C_gamma = 8.846e-5 m/GeV^3 and C_q = 3.832e-13 m."""
+    from oracle import optics as O
+    el, ref, _ = I.lepton_ring(n_cells=20, E0=10e9, v_total=100e6)
+    tw = O.twiss_uncoupled(el, ref)
+    I2, I3, I5 = O.radiation_integrals(el, ref, tw)
+    rad = [i for i in range(el.shape[0]) if int(el[i]["type"]) == I.MULTIPOLE and el[i]["p"][23] > 0
+           and el[i]["p"][0] != 0]
+    h = np.array([el[i]["p"][0] / el[i]["p"][23] for i in rad])
+    assert np.allclose(h, h[0], rtol=1e-14, atol=0)
+    rho = 1 / h[0]
+    assert I2 == pytest.approx(2 * math.pi / rho, rel=1e-12)
+    assert I3 == pytest.approx(2 * math.pi / rho ** 2, rel=1e-12)
+    assert O.C_GAMMA == pytest.approx(8.846e-5, rel=1e-4)
+    assert O.C_Q == pytest.approx(3.832e-13, rel=1e-4)
+    # H from the local one-turn matrices
+    elx = O.without_cavities(el)
+    z0 = oracle.closed_orbit(elx, ref, rad_mode=0, dim=4)
+    _, M, _, Ms = oracle.track_jacobian(elx, ref, z0, along=True)
+    A = M[:2, :2]
+    m5 = M[:2, 5]
+    I5b = 0.0
+    for i in rad:
+        T = np.eye(6) if i == 0 else Ms[i - 1]
+        Ti = np.linalg.inv(T)
+        Mi = T @ M @ Ti           # one-turn matrix starting at the entry of row i
+        Ai = Mi[:2, :2]
+        c = 0.5 * np.trace(Ai)
+        s = math.copysign(math.sqrt(1 - c * c), Ai[0, 1])
+        b, a, g = Ai[0, 1] / s, (Ai[0, 0] - Ai[1, 1]) / (2 * s), -Ai[1, 0] / s
+        D = np.linalg.solve(np.eye(2) - Ai, Mi[:2, 5])
+        H = g * D[0] ** 2 + 2 * a * D[0] * D[1] + b * D[1] ** 2
+        L = el[i]["p"][23]
+        I5b += H * abs(el[i]["p"][0] / L) ** 3 * L
+    assert I5 > 0 and I5b == pytest.approx(I5, rel=1e-9)
+    assert np.trace(A) != 2.0 and np.any(m5 != 0)
