@@ -102,3 +102,29 @@ def test_batched_seed_counts():
     assert c.shape == (64,) and c.min() >= 1000 and c.max() <= 100000
     assert int(c.sum()) == 1737245
     assert abs(np.median(np.log10(c)) - 4.0) < 0.35
+
+
+def test_lepton_ring_recipe():
+    """45.6 GeV electrons, 200 cells of 50 rows (10,000), 16 dipole slices
+    per cell of theta = 2 pi/3200 and L_rad = 10.7/4 m (rho = 1.36 km), one
+    400 MHz cavity per cell adding to 500 MV at 180 deg - arcsin(U0/V), and
+    U0 = C_gamma E0^4 / rho (isomagnetic) of about 0.6 % of E0 per turn."""
+    el, ref, info = I.lepton_ring()
+    t = el["type"]
+    assert el.shape[0] == 10000
+    rc = oracle.ref_constants(ref)
+    assert rc["E0"] == pytest.approx(45.6e9, rel=1e-15)
+    mp = el[t == I.MULTIPOLE]
+    dip = mp[mp["p"][:, 0] != 0]
+    assert dip.shape[0] == 16 * 200
+    theta = 2 * math.pi / 3200
+    assert np.allclose(dip["p"][:, 0], theta, rtol=1e-15) and np.allclose(dip["p"][:, 22], theta, rtol=1e-15)
+    rho = (10.7 / 4) / theta
+    assert rho == pytest.approx(1362.5, rel=1e-3)
+    cav = el[t == I.CAVITY]
+    assert cav.shape[0] == 200 and np.sum(cav["p"][:, 0]) == pytest.approx(500e6, rel=1e-12)
+    assert np.all(cav["p"][:, 1] == 400e6)
+    U0 = 8.846e-5 * (45.6 ** 4) / rho * 1e9
+    assert info["U0"] == pytest.approx(U0, rel=1e-12)
+    assert np.all(cav["p"][:, 2] == pytest.approx(180.0 - math.degrees(math.asin(U0 / 500e6)), rel=1e-12))
+    assert 0.004 < U0 / 45.6e9 < 0.008
