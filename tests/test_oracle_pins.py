@@ -1452,3 +1452,27 @@ def test_radiation_integrals_isomagnetic_and_H_from_local_one_turn_matrices():
         I5b += H * abs(el[i]["p"][0] / L) ** 3 * L
     assert I5 > 0 and I5b == pytest.approx(I5, rel=1e-9)
     assert np.trace(A) != 2.0 and np.any(m5 != 0)
+
+
+def test_closed_orbit_of_a_corrector_kick():
+    """A thin corrector (knl0 = theta, no curvature: px -= theta) in a linear
+    thin FODO ring of 10 cells: the 4D closed orbit found by the oracle's
+    Newton iteration sits, at the corrector, at x = theta_k beta/(2 tan(pi Q))
+    with theta_k = -theta (textbook closed-orbit distortion of a single kick);
+    beta and Q are those of the thin FODO in closed form.  The only
+    non-linearity left is the exact drift's, of relative order px^2."""
+    f, Ld = 5.0, 2.0
+    cell = [I.multipole(knl=[0, 1 / f]), I.drift(Ld), I.multipole(knl=[0, -1 / f]), I.drift(Ld)]
+    theta = 1e-6
+    el = I.table([I.multipole(knl=[theta])] + cell * 10)
+    z = oracle.closed_orbit(el, PROTON, dim=4)
+    s2 = Ld / (2 * f)
+    mu = 2 * math.asin(s2)
+    beta = 2 * Ld * (1 + s2) / math.sin(mu)   # at the QF, where the corrector sits
+    Q = 10 * mu / (2 * math.pi)
+    x_co = -theta * beta / (2 * math.tan(math.pi * Q))
+    assert z[0] == pytest.approx(x_co, rel=1e-9)
+    assert abs(z[2]) < 1e-20 and abs(z[3]) < 1e-20
+    # a fixed point of the one-turn map
+    zo, _ = oracle.track_jacobian(el, PROTON, z)
+    assert np.allclose(zo[:4], z[:4], rtol=0, atol=1e-15)  # the Newton tolerance
