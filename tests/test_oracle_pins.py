@@ -1476,3 +1476,36 @@ def test_closed_orbit_of_a_corrector_kick():
     # a fixed point of the one-turn map
     zo, _ = oracle.track_jacobian(el, PROTON, z)
     assert np.allclose(zo[:4], z[:4], rtol=0, atol=1e-15)  # the Newton tolerance
+
+
+def test_natural_chromaticity_of_a_thin_fodo():
+    """Thin FODO cell (f = 5 m, 2 m drifts) off momentum: the exact drift
+    turns the quadrupoles' angle kicks into K L/(1+delta), so the first-order
+    chromaticity is the textbook -(1/4 pi) sum beta_i K_i L_i = -(beta_max -
+    beta_min)/(4 pi f) per cell, in both planes.  Measured by central
+    differences of the cell tune at delta = +-1e-5 (4D fixed point at fixed
+    pzeta; no bends, so the orbit stays on axis)."""
+    f, Ld = 5.0, 2.0
+    cell = I.table([I.multipole(knl=[0, 1 / f]), I.drift(Ld), I.multipole(knl=[0, -1 / f]), I.drift(Ld)])
+    rc = oracle.ref_constants(PROTON)
+    b0 = rc["beta0"]
+
+    def tunes(delta):
+        # pzeta of a particle with momentum deviation delta: ptau = (E - E0)/(P0 c)
+        E = math.sqrt((PROTON[2] * (1 + delta)) ** 2 + PROTON[0] ** 2)
+        ptau = (E - rc["E0"]) / PROTON[2]
+        z = np.array([0, 0, 0, 0, 0, ptau / b0])
+        _, M = oracle.track_jacobian(cell, PROTON, z)
+        return (math.acos(0.5 * np.trace(M[:2, :2])) / (2 * math.pi),
+                math.acos(0.5 * np.trace(M[2:4, 2:4])) / (2 * math.pi))
+
+    d = 1e-5
+    qp, qm = tunes(d), tunes(-d)
+    s2 = Ld / (2 * f)
+    mu = 2 * math.asin(s2)
+    bmax = 2 * Ld * (1 + s2) / math.sin(mu)
+    bmin = 2 * Ld * (1 - s2) / math.sin(mu)
+    xi = -(bmax - bmin) / (4 * math.pi * f)
+    assert (qp[0] - qm[0]) / (2 * d) == pytest.approx(xi, rel=1e-6)
+    assert (qp[1] - qm[1]) / (2 * d) == pytest.approx(xi, rel=1e-6)
+    assert tunes(0.0)[0] == pytest.approx(mu / (2 * math.pi), rel=1e-14)
