@@ -1509,3 +1509,32 @@ def test_natural_chromaticity_of_a_thin_fodo():
     assert (qp[0] - qm[0]) / (2 * d) == pytest.approx(xi, rel=1e-6)
     assert (qp[1] - qm[1]) / (2 * d) == pytest.approx(xi, rel=1e-6)
     assert tunes(0.0)[0] == pytest.approx(mu / (2 * math.pi), rel=1e-14)
+
+
+def test_momentum_compaction_on_the_dispersive_closed_orbit():
+    """Lepton ring of 20 cells with RF off: a particle on the 4D closed orbit
+    of momentum deviation pzeta slips per turn by dzeta = -C (alpha_c -
+    1/gamma0^2) pzeta to first order, with the momentum compaction of thin
+    dipoles alpha_c = sum theta_i D_i / C (D at each dipole slice from the
+    propagated lattice functions) and C the sum of drift lengths.  The slip
+    comes from Newton closed orbits at pzeta = +-1e-6 tracked for one turn:
+    it checks the curvature path-length term against the dispersion that the
+    curvature kick creates, and the drift's 1/gamma^2 term."""
+    from oracle import optics as O
+    el, ref, _ = I.lepton_ring(n_cells=20, E0=10e9, v_total=100e6)
+    elx = O.without_cavities(el)
+    tw = O.twiss_uncoupled(elx, ref)
+    rc = oracle.ref_constants(ref)
+    C = float(np.sum(elx[elx["type"] == I.DRIFT]["p"][:, 0]))
+    dip = [i for i in range(elx.shape[0]) if int(elx[i]["type"]) == I.MULTIPOLE and elx[i]["p"][22] != 0]
+    alpha_c = sum(elx[i]["p"][22] * tw["dx"][i] for i in dip) / C
+    eta = alpha_c - 1.0 / rc["gamma0"] ** 2
+
+    def slip(pz):
+        z = oracle.closed_orbit(elx, ref, dim=4, guess=[0, 0, 0, 0, 0, pz])
+        zo, _ = oracle.track_jacobian(elx, ref, z)
+        return zo[4] - z[4]
+
+    e = 1e-6
+    assert (slip(e) - slip(-e)) / (2 * e) == pytest.approx(-C * eta, rel=1e-6)
+    assert alpha_c > 0.0
