@@ -1538,3 +1538,41 @@ def test_momentum_compaction_on_the_dispersive_closed_orbit():
     e = 1e-6
     assert (slip(e) - slip(-e)) / (2 * e) == pytest.approx(-C * eta, rel=1e-6)
     assert alpha_c > 0.0
+
+
+def test_chromaticity_with_sextupoles_and_dispersion():
+    """Lepton ring of 20 cells (thin quadrupoles, thin dipoles with their
+    k0 h weak focusing, thin sextupoles at dispersion), RF off: the
+    chromaticities from the tunes of the Newton closed orbits at
+    pzeta = +-1e-6 equal the first-order sums
+    xi_x = (1/4 pi) sum beta_x (-(k1 L + k0 h L) + k2 L D),
+    xi_y = (1/4 pi) sum beta_y (k1 L - k2 L D), to 1e-6.  This fixes the
+    sextupole's sign and factor against the quadrupole's and the drift's
+    chromatic terms."""
+    from oracle import optics as O
+    el, ref, _ = I.lepton_ring(n_cells=20, E0=10e9, v_total=100e6)
+    elx = O.without_cavities(el)
+    tw = O.twiss_uncoupled(elx, ref)
+
+    def tunes(pz):
+        z = oracle.closed_orbit(elx, ref, dim=4, guess=[0, 0, 0, 0, 0, pz])
+        _, M = oracle.track_jacobian(elx, ref, z)
+        return np.array([math.acos(0.5 * np.trace(M[:2, :2])), math.acos(0.5 * np.trace(M[2:4, 2:4]))]) / (2 * math.pi)
+
+    e = 1e-6
+    xi = (tunes(e) - tunes(-e)) / (2 * e)
+    sx = sy = 0.0
+    n_sext = 0
+    for i in range(elx.shape[0]):
+        r = elx[i]
+        if int(r["type"]) != I.MULTIPOLE:
+            continue
+        k1, k2, hxl, L = r["p"][1], r["p"][2], r["p"][22], r["p"][23]
+        k0h = r["p"][0] * hxl / L if (hxl != 0 and L > 0) else 0.0
+        n_sext += k2 != 0
+        sx += tw["betx"][i] * (-(k1 + k0h) + k2 * tw["dx"][i])
+        sy += tw["bety"][i] * (k1 - k2 * tw["dx"][i])
+    assert n_sext > 0
+    assert xi[0] == pytest.approx(sx / (4 * math.pi), rel=1e-6)
+    assert xi[1] == pytest.approx(sy / (4 * math.pi), rel=1e-6)
+    assert xi[0] > 1.0 and xi[1] > 1.0
