@@ -89,3 +89,33 @@ def test_row_lengths():
     el = I.table([I.drift(1.5), I.quadrupole(0.1, 0.4), I.bend(0.01, 0.01, 2.5), I.multipole(knl=[0, 0.1]),
                   I.aperture(0.02), I.spacecharge(1e10, 0.0, 1e-3, 1e-3, 3.0)])
     assert np.array_equal(T.row_lengths(el), [1.5, 0.4, 2.5, 0.0, 0.0, 0.0])
+
+
+def test_functions_along_from_exact_jacobians():
+    """The host half of the lattice functions along the line (normal modes of
+    the one-turn matrix carried through per-row Jacobians, Mais-Ripken
+    readout, dispersion M_i (D_0, 1)) fed with the oracle's exact per-row
+    Jacobians of the 20-cell lepton ring instead of the GPU stencil: beta,
+    alpha and dispersion equal the oracle's Courant-Snyder propagation at
+    every row, the phase advance over the ring equals the tune modulo 1, and
+    the cross-plane betas vanish (uncoupled ring)."""
+    import oracle
+    from oracle import optics as O
+    from paper_2310_00317_gb300 import inputs as I
+    el, ref, _ = I.lepton_ring(n_cells=20, E0=10e9, v_total=100e6)
+    elx = O.without_cavities(el)
+    tw = O.twiss_uncoupled(elx, ref)
+    z = oracle.closed_orbit(elx, ref, rad_mode=0, dim=4)
+    _, M, orbit, Ms = oracle.track_jacobian(elx, ref, z, along=True)
+    Vm = T.normal_modes(M[:4, :4])
+    D0 = np.linalg.solve(np.eye(4) - M[:4, :4], M[:4, 5])
+    f = T._functions_along(elx, z, orbit, Ms, Vm, D0)
+    for k in ("betx", "alfx", "bety", "alfy", "dx", "dpx"):
+        assert np.allclose(f[k], tw[k], rtol=1e-9, atol=1e-9 * np.max(np.abs(tw[k]))), k
+    qx = math.acos(0.5 * np.trace(M[:2, :2])) / (2 * math.pi)
+    qy = math.acos(0.5 * np.trace(M[2:4, 2:4])) / (2 * math.pi)
+    assert f["mux"][-1] % 1.0 == pytest.approx(qx, abs=1e-10)
+    assert f["muy"][-1] % 1.0 == pytest.approx(qy, abs=1e-10)
+    assert np.all(np.diff(f["mux"]) >= -1e-12) and np.all(np.diff(f["muy"]) >= -1e-12)
+    assert np.max(f["betx2"]) < 1e-20 and np.max(f["bety1"]) < 1e-20
+    assert f["s"][-1] == pytest.approx(float(np.sum(elx[elx["type"] == I.DRIFT]["p"][:, 0])), rel=1e-12)
