@@ -112,3 +112,56 @@ def test_create_rejects_bad_element_parameters_before_cuda(L):
         assert rc == xtgb.XT_ERR_INVALID, (row, rc)
         assert "element 3" in xtgb.last_error(), xtgb.last_error()
         assert not h.value
+
+
+def test_every_call_rejects_null_arguments_before_cuda(L):
+    """Each entry point checks its pointers and sizes first and returns
+    XT_ERR_INVALID with a message, without touching CUDA (this machine has no
+    GPU, so any CUDA call would fail with a different code)."""
+    P = ctypes.c_void_p
+    i32, i64, u64, dbl, f32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_float
+    sig = {
+        "xt_track_host": [P, P, i64, i64, P], "xt_sync_status": [P, P], "xt_cancel": [P], "xt_reset_cancel": [P],
+        "xt_set_profiling": [P, i32], "xt_kernel_time": [P, P, P], "xt_fp64_peak": [P, P, P],
+        "xt_refine_losses": [P, P, dbl, i32, P, P], "xt_track_monitor": [P, P, i64, P, P],
+        "xt_element_flops": [P, P, i64], "xt_autotune": [P, P, i64, P], "xt_batched_sync_status": [P, P, i32, P],
+        "xt_track_noalloc": [P, P, i64, i64, P], "xt_tracker_set_options": [P, P], "xt_tracker_get_options": [P, P],
+        "xs_mlp_create": [u64, P], "xs_mlp_set_params": [P, P, i64, P], "xs_mlp_get_params": [P, P, i64, P],
+        "xs_mlp_forward": [P, P, P, i64, P], "xs_da_select": [P, i32, i32, f32, i32, i32, P, P, P, P, P],
+        "xs_da_combine": [P, P, i32, i32, P, P, P],
+    }
+    # a CDLL object of its own, so these prototypes do not replace the binding's
+    C = ctypes.CDLL(xtgb.library_path())
+    for name, args in sig.items():
+        f = getattr(C, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int32
+    p = xtgb._Particles()  # all pointers null, n = 0
+    o = xtgb._Options()
+    d, k = ctypes.c_double(), ctypes.c_int64()
+    calls = [
+        ("xt_track_host", (None, ctypes.byref(p), 0, 1, None)),
+        ("xt_sync_status", (None, None)),
+        ("xt_cancel", (None,)),
+        ("xt_reset_cancel", (None,)),
+        ("xt_set_profiling", (None, 1)),
+        ("xt_kernel_time", (None, ctypes.byref(d), ctypes.byref(k))),
+        ("xt_fp64_peak", (None, None, None)),
+        ("xt_refine_losses", (None, ctypes.byref(p), 0.01, 128, None, None)),
+        ("xt_track_monitor", (None, ctypes.byref(p), 0, None, None)),
+        ("xt_element_flops", (None, None, 0)),
+        ("xt_autotune", (None, ctypes.byref(p), 2, None)),
+        ("xt_batched_sync_status", (None, None, 0, None)),
+        ("xt_track_noalloc", (None, ctypes.byref(p), 0, 1, None)),
+        ("xt_tracker_set_options", (None, ctypes.byref(o))),
+        ("xt_tracker_get_options", (None, ctypes.byref(o))),
+        ("xs_mlp_create", (1, None)),
+        ("xs_mlp_set_params", (None, None, 202242, None)),
+        ("xs_mlp_get_params", (None, None, 202242, None)),
+        ("xs_mlp_forward", (None, None, None, 16, None)),
+        ("xs_da_select", (None, 9, 40, 0.2, 5, 5, None, None, None, None, None)),
+        ("xs_da_combine", (None, None, 9, 40, None, None, None)),
+    ]
+    for name, args in calls:
+        rc = getattr(C, name)(*args)
+        assert rc == xtgb.XT_ERR_INVALID, (name, rc)
