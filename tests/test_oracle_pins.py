@@ -1654,3 +1654,74 @@ def test_mean_radiation_map_against_40_digits():
         loss = float(v[5] - mpmath.mpf(p["ptau"][i]))
         assert o["ptau"][i] - p["ptau"][i] == pytest.approx(loss, rel=1e-9)
         assert o["ptau"][i] < off["ptau"][i]
+
+
+def test_quantum_emission_against_40_digits_with_numpy_philox():
+    """One radiating dipole slice, 45.6 GeV electrons with particle ids 1..8
+    off axis and off momentum.  Restated in 40 digits with random numbers
+    drawn by numpy's independent Philox4x64-10 at the counter (particle id,
+    turn, element, call) and key (seed, 0), one uniform (w >> 11) 2^-53 per
+    64-bit word: the photon count by inversion of the Poisson CDF of
+    n = (5/(2 sqrt 3)) alpha q0^2 gamma h L_rad at the first word, the photon
+    energies u_c xi with xi from the next words through the spectrum sampler
+    (pinned against scipy's Bessel quadrature), u_c = (3/2) hbar c gamma^3 h,
+    gamma and h = |b|/((1+delta) L_rad) of the particle, then the energy
+    update and the angle-keeping scaling.  The oracle agrees to 1e-13 of each
+    coordinate's scale, so the counter layout, the word order and both
+    formulas are fixed."""
+    mpmath.mp.dps = 40
+    mpf = mpmath.mpf
+    ref = I.electron_reference(45.6e9)
+    theta, L, seed, elem, turn = 2 * math.pi / 2400, 3.575, 77, 0, 0
+    el = I.table([I.multipole(knl=[theta, 0.01], hxl=theta, lrad=L)])
+    rng = np.random.default_rng(22)
+    n = 8
+    p = I.make_particles(ref, rng.normal(0, 1e-3, n), rng.normal(0, 1e-5, n), rng.normal(0, 5e-4, n),
+                         rng.normal(0, 1e-5, n), rng.normal(0, 1e-3, n), rng.normal(0, 1e-3, n),
+                         particle_id=np.arange(1, n + 1))
+    o = oracle.track(el, ref, p, 1, rad_mode=2, seed=seed)
+    m0, q0, p0c = [mpf(v) for v in ref]
+    E0 = mpmath.sqrt(p0c ** 2 + m0 ** 2)
+    b0 = p0c / E0
+    alpha, hbarc = mpf("7.2973525693e-3"), mpf("197.3269804e-9")
+    counts = []
+    for i in range(n):
+        pid = int(p["particle_id"][i])
+        words = []
+        for call in range(8):
+            bg = np.random.Philox(key=np.array([seed, 0], dtype=np.uint64),
+                                  counter=np.array([pid - 1, turn, elem, call], dtype=np.uint64))
+            words += [int(w) for w in bg.random_raw(4)]
+        u = [mpf(w >> 11) / mpf(2) ** 53 for w in words]
+        x, px, y, py, z, pt = [mpf(p[k][i]) for k in ("x", "px", "y", "py", "zeta", "ptau")]
+        d = mpmath.sqrt(1 + 2 * pt / b0 + pt ** 2) - 1
+        rvv = (1 + d) / (1 + b0 * pt)
+        b = mpf(theta) + mpf(0.01) * mpmath.mpc(x, y)
+        px -= b.real
+        py += b.imag
+        hx = mpf(theta)
+        px += hx * (1 + d) - mpf(theta) * hx * x / mpf(L)
+        z -= hx * x / rvv
+        h = abs(b) / ((1 + d) * mpf(L))
+        gam = (E0 + pt * p0c) / m0
+        nbar = 5 / (2 * mpmath.sqrt(3)) * alpha * q0 ** 2 * gam * h * mpf(L)
+        k, term = 0, mpmath.exp(-nbar)
+        F = term
+        while u[0] > F:
+            k += 1
+            term = term * nbar / k
+            F += term
+        assert abs(u[0] - F) > 1e-12 and k < 30
+        counts.append(k)
+        xi = sum(mpf(oracle.spectrum_sample(float(u[1 + j]))) for j in range(k))
+        uc = mpf(3) / 2 * hbarc * gam ** 3 * h
+        if k > 0:
+            pt_new = pt - uc * xi / p0c
+            dn = mpmath.sqrt(1 + 2 * pt_new / b0 + pt_new ** 2) - 1
+            px *= (1 + dn) / (1 + d)
+            py *= (1 + dn) / (1 + d)
+            pt = pt_new
+        for key, hv, scale in zip(("x", "px", "y", "py", "zeta", "ptau"), (x, px, y, py, z, pt),
+                                  (1e-3, 1e-4, 1e-3, 1e-4, 1e-3, 1e-3)):
+            assert abs(o[key][i] - float(hv)) < 1e-13 * scale, (i, key, k, o[key][i], float(hv))
+    assert max(counts) >= 2 and len(set(counts)) >= 3  # several photon counts occur
