@@ -830,16 +830,25 @@ struct BatchPlan {
 
 std::mutex g_plan_mu;
 
+// A plan bakes in every device pointer of every seed (lattice, chunk table,
+// all particle arrays) and the counts, so all of them are part of its key:
+// a call with any buffer replaced gets a plan of its own.
 std::vector<uintptr_t> plan_key(xt_tracker* const* trs, const xt_particles* ps, int32_t ns) {
   std::vector<uintptr_t> key;
   for (int i = 0; i < ns; i++) {
-    key.push_back((uintptr_t)trs[i]);
-    key.push_back(trs[i] ? (uintptr_t)trs[i]->d_chunks : 0);
-    key.push_back(trs[i] ? (uintptr_t)trs[i]->n_chunks : 0);
-    key.push_back(trs[i] ? (uintptr_t)trs[i]->chunk_built : 0);
-    key.push_back((uintptr_t)ps[i].x);
-    key.push_back((uintptr_t)ps[i].state);
-    key.push_back((uintptr_t)ps[i].n);
+    const xt_tracker* t = trs[i];
+    const xt_particles& p = ps[i];
+    key.push_back((uintptr_t)t);
+    key.push_back(t ? (uintptr_t)t->d_lat : 0);
+    key.push_back(t ? (uintptr_t)t->d_chunks : 0);
+    key.push_back(t ? (uintptr_t)t->n_chunks : 0);
+    key.push_back(t ? (uintptr_t)t->chunk_built : 0);
+    for (const void* a : {(const void*)p.x, (const void*)p.px, (const void*)p.y, (const void*)p.py,
+                          (const void*)p.zeta, (const void*)p.delta, (const void*)p.ptau, (const void*)p.rpp,
+                          (const void*)p.rvv, (const void*)p.state, (const void*)p.at_turn,
+                          (const void*)p.at_element, (const void*)p.particle_id})
+      key.push_back((uintptr_t)a);
+    key.push_back((uintptr_t)p.n);
   }
   return key;
 }
