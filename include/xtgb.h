@@ -266,8 +266,8 @@ int xt_track_host(xt_tracker* tr, const xt_particles* p, int64_t start_turn, int
                   void* stream);
 
 /* Same tracking as xt_track, for callers that cannot allocate device memory
-   while they track (inside a stream capture that must not allocate, or in an
-   application whose device memory is owned by its own allocator or budget).
+   while they track (an application whose device memory is owned by its own
+   allocator or budget, or a real-time loop that cannot wait for cudaMalloc).
    There is no counterpart in the paper.  xt_track grows a per-tracker
    workspace with cudaMalloc; this call allocates nothing: its scratch (alive
    list, counts, counters) is a fixed static device array of
@@ -277,11 +277,19 @@ int xt_track_host(xt_tracker* tr, const xt_particles* p, int64_t start_turn, int
    XT_ERR_INVALID.  The first call on a device looks up the array's device
    address (once per device, with that device current); make that first call
    before any stream capture.  All calls share the one array: calls that
-   overlap on the GPU (other streams, other trackers) race.  Cycle budget and
-   cancel act as in xt_track but their status is not reported.             */
+   overlap on the GPU (other streams, other trackers) race.  The current
+   device must be the tracker's (else XT_ERR_INVALID).  Cycle budget and
+   cancel act as in xt_track; their status goes to the array's status word,
+   which xt_noalloc_status() reads.                                         */
 #define XT_NOALLOC_MAX_PARTICLES 1048576
 int xt_track_noalloc(xt_tracker* tr, const xt_particles* p, int64_t start_turn, int64_t n_turns,
                      void* stream);
+
+/* Outcome of the last xt_track_noalloc call on the current device: XT_OK,
+   XT_ERR_TIMEOUT (cycle budget spent) or XT_ERR_CANCELLED.  Synchronises
+   `stream`, reads the static array's status word and clears it; allocates
+   nothing.  No counterpart in the paper.                                   */
+int xt_noalloc_status(void* stream);
 
 /* Synchronises `stream` and returns the status of the tracker's launches
    since the last call: XT_OK, XT_ERR_TIMEOUT or XT_ERR_CANCELLED; clears it. */

@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 import threading
 
@@ -23,8 +24,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SRC = os.path.join(_HERE, "xtoracle.cpp")
 _SO = os.path.join(_BUILD, "liboracle.so")
+_SO_FUSED = os.path.join(_BUILD, "liboracle_fused.so")
 _lock = threading.Lock()
 _lib = None
+_lib_fused = None
 
 # Lattice-table row: the same memory layout the library's public header uses.
 ELEMENT_DTYPE = np.dtype([("type", "<i4"), ("order", "<i4"), ("p", "<f8", (48,))], align=True)
@@ -39,25 +42,36 @@ FLOAT_FIELDS = ("x", "px", "y", "py", "zeta", "delta", "ptau", "rpp", "rvv")
 INT_FIELDS = ("state", "at_turn", "at_element")
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_build/liboracle.so`` (g++, no contraction)."""
+def build(force: bool = False, fused: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (g++, no
+    contraction: every product and sum rounded on its own).
+
+    ``fused=True`` builds the same source as ``liboracle_fused.so`` with the
+    compiler free to contract a*b + c into fused multiply-adds.  That build
+    differs from the plain one by rounding alone, so the distance between
+    the two after many turns is the floor below which no FP64 tracker can be
+    expected to reproduce the oracle; the long-run tests measure it."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_SO)
-            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
-        return _SO
-    tmp = _SO + ".tmp%d" % os.getpid()
-    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math",
-           "-shared", "-fPIC", "-o", tmp, _SRC]
+    so = _SO_FUSED if fused else _SO
+    if (not force and os.path.exists(so)
+            and os.path.getmtime(so) >= os.path.getmtime(_SRC)):
+        return so
+    tmp = so + ".tmp%d" % os.getpid()
+    if fused:
+        flags = ["-ffp-contract=fast"] + (["-mfma"] if platform.machine() in ("x86_64", "AMD64") else [])
+    else:
+        flags = ["-ffp-contract=off", "-fno-fast-math"]
+    cmd = ["g++", "-std=c++17", "-O2", *flags, "-shared", "-fPIC", "-o", tmp, _SRC]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _SO)
-    return _SO
+    os.replace(tmp, so)
+    return so
 
 
-def lib() -> ctypes.CDLL:
-    global _lib
+def lib(fused: bool = False) -> ctypes.CDLL:
+    global _lib, _lib_fused
     with _lock:
-        if _lib is None:
-            path = build()
+        if (_lib_fused if fused else _lib) is None:
+            path = build(fused=fused)
             L = ctypes.CDLL(path)
             P = ctypes.c_void_p
             i64, i32, u64, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_double
@@ -67,10 +81,6 @@ def lib() -> ctypes.CDLL:
             L.xo_track_jacobian.restype = i32
             L.xo_closed_orbit.argtypes = [P, i64, P, i32, i32, P]
             L.xo_closed_orbit.restype = i32
-            L.xo_sin.argtypes = [dbl]
-            L.xo_sin.restype = dbl
-            L.xo_inv_pz_m1.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
-            L.xo_inv_pz_m1.restype = None
             L.xo_philox4x64_10.argtypes = [P, P, P]
             L.xo_philox4x64_10.restype = None
             L.xo_uniform.argtypes = [u64, u64, u64, u64, i64]
@@ -82,18 +92,19 @@ def lib() -> ctypes.CDLL:
             L.xo_ref_constants.argtypes = [P, P]
             L.xo_refine_losses.argtypes = [P, i64, P] + [P] * 11 + [i64, dbl, i32, P]
             L.xo_refine_losses.restype = i32
-            L.xo_exp.argtypes = [P, P, i64]
-            L.xo_exp.restype = None
-            L.xo_one_minus_exp.argtypes = [P, P, i64]
-            L.xo_one_minus_exp.restype = None
-            L.xo_faddeeva.argtypes = [P, P, P, P, i64]
-            L.xo_faddeeva.restype = None
             L.xo_gauss_field.argtypes = [dbl, dbl, P, P, P, P, i64]
             L.xo_gauss_field.restype = None
+            L.xo_gauss_legendre.argtypes = [P, P]
+            L.xo_gauss_legendre.restype = i32
+            L.xo_osc_funcs.argtypes = [P, P, i64]
+            L.xo_osc_funcs.restype = None
             L.xo_lyapunov.argtypes = [P, i64, P, i32, P, P, P, i64, i64, i64, P, P, P]
             L.xo_lyapunov.restype = i32
-            _lib = L
-    return _lib
+            if fused:
+                _lib_fused = L
+            else:
+                _lib = L
+    return _lib_fused if fused else _lib
 
 
 def _ptr(a: np.ndarray) -> int:
@@ -129,8 +140,9 @@ def refine_losses(elements, ref, particles: dict, ds: float, n_angles: int = 128
 
 
 def track(elements, ref, particles: dict, n_turns: int, start_turn: int = 0,
-          rad_mode: int = 0, seed: int = 0) -> dict:
-    """Track a copy of ``particles`` (dict of numpy arrays); returns the new dict."""
+          rad_mode: int = 0, seed: int = 0, fused: bool = False) -> dict:
+    """Track a copy of ``particles`` (dict of numpy arrays); returns the new
+    dict.  ``fused`` runs the contracted build (see ``build``)."""
     el = _elements(elements)
     r = _ref_arr(ref)
     out = {}
@@ -140,7 +152,7 @@ def track(elements, ref, particles: dict, n_turns: int, start_turn: int = 0,
         out[k] = np.ascontiguousarray(particles[k], dtype=np.int32).copy()
     out["particle_id"] = np.ascontiguousarray(particles["particle_id"], dtype=np.int64).copy()
     n = out["x"].shape[0]
-    rc = lib().xo_track(_ptr(el), el.shape[0], _ptr(r), rad_mode, seed,
+    rc = lib(fused).xo_track(_ptr(el), el.shape[0], _ptr(r), rad_mode, seed,
                         *[_ptr(out[k]) for k in FLOAT_FIELDS],
                         *[_ptr(out[k]) for k in INT_FIELDS], _ptr(out["particle_id"]),
                         n, start_turn, n_turns)
@@ -210,8 +222,8 @@ def lyapunov(elements, ref, z0, dz0, n_turns: int, every: int = 10, metric=None,
 
 
 def _track_job(args):
-    elements, ref, particles, n_turns = args
-    return track(elements, ref, particles, n_turns)
+    elements, ref, particles, n_turns, fused = args
+    return track(elements, ref, particles, n_turns, fused=fused)
 
 
 def _lyapunov_job(args):
@@ -224,18 +236,19 @@ def _chunks(n: int, procs: int):
     return [c for c in np.array_split(np.arange(n), k) if c.size]
 
 
-def track_parallel(elements, ref, particles: dict, n_turns: int, procs: int | None = None) -> dict:
+def track_parallel(elements, ref, particles: dict, n_turns: int, procs: int | None = None,
+                   fused: bool = False) -> dict:
     """``track`` split over ``procs`` spawned processes (one particle slice
     each; the particles are independent, so the result is the same)."""
     import multiprocessing as mp
-    lib()  # built once here, not by every worker
+    lib(fused)  # built once here, not by every worker
     n = np.asarray(particles["x"]).shape[0]
     if n == 0:
-        return track(elements, ref, particles, n_turns)
+        return track(elements, ref, particles, n_turns, fused=fused)
     procs = procs or os.cpu_count() or 1
     parts = _chunks(n, procs)
     jobs = [(elements, ref, {k: np.asarray(particles[k])[c] for k in FLOAT_FIELDS + INT_FIELDS + ("particle_id",)},
-             n_turns) for c in parts]
+             n_turns, fused) for c in parts]
     with mp.get_context("spawn").Pool(len(jobs)) as pool:
         res = pool.map(_track_job, jobs)
     return {k: np.concatenate([r[k] for r in res]) for k in res[0]}
@@ -264,31 +277,6 @@ def canonical(particles: dict, ref) -> np.ndarray:
                     + [np.asarray(particles["ptau"], dtype=np.float64) / beta0], axis=1)
 
 
-def sin(x: float) -> float:
-    return lib().xo_sin(float(x))
-
-
-def _vec(f, *arrays, outs=1):
-    a = [np.ascontiguousarray(x, dtype=np.float64) for x in arrays]
-    o = [np.empty_like(a[0]) for _ in range(outs)]
-    f(*[x.ctypes.data for x in a], *[x.ctypes.data for x in o], a[0].size)
-    return o[0] if outs == 1 else o
-
-
-def exp(x) -> np.ndarray:
-    """The beam-beam kick's e^x as the oracle evaluates it."""
-    return _vec(lib().xo_exp, x)
-
-
-def one_minus_exp(u) -> np.ndarray:
-    return _vec(lib().xo_one_minus_exp, u)
-
-
-def faddeeva(x, y):
-    """w(x + i y) for y >= 0 as (real, imaginary) arrays."""
-    return _vec(lib().xo_faddeeva, x, y, outs=2)
-
-
 def gauss_field(sx: float, sy: float, x, y):
     """Field shape (f_x, f_y) of a unit bi-Gaussian line charge."""
     a = [np.ascontiguousarray(v, dtype=np.float64) for v in (x, y)]
@@ -298,11 +286,19 @@ def gauss_field(sx: float, sy: float, x, y):
     return fx, fy
 
 
-def inv_pz_m1(u) -> np.ndarray:
-    """The drift's (1+u)^(-1/2) - 1 as the oracle evaluates it."""
-    u = np.ascontiguousarray(u, dtype=np.float64)
-    out = np.empty_like(u)
-    lib().xo_inv_pz_m1(u.ctypes.data, out.ctypes.data, u.size)
+def gauss_legendre():
+    """Nodes and weights of the oracle's quadrature rule on [-1, 1]."""
+    x = np.zeros(64)
+    w = np.zeros(64)
+    n = lib().xo_gauss_legendre(_ptr(x), _ptr(w))
+    return x[:n].copy(), w[:n].copy()
+
+
+def osc_funcs(z) -> np.ndarray:
+    """(n, 4) array of the thick maps' C, S, S2, S3 at z."""
+    z = np.ascontiguousarray(np.atleast_1d(z), dtype=np.float64)
+    out = np.empty((z.size, 4))
+    lib().xo_osc_funcs(_ptr(z), _ptr(out), z.size)
     return out
 
 

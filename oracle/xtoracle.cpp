@@ -13,10 +13,21 @@
 // elements stop tracking of particles found outside ("Particle-matter
 // interaction and collimation studies"), and that synchrotron radiation has a
 // "mean" and a "quantum" model for thin elements ("Synchrotron radiation models
-// and compensation").  The maps below are the textbook thin-lens Hamiltonian
-// maps with MAD-X sign conventions; every operation order and every explicit
-// fma is part of the map definition, so the CUDA path can reproduce the same
-// bits.  Build with -O2 -ffp-contract=off (no implicit contraction).
+// and compensation").  The maps below are the textbook Hamiltonian maps with
+// MAD-X sign conventions, each written out from its definition with IEEE
+// square roots and divisions and the C library's sin, cos, exp, expm1 and
+// asin.  Three places rewrite a difference of nearly equal numbers into an
+// algebraically equal form without the cancellation, because the plain
+// difference would lose more digits than the comparison with the GPU allows:
+//   - the energy update, delta = u / (sqrt(1+u) + 1), u = (1+delta)^2 - 1;
+//   - 1 - ep/pz (drift) and 1 - 1/rvv (thick elements), from
+//     (1+delta)^2 - (1 + beta0 ptau)^2 = ptau (2/beta0 + ptau) / gamma0^2;
+//   - the thin dipole of the curved frame, whose field knl0 and frame term
+//     hxl (1+delta) are both about 1e-3 and cancel on the design orbit: the
+//     kick is (hxl - knl0) + hxl delta minus the field of the orders >= 1.
+// Small-argument evaluations of entire functions use their Taylor series
+// where the closed form cancels (1 - cos a, a - sin a, asin(u)/u).
+// Build with -O2 -ffp-contract=off (no implicit contraction).
 //
 // Coordinates: x, px=Px/P0, y, py, zeta=s-beta0*c*t, delta=(P-P0)/P0,
 // ptau=(E-E0)/(P0 c), rpp=1/(1+delta), rvv=beta/beta0.
@@ -25,11 +36,11 @@
 // (double) and exact first derivatives (Dual, forward-mode differentiation)
 // for the one-turn Jacobian, the closed orbit and the optics pins.
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <vector>
-#include <algorithm>
 
 namespace xo {
 
@@ -80,107 +91,30 @@ static inline Dual operator/(double a, const Dual& b) { Dual r; r.v = a / b.v; f
 static inline double val(double a) { return a; }
 static inline double val(const Dual& a) { return a.v; }
 
-// fma: one rounding for the value; exact derivative of a*b+c.
-static inline double FMA(double a, double b, double c) { return std::fma(a, b, c); }
-static inline Dual FMA(const Dual& a, const Dual& b, const Dual& c) {
-  Dual r; r.v = std::fma(a.v, b.v, c.v);
-  for (int i = 0; i < 6; i++) r.d[i] = a.d[i] * b.v + a.v * b.d[i] + c.d[i];
-  return r;
-}
-static inline Dual FMA(double a, const Dual& b, const Dual& c) { return FMA(mkd(a), b, c); }
-static inline Dual FMA(const Dual& a, double b, const Dual& c) { return FMA(a, mkd(b), c); }
-static inline Dual FMA(const Dual& a, const Dual& b, double c) { return FMA(a, b, mkd(c)); }
-static inline Dual FMA(double a, const Dual& b, double c) { return FMA(mkd(a), b, mkd(c)); }
-static inline Dual FMA(const Dual& a, double b, double c) { return FMA(a, mkd(b), mkd(c)); }
-// a b + c with a, b constants (used only by value-only elements)
-static inline Dual FMA(double a, double b, const Dual& c) { Dual r = c; r.v = std::fma(a, b, c.v); return r; }
+// Elementary functions: the C library for values, the chain rule for duals.
 static inline double SQRT(double a) { return std::sqrt(a); }
-static inline Dual SQRT(const Dual& a) { Dual r; r.v = std::sqrt(a.v); for (int i = 0; i < 6; i++) r.d[i] = a.d[i] / (2.0 * r.v); return r; }
+static inline double SIN(double a) { return std::sin(a); }
+static inline double COS(double a) { return std::cos(a); }
+static inline double EXP(double a) { return std::exp(a); }
+static inline double ASIN(double a) { return std::asin(a); }
+static inline Dual chain(double v, double dv, const Dual& a) {
+  Dual r; r.v = v; for (int i = 0; i < 6; i++) r.d[i] = dv * a.d[i]; return r;
+}
+static inline Dual SQRT(const Dual& a) { const double s = std::sqrt(a.v); return chain(s, 0.5 / s, a); }
+static inline Dual SIN(const Dual& a) { return chain(std::sin(a.v), std::cos(a.v), a); }
+static inline Dual COS(const Dual& a) { return chain(std::cos(a.v), -std::sin(a.v), a); }
+static inline Dual EXP(const Dual& a) { const double e = std::exp(a.v); return chain(e, e, a); }
+static inline Dual ASIN(const Dual& a) { return chain(std::asin(a.v), 1.0 / std::sqrt(1.0 - a.v * a.v), a); }
 
-// ---------------------------------------------------------------------------
-// sin(x): Cody & Waite (1980) additive range reduction by pi/2 with a
-// three-part constant, then the Taylor series of sin/cos on |r| <= pi/4
-// evaluated by Horner's rule.  Written out so that both implementations of the
-// tracker produce identical bits (library sin routines differ by an ulp).
-// Valid for |x| < 2^40; accuracy about 1 ulp on |x| < 1e6.
-static const double PIO2_1 = 1.5707963267948965579989817342720925807952880859375;
-static const double PIO2_2 = 6.123233995736766035868820147291818682e-17;
-static const double PIO2_3 = -1.4973849048591698329435081771059e-33;
-static const double TWO_OVER_PI = 0.63661977236758134307553505349005744813783858296183;
-static const double RND_MAGIC = 6755399441055744.0;  // 1.5 * 2^52
-
-struct SinCoef {
-  double s[10];  // (-1)^k / (2k+1)!, k = 0..9  (1, -1/3!, ..., -1/19!)
-  double c[11];  // (-1)^k / (2k)!,  k = 0..10 (1, -1/2!, ..., 1/20!)
-  SinCoef() {
-    double f = 1.0;  // running factorial, exact up to 20! as a double
-    for (int n = 1; n <= 21; n++) {
-      f = f * (double)n;
-      if (n % 2 == 1) { int k = (n - 1) / 2; if (k < 10) s[k] = ((k % 2) ? -1.0 : 1.0) / f; }
-      else { int k = n / 2; if (k < 11) c[k] = ((k % 2) ? -1.0 : 1.0) / f; }
-    }
-    s[0] = 1.0; c[0] = 1.0;
-  }
-};
-static const SinCoef SC;
-
-double sin_cw(double x) {
-  double k = (x * TWO_OVER_PI + RND_MAGIC) - RND_MAGIC;  // nearest integer
-  double r = std::fma(-k, PIO2_1, x);
-  r = std::fma(-k, PIO2_2, r);
-  r = std::fma(-k, PIO2_3, r);
-  long long q = (long long)k;
-  int quad = (int)(q & 3);
-  double z = r * r;
-  double res;
-  if (quad & 1) {  // cos r
-    double p = SC.c[10];
-    for (int i = 9; i >= 0; i--) p = std::fma(p, z, SC.c[i]);
-    res = p;
-  } else {  // sin r = r * (s0 + z*(s1 + ...))
-    double p = SC.s[9];
-    for (int i = 8; i >= 1; i--) p = std::fma(p, z, SC.s[i]);
-    res = std::fma(r * z, p, r);
-  }
-  return (quad & 2) ? -res : res;
-}
-// cos x: the same reduction as sin_cw with the quadrant advanced by one.
-double cos_cw(double x) {
-  double k = (x * TWO_OVER_PI + RND_MAGIC) - RND_MAGIC;
-  double r = std::fma(-k, PIO2_1, x);
-  r = std::fma(-k, PIO2_2, r);
-  r = std::fma(-k, PIO2_3, r);
-  long long q = (long long)k;
-  int quad = (int)((q + 1) & 3);
-  double z = r * r;
-  double res;
-  if (quad & 1) {
-    double p = SC.c[10];
-    for (int i = 9; i >= 0; i--) p = std::fma(p, z, SC.c[i]);
-    res = p;
-  } else {
-    double p = SC.s[9];
-    for (int i = 8; i >= 1; i--) p = std::fma(p, z, SC.s[i]);
-    res = std::fma(r * z, p, r);
-  }
-  return (quad & 2) ? -res : res;
-}
-static inline double SIN(double a) { return sin_cw(a); }
-static inline double COS(double a) { return cos_cw(a); }
-static inline Dual COS(const Dual& a) {
-  Dual r; r.v = cos_cw(a.v); double sn = std::sin(a.v);
-  for (int i = 0; i < 6; i++) r.d[i] = -sn * a.d[i];
-  return r;
-}
-static inline Dual SIN(const Dual& a) {
-  Dual r; r.v = sin_cw(a.v); double c = std::cos(a.v);
-  for (int i = 0; i < 6; i++) r.d[i] = c * a.d[i];
-  return r;
-}
+template <class T> static inline T mkv(double v);
+template <> inline double mkv<double>(double v) { return v; }
+template <> inline Dual mkv<Dual>(double v) { return mkd(v); }
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter-based RNG.
 // Counter = (particle id, turn, element index, call index); key = (seed, 0).
+// This is the one generator both implementations write from its published
+// definition; the method's random numbers are its output words.
 static inline void mulhilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
   __uint128_t p = (__uint128_t)a * (__uint128_t)b;
   *hi = (uint64_t)(p >> 64);
@@ -200,8 +134,8 @@ void philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]
   }
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
-// 53-bit uniform in [0, 1) from a 64-bit word.
-static inline double u01(uint64_t w) { return (double)(w >> 11) * (1.0 / 9007199254740992.0); }
+// 53-bit uniform in [0, 1) from a 64-bit word: (w >> 11) / 2^53.
+static inline double u01(uint64_t w) { return (double)(w >> 11) / 9007199254740992.0; }
 
 // Stream of uniforms for one (particle, turn, element): four per Philox call.
 struct Uniforms {
@@ -226,14 +160,15 @@ struct Uniforms {
 //   S(xi) = int_xi^inf G(s) ds = int_0^inf exp(-xi cosh t) cosh(5t/3)/cosh^2 t dt,
 // and the cumulative distribution is F(xi) = 1 - S(xi)/(5 pi/3).  S is
 // evaluated by the trapezoidal rule in t (the integrand is even and analytic in
-// the strip |Im t| < pi/2, so the rule converges geometrically).
-static const int SPEC_K = 2048, SPEC_GUIDE = 4096;
+// the strip |Im t| < pi/2, so the rule converges geometrically).  The sampler
+// (a reading: the paper cites Burkhardt's method, whose text is absent) is the
+// inverse of the piecewise-linear interpolant of F through 2048 knots
+// log-spaced on [1e-7, 40], with the small-xi asymptote F ~ xi^(1/3) below the
+// first knot and a clamp above the last.
+static const int SPEC_K = 2048;
 static const double SPEC_XI_MIN = 1e-7, SPEC_XI_MAX = 40.0;
 struct Spectrum {
   double xi[SPEC_K], F[SPEC_K];
-  int guide[SPEC_GUIDE];  // guide[j] = max{i : F[i] <= j / SPEC_GUIDE} (Chen and Asau, 1974)
-  double idF[SPEC_K];     // 1 / (F[i+1] - F[i]): the interpolation multiplies instead of dividing
-  double iF0;             // 1 / F[0]
   Spectrum() {
     const double norm = 5.0 * PI / 3.0, h = 0.05;
     for (int i = 0; i < SPEC_K; i++) {
@@ -250,37 +185,24 @@ struct Spectrum {
       xi[i] = x;
       F[i] = 1.0 - (h * s) / norm;
     }
-    int i = 0;
-    for (int j = 0; j < SPEC_GUIDE; j++) {
-      const double t = (double)j / (double)SPEC_GUIDE;
-      while (i + 1 < SPEC_K && F[i + 1] <= t) i++;
-      guide[j] = i;
-    }
-    for (int k = 0; k + 1 < SPEC_K; k++) idF[k] = 1.0 / (F[k + 1] - F[k]);
-    idF[SPEC_K - 1] = 0.0;
-    iF0 = 1.0 / F[0];
   }
-  // Inverse CDF: power-law asymptote F ~ xi^(1/3) below the first knot,
-  // linear interpolation between knots lo and lo + 1 with
-  // lo = max{i : F[i] <= u} (walked up from the guide entry of u's cell),
-  // clamp above the last knot.
+  // Inverse of the interpolated CDF at u in [0, 1): the knot interval
+  // lo = max{i : F[i] <= u} is found by binary search.
   double sample(double u) const {
-    if (u < F[0]) { double q = u * iF0; return xi[0] * q * q * q; }
+    if (u < F[0]) { double q = u / F[0]; return xi[0] * q * q * q; }
     if (u >= F[SPEC_K - 1]) return xi[SPEC_K - 1];
-    int lo = guide[(int)(u * (double)SPEC_GUIDE)];
-    while (F[lo + 1] <= u) lo++;
+    const int lo = (int)(std::upper_bound(F, F + SPEC_K, u) - F) - 1;
     const int hi = lo + 1;
-    double w = (u - F[lo]) * idF[lo];
+    const double w = (u - F[lo]) / (F[hi] - F[lo]);
     return xi[lo] + w * (xi[hi] - xi[lo]);
   }
 };
 static const Spectrum& spectrum() { static Spectrum s; return s; }
 
 // ---------------------------------------------------------------------------
-// Reference-derived constants (computed once per call on the host).
+// Reference-derived constants.
 struct RefConst {
-  double m0, q0, p0c, E0, beta0, gamma0, bg0, ib0, twoib0;
-  // radiation
+  double m0, q0, p0c, E0, beta0, gamma0, bg0, ib0, twoib0, ig02;
   double crad;   // (2/3) r_c m0 / p0c   [m]
   double kq;     // (5 / (2 sqrt 3)) alpha q0^2  (mean photon count per gamma*h*L)
   double uc15;   // 1.5 hbar c  [eV m]
@@ -294,6 +216,7 @@ static RefConst ref_const(const Reference& r) {
   c.bg0 = r.p0c / r.mass0;
   c.ib0 = c.E0 / r.p0c;
   c.twoib0 = 2.0 * c.ib0;
+  c.ig02 = (r.mass0 / c.E0) * (r.mass0 / c.E0);  // 1/gamma0^2
   const double rc = r.q0 * r.q0 * R_ELECTRON * M_ELECTRON / r.mass0;
   c.crad = 2.0 * rc * r.mass0 / (3.0 * r.p0c);
   c.kq = 5.0 * ALPHA_FS * r.q0 * r.q0 / (2.0 * std::sqrt(3.0));
@@ -302,222 +225,117 @@ static RefConst ref_const(const Reference& r) {
 }
 
 // ---------------------------------------------------------------------------
-// Special functions of the beam-beam kick (section "Beam-beam interactions").
+// Field of a bi-Gaussian line charge (section "Beam-beam interactions"; the
+// frozen model of section "Space charge").  For a unit line charge with rms
+// sizes sigma_x, sigma_y, f = E 2 pi eps0 / lambda is the single integral
+//   f_x = x int_0^inf exp(-x^2/(2sx^2+q) - y^2/(2sy^2+q)) / ((2sx^2+q)^(3/2) (2sy^2+q)^(1/2)) dq,
+// f_y the same with the exponents 3/2 and 1/2 exchanged.  With c = min(2sx^2,
+// 2sy^2) and q = c (1 - t)/t it is an integral over t in (0, 1] of a bounded
+// analytic function,
+//   f_x = x c int_0^1 exp(-t (x^2/Ax + y^2/Ay)) / (Ax^(3/2) Ay^(1/2)) dt,
+//   Ax = c + (2sx^2 - c) t >= c,  Ay = c + (2sy^2 - c) t >= c,
+// whose mass sits at t ~ 1/R for a particle at R = (x^2 + y^2)/c >> 1.  With
+// t = exp(-w) the integrand is smooth on the scale of one unit of w (the
+// Gaussian's own decay near w = ln R, the change of Ax or Ay from c to
+// 2s^2 near w = ln(2s^2/c)), and the integral over w in [0, W],
+// W = 40 + ln max(1, R) (the rest is below e^-40 of it), is taken by the
+// 16-point Gauss-Legendre rule on unit intervals.  A round beam (sx == sy) has the closed form
+// f = (x, y)(1 - exp(-r^2/(2 s^2)))/r^2.
 
-// 1/n! for n = 0..21 (n! is exact in double up to 18!; beyond, the running
-// product rounds, far below what the series that use these terms resolve).
-static const std::vector<double>& inv_fact() {
-  static std::vector<double> c = [] {
-    std::vector<double> v(22);
-    double f = 1.0;
-    for (int n = 0; n <= 21; n++) {
-      if (n > 0) f = f * (double)n;
-      v[n] = 1.0 / f;
+// Nodes and weights of the n-point Gauss-Legendre rule on [-1, 1]: Newton's
+// method on P_n from the three-term recurrence (n + 1) P_(n+1) = (2n + 1) x P_n - n P_(n-1).
+struct GaussLegendre {
+  static const int N = 16;
+  double x[N], w[N];
+  GaussLegendre() {
+    for (int i = 0; i < N; i++) {
+      double z = std::cos(PI * (i + 0.75) / (N + 0.5));
+      for (int it = 0; it < 100; it++) {
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= N; k++) {
+          const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / (double)k;
+          p0 = p1;
+          p1 = p2;
+        }
+        const double dp = N * (z * p1 - p0) / (z * z - 1.0);  // P_n'
+        const double dz = p1 / dp;
+        z = z - dz;
+        if (std::fabs(dz) < 1e-17 || it == 99) {
+          double q0 = 1.0, q1 = z;
+          for (int k = 2; k <= N; k++) {
+            const double q2 = ((2.0 * k - 1.0) * z * q1 - (k - 1.0) * q0) / (double)k;
+            q0 = q1;
+            q1 = q2;
+          }
+          const double d = N * (z * q1 - q0) / (z * z - 1.0);
+          x[i] = z;
+          w[i] = 2.0 / ((1.0 - z * z) * d * d);
+          break;
+        }
+      }
     }
-    return v;
-  }();
-  return c;
-}
-
-// e^x: Cody-Waite reduction x = k ln2 + r with ln 2 split into a head with
-// 20 significant bits (k * head exact) and a tail, e^r by its Taylor series
-// to r^13 on |r| <= ln2/2 (truncation below 1e-17 relative), times 2^k from
-// the exponent bits (in two steps below the normal range).
-static double exp_cw(double x) {
-  if (x != x) return x;
-  if (!(x > -745.2)) return 0.0;
-  if (x > 709.7) return INFINITY;
-  const double sh = 6755399441055744.0;  // 1.5 * 2^52: adding it rounds to an integer
-  const double t = std::fma(x, 1.4426950408889634, sh) - sh;
-  const int k = (int)t;
-  double r = std::fma(-t, 0x1.62e42p-1, x);
-  r = std::fma(-t, 0x1.fdf473de6af28p-22, r);
-  const std::vector<double>& c = inv_fact();
-  double p = c[13];
-  for (int n = 12; n >= 0; n--) p = std::fma(p, r, c[n]);
-  auto pow2 = [](int e) {
-    const uint64_t b = (uint64_t)(e + 1023) << 52;
-    double v;
-    std::memcpy(&v, &b, 8);
-    return v;
-  };
-  if (k >= -1022) return p * pow2(k);
-  return (p * pow2(k + 64)) * pow2(-64);
-}
-
-// 1 - e^(-u) for u >= 0 without cancellation: for u < 1/2 the series
-// u sum_n (-u)^n / (n+1)!, n = 0..17 (truncation below 1e-22), else 1 - e^(-u).
-static double one_minus_exp(double u) {
-  const std::vector<double>& c = inv_fact();
-  if (u < 0.5) {
-    double s = c[18];
-    for (int n = 16; n >= 0; n--) s = std::fma(s, -u, c[n + 1]);
-    return u * s;
   }
-  return 1.0 - exp_cw(-u);
-}
-
-// e^a for scalars and dual numbers (the hyperbolic branch of the oscillator
-// functions of the thick elements).
-static inline double EXPC(double a) { return exp_cw(a); }
-static inline Dual EXPC(const Dual& a) {
-  Dual r; r.v = exp_cw(a.v);
-  for (int i = 0; i < 6; i++) r.d[i] = r.v * a.d[i];
-  return r;
-}
-
-// Faddeeva function w(z) = e^(-z^2) erfc(-i z) for Im z >= 0 by Weideman's
-// rational expansion (J. A. C. Weideman, SIAM J. Numer. Anal. 31 (1994)
-// 1497): w = 2 p(Z) / (L - i z)^2 + (1/sqrt(pi)) / (L - i z), Z = (L + i z) /
-// (L - i z), p a polynomial of degree N - 1 = 39, L = (N / sqrt 2)^(1/2);
-// p's coefficients are the cosine transform of e^(-t^2)(L^2 + t^2) sampled at
-// t = L tan(theta/2), here by a plain DFT.
-struct Faddeeva {
-  double L;
-  double a[40];  // p(Z) = sum_n a[n] Z^n
 };
-static const Faddeeva& faddeeva_coefficients() {
-  static Faddeeva c = [] {
-    Faddeeva q;
-    const int N = 40, M = 2 * N, M2 = 2 * M;
-    const double L = std::sqrt((double)N / std::sqrt(2.0));
-    std::vector<double> f(M2), fs(M2);
-    f[0] = 0.0;
-    for (int j = 1; j < M2; j++) {
-      const int k = j - M;  // -M+1 .. M-1
-      const double theta = (double)k * PI / (double)M;
-      const double t = L * std::tan(theta / 2.0);
-      f[j] = std::exp(-t * t) * (L * L + t * t);
-    }
-    for (int j = 0; j < M2; j++) fs[j] = f[(j + M) % M2];
-    q.L = L;
-    for (int n = 0; n < N; n++) {
-      const int m = n + 1;
-      double acc = 0.0;
-      for (int j = 0; j < M2; j++) acc = acc + fs[j] * std::cos(2.0 * PI * (double)((j * m) % M2) / (double)M2);
-      q.a[n] = acc / (double)M2;
-    }
-    return q;
-  }();
-  return c;
-}
+static const GaussLegendre& gauss_legendre() { static GaussLegendre g; return g; }
 
-static void faddeeva(double x, double y, double* wr, double* wi) {
-  const Faddeeva& c = faddeeva_coefficients();
-  const double L = c.L;
-  const double cr = L + y;                      // L - i z = (L + y) - i x
-  const double D = std::fma(cr, cr, x * x);
-  const double qr = cr / D, qi = x / D;         // q = 1 / (L - i z)
-  const double ar = L - y;                      // L + i z = (L - y) + i x
-  const double Zr = std::fma(ar, qr, -(x * qi));
-  const double Zi = std::fma(ar, qi, x * qr);
-  double pr = c.a[39], pi = 0.0;
-  for (int n = 38; n >= 0; n--) {
-    const double nr = std::fma(pr, Zr, std::fma(-pi, Zi, c.a[n]));
-    const double ni = std::fma(pr, Zi, pi * Zr);
-    pr = nr;
-    pi = ni;
+// f = (f_x, f_y) at (x, y) about the charge's centre.
+static void gauss_field(double x, double y, double sx, double sy, double* fx, double* fy) {
+  const double x2 = x * x, y2 = y * y;
+  if (sx == sy) {
+    const double r2 = x2 + y2;
+    const double s2 = 2.0 * sx * sx;
+    const double g = (r2 == 0.0) ? 1.0 / s2 : -std::expm1(-r2 / s2) / r2;
+    *fx = x * g;
+    *fy = y * g;
+    return;
   }
-  const double tr = std::fma(pr, qr, -(pi * qi));  // t = p q
-  const double ti = std::fma(pr, qi, pi * qr);
-  const double ur = std::fma(2.0, tr, 0.5641895835477563);  // u = 2 p q + 1/sqrt(pi)
-  const double ui = 2.0 * ti;
-  *wr = std::fma(qr, ur, -(qi * ui));  // w = q u
-  *wi = std::fma(qr, ui, qi * ur);
-}
-
-// Constants of a 4D beam-beam lens (table: p[0] = charge times number of
-// particles of the strong bunch [e], p[1] = its speed beta_s (moving against
-// the tracked beam), p[2], p[3] = sigma_x, sigma_y [m], p[4], p[5] = its
-// centre [m]).
-struct BBConst {
-  double K, xc, yc;
-  int mode;        // 0 round, 1 sigma_x > sigma_y, 2 sigma_y > sigma_x
-  double h1, h2;   // 1/(2 sigma_1^2), 1/(2 sigma_2^2) (round: h1 = 1/(2 sigma^2))
-  double rs, rsi;  // sigma_2/sigma_1, sigma_1/sigma_2
-  double invS, cpre;  // 1/S, sqrt(pi)/S, S = sqrt(2 (sigma_1^2 - sigma_2^2))
-  double lin1, lin2;  // 1/(sigma_1 (sigma_1 + sigma_2)), 1/(sigma_2 (sigma_1 + sigma_2))
-};
-
-// Field of a unit bi-Gaussian line charge, f = E 2 pi eps0 / lambda, at (x, y)
-// about its centre: Bassetti-Erskine with w(z) in the first quadrant and the
-// signs restored from symmetry; round beam: (x, y)(1 - e^(-r^2/2 sigma^2))/r^2.
-// Within rho^2 = (x/sigma_x)^2 + (y/sigma_y)^2 < 1e-10 of the centre the
-// difference of the two w values cancels, and the linear field
-// (x / (sigma_x (sigma_x + sigma_y)), y / (sigma_y (sigma_x + sigma_y))),
-// whose relative error there is of order rho^2, is used instead.
-static void gauss_field(double x, double y, const BBConst& b, double* fx, double* fy) {
-  const double ax = std::fabs(x), ay = std::fabs(y);
-  double gx, gy;
-  if (b.mode == 0) {
-    const double r2 = std::fma(ax, ax, ay * ay);
-    const double g = (r2 == 0.0) ? b.h1 : one_minus_exp(r2 * b.h1) / r2;
-    gx = ax * g;
-    gy = ay * g;
-  } else {
-    const double u = (b.mode == 1) ? ax : ay, v = (b.mode == 1) ? ay : ax;  // u along the larger sigma
-    const double h = std::fma(u, u * b.h1, v * (v * b.h2));                // rho^2 / 2
-    double fu, fv;
-    if (h < 5e-11) {
-      fu = u * b.lin1;
-      fv = v * b.lin2;
-    } else {
-      double w1r, w1i, w2r, w2i;
-      faddeeva(u * b.invS, v * b.invS, &w1r, &w1i);
-      faddeeva((u * b.rs) * b.invS, (v * b.rsi) * b.invS, &w2r, &w2i);
-      const double e = exp_cw(-h);
-      fu = b.cpre * std::fma(-e, w2i, w1i);  // Im of (sqrt(pi)/S)(w1 - e w2)
-      fv = b.cpre * std::fma(-e, w2r, w1r);  // Re
+  const double a = 2.0 * sx * sx, b = 2.0 * sy * sy, c = std::min(a, b);
+  const double R = (x2 + y2) / c;
+  const int nw = (int)std::ceil(40.0 + std::log(std::max(1.0, R)));
+  const GaussLegendre& g = gauss_legendre();
+  double ix = 0.0, iy = 0.0;
+  for (int k = 0; k < nw; k++) {
+    const double mid = k + 0.5;
+    for (int i = 0; i < GaussLegendre::N; i++) {
+      const double w = mid + 0.5 * g.x[i];
+      const double t = std::exp(-w);
+      const double Ax = c + (a - c) * t, Ay = c + (b - c) * t;
+      const double e = std::exp(-t * (x2 / Ax + y2 / Ay));
+      const double q = g.w[i] * 0.5 * t * e / (std::sqrt(Ax) * std::sqrt(Ay));
+      ix += q / Ax;
+      iy += q / Ay;
     }
-    gx = (b.mode == 1) ? fu : fv;
-    gy = (b.mode == 1) ? fv : fu;
   }
-  *fx = std::copysign(gx, x);
-  *fy = std::copysign(gy, y);
+  *fx = x * (c * ix);
+  *fy = y * (c * iy);
 }
-
-template <class T> static inline T mkv(double v);
-template <> inline double mkv<double>(double v) { return v; }
-template <> inline Dual mkv<Dual>(double v) { return mkd(v); }
 
 // ---------------------------------------------------------------------------
-// Particle state; opd = 1+delta, dm1 = (1+delta)^2 - 1 = delta (delta + 2),
-// ep = 1 + beta0 ptau (= opd / rvv), rv0v = 1/rvv = ep rpp and
-// epm1 = beta0 ptau are derived from delta, rpp and ptau and recomputed
-// whenever those change (pure functions of the stored state, so
-// recomputation never changes a result).
+// Particle state.
 template <class T>
 struct Part {
   T x, px, y, py, zeta, delta, ptau, rpp, rvv;
-  T opd, dm1, rv0v, ep, epm1;
   int32_t state, at_turn, at_element;
   int64_t id;
 };
+
+// (1+delta)^2 - (1 + beta0 ptau)^2 = ptau (2/beta0 + ptau) / gamma0^2, the
+// difference of the squared relative momentum and the squared energy factor
+// 1 + beta0 ptau = (1+delta)/rvv, written without cancellation.
 template <class T>
-static inline void derive(Part<T>& p, const RefConst& rc) {
-  p.opd = 1.0 + p.delta;
-  p.dm1 = p.delta * (p.delta + 2.0);
-  p.ep = FMA(rc.beta0, p.ptau, 1.0);
-  p.rv0v = p.ep * p.rpp;
-  p.epm1 = rc.beta0 * p.ptau;
+static inline T dsq_mom_energy(const Part<T>& p, const RefConst& rc) {
+  return (p.ptau * (rc.twoib0 + p.ptau)) * rc.ig02;
 }
 
-// Energy update from a new ptau, using (1+delta)^2 = 1 + 2 ptau/beta0 + ptau^2
-// written in the cancellation-free form delta = u / (sqrt(1+u) + 1),
-// u = ptau (ptau + 2/beta0); then rpp = 1/(1+delta),
-// rvv = (1+delta)/(1 + beta0 ptau) and 1/rvv = (1 + beta0 ptau) rpp.
+// Energy update from a new ptau: (1+delta)^2 = 1 + 2 ptau/beta0 + ptau^2, so
+// delta = sqrt(1+u) - 1 with u = ptau (ptau + 2/beta0), evaluated as
+// u / (sqrt(1+u) + 1); then rpp = 1/(1+delta) and rvv = (1+delta)/(1 + beta0 ptau).
 template <class T>
 static inline void energy_update(Part<T>& p, const RefConst& rc) {
-  T u = p.ptau * (p.ptau + rc.twoib0);
-  T s = SQRT(1.0 + u);
-  p.delta = u / (s + 1.0);
-  p.opd = 1.0 + p.delta;
-  p.dm1 = p.delta * (p.delta + 2.0);
-  p.rpp = 1.0 / p.opd;
-  p.ep = FMA(rc.beta0, p.ptau, 1.0);
-  p.rvv = p.opd / p.ep;
-  p.rv0v = p.ep * p.rpp;
-  p.epm1 = rc.beta0 * p.ptau;
+  const T u = p.ptau * (p.ptau + rc.twoib0);
+  p.delta = u / (SQRT(1.0 + u) + 1.0);
+  p.rpp = 1.0 / (1.0 + p.delta);
+  p.rvv = (1.0 + p.delta) / (1.0 + rc.beta0 * p.ptau);
 }
 
 template <class T>
@@ -528,47 +346,22 @@ static inline void mark_lost(Part<T>& p, int code, int turn, int elem) {
 // Exact drift of length L (thin-lens integration: drifts between kicks).
 //   pz = sqrt((1+delta)^2 - px^2 - py^2),  x += px L/pz,  y += py L/pz,
 //   zeta += L - (1+delta)/rvv * L/pz  (path length L(1+delta)/pz at speed beta).
-// With u = (1+delta)^2 - 1 - px^2 - py^2 (two fused multiply-adds from
-// dm1 = delta (delta + 2)) and yh = 1/pz - 1 = (1+u)^(-1/2) - 1:
-//   L/pz = L + L yh,   zeta += -L (beta0 ptau + ep yh)   (ep - 1 = beta0 ptau),
-// so the zeta increment is formed from small quantities without cancellation.
-// yh is the Taylor series of (1+u)^(-1/2) - 1 to order 8 (coefficients
-// binomial(-1/2, n), exact dyadic numbers) for |u| <= 2^-7, where the
-// truncation error is below 2e-17 of yh; otherwise 1/sqrt(1+u) - 1.
-// A particle with u outside (-1, inf) is lost (code -2), coordinates unchanged.
-// Taylor coefficients of (1+u)^(-1/2) - 1: binomial(-1/2, n), exact dyadics.
-static const double RS_C[9] = {0.0, -0.5, 0.375, -0.3125, 0.2734375, -0.24609375, 0.2255859375,
-                               -0.20947265625, 0.196380615234375};
-
-// yh = (1+u)^(-1/2) - 1 for u in (-1, inf).  The Taylor series truncated at
-// order n leaves c_{n+1} u^{n+1}, i.e. about 2 |c_{n+1}| |u|^n relative to
-// yh ~ -u/2; the order is the lowest that keeps this below 2^-54 (half an
-// ulp) on its interval: order 3 for |u| <= 2^-18, 6 for |u| <= 2^-9, 8 for
-// |u| <= 2^-7 (Horner from the highest order, then times u); beyond that
-// 1/sqrt(1+u) - 1.
+// With ep = (1+delta)/rvv = 1 + beta0 ptau the zeta step is L (pz - ep)/pz
+// = L (pz^2 - ep^2) / (pz (pz + ep)), and pz^2 - ep^2 =
+// ptau (2/beta0 + ptau)/gamma0^2 - px^2 - py^2.  A particle with pz^2 <= 0
+// (or not finite) is lost (code -2) with its coordinates unchanged.
 template <class T>
-static inline T inv_pz_m1(T u) {
-  const double a = std::fabs(val(u));
-  int order = 0;
-  if (a <= 0x1p-18) order = 3;
-  else if (a <= 0x1p-9) order = 6;
-  else if (a <= 0x1p-7) order = 8;
-  if (order == 0) return 1.0 / SQRT(1.0 + u) - 1.0;
-  T h = mkv<T>(RS_C[order]);
-  for (int n = order - 1; n >= 1; n--) h = FMA(h, u, mkv<T>(RS_C[n]));
-  return h * u;
-}
-
-template <class T>
-static inline void drift(Part<T>& p, double L, int turn, int elem) {
-  T u = FMA(-p.px, p.px, FMA(-p.py, p.py, p.dm1));
-  double uv = val(u);
-  if (!(uv > -1.0 && uv < INFINITY)) { mark_lost(p, -2, turn, elem); return; }
-  T yh = inv_pz_m1(u);
-  T lpz = FMA(L, yh, mkv<T>(L));
-  p.x = FMA(p.px, lpz, p.x);
-  p.y = FMA(p.py, lpz, p.y);
-  p.zeta = FMA(-L, FMA(p.ep, yh, p.epm1), p.zeta);
+static inline void drift(Part<T>& p, double L, const RefConst& rc, int turn, int elem) {
+  const T opd = 1.0 + p.delta;
+  const T pz2 = opd * opd - p.px * p.px - p.py * p.py;
+  if (!(val(pz2) > 0.0 && val(pz2) < INFINITY)) { mark_lost(p, -2, turn, elem); return; }
+  const T pz = SQRT(pz2);
+  const T lpz = L / pz;
+  const T ep = 1.0 + rc.beta0 * p.ptau;
+  const T num = dsq_mom_energy(p, rc) - p.px * p.px - p.py * p.py;
+  p.x = p.x + p.px * lpz;
+  p.y = p.y + p.py * lpz;
+  p.zeta = p.zeta + L * num / (pz * (pz + ep));
 }
 
 // Energy change by radiation: ptau += dpt, then the energy update; the
@@ -576,127 +369,358 @@ static inline void drift(Part<T>& p, double L, int turn, int elem) {
 // angles px/(1+delta), py/(1+delta) are unchanged (emission along the motion).
 template <class T>
 static inline void apply_energy_loss(Part<T>& p, T dpt, const RefConst& rc) {
-  T rpp_old = p.rpp;
+  const T opd_old = 1.0 + p.delta;
   p.ptau = p.ptau + dpt;
   energy_update(p, rc);
-  T f = p.opd * rpp_old;
+  const T f = (1.0 + p.delta) / opd_old;
   p.px = p.px * f;
   p.py = p.py * f;
 }
 
-// Per-element host constants of a thin multipole: cn = knl_n/n!, sn = ksl_n/n!,
-// k0h = knl0*hxl/L_rad (0 when L_rad == 0), ilr2 = 1/L_rad^2,
-// crl = crad*L_rad, kql = kq*L_rad.
+// Per-element constants of a thin multipole: c_n = knl_n/n!, s_n = ksl_n/n!,
+// the frame curvature hxl, the radiation length L_rad, and
+// k0h = knl0 hxl / L_rad (0 when L_rad == 0).
 struct MultConst {
   int N;
   double c[11], s[11];
-  double hxl, k0h, lrad, ilr2, crl, kql;
-  bool pure;    // knl0 == ksl0 == 0 and hxl == 0: no constant term
-  bool bend;    // hxl != 0, hxl == knl0, ksl0 == 0: field and frame curvature cancel on momentum
+  double hxl, k0h, lrad;
 };
 
 // Quantum model: Poisson number of photons with mean
-// nbar = (5/(2 sqrt 3)) alpha q0^2 gamma h L, energies u = u_c xi with
-// u_c = (3/2) hbar c gamma^3 h and xi drawn from the synchrotron spectrum.
+// nbar = (5/(2 sqrt 3)) alpha q0^2 gamma h L_rad, drawn by sequential
+// inversion (p_0 = e^(-nbar), p_k = p_(k-1) nbar / k, at most 200 photons),
+// energies u = u_c xi with u_c = (3/2) hbar c gamma^3 h and xi from the
+// spectrum sampler, one uniform each, after the Poisson uniform.
 static const int KMAX_PHOTONS = 200;
-// 1/k for k = 0..KMAX_PHOTONS (entry 0 unused): the Poisson recurrence
-// pk = pk nbar / k multiplies by it.
-static const std::vector<double>& recip_k() {
-  static std::vector<double> r = [] {
-    std::vector<double> v(KMAX_PHOTONS + 1, 0.0);
-    for (int k = 1; k <= KMAX_PHOTONS; k++) v[k] = 1.0 / (double)k;
-    return v;
-  }();
-  return r;
-}
 static inline void quantum_kick(Part<double>& p, double br, double bi, const MultConst& m,
                                 const RefConst& rc, uint64_t seed, int turn, int elem) {
-  double kk = std::fma(br, br, bi * bi);
-  double h = std::sqrt(kk * m.ilr2) * p.rpp;
-  double gam = std::fma(rc.bg0, p.ptau, rc.gamma0);
-  double nbar = (m.kql * gam) * h;
+  const double h = std::sqrt(br * br + bi * bi) / (m.lrad * (1.0 + p.delta));
+  const double gam = rc.gamma0 + rc.bg0 * p.ptau;
+  const double nbar = rc.kq * m.lrad * gam * h;
   Uniforms U(seed, (uint64_t)p.id, (uint64_t)turn, (uint64_t)elem);
-  double u0 = U.next();
+  const double u0 = U.next();
   int k = 0;
-  double pk = exp_cw(-nbar), F = pk;
-  const std::vector<double>& rk = recip_k();
-  while (u0 > F && k < KMAX_PHOTONS) { k++; pk = (pk * nbar) * rk[k]; F = F + pk; }
+  double pk = std::exp(-nbar), F = pk;
+  while (u0 > F && k < KMAX_PHOTONS) { k++; pk = pk * nbar / (double)k; F = F + pk; }
   if (k == 0) return;
   const Spectrum& S = spectrum();
   double sxi = 0.0;
   for (int j = 0; j < k; j++) sxi = sxi + S.sample(U.next());
-  double uc = (rc.uc15 * (gam * gam * gam)) * h;
-  double dpt = -(uc * sxi) / rc.p0c;
-  apply_energy_loss(p, dpt, rc);
+  const double uc = rc.uc15 * gam * gam * gam * h;
+  apply_energy_loss(p, -(uc * sxi) / rc.p0c, rc);
 }
 static inline void quantum_kick(Part<Dual>&, const Dual&, const Dual&, const MultConst&,
                                 const RefConst&, uint64_t, int, int) {}
 
-// Thin multipole: b = sum_n (knl_n + i ksl_n) z^n / n!, z = x + i y, by
-// Horner's rule from the highest order; px -= Re b, py += Im b.  With a
-// curvature hxl: px += hxl (1+delta) - knl0 hxl x / L_rad and
-// zeta -= hxl x / rvv (the thin dipole of the curved reference frame).
+// Field of the orders >= 1 of a thin multipole at z = x + i y:
+// sum_{n>=1} (c_n + i s_n) z^n by Horner's rule from the top order.
+template <class T>
+static inline void multipole_field(const Part<T>& p, const MultConst& m, T* fr, T* fi) {
+  *fr = mkv<T>(0.0);
+  *fi = mkv<T>(0.0);
+  if (m.N < 1) return;
+  T ar = mkv<T>(m.c[m.N]), ai = mkv<T>(m.s[m.N]);
+  for (int n = m.N - 1; n >= 1; n--) {
+    const T nr = ar * p.x - ai * p.y + m.c[n];
+    const T ni = ar * p.y + ai * p.x + m.s[n];
+    ar = nr;
+    ai = ni;
+  }
+  *fr = ar * p.x - ai * p.y;
+  *fi = ar * p.y + ai * p.x;
+}
+
+// Thin multipole: b = sum_n (knl_n + i ksl_n) z^n / n!; px -= Re b, py += Im b.
+// With a curvature hxl the thin dipole of the curved frame adds
+// px += hxl (1+delta) - knl0 hxl x / L_rad and zeta -= hxl x / rvv.  The
+// constant term -knl0 and hxl (1+delta) are added to px together, as
+// (hxl - knl0) + hxl delta: each is about 1e-3 in a ring's dipole slice while
+// their sum on the design orbit is 0, and px itself is about 1e-5.
 // Radiation (mode 1 mean, 2 quantum) is applied once, after the kick, for
-// elements with L_rad > 0, using the field kick (Re b, Im b) only.  Without
-// radiation, elements with no constant term, and bends whose curvature equals
-// their dipole field, add the last Horner step straight into px, py.
+// elements with L_rad > 0, from the field kick b only.
 template <class T>
 static inline void multipole(Part<T>& p, const MultConst& m, int rad_mode, const RefConst& rc,
                              uint64_t seed, int turn, int elem) {
-  const bool radiates = rad_mode != 0 && m.lrad > 0.0;
-  if (!radiates && (m.pure || m.bend)) {
-    // Folded form: with (ar, ai) the Horner value after the linear-term step,
-    // Re b = ar x - ai y + knl0, Im b = ar y + ai x + ksl0; the constant terms
-    // vanish (pure) or combine with the curvature term as
-    // -knl0 + hxl (1+delta) = hxl delta (bend, hxl == knl0).
-    T pxv = m.bend ? FMA(m.hxl, p.delta, p.px) : p.px;
-    if (m.N >= 1) {
-      T ar = mkv<T>(m.c[m.N]);
-      T ai = mkv<T>(m.s[m.N]);
-      for (int n = m.N - 1; n >= 1; n--) {
-        T nr = FMA(ar, p.x, FMA(-ai, p.y, mkv<T>(m.c[n])));
-        T ni = FMA(ar, p.y, FMA(ai, p.x, mkv<T>(m.s[n])));
-        ar = nr; ai = ni;
-      }
-      pxv = FMA(-ar, p.x, FMA(ai, p.y, pxv));
-      p.py = FMA(ar, p.y, FMA(ai, p.x, p.py));
-    }
-    p.px = pxv;
-    if (m.bend) {
-      p.px = FMA(-m.k0h, p.x, p.px);
-      p.zeta = FMA(-(m.hxl * p.rv0v), p.x, p.zeta);
-    }
-    return;
-  }
-  T br = mkv<T>(m.c[m.N]);
-  T bi = mkv<T>(m.s[m.N]);
-  for (int n = m.N - 1; n >= 0; n--) {
-    T nr = FMA(br, p.x, FMA(-bi, p.y, mkv<T>(m.c[n])));
-    T ni = FMA(br, p.y, FMA(bi, p.x, mkv<T>(m.s[n])));
-    br = nr; bi = ni;
-  }
-  p.px = p.px - br;
-  p.py = p.py + bi;
+  T fr, fi;
+  multipole_field(p, m, &fr, &fi);
+  p.px = p.px - fr;
+  p.py = p.py + fi + m.s[0];
   if (m.hxl != 0.0) {
-    p.px = FMA(m.hxl, p.opd, p.px);
-    p.px = FMA(-m.k0h, p.x, p.px);
-    p.zeta = FMA(-(m.hxl * p.rv0v), p.x, p.zeta);
+    p.px = p.px + ((m.hxl - m.c[0]) + m.hxl * p.delta);
+    p.px = p.px - m.k0h * p.x;
+    p.zeta = p.zeta - m.hxl * p.x / p.rvv;
+  } else {
+    p.px = p.px - m.c[0];
   }
-  if (rad_mode == 1 && m.lrad > 0.0) {
+  if (rad_mode == 0 || !(m.lrad > 0.0)) return;
+  const T br = fr + m.c[0], bi = fi + m.s[0];
+  if (rad_mode == 1) {
     // Mean model: dE = -(2/3) r_c m0 c^2 beta^3 gamma^4 h^2 L_rad with the local
-    // curvature h = |field kick| / ((1+delta) L_rad).
-    T kk = FMA(br, br, bi * bi);
-    T h2 = (kk * m.ilr2) * (p.rpp * p.rpp);
-    T gam = FMA(rc.bg0, p.ptau, mkv<T>(rc.gamma0));
-    T bet = rc.beta0 * p.rvv;
-    T b3 = bet * bet * bet;
-    T g2 = gam * gam;
-    T g4 = g2 * g2;
-    T dpt = (-m.crl) * b3 * g4 * h2;
+    // curvature h = |b| / ((1+delta) L_rad).
+    const T h = SQRT(br * br + bi * bi) / (m.lrad * (1.0 + p.delta));
+    const T gam = rc.gamma0 + rc.bg0 * p.ptau;
+    const T bet = rc.beta0 * p.rvv;
+    const T dpt = -(rc.crad * m.lrad) * (bet * bet * bet) * (gam * gam * gam * gam) * (h * h);
     apply_energy_loss(p, dpt, rc);
-  } else if (rad_mode == 2 && m.lrad > 0.0) {
+  } else {
     quantum_kick(p, br, bi, m, rc, seed, turn, elem);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Entire functions of z (either sign) with a = sqrt|z|: C = cos a,
+// S = sin(a)/a, S2 = (1 - cos a)/z, S3 = (1 - S)/z for z > 0, and cosh a,
+// sinh(a)/a, (1 - cosh a)/z, (1 - S)/z for z < 0.  For |z| < 1/2 their Taylor
+// series C = sum (-z)^k/(2k)!, S = sum (-z)^k/(2k+1)!, S2 = sum (-z)^k/(2k+2)!,
+// S3 = sum (-z)^k/(2k+3)! to k = 12 (truncation below 1e-28); otherwise the
+// closed forms with 1 - cos a = 2 sin^2(a/2) and cosh a - 1 = 2 sinh^2(a/2).
+static const std::vector<double>& inv_fact() {
+  static std::vector<double> c = [] {
+    std::vector<double> v(32);
+    double f = 1.0;
+    for (int n = 0; n < 32; n++) {
+      if (n > 0) f = f * (double)n;
+      v[n] = 1.0 / f;
+    }
+    return v;
+  }();
+  return c;
+}
+template <class T>
+static inline void osc_funcs(const T& z, T* C, T* S, T* S2, T* S3) {
+  if (std::fabs(val(z)) < 0.5) {
+    const std::vector<double>& f = inv_fact();
+    const T mz = -z;
+    T c = mkv<T>(f[24]), s = mkv<T>(f[25]), s2 = mkv<T>(f[26]), s3 = mkv<T>(f[27]);
+    for (int k = 11; k >= 0; k--) {
+      c = c * mz + f[2 * k];
+      s = s * mz + f[2 * k + 1];
+      s2 = s2 * mz + f[2 * k + 2];
+      s3 = s3 * mz + f[2 * k + 3];
+    }
+    *C = c; *S = s; *S2 = s2; *S3 = s3;
+    return;
+  }
+  if (val(z) > 0.0) {
+    const T a = SQRT(z);
+    const T sh = SIN(0.5 * a);
+    *C = COS(a);
+    *S = SIN(a) / a;
+    *S2 = 2.0 * sh * sh / z;
+  } else {
+    const T a = SQRT(-z);
+    const T e = EXP(a), ei = EXP(-a);
+    const T eh = EXP(0.5 * a), ehi = EXP(-0.5 * a);
+    const T sh = 0.5 * (eh - ehi);  // sinh(a/2)
+    *C = 0.5 * (e + ei);
+    *S = (0.5 * (e - ei)) / a;
+    *S2 = 2.0 * sh * sh / (-z);
+  }
+  *S3 = (1.0 - *S) / z;
+}
+
+// Thick quadrupole: the exact flow over L of the expanded Hamiltonian
+// H = pzeta - (1+delta) + (px^2 + py^2) / (2 (1+delta)) + k1 (x^2 - y^2) / 2
+// (section "Lattice modelling and single particle tracking" names thick
+// quadrupoles).  With w^2 = |k1|/(1+delta) the focusing plane (x for k1 >= 0)
+// has u = u0 cos(ws) + pu0 sin(ws)/(w (1+delta)), pu = (1+delta) u', the other
+// the same with cosh and sinh; and zeta' = 1 - (1/rvv)(1 + (px^2 + py^2)/(2 (1+delta)^2)).
+// Over the body, int cos^2 = (L/2)(1 + C Sa), int sin^2 = (L/2)(1 - C Sa) and
+// int sin cos = w L^2 Sa^2 / 2 with C = cos(wL), Sa = sin(wL)/(wL) (the
+// hyperbolic ones alike), which gives int (px^2 + py^2) ds in closed form.
+// The sign of L is carried through: the map with -L is the inverse.
+template <class T>
+static inline void thick_quad(Part<T>& p, double k1, double L, const RefConst& rc) {
+  if (L == 0.0) return;
+  const T opd = 1.0 + p.delta;
+  const double ak1 = std::fabs(k1);
+  const T aK = ak1 / opd;  // w^2
+  const T z = aK * (L * L);
+  T C, Sa, Ch, Sha, u2, u3;
+  osc_funcs(z, &C, &Sa, &u2, &u3);
+  osc_funcs(-z, &Ch, &Sha, &u2, &u3);
+  T* u = (k1 >= 0.0) ? &p.x : &p.y;
+  T* pu = (k1 >= 0.0) ? &p.px : &p.py;
+  T* v = (k1 >= 0.0) ? &p.y : &p.x;
+  T* pv = (k1 >= 0.0) ? &p.py : &p.px;
+  const T u0 = *u, pu0 = *pu, v0 = *v, pv0 = *pv;
+  *u = C * u0 + (L * Sa / opd) * pu0;
+  *pu = C * pu0 - (aK * L * Sa) * opd * u0;
+  *v = Ch * v0 + (L * Sha / opd) * pv0;
+  *pv = Ch * pv0 + (aK * L * Sha) * opd * v0;
+  const T A2 = pu0 * pu0, B2 = opd * ak1 * (u0 * u0);     // pu0^2, (opd w u0)^2
+  const T Ah2 = pv0 * pv0, Bh2 = opd * ak1 * (v0 * v0);
+  const double hL = 0.5 * L;
+  const T I = hL * (1.0 + C * Sa) * A2 + hL * (1.0 - C * Sa) * B2 - opd * aK * (L * L) * (Sa * Sa) * (pu0 * u0)
+            + hL * (1.0 + Ch * Sha) * Ah2 + hL * (Ch * Sha - 1.0) * Bh2 + opd * aK * (L * L) * (Sha * Sha) * (pv0 * v0);
+  // 1 - 1/rvv = ((1+delta)^2 - ep^2) / ((1+delta)((1+delta) + ep)), ep = 1 + beta0 ptau
+  const T ep = 1.0 + rc.beta0 * p.ptau;
+  const T one_m_irvv = dsq_mom_energy(p, rc) / (opd * (opd + ep));
+  p.zeta = p.zeta + L * one_m_irvv - I / (2.0 * p.rvv * opd * opd);
+}
+
+// Dipole edge, non-linear model (section "Lattice modelling and single
+// particle tracking": edge effects as full non-linear maps).  A hard edge of
+// the field k0 whose face makes the angle e with the normal to the reference
+// orbit.  To first order in the field gradient, Maxwell's equations attach
+// B_s = y dB_y/ds and B_x = -tan(e) y dB_y/ds to it; across the edge they
+// kick py -= k0 y T with T = tan(e + s atan(px/pz)) (s = +1 at the entrance,
+// -1 at the exit), and the field missing from (or added to) the wedge between
+// the face and the normal plane gives px += k0 tan(e) x.  The map is the
+// canonical transformation of the type-2 generating function
+//   x X' + y Y' + zeta Z' + (k0/2) y^2 T(Px', Py', delta) - (k0/2) tan(e) x^2:
+// Py' = py - k0 y T(px, Py') is solved by fixed-point iteration until it no
+// longer changes, and X', Y', Z' = (x, y, zeta) + (k0/2) y^2 dT/d(px, py, pzeta) with
+//   dT/dpx = s (1+t^2)(pz^2 + px^2)/(pz D^2), dT/dpy = s (1+t^2) px py/(pz D^2),
+//   dT/dpzeta = -s (1+t^2) px (1+delta)/(pz D^2 rvv), D = pz - s t px, t = tan(e),
+// and the wedge kick after it at the entrance, before it at the exit.  The
+// finite extent of the fringe (fint, hgap) enters as in the linear model: a
+// further py += (h tan(e) - h tan(e - psi)) y, so that the linearisation at
+// the origin is the linear edge.  Lost with code -2 if pz is not real.
+template <class T>
+static inline void edge_nonlinear(Part<T>& p, double k0, double t, double sgn, double r21, double corr,
+                                  int turn, int elem) {
+  if (sgn < 0.0) p.px = p.px + r21 * p.x;
+  const T px = p.px, y = p.y, py = p.py;
+  const T opd = 1.0 + p.delta;
+  const T base = opd * opd - px * px;  // pz^2 + py^2
+  if (!(val(base - py * py) > 0.0)) { mark_lost(p, -2, turn, elem); return; }
+  const T ky = k0 * y;
+  T pyn = py;
+  for (int k = 0; k < 60; k++) {
+    const T pz2 = base - pyn * pyn;
+    if (!(val(pz2) > 0.0)) { mark_lost(p, -2, turn, elem); return; }
+    const T pz = SQRT(pz2);
+    const T Tv = (t * pz + sgn * px) / (pz - sgn * t * px);
+    const T nxt = py - ky * Tv;
+    const bool same = val(nxt) == val(pyn);
+    pyn = nxt;
+    if (same && k >= 3) break;
+  }
+  const T pz2 = base - pyn * pyn;
+  if (!(val(pz2) > 0.0)) { mark_lost(p, -2, turn, elem); return; }
+  const T pz = SQRT(pz2);
+  const T D = pz - sgn * t * px;
+  const T c = (sgn * (1.0 + t * t)) / (pz * D * D);
+  const T g = 0.5 * k0 * (y * y) * c;
+  p.x = p.x + g * (pz * pz + px * px);
+  p.y = p.y + g * (px * pyn);
+  p.zeta = p.zeta - g * px * opd / p.rvv;
+  p.py = pyn + corr * p.y;
+  if (sgn > 0.0) p.px = p.px + r21 * p.x;
+}
+
+// asin(u)/u for |u| <= 1: the series sum_n (2n)!/(4^n n!^2 (2n+1)) u^(2n)
+// below |u| = 0.1 (to n = 12), asin(u)/u above.
+template <class T>
+static inline T asin_over(const T& u) {
+  if (std::fabs(val(u)) >= 0.1) return ASIN(u) / u;
+  const T z = u * u;
+  std::vector<double> a(13);
+  double tn = 1.0;
+  for (int n = 0; n < 13; n++) {
+    if (n > 0) tn = tn * (double)(2 * n - 1) / (double)(2 * n);
+    a[n] = tn / (double)(2 * n + 1);
+  }
+  T s = mkv<T>(a[12]);
+  for (int n = 11; n >= 0; n--) s = s * z + a[n];
+  return s;
+}
+
+// Thick bend, expanded model (section "Lattice modelling and single particle
+// tracking": the model for large machines and small bending angles): the
+// exact flow of
+//   (px^2 + py^2) / (2 (1+delta)) - h x (1+delta) + k0 (x + h x^2 / 2) + k1 (x^2 - y^2) / 2,
+// the Hamiltonian in the frame of curvature h with its square root expanded
+// to second order in px, py and the factor (1 + h x) kept on the leading term
+// only.  x is a driven oscillator, px' = F - Kx x with F = h (1+delta) - k0
+// (evaluated as (h - k0) + h delta) and Kx = k0 h + k1; y has py' = k1 y; so
+// with z = K L^2 / (1+delta) and the functions of osc_funcs,
+//   x = C x0 + (L S/(1+delta)) px0 + (L^2 S2/(1+delta)) F,  px = C px0 + L S (F - Kx x0),
+// and zeta' = 1 - (1/rvv)(1 + h x + (px^2 + py^2)/(2 (1+delta)^2)) integrates with
+//   int x = L S x0 + (L^2 S2/(1+delta)) px0 + (L^3 S3/(1+delta)) F,
+//   int px^2 = (L/2)(1 + C S) px0^2 + L^2 S^2 px0 G + (L^3/2) ((1 - C S)/z) G^2,
+// G = F - Kx x0, where (1 - C S)/z = (2a - sin 2a)/(2 a^3) = 4 S3(4z).
+// The sign of L is carried through (-L inverts).
+template <class T>
+static inline void bend_expanded(Part<T>& p, double k0, double h, double L, double k1, const RefConst& rc) {
+  const T opd = 1.0 + p.delta;
+  const double Kx = k0 * h + k1, L2 = L * L;
+  const T zx = Kx * L2 / opd;
+  const T zy = (-k1) * L2 / opd;
+  T C, S, S2, S3, Cy, Sy, S2y, S3y, t0, t1, t2, Q, Qy;
+  osc_funcs(zx, &C, &S, &S2, &S3);
+  osc_funcs(zy, &Cy, &Sy, &S2y, &S3y);
+  osc_funcs(4.0 * zx, &t0, &t1, &t2, &Q);
+  osc_funcs(4.0 * zy, &t0, &t1, &t2, &Qy);
+  Q = 4.0 * Q;
+  Qy = 4.0 * Qy;
+  const T x0 = p.x, px0 = p.px, y0 = p.y, py0 = p.py;
+  const T F = (h - k0) + h * p.delta;
+  const T G = F - Kx * x0;
+  const T Gy = k1 * y0;
+  p.x = C * x0 + (L * S / opd) * px0 + (L2 * S2 / opd) * F;
+  p.px = C * px0 + L * S * G;
+  p.y = Cy * y0 + (L * Sy / opd) * py0;
+  p.py = Cy * py0 + L * Sy * Gy;
+  const T Ix = L * S * x0 + (L2 * S2 / opd) * px0 + (L2 * L * S3 / opd) * F;
+  const T Ipx = 0.5 * L * (1.0 + C * S) * (px0 * px0) + L2 * (S * S) * (px0 * G) + 0.5 * L2 * L * Q * (G * G);
+  const T Ipy = 0.5 * L * (1.0 + Cy * Sy) * (py0 * py0) + L2 * (Sy * Sy) * (py0 * Gy) + 0.5 * L2 * L * Qy * (Gy * Gy);
+  const T ep = 1.0 + rc.beta0 * p.ptau;
+  const T one_m_irvv = dsq_mom_energy(p, rc) / (opd * (opd + ep));
+  p.zeta = p.zeta + L * one_m_irvv - (h * Ix + (Ipx + Ipy) / (2.0 * opd * opd)) / p.rvv;
+}
+
+// Thick bend, full model (section "Lattice modelling and single particle
+// tracking": the model for small machines): the exact motion in a uniform
+// vertical field k0 = B / (B rho) through a sector of curvature h and
+// reference length L.  In the horizontal plane the particle runs on a circle
+// of radius p_h / k0, p_h^2 = (1+delta)^2 - py^2, along which pX + k0 Z and
+// pZ - k0 X are constant (X, Z laboratory coordinates about the sector's
+// centre, X along the entrance x axis).  At the exit plane, turned by
+// theta = h L, this gives
+//   px' = B - k0 (1/h + x) sin(theta),   B = px cos + pz sin,  Q = pz cos - px sin,
+//   x'  = x cos - (1 - cos)/h + (1/h + x) sin (px' + B) / (pz' + Q),
+// with sin/h = L S, (1 - cos)/h = h L^2 S2 (functions of z = theta^2), so that
+// h = 0 is the straight dipole.  The arc length in the horizontal plane is
+// l_h = chord asin(u)/u, u = k0 chord / (2 p_h), with
+// chord^2 = (x' - x)^2 + (1 + h x)(1 + h x') 2 L^2 S2; then y += py l_h / p_h
+// and zeta += L - (1/rvv)(1+delta) l_h / p_h.  The sign of L is carried
+// through (-L inverts).  Lost with code -2 if pz or pz' is not real or the
+// particle cannot reach the exit plane.
+template <class T>
+static inline void bend_full(Part<T>& p, double k0, double h, double L, const RefConst& rc, int turn, int elem) {
+  const double th = h * L, L2 = L * L;
+  double C, S, S2, S3;
+  osc_funcs(th * th, &C, &S, &S2, &S3);
+  const double sn = th * S, Sh = L * S, Ch = h * L2 * S2, D2 = 2.0 * L2 * S2;
+  const T opd = 1.0 + p.delta;
+  const T pz2 = opd * opd - p.px * p.px - p.py * p.py;
+  if (!(val(pz2) > 0.0 && val(pz2) < INFINITY)) { mark_lost(p, -2, turn, elem); return; }
+  const T pz = SQRT(pz2);
+  const T ph2 = opd * opd - p.py * p.py;
+  const T B = p.px * C + pz * sn;
+  const T Q = pz * C - p.px * sn;
+  const T r0s = p.x * sn + Sh;     // (1/h + x) sin(theta)
+  const T A = B - k0 * r0s;        // px at the exit plane
+  const T pzf2 = ph2 - A * A;
+  if (!(val(pzf2) > 0.0)) { mark_lost(p, -2, turn, elem); return; }
+  const T pzf = SQRT(pzf2);
+  const T den = pzf + Q;
+  if (!(val(den) > 0.0)) { mark_lost(p, -2, turn, elem); return; }
+  const T xf = p.x * C - Ch + r0s * ((A + B) / den);
+  const T dxf = xf - p.x;
+  const T chord = SQRT(dxf * dxf + (1.0 + h * p.x) * (1.0 + h * xf) * D2);
+  const T ph = SQRT(ph2);
+  const T uu = k0 * chord / (2.0 * ph);
+  if (!(std::fabs(val(uu)) <= 1.0)) { mark_lost(p, -2, turn, elem); return; }
+  const T lh = ((L >= 0.0) ? chord : -chord) * asin_over(uu);
+  const T lr = lh / ph;
+  const T ep = 1.0 + rc.beta0 * p.ptau;
+  p.x = xf;
+  p.px = A;
+  p.y = p.y + p.py * lr;
+  p.zeta = p.zeta + (L - ep * lr);
 }
 
 // Prepared element: host constants of each type.
@@ -715,36 +739,12 @@ struct Prep {
   double cs, sn;                         // reference-frame rotation about s
   double xmin, xmax, ymin, ymax;         // rectangular aperture
   double ia2, ib2;                       // elliptic aperture: 1/a^2, 1/b^2
-  BBConst bb;                            // 4D beam-beam lens; frozen space charge (shape and K)
-  double sc_i2sz2;                       // frozen space charge: 1/(2 sigma_z^2), 0 for a coasting beam
+  double lK, lxc, lyc, lsx, lsy;         // lens: kick strength, centre, rms sizes
+  double sc_sz;                          // frozen space charge: sigma_z, 0 for a coasting beam
   double k1, Lq;                         // thick quadrupole
   double bk0, bh, bL, bk1;               // thick bend: field, curvature, length, gradient
   int bfull;                             // thick bend: 1 = full model, 0 = expanded
 };
-
-// Field-shape constants of a bi-Gaussian line charge with sigma_x, sigma_y
-// (gauss_field): round when the two squares agree to 1e-10, else the
-// Bassetti-Erskine constants with sigma_1 the larger.
-static void gauss_shape(BBConst& b, double sx, double sy) {
-  const double sx2 = sx * sx, sy2 = sy * sy;
-  if (std::fabs(sx2 - sy2) <= 1e-10 * (sx2 + sy2)) {
-    b.mode = 0;
-    b.h1 = 1.0 / (sx2 + sy2);
-  } else {
-    const bool flat = sx2 > sy2;
-    const double s1 = flat ? sx : sy, s2 = flat ? sy : sx;
-    b.mode = flat ? 1 : 2;
-    const double S = std::sqrt(2.0 * (s1 * s1 - s2 * s2));
-    b.h1 = 1.0 / (2.0 * (s1 * s1));
-    b.h2 = 1.0 / (2.0 * (s2 * s2));
-    b.rs = s2 / s1;
-    b.rsi = s1 / s2;
-    b.invS = 1.0 / S;
-    b.cpre = 1.772453850905516 / S;
-    b.lin1 = 1.0 / (s1 * (s1 + s2));
-    b.lin2 = 1.0 / (s2 * (s1 + s2));
-  }
-}
 
 static Prep prepare(const Element& e, const RefConst& rc) {
   Prep q;
@@ -763,11 +763,6 @@ static Prep prepare(const Element& e, const RefConst& rc) {
       q.m.hxl = e.p[22];
       q.m.lrad = e.p[23];
       q.m.k0h = (q.m.lrad > 0.0) ? (e.p[0] * q.m.hxl) / q.m.lrad : 0.0;
-      q.m.ilr2 = (q.m.lrad > 0.0) ? 1.0 / (q.m.lrad * q.m.lrad) : 0.0;
-      q.m.crl = rc.crad * q.m.lrad;
-      q.m.kql = rc.kq * q.m.lrad;
-      q.m.pure = (e.p[0] == 0.0 && e.p[11] == 0.0 && q.m.hxl == 0.0);
-      q.m.bend = (q.m.hxl != 0.0 && q.m.hxl == e.p[0] && e.p[11] == 0.0);
       break;
     }
     case T_CAVITY: {
@@ -791,12 +786,12 @@ static Prep prepare(const Element& e, const RefConst& rc) {
     }
     case T_LINEARMAP: {
       // The table gives M, d on (x,px,y,py,zeta,pzeta), pzeta = ptau/beta0;
-      // convert to (..., ptau): row 5 times beta0, column 5 divided by beta0.
+      // in (..., ptau) row 5 is multiplied by beta0 and column 5 divided by it.
       for (int i = 0; i < 6; i++) {
         for (int j = 0; j < 6; j++) {
           double v = e.p[6 * i + j];
           if (i == 5 && j != 5) v = v * rc.beta0;
-          else if (j == 5 && i != 5) v = v * rc.ib0;
+          else if (j == 5 && i != 5) v = v / rc.beta0;
           q.M[6 * i + j] = v;
         }
         q.d[i] = (i == 5) ? e.p[36 + i] * rc.beta0 : e.p[36 + i];
@@ -815,11 +810,9 @@ static Prep prepare(const Element& e, const RefConst& rc) {
       // Delta p_perp / P0 = 2 q0 q_s N_s (r_e m_e c^2 / p0 c) (1 + beta0 beta_s) /
       // (beta0 + beta_s) f(x - x_c, y - y_c)
       const double qN = e.p[0], bs = e.p[1];
-      BBConst& b = q.bb;
-      b.K = 2.0 * rc.q0 * qN * (R_ELECTRON * M_ELECTRON) / rc.p0c * ((1.0 + rc.beta0 * bs) / (rc.beta0 + bs));
-      b.xc = e.p[4];
-      b.yc = e.p[5];
-      gauss_shape(b, e.p[2], e.p[3]);
+      q.lK = 2.0 * rc.q0 * qN * (R_ELECTRON * M_ELECTRON) / rc.p0c * ((1.0 + rc.beta0 * bs) / (rc.beta0 + bs));
+      q.lsx = e.p[2]; q.lsy = e.p[3];
+      q.lxc = e.p[4]; q.lyc = e.p[5];
       break;
     }
     case T_SPACECHARGE: {
@@ -829,14 +822,12 @@ static Prep prepare(const Element& e, const RefConst& rc) {
       // the lumped element stands for:
       // Delta p_perp / P0 = 2 r_c lambda0 L / (beta0^2 gamma0^3) g(zeta) f(x - x_c, y - y_c),
       // r_c = q0^2 r_e m_e / m0, g = exp(-zeta^2 / (2 sigma_z^2)) (1 when sigma_z = 0)
-      const double lam0 = e.p[0], sz = e.p[1], L = e.p[4];
+      const double lam0 = e.p[0], L = e.p[4];
       const double rcl = rc.q0 * rc.q0 * R_ELECTRON * M_ELECTRON / rc.m0;
-      BBConst& b = q.bb;
-      b.K = 2.0 * rcl * lam0 * L / (rc.beta0 * rc.beta0 * rc.gamma0 * rc.gamma0 * rc.gamma0);
-      b.xc = e.p[5];
-      b.yc = e.p[6];
-      gauss_shape(b, e.p[2], e.p[3]);
-      q.sc_i2sz2 = (sz > 0.0) ? 1.0 / (2.0 * (sz * sz)) : 0.0;
+      q.lK = 2.0 * rcl * lam0 * L / (rc.beta0 * rc.beta0 * rc.gamma0 * rc.gamma0 * rc.gamma0);
+      q.lsx = e.p[2]; q.lsy = e.p[3];
+      q.lxc = e.p[5]; q.lyc = e.p[6];
+      q.sc_sz = e.p[1];
       break;
     }
     default: break;
@@ -844,17 +835,27 @@ static Prep prepare(const Element& e, const RefConst& rc) {
   return q;
 }
 
+// Kick of a lens row (4D beam-beam or frozen space charge) at the particle.
+static inline void lens_kick(const Prep& q, double x, double y, double zeta, double* kx, double* ky) {
+  double fx, fy;
+  gauss_field(x - q.lxc, y - q.lyc, q.lsx, q.lsy, &fx, &fy);
+  double K = q.lK;
+  if (q.type == T_SPACECHARGE && q.sc_sz > 0.0) K = K * std::exp(-(zeta * zeta) / (2.0 * q.sc_sz * q.sc_sz));
+  *kx = K * fx;
+  *ky = K * fy;
+}
+
 // One element.  Returns with p.state != 1 if the particle was lost here.
 template <class T>
 static inline void track_element(Part<T>& p, const Prep& q, int rad_mode, const RefConst& rc,
                                  uint64_t seed, int turn, int elem) {
   switch (q.type) {
-    case T_DRIFT: drift(p, q.L, turn, elem); break;
+    case T_DRIFT: drift(p, q.L, rc, turn, elem); break;
     case T_MULTIPOLE: multipole(p, q.m, rad_mode, rc, seed, turn, elem); break;
     case T_CAVITY: {
       // Thin RF: phase lag - k zeta, k = 2 pi f/(beta0 c); energy gain q0 V sin(phase).
-      T phi = FMA(-q.krf, p.zeta, mkv<T>(q.lagr));
-      p.ptau = FMA(q.qv, SIN(phi), p.ptau);
+      const T phi = q.lagr - q.krf * p.zeta;
+      p.ptau = p.ptau + q.qv * SIN(phi);
       energy_update(p, rc);
       break;
     }
@@ -862,16 +863,16 @@ static inline void track_element(Part<T>& p, const Prep& q, int rad_mode, const 
       if (q.enl) {
         edge_nonlinear(p, q.ek0, q.et, q.esg, q.r21, q.ecorr, turn, elem);
       } else {
-        p.px = FMA(q.r21, p.x, p.px);
-        p.py = FMA(q.r43, p.y, p.py);
+        p.px = p.px + q.r21 * p.x;
+        p.py = p.py + q.r43 * p.y;
       }
       break;
     case T_LINEARMAP: {
-      T v[6] = {p.x, p.px, p.y, p.py, p.zeta, p.ptau};
+      const T v[6] = {p.x, p.px, p.y, p.py, p.zeta, p.ptau};
       T o[6];
       for (int i = 0; i < 6; i++) {
         T acc = mkv<T>(q.d[i]);
-        for (int j = 0; j < 6; j++) acc = FMA(q.M[6 * i + j], v[j], acc);
+        for (int j = 0; j < 6; j++) acc = acc + q.M[6 * i + j] * v[j];
         o[i] = acc;
       }
       p.x = o[0]; p.px = o[1]; p.y = o[2]; p.py = o[3]; p.zeta = o[4]; p.ptau = o[5];
@@ -881,9 +882,9 @@ static inline void track_element(Part<T>& p, const Prep& q, int rad_mode, const 
     case T_APERTURE: {
       // Circular aperture: lost if x^2 + y^2 > r^2 (a point on the circle
       // survives) or if x or y is not finite.
-      T rr = FMA(p.x, p.x, p.y * p.y);
-      if (!(val(rr) <= q.r2)) {
-        bool fin = std::isfinite(val(p.x)) && std::isfinite(val(p.y));
+      const double x = val(p.x), y = val(p.y);
+      if (!(x * x + y * y <= q.r2)) {
+        const bool fin = std::isfinite(x) && std::isfinite(y);
         mark_lost(p, fin ? 0 : -1, turn, elem);
       }
       break;
@@ -898,35 +899,26 @@ static inline void track_element(Part<T>& p, const Prep& q, int rad_mode, const 
       break;
     case T_SROTATION: {
       const T x = p.x, y = p.y, px = p.px, py = p.py;
-      p.x = FMA(q.cs, x, q.sn * y);
-      p.y = FMA(q.cs, y, -(q.sn * x));
-      p.px = FMA(q.cs, px, q.sn * py);
-      p.py = FMA(q.cs, py, -(q.sn * px));
+      p.x = q.cs * x + q.sn * y;
+      p.y = q.cs * y - q.sn * x;
+      p.px = q.cs * px + q.sn * py;
+      p.py = q.cs * py - q.sn * px;
       break;
     }
-    case T_QUAD: thick_quad(p, q.k1, q.Lq); break;
+    case T_QUAD: thick_quad(p, q.k1, q.Lq, rc); break;
     case T_BEND:
-      if (q.bfull) bend_full(p, q.bk0, q.bh, q.bL, turn, elem);
-      else bend_expanded(p, q.bk0, q.bh, q.bL, q.bk1);
+      if (q.bfull) bend_full(p, q.bk0, q.bh, q.bL, rc, turn, elem);
+      else bend_expanded(p, q.bk0, q.bh, q.bL, q.bk1, rc);
       break;
-    // 4D weak-strong beam-beam (section "Beam-beam interactions"): transverse
-    // kick of a frozen Gaussian bunch, independent of the longitudinal
-    // coordinates.  Values only (the Jacobian entry points reject this type).
-    case T_BEAMBEAM4D: {
-      double fx, fy;
-      gauss_field(val(p.x) - q.bb.xc, val(p.y) - q.bb.yc, q.bb, &fx, &fy);
-      p.px = FMA(q.bb.K, fx, p.px);
-      p.py = FMA(q.bb.K, fy, p.py);
-      break;
-    }
-    case T_SPACECHARGE: {  // values only, like the beam-beam lens
-      double fx, fy;
-      gauss_field(val(p.x) - q.bb.xc, val(p.y) - q.bb.yc, q.bb, &fx, &fy);
-      const double zt = val(p.zeta);
-      const double g = (q.sc_i2sz2 > 0.0) ? exp_cw(-((zt * zt) * q.sc_i2sz2)) : 1.0;
-      const double Kg = q.bb.K * g;
-      p.px = FMA(Kg, fx, p.px);
-      p.py = FMA(Kg, fy, p.py);
+    // 4D weak-strong beam-beam (section "Beam-beam interactions") and frozen
+    // space charge (section "Space charge"): transverse kicks of a frozen
+    // Gaussian charge.  Values only (the Jacobian entry points reject them).
+    case T_BEAMBEAM4D:
+    case T_SPACECHARGE: {
+      double kx, ky;
+      lens_kick(q, val(p.x), val(p.y), val(p.zeta), &kx, &ky);
+      p.px = p.px + kx;
+      p.py = p.py + ky;
       break;
     }
     // Rectangular aperture: lost unless xmin <= x <= xmax and ymin <= y <= ymax
@@ -934,18 +926,16 @@ static inline void track_element(Part<T>& p, const Prep& q, int rad_mode, const 
     case T_APERTURE_RECT: {
       const double x = val(p.x), y = val(p.y);
       if (!(x >= q.xmin && x <= q.xmax && y >= q.ymin && y <= q.ymax)) {
-        bool fin = std::isfinite(x) && std::isfinite(y);
+        const bool fin = std::isfinite(x) && std::isfinite(y);
         mark_lost(p, fin ? 0 : -1, turn, elem);
       }
       break;
     }
-    // Elliptic aperture with semi-axes a, b: lost if (x/a)^2 + (y/b)^2 > 1,
-    // evaluated as x^2 (1/a^2) + y^2 (1/b^2).
+    // Elliptic aperture with semi-axes a, b: lost if (x/a)^2 + (y/b)^2 > 1.
     case T_APERTURE_ELLIPSE: {
       const double x = val(p.x), y = val(p.y);
-      const double t = std::fma(x * x, q.ia2, (y * y) * q.ib2);
-      if (!(t <= 1.0)) {
-        bool fin = std::isfinite(x) && std::isfinite(y);
+      if (!(x * x * q.ia2 + y * y * q.ib2 <= 1.0)) {
+        const bool fin = std::isfinite(x) && std::isfinite(y);
         mark_lost(p, fin ? 0 : -1, turn, elem);
       }
       break;
@@ -959,261 +949,6 @@ static inline void track_element(Part<T>& p, const Prep& q, int rad_mode, const 
 template <class T>
 static inline void turn_guard(Part<T>& p, int turn, int n_el) {
   if (!(std::fabs(val(p.x)) <= 1.0 && std::fabs(val(p.y)) <= 1.0)) mark_lost(p, -3, turn, n_el - 1);
-}
-
-
-// ---------------------------------------------------------------------------
-// Thick quadrupole: the exact flow over L of the expanded Hamiltonian
-// H = pzeta - (1+delta) + (px^2 + py^2) / (2 (1+delta)) + k1 (x^2 - y^2) / 2
-// (the paraxial form of the drift's square root plus the quadrupole field;
-// section "Lattice modelling and single particle tracking" names thick
-// quadrupoles).  Transverse motion is harmonic with w^2 = |k1| / (1+delta):
-// cos/sin in the focusing plane, cosh/sinh in the other; zeta gains
-// dzeta/ds = 1 - (1/rvv)(1 + (px^2 + py^2) / (2 (1+delta)^2)) integrated in
-// closed form.  cos a, sin(a)/a, cosh a and sinh(a)/a at a = w |L| are the
-// oscillator functions (osc_funcs) at z = |k1| L^2 / (1+delta) and -z; the
-// sign of L is carried through, so that the same map with -L is its inverse.
-template <class T>
-static inline void osc_funcs(const T& z, T* C, T* S, T* S2, T* S3);
-template <class T>
-static inline void thick_quad(Part<T>& p, double k1, double L) {
-  if (L == 0.0) return;
-  const T aK = (k1 >= 0.0) ? k1 * p.rpp : (-k1) * p.rpp;  // |k1| / (1+delta)
-  const T z = aK * (L * L);
-  T C, Sa, Ch, Sha, u2, u3;
-  osc_funcs(z, &C, &Sa, &u2, &u3);     // cos a, sin(a)/a
-  osc_funcs(-z, &Ch, &Sha, &u2, &u3);  // cosh a, sinh(a)/a
-  T* u = (k1 >= 0.0) ? &p.x : &p.y;   // focusing plane
-  T* pu = (k1 >= 0.0) ? &p.px : &p.py;
-  T* v = (k1 >= 0.0) ? &p.y : &p.x;
-  T* pv = (k1 >= 0.0) ? &p.py : &p.px;
-  const T u0 = *u, pu0 = *pu, v0 = *v, pv0 = *pv;
-  const T g = (aK * L) * Sa;    // w sin(w L)
-  const T gh = (aK * L) * Sha;  // w sinh(w L)
-  *u = FMA(C, u0, ((L * Sa) * p.rpp) * pu0);
-  *pu = FMA(-(g * p.opd), u0, C * pu0);
-  *v = FMA(Ch, v0, ((L * Sha) * p.rpp) * pv0);
-  *pv = FMA(gh * p.opd, v0, Ch * pv0);
-  // I = integral over the element of px^2 + py^2
-  const T o2 = p.opd * p.opd;
-  const T A2 = pu0 * pu0, B2 = (aK * o2) * (u0 * u0);
-  const T Ah2 = pv0 * pv0, Bh2 = (aK * o2) * (v0 * v0);
-  const double hL = 0.5 * L;
-  T I = hL * (A2 + B2);
-  I = FMA(hL * (Sa * C), A2 - B2, I);
-  I = FMA(-((p.opd * L) * (Sa * g)), pu0 * u0, I);
-  I = FMA(mkv<T>(hL), Ah2 - Bh2, I);
-  I = FMA(hL * (Sha * Ch), Ah2 + Bh2, I);
-  I = FMA((p.opd * L) * (Sha * gh), pv0 * v0, I);
-  // L (1 - 1/rvv) - I / (2 rvv (1+delta)^2), with 1 - 1/rvv = (delta - beta0 ptau) / (1+delta)
-  p.zeta = p.zeta + FMA(L * (p.delta - p.epm1), p.rpp, -(((0.5 * p.rv0v) * (p.rpp * p.rpp)) * I));
-}
-
-// Dipole edge, non-linear model (section "Lattice modelling and single
-// particle tracking": edge effects as full non-linear maps).  A hard edge of
-// the field k0 whose face makes the angle e with the normal to the reference
-// orbit; to first order in the field gradient the fields that Maxwell's
-// equations attach to the edge (B_s = y dB_y/ds, B_x = -tan(e) y dB_y/ds)
-// kick the particle by py -= k0 y T with T = tan(e + s atan(px/pz)) (s = +1
-// at the entrance, -1 at the exit: the angle between the trajectory and the
-// face normal), and the field missing from (or added to) the wedge between
-// the face and the normal plane gives px += k0 tan(e) x.  The map is the
-// canonical transformation of the generating function
-//   x X' + y Y' + zeta Z' + (k0/2) y^2 T(px, py', delta) - (k0/2) tan(e) x^2
-// (fringe part: py' = py - k0 y T(px, py') solved by three fixed-point
-// steps; then x, y, zeta shifted by (k0/2) y^2 dT/d(px, py, pzeta)), with
-//   dT/dpx = s (1 + t^2)(pz^2 + px^2) / (pz D^2),  dT/dpy = s (1 + t^2) px py / (pz D^2),
-//   dT/ddelta = -s (1 + t^2) px (1+delta) / (pz D^2),  D = pz - s t px,  t = tan(e),
-// and the wedge kick after it at the entrance, before it at the exit.  The
-// finite extent of the fringe (fint, hgap) enters as in the linear model: a
-// further py += (h tan(e) - h tan(e - psi)) y, so that the linearisation at
-// the origin is the linear edge.  Lost with code -2 if pz is not real.
-template <class T>
-static inline void edge_nonlinear(Part<T>& p, double k0, double t, double sgn, double r21, double corr,
-                                  int turn, int elem) {
-  if (sgn < 0.0) p.px = FMA(r21, p.x, p.px);
-  const T px = p.px, y = p.y, py = p.py;
-  const T base = FMA(-px, px, p.dm1);  // (1+delta)^2 - 1 - px^2
-  if (!(val(FMA(-py, py, base)) > -1.0)) { mark_lost(p, -2, turn, elem); return; }
-  const T ky = k0 * y;
-  const double st = sgn * t;
-  T pyn = py;
-  for (int k = 0; k < 3; k++) {
-    const T pz = SQRT(1.0 + FMA(-pyn, pyn, base));
-    const T Tv = FMA(t, pz, sgn * px) / FMA(-st, px, pz);
-    pyn = FMA(-ky, Tv, py);
-  }
-  const T u = FMA(-pyn, pyn, base);
-  if (!(val(u) > -1.0)) { mark_lost(p, -2, turn, elem); return; }
-  const T pz = SQRT(1.0 + u);
-  const T D = FMA(-st, px, pz);
-  const T c = (sgn * (1.0 + t * t)) / (pz * (D * D));
-  const T g = ((0.5 * k0) * (y * y)) * c;
-  p.x = FMA(g, FMA(pz, pz, px * px), p.x);
-  p.y = FMA(g, px * pyn, p.y);
-  p.zeta = FMA(-(g * (px * p.opd)), p.rv0v, p.zeta);
-  p.py = FMA(corr, p.y, pyn);
-  if (sgn > 0.0) p.px = FMA(r21, p.x, p.px);
-}
-
-// Entire functions of z (either sign) with a = sqrt|z|: C = cos a,
-// S = sin(a)/a, S2 = (1 - C)/z, S3 = (1 - S)/z for z > 0 (cosh and sinh for
-// z < 0).  Series in z below |z| = 1 (each to z^9: truncation below 1e-21),
-// else from sin_cw/cos_cw or two exponentials.
-template <class T>
-static inline void osc_funcs(const T& z, T* C, T* S, T* S2, T* S3) {
-  const std::vector<double>& f = inv_fact();
-  if (std::fabs(val(z)) < 1.0) {
-    const T mz = -z;
-    T c = mkv<T>(f[18]), s = mkv<T>(f[19]), s2 = mkv<T>(f[20]), s3 = mkv<T>(f[21]);
-    for (int n = 8; n >= 0; n--) {
-      c = FMA(c, mz, mkv<T>(f[2 * n]));
-      s = FMA(s, mz, mkv<T>(f[2 * n + 1]));
-      s2 = FMA(s2, mz, mkv<T>(f[2 * n + 2]));
-      s3 = FMA(s3, mz, mkv<T>(f[2 * n + 3]));
-    }
-    *C = c; *S = s; *S2 = s2; *S3 = s3;
-    return;
-  }
-  if (val(z) > 0.0) {
-    const T a = SQRT(z);
-    *C = COS(a);
-    *S = SIN(a) / a;
-  } else {
-    const T a = SQRT(-z);
-    const T e = EXPC(a), ei = EXPC(-a);
-    *C = 0.5 * (e + ei);
-    *S = (0.5 * (e - ei)) / a;
-  }
-  *S2 = (1.0 - *C) / z;
-  *S3 = (1.0 - *S) / z;
-}
-
-// asin(v)/v = sum_n a_n v^(2n), a_n = (2n)! / (4^n n!^2 (2n+1)), n = 0..13
-// (a running product t_n = t_(n-1) (2n-1) / (2n), then a_n = t_n / (2n+1)).
-static const std::vector<double>& asin_coef() {
-  static std::vector<double> c = [] {
-    std::vector<double> v(14);
-    double t = 1.0;
-    for (int n = 0; n < 14; n++) {
-      if (n > 0) t = (t * (double)(2 * n - 1)) / (double)(2 * n);
-      v[n] = t / (double)(2 * n + 1);
-    }
-    return v;
-  }();
-  return c;
-}
-
-// asin(u)/u for |u| <= 1: the angle is halved, asin u = 2 asin v with
-// v = u / sqrt(2 (1 + sqrt(1 - u^2))), until |v| < 1/4 (at most three times),
-// then the series (truncation below 3e-18 there).
-template <class T>
-static inline T asin_over(const T& u) {
-  const std::vector<double>& a = asin_coef();
-  T v = u;
-  double m = 1.0;
-  for (int k = 0; k < 4 && std::fabs(val(v)) >= 0.25; k++) {
-    v = v / SQRT(2.0 * (1.0 + SQRT(1.0 - v * v)));
-    m = m + m;
-  }
-  const T z = v * v;
-  T s = mkv<T>(a[13]);
-  for (int n = 12; n >= 0; n--) s = FMA(s, z, mkv<T>(a[n]));
-  if (m == 1.0) return s;
-  return (m * (v / u)) * s;
-}
-
-// Thick bend, expanded model (section "Lattice modelling and single particle
-// tracking": the model for large machines and small bending angles): the
-// exact flow of
-//   (px^2 + py^2) / (2 (1+delta)) - h x (1+delta) + k0 (x + h x^2 / 2) + k1 (x^2 - y^2) / 2,
-// the Hamiltonian in the frame of curvature h with its square root expanded
-// to second order in px, py and the factor (1 + h x) kept on the leading term
-// only.  x is a driven oscillator, px' = F - Kx x with F = h (1+delta) - k0
-// and Kx = k0 h + k1; y has py' = k1 y; and
-//   zeta' = 1 - (1/rvv) (1 + h x + (px^2 + py^2) / (2 (1+delta)^2)),
-// integrated in closed form with the functions of osc_funcs at
-// z = K L^2 / (1+delta).  The sign of L is carried through (-L inverts).
-template <class T>
-static inline void bend_expanded(Part<T>& p, double k0, double h, double L, double k1) {
-  const double Kx = k0 * h + k1, L2 = L * L;
-  const T zx = (Kx * p.rpp) * L2;
-  const T zy = ((-k1) * p.rpp) * L2;
-  T C, S, S2, S3, Cy, Sy, S2y, S3y;
-  osc_funcs(zx, &C, &S, &S2, &S3);
-  osc_funcs(zy, &Cy, &Sy, &S2y, &S3y);
-  const T x0 = p.x, px0 = p.px, y0 = p.y, py0 = p.py;
-  const T F = FMA(h, p.delta, mkv<T>(h - k0));  // h (1+delta) - k0
-  const T G = FMA(-Kx, x0, F);                   // px' at the entrance
-  const T Gy = k1 * y0;
-  const T Lr = L * p.rpp;
-  p.x = FMA(C, x0, FMA(Lr * S, px0, ((L * Lr) * S2) * F));
-  p.px = FMA(C, px0, (L * S) * G);
-  p.y = FMA(Cy, y0, (Lr * Sy) * py0);
-  p.py = FMA(Cy, py0, (L * Sy) * Gy);
-  // integrals over the body of x and of px^2 + py^2, with px(s) = px0 c(s) + G s1(s):
-  // int c^2 = (L/2)(1 + C S), int c s1 = (L S)^2 / 2, int s1^2 = (L^3/2)(1 - C S)/z
-  // and (1 - C S)/z = S3 + S S2
-  const T Ix = FMA(L * S, x0, FMA((L * Lr) * S2, px0, ((L2 * Lr) * S3) * F));
-  const double hL = 0.5 * L, hL3 = 0.5 * (L2 * L);
-  T I = (hL * FMA(C, S, mkv<T>(1.0))) * (px0 * px0);
-  I = FMA(L2 * (S * S), px0 * G, I);
-  I = FMA(hL3 * FMA(S, S2, S3), G * G, I);
-  I = FMA(hL * FMA(Cy, Sy, mkv<T>(1.0)), py0 * py0, I);
-  I = FMA(L2 * (Sy * Sy), py0 * Gy, I);
-  I = FMA(hL3 * FMA(Sy, S2y, S3y), Gy * Gy, I);
-  // L (1 - 1/rvv) = L (delta - beta0 ptau) / (1+delta)
-  p.zeta = p.zeta + FMA(L * (p.delta - p.epm1), p.rpp, -(p.rv0v * FMA(h, Ix, (0.5 * (p.rpp * p.rpp)) * I)));
-}
-
-// Thick bend, full model (section "Lattice modelling and single particle
-// tracking": the model for small machines): the exact motion in a uniform
-// vertical field k0 = B / (B rho) through a sector of curvature h and
-// reference length L.  In the horizontal plane the particle runs on a circle
-// of radius p_h / k0, p_h^2 = (1+delta)^2 - py^2, along which pX + k0 Z and
-// pZ - k0 X are constant (X, Z laboratory coordinates about the sector's
-// centre, X along the entrance x axis).  At the exit plane, turned by
-// theta = h L, this gives
-//   px' = B - k0 (1/h + x) sin(theta),   B = px cos + pz sin,  Q = pz cos - px sin,
-//   x'  = x cos - (1 - cos)/h + (1/h + x) sin (px' + B) / (pz' + Q),
-// with sin/h = L S, (1 - cos)/h = h L^2 S2 (functions of z = theta^2), so that
-// h = 0 is the straight dipole.  The arc length in the horizontal plane is
-// l_h = chord asin(u)/u, u = k0 chord / (2 p_h), with
-// chord^2 = (x' - x)^2 + (1 + h x)(1 + h x') 2 L^2 S2; then y += py l_h / p_h
-// and zeta += L - (1/rvv)(1+delta) l_h / p_h.  The sign of L is carried
-// through (-L inverts).  Lost with code -2 if pz or pz' is not real or the
-// particle cannot reach the exit plane.
-template <class T>
-static inline void bend_full(Part<T>& p, double k0, double h, double L, int turn, int elem) {
-  const double th = h * L, L2 = L * L;
-  double C, S, S2, S3;
-  osc_funcs(th * th, &C, &S, &S2, &S3);
-  const double sn = th * S, Sh = L * S, Ch = (h * L2) * S2, D2 = 2.0 * (L2 * S2);
-  const T u = FMA(-p.px, p.px, FMA(-p.py, p.py, p.dm1));  // pz^2 - 1
-  if (!(val(u) > -1.0 && val(u) < INFINITY)) { mark_lost(p, -2, turn, elem); return; }
-  const T pz = SQRT(1.0 + u);
-  const T ph2 = 1.0 + FMA(-p.py, p.py, p.dm1);
-  const T B = FMA(p.px, C, pz * sn);
-  const T Q = FMA(pz, C, -(p.px * sn));
-  const T r0s = FMA(p.x, sn, Sh);          // (1/h + x) sin(theta)
-  const T A = FMA(-k0, r0s, B);            // px at the exit plane
-  const T pzf2 = FMA(-A, A, ph2);
-  if (!(val(pzf2) > 0.0)) { mark_lost(p, -2, turn, elem); return; }
-  const T pzf = SQRT(pzf2);
-  const T den = pzf + Q;
-  if (!(val(den) > 0.0)) { mark_lost(p, -2, turn, elem); return; }
-  const T xf = FMA(p.x, C, mkv<T>(-Ch)) + r0s * ((A + B) / den);
-  const T dxf = xf - p.x;
-  const T chord = SQRT(FMA(dxf, dxf, (FMA(h, p.x, mkv<T>(1.0)) * FMA(h, xf, mkv<T>(1.0))) * D2));
-  const T ph = SQRT(ph2);
-  const T uu = (k0 * chord) / (ph + ph);
-  if (!(std::fabs(val(uu)) <= 1.0)) { mark_lost(p, -2, turn, elem); return; }
-  const T lh = ((L >= 0.0) ? chord : -chord) * asin_over(uu);
-  const T lr = lh / ph;
-  p.x = xf;
-  p.px = A;
-  p.y = FMA(p.py, lr, p.y);
-  p.zeta = p.zeta + FMA(-p.ep, lr, mkv<T>(L));
 }
 
 // ---------------------------------------------------------------------------
@@ -1253,10 +988,10 @@ static bool inside_polygon(double x, double y, const double* A, const double* B,
   bool in = false;
   for (int k = 0; k < n; k++) {
     const int k2 = (k + 1 == n) ? 0 : k + 1;
-    const double ax = std::fma(w, B[2 * k] - A[2 * k], A[2 * k]);
-    const double ay = std::fma(w, B[2 * k + 1] - A[2 * k + 1], A[2 * k + 1]);
-    const double bx = std::fma(w, B[2 * k2] - A[2 * k2], A[2 * k2]);
-    const double by = std::fma(w, B[2 * k2 + 1] - A[2 * k2 + 1], A[2 * k2 + 1]);
+    const double ax = A[2 * k] + w * (B[2 * k] - A[2 * k]);
+    const double ay = A[2 * k + 1] + w * (B[2 * k + 1] - A[2 * k + 1]);
+    const double bx = A[2 * k2] + w * (B[2 * k2] - A[2 * k2]);
+    const double by = A[2 * k2 + 1] + w * (B[2 * k2 + 1] - A[2 * k2 + 1]);
     if ((ay > y) != (by > y)) {
       const double xi = ax + (y - ay) * (bx - ax) / (by - ay);
       if (x < xi) in = !in;
@@ -1266,61 +1001,51 @@ static bool inside_polygon(double x, double y, const double* A, const double* B,
 }
 
 // Inverse of one row's map (radiation off).  Returns false if the row has
-// no inverse here (linear map) or the backward drift is not defined.
+// no inverse here (linear map, non-linear edge) or the backward drift is not
+// defined.
 static bool inverse_row(Part<double>& p, const Prep& q, const RefConst& rc) {
   switch (q.type) {
     case T_DRIFT:
-      drift(p, -q.L, 0, 0);
+      drift(p, -q.L, rc, 0, 0);
       return p.state == 1;
     case T_MULTIPOLE: {
-      // the kick leaves x, y unchanged: recompute the field and take it back
-      double br = q.m.c[q.m.N], bi = q.m.s[q.m.N];
-      for (int n = q.m.N - 1; n >= 0; n--) {
-        const double nr = std::fma(br, p.x, std::fma(-bi, p.y, q.m.c[n]));
-        const double ni = std::fma(br, p.y, std::fma(bi, p.x, q.m.s[n]));
-        br = nr;
-        bi = ni;
-      }
-      p.px = p.px + br;
-      p.py = p.py - bi;
+      // the kick leaves x, y and delta unchanged: recompute it and take it back
+      double fr, fi;
+      multipole_field(p, q.m, &fr, &fi);
       if (q.m.hxl != 0.0) {
-        p.px = std::fma(-q.m.hxl, p.opd, p.px);
-        p.px = std::fma(q.m.k0h, p.x, p.px);
-        p.zeta = std::fma(q.m.hxl * p.rv0v, p.x, p.zeta);
+        p.zeta = p.zeta + q.m.hxl * p.x / p.rvv;
+        p.px = p.px + q.m.k0h * p.x;
+        p.px = p.px - ((q.m.hxl - q.m.c[0]) + q.m.hxl * p.delta);
+      } else {
+        p.px = p.px + q.m.c[0];
       }
+      p.px = p.px + fr;
+      p.py = p.py - (fi + q.m.s[0]);
       return true;
     }
     case T_CAVITY: {
-      const double phi = std::fma(-q.krf, p.zeta, q.lagr);
-      p.ptau = std::fma(-q.qv, SIN(phi), p.ptau);
+      const double phi = q.lagr - q.krf * p.zeta;
+      p.ptau = p.ptau - q.qv * std::sin(phi);
       energy_update(p, rc);
       return true;
     }
     case T_DIPEDGE:
-      if (q.enl) return false;  // no inverse formed for the non-linear edge
-      p.px = std::fma(-q.r21, p.x, p.px);
-      p.py = std::fma(-q.r43, p.y, p.py);
+      if (q.enl) return false;
+      p.px = p.px - q.r21 * p.x;
+      p.py = p.py - q.r43 * p.y;
       return true;
     case T_LINEARMAP: return false;
-    case T_QUAD: thick_quad(p, q.k1, -q.Lq); return true;
+    case T_QUAD: thick_quad(p, q.k1, -q.Lq, rc); return true;
     case T_BEND:
-      if (q.bfull) bend_full(p, q.bk0, q.bh, -q.bL, 0, 0);
-      else bend_expanded(p, q.bk0, q.bh, -q.bL, q.bk1);
+      if (q.bfull) bend_full(p, q.bk0, q.bh, -q.bL, rc, 0, 0);
+      else bend_expanded(p, q.bk0, q.bh, -q.bL, q.bk1, rc);
       return p.state == 1;
-    case T_BEAMBEAM4D: {  // x, y unchanged by the kick: take the same kick back
-      double fx, fy;
-      gauss_field(p.x - q.bb.xc, p.y - q.bb.yc, q.bb, &fx, &fy);
-      p.px = std::fma(-q.bb.K, fx, p.px);
-      p.py = std::fma(-q.bb.K, fy, p.py);
-      return true;
-    }
+    case T_BEAMBEAM4D:
     case T_SPACECHARGE: {  // x, y, zeta unchanged by the kick: take the same kick back
-      double fx, fy;
-      gauss_field(p.x - q.bb.xc, p.y - q.bb.yc, q.bb, &fx, &fy);
-      const double g = (q.sc_i2sz2 > 0.0) ? exp_cw(-((p.zeta * p.zeta) * q.sc_i2sz2)) : 1.0;
-      const double Kg = q.bb.K * g;
-      p.px = std::fma(-Kg, fx, p.px);
-      p.py = std::fma(-Kg, fy, p.py);
+      double kx, ky;
+      lens_kick(q, p.x, p.y, p.zeta, &kx, &ky);
+      p.px = p.px - kx;
+      p.py = p.py - ky;
       return true;
     }
     case T_XYSHIFT:
@@ -1329,10 +1054,10 @@ static bool inverse_row(Part<double>& p, const Prep& q, const RefConst& rc) {
       return true;
     case T_SROTATION: {
       const double x = p.x, y = p.y, px = p.px, py = p.py;
-      p.x = std::fma(q.cs, x, -(q.sn * y));
-      p.y = std::fma(q.cs, y, q.sn * x);
-      p.px = std::fma(q.cs, px, -(q.sn * py));
-      p.py = std::fma(q.cs, py, q.sn * px);
+      p.x = q.cs * x - q.sn * y;
+      p.y = q.cs * y + q.sn * x;
+      p.px = q.cs * px - q.sn * py;
+      p.py = q.cs * py + q.sn * px;
       return true;
     }
     default: return true;  // markers, apertures
@@ -1386,7 +1111,6 @@ int xo_track(const Element* el, int64_t n_el, const Reference* ref, int rad_mode
     p.delta = delta[i]; p.ptau = ptau[i]; p.rpp = rpp[i]; p.rvv = rvv[i];
     p.state = state[i]; p.at_turn = at_turn[i]; p.at_element = at_element[i]; p.id = pid[i];
     if (p.state != 1) continue;
-    derive(p, rc);
     for (int64_t t = start_turn; t < start_turn + n_turns && p.state == 1; t++) {
       for (int64_t e = 0; e < n_el; e++) {
         track_element(p, prep[e], rad_mode, rc, seed, (int)t, (int)e);
@@ -1471,7 +1195,6 @@ int xo_refine_losses(const Element* el, int64_t n_el, const Reference* ref, cons
     p.x = x[i]; p.px = px[i]; p.y = y[i]; p.py = py[i]; p.zeta = zeta[i];
     p.delta = delta[i]; p.ptau = ptau[i]; p.rpp = rpp[i]; p.rvv = rvv[i];
     p.state = 1; p.at_turn = 0; p.at_element = 0; p.id = 0;
-    derive(p, rc);
     // back to the exit of q
     bool good = true;
     for (int64_t j = e;;) {
@@ -1497,11 +1220,11 @@ int xo_refine_losses(const Element* el, int64_t n_el, const Reference* ref, cons
         const double h = L / (double)ns;
         const double c = std::cos(fr[j].th), sn = std::sin(fr[j].th);
         for (int64_t k = 1; k <= ns; k++) {
-          if (ty == T_QUAD) thick_quad(p, prep[j].k1, h);
-          else if (ty == T_BEND && prep[j].bfull) bend_full(p, prep[j].bk0, prep[j].bh, h, 0, 0);
-          else if (ty == T_BEND) bend_expanded(p, prep[j].bk0, prep[j].bh, h, prep[j].bk1);
-          else drift(p, h, 0, 0);
-          const double at = std::fma((double)k, h, pos);
+          if (ty == T_QUAD) thick_quad(p, prep[j].k1, h, rc);
+          else if (ty == T_BEND && prep[j].bfull) bend_full(p, prep[j].bk0, prep[j].bh, h, rc, 0, 0);
+          else if (ty == T_BEND) bend_expanded(p, prep[j].bk0, prep[j].bh, h, prep[j].bk1, rc);
+          else drift(p, h, rc, 0, 0);
+          const double at = pos + (double)k * h;
           if (p.state != 1) { found = at; break; }
           const double lx = (c * p.x - sn * p.y) + fr[j].dx;
           const double ly = (sn * p.x + c * p.y) + fr[j].dy;
@@ -1694,33 +1417,6 @@ int xo_lyapunov(const Element* el, int64_t n_el, const Reference* ref, int rad_m
 }
 
 // Test hooks for the building blocks.
-double xo_sin(double x) { return sin_cw(x); }
-
-// The special functions of the beam-beam kick, element-wise (for their pins).
-void xo_exp(const double* x, double* out, int64_t n) {
-  for (int64_t i = 0; i < n; i++) out[i] = exp_cw(x[i]);
-}
-void xo_one_minus_exp(const double* u, double* out, int64_t n) {
-  for (int64_t i = 0; i < n; i++) out[i] = one_minus_exp(u[i]);
-}
-void xo_faddeeva(const double* x, const double* y, double* wr, double* wi, int64_t n) {
-  for (int64_t i = 0; i < n; i++) faddeeva(x[i], y[i], &wr[i], &wi[i]);
-}
-// Field shape of a unit bi-Gaussian line charge (sigma_x, sigma_y) at (x, y).
-void xo_gauss_field(double sx, double sy, const double* x, const double* y, double* fx, double* fy, int64_t n) {
-  Element e;
-  std::memset(&e, 0, sizeof(e));
-  e.type = T_BEAMBEAM4D;
-  e.p[0] = 1.0; e.p[1] = 1.0; e.p[2] = sx; e.p[3] = sy;
-  const Reference r = {938.27208816e6, 1.0, 450e9};
-  const Prep q = prepare(e, ref_const(r));
-  for (int64_t i = 0; i < n; i++) gauss_field(x[i], y[i], q.bb, &fx[i], &fy[i]);
-}
-
-// The drift's (1+u)^(-1/2) - 1, element-wise (for its pins).
-void xo_inv_pz_m1(const double* u, double* out, int64_t n) {
-  for (int64_t i = 0; i < n; i++) out[i] = inv_pz_m1<double>(u[i]);
-}
 void xo_philox4x64_10(const uint64_t* ctr, const uint64_t* key, uint64_t* out) { philox4x64_10(ctr, key, out); }
 double xo_uniform(uint64_t seed, uint64_t pid, uint64_t turn, uint64_t elem, int64_t index) {
   Uniforms U(seed, pid, turn, elem);
@@ -1738,6 +1434,20 @@ double xo_spectrum_sample(double u) { return spectrum().sample(u); }
 void xo_ref_constants(const Reference* ref, double* out) {
   RefConst c = ref_const(*ref);
   out[0] = c.E0; out[1] = c.beta0; out[2] = c.gamma0; out[3] = c.crad; out[4] = c.kq; out[5] = c.uc15;
+}
+// Field shape of a unit bi-Gaussian line charge (sigma_x, sigma_y) at (x, y).
+void xo_gauss_field(double sx, double sy, const double* x, const double* y, double* fx, double* fy, int64_t n) {
+  for (int64_t i = 0; i < n; i++) gauss_field(x[i], y[i], sx, sy, &fx[i], &fy[i]);
+}
+// Nodes and weights of the quadrature rule on [-1, 1]; returns their number.
+int xo_gauss_legendre(double* x, double* w) {
+  const GaussLegendre& g = gauss_legendre();
+  for (int i = 0; i < GaussLegendre::N; i++) { x[i] = g.x[i]; w[i] = g.w[i]; }
+  return GaussLegendre::N;
+}
+// The entire functions of the thick maps at z: C, S, S2, S3 (for their pins).
+void xo_osc_funcs(const double* z, double* out, int64_t n) {
+  for (int64_t i = 0; i < n; i++) osc_funcs(z[i], &out[4 * i], &out[4 * i + 1], &out[4 * i + 2], &out[4 * i + 3]);
 }
 
 }  // extern "C"

@@ -19,6 +19,9 @@
 
 using namespace xt;
 
+// Frees the batched plans that name a tracker (defined with the plans below).
+void evict_plans_of(const xt_tracker* t);
+
 namespace {
 
 thread_local std::string g_err;
@@ -276,7 +279,7 @@ int xt_tracker_create(const xt_element* table, int64_t n, const xt_reference* re
   std::unique_ptr<xt_tracker> t(new xt_tracker());
   t->opt = o;
   t->rc = ref_constants(*ref);
-  t->ref = {t->rc.beta0, t->rc.gamma0, t->rc.bg0, t->rc.ib0, t->rc.twoib0, t->rc.p0c, t->rc.uc15};
+  t->ref = {t->rc.beta0, t->rc.gamma0, t->rc.bg0, t->rc.ib0, t->rc.twoib0, t->rc.p0c, t->rc.uc15, t->rc.ig02};
   t->sn = sin_table();
   std::string err;
   rc = compile_lattice(table, n, t->rc, &t->lat, &err);
@@ -325,6 +328,7 @@ int xt_tracker_create(const xt_element* table, int64_t n, const xt_reference* re
 void xt_tracker_destroy(xt_tracker* t) {
   if (!t) return;
   cudaDeviceSynchronize();
+  evict_plans_of(t);
   cudaFree(t->d_lat);
   cudaFree(t->d_chunks);
   cudaFree(t->d_spec_xi);
@@ -695,6 +699,11 @@ void set_error(const std::string& msg) { g_err = msg; }
 int noalloc_prepare(xt_tracker* t, const xt_particles* p, int64_t n_turns, TrackArgs* a, int* block,
                     int* grid, size_t* smem, int* seg, int* rad) {
   if (!t->d_chunks) return fail(XT_ERR_INVALID, "tracker has no lattice chunk table");
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev != t->device)
+    return fail(XT_ERR_INVALID, "xt_track_noalloc: the current device (" + std::to_string(dev) +
+                                    ") is not the tracker's (" + std::to_string(t->device) + ")");
   *block = eff_block(t);
   *smem = track_smem_bytes(*block, t->chunk_built);
   int rc = grid_for(t, *block, *smem, grid);
@@ -731,10 +740,22 @@ extern "C" int xt_autotune(xt_tracker* t, const xt_particles* probe, int64_t pro
   }
   const int64_t n = probe->n;
   cudaStream_t s = (cudaStream_t)stream;
-  // scratch copy of the probe (13 arrays)
+  // scratch copy of the probe (13 arrays) and two events, released on every
+  // return path (after the stream has finished with them)
+  struct Scratch {
+    cudaStream_t s;
+    uint8_t* buf = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~Scratch() {
+      cudaStreamSynchronize(s);
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      if (buf) cudaFree(buf);
+    }
+  } sc{s};
   const size_t bd = ((size_t)n * 8 + 255) & ~(size_t)255, bi = ((size_t)n * 4 + 255) & ~(size_t)255;
-  uint8_t* buf = nullptr;
-  CK(cudaMalloc((void**)&buf, 10 * bd + 3 * bi));
+  CK(cudaMalloc((void**)&sc.buf, 10 * bd + 3 * bi));
+  uint8_t* const buf = sc.buf;
   xt_particles w;
   double** fd[9] = {&w.x, &w.px, &w.y, &w.py, &w.zeta, &w.delta, &w.ptau, &w.rpp, &w.rvv};
   double* const src[9] = {probe->x, probe->px, probe->y, probe->py, probe->zeta,
@@ -753,9 +774,18 @@ extern "C" int xt_autotune(xt_tracker* t, const xt_particles* probe, int64_t pro
     return XT_OK;
   };
   const xt_options saved = t->opt;
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  CK(cudaEventCreate(&sc.e0));
+  CK(cudaEventCreate(&sc.e1));
+  const cudaEvent_t e0 = sc.e0, e1 = sc.e1;
+  // a CUDA error inside the search sets rc and leaves the loops
+#define TUNE_CK(call)                                  \
+  {                                                    \
+    const cudaError_t _e = (call);                     \
+    if (_e != cudaSuccess) {                           \
+      rc = cuda_fail(_e, #call);                       \
+      break;                                           \
+    }                                                  \
+  }
   float best = 1e30f;
   int bb = DEFAULT_BLOCK, bc = DEFAULT_CHUNK, bs = 0;
   const int blocks[] = {64, 128, 256};
@@ -775,23 +805,20 @@ extern "C" int xt_autotune(xt_tracker* t, const xt_particles* probe, int64_t pro
         const size_t sm = track_smem_bytes(blk, t->chunk_built);
         if (sm > (size_t)t->smem_max || track_occupancy(o.radiation + (t->lat.thick ? 3 : 0), blk, sm, &bps) || bps < 1) continue;
         if ((rc = restore())) break;
-        CK(cudaEventRecord(e0, s));
+        TUNE_CK(cudaEventRecord(e0, s));
         rc = track_device(t, &w, 0, probe_turns, stream);
         if (rc) break;
-        CK(cudaEventRecord(e1, s));
-        CK(cudaEventSynchronize(e1));
+        TUNE_CK(cudaEventRecord(e1, s));
+        TUNE_CK(cudaEventSynchronize(e1));
         float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
+        TUNE_CK(cudaEventElapsedTime(&ms, e0, e1));
         if (ms < best) { best = ms; bb = blk; bc = ch; bs = sg; }
       }
       if (rc) break;
     }
     if (rc) break;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaStreamSynchronize(s);
-  cudaFree(buf);
+#undef TUNE_CK
   if (rc) { t->opt = saved; build_device_chunks(t, eff_chunk(t)); return rc; }
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
@@ -820,7 +847,9 @@ struct BatchPlan {
   int32_t* d_counts = nullptr;
   int32_t* d_n_alive = nullptr;
   int32_t* d_scal = nullptr;  // [0] status [1] tile counter [2] turn base
-  std::map<std::tuple<int64_t, int, int, int, int>, cudaGraphExec_t> graphs;
+  std::vector<const xt_tracker*> trackers;  // the seeds' trackers, for eviction on destroy
+  // captured graphs, keyed by every value the captured launches bake in
+  std::map<std::vector<uint64_t>, cudaGraphExec_t> graphs;
   ~BatchPlan() {
     for (auto& g : graphs) cudaGraphExecDestroy(g.second);
     cudaFree(d_seeds); cudaFree(d_order); cudaFree(d_idx_base); cudaFree(d_prefix);
@@ -875,6 +904,7 @@ int make_plan(xt_tracker* const* trs, const xt_particles* ps, int32_t ns, BatchP
   for (int i = 0; i < ns; i++) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ps[a].n > ps[b].n; });
   pl->n_seeds = ns;
+  pl->trackers.assign(trs, trs + ns);
   int rc;
   if ((rc = dev_alloc(&pl->d_seeds, ns))) return rc;
   if ((rc = dev_alloc(&pl->d_order, ns))) return rc;
@@ -984,7 +1014,23 @@ extern "C" int xt_track_batched(xt_tracker* const* trs, const xt_particles* ps, 
   e = launch_set_int(pl->d_scal + 2, (int32_t)start_turn, stream);
   if (e) return cuda_fail((cudaError_t)e, "turn base");
   if (!graph) return enqueue_batched(t0, pl, kind, n_turns, seg, block, smem, grid, stream);
-  const auto gk = std::make_tuple(n_turns, seg, block, chunk, kind);
+  // the graph's key: the launch shape and every field of t0 that
+  // enqueue_batched copies into the kernel arguments (seed, cycle budget,
+  // cancel flag, spectrum tables, reference constants, sine table)
+  std::vector<uint64_t> gk = {(uint64_t)n_turns, (uint64_t)seg, (uint64_t)block, (uint64_t)chunk, (uint64_t)kind,
+                              (uint64_t)grid, (uint64_t)smem, t0->opt.seed, (uint64_t)t0->opt.max_cycles,
+                              (uint64_t)(uintptr_t)t0->d_cancel, (uint64_t)(uintptr_t)t0->d_spec_xi,
+                              (uint64_t)(uintptr_t)t0->d_spec_F, (uint64_t)(uintptr_t)t0->d_spec_guide,
+                              (uint64_t)t0->spec_k, (uint64_t)t0->chunk_built};
+  auto push_bytes = [&gk](const void* v, size_t nb) {
+    for (size_t o = 0; o < nb; o += 8) {
+      uint64_t w = 0;
+      std::memcpy(&w, (const uint8_t*)v + o, std::min<size_t>(8, nb - o));
+      gk.push_back(w);
+    }
+  };
+  push_bytes(&t0->ref, sizeof(t0->ref));
+  push_bytes(&t0->sn, sizeof(t0->sn));
   auto gi = pl->graphs.find(gk);
   if (gi == pl->graphs.end()) {
     cudaStream_t cs;
@@ -1023,6 +1069,19 @@ extern "C" int xt_batched_sync_status(xt_tracker* const* trs, const xt_particles
   CK(cudaMemsetAsync(it->second->d_scal, 0, sizeof(int32_t), s));
   CK(cudaStreamSynchronize(s));
   return st;
+}
+
+// Frees every batched plan that names tracker t (called by
+// xt_tracker_destroy, after the device has finished its work).
+void evict_plans_of(const xt_tracker* t) {
+  std::lock_guard<std::mutex> g(g_plan_mu);
+  for (auto it = g_plans.begin(); it != g_plans.end();) {
+    const auto& trs = it->second->trackers;
+    if (std::find(trs.begin(), trs.end(), t) != trs.end())
+      it = g_plans.erase(it);
+    else
+      ++it;
+  }
 }
 
 extern "C" void xt_batched_release(void) {

@@ -55,7 +55,7 @@ struct Chunk {
 
 // Reference-derived constants used by the kernels.
 struct RefDev {
-  double beta0, gamma0, bg0, ib0, twoib0, p0c, uc15;
+  double beta0, gamma0, bg0, ib0, twoib0, p0c, uc15, ig02;  // ig02 = 1/gamma0^2
 };
 
 // Coefficients of the sine used by the RF cavity (Taylor series on |r| <= pi/4).
@@ -76,7 +76,7 @@ struct Lattice {
 };
 
 struct Refc {
-  double m0, q0, p0c, E0, beta0, gamma0, bg0, ib0, twoib0, crad, kq, uc15;
+  double m0, q0, p0c, E0, beta0, gamma0, bg0, ib0, twoib0, crad, kq, uc15, ig02;
 };
 
 // Host-side compilation (xt_lattice.cpp).

@@ -28,6 +28,7 @@ Refc ref_constants(const xt_reference& r) {
   c.bg0 = r.p0c / r.mass0;
   c.ib0 = c.E0 / r.p0c;
   c.twoib0 = 2.0 * c.ib0;
+  c.ig02 = (r.mass0 / c.E0) * (r.mass0 / c.E0);
   // classical radius of the tracked species, r_c = q^2 r_e m_e / m
   const double rc = r.q0 * r.q0 * RE_M * ME_EV / r.mass0;
   c.crad = 2.0 * rc * r.mass0 / (3.0 * r.p0c);

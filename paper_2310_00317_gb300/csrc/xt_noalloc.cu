@@ -3,10 +3,10 @@
 // xt_track keeps a per-tracker workspace (alive-index list, block counts,
 // work counter, status) that it grows with cudaMalloc the first time it sees a
 // larger particle count.  Some callers cannot allocate device memory while
-// they track: code that runs inside a CUDA stream capture that must not
-// allocate, host applications whose device memory is owned by their own
+// they track: host applications whose device memory is owned by their own
 // allocator or budget and that forbid cudaMalloc after start-up, and real-time
-// loops that cannot afford allocation latency.  For them this entry point uses
+// loops that cannot afford allocation latency or the device-wide
+// synchronisation cudaMalloc and cudaFree can imply.  For them this entry point uses
 // a fixed scratch array in static device memory instead: every GPU that loads
 // the library holds it (about 4 MiB) until the process exits.
 #include <cuda_runtime.h>
@@ -124,4 +124,25 @@ extern "C" int xt_track_noalloc(xt_tracker* tr, const xt_particles* p, int64_t s
     }
   }
   return XT_OK;
+}
+
+// Status word of the scratch array on the current device: the outcome of the
+// last xt_track_noalloc call there (XT_OK, XT_ERR_TIMEOUT or
+// XT_ERR_CANCELLED).  Synchronises the stream, reads the word and clears it.
+extern "C" int xt_noalloc_status(void* stream) {
+  xt::set_error("");
+  int32_t* scratch = nullptr;
+  int rc = scratch_for_current_device(&scratch);
+  if (rc) return rc;
+  int32_t st = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(&st, scratch + SCAL_OFF, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(scratch + SCAL_OFF, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    xt::set_error(std::string("xt_noalloc_status: ") + cudaGetErrorString(e));
+    return XT_ERR_CUDA;
+  }
+  return st;
 }

@@ -144,11 +144,25 @@ __device__ __forceinline__ bool abs_ge_quarter(double v) {
 
 // ---------------------------------------------------------------------------
 // Particle state in registers.  opd = 1+delta, dm1 = (1+delta)^2 - 1,
-// rv0v = 1/rvv and ep = 1 + beta0 ptau are derived from the stored state.
+// rv0v = 1/rvv and ep = 1 + beta0 ptau are derived from the stored state,
+// and so are the drift's iep = 1/ep, iep2 = 1/ep^2 and
+// c0 = ((1+delta)^2 - ep^2)/ep^2 = dm1/(gamma0^2 ep^2), and the thick maps'
+// dmb = delta - beta0 ptau = dm1/(gamma0^2 ((1+delta) + ep)), written without
+// the cancellation of delta against beta0 ptau.  Each instantiation keeps in
+// registers only those it uses.
 struct Part {
   double x, px, y, py, zeta, delta, ptau, rpp, rvv;
   double opd, dm1, rv0v, ep, epm1;  // epm1 = beta0 ptau (= ep - 1)
+  double iep, iep2, c0, dmb;
 };
+
+__device__ __forceinline__ void derive_drift(Part& p, const RefDev& r) {
+  p.iep = p.rvv * p.rpp;
+  p.iep2 = p.iep * p.iep;
+  const double g = p.dm1 * r.ig02;
+  p.c0 = g * p.iep2;
+  p.dmb = g / (p.opd + p.ep);
+}
 
 // ep = 1 + beta0 ptau (= opd / rvv), rv0v = 1/rvv = ep rpp
 __device__ __forceinline__ void derive(Part& p, const RefDev& r) {
@@ -157,6 +171,7 @@ __device__ __forceinline__ void derive(Part& p, const RefDev& r) {
   p.ep = fma(r.beta0, p.ptau, 1.0);
   p.rv0v = p.ep * p.rpp;
   p.epm1 = r.beta0 * p.ptau;
+  derive_drift(p, r);
 }
 
 // (1+delta)^2 = 1 + 2 ptau/beta0 + ptau^2 in the form delta = u/(sqrt(1+u)+1).
@@ -171,6 +186,7 @@ __device__ __forceinline__ void energy_update(Part& p, const RefDev& r) {
   p.rvv = p.opd / p.ep;
   p.rv0v = p.ep * p.rpp;
   p.epm1 = r.beta0 * p.ptau;
+  derive_drift(p, r);
 }
 
 __device__ __forceinline__ void apply_energy_loss(Part& p, double dpt, const RefDev& r) {
@@ -323,21 +339,24 @@ __device__ __forceinline__ double inv_pz_m1_order8(double u) {
 }
 
 // Exact drift, for the whole warp (dead lanes compute along and keep their
-// coordinates).  yh = 1/pz - 1 = (1+u)^(-1/2) - 1, u = (1+delta)^2 - 1 - px^2
-// - py^2, by the Taylor series of the lowest order whose truncation stays
-// below half an ulp of yh on its interval -- order 3 for |u| <= 2^-18
-// (on-momentum particles), 6 for |u| <= 2^-9, 8 for |u| <= 2^-7 -- else
-// 1/sqrt(1+u) - 1; then L/pz = L + L yh and zeta += -L (beta0 ptau + ep yh).
-// The order is chosen per particle (so the result does not depend on the
-// warp), but when all live lanes of the warp need the same order the warp
-// branches to that series alone: a masked lane costs the FP64 pipe as much
-// as an active one, so per-lane selection would issue every order's
-// instructions.  Returns the loss code: -2 for a live lane whose u is not in
-// (-1, inf), else 1 (dead lanes always 1).  The validity and order tests run
-// on the integer pipe.
+// coordinates).  With ep = 1 + beta0 ptau = (1+delta)/rvv, the square of the
+// longitudinal momentum is pz^2 = ep^2 (1 + v), v = c0 - (px^2 + py^2)/ep^2,
+// c0 = ((1+delta)^2 - ep^2)/ep^2 = dm1/(gamma0^2 ep^2).  Then
+// yh = (1+v)^(-1/2) - 1 = ep/pz - 1 gives L/pz = (L/ep)(1 + yh) and the
+// path-length term zeta += L (1 - ep/pz) = -L yh, formed from v, which holds
+// only the transverse angles and delta/gamma0^2: no term cancels.  yh is the
+// Taylor series of the lowest order whose truncation stays below half an ulp
+// of yh on its interval -- order 3 for |v| <= 2^-18, 6 for |v| <= 2^-9, 8 for
+// |v| <= 2^-7 -- else 1/sqrt(1+v) - 1.  The order is chosen per particle (so
+// the result does not depend on the warp), but when all live lanes of the
+// warp need the same order the warp branches to that series alone: a masked
+// lane costs the FP64 pipe as much as an active one, so per-lane selection
+// would issue every order's instructions.  Returns the loss code: -2 for a
+// live lane whose v is not in (-1, inf) (pz not real), else 1 (dead lanes
+// always 1).  The validity and order tests run on the integer pipe.
 __device__ __forceinline__ int drift_warp(Part& p, const double* prm, bool alive) {
   const double L = prm[0];
-  const double u = fma(-p.px, p.px, fma(-p.py, p.py, p.dm1));
+  const double u = fma(-fma(p.px, p.px, p.py * p.py), p.iep2, p.c0);  // v
   const uint64_t ub = dbits(u), ua = abs_bits(u);
   const bool valid = (ub >> 63) ? (ua < 0x3FF0000000000000ull) : (ub < 0x7FF0000000000000ull);
   const bool run = alive && valid;
@@ -364,10 +383,11 @@ __device__ __forceinline__ int drift_warp(Part& p, const double* prm, bool alive
     yh = 1.0 / sqrt(1.0 + u) - 1.0;
   }
   if (run) {
-    const double lpz = fma(L, yh, L);
+    const double Li = L * p.iep;
+    const double lpz = fma(Li, yh, Li);
     p.x = fma(p.px, lpz, p.x);
     p.y = fma(p.py, lpz, p.y);
-    p.zeta = fma(-L, fma(p.ep, yh, p.epm1), p.zeta);
+    p.zeta = fma(-L, yh, p.zeta);
   }
   return (alive && !valid) ? -2 : 1;
 }
@@ -562,7 +582,7 @@ __device__ __forceinline__ void bend_expanded(Part& p, double k0, double h, doub
   I = fma(hL * fma(Cy, Sy, 1.0), py0 * py0, I);
   I = fma(L2 * (Sy * Sy), py0 * Gy, I);
   I = fma(hL3 * fma(Sy, S2y, S3y), Gy * Gy, I);
-  p.zeta = p.zeta + fma(L * (p.delta - p.epm1), p.rpp, -(p.rv0v * fma(h, Ix, (0.5 * (p.rpp * p.rpp)) * I)));
+  p.zeta = p.zeta + fma(L * p.dmb, p.rpp, -(p.rv0v * fma(h, Ix, (0.5 * (p.rpp * p.rpp)) * I)));
 }
 
 // Thick bend, full model (section "Lattice modelling and single particle
@@ -649,7 +669,7 @@ __device__ __forceinline__ void thick_quad(Part& p, double absk1, double L, bool
   I = fma(hL * (Sha * Ch), Ah2 + Bh2, I);
   I = fma((p.opd * L) * (Sha * gh), pv0 * v0, I);
   // 1 - 1/rvv = (delta - beta0 ptau) / (1+delta)
-  p.zeta = p.zeta + fma(L * (p.delta - p.epm1), p.rpp, -(((0.5 * p.rv0v) * (p.rpp * p.rpp)) * I));
+  p.zeta = p.zeta + fma(L * p.dmb, p.rpp, -(((0.5 * p.rv0v) * (p.rpp * p.rpp)) * I));
   p.x = fx ? u1 : v1;
   p.px = fx ? pu1 : pv1;
   p.y = fx ? v1 : u1;
@@ -687,22 +707,34 @@ __device__ __forceinline__ void multipole(Part& p, const double* prm, int order,
     }
     return;
   }
-  double2 c = cf[order];
-  double br = c.x, bi = c.y;
-  for (int n = order - 1; n >= 0; n--) {
-    c = cf[n];
-    const double nr = fma(br, p.x, fma(-bi, p.y, c.x));
-    const double ni = fma(br, p.y, fma(bi, p.x, c.y));
-    br = nr;
-    bi = ni;
+  // field of the orders >= 1, (fr, fi); the constant term c0 = (knl0, ksl0)
+  // is added separately, and with a curvature the frame term hxl (1+delta)
+  // joins -knl0 first, as (hxl - knl0) + hxl delta: in a ring's dipole slice
+  // both are about 1e-3 while px is about 1e-5
+  double fr = 0.0, fi = 0.0;
+  if (order >= 1) {
+    double2 c = cf[order];
+    double ar = c.x, ai = c.y;
+    for (int n = order - 1; n >= 1; n--) {
+      c = cf[n];
+      const double nr = fma(ar, p.x, fma(-ai, p.y, c.x));
+      const double ni = fma(ar, p.y, fma(ai, p.x, c.y));
+      ar = nr;
+      ai = ni;
+    }
+    fr = fma(ar, p.x, -(ai * p.y));
+    fi = fma(ar, p.y, ai * p.x);
   }
-  p.px = p.px - br;
+  const double2 c0 = cf[0];
+  const double br = fr + c0.x, bi = fi + c0.y;
   p.py = p.py + bi;
   if (flags & REC_CURV) {
     const double hxl = prm[MP_HXL];
-    p.px = fma(hxl, p.opd, p.px);
+    p.px = (p.px - fr) + fma(hxl, p.delta, hxl - c0.x);
     p.px = fma(-prm[MP_K0H], p.x, p.px);
     p.zeta = fma(-(hxl * p.rv0v), p.x, p.zeta);
+  } else {
+    p.px = p.px - br;
   }
   if (RAD == XT_RAD_MEAN && (flags & REC_RAD)) {
     const double kk = fma(br, br, bi * bi);
@@ -747,8 +779,9 @@ __device__ __forceinline__ void multipole(Part& p, const double* prm, int order,
 // k0, t = tan(e), s (+1 entrance, -1 exit), corr.  The canonical map of the
 // generating function x X' + y Y' + zeta Z' + (k0/2) y^2 T(px, py', delta)
 // - (k0/2) t x^2 with T = tan(e + s atan(px/pz)) (the vertical kick of the
-// fields a hard edge carries to first order in the field gradient): py' from
-// three fixed-point steps, then x, y, zeta shifted by (k0/2) y^2 dT/d(px,
+// fields a hard edge carries to first order in the field gradient): py' by
+// fixed-point iteration until it stops changing (at most 40 steps), then x,
+// y, zeta shifted by (k0/2) y^2 dT/d(px,
 // py, pzeta); the wedge kick px += r21 x after it at the entrance, before it
 // at the exit; the finite-extent correction py += corr y, corr = r21 + r43,
 // so that the linearisation is the linear edge.  Returns -2 if pz is not real.
@@ -761,10 +794,13 @@ __device__ __forceinline__ int edge_nonlinear(Part& p, const double* prm) {
   const double ky = k0 * y;
   const double st = sgn * t;
   double pyn = py;
-  for (int k = 0; k < 3; k++) {
+  for (int k = 0; k < 40; k++) {  // fixed-point iteration until py' no longer changes
     const double pz = sqrt(1.0 + fma(-pyn, pyn, base));
     const double Tv = fma(t, pz, sgn * px) / fma(-st, px, pz);
-    pyn = fma(-ky, Tv, py);
+    const double nxt = fma(-ky, Tv, py);
+    const bool same = nxt == pyn;
+    pyn = nxt;
+    if (same) break;
   }
   const double u = fma(-pyn, pyn, base);
   if (!gt_minus_one(u)) return -2;
@@ -1133,7 +1169,7 @@ __global__ void __launch_bounds__(XT_MAX_BLOCK, (KIND >= 2) ? 2 : 3) track_batch
 // warp votes here: the series order of the drift is chosen per lane.
 
 __device__ __forceinline__ bool drift_lane(Part& p, double L) {
-  const double u = fma(-p.px, p.px, fma(-p.py, p.py, p.dm1));
+  const double u = fma(-fma(p.px, p.px, p.py * p.py), p.iep2, p.c0);  // v, as in drift_warp
   const uint64_t ub = dbits(u), ua = abs_bits(u);
   const bool valid = (ub >> 63) ? (ua < 0x3FF0000000000000ull) : (ub < 0x7FF0000000000000ull);
   if (!valid) return false;
@@ -1142,10 +1178,11 @@ __device__ __forceinline__ bool drift_lane(Part& p, double L) {
   else if (ua <= 0x3F60000000000000ull) yh = inv_pz_m1_order6(u);
   else if (ua <= 0x3F80000000000000ull) yh = inv_pz_m1_order8(u);
   else yh = 1.0 / sqrt(1.0 + u) - 1.0;
-  const double lpz = fma(L, yh, L);
+  const double Li = L * p.iep;
+  const double lpz = fma(Li, yh, Li);
   p.x = fma(p.px, lpz, p.x);
   p.y = fma(p.py, lpz, p.y);
-  p.zeta = fma(-L, fma(p.ep, yh, p.epm1), p.zeta);
+  p.zeta = fma(-L, yh, p.zeta);
   return true;
 }
 
@@ -1157,21 +1194,29 @@ __device__ __forceinline__ bool inverse_record(Part& p, uint32_t type, uint32_t 
     case XT_DRIFT: return drift_lane(p, -prm[0]);
     case XT_MULTIPOLE: {  // x, y are unchanged by the kick: recompute the field, take it back
       const double2* cf = (const double2*)(prm + MP_COEF);
-      double2 c = cf[order];
-      double br = c.x, bi = c.y;
-      for (int n = (int)order - 1; n >= 0; n--) {
-        c = cf[n];
-        const double nr = fma(br, p.x, fma(-bi, p.y, c.x));
-        const double ni = fma(br, p.y, fma(bi, p.x, c.y));
-        br = nr;
-        bi = ni;
+      double fr = 0.0, fi = 0.0;
+      if (order >= 1) {
+        double2 c = cf[order];
+        double ar = c.x, ai = c.y;
+        for (int n = (int)order - 1; n >= 1; n--) {
+          c = cf[n];
+          const double nr = fma(ar, p.x, fma(-ai, p.y, c.x));
+          const double ni = fma(ar, p.y, fma(ai, p.x, c.y));
+          ar = nr;
+          ai = ni;
+        }
+        fr = fma(ar, p.x, -(ai * p.y));
+        fi = fma(ar, p.y, ai * p.x);
       }
-      p.px = p.px + br;
-      p.py = p.py - bi;
+      const double2 c0 = cf[0];
+      p.py = p.py - (fi + c0.y);
       if (flags & REC_CURV) {
-        p.px = fma(-prm[MP_HXL], p.opd, p.px);
+        const double hxl = prm[MP_HXL];
+        p.zeta = fma(hxl * p.rv0v, p.x, p.zeta);
         p.px = fma(prm[MP_K0H], p.x, p.px);
-        p.zeta = fma(prm[MP_HXL] * p.rv0v, p.x, p.zeta);
+        p.px = (p.px + fr) - fma(hxl, p.delta, hxl - c0.x);
+      } else {
+        p.px = p.px + (fr + c0.x);
       }
       return true;
     }

@@ -1,11 +1,16 @@
-"""GPU parity: the CUDA tracker against the oracle, element by element.
+"""GPU parity: the CUDA tracker against the independent oracle.
 
-The maps have a fixed operation order and every fma is explicit on both
-sides, so coordinates, loss codes, loss turns and loss elements must agree
-bit for bit (the RF sine and the exponential are the same Cody-Waite/Taylor
-evaluations on both sides).  The quantum radiation model draws the same
-Philox numbers and samples spectrum tables built by the same steps, so it is
-compared bit for bit too, besides its closed-form variance.
+The oracle (``oracle/``) writes each map out from its definition with IEEE
+square roots and divisions and the C library's elementary functions; the
+kernel keeps its own arithmetic (series, explicit fused multiply-adds, its own
+sine and exponential, Weideman's w(z)).  They are compared by the FP64
+criterion of the tracking path: every particle's loss outcome (state, loss
+turn, loss element) identical, and every coordinate within 1e-12 relative,
+judged against the larger of its own size and its spread over the ensemble.
+Quantum radiation draws the same Philox numbers on both sides and is compared
+per particle and in distribution.  Bit-for-bit checks remain only between
+two runs of the kernel (segmentation, block and chunk sizes, the host-buffer
+path, batched against per-seed launches).
 """
 import math
 
@@ -19,6 +24,7 @@ from paper_2310_00317_gb300 import xtgb
 pytestmark = pytest.mark.gpu
 
 FIELDS = oracle.FLOAT_FIELDS + oracle.INT_FIELDS
+RTOL = 1e-12
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -41,14 +47,50 @@ def gpu_track(el, ref, p, n_turns, start_turn=0, **opt):
 
 
 def assert_same(g, o, where=""):
+    """Bit-for-bit equality of two kernel runs."""
     for k in FIELDS:
         a, b = g[k], o[k]
         same = (a == b) | (np.isnan(a) & np.isnan(b)) if a.dtype.kind == "f" else (a == b)
         if not np.all(same):
             bad = np.flatnonzero(~same)
             i = bad[0]
-            raise AssertionError("%s%s differs for %d of %d particles; first %d: gpu %r oracle %r"
+            raise AssertionError("%s%s differs for %d of %d particles; first %d: %r vs %r"
                                  % (where, k, bad.size, a.size, i, a[i], b[i]))
+
+
+def rel_errors(g, o, keys=oracle.FLOAT_FIELDS):
+    """Per coordinate, |g - o| / max(|o|, rms of o over the finite entries);
+    0 where both are NaN, inf where only one is."""
+    out = {}
+    for k in keys:
+        a, b = np.asarray(g[k], float), np.asarray(o[k], float)
+        fin = np.isfinite(b)
+        rms = math.sqrt(float(np.mean(b[fin] ** 2))) if fin.any() else 0.0
+        scale = np.maximum(np.abs(b), rms if rms > 0 else 1e-300)
+        with np.errstate(invalid="ignore"):
+            e = np.abs(a - b) / scale
+        e = np.where(np.isnan(a) & np.isnan(b), 0.0, e)
+        e = np.where(np.isnan(a) != np.isnan(b), np.inf, e)
+        out[k] = e
+    return out
+
+
+def assert_close(g, o, rtol=RTOL, where=""):
+    """The FP64 criterion against the oracle: identical loss outcomes, and
+    coordinates within rtol relative (see rel_errors)."""
+    for k in oracle.INT_FIELDS:
+        same = np.asarray(g[k]) == np.asarray(o[k])
+        if not np.all(same):
+            bad = np.flatnonzero(~same)
+            i = bad[0]
+            raise AssertionError("%s%s differs for %d of %d particles; first %d: gpu %r oracle %r"
+                                 % (where, k, bad.size, same.size, i, g[k][i], o[k][i]))
+    for k, e in rel_errors(g, o).items():
+        if e.size and not np.all(e <= rtol):
+            i = int(np.argmax(np.where(np.isfinite(e), e, np.inf)))
+            raise AssertionError("%s%s: relative difference %.3g > %.1g for %d of %d particles; worst %d: "
+                                 "gpu %r oracle %r" % (where, k, e[i], rtol, int(np.sum(~(e <= rtol))), e.size,
+                                                       i, g[k][i], o[k][i]))
 
 
 def random_particles(ref, n, seed, sx=2e-3, spx=1e-4, sz=0.05, sd=1e-3):
@@ -58,18 +100,33 @@ def random_particles(ref, n, seed, sx=2e-3, spx=1e-4, sz=0.05, sd=1e-3):
 
 
 PROTON = I.proton_reference(450e9)
+# Particles spread over several RF buckets (0.5 m rms in zeta at a 0.75 m RF
+# wavelength) run on unstable longitudinal orbits, whose rounding differences
+# pass 1e-12 within 100 turns; 50 turns give every particle 550 lens passes.
+SC_TURNS = 50
 
 
 # --------------------------------------------------------------------------
-def test_fodo10_full_bitwise():
-    """FODO-10 ring, 1000 matched protons, 1000 turns (the full small config)."""
+def test_fodo10_full_1e12():
+    """FODO-10 ring, 1000 matched protons, 1000 turns (the full small
+    configuration): every particle's coordinates within 1e-12 relative of
+    the oracle after 1000 turns, also in the normalised phase space of each
+    plane, and identical loss outcomes."""
     el, ref = I.fodo10()
     p = I.matched_gaussian(el, ref, 1000, 2.5e-6, 3e-4, seed=I.BASE_SEED)
-    assert_same(gpu_track(el, ref, p, 1000), oracle.track(el, ref, p, 1000))
+    g, o = gpu_track(el, ref, p, 1000), oracle.track(el, ref, p, 1000)
+    assert_close(g, o)
+    opt = I.design_optics(el, ref)
+    for u, pu, bet, alf in (("x", "px", opt["betx"][0], opt["alfx"][0]), ("y", "py", opt["bety"][0], opt["alfy"][0])):
+        def nrm(a):
+            return np.stack([a[u] / math.sqrt(bet), (alf * a[u] + bet * a[pu]) / math.sqrt(bet)], axis=1)
+        zg, zo = nrm(g), nrm(o)
+        err = np.linalg.norm(zg - zo, axis=1) / np.linalg.norm(zo, axis=1)
+        assert err.max() <= RTOL, (u, err.max())
 
 
 @pytest.mark.parametrize("order", [0, 1, 2, 5, 10])
-def test_multipole_orders_bitwise(order):
+def test_multipole_orders(order):
     rng = np.random.default_rng(order)
     knl = rng.normal(0, 1, order + 1) * 10.0 ** -np.arange(order + 1)
     ksl = rng.normal(0, 1, order + 1) * 10.0 ** -np.arange(order + 1)
@@ -77,10 +134,10 @@ def test_multipole_orders_bitwise(order):
                   I.multipole(knl=[1e-3] + [0] * order, hxl=1e-3, lrad=2.0, order=order), I.drift(0.7),
                   I.aperture(0.05)])
     p = random_particles(PROTON, 333, order)
-    assert_same(gpu_track(el, PROTON, p, 7), oracle.track(el, PROTON, p, 7))
+    assert_close(gpu_track(el, PROTON, p, 7), oracle.track(el, PROTON, p, 7))
 
 
-def test_every_element_type_bitwise():
+def test_every_element_type():
     rng = np.random.default_rng(5)
     # a focusing linear map (phase advance 0.27 turns, beta 3 m) keeps most particles bounded
     c, s = math.cos(2 * math.pi * 0.27), math.sin(2 * math.pi * 0.27)
@@ -93,15 +150,15 @@ def test_every_element_type_bitwise():
                   I.drift(1.0), I.aperture(0.01), I.dipedge(-1 / 300, 0.05, 0.03, 0.5), I.marker()])
     p = random_particles(PROTON, 1000, 6, sx=3e-3)
     g, o = gpu_track(el, PROTON, p, 25), oracle.track(el, PROTON, p, 25)
-    assert_same(g, o)
+    assert_close(g, o)
     assert np.any(o["state"] == 0) and np.any(o["state"] == 1)
 
 
-def test_misaligned_elements_and_aperture_shapes_bitwise():
+def test_misaligned_elements_and_aperture_shapes():
     """Misaligned and tilted quadrupoles and sextupoles (shift + rotation
     frames), and the paper's loss-location setting: a rectangular aperture
     followed by an elliptic one, shifted and tilted with respect to each
-    other.  2,000 particles (a ragged last warp), 150 turns, bit for bit."""
+    other.  2,000 particles (a ragged last warp), 150 turns."""
     qf = I.multipole(knl=[0.0, 0.2])
     qd = I.multipole(knl=[0.0, -0.2])
     sx = I.multipole(knl=[0.0, 0.0, 0.05], ksl=[0.0, 0.0, 0.01])
@@ -119,7 +176,7 @@ def test_misaligned_elements_and_aperture_shapes_bitwise():
     el = I.table(rows)
     p = random_particles(PROTON, 2000, 31, sx=1.6e-3, spx=8e-5, sd=2e-4)
     g, o = gpu_track(el, PROTON, p, 150), oracle.track(el, PROTON, p, 150)
-    assert_same(g, o)
+    assert_close(g, o)
     rect_at = len(rows) - 9  # [shift, rotation, aperture, rotation, shift] x 2 with a drift between
     ell_at = len(rows) - 3
     lost = o["state"] == 0
@@ -127,8 +184,21 @@ def test_misaligned_elements_and_aperture_shapes_bitwise():
     assert np.sum(o["state"] == 1) > 500
 
 
-def test_refine_losses_bitwise():
-    """Loss-location refinement on the GPU against the oracle, bit for bit:
+def assert_refined_close(s_g, s_o, ds):
+    """Refined loss positions: NaN for the same particles; each position is
+    the end of the first ds-step found outside the aperture polygon, so the
+    two sides agree to rounding unless a step end lies within rounding of
+    the polygon -- then they differ by one step.  At least 99.9 % must agree
+    to 1e-9 m and the rest within one step."""
+    assert np.array_equal(np.isnan(s_g), np.isnan(s_o))
+    f = ~np.isnan(s_o)
+    d = np.abs(s_g[f] - s_o[f])
+    assert np.mean(d <= 1e-9) >= 0.999, np.sort(d)[-5:]
+    assert np.all(d <= ds * (1 + 1e-9) + 1e-9), d.max()
+
+
+def test_refine_losses():
+    """Loss-location refinement on the GPU against the oracle:
     a misaligned FODO ring with a rectangular then an elliptic aperture
     (shifted and tilted with respect to each other) and circular apertures
     in the cells, particles lost over 40 turns, refined to 1 cm with
@@ -153,8 +223,7 @@ def test_refine_losses_bitwise():
     P = xtgb.Particles.from_numpy(o)
     s_g = tr.refine_losses(P, 0.01, 128).cpu().numpy()
     tr.close()
-    same = (s_g == s_o) | (np.isnan(s_g) & np.isnan(s_o))
-    assert np.all(same), np.flatnonzero(~same)[:5]
+    assert_refined_close(s_g, s_o, 0.01)
     assert np.all(np.isnan(s_o[o["state"] != 0])) and not np.any(np.isnan(s_o[o["state"] == 0]))
     # a linear map between two apertures: no inverse, NaN on both sides
     el2 = I.table([I.aperture(0.01), I.drift(1.0), I.linear_map(np.eye(6)), I.drift(1.0), I.aperture(0.01)])
@@ -183,22 +252,22 @@ def thick_quad_ring(n_cells=8, aperture=0.006):
     return rows
 
 
-def test_thick_quadrupole_ring_bitwise():
-    """2,000 particles (5e-4 momentum spread, so a crosses 1/2 differently
-    per particle), 120 turns through a ring of thick quadrupoles, bit for bit
-    with the oracle, losses included."""
+def test_thick_quadrupole_ring():
+    """2,000 particles (5e-4 momentum spread), 120 turns through a ring of
+    thick quadrupoles (the series and the trigonometric and hyperbolic
+    branches of the kernel's oscillator functions), losses included."""
     el = I.table(thick_quad_ring())
     p = random_particles(PROTON, 2000, 47, sx=1.5e-3, spx=8e-5, sd=5e-4)
     g, o = gpu_track(el, PROTON, p, 120), oracle.track(el, PROTON, p, 120)
-    assert_same(g, o)
+    assert_close(g, o)
     assert 200 < np.sum(o["state"] == 1) < 1800
 
 
-def test_refine_losses_through_thick_quadrupoles_bitwise():
+def test_refine_losses_through_thick_quadrupoles():
     """Loss refinement that steps through thick quadrupole bodies (the
     quadrupole's flow in steps of ds) and backtracks through them (the flow
-    with -L), GPU against oracle bit for bit; some refined losses lie inside
-    a quadrupole."""
+    with -L), GPU against oracle; some refined losses lie inside a
+    quadrupole."""
     rows = thick_quad_ring(n_cells=6, aperture=0.0055)
     el = I.table(rows)
     p = random_particles(PROTON, 3000, 53, sx=1.6e-3, spx=8e-5, sd=3e-4)
@@ -208,8 +277,7 @@ def test_refine_losses_through_thick_quadrupoles_bitwise():
     tr = xtgb.Tracker(el, PROTON)
     s_g = tr.refine_losses(xtgb.Particles.from_numpy(o), 0.01, 128).cpu().numpy()
     tr.close()
-    same = (s_g == s_o) | (np.isnan(s_g) & np.isnan(s_o))
-    assert np.all(same), np.flatnonzero(~same)[:5]
+    assert_refined_close(s_g, s_o, 0.01)
     pos, body = 0.0, []
     for r in rows:
         L = float(r["p"][0]) if int(r["type"]) == I.DRIFT else (float(r["p"][1]) if int(r["type"]) == I.QUAD else 0.0)
@@ -236,22 +304,22 @@ def bend_ring(n_cells=8, aperture=0.02):
     return rows
 
 
-def test_thick_bend_ring_bitwise():
+def test_thick_bend_ring():
     """2,000 particles (plus a few at steep angles) for 100 turns through
-    full and expanded bends, bit for bit with the oracle, losses included."""
+    full and expanded bends, losses included."""
     el = I.table(bend_ring())
     p = random_particles(PROTON, 2000, 59, sx=5e-3, spx=2.5e-3, sd=1e-3)
     for i, (px, py) in enumerate([(0.9, 0.0), (-0.9, 0.1), (0.3, 0.95), (0.99, 0.0)]):
         p["px"][i], p["py"][i] = px, py
     g, o = gpu_track(el, PROTON, p, 100), oracle.track(el, PROTON, p, 100)
-    assert_same(g, o)
+    assert_close(g, o)
     assert 200 < np.sum(o["state"] == 1) < 1900
 
 
-def test_refine_losses_through_thick_bends_bitwise():
+def test_refine_losses_through_thick_bends():
     """Refinement stepping through full and expanded bend bodies and
-    backtracking through them with -L, GPU against oracle bit for bit; some
-    refined losses lie inside a bend."""
+    backtracking through them with -L, GPU against oracle; some refined
+    losses lie inside a bend."""
     rows = bend_ring(n_cells=6, aperture=0.012)
     el = I.table(rows)
     p = random_particles(PROTON, 3000, 61, sx=5e-3, spx=2.5e-3, sd=1e-3)
@@ -261,8 +329,7 @@ def test_refine_losses_through_thick_bends_bitwise():
     tr = xtgb.Tracker(el, PROTON)
     s_g = tr.refine_losses(xtgb.Particles.from_numpy(o), 0.01, 128).cpu().numpy()
     tr.close()
-    same = (s_g == s_o) | (np.isnan(s_g) & np.isnan(s_o))
-    assert np.all(same), np.flatnonzero(~same)[:5]
+    assert_refined_close(s_g, s_o, 0.01)
     pos, body = 0.0, []
     for r in rows:
         t = int(r["type"])
@@ -274,11 +341,11 @@ def test_refine_losses_through_thick_bends_bitwise():
     assert sum(np.sum((lost > a + 1e-9) & (lost < b - 1e-9)) for a, b in body) > 20
 
 
-def test_nonlinear_dipole_edges_bitwise():
+def test_nonlinear_dipole_edges():
     """Rectangular bends: non-linear entrance and exit edges (face angle
     theta/2, fint * hgap set) around full-model bends, linear edges around
     the expanded ones, in the small ring; 2,000 particles at up to 5 mrad
-    plus a few steep ones, 100 turns, bit for bit."""
+    plus a few steep ones, 100 turns."""
     h = 1 / 1.5
     th = h * 0.9
     rows = [I.cavity(2e6, 400e6, 180.0)]
@@ -295,14 +362,15 @@ def test_nonlinear_dipole_edges_bitwise():
     for i, (px, py) in enumerate([(0.3, 0.2), (-0.5, 0.1), (0.05, 0.9)]):
         p["px"][i], p["py"][i] = px, py
     g, o = gpu_track(el, PROTON, p, 100), oracle.track(el, PROTON, p, 100)
-    assert_same(g, o)
+    assert_close(g, o)
     assert 100 < np.sum(o["state"] == 1) < 1950
 
 
-def test_space_charge_lenses_bitwise():
+def test_space_charge_lenses():
     """Frozen space-charge lenses (bunched flat, coasting round, off-centre
     tall) in FODO-10 at 2 GeV/c: 1,500 particles with a zeta spread across
-    the bunch, 200 turns, bit for bit."""
+    the bunch, against the oracle's field by quadrature of its single-integral
+    form."""
     el0, _ = I.fodo10()
     ref = I.proton_reference(2e9)
     rows = []
@@ -316,12 +384,12 @@ def test_space_charge_lenses_bitwise():
     rows.append(I.aperture(0.01))
     el = I.table(rows)
     p = random_particles(ref, 1500, 101, sx=2.5e-3, spx=2e-4, sz=0.5, sd=5e-4)
-    g, o = gpu_track(el, ref, p, 200), oracle.track(el, ref, p, 200)
-    assert_same(g, o)
+    g, o = gpu_track(el, ref, p, SC_TURNS), oracle.track_parallel(el, ref, p, SC_TURNS)
+    assert_close(g, o)
 
 
-def test_thick_element_edge_cases_bitwise():
-    """Degenerate and extreme thick rows, bit for bit: a quadrupole without
+def test_thick_element_edge_cases():
+    """Degenerate and extreme thick rows: a quadrupole without
     gradient, one of zero length, strong ones past |z| = 1 (trigonometric
     and exponential branches); full bends without field (a curved drift),
     without curvature (a straight dipole), with the field reversed, of
@@ -346,7 +414,7 @@ def test_thick_element_edge_cases_bitwise():
     # second pass loses them all in the full bend (code -2)
     for turns, want in ((1, 1), (2, -2)):
         g, o = gpu_track(el, PROTON, p, turns), oracle.track(el, PROTON, p, turns)
-        assert_same(g, o)
+        assert_close(g, o)
         assert np.all(o["state"] == want)
 
 
@@ -354,11 +422,12 @@ def bb_lens(qN, beta_s, sx, sy, xc=0.0, yc=0.0):
     return I.beambeam4d(qN, beta_s, sx, sy, xc, yc)
 
 
-def test_beambeam_lenses_bitwise():
+def test_beambeam_lenses():
     """4D beam-beam lenses (round, flat and tall strong bunches, one off
     centre) in a FODO ring with sextupoles: 1,500 particles spanning the
-    lenses' linear cores and tails, 300 turns, bit for bit (the Faddeeva
-    function and the exponential are the same evaluation on both sides)."""
+    lenses' linear cores and tails, 300 turns.  The kernel's field comes
+    from Weideman's w(z), the oracle's from quadrature of the field's
+    single-integral form."""
     rows = [I.cavity(2e6, 400e6, 180.0)]
     lenses = [bb_lens(1.5e11, 1.0, 0.4e-3, 0.4e-3), bb_lens(1.5e11, 1.0, 0.8e-3, 0.25e-3, 5e-5, -2e-5),
               bb_lens(-1.0e11, 0.9999, 0.3e-3, 0.9e-3, -1e-4, 3e-5)]
@@ -371,12 +440,12 @@ def test_beambeam_lenses_bitwise():
         rows += [I.drift(2.0), I.aperture(0.01)]
     el = I.table(rows)
     p = random_particles(PROTON, 1500, 43, sx=8e-4, spx=5e-5, sd=2e-4)
-    g, o = gpu_track(el, PROTON, p, 300), oracle.track(el, PROTON, p, 300)
-    assert_same(g, o)
+    g, o = gpu_track(el, PROTON, p, 300), oracle.track_parallel(el, PROTON, p, 300)
+    assert_close(g, o)
     assert np.sum(o["state"] == 1) > 300
 
 
-def test_lhc_ring_sample_bitwise():
+def test_lhc_ring_sample():
     """LHC-scale ring (20,000 elements, order-10 errors, RF, apertures):
     500 DA-grid particles at large amplitude (some are lost), 5 turns."""
     el, ref = I.lhc_ring()
@@ -384,12 +453,13 @@ def test_lhc_ring_sample_bitwise():
     idx = np.random.default_rng(1).choice(np.flatnonzero(g["grid"][0] > 14.0), 500, replace=False)
     p = I.subset(g, np.sort(idx))
     go, oo = gpu_track(el, ref, p, 5), oracle.track(el, ref, p, 5)
-    assert_same(go, oo)
+    assert_close(go, oo)
 
 
 def test_lhc_ring_full_size_sampled():
     """All 999,990 DA-grid particles in the default launch configuration for
-    2 turns; 200 sampled particles (incl. lost ones) checked bit for bit."""
+    2 turns; 200 sampled particles (incl. lost ones) checked against the
+    oracle."""
     el, ref = I.lhc_ring()
     g = I.da_grid(el, ref)
     full = I.subset(g, np.arange(g["x"].shape[0]))
@@ -400,15 +470,15 @@ def test_lhc_ring_full_size_sampled():
                            rng.choice(out["x"].shape[0], 160, replace=False)])
     pick = np.unique(pick)
     o = oracle.track(el, ref, I.subset(full, pick), 2)
-    assert_same({k: out[k][pick] for k in FIELDS}, o)
+    assert_close({k: out[k][pick] for k in FIELDS}, o)
 
 
-def test_lepton_mean_radiation_bitwise():
+def test_lepton_mean_radiation():
     el, ref, _ = I.lepton_ring()
     p = I.matched_gaussian(el, ref, 256, 0.0, 1e-3, seed=3, emit_x=2e-9, emit_y=2e-11)
     g = gpu_track(el, ref, p, 20, radiation=xtgb.RAD_MEAN)
     o = oracle.track(el, ref, p, 20, rad_mode=1)
-    assert_same(g, o)
+    assert_close(g, o)
     assert np.all(o["ptau"] != p["ptau"])
 
 
@@ -426,7 +496,7 @@ def test_segmentation_block_chunk_invariance():
     tr.track(P, 5, 0)
     tr.track(P, 7, 5)
     assert_same(P.to_numpy(), base, "5+7 turns: ")
-    assert_same(base, oracle.track(el, ref, p, 12))
+    assert_close(base, oracle.track(el, ref, p, 12))
 
 
 def test_edge_cases():
@@ -445,7 +515,7 @@ def test_edge_cases():
     p["py"][6] = 0.9
     g = gpu_track(el, ref, p, 50, start_turn=123)
     o = oracle.track(el, ref, p, 50, start_turn=123)
-    assert_same(g, o)
+    assert_close(g, o)
     assert g["state"][6] == -2 and g["at_turn"][6] == 123
     assert g["state"][5] == -2  # NaN reaches px at the first quadrupole, then fails the drift
     assert np.all(g["at_turn"][::7] == 3)
@@ -453,7 +523,7 @@ def test_edge_cases():
     mk = I.table([I.marker(), I.marker()])
     q = random_particles(ref, 64, 12)
     q["x"][0] = 2.0
-    assert_same(gpu_track(mk, ref, q, 3), oracle.track(mk, ref, q, 3))
+    assert_close(gpu_track(mk, ref, q, 3), oracle.track(mk, ref, q, 3))
     # zero turns leaves everything untouched
     assert_same(gpu_track(el, ref, q, 0), q)
 
@@ -488,7 +558,7 @@ def test_batched_seeds_equal_individual():
         for i in range(len(counts)):
             assert_same(P[i].to_numpy(), ref_out[i], "seed %d graph %d: " % (i, graph))
     el0, ref0 = I.lhc_ring(seed=I.BASE_SEED + 1, n_cells=4, error_scales=I.seed_error_scales(1)[0])
-    assert_same(ref_out[1], oracle.track(el0, ref0, ps[1], 30))
+    assert_close(ref_out[1], oracle.track(el0, ref0, ps[1], 30))
     xtgb.batched_release()
     for t in trs:
         t.close()
@@ -497,7 +567,9 @@ def test_batched_seeds_equal_individual():
 def test_batched_mixed_thin_and_thick_seeds():
     """A batch mixing a thin-lattice seed with thick-element seeds runs the
     thick instantiation of the batched kernel for all of them: plain and
-    graph launches equal per-seed tracking and the oracle, bit for bit."""
+    graph launches equal per-seed tracking bit for bit (the thin seed runs
+    the thin instantiation alone, with the same maps), and per-seed
+    tracking matches the oracle."""
     seeds = [(I.table(bend_ring(n_cells=4)), PROTON, 700, 3e-3),
              (I.table(thick_quad_ring(n_cells=5)), PROTON, 1300, 1.2e-3),
              (I.fodo10()[0], PROTON, 250, 3e-3)]
@@ -506,7 +578,8 @@ def test_batched_mixed_thin_and_thick_seeds():
         p = random_particles(ref, n, 200 + i, sx=sx, spx=sx / 3, sd=5e-4)
         trs.append(xtgb.Tracker(el, ref))
         ps.append(p)
-        ref_out.append(oracle.track(el, ref, p, 40))
+        ref_out.append(gpu_track(el, ref, p, 40))
+        assert_close(ref_out[-1], oracle.track(el, ref, p, 40), where="seed %d: " % i)
     for graph in (False, True):
         P = [xtgb.Particles.from_numpy(p) for p in ps]
         xtgb.track_batched(trs, P, 15, 0, graph=graph)
@@ -522,7 +595,8 @@ def test_batched_mixed_thin_and_thick_seeds():
 def test_batched_seeds_with_quantum_radiation():
     """Quantum radiation in a batch of two lepton rings, one with thick rows
     (so the batch runs the radiating thick instantiation): plain and graph
-    launches equal per-seed tracking and the oracle, bit for bit."""
+    launches equal per-seed tracking bit for bit, and per-seed tracking
+    matches the oracle (the same Philox numbers on both sides)."""
     el0, ref, _ = I.lepton_ring(n_cells=4, E0=5e9, v_total=30e6)
     rows = list(el0)
     thick = I.table(rows[:20] + [I.quadrupole(0.02, 0.5), I.quadrupole(-0.02, 0.5)] + rows[20:])
@@ -532,7 +606,8 @@ def test_batched_seeds_with_quantum_radiation():
         q = I.matched_gaussian(el0, ref, n, 1e-3, 1e-3, seed=300 + i)
         trs.append(xtgb.Tracker(el, ref, radiation=xtgb.RAD_QUANTUM, seed=17))
         ps.append(q)
-        ref_out.append(oracle.track(el, ref, q, 20, rad_mode=2, seed=17))
+        ref_out.append(gpu_track(el, ref, q, 20, radiation=xtgb.RAD_QUANTUM, seed=17))
+        assert_close(ref_out[-1], oracle.track(el, ref, q, 20, rad_mode=2, seed=17), where="seed %d: " % i)
     for graph in (False, True):
         P = [xtgb.Particles.from_numpy(q) for q in ps]
         xtgb.track_batched(trs, P, 8, 0, graph=graph)
@@ -546,10 +621,10 @@ def test_batched_seeds_with_quantum_radiation():
 
 
 @pytest.mark.parametrize("rad", [1, 2])
-def test_radiation_with_thick_elements_bitwise(rad):
+def test_radiation_with_thick_elements(rad):
     """A small lepton ring with thick quadrupoles, a full bend between
     non-linear edges and a beam-beam lens added, mean and quantum radiation
-    (the radiating instantiations of the thick kernel): bit for bit."""
+    (the radiating instantiations of the thick kernel)."""
     el0, ref, _ = I.lepton_ring(n_cells=4, E0=5e9, v_total=30e6)
     rows = list(el0)
     h = 0.01
@@ -561,13 +636,15 @@ def test_radiation_with_thick_elements_bitwise(rad):
     q = I.matched_gaussian(el0, ref, 800, 1e-3, 1e-3, seed=11)
     g = gpu_track(el, ref, q, 25, radiation=rad, seed=3)
     o = oracle.track(el, ref, q, 25, rad_mode=rad, seed=3)
-    assert_same(g, o)
+    assert_close(g, o)
 
 
-def test_quantum_radiation_bitwise_and_distribution():
-    """Quantum model: reproducible bit for bit on the GPU for a given seed,
-    segmentation-independent, equal to the oracle bit for bit, and the energy
-    spread after emission in one dipole slice has the closed-form variance."""
+def test_quantum_radiation_reproducible_and_in_distribution():
+    """Quantum model: reproducible bit for bit on the GPU for a given seed and
+    segmentation-independent; in distribution, the energy lost in one dipole
+    slice matches the oracle's (two-sample KS) and has the closed-form
+    variance n u_c^2 11/27; per particle, the same Philox numbers drive both
+    sides to the same photons."""
     ref = I.electron_reference(45.6e9)
     theta, L = 2 * math.pi / 2400, 3.575
     el = I.table([I.multipole(knl=[theta], hxl=theta, lrad=L)])
@@ -586,9 +663,11 @@ def test_quantum_radiation_bitwise_and_distribution():
     nbar = 5 / (2 * math.sqrt(3)) * 7.2973525693e-3 * g * h * L
     uc = 1.5 * 197.3269804e-9 * g ** 3 * h
     assert dg.var() == pytest.approx(nbar * 11 / 27 * uc ** 2, rel=0.02)
-    # same Philox counters, Poisson inversion with the same exponential, and
-    # spectrum tables built by the same steps: every particle bit for bit
-    assert_same({k: v[:do.size] for k, v in g1.items()}, o)
+    assert do.var() == pytest.approx(nbar * 11 / 27 * uc ** 2, rel=0.03)
+    assert dg.mean() == pytest.approx(nbar * 8 / (15 * math.sqrt(3)) * uc, rel=0.01)
+    # per particle: the photon count and each photon's energy come from the
+    # same counter-based draws on both sides
+    assert_close({k: v[:do.size] for k, v in g1.items()}, o)
     # segment resume on a small ring with quantum radiation
     el2, ref2, _ = I.lepton_ring(n_cells=4, E0=5e9, v_total=30e6)
     q = I.matched_gaussian(el2, ref2, 500, 1e-3, 1e-3, seed=7)
@@ -613,11 +692,11 @@ def test_cycle_budget_and_cancel_return_status():
     assert np.all(out["state"] == 1)
     stopped = out["at_turn"]
     assert np.all((stopped > 0) & (stopped < 200000))
-    # resume each particle from its own turn: equal to the oracle
+    # the stopped particles are where the oracle is after their own turn count
     first = int(stopped.min())
     o = oracle.track(el, ref, p, first)
     sel = np.flatnonzero(stopped == first)
-    assert_same({k: out[k][sel] for k in FIELDS}, {k: o[k][sel] for k in FIELDS})
+    assert_close({k: out[k][sel] for k in FIELDS}, {k: o[k][sel] for k in FIELDS})
     tr.close()
     tr = xtgb.Tracker(el, ref)
     tr.cancel()
@@ -628,7 +707,7 @@ def test_cycle_budget_and_cancel_return_status():
     P = xtgb.Particles.from_numpy(p)
     tr.track(P, 100)
     assert tr.sync_status() == xtgb.XT_OK
-    assert_same(P.to_numpy(), oracle.track(el, ref, p, 100))
+    assert_close(P.to_numpy(), oracle.track(el, ref, p, 100))
 
 
 def test_autotune_keeps_results():
@@ -640,7 +719,9 @@ def test_autotune_keeps_results():
     assert opts["block"] in (64, 128, 256) and opts["chunk_bytes"] in (2048, 4096, 8192, 16384)
     P = xtgb.Particles.from_numpy(p)
     tr.track(P, 6)
-    assert_same(P.to_numpy(), oracle.track(el, ref, p, 6))
+    res = P.to_numpy()
+    assert_same(res, gpu_track(el, ref, p, 6))
+    assert_close(res, oracle.track(el, ref, p, 6))
     assert_same(probe.to_numpy(), {k: np.asarray(p[k]) for k in FIELDS})
 
 
@@ -648,7 +729,7 @@ def test_lepton_quantum_full_size_sampled():
     """The 45.6 GeV lepton ring (10,000 rows) with mean radiation and quantum
     excitation: 200,000 matched particles for 2 turns in the default launch
     configuration, as the benchmark times it; about 120 sampled particles
-    (lost ones included) checked bit for bit against the oracle."""
+    (lost ones included) checked against the oracle."""
     el, ref, _ = I.lepton_ring()
     n = 200000
     p = I.matched_gaussian(el, ref, n, 0.0, 1.06e-3, seed=5, emit_x=2 * 3.9e-8, emit_y=2 * 3.9e-10)
@@ -658,7 +739,7 @@ def test_lepton_quantum_full_size_sampled():
     pick = np.unique(np.concatenate([rng.choice(lost, min(20, lost.size), replace=False),
                                      rng.choice(n, 100, replace=False)]))
     o = oracle.track(el, ref, I.subset(p, pick), 2, rad_mode=2, seed=1)
-    assert_same({k: out[k][pick] for k in FIELDS}, o)
+    assert_close({k: out[k][pick] for k in FIELDS}, o)
     assert np.all(o["ptau"][o["state"] == 1] != p["ptau"][pick][o["state"] == 1])
 
 
@@ -667,7 +748,7 @@ def test_batched_seeds_full_size_sampled():
     counts round(10^U(3,5)), 1.74e6 particles: the autotuned options on a
     65,536-particle probe, then one batched launch of 2 turns in a CUDA graph,
     as the benchmark times it; per seed a lost particle (if any) and a random
-    one checked bit for bit against the oracle."""
+    one checked against the oracle."""
     counts = I.batched_seed_counts(64)
     el0, ref = I.lhc_ring(seed=I.BASE_SEED)
     optics = I.design_optics(el0, ref)
@@ -692,7 +773,7 @@ def test_batched_seeds_full_size_sampled():
         n_lost += lost.size
         pick = np.unique(np.concatenate([lost[:1], rng.choice(int(counts[i]), 1)]))
         o = oracle.track(els[i], ref, I.subset(ps[i], pick), 2)
-        assert_same({k: g[k][pick] for k in FIELDS}, o, "seed %d: " % i)
+        assert_close({k: g[k][pick] for k in FIELDS}, o, where="seed %d: " % i)
     assert n_lost > 0
     xtgb.batched_release()
     for t in trs:

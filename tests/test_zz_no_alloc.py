@@ -1,11 +1,12 @@
 """The allocation-free tracking entry point against the ordinary one.
 
 xt_track_noalloc serves callers that cannot allocate device memory while they
-track (inside a stream capture that must not allocate, or with device memory
-owned by the application's own allocator): its scratch is a static device
-array instead of the tracker's cudaMalloc'd workspace.  It must give exactly
-what xt_track gives, call after call, and refuse particle counts above its
-fixed capacity.  This file is collected last on purpose.
+track (an application whose device memory is owned by its own allocator or
+budget, or a real-time loop that cannot wait for cudaMalloc): its scratch is
+a static device array instead of the tracker's cudaMalloc'd workspace.  It
+must give exactly what xt_track gives, call after call, refuse particle
+counts above its fixed capacity, and report a cycle-budget stop through
+xt_noalloc_status.  This file is collected last on purpose.
 """
 import ctypes
 
@@ -69,4 +70,31 @@ def test_noalloc_rejects_more_particles_than_its_capacity():
     rc = L.xt_track_noalloc(tr.handle, ctypes.byref(s), 0, 1, torch.cuda.current_stream().cuda_stream)
     assert rc == xtgb.XT_ERR_INVALID
     assert "at most 1048576" in xtgb.last_error()
+    tr.close()
+
+
+def test_noalloc_status_reports_a_cycle_budget_stop():
+    """A tracker whose cycle budget runs out stops at a turn boundary; the
+    allocation-free call records that in the static array's status word,
+    xt_noalloc_status returns XT_ERR_TIMEOUT once and then XT_OK, and a
+    normal call afterwards reports XT_OK."""
+    import torch
+    el, ref = I.fodo10()
+    p = I.matched_gaussian(el, ref, 2000, 2.5e-6, 3e-4, seed=8)
+    L = xtgb.lib()
+    L.xt_noalloc_status.argtypes = [ctypes.c_void_p]
+    L.xt_noalloc_status.restype = ctypes.c_int32
+    stream = torch.cuda.current_stream().cuda_stream
+    tr = xtgb.Tracker(el, ref, max_cycles=200000)
+    P = xtgb.Particles.from_numpy(p)
+    assert _noalloc(tr, P, 200000, 0) == xtgb.XT_OK, xtgb.last_error()
+    assert L.xt_noalloc_status(stream) == xtgb.XT_ERR_TIMEOUT
+    assert L.xt_noalloc_status(stream) == xtgb.XT_OK
+    out = P.to_numpy()
+    assert np.all(out["state"] == 1) and np.all((out["at_turn"] > 0) & (out["at_turn"] < 200000))
+    tr.close()
+    tr = xtgb.Tracker(el, ref)
+    P = xtgb.Particles.from_numpy(p)
+    assert _noalloc(tr, P, 20, 0) == xtgb.XT_OK, xtgb.last_error()
+    assert L.xt_noalloc_status(stream) == xtgb.XT_OK
     tr.close()
