@@ -167,10 +167,12 @@ def _passes(before, after, start, T, n_el):
     return int(surv.sum()) * T * n_el + int(((at[lost] - start) * n_el + ae[lost] + 1).sum())
 
 
-def measure_batched(T=2, steps=3):
+def measure_batched(T=20, steps=5, plain_steps=1):
     """64 error seeds of the LHC-scale ring, uneven particle counts
-    round(10^U(3,5)), one persistent launch per turn; with and without the
-    CUDA graph."""
+    round(10^U(3,5)), one persistent launch per segment: `steps` x T turns
+    replayed from a CUDA graph (100 turns by default, so that seeds losing
+    particles at different rates show in the (seed, tile) queue's balance),
+    then `plain_steps` x T turns without the graph."""
     import torch
     from paper_2310_00317_gb300 import inputs as I
     from paper_2310_00317_gb300 import xtgb
@@ -206,7 +208,8 @@ def measure_batched(T=2, steps=3):
     turn += T
     for graph in (True, False):
         ms, units = 0.0, 0
-        for _ in range(steps):
+        n_steps = steps if graph else plain_steps
+        for _ in range(n_steps):
             before = [P.t["state"].cpu().numpy() for P in ps]
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
@@ -219,13 +222,71 @@ def measure_batched(T=2, steps=3):
                 units += _passes(b, {k: P.t[k].cpu().numpy() for k in ("state", "at_turn", "at_element")},
                                  turn, T, n_el)
             turn += T
-        out["graph" if graph else "no_graph"] = {"value": units / (ms * 1e-3), "ms_per_step": ms / steps}
+        out["graph" if graph else "no_graph"] = {"value": units / (ms * 1e-3), "ms_per_step": ms / n_steps,
+                                                 "turns": [turn - n_steps * T, turn],
+                                                 "alive_at_end": int(sum(int((P.t["state"] == 1).sum()) for P in ps))}
     if xtgb.batched_sync_status(trs, ps) != xtgb.XT_OK:
         raise RuntimeError("batched tracking reported an error status")
     xtgb.batched_release()
     for t in trs:
         t.close()
     out["unit"] = UNIT
+    return out
+
+
+def measure_steady(turns=200, window=50, n=0):
+    """The headline workload from turn 0 through the DA-boundary losses: a
+    fresh copy of the full grid tracked `turns` turns in windows of `window`
+    turns (one xt_track call each, the tracker's own segmentation and
+    compaction inside), the rate, alive count and FP64 fraction per window."""
+    import torch
+    from paper_2310_00317_gb300 import inputs as I
+    from paper_2310_00317_gb300 import xtgb
+    el, ref = I.lhc_ring(seed=I.BASE_SEED)
+    n_el = el.shape[0]
+    grid = I.da_grid(el, ref)
+    N = grid["x"].shape[0]
+    sel = np.arange(N) if n <= 0 or n >= N else np.unique(np.linspace(0, N - 1, n).astype(np.int64))
+    tr = xtgb.Tracker(el, ref)
+    fprefix = np.cumsum(tr.element_flops().astype(np.float64))
+    P = xtgb.Particles.from_numpy(I.subset(grid, sel))
+    out = {"workload": WORKLOAD if sel.size == N else WORKLOAD + " (evenly spaced subset of %d)" % sel.size,
+           "turns": turns, "window_turns": window, "windows": []}
+    tr.set_profiling(True)
+    tr.kernel_time()
+    ms_all, units_all, flops_all = 0.0, 0, 0.0
+    for start in range(0, turns, window):
+        T = min(window, turns - start)
+        before = P.t["state"].cpu().numpy()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        tr.track(P, T, start)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        kms, _ = tr.kernel_time()
+        after = {k: P.t[k].cpu().numpy() for k in ("state", "at_turn", "at_element")}
+        alive0 = before == 1
+        surv = alive0 & (after["state"] == 1)
+        lost = alive0 & (after["state"] != 1)
+        at, ae = after["at_turn"].astype(np.int64), after["at_element"].astype(np.int64)
+        units = int(surv.sum()) * T * n_el + int(((at[lost] - start) * n_el + ae[lost] + 1).sum())
+        flops = float(surv.sum()) * T * fprefix[-1] + float(((at[lost] - start) * fprefix[-1] + fprefix[ae[lost]]).sum())
+        out["windows"].append({"turns": [start, start + T], "alive_at_end": int(surv.sum()),
+                               "value": units / (ms * 1e-3), "frac": flops / (kms * 1e-3) / NOMINAL_FP64,
+                               "ms": ms})
+        ms_all += ms
+        units_all += units
+        flops_all += flops
+    tr.set_profiling(False)
+    if tr.sync_status() != xtgb.XT_OK:
+        raise RuntimeError("tracking reported an error status")
+    tr.close()
+    out.update(value=units_all / (ms_all * 1e-3), unit=UNIT, seconds=ms_all * 1e-3,
+               roofline={"bound": "alu", "achieved": flops_all / (ms_all * 1e-3) / 1e12, "peak": NOMINAL_FP64 / 1e12,
+                         "unit": "TFLOP/s", "frac": flops_all / (ms_all * 1e-3) / NOMINAL_FP64,
+                         "note": "achieved over the windows' whole event-timed duration, compaction included"})
     return out
 
 
@@ -390,6 +451,104 @@ def measure_lepton(n=200000, turns=10):
                                  "look-ups that count no FP64 flops"}}
 
 
+def measure_lepton_equilibrium(n=200000, turns=2000, every=10, tail=500):
+    """The lepton ring with mean radiation and quantum excitation at its
+    stated size: 200,000 electrons started at twice the equilibrium
+    emittance in both planes and twice the longitudinal one, tracked 2000
+    turns.  eps_x, eps_y and sigma_delta are read every `every` turns at
+    element 0 (betatron parts about the dispersion), averaged over the last
+    `tail` turns and compared with the synchrotron integrals
+    eps_x = C_q gamma^2 I5 / (J_x I2) and sigma_delta^2 = C_q gamma^2 I3 / (J_z I2)
+    (I2, I3, I5 from the ring's dipole slices and the lattice functions that
+    the twiss module computes on the GPU, J_k = 4 alpha_k / sum alpha from
+    the one-turn damping decrements).  The damping times come from fits of
+    the decays against 1/alpha_k."""
+    import torch
+    from paper_2310_00317_gb300 import inputs as I
+    from paper_2310_00317_gb300 import twiss as TW
+    from paper_2310_00317_gb300 import xtgb
+    el, ref, info = I.lepton_ring()
+    m0, _, p0c = ref
+    gamma0 = math.sqrt(p0c * p0c + m0 * m0) / m0
+    t0 = time.perf_counter()
+    tw = TW.twiss_along(el, ref, dim=4)
+    dmp = TW.damping(el, ref)
+    I2 = I3 = I5 = 0.0
+    for i, r in enumerate(el):
+        if int(r["type"]) != I.MULTIPOLE or r["p"][23] <= 0.0 or r["p"][0] == 0.0:
+            continue
+        L = float(r["p"][23])
+        h = float(r["p"][0]) / L
+        b, a, d = tw["betx"][i + 1], tw["alfx"][i + 1], tw["dx"][i + 1]
+        dp = 0.5 * (tw["dpx"][i] + tw["dpx"][i + 1])  # the slope jumps across the thin slice
+        H = ((1 + a * a) / b) * d * d + 2 * a * d * dp + b * dp * dp
+        I2 += h * h * L
+        I3 += abs(h) ** 3 * L
+        I5 += H * abs(h) ** 3 * L
+    alpha = np.asarray(dmp["alpha"])
+    J = 4 * alpha / alpha.sum()
+    CQ = 55.0 / (32.0 * math.sqrt(3.0)) * 3.8615926796e-13  # hbar / (m_e c) in m
+    eps_th = CQ * gamma0 ** 2 * I5 / (J[0] * I2)
+    sd_th = math.sqrt(CQ * gamma0 ** 2 * I3 / (J[2] * I2))
+    optics_s = time.perf_counter() - t0
+    bx, ax, dx, dpx = tw["betx"][0], tw["alfx"][0], tw["dx"][0], tw["dpx"][0]
+    p = I.matched_gaussian(el, ref, n, 0.0, math.sqrt(2.0) * sd_th, seed=2025, emit_x=2 * eps_th,
+                           emit_y=2 * eps_th)
+    tr = xtgb.Tracker(el, ref, radiation=xtgb.RAD_QUANTUM, seed=77)
+    P = xtgb.Particles.from_numpy(p)
+
+    def emit(u, pu, d, alive):
+        u, pu = u[alive], pu[alive]
+        ub = u - u.mean()
+        pb = pu - pu.mean()
+        return float(torch.sqrt((ub * ub).mean() * (pb * pb).mean() - (ub * pb).mean() ** 2))
+
+    hist = []
+    ms_all = 0.0
+    for start in range(0, turns, every):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        tr.track(P, every, start)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_all += e0.elapsed_time(e1)
+        alive = P.t["state"] == 1
+        d = P.t["delta"]
+        ex = emit(P.t["x"] - dx * d, P.t["px"] - dpx * d, d, alive)
+        ey = emit(P.t["y"], P.t["py"], d, alive)
+        hist.append((start + every, ex, ey, float(d[alive].std()), int(alive.sum())))
+    if tr.sync_status() != xtgb.XT_OK:
+        raise RuntimeError("tracking reported an error status")
+    tr.close()
+    h = np.array(hist)
+    last = h[:, 0] > turns - tail
+    ex_m, ey_m, sd_m = h[last, 1].mean(), h[last, 2].mean(), h[last, 3].mean()
+    # damping times: eps - eps_end decays as exp(-2 t / tau) (amplitude decrement alpha = 1/tau)
+    early = h[:, 0] <= 600
+
+    def tau_fit(col, floor):
+        y = h[early, col] - floor
+        ok = y > 0
+        return -2.0 / np.polyfit(h[early, 0][ok], np.log(y[ok]), 1)[0]
+
+    tau_x = tau_fit(1, ex_m)
+    tau_y = tau_fit(2, 0.0)
+    tau_z = 2 * tau_fit(3, sd_m)  # sigma_delta is an amplitude: its excess decays as exp(-t / tau_z)
+    units = n * turns * el.shape[0]
+    return {"workload": "lepton ring 10,000 elements, 45.6 GeV electrons, mean radiation + quantum excitation, "
+                        "%d particles from 2x the equilibrium emittances, %d turns" % (n, turns),
+            "eps_x": {"tracked": ex_m, "integrals": eps_th, "rel": ex_m / eps_th - 1,
+                      "stat_error": math.sqrt(2.0 / n)},
+            "sigma_delta": {"tracked": sd_m, "integrals": sd_th, "rel": sd_m / sd_th - 1,
+                            "stat_error": math.sqrt(1.0 / (2 * n))},
+            "eps_y_tracked": ey_m,
+            "damping_turns": {"x": {"fit": tau_x, "eigen": 1 / alpha[0]}, "y": {"fit": tau_y, "eigen": 1 / alpha[1]},
+                              "z": {"fit": tau_z, "eigen": 1 / alpha[2]}},
+            "I2": I2, "I3": I3, "I5": I5, "J": J.tolist(), "optics_seconds": optics_s,
+            "tracking_seconds": ms_all * 1e-3, "value": units / (ms_all * 1e-3), "unit": UNIT,
+            "history_every_100_turns": [[int(r[0]), r[1], r[2], r[3]] for r in h[9::10]]}
+
+
 def measure_da_scan(n_turns=300):
     """Surrogate-guided DA scan against the plain FP64 scan at equal turns."""
     from paper_2310_00317_gb300 import surrogate as S
@@ -538,7 +697,7 @@ def run_ours(args):
     H = xtgb.HostParticles(host, copy=False)
     h2d = n * (9 * 8 + 3 * 4 + 8)
     d2h = n * (9 * 8 + 3 * 4)
-    e2e_steps = max(2, args.steps // 3)
+    e2e_steps = args.steps
     e_units = 0
     e_time = 0.0
     for s in range(e2e_steps):
@@ -558,6 +717,7 @@ def run_ours(args):
 
     extras = {}
     if ws == 1 and not args.no_extras:
+        extras["steady_state"] = measure_steady()
         extras["loss_refinement"] = measure_refinement(tr, H.a)
         extras["beambeam_lens"] = measure_beambeam()
         extras["thick_elements"] = measure_thick()
@@ -670,7 +830,8 @@ def main():
                     help="time only this many surrogate training steps (batch 4096)")
     ap.add_argument("--only", default="",
                     help="run one extra measurement alone and print its JSON: thick_elements[:n[:turns]], "
-                         "beambeam_lens[:n[:turns]], lepton_quantum[:n[:turns]] or twiss")
+                         "beambeam_lens[:n[:turns]], lepton_quantum[:n[:turns]], twiss, steady[:turns[:window]], "
+                         "batched_seeds[:turns_per_step:steps], lepton_equilibrium[:n[:turns]]")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -689,8 +850,15 @@ def run_only(spec: str) -> int:
         kw["n"] = int(nums[0])
     if len(nums) > 1:
         kw["turns"] = int(nums[1])
+    if name == "steady":
+        kw = {"turns": int(nums[0])} if nums else {}
+        if len(nums) > 1:
+            kw["window"] = int(nums[1])
+    elif name == "batched_seeds":
+        kw = {"T": int(nums[0]), "steps": int(nums[1])} if len(nums) > 1 else {}
     fn = {"thick_elements": measure_thick, "beambeam_lens": measure_beambeam, "twiss": measure_twiss,
-          "lepton_quantum": measure_lepton}.get(name)
+          "lepton_quantum": measure_lepton, "steady": measure_steady, "batched_seeds": measure_batched,
+          "lepton_equilibrium": measure_lepton_equilibrium}.get(name)
     if fn is None:
         raise SystemExit("--only: unknown measurement %r" % name)
     print(json.dumps({name: fn(**kw)}))

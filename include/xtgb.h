@@ -328,8 +328,11 @@ int xt_element_flops(const xt_tracker* tr, int64_t* flops_per_element, int64_t n
 int xt_set_profiling(xt_tracker* tr, int enable);
 int xt_kernel_time(xt_tracker* tr, double* total_ms, int64_t* launches);
 
-/* Diagnostic: FP64 fma throughput of the current device [flop/s] measured by a
-   kernel of independent fma chains on `stream` (blocks until done).         */
+/* Diagnostic: FP64 fma throughput of the current device [flop/s]: the
+   fastest of twelve probe launches (8 or 16 independent fma chains per
+   thread, shared or per-chain operands, 4, 8 or 16 blocks of 128 threads
+   per SM) on `stream`, blocking until done; *elapsed_ms is that launch's
+   duration.  Allocates a scratch buffer with cudaMalloc.                   */
 int xt_fp64_peak(double* flops_per_s, double* elapsed_ms, void* stream);
 
 /* Picks block size, chunk size and segment length by timing short probe runs

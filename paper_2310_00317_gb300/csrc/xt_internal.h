@@ -233,7 +233,7 @@ int launch_track_batched(const BatchArgs& a, int kind, int block, int grid, size
 int batched_occupancy(int kind, int block, size_t smem, int* blocks_per_sm);
 int device_sm_count(int* n);
 int device_smem_optin(int* bytes);
-int launch_fp64_probe(double* out, int grid, int block, int iters, void* stream);
+int launch_fp64_probe(double* out, int grid, int block, int iters, int variant, int* chains, void* stream);
 
 size_t track_smem_bytes(int block, int chunk_bytes);
 

@@ -1672,24 +1672,43 @@ int launch_tile_prefix(const int32_t* n_alive, const int32_t* order, int32_t n_s
 __global__ void set_int_kernel(int32_t* dst, int32_t v) { *dst = v; }
 
 // FP64 throughput probe: 16 independent fma chains per thread.
-__global__ void __launch_bounds__(256) fp64_probe_kernel(double* out, int iters) {
+// FP64 throughput probe: CH independent fma chains per thread, all operands
+// in registers.  MODE 0: a_j = a_j * m + c with m, c shared by the chains;
+// MODE 1: a_j = b_j * c_j + a_j with per-chain b_j, c_j (three distinct
+// register pairs per instruction).  The values stay finite and the chains
+// cannot be merged, so the kernel issues exactly CH fmas per iteration.
+template <int CH, int MODE>
+__global__ void __launch_bounds__(128) fp64_probe_kernel(double* out, int iters) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  double a[16];
+  double a[CH], b[CH], c[CH];
 #pragma unroll
-  for (int j = 0; j < 16; j++) a[j] = 1.0 + 1e-9 * (gid + j);
-  const double m = 0.9999999, c = 1e-7;
+  for (int j = 0; j < CH; j++) {
+    a[j] = 1.0 + 1e-9 * (gid + j);
+    b[j] = 1e-5 * (1.0 + 1e-3 * j + 1e-12 * gid);
+    c[j] = 1e-5 * (1.0 - 1e-3 * j);
+  }
+  const double m = 0.9999999 + 1e-17 * (threadIdx.x & 7), cc = 1e-7 * (1.0 + 1e-9 * (threadIdx.x & 3));
   for (int i = 0; i < iters; i++) {
 #pragma unroll
-    for (int j = 0; j < 16; j++) a[j] = fma(a[j], m, c);
+    for (int j = 0; j < CH; j++) a[j] = (MODE == 0) ? fma(a[j], m, cc) : fma(b[j], c[j], a[j]);
   }
   double s = 0.0;
 #pragma unroll
-  for (int j = 0; j < 16; j++) s += a[j];
+  for (int j = 0; j < CH; j++) s += a[j];
   out[gid] = s;
 }
 
-int launch_fp64_probe(double* out, int grid, int block, int iters, void* stream) {
-  fp64_probe_kernel<<<grid, block, 0, (cudaStream_t)stream>>>(out, iters);
+// variant: 0 = 8 chains shared operands, 1 = 16 chains shared operands,
+// 2 = 8 chains per-chain operands, 3 = 16 chains per-chain operands.
+// Returns the chains per thread through *chains.
+int launch_fp64_probe(double* out, int grid, int block, int iters, int variant, int* chains, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (variant) {
+    case 0: fp64_probe_kernel<8, 0><<<grid, block, 0, s>>>(out, iters); *chains = 8; break;
+    case 1: fp64_probe_kernel<16, 0><<<grid, block, 0, s>>>(out, iters); *chains = 16; break;
+    case 2: fp64_probe_kernel<8, 1><<<grid, block, 0, s>>>(out, iters); *chains = 8; break;
+    default: fp64_probe_kernel<16, 1><<<grid, block, 0, s>>>(out, iters); *chains = 16; break;
+  }
   return (int)cudaGetLastError();
 }
 
