@@ -533,7 +533,11 @@ def measure_lepton_equilibrium(n=200000, turns=2000, every=10, tail=500):
 
     tau_x = tau_fit(1, ex_m)
     tau_y = tau_fit(2, 0.0)
-    tau_z = 2 * tau_fit(3, sd_m)  # sigma_delta is an amplitude: its excess decays as exp(-t / tau_z)
+    # the longitudinal emittance goes as sigma_delta^2: its excess over the
+    # equilibrium decays as exp(-2 t / tau_z); fitted while it is well above
+    # the noise of the second moment (the first 300 turns)
+    zz = (h[:, 0] <= 300) & (h[:, 3] ** 2 > sd_m ** 2)
+    tau_z = -2.0 / np.polyfit(h[zz, 0], np.log(h[zz, 3] ** 2 - sd_m ** 2), 1)[0]
     units = n * turns * el.shape[0]
     return {"workload": "lepton ring 10,000 elements, 45.6 GeV electrons, mean radiation + quantum excitation, "
                         "%d particles from 2x the equilibrium emittances, %d turns" % (n, turns),
@@ -559,6 +563,21 @@ def measure_da_scan(n_turns=300):
                        "limits from plain scans of 3 validation seeds of the family on 2,222 radii, 4 test seeds "
                        "of the family each scanned on 22,222 radii x 45 angles (999,990 points), %d turns"
                        % n_turns)
+    return out
+
+
+def measure_da_scan_full(n_turns=100, base_mult=1.0):
+    """The surrogate-guided DA scan on the LHC-scale ring itself: a family of
+    64 error seeds of the 20,000-element ring, 5e6 labels from one batched
+    launch per segment, the full 999,990-point grid of the test seeds."""
+    from paper_2310_00317_gb300 import surrogate as S
+    r = S.da_study_full(n_turns=n_turns, base_mult=base_mult)
+    out = {k: v for k, v in r.items() if k not in ("loss_history",)}
+    out["workload"] = ("family of 64 error seeds of the LHC-scale ring (200 cells, 20,000 elements, orders 2..6 "
+                       "scaled log-uniformly in [0.5, 2] x %g): %d random-amplitude labels (momentum deviations "
+                       "N(0, 3e-4)) tracked by the batched tracker, band limits from plain scans of 3 validation "
+                       "seeds on 2,222 radii, 4 test seeds each scanned on the full grid of 22,222 radii x 9 angles "
+                       "x 5 momentum offsets (999,990 points), %d turns" % (base_mult, r["n_train"], n_turns))
     return out
 
 
@@ -856,9 +875,13 @@ def run_only(spec: str) -> int:
             kw["window"] = int(nums[1])
     elif name == "batched_seeds":
         kw = {"T": int(nums[0]), "steps": int(nums[1])} if len(nums) > 1 else {}
+    elif name == "da_scan_full":
+        kw = {"n_turns": int(nums[0])} if nums else {}
+        if len(nums) > 1:
+            kw["base_mult"] = float(nums[1])
     fn = {"thick_elements": measure_thick, "beambeam_lens": measure_beambeam, "twiss": measure_twiss,
           "lepton_quantum": measure_lepton, "steady": measure_steady, "batched_seeds": measure_batched,
-          "lepton_equilibrium": measure_lepton_equilibrium}.get(name)
+          "lepton_equilibrium": measure_lepton_equilibrium, "da_scan_full": measure_da_scan_full}.get(name)
     if fn is None:
         raise SystemExit("--only: unknown measurement %r" % name)
     print(json.dumps({name: fn(**kw)}))

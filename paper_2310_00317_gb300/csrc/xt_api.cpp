@@ -279,7 +279,8 @@ int xt_tracker_create(const xt_element* table, int64_t n, const xt_reference* re
   std::unique_ptr<xt_tracker> t(new xt_tracker());
   t->opt = o;
   t->rc = ref_constants(*ref);
-  t->ref = {t->rc.beta0, t->rc.gamma0, t->rc.bg0, t->rc.ib0, t->rc.twoib0, t->rc.p0c, t->rc.uc15, t->rc.ig02};
+  t->ref = {t->rc.beta0, t->rc.gamma0, t->rc.bg0, t->rc.ib0, t->rc.twoib0, t->rc.p0c, t->rc.uc15, t->rc.ig02,
+            1.0 / t->rc.p0c};
   t->sn = sin_table();
   std::string err;
   rc = compile_lattice(table, n, t->rc, &t->lat, &err);
@@ -304,6 +305,7 @@ int xt_tracker_create(const xt_element* table, int64_t n, const xt_reference* re
   std::vector<int32_t> guide;
   photon_table(&xi, &F, &guide);
   t->spec_k = (int)xi.size();
+  for (int j = 0; j < XT_EXPNEG_N; j++) xi.push_back(std::exp(-(double)j / 64.0));
   rc = dev_alloc(&t->d_spec_xi, xi.size());
   if (rc) return rc;
   rc = dev_alloc(&t->d_spec_F, F.size());

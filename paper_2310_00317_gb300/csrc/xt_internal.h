@@ -55,7 +55,7 @@ struct Chunk {
 
 // Reference-derived constants used by the kernels.
 struct RefDev {
-  double beta0, gamma0, bg0, ib0, twoib0, p0c, uc15, ig02;  // ig02 = 1/gamma0^2
+  double beta0, gamma0, bg0, ib0, twoib0, p0c, uc15, ig02, ip0c;  // ig02 = 1/gamma0^2, ip0c = 1/p0c
 };
 
 // Coefficients of the sine used by the RF cavity (Taylor series on |r| <= pi/4).
@@ -78,6 +78,10 @@ struct Lattice {
 struct Refc {
   double m0, q0, p0c, E0, beta0, gamma0, bg0, ib0, twoib0, crad, kq, uc15, ig02;
 };
+
+// e^(-j/64), j = 0..XT_EXPNEG_N - 1, stored after the photon spectrum's knots
+// (the quantum model's e^(-nbar) for nbar < 16).
+constexpr int XT_EXPNEG_N = 1025;
 
 // Host-side compilation (xt_lattice.cpp).
 Refc ref_constants(const xt_reference& r);

@@ -174,16 +174,21 @@ __device__ __forceinline__ void derive(Part& p, const RefDev& r) {
   derive_drift(p, r);
 }
 
-// (1+delta)^2 = 1 + 2 ptau/beta0 + ptau^2 in the form delta = u/(sqrt(1+u)+1).
+// (1+delta)^2 = 1 + 2 ptau/beta0 + ptau^2 = 1 + u in the form
+// delta = u/(s+1), s = sqrt(1+u) = 1+delta; rpp = 1/s and rvv = s/ep.  The
+// three quotients share one division, q = 1/(s (s+1) ep).
 __device__ __forceinline__ void energy_update(Part& p, const RefDev& r) {
   const double u = p.ptau * (p.ptau + r.twoib0);
   const double s = sqrt(1.0 + u);
-  p.delta = u / (s + 1.0);
+  const double a = s + 1.0;
+  p.ep = fma(r.beta0, p.ptau, 1.0);
+  const double sa = s * a;
+  const double q = 1.0 / (sa * p.ep);
+  p.delta = (u * (s * p.ep)) * q;
   p.opd = 1.0 + p.delta;
   p.dm1 = p.delta * (p.delta + 2.0);
-  p.rpp = 1.0 / p.opd;
-  p.ep = fma(r.beta0, p.ptau, 1.0);
-  p.rvv = p.opd / p.ep;
+  p.rpp = (a * p.ep) * q;
+  p.rvv = (s * sa) * q;
   p.rv0v = p.ep * p.rpp;
   p.epm1 = r.beta0 * p.ptau;
   derive_drift(p, r);
@@ -676,6 +681,28 @@ __device__ __forceinline__ void thick_quad(Part& p, double absk1, double L, bool
   p.py = fx ? pv1 : pu1;
 }
 
+// e^(-x) for the photon-count recurrence, x = nbar >= 0: x = j/64 + d with
+// j = round(64 x) (the 1.5 * 2^52 shift; the integer read from the bits) and
+// |d| <= 1/128, e^(-x) = E[j] e^(-d), E[j] = e^(-j/64) from the table that
+// follows the spectrum's knots, e^(-d) by its Taylor series to d^7
+// (truncation below 4e-19); x outside [0, 16) (or NaN) falls back to
+// exp_cw, so the table index stays in 0..1024.
+__device__ __forceinline__ double exp_neg(double x, const double* E) {
+  if (!(x >= 0.0 && x < 16.0)) return exp_cw(-x);
+  const double SH = 6755399441055744.0;
+  const double t = fma(x, 64.0, SH);
+  const int j = (int)(dbits(t) - dbits(SH));
+  const double d = fma(-(t - SH), 0.015625, x);
+  double e = fma(-d, 1.0 / 5040.0, 1.0 / 720.0);
+  e = fma(e, -d, 1.0 / 120.0);
+  e = fma(e, -d, 1.0 / 24.0);
+  e = fma(e, -d, 1.0 / 6.0);
+  e = fma(e, -d, 0.5);
+  e = fma(e, -d, 1.0);
+  e = fma(e, -d, 1.0);
+  return __ldg(E + j) * e;
+}
+
 template <int RAD>
 __device__ __forceinline__ void multipole(Part& p, const double* prm, int order, int flags,
                                           const RefDev& r, const RadCtx& rc, int64_t pid, int turn,
@@ -758,7 +785,7 @@ __device__ __forceinline__ void multipole(Part& p, const double* prm, int order,
     // is): the test u0 > F compares their bit patterns
     const uint64_t u0b = dbits(unit53(uni_word(u) >> 11));
     int k = 0;
-    double pk = exp_cw(-nbar), F = pk;
+    double pk = exp_neg(nbar, rc.xi + rc.K), F = pk;
     while (u0b > dbits(F) && k < 200) {
       k++;
       pk = (pk * nbar) * c_special[XT_SPECIAL_RECIP + k];
@@ -768,7 +795,7 @@ __device__ __forceinline__ void multipole(Part& p, const double* prm, int order,
       double sxi = 0.0;
       for (int j = 0; j < k; j++) sxi = sxi + sample_xi(uni_word(u), rc.xi, rc.F, rc.guide, rc.K);
       const double uc = (r.uc15 * (gam * gam * gam)) * h;
-      const double dpt = -(uc * sxi) / r.p0c;
+      const double dpt = -(uc * sxi) * r.ip0c;
       apply_energy_loss(p, dpt, r);
     }
   }

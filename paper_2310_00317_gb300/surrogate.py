@@ -279,15 +279,18 @@ def _stats(off):
 
 def da_study(family=(13, 61), test_seeds=(60, 13, 30, 45), val_seeds=(59, 41, 20), unseen_seed=200,
              mean_count=16000, n_turns=300, n_cells=20, base_mult=1.5, epochs=16, n_r=22222, n_theta=45, deltas=(0,),
-             p_lo=0.2, margin_sigma=None, window_sigma=None, pad_sigma=0.1, step_sigma=0.25):
+             p_lo=0.2, margin_sigma=None, window_sigma=None, pad_sigma=0.1, step_sigma=0.25,
+             total_labels=None, label_sigma_delta=0.0):
     """The surrogate workflow on a family of error seeds (seeds family[0] ..
     family[1]-1): random-amplitude labels of every seed tracked together in
     one batched launch per segment, the network trained on them, the band
     limits calibrated on validation seeds of the family (unless given), then
     plain / surrogate-guided / coarse scans of the test seeds of the family.
     The network's offsets on a seed outside the family measure how far it
-    generalises.  Returns a dict of the measured quantities; `per_seed` holds
-    one entry per test seed and the totals are summed over them."""
+    generalises.  total_labels scales the per-seed counts to that total;
+    label_sigma_delta draws the labels' momentum deviations (0: on momentum).
+    Returns a dict of the measured quantities; `per_seed` holds one entry per
+    test seed and the totals are summed over them."""
     import torch
     seeds = list(range(family[0], family[1]))
     if (any(t not in seeds for t in test_seeds) or any(v not in seeds for v in val_seeds)
@@ -296,7 +299,10 @@ def da_study(family=(13, 61), test_seeds=(60, 13, 30, 45), val_seeds=(59, 41, 20
     rng = np.random.default_rng(I.BASE_SEED + 77)
     lo, hi = math.log10(mean_count) - 0.75, math.log10(mean_count) + 0.75
     counts = np.round(10.0 ** rng.uniform(lo, hi, len(seeds))).astype(np.int64)
-    data, t_label, label_passes = make_training_set(seeds, counts, n_turns, n_cells, base_mult)
+    if total_labels is not None:  # the same log-uniform shape, scaled to the stated total
+        counts = np.maximum(1, np.round(counts * (total_labels / counts.sum()))).astype(np.int64)
+    data, t_label, label_passes = make_training_set(seeds, counts, n_turns, n_cells, base_mult,
+                                                    sigma_delta=label_sigma_delta)
     net = xtgb.Surrogate(seed=7)
     hist, t_train = train(net, data, epochs=epochs)
     acc_train = accuracy(net, data)
@@ -371,3 +377,17 @@ def da_study(family=(13, 61), test_seeds=(60, 13, 30, 45), val_seeds=(59, 41, 20
         coarse_rays_within_0p2_sigma=float(np.mean([r["coarse_rays_within_0p2_sigma"] for r in per_seed])),
         per_seed=per_seed,
     )
+
+
+def da_study_full(n_turns: int = 100, base_mult: float = 1.0, total_labels: int = 5_000_000, epochs: int = 16,
+                  test_seeds=(60, 13, 30, 45), val_seeds=(59, 41, 20), unseen_seed=200):
+    """The surrogate workflow on the LHC-scale ring itself (200 cells,
+    20,000 elements): a family of 64 error seeds with per-seed log-uniform
+    scales of the orders 2..6 in [0.5, 2] (times base_mult), total_labels
+    random-amplitude labels over the family with momentum deviations
+    N(0, sigma_delta), and scans of the full 999,990-point grid (22,222 radii
+    x 9 angles x 5 momentum offsets -2..2 sigma_delta) of the test seeds."""
+    return da_study(family=(0, 64), test_seeds=test_seeds, val_seeds=val_seeds, unseen_seed=unseen_seed,
+                    mean_count=total_labels / 64, n_turns=n_turns, n_cells=200, base_mult=base_mult,
+                    epochs=epochs, n_r=22222, n_theta=9, deltas=(-2, -1, 0, 1, 2), total_labels=total_labels,
+                    label_sigma_delta=SIGMA_DELTA)
