@@ -225,7 +225,7 @@ static int track_device(xt_tracker* t, const xt_particles* p, int64_t start_turn
   const int block = eff_block(t);
   rc = build_device_chunks(t, eff_chunk(t));
   if (rc) return rc;
-  const size_t smem = track_smem_bytes(block, t->chunk_built);
+  const size_t smem = track_smem_bytes(block, t->chunk_built, kind_of(t));
   int grid = 0;
   rc = grid_for(t, block, smem, &grid);
   if (rc) return rc;
@@ -720,7 +720,7 @@ int noalloc_prepare(xt_tracker* t, const xt_particles* p, int64_t n_turns, Track
     return fail(XT_ERR_INVALID, "xt_track_noalloc: the current device (" + std::to_string(dev) +
                                     ") is not the tracker's (" + std::to_string(t->device) + ")");
   *block = eff_block(t);
-  *smem = track_smem_bytes(*block, t->chunk_built);
+  *smem = track_smem_bytes(*block, t->chunk_built, kind_of(t));
   int rc = grid_for(t, *block, *smem, grid);
   if (rc) return rc;
   *seg = eff_segment(t, p->n, n_turns);
@@ -817,7 +817,7 @@ extern "C" int xt_autotune(xt_tracker* t, const xt_particles* probe, int64_t pro
         o.segment_turns = sg;
         if (xt_tracker_set_options(t, &o) != XT_OK) continue;
         int bps = 0;
-        const size_t sm = track_smem_bytes(blk, t->chunk_built);
+        const size_t sm = track_smem_bytes(blk, t->chunk_built, kind_of(t));
         if (sm > (size_t)t->smem_max || track_occupancy(o.radiation + (t->lat.thick ? 3 : 0), blk, sm, &bps) || bps < 1) continue;
         if ((rc = restore())) break;
         TUNE_CK(cudaEventRecord(e0, s));
@@ -1006,7 +1006,7 @@ extern "C" int xt_track_batched(xt_tracker* const* trs, const xt_particles* ps, 
     int rc = build_device_chunks(trs[i], chunk);
     if (rc) return rc;
   }
-  const size_t smem = track_smem_bytes(block, chunk);
+  const size_t smem = track_smem_bytes(block, chunk, kind);
   if (smem > (size_t)t0->smem_max)
     return fail(XT_ERR_INVALID, "block x 2 x chunk_bytes exceeds the shared memory of one block");
   int bpsm = 0;

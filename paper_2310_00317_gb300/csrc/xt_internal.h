@@ -83,6 +83,10 @@ struct Refc {
 // (the quantum model's e^(-nbar) for nbar < 16).
 constexpr int XT_EXPNEG_N = 1025;
 
+// Photons a warp samples together in shared memory per radiating slice
+// (quantum radiation); more fall back to sampling by each particle.
+constexpr int XT_PHOTON_CAP = 128;
+
 // Host-side compilation (xt_lattice.cpp).
 Refc ref_constants(const xt_reference& r);
 int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice* out, std::string* err);
@@ -239,7 +243,7 @@ int device_sm_count(int* n);
 int device_smem_optin(int* bytes);
 int launch_fp64_probe(double* out, int grid, int block, int iters, int variant, int* chains, void* stream);
 
-size_t track_smem_bytes(int block, int chunk_bytes);
+size_t track_smem_bytes(int block, int chunk_bytes, int kind);
 
 // Launch parameters of a tracker for the allocation-free entry point
 // (xt_api.cpp): fills everything but the scratch pointers, allocates nothing.

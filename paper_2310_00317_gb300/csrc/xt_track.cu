@@ -154,6 +154,9 @@ struct Part {
   double x, px, y, py, zeta, delta, ptau, rpp, rvv;
   double opd, dm1, rv0v, ep, epm1;  // epm1 = beta0 ptau (= ep - 1)
   double iep, iep2, c0, dmb;
+  // quantum emission left to the warp (track_tile): photon count, curvature, gamma
+  int em_k;
+  double em_h, em_g;
 };
 
 __device__ __forceinline__ void derive_drift(Part& p, const RefDev& r) {
@@ -703,7 +706,7 @@ __device__ __forceinline__ double exp_neg(double x, const double* E) {
   return __ldg(E + j) * e;
 }
 
-template <int RAD>
+template <int RAD, bool DEFER = false>
 __device__ __forceinline__ void multipole(Part& p, const double* prm, int order, int flags,
                                           const RefDev& r, const RadCtx& rc, int64_t pid, int turn,
                                           uint32_t elem) {
@@ -781,15 +784,49 @@ __device__ __forceinline__ void multipole(Part& p, const double* prm, int order,
     Uni u;
     u.c0 = (uint64_t)pid; u.c1 = (uint64_t)(uint32_t)turn; u.c2 = elem; u.c3 = 0;
     u.key = rc.seed; u.pos = 4;
-    // u0 and the partial sums F are non-negative (F is NaN only if nbar
-    // is): the test u0 > F compares their bit patterns
-    const uint64_t u0b = dbits(unit53(uni_word(u) >> 11));
+    // k = min{k : u0 <= F_k} (at most 200), F_k = sum_{j<=k} e^-nbar nbar^j / j!,
+    // decided first in FP32: F_k's FP32 value differs from its FP64 value
+    // by less than 1e-5 for k <= 30 and nbar < 16 (expf and __fdividef within
+    // 2 ulp, three roundings per step, nbar and u0 rounded to float), so
+    // wherever u0 stays more than 2e-5 from every partial sum it passes, the
+    // FP32 decision is the FP64 one.  Otherwise (or for larger k, nbar) the
+    // FP64 recurrence decides, as below.
+    const uint64_t w0 = uni_word(u);
     int k = 0;
-    double pk = exp_neg(nbar, rc.xi + rc.K), F = pk;
-    while (u0b > dbits(F) && k < 200) {
-      k++;
-      pk = (pk * nbar) * c_special[XT_SPECIAL_RECIP + k];
-      F = F + pk;
+    bool sure = nbar >= 0.0 && nbar < 16.0;
+    if (sure) {
+      const float nb = (float)nbar;
+      const float u0f = __uint2float_rn((uint32_t)(w0 >> 40)) * 5.9604644775390625e-8f;  // top 24 bits / 2^24
+      float pkf = expf(-nb), Ff = pkf;
+      while (true) {
+        const float gap = u0f - Ff;
+        if (fabsf(gap) <= 2e-5f || k >= 30) {
+          sure = false;
+          break;
+        }
+        if (gap < 0.0f) break;
+        k++;
+        pkf = __fdividef(pkf * nb, (float)k);
+        Ff = Ff + pkf;
+      }
+    }
+    if (!sure) {
+      // u0 and the partial sums F are non-negative (F is NaN only if nbar
+      // is): the test u0 > F compares their bit patterns
+      const uint64_t u0b = dbits(unit53(w0 >> 11));
+      k = 0;
+      double pk = exp_neg(nbar, rc.xi + rc.K), F = pk;
+      while (u0b > dbits(F) && k < 200) {
+        k++;
+        pk = (pk * nbar) * c_special[XT_SPECIAL_RECIP + k];
+        F = F + pk;
+      }
+    }
+    if (DEFER) {  // the warp samples the photons together (emit_photons_warp)
+      p.em_k = k;
+      p.em_h = h;
+      p.em_g = gam;
+      return;
     }
     if (k > 0) {
       double sxi = 0.0;
@@ -798,6 +835,75 @@ __device__ __forceinline__ void multipole(Part& p, const double* prm, int order,
       const double dpt = -(uc * sxi) * r.ip0c;
       apply_energy_loss(p, dpt, r);
     }
+  }
+}
+
+// Word idx (0-based) of the Philox stream of counter (c0, c1, c2): block
+// idx / 4, position idx % 4, the order in which uni_word hands them out.
+__device__ __forceinline__ uint64_t philox_word(uint64_t key, uint64_t c0, uint64_t c1, uint64_t c2, uint32_t idx) {
+  uint64_t a = c0, b = c1, c = c2, d = (uint64_t)(idx >> 2);
+  philox4x64(a, b, c, d, key, 0ull);
+  const uint32_t q = idx & 3u;
+  return q == 0 ? a : (q == 1 ? b : (q == 2 ? c : d));
+}
+
+// The photons of one radiating slice, sampled by the whole warp.  Every lane
+// (lanes without photons, lost ones included, with em_k = 0) enters with its
+// photon count; the warp's K photons are numbered by an exclusive prefix of
+// the counts, and lane L samples photons L, L + 32, ...: photon j of owner o
+// is word 1 + j of o's Philox stream (word 0 drew the count), so each value
+// is the one the owner would draw itself.  The values go to this warp's
+// XT_PHOTON_CAP doubles of shared memory, and each owner adds its own in the
+// order j = 0, 1, ... -- the same sum, in the same order, as sampling them
+// one by one, independent of which particles share the warp.  More than
+// XT_PHOTON_CAP photons in the warp: every owner samples its own.
+__device__ __forceinline__ void emit_photons_warp(Part& p, int64_t pid, int turn, uint32_t elem, const RadCtx& rc,
+                                                  const RefDev& r, int lane, double* ph) {
+  const int k = p.em_k;
+  int incl = k;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int v = __shfl_up_sync(FULL_MASK, incl, off);
+    if (lane >= off) incl += v;
+  }
+  const int K = __shfl_sync(FULL_MASK, incl, 31);
+  if (K == 0) return;
+  const int excl = incl - k;
+  const uint64_t c1 = (uint64_t)(uint32_t)turn;
+  double sxi = 0.0;
+  if (K <= XT_PHOTON_CAP) {
+    for (int base = 0; base < K; base += 32) {
+      const int t = base + lane;
+      // owner: the number of lanes whose inclusive count is <= t
+      int o = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        const int v = __shfl_sync(FULL_MASK, incl, o + step - 1);
+        if (v <= t) o += step;
+      }
+      const int os = o & 31;
+      const int ex_o = __shfl_sync(FULL_MASK, excl, os);
+      const int64_t pid_o = __shfl_sync(FULL_MASK, pid, os);
+      if (t < K) {
+        const uint64_t w = philox_word(rc.seed, (uint64_t)pid_o, c1, elem, (uint32_t)(1 + t - ex_o));
+        ph[t] = sample_xi(w, rc.xi, rc.F, rc.guide, rc.K);
+      }
+    }
+    __syncwarp();
+    for (int j = 0; j < k; j++) sxi = sxi + ph[excl + j];
+    __syncwarp();
+  } else {
+    Uni u;
+    u.c0 = (uint64_t)pid; u.c1 = c1; u.c2 = elem; u.c3 = 0;
+    u.key = rc.seed; u.pos = 4;
+    uni_word(u);  // the count's word
+    for (int j = 0; j < k; j++) sxi = sxi + sample_xi(uni_word(u), rc.xi, rc.F, rc.guide, rc.K);
+  }
+  if (k > 0) {
+    const double gam = p.em_g;
+    const double uc = (r.uc15 * (gam * gam * gam)) * p.em_h;
+    const double dpt = -(uc * sxi) * r.ip0c;
+    apply_energy_loss(p, dpt, r);
   }
 }
 
@@ -847,13 +953,13 @@ __device__ __forceinline__ int edge_nonlinear(Part& p, const double* prm) {
 // instantiation for tables without beam-beam lenses, thick quadrupoles,
 // bends or non-linear edges (the host chooses it only for such tables): their
 // bodies then stay out of the thin-element tracking loop.
-template <int RAD, bool THICK = true>
+template <int RAD, bool THICK = true, bool DEFER = false>
 __device__ __forceinline__ int element(Part& p, uint32_t type, uint32_t order, uint32_t flags,
                                        uint32_t elem, const double* prm, const RefDev& r,
                                        const SinTab& sn, const RadCtx& rc, int64_t pid, int turn) {
   switch (type) {
     case XT_MULTIPOLE:
-      multipole<RAD>(p, prm, (int)order, (int)flags, r, rc, pid, turn, elem);
+      multipole<RAD, DEFER>(p, prm, (int)order, (int)flags, r, rc, pid, turn, elem);
       return 1;
     case XT_APERTURE: {
       const double rr = fma(p.x, p.x, p.y * p.y);
@@ -971,7 +1077,7 @@ template <int RAD, bool THICK>
 __device__ __forceinline__ int track_tile(const TileLat& L, const TileArrays& A, int i, bool active, int turn0,
                           int n_turns, Stage& st, int& resident_key, int lat_key,
                           const RefDev& ref, const SinTab& sn, const RadCtx& rc, Ctl& ctl,
-                          int lane) {
+                          int lane, double* ph) {
   Part p;
   int code = 0, lturn = 0;
   uint32_t lelem = 0;
@@ -1020,6 +1126,7 @@ __device__ __forceinline__ int track_tile(const TileLat& L, const TileArrays& A,
         const uint32_t flags = hv.y & 0xFFFFu, size16 = hv.y >> 16;
         const double* prm = (const double*)(q + 16);
         int lc = 1;
+        if (RAD == XT_RAD_QUANTUM) p.em_k = 0;
         if (type == XT_DRIFT) {
           lc = drift_warp(p, prm, alive);
         } else if (type == XT_APERTURE) {
@@ -1030,8 +1137,12 @@ __device__ __forceinline__ int track_tile(const TileLat& L, const TileArrays& A,
           if (!__all_sync(FULL_MASK, in) && alive) lc = element<RAD, THICK>(p, type, order, flags, hv.z, prm, ref,
                                                                       sn, rc, pid, turn);
         } else if (alive) {
-          lc = element<RAD, THICK>(p, type, order, flags, hv.z, prm, ref, sn, rc, pid, turn);
+          lc = element<RAD, THICK, RAD == XT_RAD_QUANTUM>(p, type, order, flags, hv.z, prm, ref, sn, rc, pid, turn);
         }
+        // quantum emission of a radiating multipole: the whole warp samples
+        // the photons its lanes drew (the record is the same for every lane)
+        if (RAD == XT_RAD_QUANTUM && type == XT_MULTIPOLE && (flags & REC_RAD))
+          emit_photons_warp(p, pid, turn, hv.z, rc, ref, lane, ph);
         if (lc != 1) {
           alive = false;
           code = lc;
@@ -1087,6 +1198,14 @@ __device__ __forceinline__ int track_tile(const TileLat& L, const TileArrays& A,
   return err;
 }
 
+// This warp's XT_PHOTON_CAP doubles after the chunk buffers (allocated by
+// the host for the quantum-radiation kinds only; see track_smem_bytes).
+__device__ __forceinline__ double* photon_buffer(uint8_t* smem, int chunk_bytes) {
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  uint8_t* end = smem + ((nwarps * 16 + 127) & ~127) + (size_t)nwarps * 2 * chunk_bytes;
+  return (double*)end + (size_t)warp * XT_PHOTON_CAP;
+}
+
 __device__ __forceinline__ void stage_setup(Stage& st, uint8_t* smem, int chunk_bytes, int lane) {
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   uint64_t* bars = (uint64_t*)smem;
@@ -1120,6 +1239,7 @@ __global__ void __launch_bounds__(XT_MAX_BLOCK, (KIND >= 2) ? 2 : 3) track_kerne
   const int lane = threadIdx.x & 31;
   Stage st;
   stage_setup(st, smem, a.chunk_bytes, lane);
+  double* const ph = photon_buffer(smem, a.chunk_bytes);
   if (*(volatile int32_t*)a.status != 0) return;
   const int n_alive = *a.n_alive;
   const TileLat L = {a.lat, a.chunks, a.n_chunks, a.n_el};
@@ -1138,7 +1258,7 @@ __global__ void __launch_bounds__(XT_MAX_BLOCK, (KIND >= 2) ? 2 : 3) track_kerne
     const bool active = k < n_alive;
     const int i = active ? __ldg(a.idx + k) : 0;
     const int err = track_tile<KIND % 3, (KIND >= 3)>(L, A, i, active, a.turn0, a.n_turns, st, resident, 0,
-                                                     a.ref, a.sn, rc, ctl, lane);
+                                                     a.ref, a.sn, rc, ctl, lane, ph);
     if (err) {
       if (lane == 0) set_status(a.status, err);
       break;
@@ -1152,6 +1272,7 @@ __global__ void __launch_bounds__(XT_MAX_BLOCK, (KIND >= 2) ? 2 : 3) track_batch
   const int lane = threadIdx.x & 31;
   Stage st;
   stage_setup(st, smem, a.chunk_bytes, lane);
+  double* const ph = photon_buffer(smem, a.chunk_bytes);
   if (*(volatile int32_t*)a.status != 0) return;
   const int64_t total_tiles = a.tile_prefix[a.n_seeds];
   const int turn0 = *a.turn_base + a.turn_off;
@@ -1179,7 +1300,7 @@ __global__ void __launch_bounds__(XT_MAX_BLOCK, (KIND >= 2) ? 2 : 3) track_batch
     const TileArrays A = {S.x, S.px, S.y, S.py, S.zeta, S.delta, S.ptau, S.rpp, S.rvv,
                           S.state, S.at_turn, S.at_element, S.pid};
     const int err = track_tile<KIND % 3, (KIND >= 3)>(L, A, i, active, turn0, a.n_turns, st, resident, s,
-                                                     a.ref, a.sn, rc, ctl, lane);
+                                                     a.ref, a.sn, rc, ctl, lane, ph);
     if (err) {
       if (lane == 0) set_status(a.status, err);
       break;
@@ -1587,9 +1708,13 @@ __global__ void tile_prefix_kernel(const int32_t* __restrict__ n_alive, const in
 
 // ---------------------------------------------------------------------------
 // Launchers.
-size_t track_smem_bytes(int block, int chunk_bytes) {
+// Dynamic shared memory of a tracking block: the warps' mbarriers, two
+// lattice-chunk buffers per warp, and with quantum radiation (kind 2 or 5)
+// XT_PHOTON_CAP doubles per warp for the photons it samples together.
+size_t track_smem_bytes(int block, int chunk_bytes, int kind) {
   const int nw = block / 32;
-  return (size_t)((nw * 16 + 127) & ~127) + (size_t)nw * 2 * (size_t)chunk_bytes;
+  const size_t photons = (kind % 3 == XT_RAD_QUANTUM) ? (size_t)nw * XT_PHOTON_CAP * sizeof(double) : 0;
+  return (size_t)((nw * 16 + 127) & ~127) + (size_t)nw * 2 * (size_t)chunk_bytes + photons;
 }
 
 template <int KIND>
