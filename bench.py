@@ -43,10 +43,11 @@ N_SM = 152
 SM_MAX_MHZ = 2070.0
 NOMINAL_FP64 = FP64_FLOP_PER_CLK_SM * N_SM * SM_MAX_MHZ * 1e6
 # DRAM bytes (read + write) of a tracking launch per particle and turn: ncu
-# capture of the current kernel on a 60,000-particle subset of this workload
-# over one turn (7,375,616 B read, 0 B written).  The per-launch traffic is the
-# particle state, so it scales with the particle count.
-TRACK_DRAM_BYTES_PER_PARTICLE_TURN = 7375616.0 / 60000.0
+# capture of the current kernel on a 400,000-particle subset of this workload
+# over one turn (34,624,256 B read, 0 B written; all 152 SMs busy).  The
+# per-launch traffic is the particle state, so it scales with the particle
+# count.
+TRACK_DRAM_BYTES_PER_PARTICLE_TURN = 34624256.0 / 400000.0
 
 
 def dist_env():
@@ -761,7 +762,7 @@ def run_ours(args):
                      "unit": "TFLOP/s", "frac": achieved / NOMINAL_FP64,
                      "traffic": TRACK_DRAM_BYTES_PER_PARTICLE_TURN * n * T * args.steps / max(kern_launches, 1),
                      "traffic_unit": "bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum of an ncu "
-                                     "capture of 60,000 particles, scaled by particles)",
+                                     "capture of 400,000 particles, scaled by particles)",
                      "kernel": "xt::track_kernel<0>", "kernel_ms_total": kern_ms,
                      "kernel_launches": kern_launches,
                      "peak_source": "nominal FP64 from unit counts and clocks: 4 flop/clk/SM x 152 SMs x 2070 MHz",
