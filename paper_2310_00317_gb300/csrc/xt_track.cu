@@ -1248,10 +1248,12 @@ __global__ void __launch_bounds__(XT_MAX_BLOCK, (KIND >= 2) ? 2 : 3) track_kerne
   const RadCtx rc = {a.seed, a.spec_xi, a.spec_F, a.spec_guide, a.spec_k};
   Ctl ctl = {a.status, a.cancel, a.max_cycles, clock64(), clock64()};
   int resident = -1;
-  while (true) {
-    int tile = 0;
-    if (lane == 0) tile = atomicAdd(a.tile_counter, 1);
-    tile = __shfl_sync(FULL_MASK, tile, 0);
+  // First tile: warp j of block b takes tile j * gridDim.x + b, so that when
+  // there are fewer tiles than warps they spread evenly over the blocks and
+  // hence the SMs; later tiles come from the queue, after the first round.
+  const int first_round = gridDim.x * (blockDim.x >> 5);
+  int tile = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  for (;; ) {
     const int64_t base = (int64_t)tile * 32;
     if (base >= n_alive) break;
     const int64_t k = base + lane;
@@ -1263,6 +1265,9 @@ __global__ void __launch_bounds__(XT_MAX_BLOCK, (KIND >= 2) ? 2 : 3) track_kerne
       if (lane == 0) set_status(a.status, err);
       break;
     }
+    int t = 0;
+    if (lane == 0) t = first_round + atomicAdd(a.tile_counter, 1);
+    tile = __shfl_sync(FULL_MASK, t, 0);
   }
 }
 
@@ -1279,10 +1284,10 @@ __global__ void __launch_bounds__(XT_MAX_BLOCK, (KIND >= 2) ? 2 : 3) track_batch
   const RadCtx rc = {a.seed, a.spec_xi, a.spec_F, a.spec_guide, a.spec_k};
   Ctl ctl = {a.status, a.cancel, a.max_cycles, clock64(), clock64()};
   int resident = -1;
-  while (true) {
-    int tile = 0;
-    if (lane == 0) tile = atomicAdd(a.tile_counter, 1);
-    tile = __shfl_sync(FULL_MASK, tile, 0);
+  // first tile interleaved over the blocks, as in track_kernel
+  const int first_round = gridDim.x * (blockDim.x >> 5);
+  int tile = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  for (;; ) {
     if ((int64_t)tile >= total_tiles) break;
     // seed j in processing order with tile_prefix[j] <= tile < tile_prefix[j+1]
     int lo = 0, hi = a.n_seeds;
@@ -1305,6 +1310,9 @@ __global__ void __launch_bounds__(XT_MAX_BLOCK, (KIND >= 2) ? 2 : 3) track_batch
       if (lane == 0) set_status(a.status, err);
       break;
     }
+    int t = 0;
+    if (lane == 0) t = first_round + atomicAdd(a.tile_counter, 1);
+    tile = __shfl_sync(FULL_MASK, t, 0);
   }
 }
 
