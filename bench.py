@@ -291,6 +291,46 @@ def measure_steady(turns=200, window=50, n=0):
     return out
 
 
+def measure_fodo(n=1000000, turns=300):
+    """A short lattice with many particles: the FODO-10 ring (51 elements)
+    with n matched protons.  The tracker's own segmentation (about 1e8
+    particle-element passes per launch) reloads the particle state every few
+    turns here; the rate shows what that costs next to the 20,000-element
+    ring, where a launch covers one turn."""
+    import torch
+    from paper_2310_00317_gb300 import inputs as I
+    from paper_2310_00317_gb300 import xtgb
+    el, ref = I.fodo10()
+    p = I.matched_gaussian(el, ref, n, 2.5e-6, 3e-4, seed=I.BASE_SEED + 9)
+    tr = xtgb.Tracker(el, ref)
+    fl = tr.element_flops().astype(np.float64)
+    P = xtgb.Particles.from_numpy(p)
+    tr.track(P, 3, 0)
+    before = P.t["state"].cpu().numpy()
+    tr.set_profiling(True)
+    tr.kernel_time()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    tr.track(P, turns, 3)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kms, launches = tr.kernel_time()
+    tr.set_profiling(False)
+    units = _passes(before, {k: P.t[k].cpu().numpy() for k in ("state", "at_turn", "at_element")}, 3, turns,
+                    el.shape[0])
+    per_pass = float(fl.sum()) / el.shape[0]
+    tr.close()
+    return {"workload": "FODO-10 ring (51 elements), %d matched protons at 450 GeV" % n, "turns": turns,
+            "value": units / (ms * 1e-3), "unit": UNIT, "tracking_launches": launches,
+            "turns_per_launch": turns / max(launches, 1), "kernel_ms": kms, "event_ms": ms,
+            "roofline": {"bound": "alu", "achieved": units * per_pass / (ms * 1e-3) / 1e12,
+                         "peak": NOMINAL_FP64 / 1e12, "unit": "TFLOP/s",
+                         "frac": units * per_pass / (ms * 1e-3) / NOMINAL_FP64,
+                         "algorithmic_flops_per_pass": per_pass}}
+
+
 def measure_refinement(tr, host, ds=0.01, n_angles=128, reps=5):
     """Loss-location refinement of the particles the headline run lost at the
     LHC-scale ring's apertures (state 0): CUDA-event time per call."""
@@ -882,7 +922,8 @@ def run_only(spec: str) -> int:
             kw["base_mult"] = float(nums[1])
     fn = {"thick_elements": measure_thick, "beambeam_lens": measure_beambeam, "twiss": measure_twiss,
           "lepton_quantum": measure_lepton, "steady": measure_steady, "batched_seeds": measure_batched,
-          "lepton_equilibrium": measure_lepton_equilibrium, "da_scan_full": measure_da_scan_full}.get(name)
+          "lepton_equilibrium": measure_lepton_equilibrium, "da_scan_full": measure_da_scan_full,
+          "fodo10": measure_fodo}.get(name)
     if fn is None:
         raise SystemExit("--only: unknown measurement %r" % name)
     print(json.dumps({name: fn(**kw)}))

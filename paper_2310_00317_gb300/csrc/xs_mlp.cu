@@ -84,6 +84,7 @@ struct Epi {
   const float* zprev;   // EPI_DGRAD: pre-activation of this layer's output
   bf16_t* out_b;        // EPI_GELU: activation; EPI_DGRAD: bf16 dZ
   float* out_f;         // EPI_F32ADD
+  float* colsum;        // EPI_DGRAD (may be null): column sums of the fp32 dZ added here (the bias gradient)
   int ld;               // leading dimension of every output / zprev (a multiple of 4)
   int* status;          // set to 1 if a tensor-core or copy wait gave up
 };
@@ -157,9 +158,10 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// Epilogue of CH accumulator columns [col, col + CH) of one row.
+// Epilogue of CH accumulator columns [col, col + CH) of one row; v receives
+// the fp32 values written (EPI_DGRAD: dZ).
 template <int EPI, int CH>
-__device__ __forceinline__ void epilogue(const Epi& e, int row, int col, const uint32_t* r) {
+__device__ __forceinline__ void epilogue(const Epi& e, int row, int col, const uint32_t* r, float* vout) {
   const int64_t o = (int64_t)row * e.ld + col;
   if (EPI == EPI_F32ADD) {
 #pragma unroll
@@ -186,6 +188,10 @@ __device__ __forceinline__ void epilogue(const Epi& e, int row, int col, const u
       for (int q = 0; q < CH / 4; q++)
         *(float4*)(e.z + o + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     }
+    if (EPI == EPI_DGRAD) {
+#pragma unroll
+      for (int i = 0; i < CH; i++) vout[i] = v[i];
+    }
     uint32_t h[CH / 2];
 #pragma unroll
     for (int i = 0; i < CH / 2; i++) {
@@ -197,6 +203,24 @@ __device__ __forceinline__ void epilogue(const Epi& e, int row, int col, const u
     for (int q = 0; q < CH / 8; q++)
       *(uint4*)(e.out_b + o + 8 * q) = make_uint4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
   }
+}
+
+// Sum over the warp's 32 lanes (rows) of each of 32 columns: a butterfly
+// that halves the columns a lane keeps at every step (16 + 8 + 4 + 2 + 1
+// shuffles), after which lane l holds column l; a fixed order, so the sums
+// are reproducible.  Lane l then adds it to out[l].
+__device__ __forceinline__ void warp_colsum32(float* v, int lane, float* out) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int j = 0; j < off; j++) {
+      const float send = upper ? v[j] : v[j + off];
+      const float recv = __shfl_xor_sync(0xFFFFFFFFu, send, off);
+      v[j] = (upper ? v[j + off] : v[j]) + recv;
+    }
+  }
+  atomicAdd(out + lane, v[0]);
 }
 
 template <int EPI, int BN>
@@ -309,7 +333,13 @@ __global__ void __launch_bounds__(256) tc_gemm_kernel(const __grid_constant__ CU
     for (int c0 = (warp >> 2) * CH; c0 < BN; c0 += 2 * CH) {
       uint32_t r[CH];
       tmem_load<CH>(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, r);
-      if (row < M) epilogue<EPI, CH>(e, row, n0 + c0, r);
+      float v[CH];
+#pragma unroll
+      for (int i = 0; i < CH; i++) v[i] = 0.0f;
+      if (row < M) epilogue<EPI, CH>(e, row, n0 + c0, r, v);
+      if constexpr (EPI == EPI_DGRAD && CH == 32) {
+        if (e.colsum) warp_colsum32(v, lane, e.colsum + n0 + c0);  // rows past M add 0
+      }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -499,14 +529,15 @@ __global__ void loss_kernel(const float* __restrict__ out, const float* __restri
   if ((threadIdx.x & 31) == 0) atomicAdd(&scal[0], s);
 }
 
-// Head backward: dW5, db5 (atomics over batch slices) and dZ4.
+// Head backward: dW5, db5 (atomics over batch slices), dZ4 and its column
+// sums (the top hidden layer's bias gradient).
 __global__ void head_backward_kernel(const float* __restrict__ dout, const bf16_t* __restrict__ a4,
                                      const bf16_t* __restrict__ w5, const float* __restrict__ z4, int64_t B,
                                      float* __restrict__ gw5, float* __restrict__ gb5, float* __restrict__ dzf,
-                                     bf16_t* __restrict__ dzb) {
+                                     bf16_t* __restrict__ dzb, float* __restrict__ gb4) {
   const int k = threadIdx.x;  // 256 threads: one hidden unit each
   const float w0 = bf2f(w5[k]), w1 = bf2f(w5[256 + k]);
-  float s0 = 0.f, s1 = 0.f, d0 = 0.f, d1 = 0.f;
+  float s0 = 0.f, s1 = 0.f, d0 = 0.f, d1 = 0.f, sb = 0.f;
   for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
     const float g0 = dout[2 * b], g1 = dout[2 * b + 1];
     const float a = bf2f(a4[b * 256 + k]);
@@ -516,7 +547,9 @@ __global__ void head_backward_kernel(const float* __restrict__ dout, const bf16_
     const float dz = (g0 * w0 + g1 * w1) * gelu_grad_f(z4[b * 256 + k]);
     dzf[b * 256 + k] = dz;
     dzb[b * 256 + k] = f2bf(dz);
+    sb += dz;
   }
+  atomicAdd(&gb4[k], sb);  // the top hidden layer's bias gradient
   atomicAdd(&gw5[k], s0);
   atomicAdd(&gw5[256 + k], s1);
   if (k == 0) {
@@ -544,25 +577,32 @@ __global__ void transpose_kernel(const bf16_t* __restrict__ src, int64_t B, int 
   }
 }
 
-// db[n] = sum_b dz[b][n]
-__global__ void colsum_kernel(const float* __restrict__ dz, int64_t B, int C, float* __restrict__ db) {
-  const int c = threadIdx.x;
-  if (c >= C) return;
-  float s = 0.f;
-  for (int64_t b = blockIdx.x; b < B; b += gridDim.x) s += dz[b * C + c];
-  atomicAdd(&db[c], s);
-}
-
-__global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
-                            float* __restrict__ v, int64_t n, float lr, float b1, float b2, float c1, float c2,
-                            float eps) {
+// Adam on the fp32 master parameters, and in the same pass the bfloat16
+// copies of every weight the next step's GEMMs read: W (out x in) and its
+// transpose (in x out), which the separate refresh pass wrote before.
+__constant__ int64_t c_off_w[NL] = {OFF_W[0], OFF_W[1], OFF_W[2], OFF_W[3], OFF_W[4]};
+__constant__ int c_width[NL + 1] = {WIDTH[0], WIDTH[1], WIDTH[2], WIDTH[3], WIDTH[4], WIDTH[5]};
+__global__ void adam_refresh_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                                    float* __restrict__ v, int64_t n, float lr, float b1, float b2, float c1,
+                                    float c2, float eps, bf16_t* __restrict__ wb, bf16_t* __restrict__ wtb) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.f - b1) * gi;
     const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
-    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+#pragma unroll
+    for (int l = 0; l < NL; l++) {
+      const int out = c_width[l + 1], in = c_width[l];
+      const int64_t j = i - c_off_w[l];
+      if (j >= 0 && j < (int64_t)out * in) {
+        const bf16_t h = f2bf(wi);
+        wb[i] = h;
+        wtb[c_off_w[l] + (j % in) * out + j / in] = h;
+      }
+    }
   }
 }
 
@@ -671,7 +711,8 @@ static int loss_grad(xs_mlp* n, const float* X, const float* y, const float* t, 
   CK(cudaMemsetAsync(n->grad, 0, NPARAM * sizeof(float), s));
   const int hb = (int)std::min<int64_t>(B, 1024);
   head_backward_kernel<<<hb, 256, 0, s>>>(n->dout, n->a[NL - 1], n->wb + OFF_W[NL - 1], n->z[NL - 2], B,
-                                          n->grad + OFF_W[NL - 1], n->grad + OFF_B[NL - 1], n->dzf[0], n->dzb[0]);
+                                          n->grad + OFF_W[NL - 1], n->grad + OFF_B[NL - 1], n->dzf[0], n->dzb[0],
+                                          n->grad + OFF_B[NL - 2]);
   CK(cudaGetLastError());
   const int64_t Bp = pad16(B);
   int cur = 0;
@@ -690,8 +731,8 @@ static int loss_grad(xs_mlp* n, const float* X, const float* y, const float* t, 
     // K (the batch) is split in slices of 256 whose partial sums add up in the gradient
     rc = gemm<EPI_F32ADD>(n->dzT, (int)Bp, n->aT, (int)Bp, 256, in, (int)Bp, e, s);
     if (rc) return rc;
-    colsum_kernel<<<(int)std::min<int64_t>(B, 1024), 256, 0, s>>>(n->dzf[cur], B, 256, n->grad + OFF_B[l]);
-    CK(cudaGetLastError());
+    // the bias gradient of layer l (column sums of its fp32 dZ) was added by
+    // the kernel that produced dZ: head_backward_kernel or the dgrad epilogue
     if (l > 0) {
       // dgrad: dA_{l-1} = dZ_l W_l, then times GELU'(z_{l-1})
       Epi d;
@@ -699,6 +740,7 @@ static int loss_grad(xs_mlp* n, const float* X, const float* y, const float* t, 
       d.zprev = n->z[l - 1];
       d.z = n->dzf[1 - cur];
       d.out_b = n->dzb[1 - cur];
+      d.colsum = n->grad + OFF_B[l - 1];
       d.ld = 256;
       d.status = (int*)(n->scal + 3);
       rc = gemm<EPI_DGRAD>(n->dzb[cur], 256, n->wtb + OFF_W[l], 256, (int)B, 256, 256, d, s);
@@ -820,11 +862,9 @@ int xs_mlp_train_step(xs_mlp* n, const float* X, const float* y, const float* t,
   const double b1 = 0.9, b2 = 0.999;
   const float c1 = (float)(1.0 - std::pow(b1, (double)n->step));
   const float c2 = (float)(1.0 - std::pow(b2, (double)n->step));
-  adam_kernel<<<grid_1d(NPARAM, 256), 256, 0, s>>>(n->master, n->grad, n->m, n->v, NPARAM, lr, (float)b1,
-                                                   (float)b2, c1, c2, 1e-8f);
+  adam_refresh_kernel<<<grid_1d(NPARAM, 256), 256, 0, s>>>(n->master, n->grad, n->m, n->v, NPARAM, lr, (float)b1,
+                                                           (float)b2, c1, c2, 1e-8f, n->wb, n->wtb);
   CK(cudaGetLastError());
-  rc = refresh(n, s);
-  if (rc) return rc;
   if (loss_out) CK(cudaMemcpyAsync(loss_out, n->scal, sizeof(float), cudaMemcpyDeviceToDevice, s));
   return XT_OK;
 }
