@@ -141,8 +141,9 @@ extern "C" {
                            [1/m], p[1] = frame curvature h [1/m] (k0 = h on
                            the design orbit; h = 0 is a straight frame),
                            p[2] = reference length L [m] (finite, >= 0),
-                           p[3] = gradient k1 [m^-2] (expanded model only),
-                           p[4] = model: 0 expanded, 1 full (k1 must be 0).
+                           p[3] = gradient k1 [m^-2], p[4] = model: 0
+                           expanded, 1 full, p[5] = gradient kicks n of the
+                           full model (integer 0..64, 0 means 1).
                            Expanded: the exact flow of
                            (px^2 + py^2) / (2 (1+delta)) - h x (1+delta)
                            + k0 (x + h x^2 / 2) + k1 (x^2 - y^2) / 2, with
@@ -151,8 +152,14 @@ extern "C" {
                            uniform field through the sector (arc of a circle
                            in the horizontal plane, straight in y); lost with
                            state -2 if the particle cannot reach the exit
-                           plane.  Delta and ptau are unchanged.  Loss
-                           refinement steps through it like a drift.        */
+                           plane.  A gradient in the full model has no
+                           closed form: the body is cut into n slices, each
+                           an exact half body, a thin kick px -= k1 (L/n) x,
+                           py += k1 (L/n) y and an exact half body (second
+                           order in L/n; -L inverts it).  Delta and ptau are
+                           unchanged.  Loss refinement steps through it like
+                           a drift, except a full bend with a gradient, which
+                           it passes whole (its slices are not a flow).     */
 #define XT_SPACECHARGE 14 /* Frozen space-charge lens (section "Space charge",
                            frozen model): p[0] = peak line density lambda0
                            [particles/m], p[1] = sigma_z [m] (> 0 a Gaussian

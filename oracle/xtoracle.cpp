@@ -723,6 +723,25 @@ static inline void bend_full(Part<T>& p, double k0, double h, double L, const Re
   p.zeta = p.zeta + (L - ep * lr);
 }
 
+// Thick bend, full model with a gradient k1: no closed form, so the body is
+// split into n equal slices and each slice's gradient is applied as one thin
+// quadrupole kick k1 L/n at its centre, between exact uniform-field bodies
+// (px -= k1 L/n x, py += k1 L/n y).  Symmetric in s, hence of second order
+// in L/n and inverted by -L.  Lost bodies end the element.
+template <class T>
+static inline void bend_full_gradient(Part<T>& p, double k0, double h, double L, double k1, int n,
+                                      const RefConst& rc, int turn, int elem) {
+  const double ls = L / n, kl = k1 * ls;
+  for (int i = 0; i < n; i++) {
+    bend_full(p, k0, h, 0.5 * ls, rc, turn, elem);
+    if (p.state != 1) return;
+    p.px = p.px - kl * p.x;
+    p.py = p.py + kl * p.y;
+    bend_full(p, k0, h, 0.5 * ls, rc, turn, elem);
+    if (p.state != 1) return;
+  }
+}
+
 // Prepared element: host constants of each type.
 struct Prep {
   int type;
@@ -743,7 +762,7 @@ struct Prep {
   double sc_sz;                          // frozen space charge: sigma_z, 0 for a coasting beam
   double k1, Lq;                         // thick quadrupole
   double bk0, bh, bL, bk1;               // thick bend: field, curvature, length, gradient
-  int bfull;                             // thick bend: 1 = full model, 0 = expanded
+  int bfull, bn;                         // thick bend: 1 = full model, 0 = expanded; gradient kicks (full)
 };
 
 static Prep prepare(const Element& e, const RefConst& rc) {
@@ -804,7 +823,10 @@ static Prep prepare(const Element& e, const RefConst& rc) {
     case T_APERTURE_RECT: q.xmin = e.p[0]; q.xmax = e.p[1]; q.ymin = e.p[2]; q.ymax = e.p[3]; break;
     case T_APERTURE_ELLIPSE: q.ia2 = 1.0 / (e.p[0] * e.p[0]); q.ib2 = 1.0 / (e.p[1] * e.p[1]); break;
     case T_QUAD: q.k1 = e.p[0]; q.Lq = e.p[1]; break;
-    case T_BEND: q.bk0 = e.p[0]; q.bh = e.p[1]; q.bL = e.p[2]; q.bk1 = e.p[3]; q.bfull = (e.p[4] != 0.0); break;
+    case T_BEND:
+      q.bk0 = e.p[0]; q.bh = e.p[1]; q.bL = e.p[2]; q.bk1 = e.p[3]; q.bfull = (e.p[4] != 0.0);
+      q.bn = (e.p[5] >= 1.0) ? (int)e.p[5] : 1;
+      break;
     case T_BEAMBEAM4D: {
       // kick of a counter-moving Gaussian bunch integrated over the crossing:
       // Delta p_perp / P0 = 2 q0 q_s N_s (r_e m_e c^2 / p0 c) (1 + beta0 beta_s) /
@@ -907,7 +929,8 @@ static inline void track_element(Part<T>& p, const Prep& q, int rad_mode, const 
     }
     case T_QUAD: thick_quad(p, q.k1, q.Lq, rc); break;
     case T_BEND:
-      if (q.bfull) bend_full(p, q.bk0, q.bh, q.bL, rc, turn, elem);
+      if (q.bfull && q.bk1 != 0.0) bend_full_gradient(p, q.bk0, q.bh, q.bL, q.bk1, q.bn, rc, turn, elem);
+      else if (q.bfull) bend_full(p, q.bk0, q.bh, q.bL, rc, turn, elem);
       else bend_expanded(p, q.bk0, q.bh, q.bL, q.bk1, rc);
       break;
     // 4D weak-strong beam-beam (section "Beam-beam interactions") and frozen
@@ -1037,7 +1060,8 @@ static bool inverse_row(Part<double>& p, const Prep& q, const RefConst& rc) {
     case T_LINEARMAP: return false;
     case T_QUAD: thick_quad(p, q.k1, -q.Lq, rc); return true;
     case T_BEND:
-      if (q.bfull) bend_full(p, q.bk0, q.bh, -q.bL, rc, 0, 0);
+      if (q.bfull && q.bk1 != 0.0) bend_full_gradient(p, q.bk0, q.bh, -q.bL, q.bk1, q.bn, rc, 0, 0);
+      else if (q.bfull) bend_full(p, q.bk0, q.bh, -q.bL, rc, 0, 0);
       else bend_expanded(p, q.bk0, q.bh, -q.bL, q.bk1, rc);
       return p.state == 1;
     case T_BEAMBEAM4D:
@@ -1070,11 +1094,12 @@ using namespace xo;
 extern "C" {
 
 // A table row the oracle accepts: a known type, a multipole order 0..10, a
-// bend model 0 (expanded) or 1 (full, without gradient).
+// bend model 0 (expanded) or 1 (full) with 0..64 gradient kicks.
 static bool row_ok(const Element& e) {
   if (e.type < 0 || e.type > T_SPACECHARGE) return false;
   if (e.type == T_MULTIPOLE && (e.order < 0 || e.order > 10)) return false;
-  if (e.type == T_BEND && !(e.p[4] == 0.0 || (e.p[4] == 1.0 && e.p[3] == 0.0))) return false;
+  if (e.type == T_BEND && !(e.p[4] == 0.0 || e.p[4] == 1.0)) return false;
+  if (e.type == T_BEND && !(e.p[5] >= 0.0 && e.p[5] <= 64.0 && e.p[5] == std::floor(e.p[5]))) return false;
   return true;
 }
 
@@ -1212,10 +1237,12 @@ int xo_refine_losses(const Element* el, int64_t n_el, const Reference* ref, cons
       j = (j + 1 == n_el) ? 0 : j + 1;
       if (j == e) break;
       // drifts, thick quadrupoles and thick bends in steps of at most ds (the
-      // thick maps are flows: their steps compose to the same map as one pass)
+      // thick maps are flows: their steps compose to the same map as one pass;
+      // a full bend with a gradient is not, and is passed whole)
       const int ty = prep[j].type;
       const double L = row_length(el[j]);
-      if ((ty == T_DRIFT || ty == T_QUAD || ty == T_BEND) && L > 0.0) {
+      const bool kicked = ty == T_BEND && prep[j].bfull && prep[j].bk1 != 0.0;
+      if ((ty == T_DRIFT || ty == T_QUAD || ty == T_BEND) && L > 0.0 && !kicked) {
         const int64_t ns = (int64_t)std::ceil(L / ds);
         const double h = L / (double)ns;
         const double c = std::cos(fr[j].th), sn = std::sin(fr[j].th);
@@ -1236,6 +1263,7 @@ int xo_refine_losses(const Element* el, int64_t n_el, const Reference* ref, cons
       } else {
         track_element(p, prep[j], 0, rc, 0, 0, 0);
         if (p.state != 1) { found = pos; break; }
+        if (kicked) pos = pos + L;
       }
     }
     if (!(found == found)) found = spos[e];

@@ -28,8 +28,8 @@ static_assert(sizeof(RecHdr) == 16, "record header is 16 bytes");
 enum : uint16_t { REC_CURV = 1, REC_RAD = 2, REC_PURE = 4, REC_BEND = 8 };
 // thick quadrupole: x is the focusing plane (k1 >= 0)
 enum : uint16_t { REC_QF = 1 };
-// thick bend: the full (exact) model
-enum : uint16_t { REC_BFULL = 1 };
+// thick bend: the full (exact) model; the full model with a gradient (kicks)
+enum : uint16_t { REC_BFULL = 1, REC_BKICK = 2 };
 // dipole edge: the non-linear model
 enum : uint16_t { REC_ENL = 1 };
 // REC_PURE: knl0 == ksl0 == 0 and hxl == 0.  REC_BEND: hxl != 0, hxl == knl0,

@@ -62,7 +62,12 @@ int64_t flops_of_row(const xt_element& e, int rad_mode) {
     // integrals (50) and zeta (10); full (the sector functions are per-element
     // constants): pz and the exit momentum (20), x (10), the chord and the arc
     // length (45), y and zeta (8)
-    case XT_BEND: return (e.p[4] != 0.0) ? 83 : 98;
+    case XT_BEND: {
+      if (e.p[4] == 0.0) return 98;
+      if (e.p[3] == 0.0) return 83;
+      const int64_t n = e.p[5] >= 1.0 ? (int64_t)e.p[5] : 1;
+      return 83 * (n + 1) + 4 * n;  // n + 1 bodies and n thin quadrupole kicks
+    }
     case XT_BEAMBEAM4D: {
       // round: the field and the kick; else two 40-term w(z) (~300 each), e^x and the rest
       const double sx2 = e.p[2] * e.p[2], sy2 = e.p[3] * e.p[3];
@@ -307,8 +312,10 @@ int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice*
           *err = "element " + std::to_string(i) + ": thick bend needs finite k0, h, k1 and a length L >= 0";
           return XT_ERR_INVALID;
         }
-        if (!(model == 0.0 || (model == 1.0 && k1 == 0.0))) {
-          *err = "element " + std::to_string(i) + ": thick bend model must be 0 (expanded) or 1 (full, k1 = 0)";
+        const double nk = e.p[5];
+        if (!(model == 0.0 || model == 1.0) || !(nk >= 0.0 && nk <= 64.0 && nk == std::floor(nk))) {
+          *err = "element " + std::to_string(i) + ": thick bend model must be 0 (expanded) or 1 (full), "
+                 "and the number of gradient kicks an integer in 0..64";
           return XT_ERR_INVALID;
         }
         prm = {k0, h, L, k1};
@@ -320,6 +327,23 @@ int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice*
           prm.push_back(C);
           prm.push_back(S);
           prm.push_back(S2);
+          if (k1 != 0.0) {  // the gradient by n kicks between exact bodies (see bend_full_kicks)
+            flags |= REC_BKICK;
+            const int n = nk >= 1.0 ? (int)nk : 1;
+            const double lh = L / (2.0 * n), ls = L / (double)n;
+            prm.push_back((double)n);
+            sector_funcs((h * lh) * (h * lh), &C, &S, &S2);
+            prm.push_back(C);
+            prm.push_back(S);
+            prm.push_back(S2);
+            sector_funcs((h * ls) * (h * ls), &C, &S, &S2);
+            prm.push_back(C);
+            prm.push_back(S);
+            prm.push_back(S2);
+            prm.push_back(lh);
+            prm.push_back(ls);
+            prm.push_back(k1 * ls);
+          }
         }
         break;
       }

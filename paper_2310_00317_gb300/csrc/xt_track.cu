@@ -636,6 +636,27 @@ __device__ __forceinline__ int bend_full_c(Part& p, double k0, double h, double 
   p.zeta = p.zeta + fma(-p.ep, lr, L);
   return 1;
 }
+// Full-model bend with a gradient k1 (no closed form): n thin quadrupole
+// kicks of strength k1 L/n between exact uniform-field bodies of lengths
+// L/(2n), L/n, ..., L/n, L/(2n) -- drift-kick splitting, symplectic and of
+// second order in L/n.  prm = k0, h, L, k1, C, S, S2 (whole body, unused
+// here), n, C, S, S2 at z = (h L/(2n))^2, C, S, S2 at z = (h L/n)^2,
+// L/(2n), L/n, k1 L/n.  sgn = -1 gives the inverse (the splitting is
+// symmetric, so the same sequence with every length and kick negated).
+__device__ __forceinline__ int bend_full_kicks(Part& p, const double* prm, double sgn) {
+  const double k0 = prm[0], h = prm[1];
+  const int n = (int)prm[7];
+  const double lh = sgn * prm[14], ls = sgn * prm[15], kl = sgn * prm[16];
+  int r = bend_full_c(p, k0, h, lh, prm[8], prm[9], prm[10]);
+  for (int i = 0; i < n && r == 1; i++) {
+    p.px = fma(-kl, p.x, p.px);
+    p.py = fma(kl, p.y, p.py);
+    r = (i + 1 < n) ? bend_full_c(p, k0, h, ls, prm[11], prm[12], prm[13])
+                    : bend_full_c(p, k0, h, lh, prm[8], prm[9], prm[10]);
+  }
+  return r;
+}
+
 __device__ __forceinline__ int bend_full(Part& p, double k0, double h, double L, const SinTab& sn) {
   const double th = h * L;
   double C, S, S2, S3;
@@ -1028,6 +1049,7 @@ __device__ __forceinline__ int element(Part& p, uint32_t type, uint32_t order, u
       return 1;
     case XT_BEND:  // prm = k0, h, L, k1; flags = REC_BFULL for the full model
       if constexpr (THICK) {
+        if (flags & REC_BKICK) return bend_full_kicks(p, prm, 1.0);
         if (flags & REC_BFULL) return bend_full_c(p, prm[0], prm[1], prm[2], prm[4], prm[5], prm[6]);
         bend_expanded(p, prm[0], prm[1], prm[2], prm[3], sn);
       }
@@ -1391,6 +1413,7 @@ __device__ __forceinline__ bool inverse_record(Part& p, uint32_t type, uint32_t 
       thick_quad(p, prm[0], -prm[1], (flags & REC_QF) != 0, sn);
       return true;
     case XT_BEND:
+      if (flags & REC_BKICK) return bend_full_kicks(p, prm, -1.0) == 1;
       if (flags & REC_BFULL) return bend_full_c(p, prm[0], prm[1], -prm[2], prm[4], prm[5], prm[6]) == 1;
       bend_expanded(p, prm[0], prm[1], -prm[2], prm[3], sn);
       return true;
@@ -1489,9 +1512,11 @@ __global__ void __launch_bounds__(128) refine_kernel(RefineArgs a) {
     const uint32_t type = hv.x & 0xFFFFu;
     const double* prm = (const double*)(a.lat + off + 16);
     // drifts, thick quadrupoles and thick bends in steps of at most ds (the
-    // thick maps are flows: their steps compose to the same map as one pass)
+    // thick maps are flows: their steps compose to the same map as one pass;
+    // a full bend with kicks is not, and is passed whole)
     const double L = (type == XT_DRIFT) ? prm[0] : (type == XT_QUAD) ? prm[1] : (type == XT_BEND) ? prm[2] : 0.0;
-    if ((type == XT_DRIFT || type == XT_QUAD || type == XT_BEND) && L > 0.0) {
+    const bool kicked = type == XT_BEND && ((hv.y & 0xFFFFu) & REC_BKICK);
+    if ((type == XT_DRIFT || type == XT_QUAD || type == XT_BEND) && L > 0.0 && !kicked) {
       const int64_t ns = (int64_t)ceil(L / a.ds);
       const double h = L / (double)ns;
       const double c = a.frame[4 * j], sn = a.frame[4 * j + 1], dx = a.frame[4 * j + 2], dy = a.frame[4 * j + 3];
@@ -1517,6 +1542,8 @@ __global__ void __launch_bounds__(128) refine_kernel(RefineArgs a) {
       found = pos;
       hit = true;
       break;
+    } else if (kicked) {
+      pos = pos + L;
     }
   }
   if (!hit) found = a.spos[e];

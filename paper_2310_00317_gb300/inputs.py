@@ -103,11 +103,12 @@ def quadrupole(k1: float, length: float):
     return _row(QUAD, 0, [k1, length])
 
 
-def bend(k0: float, h: float, length: float, k1: float = 0.0, full: bool = False):
+def bend(k0: float, h: float, length: float, k1: float = 0.0, full: bool = False, kicks: int = 0):
     """Thick sector bend: field k0 = B / (B rho) [1/m], frame curvature h
     [1/m] (k0 = h on the design orbit), reference length [m], gradient k1
-    [m^-2] (expanded model only); full=True selects the exact model."""
-    return _row(BEND, 0, [k0, h, length, k1, 1.0 if full else 0.0])
+    [m^-2]; full=True selects the exact model, in which a gradient is applied
+    as `kicks` thin quadrupole kicks (0 means 1) between exact bodies."""
+    return _row(BEND, 0, [k0, h, length, k1, 1.0 if full else 0.0, float(kicks)])
 
 
 def beambeam4d(q_n: float, beta_s: float, sigma_x: float, sigma_y: float, x_c: float = 0.0, y_c: float = 0.0):

@@ -93,7 +93,8 @@ def test_create_rejects_bad_element_parameters_before_cuda(L):
         I.quadrupole(0.1, -1.0),                      # negative length
         I.quadrupole(float("nan"), 1.0),              # non-finite gradient
         I._row(I.BEND, 0, [0.1, 0.1, 1.0, 0.0, 2.0]),  # unknown model
-        I.bend(0.1, 0.1, 1.0, k1=0.2, full=True),     # gradient in the full model
+        I.bend(0.1, 0.1, 1.0, k1=0.2, full=True, kicks=65),   # too many gradient kicks
+        I._row(I.BEND, 0, [0.1, 0.1, 1.0, 0.2, 1.0, 1.5]),  # a fractional number of kicks
         I.bend(0.1, 0.1, -1.0),                       # negative length
         I.bend(0.1, float("inf"), 1.0),               # non-finite curvature
         I._row(I.DIPEDGE, 0, [0.1, 0.1, 0.0, 0.0, 2.0, 0.0]),  # unknown edge model

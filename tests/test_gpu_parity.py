@@ -341,6 +341,37 @@ def test_refine_losses_through_thick_bends():
     assert sum(np.sum((lost > a + 1e-9) & (lost < b - 1e-9)) for a, b in body) > 20
 
 
+def combined_full_ring(n_cells=8, aperture=0.02):
+    """The small ring with combined-function full-model bends: a gradient of
+    -0.05 m^-2 (3 kicks) and of +0.04 m^-2 (1 kick) in the exact bodies."""
+    h = 1 / 1.5
+    rows = [I.cavity(2e6, 400e6, 180.0)]
+    for c in range(n_cells):
+        rows += [I.quadrupole(0.8, 0.3), I.drift(0.3), I.bend(h, h, 0.9, k1=-0.05, full=True, kicks=3), I.drift(0.3)]
+        rows += [I.multipole(knl=[0.0, 0.0, 0.5])]
+        rows += [I.quadrupole(-0.8, 0.3), I.drift(0.3), I.bend(h * 1.002, h, 0.9, k1=0.04, full=True), I.drift(0.3),
+                 I.aperture(aperture)]
+    return rows
+
+
+def test_full_bend_with_gradient_ring():
+    """2,000 particles for 100 turns through full bends with gradient kicks,
+    losses included, and the loss refinement backtracking through them."""
+    el = I.table(combined_full_ring())
+    p = random_particles(PROTON, 2000, 97, sx=5e-3, spx=2.5e-3, sd=1e-3)
+    g, o = gpu_track(el, PROTON, p, 100), oracle.track(el, PROTON, p, 100)
+    assert_close(g, o)
+    assert 200 < np.sum(o["state"] == 1) < 1900
+    el2 = I.table(combined_full_ring(n_cells=6, aperture=0.012))
+    o = oracle.track(el2, PROTON, p, 20)
+    assert np.sum(o["state"] == 0) > 300
+    s_o = oracle.refine_losses(el2, PROTON, o, 0.01, 128)
+    tr = xtgb.Tracker(el2, PROTON)
+    s_g = tr.refine_losses(xtgb.Particles.from_numpy(o), 0.01, 128).cpu().numpy()
+    tr.close()
+    assert_refined_close(s_g, s_o, 0.01)
+
+
 def test_nonlinear_dipole_edges():
     """Rectangular bends: non-linear entrance and exit edges (face angle
     theta/2, fint * hgap set) around full-model bends, linear edges around

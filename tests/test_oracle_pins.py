@@ -1038,6 +1038,85 @@ def test_full_and_expanded_bends_agree_to_first_order():
     assert 3.6 < gaps[0] / gaps[1] < 4.4
 
 
+def _gradient_bend_by_ode(k0, h, k1, L, z, ep):
+    """The flow of H = -(1 + h x) pz + k0 (x + h x^2 / 2) + k1 (x^2 - y^2) / 2,
+    pz = sqrt((1+delta)^2 - px^2 - py^2), integrated over s (DOP853 at
+    rtol 1e-13): x' = (1 + h x) px / pz, px' = h pz - k0 (1 + h x) - k1 x,
+    y' = (1 + h x) py / pz, py' = k1 y, zeta' = 1 - (1 + h x) ep / pz with
+    ep = (1+delta) beta0 / beta."""
+    from scipy.integrate import solve_ivp
+    x, px, y, py, zeta, opd = z
+
+    def rhs(_, u):
+        x_, px_, y_, py_, _z = u
+        pz = math.sqrt(opd * opd - px_ * px_ - py_ * py_)
+        f = 1.0 + h * x_
+        return [f * px_ / pz, h * pz - k0 * f - k1 * x_, f * py_ / pz, k1 * y_, 1.0 - f * ep / pz]
+
+    r = solve_ivp(rhs, (0.0, L), [x, px, y, py, zeta], method="DOP853", rtol=1e-13, atol=1e-16)
+    return r.y[:, -1]
+
+
+def test_full_bend_gradient_kicks_converge_to_the_exact_flow():
+    """The full model with a gradient (thin quadrupole kicks between exact
+    bodies) against the integrated equations of motion of the full bend's
+    Hamiltonian plus k1 (x^2 - y^2) / 2: the splitting is symmetric, so the
+    gap falls four-fold from 8 to 16 kicks (a wrong sign or strength of the
+    kick, or a body of the wrong length, leaves a gap that does not fall)."""
+    k0, h, k1, L = 0.52, 0.5, 0.35, 1.2
+    rng = np.random.default_rng(83)
+    n = 6
+    p = I.make_particles(PROTON, rng.normal(0, 2e-3, n), rng.normal(0, 1e-3, n), rng.normal(0, 2e-3, n),
+                         rng.normal(0, 1e-3, n), np.full(n, 0.01), rng.normal(0, 2e-3, n))
+    want = []
+    for i in range(n):
+        opd = 1.0 + p["delta"][i]
+        ep = opd / p["rvv"][i]
+        want.append(_gradient_bend_by_ode(k0, h, k1, L, (p["x"][i], p["px"][i], p["y"][i], p["py"][i],
+                                                        p["zeta"][i], opd), ep))
+    want = np.array(want)
+    gaps = []
+    for nk in (8, 16):
+        o = oracle.track(I.table([I.bend(k0, h, L, k1=k1, full=True, kicks=nk)]), PROTON, p, 1)
+        assert np.all(o["state"] == 1)
+        got = np.stack([o[k] for k in ("x", "px", "y", "py", "zeta")], 1)
+        gaps.append(np.max(np.abs(got - want) / (np.abs(want).max(0) + 1e-3)))
+    assert gaps[1] < 3e-4
+    assert 3.9 < gaps[0] / gaps[1] < 4.1, gaps
+
+
+def test_full_bend_gradient_linear_matrix():
+    """On the design orbit the full model with a gradient linearises to the
+    combined-function sector matrix (Kx = h^2 + k1 in x, cosh/sinh in y for
+    k1 > 0), the kicks' gap falling four-fold from 16 to 32 kicks."""
+    h, L, k1 = 0.2, 1.5, 0.3
+    w, wy = math.sqrt(h * h + k1), math.sqrt(k1)
+    c, s = math.cos(w * L), math.sin(w * L)
+    want = {(0, 0): c, (0, 1): s / w, (1, 0): -w * s, (1, 1): c, (0, 5): h * (1 - c) / (w * w), (1, 5): h * s / w,
+            (2, 2): math.cosh(wy * L), (2, 3): math.sinh(wy * L) / wy, (3, 2): wy * math.sinh(wy * L),
+            (3, 3): math.cosh(wy * L)}
+    gaps = []
+    for nk in (16, 32):
+        _, M = oracle.track_jacobian(I.table([I.bend(h, h, L, k1=k1, full=True, kicks=nk)]), PROTON, np.zeros(6))
+        gaps.append(max(abs(M[i, j] - v) for (i, j), v in want.items()))
+    assert gaps[1] < 2e-4
+    assert 3.8 < gaps[0] / gaps[1] < 4.2, gaps
+
+
+@pytest.mark.parametrize("nk", [1, 7])
+def test_full_bend_gradient_symplectic_and_reversible(nk):
+    """Off axis, off momentum, field and frame mismatched: M^T J M = J, and
+    the same element with -L brings the particle back."""
+    b = I.bend(0.55, 0.5, 1.3, k1=-0.4, full=True, kicks=nk)
+    z0 = np.array([2e-3, 1e-3, -1.5e-3, -2e-4, 0.02, 3e-3])
+    _, M = oracle.track_jacobian(I.table([b]), PROTON, z0)
+    assert np.max(np.abs(M.T @ J6 @ M - J6)) < 1e-12
+    p = I.make_particles(PROTON, [2e-3], [1e-3], [-1.5e-3], [-2e-4], [0.02], [3e-3])
+    o = oracle.track(I.table([b, I.bend(0.55, 0.5, -1.3, k1=-0.4, full=True, kicks=nk)]), PROTON, p, 1)
+    for k, sc in (("x", 2e-3), ("px", 1e-3), ("y", 1.5e-3), ("py", 2e-4), ("zeta", 0.02)):
+        assert abs(o[k][0] - p[k][0]) < 1e-13 * sc + 1e-15, k
+
+
 # --------------------------------------------------------------------------
 # Non-linear dipole edge
 
