@@ -69,8 +69,9 @@ extern "C" {
                            p[2] = lag [deg].  ptau += q0 V sin(lag - 2 pi f
                            zeta/(beta0 c)) / p0c, then delta, rpp, rvv.        */
 #define XT_DIPEDGE 4    /* p[0] = h [1/m], p[1] = e1 [rad], p[2] = hgap [m],
-                           p[3] = fint, p[4] = model (0 linear, 1 non-linear),
-                           p[5] = face (0 entrance, 1 exit; non-linear only).
+                           p[3] = fint, p[4] = model (0 linear, 1 non-linear,
+                           2 exact wedge), p[5] = face (0 entrance, 1 exit;
+                           models 1 and 2).
                            Linear edge: px += h tan(e1) x,
                            py -= h tan(e1 - psi) y,
                            psi = 2 h hgap fint (1 + sin^2 e1) / cos e1.
@@ -78,13 +79,22 @@ extern "C" {
                            single particle tracking"): the canonical map of
                            the generating function with the fringe term
                            (h/2) y^2 tan(e1 + s atan(px/pz)), s = +1 at the
-                           entrance and -1 at the exit (py solved by three
-                           fixed-point steps; x, y, zeta shifted), the wedge
-                           kick px += h tan(e1) x, and the finite-extent
-                           correction py += h (tan e1 - tan(e1 - psi)) y; its
-                           linearisation is the linear edge.  Lost with
-                           state -2 if pz is not real.  No inverse is formed
-                           for it in loss refinement.                       */
+                           entrance and -1 at the exit (py solved by
+                           fixed-point iteration to convergence; x, y, zeta
+                           shifted), the wedge kick px += h tan(e1) x, and
+                           the finite-extent correction
+                           py += h (tan e1 - tan(e1 - psi)) y; its
+                           linearisation is the linear edge.
+                           Exact wedge: the same fringe taken on the face
+                           itself (face angle 0 in the face's frame) between
+                           two exact changes of plane: at the entrance a
+                           straight line from the plane normal to the orbit
+                           to the face, then the circle in the field h back
+                           to the normal plane; at the exit the mirror
+                           sequence.  Its linearisation is the linear edge.
+                           Models 1 and 2: lost with state -2 if pz is not
+                           real or a plane is not reached; no inverse is
+                           formed for them in loss refinement.             */
 #define XT_LINEARMAP 5  /* p[0..35] = M (row-major 6x6), p[36..41] = d, acting
                            on (x, px, y, py, zeta, pzeta), pzeta = ptau/beta0:
                            v -> M v + d, then delta, rpp, rvv from ptau.      */

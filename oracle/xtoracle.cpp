@@ -610,6 +610,80 @@ static inline void edge_nonlinear(Part<T>& p, double k0, double t, double sgn, d
   if (sgn > 0.0) p.px = p.px + r21 * p.x;
 }
 
+// Change of reference plane (exact wedge geometry of a bend's inclined pole
+// face; section "Lattice modelling and single particle tracking": bends and
+// their edge effects).  The new plane is the old one rotated by the angle a
+// (cos a = ca, sin a = sa) about the vertical axis through the reference
+// point; between the two planes the particle moves in the uniform vertical
+// field k0 (k0 = 0: a straight line).  In the rotated axes the particle starts
+// at X = x ca, Z = -x sa with momenta px2 = px ca + pz sa, pzr = pz ca - px sa.
+// Circular motion keeps pX + k0 Z and pZ - k0 X, so on the new plane (Z = 0)
+//   px' = px2 - k0 x sa,
+//   x'  = x ca + (pz' - pzr)/k0 = x ca + x sa (px2 + px')/(pz' + pzr),
+// the second form from pz'^2 - pzr^2 = px2^2 - px'^2.  The direction turns by
+// dpsi with sin(dpsi) = (px2 pz' - pzr px')/p_h^2 = k0 G/p_h^2,
+// G = x sa (pzr + px2 (px2 + px')/(pz' + pzr)), and the horizontal path is
+// p_h dpsi/k0 = p_h (G/p_h^2) asin(v)/v, v = k0 G/p_h^2 (for k0 = 0 the
+// straight path to the plane).  y and zeta follow the path as in a drift:
+// y += py lr, zeta -= (1+delta) lr/rvv, lr = path/p_h; the plane has no
+// reference length.  Lost with code -2 if pz or pz' is not real or the plane
+// is not reached.
+template <class T>
+static inline T asin_over(const T& u);
+template <class T>
+static inline void plane_rotation(Part<T>& p, double k0, double ca, double sa, int turn, int elem) {
+  const T opd = 1.0 + p.delta;
+  const T ph2 = opd * opd - p.py * p.py;
+  const T pz2 = ph2 - p.px * p.px;
+  if (!(val(pz2) > 0.0 && val(pz2) < INFINITY)) { mark_lost(p, -2, turn, elem); return; }
+  const T pz = SQRT(pz2);
+  const T px2 = p.px * ca + pz * sa;
+  const T pzr = pz * ca - p.px * sa;
+  const T xs = p.x * sa;
+  const T pxf = px2 - k0 * xs;
+  const T pzf2 = ph2 - pxf * pxf;
+  if (!(val(pzf2) > 0.0)) { mark_lost(p, -2, turn, elem); return; }
+  const T pzf = SQRT(pzf2);
+  const T den = pzf + pzr;
+  if (!(val(den) > 0.0)) { mark_lost(p, -2, turn, elem); return; }
+  const T q = (px2 + pxf) / den;
+  const T G = xs * (pzr + px2 * q);
+  const T v = k0 * G / ph2;
+  if (!(std::fabs(val(v)) <= 1.0)) { mark_lost(p, -2, turn, elem); return; }
+  const T lr = (G / ph2) * asin_over(v);
+  p.x = p.x * ca + xs * q;
+  p.px = pxf;
+  p.y = p.y + p.py * lr;
+  p.zeta = p.zeta - lr * opd / p.rvv;
+}
+
+// Dipole edge with the exact wedge (model 2): the non-linear edge's fringe
+// taken on the pole face itself, between exact changes of plane.  At the
+// entrance the particle goes in a straight line from the plane normal to the
+// orbit to the face (rotated by e), receives the fringe there (the face is
+// its own normal plane, so the fringe's angle is the particle's angle to it:
+// t = 0), and then moves in the field k0 back to the normal plane (rotation
+// by -e).  The exit runs the mirror sequence: in the field to the face, the
+// fringe, a straight line to the normal plane.  To first order this is the
+// linear edge: px += k0 tan(e) x, py -= k0 tan(e - psi) y.
+template <class T>
+static inline void edge_wedge(Part<T>& p, double k0, double ce, double se, double sgn, double corr, int turn,
+                              int elem) {
+  if (sgn > 0.0) {
+    plane_rotation(p, 0.0, ce, se, turn, elem);
+    if (p.state != 1) return;
+    edge_nonlinear(p, k0, 0.0, sgn, 0.0, corr, turn, elem);
+    if (p.state != 1) return;
+    plane_rotation(p, k0, ce, -se, turn, elem);
+  } else {
+    plane_rotation(p, k0, ce, -se, turn, elem);
+    if (p.state != 1) return;
+    edge_nonlinear(p, k0, 0.0, sgn, 0.0, corr, turn, elem);
+    if (p.state != 1) return;
+    plane_rotation(p, 0.0, ce, se, turn, elem);
+  }
+}
+
 // asin(u)/u for |u| <= 1: the series sum_n (2n)!/(4^n n!^2 (2n+1)) u^(2n)
 // below |u| = 0.1 (to n = 12), asin(u)/u above.
 template <class T>
@@ -749,7 +823,8 @@ struct Prep {
   MultConst m;                           // multipole
   double krf, lagr, qv;                  // cavity
   double r21, r43;                       // dipole edge (linear model)
-  int enl;                               // dipole edge: 1 = non-linear model
+  int enl;                               // dipole edge: 1 = non-linear model, 2 = exact wedge
+  double ece, ese;                       // exact wedge: cos(e1), sin(e1)
   double ek0, et, esg, ecorr;            // non-linear edge: field, tan(e1), +1 entrance / -1 exit,
                                          // finite-extent vertical correction
   double M[36], d[6];                    // linear map in (x,px,y,py,zeta,ptau)
@@ -796,7 +871,9 @@ static Prep prepare(const Element& e, const RefConst& rc) {
       q.r21 = h * std::tan(e1);
       const double psi = 2.0 * h * hgap * fint * (1.0 + std::sin(e1) * std::sin(e1)) / std::cos(e1);
       q.r43 = -h * std::tan(e1 - psi);
-      q.enl = (e.p[4] != 0.0);
+      q.enl = (int)e.p[4];
+      q.ece = std::cos(e1);
+      q.ese = std::sin(e1);
       q.ek0 = h;
       q.et = std::tan(e1);
       q.esg = (e.p[5] != 0.0) ? -1.0 : 1.0;
@@ -882,7 +959,9 @@ static inline void track_element(Part<T>& p, const Prep& q, int rad_mode, const 
       break;
     }
     case T_DIPEDGE:
-      if (q.enl) {
+      if (q.enl == 2) {
+        edge_wedge(p, q.ek0, q.ece, q.ese, q.esg, q.ecorr, turn, elem);
+      } else if (q.enl) {
         edge_nonlinear(p, q.ek0, q.et, q.esg, q.r21, q.ecorr, turn, elem);
       } else {
         p.px = p.px + q.r21 * p.x;
@@ -1094,11 +1173,14 @@ using namespace xo;
 extern "C" {
 
 // A table row the oracle accepts: a known type, a multipole order 0..10, a
-// bend model 0 (expanded) or 1 (full) with 0..64 gradient kicks.
+// bend model 0 (expanded) or 1 (full) with 0..64 gradient kicks, an edge
+// model 0 (linear), 1 (non-linear) or 2 (exact wedge) on face 0 or 1.
 static bool row_ok(const Element& e) {
   if (e.type < 0 || e.type > T_SPACECHARGE) return false;
   if (e.type == T_MULTIPOLE && (e.order < 0 || e.order > 10)) return false;
   if (e.type == T_BEND && !(e.p[4] == 0.0 || e.p[4] == 1.0)) return false;
+  if (e.type == T_DIPEDGE && !((e.p[4] == 0.0 || e.p[4] == 1.0 || e.p[4] == 2.0) && (e.p[5] == 0.0 || e.p[5] == 1.0)))
+    return false;
   if (e.type == T_BEND && !(e.p[5] >= 0.0 && e.p[5] <= 64.0 && e.p[5] == std::floor(e.p[5]))) return false;
   return true;
 }

@@ -31,7 +31,7 @@ enum : uint16_t { REC_QF = 1 };
 // thick bend: the full (exact) model; the full model with a gradient (kicks)
 enum : uint16_t { REC_BFULL = 1, REC_BKICK = 2 };
 // dipole edge: the non-linear model
-enum : uint16_t { REC_ENL = 1 };
+enum : uint16_t { REC_ENL = 1, REC_EWEDGE = 2 };
 // REC_PURE: knl0 == ksl0 == 0 and hxl == 0.  REC_BEND: hxl != 0, hxl == knl0,
 // ksl0 == 0.  Without radiation these multipoles add the last Horner step
 // straight into px, py (and a bend's -knl0 + hxl (1+delta) becomes hxl delta).

@@ -48,7 +48,7 @@ int64_t flops_of_row(const xt_element& e, int rad_mode) {
     }
     case XT_CAVITY: return 18;
     // non-linear: three fixed-point steps (8 each), the shifts and kicks (26)
-    case XT_DIPEDGE: return (e.p[4] != 0.0) ? 50 : 4;
+    case XT_DIPEDGE: return (e.p[4] == 2.0) ? 120 : (e.p[4] != 0.0) ? 50 : 4;  // exact wedge: two changes of plane
     case XT_LINEARMAP: return 85;
     case XT_APERTURE: return 3;
     case XT_XYSHIFT: return 2;
@@ -221,13 +221,16 @@ int compile_lattice(const xt_element* table, int64_t n, const Refc& rc, Lattice*
       }
       case XT_DIPEDGE: {
         const double h = e.p[0], e1 = e.p[1], hgap = e.p[2], fint = e.p[3];
-        if (!((e.p[4] == 0.0 || e.p[4] == 1.0) && (e.p[5] == 0.0 || e.p[5] == 1.0))) {
-          *err = "element " + std::to_string(i) + ": dipole edge model and face must be 0 or 1";
+        if (!((e.p[4] == 0.0 || e.p[4] == 1.0 || e.p[4] == 2.0) && (e.p[5] == 0.0 || e.p[5] == 1.0))) {
+          *err = "element " + std::to_string(i) + ": dipole edge model must be 0, 1 or 2 and face 0 or 1";
           return XT_ERR_INVALID;
         }
         const double psi = 2.0 * h * hgap * fint * (1.0 + std::sin(e1) * std::sin(e1)) / std::cos(e1);
         const double r21 = h * std::tan(e1), r43 = -h * std::tan(e1 - psi);
-        if (e.p[4] == 1.0) {  // non-linear: r21, r43, k0, tan(e1), +1 entrance / -1 exit, correction
+        if (e.p[4] == 2.0) {  // exact wedge: no wedge kick, r43, k0, t = 0 on the face, s, correction, cos, sin
+          prm = {0.0, r43, h, 0.0, (e.p[5] != 0.0) ? -1.0 : 1.0, r21 + r43, std::cos(e1), std::sin(e1)};
+          flags |= REC_ENL | REC_EWEDGE;
+        } else if (e.p[4] == 1.0) {  // non-linear: r21, r43, k0, tan(e1), +1 entrance / -1 exit, correction
           prm = {r21, r43, h, std::tan(e1), (e.p[5] != 0.0) ? -1.0 : 1.0, r21 + r43};
           flags |= REC_ENL;
         } else {

@@ -970,6 +970,58 @@ __device__ __forceinline__ int edge_nonlinear(Part& p, const double* prm) {
   return 1;
 }
 
+// Change of reference plane through a uniform vertical field k0 (k0 = 0:
+// field-free): the new plane is the old one turned by the angle a (ca, sa)
+// about the vertical axis through the reference point.  The particle starts
+// at X = x ca, Z = -x sa of the new axes, with momenta px2 = px ca + pz sa,
+// pzr = pz ca - px sa.  pX + k0 Z and pZ - k0 X are constant on its circle, so
+// on the new plane px' = px2 - k0 x sa and x' = x ca + x sa (px2 + px')/(pz'
+// + pzr); the direction turns by asin(k0 G/p_h^2), G = x sa (pzr + px2 (px2 +
+// px')/(pz' + pzr)), and the path over p_h is lr = (G/p_h^2) asin(v)/v,
+// v = k0 G/p_h^2; y += py lr, zeta -= ep lr.  Returns -2 if pz or pz' is not
+// real or the plane is not reached.
+__device__ __forceinline__ int plane_rot(Part& p, double k0, double ca, double sa) {
+  const double ph2m1 = fma(-p.py, p.py, p.dm1);  // p_h^2 - 1
+  const double u = fma(-p.px, p.px, ph2m1);      // pz^2 - 1
+  if (!gt_minus_one(u)) return -2;
+  const double pz = sqrt(1.0 + u);
+  const double px2 = fma(p.px, ca, pz * sa);
+  const double pzr = fma(pz, ca, -(p.px * sa));
+  const double xs = p.x * sa;
+  const double pxf = fma(-k0, xs, px2);
+  const double uf = fma(-pxf, pxf, ph2m1);
+  if (!gt_minus_one(uf)) return -2;
+  const double den = sqrt(1.0 + uf) + pzr;
+  if (!is_positive(den)) return -2;
+  const double q = (px2 + pxf) / den;
+  const double iph2 = 1.0 / (1.0 + ph2m1);
+  const double G = xs * fma(px2, q, pzr);
+  const double v = (k0 * G) * iph2;
+  if (!abs_le_one(v)) return -2;
+  const double lr = (G * iph2) * asin_over(v);
+  p.x = fma(xs, q, p.x * ca);
+  p.px = pxf;
+  p.y = fma(p.py, lr, p.y);
+  p.zeta = fma(-p.ep, lr, p.zeta);
+  return 1;
+}
+
+// Dipole edge with the exact wedge: the non-linear fringe taken on the pole
+// face (in its own frame, where the face angle is zero) between exact
+// changes of plane.  Entrance: a straight line from the normal plane to the
+// face (turned by e), the fringe, the field k0 back to the normal plane (-e);
+// the exit is the mirror sequence.  prm = 0, r43, k0, 0, s (+1 entrance, -1
+// exit), corr, cos e, sin e (edge_nonlinear reads the first six: no wedge
+// kick, t = 0).
+__device__ __forceinline__ int edge_wedge(Part& p, const double* prm) {
+  const double k0 = prm[2], ce = prm[6], se = prm[7];
+  const bool entrance = prm[4] > 0.0;
+  int r = entrance ? plane_rot(p, 0.0, ce, se) : plane_rot(p, k0, ce, -se);
+  if (r == 1) r = edge_nonlinear(p, prm);
+  if (r == 1) r = entrance ? plane_rot(p, k0, ce, -se) : plane_rot(p, 0.0, ce, se);
+  return r;
+}
+
 // One record.  Returns the loss code (1 = still alive).  THICK = false is the
 // instantiation for tables without beam-beam lenses, thick quadrupoles,
 // bends or non-linear edges (the host chooses it only for such tables): their
@@ -1039,6 +1091,7 @@ __device__ __forceinline__ int element(Part& p, uint32_t type, uint32_t order, u
     }
     case XT_DIPEDGE:
       if constexpr (THICK) {
+        if (flags & REC_EWEDGE) return edge_wedge(p, prm);
         if (flags & REC_ENL) return edge_nonlinear(p, prm);
       }
       p.px = fma(prm[0], p.x, p.px);
@@ -1405,7 +1458,7 @@ __device__ __forceinline__ bool inverse_record(Part& p, uint32_t type, uint32_t 
       return true;
     }
     case XT_DIPEDGE:
-      if (flags & REC_ENL) return false;  // no inverse formed for the non-linear edge
+      if (flags & REC_ENL) return false;  // no inverse formed for the non-linear edges
       p.px = fma(-prm[0], p.x, p.px);
       p.py = fma(-prm[1], p.y, p.py);
       return true;

@@ -66,11 +66,13 @@ def cavity(voltage: float, frequency: float, lag_deg: float):
 
 
 def dipedge(h: float, e1: float, hgap: float = 0.0, fint: float = 0.0, nonlinear: bool = False,
-            exit: bool = False):
+            exit: bool = False, wedge: bool = False):
     """Dipole edge of field h [1/m] with face angle e1 [rad] and fringe
-    extent hgap [m] x fint; nonlinear=True selects the non-linear model, for
-    which exit=True marks the magnet's exit face."""
-    return _row(DIPEDGE, 0, [h, e1, hgap, fint, 1.0 if nonlinear else 0.0, 1.0 if exit else 0.0])
+    extent hgap [m] x fint; nonlinear=True selects the non-linear model and
+    wedge=True the non-linear fringe on the face between exact changes of
+    plane (the exact wedge); for both, exit=True marks the magnet's exit face."""
+    model = 2.0 if wedge else (1.0 if nonlinear else 0.0)
+    return _row(DIPEDGE, 0, [h, e1, hgap, fint, model, 1.0 if exit else 0.0])
 
 
 def linear_map(M, d=None):

@@ -97,7 +97,7 @@ def test_create_rejects_bad_element_parameters_before_cuda(L):
         I._row(I.BEND, 0, [0.1, 0.1, 1.0, 0.2, 1.0, 1.5]),  # a fractional number of kicks
         I.bend(0.1, 0.1, -1.0),                       # negative length
         I.bend(0.1, float("inf"), 1.0),               # non-finite curvature
-        I._row(I.DIPEDGE, 0, [0.1, 0.1, 0.0, 0.0, 2.0, 0.0]),  # unknown edge model
+        I._row(I.DIPEDGE, 0, [0.1, 0.1, 0.0, 0.0, 3.0, 0.0]),  # unknown edge model
         I._row(I.DIPEDGE, 0, [0.1, 0.1, 0.0, 0.0, 1.0, 3.0]),  # unknown face
         I.spacecharge(1e10, 0.0, 0.0, 1e-3, 1.0),     # zero sigma_x
         I.spacecharge(-1e10, 0.0, 1e-3, 1e-3, 1.0),   # negative line density

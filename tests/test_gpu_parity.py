@@ -75,9 +75,31 @@ def rel_errors(g, o, keys=oracle.FLOAT_FIELDS):
     return out
 
 
-def assert_close(g, o, rtol=RTOL, where=""):
+def assert_close(g, o, rtol=RTOL, where="", floor=None):
     """The FP64 criterion against the oracle: identical loss outcomes, and
-    coordinates within rtol relative (see rel_errors)."""
+    coordinates within rtol relative (see rel_errors).  With floor (the
+    oracle's contracted build on the same input, which differs from the
+    oracle by rounding alone), a coordinate whose floor exceeds rtol
+    somewhere in the ensemble is held to three times the floor's worst
+    difference and its 90th percentile to three times the floor's: the
+    kernel must reproduce the oracle as closely as the oracle reproduces
+    itself (small rings of strong bends, where each pass rounds the exit
+    momentum to 1e-13 of the beam size and 100 turns reach 2e-12)."""
+    if floor is not None:
+        for k in oracle.INT_FIELDS:
+            assert np.array_equal(np.asarray(floor[k]), np.asarray(o[k])), "floor run: " + k
+        ef = rel_errors(floor, o)
+        eg = rel_errors(g, o)
+        for k in oracle.FLOAT_FIELDS:
+            e, f = eg[k], ef[k]
+            if not e.size:
+                continue
+            bound = max(rtol, 3.0 * float(np.max(f)))
+            if not np.all(e <= bound):
+                i = int(np.argmax(np.where(np.isfinite(e), e, np.inf)))
+                raise AssertionError("%s%s: relative difference %.3g > %.3g (floor %.3g) for %d particles"
+                                     % (where, k, e[i], bound, float(np.max(f)), int(np.sum(~(e <= bound)))))
+            assert np.percentile(e, 90) <= max(rtol, 3.0 * np.percentile(f, 90)), (where, k)
     for k in oracle.INT_FIELDS:
         same = np.asarray(g[k]) == np.asarray(o[k])
         if not np.all(same):
@@ -85,6 +107,8 @@ def assert_close(g, o, rtol=RTOL, where=""):
             i = bad[0]
             raise AssertionError("%s%s differs for %d of %d particles; first %d: gpu %r oracle %r"
                                  % (where, k, bad.size, same.size, i, g[k][i], o[k][i]))
+    if floor is not None:
+        return
     for k, e in rel_errors(g, o).items():
         if e.size and not np.all(e <= rtol):
             i = int(np.argmax(np.where(np.isfinite(e), e, np.inf)))
@@ -312,7 +336,7 @@ def test_thick_bend_ring():
     for i, (px, py) in enumerate([(0.9, 0.0), (-0.9, 0.1), (0.3, 0.95), (0.99, 0.0)]):
         p["px"][i], p["py"][i] = px, py
     g, o = gpu_track(el, PROTON, p, 100), oracle.track(el, PROTON, p, 100)
-    assert_close(g, o)
+    assert_close(g, o, floor=oracle.track(el, PROTON, p, 100, fused=True))
     assert 200 < np.sum(o["state"] == 1) < 1900
 
 
@@ -360,7 +384,7 @@ def test_full_bend_with_gradient_ring():
     el = I.table(combined_full_ring())
     p = random_particles(PROTON, 2000, 97, sx=5e-3, spx=2.5e-3, sd=1e-3)
     g, o = gpu_track(el, PROTON, p, 100), oracle.track(el, PROTON, p, 100)
-    assert_close(g, o)
+    assert_close(g, o, floor=oracle.track(el, PROTON, p, 100, fused=True))
     assert 200 < np.sum(o["state"] == 1) < 1900
     el2 = I.table(combined_full_ring(n_cells=6, aperture=0.012))
     o = oracle.track(el2, PROTON, p, 20)
@@ -393,8 +417,35 @@ def test_nonlinear_dipole_edges():
     for i, (px, py) in enumerate([(0.3, 0.2), (-0.5, 0.1), (0.05, 0.9)]):
         p["px"][i], p["py"][i] = px, py
     g, o = gpu_track(el, PROTON, p, 100), oracle.track(el, PROTON, p, 100)
-    assert_close(g, o)
+    assert_close(g, o, floor=oracle.track(el, PROTON, p, 100, fused=True))
     assert 100 < np.sum(o["state"] == 1) < 1950
+
+
+def test_exact_wedge_dipole_edges():
+    """Rectangular bends with the exact wedge: entrance and exit edges at
+    theta/2 and at unequal angles (fint * hgap set on one pair) around
+    full-model bends, in the small ring; 2,000 particles at up to 5 mrad plus
+    a few steep ones (some lost at a plane they cannot reach), 100 turns."""
+    h = 1 / 1.5
+    th = h * 0.9
+    rows = [I.cavity(2e6, 400e6, 180.0)]
+    for c in range(8):
+        rows += [I.quadrupole(0.8, 0.3), I.drift(0.3),
+                 I.dipedge(h, th / 2, hgap=0.02, fint=0.5, wedge=True),
+                 I.bend(h, h, 0.9, full=True),
+                 I.dipedge(h, th / 2, hgap=0.02, fint=0.5, wedge=True, exit=True), I.drift(0.3),
+                 I.multipole(knl=[0.0, 0.0, 0.5]), I.quadrupole(-0.8, 0.3), I.drift(0.3),
+                 I.dipedge(h, 0.05, wedge=True), I.bend(h, h, 0.9, k1=-0.05, full=True, kicks=2),
+                 I.dipedge(h, 0.08, wedge=True, exit=True), I.drift(0.3),
+                 I.aperture(0.02)]
+    el = I.table(rows)
+    p = random_particles(PROTON, 2000, 101, sx=4e-3, spx=2e-3, sd=1e-3)
+    for i, (px, py) in enumerate([(0.3, 0.2), (-0.5, 0.1), (0.05, 0.9), (0.97, 0.0)]):
+        p["px"][i], p["py"][i] = px, py
+    g, o = gpu_track(el, PROTON, p, 100), oracle.track(el, PROTON, p, 100)
+    assert_close(g, o, floor=oracle.track(el, PROTON, p, 100, fused=True))
+    assert 100 < np.sum(o["state"] == 1) < 1950
+    assert np.any(o["state"] == -2)
 
 
 def test_space_charge_lenses():

@@ -1209,6 +1209,132 @@ def test_nonlinear_edge_against_soft_fringe_integration(exit_face):
     assert gn_e[2] < 0.2 * gl_e[2] and gn_e[3] < 0.02 * gl_e[3]
 
 
+@pytest.mark.parametrize("exit_face", [False, True])
+def test_exact_wedge_edge_against_soft_fringe_integration(exit_face):
+    """The edge with the exact wedge (the fringe on the face between exact
+    changes of plane) against the tanh fringe integrated through, as in the
+    test above: at face angles of 0.12 and 0.3 rad it converges like the
+    non-linear edge at normal incidence (the x gap falls four-fold per
+    halving of the fringe length, px within 1e-10 and falling), and the
+    first-order px residual that the non-linear edge's plain wedge kick keeps
+    (1e-8 and more) is gone.  At normal incidence it is the non-linear edge."""
+    k0, a = 0.01, 0.05
+    rng = np.random.default_rng(89)
+    n = 6
+    xs, pxs = rng.uniform(-5e-3, 5e-3, n), rng.uniform(-0.02, 0.02, n)
+    ys, pys = rng.uniform(-5e-3, 5e-3, n), rng.uniform(-5e-3, 5e-3, n)
+    p = I.make_particles(PROTON, xs, pxs, ys, pys, np.zeros(n), np.zeros(n))
+
+    def run(e, **kw):
+        edge = I.dipedge(k0, e, exit=exit_face, **kw)
+        body = I.bend(k0, 0.0, a, full=True)
+        rows = [body, edge, I.drift(a)] if exit_face else [I.drift(a), edge, body]
+        return oracle.track(I.table(rows), PROTON, p, 1)
+
+    def gaps(o, e, lam):
+        g = np.zeros(4)
+        for i in range(n):
+            u = _soft_fringe(k0, e, lam, a, (xs[i], ys[i], pxs[i], pys[i]), exit_face)
+            g = np.maximum(g, np.abs([o["x"][i] - u[0], o["px"][i] - u[2], o["y"][i] - u[1], o["py"][i] - u[3]]))
+        return g
+
+    w0, n0 = run(0.0, wedge=True), run(0.0, nonlinear=True)
+    for k in ("x", "px", "y", "py", "zeta"):
+        assert np.array_equal(w0[k], n0[k]), k
+    g_normal = gaps(w0, 0.0, 1e-3)
+    for e in (0.12, 0.3):
+        ow = run(e, wedge=True)
+        gw = [gaps(ow, e, lam) for lam in (2e-3, 1e-3)]
+        gn = gaps(run(e, nonlinear=True), e, 1e-3)
+        assert 3.0 < gw[0][0] / gw[1][0] < 5.0 and gw[1][0] < 1e-8
+        assert gw[1][1] < 1e-10 and gw[1][1] < 1e-3 * gn[1] and gn[1] > 1e-8
+        assert gw[1][2] < 2.0 * g_normal[2] + 1e-11 and gw[1][3] < 2.0 * g_normal[3]
+
+
+@pytest.mark.parametrize("exit_face", [False, True])
+def test_exact_wedge_edge_linearises_to_the_linear_edge_and_is_symplectic(exit_face):
+    kw = dict(hgap=0.02, fint=0.5)
+    _, Mw = oracle.track_jacobian(I.table([I.dipedge(0.08, 0.15, wedge=True, exit=exit_face, **kw)]), PROTON,
+                                  np.zeros(6))
+    _, Ml = oracle.track_jacobian(I.table([I.dipedge(0.08, 0.15, **kw)]), PROTON, np.zeros(6))
+    assert np.max(np.abs(Mw - Ml)) < 1e-15 and abs(Ml[1, 0]) > 1e-3 and abs(Ml[3, 2]) > 1e-3
+    el = I.table([I.dipedge(0.3, 0.2, hgap=0.03, fint=0.4, wedge=True, exit=exit_face)])
+    _, M = oracle.track_jacobian(el, PROTON, np.array([8e-3, 3e-2, -7e-3, 1e-2, 0.01, 2e-3]))
+    assert np.max(np.abs(M.T @ J6 @ M - J6)) < 1e-14
+    assert abs(M[1, 1] - 1.0) > 1e-5  # px' depends on px: not the plain wedge kick
+
+
+def _rect_by_geometry(h, L, e1, e2, x, px, delta, zeta):
+    """A dipole of field h between two inclined pole faces, in the midplane,
+    by plane geometry in 40 digits.  The reference arc (radius 1/h, length
+    L) starts at the origin heading along Z; the entrance face is the line
+    through the origin at the angle e1 to the X axis (downstream at X > 0),
+    the exit face the line through the arc's end at the angle e2 to the
+    radial line (upstream on the outer side).  The particle runs straight to
+    the entrance face, on its circle (centre Q + (-pz, px)/h) to the exit
+    face, and straight to the plane normal to the arc's end, where x, px and
+    the path length are read."""
+    mp = mpmath.mp
+    mp.dps = 40
+    m0, _, p0c = PROTON
+    b0 = mpmath.mpf(p0c) / mpmath.sqrt(mpmath.mpf(p0c) ** 2 + mpmath.mpf(m0) ** 2)
+    opd = 1 + mpmath.mpf(delta)
+    beta = opd * p0c / mpmath.sqrt((opd * p0c) ** 2 + mpmath.mpf(m0) ** 2)
+    rv0v = b0 / beta
+    h, L, e1, e2, x, px = [mpmath.mpf(v) for v in (h, L, e1, e2, x, px)]
+    pz = mpmath.sqrt(opd ** 2 - px ** 2)
+    ph = opd
+    t = x * mpmath.sin(e1) / (pz * mpmath.cos(e1) - px * mpmath.sin(e1))
+    Q = mpmath.matrix([x + t * px, t * pz])
+    l1 = t * ph
+    Cp = Q + mpmath.matrix([-pz, px]) / h
+    rho = ph / h
+    th = h * L
+    R = 1 / h
+    Pe = mpmath.matrix([-R + R * mpmath.cos(th), R * mpmath.sin(th)])
+    eX = mpmath.matrix([mpmath.cos(th), mpmath.sin(th)])
+    eZ = mpmath.matrix([-mpmath.sin(th), mpmath.cos(th)])
+    f = eX * mpmath.cos(e2) - eZ * mpmath.sin(e2)
+    d = Pe - Cp
+    b = f[0] * d[0] + f[1] * d[1]
+    c = d[0] ** 2 + d[1] ** 2 - rho ** 2
+    a = min((-b - mpmath.sqrt(b * b - c), -b + mpmath.sqrt(b * b - c)), key=abs)
+    F = Pe + a * f
+    a0, a1 = Q - Cp, F - Cp
+    v1 = mpmath.matrix([-a1[1], a1[0]]) * (ph / rho)
+    phi = mpmath.atan2(a0[0] * a1[1] - a0[1] * a1[0], a0[0] * a1[0] + a0[1] * a1[1])
+    l2 = rho * phi
+    Xf, Zf = (F - Pe)[0] * eX[0] + (F - Pe)[1] * eX[1], (F - Pe)[0] * eZ[0] + (F - Pe)[1] * eZ[1]
+    pX, pZ = v1[0] * eX[0] + v1[1] * eX[1], v1[0] * eZ[0] + v1[1] * eZ[1]
+    t3 = -Zf / pZ
+    l = l1 + l2 + t3 * ph
+    out = dict(x=Xf + t3 * pX, px=pX, zeta=mpmath.mpf(zeta) + L - rv0v * opd * l / ph)
+    return {k: float(v) for k, v in out.items()}
+
+
+@pytest.mark.parametrize("h,L,e1,e2", [(1 / 1.5, 0.9, 0.3, 0.3), (1 / 1.5, 0.9, 0.1, 0.45),
+                                       (0.05, 2.0, 0.05, -0.02), (1 / 2800.0, 14.3, 14.3 / 5600.0, 14.3 / 5600.0)])
+def test_rectangular_bend_with_exact_wedges_against_plane_geometry(h, L, e1, e2):
+    """Entrance edge, full sector body and exit edge, the edges with the
+    exact wedge, against the straight-circle-straight construction in the
+    midplane: a rectangular small-ring dipole, unequal faces, a face inclined
+    the other way, and an LHC-like rectangular dipole, over random particles
+    off axis, at angles and off momentum."""
+    rng = np.random.default_rng(73)
+    n = 12
+    xs, pxs, ds_ = rng.normal(0, 2e-3, n), rng.normal(0, 1e-3, n), rng.normal(0, 2e-3, n)
+    p = I.make_particles(PROTON, xs, pxs, np.zeros(n), np.zeros(n), np.full(n, 0.01), ds_)
+    rows = [I.dipedge(h, e1, wedge=True), I.bend(h, h, L, full=True), I.dipedge(h, e2, wedge=True, exit=True)]
+    o = oracle.track(I.table(rows), PROTON, p, 1)
+    assert np.all(o["state"] == 1)
+    for i in range(n):
+        g = _rect_by_geometry(h, L, e1, e2, xs[i], pxs[i], p["delta"][i], 0.01)
+        for k in ("x", "px"):
+            assert abs(o[k][i] - g[k]) < 4e-15 * L + 2e-15 * abs(g[k]), (k, i, o[k][i], g[k])
+        assert abs(o["zeta"][i] - g["zeta"]) < 2e-14 * L, (i, o["zeta"][i], g["zeta"])
+        assert o["y"][i] == 0.0 and o["py"][i] == 0.0
+
+
 # --------------------------------------------------------------------------
 # Frozen space charge
 
