@@ -85,7 +85,9 @@ struct Epi {
   bf16_t* out_b;        // EPI_GELU: activation; EPI_DGRAD: bf16 dZ
   float* out_f;         // EPI_F32ADD
   float* colsum;        // EPI_DGRAD (may be null): column sums of the fp32 dZ added here (the bias gradient)
+  bf16_t* out_bt;       // EPI_GELU, EPI_DGRAD (may be null): out_b transposed, element (row, col) at col * ldt + row
   int ld;               // leading dimension of every output / zprev (a multiple of 4)
+  int ldt;              // leading dimension of out_bt (>= M)
   int* status;          // set to 1 if a tensor-core or copy wait gave up
 };
 
@@ -202,6 +204,17 @@ __device__ __forceinline__ void epilogue(const Epi& e, int row, int col, const u
 #pragma unroll
     for (int q = 0; q < CH / 8; q++)
       *(uint4*)(e.out_b + o + 8 * q) = make_uint4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+    if (e.out_bt) {
+      // the transposed copy the weight gradient reads (its K is the batch):
+      // the warp's 32 lanes are 32 consecutive rows, so each column is one
+      // contiguous 64-byte store
+      bf16_t* t = e.out_bt + (int64_t)col * e.ldt + row;
+#pragma unroll
+      for (int i = 0; i < CH / 2; i++) {  // the packed pair's bits: column 2i low, 2i + 1 high
+        t[(int64_t)(2 * i) * e.ldt] = (bf16_t)(h[i] & 0xFFFFu);
+        t[(int64_t)(2 * i + 1) * e.ldt] = (bf16_t)(h[i] >> 16);
+      }
+    }
   }
 }
 
@@ -466,6 +479,18 @@ __global__ void to_bf16_kernel(const float* __restrict__ x, bf16_t* __restrict__
     y[i] = f2bf(x[i]);
 }
 
+// The 16-wide input batch in bf16, row-major (y) and transposed (yt, row c
+// of length ldt holds column c), for training.
+__global__ void to_bf16_t_kernel(const float* __restrict__ x, bf16_t* __restrict__ y, bf16_t* __restrict__ yt,
+                                 int64_t B, int64_t ldt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B * 16;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const bf16_t h = f2bf(x[i]);
+    y[i] = h;
+    yt[(i & 15) * ldt + (i >> 4)] = h;
+  }
+}
+
 // bf16 copies of the weights: W (out x in) and W^T (in x out).
 __global__ void refresh_weights_kernel(const float* __restrict__ master, bf16_t* __restrict__ wb,
                                        bf16_t* __restrict__ wtb, int out, int in) {
@@ -529,25 +554,46 @@ __global__ void loss_kernel(const float* __restrict__ out, const float* __restri
   if ((threadIdx.x & 31) == 0) atomicAdd(&scal[0], s);
 }
 
-// Head backward: dW5, db5 (atomics over batch slices), dZ4 and its column
-// sums (the top hidden layer's bias gradient).
+// Head backward: dW5, db5 (atomics over batch slices), dZ4, its transpose
+// (dzT, leading dimension ldt, for the weight gradient) and its column sums
+// (the top hidden layer's bias gradient).  A block takes HB_TILE samples at
+// a time and stages their bf16 dZ in shared memory, so that each transposed
+// row goes out as one contiguous 16-byte piece.
+constexpr int HB_TILE = 8;
 __global__ void head_backward_kernel(const float* __restrict__ dout, const bf16_t* __restrict__ a4,
                                      const bf16_t* __restrict__ w5, const float* __restrict__ z4, int64_t B,
                                      float* __restrict__ gw5, float* __restrict__ gb5, float* __restrict__ dzf,
-                                     bf16_t* __restrict__ dzb, float* __restrict__ gb4) {
+                                     bf16_t* __restrict__ dzb, float* __restrict__ gb4, bf16_t* __restrict__ dzT,
+                                     int64_t ldt) {
+  __shared__ __align__(16) bf16_t tile[256][HB_TILE];
   const int k = threadIdx.x;  // 256 threads: one hidden unit each
   const float w0 = bf2f(w5[k]), w1 = bf2f(w5[256 + k]);
   float s0 = 0.f, s1 = 0.f, d0 = 0.f, d1 = 0.f, sb = 0.f;
-  for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
-    const float g0 = dout[2 * b], g1 = dout[2 * b + 1];
-    const float a = bf2f(a4[b * 256 + k]);
-    s0 = fmaf(g0, a, s0);
-    s1 = fmaf(g1, a, s1);
-    if (k == 0) { d0 += g0; d1 += g1; }
-    const float dz = (g0 * w0 + g1 * w1) * gelu_grad_f(z4[b * 256 + k]);
-    dzf[b * 256 + k] = dz;
-    dzb[b * 256 + k] = f2bf(dz);
-    sb += dz;
+  for (int64_t b0 = (int64_t)blockIdx.x * HB_TILE; b0 < B; b0 += (int64_t)gridDim.x * HB_TILE) {
+#pragma unroll
+    for (int j = 0; j < HB_TILE; j++) {
+      const int64_t b = b0 + j;
+      bf16_t hb = f2bf(0.0f);
+      if (b < B) {
+        const float g0 = dout[2 * b], g1 = dout[2 * b + 1];
+        const float a = bf2f(a4[b * 256 + k]);
+        s0 = fmaf(g0, a, s0);
+        s1 = fmaf(g1, a, s1);
+        if (k == 0) { d0 += g0; d1 += g1; }
+        const float dz = (g0 * w0 + g1 * w1) * gelu_grad_f(z4[b * 256 + k]);
+        dzf[b * 256 + k] = dz;
+        hb = f2bf(dz);
+        dzb[b * 256 + k] = hb;
+        sb += dz;
+      }
+      tile[k][j] = hb;
+    }
+    __syncthreads();
+    // row r of dzT gets tile[r][0 .. HB_TILE): thread k writes row k (ldt and
+    // b0 are multiples of 8, so the piece is 16-byte aligned; a piece past
+    // ldt is never written because ldt is a multiple of 16 >= B)
+    if (b0 + HB_TILE <= ldt) *(uint4*)(dzT + (int64_t)k * ldt + b0) = *(const uint4*)&tile[k][0];
+    __syncthreads();
   }
   atomicAdd(&gb4[k], sb);  // the top hidden layer's bias gradient
   atomicAdd(&gw5[k], s0);
@@ -555,25 +601,6 @@ __global__ void head_backward_kernel(const float* __restrict__ dout, const bf16_
   if (k == 0) {
     atomicAdd(&gb5[0], d0);
     atomicAdd(&gb5[1], d1);
-  }
-}
-
-// dst[c][b] = src[b][c] (bf16), rows b >= B of dst padded with zeros up to Bp.
-__global__ void transpose_kernel(const bf16_t* __restrict__ src, int64_t B, int C, bf16_t* __restrict__ dst,
-                                 int64_t Bp) {
-  __shared__ bf16_t tile[32][33];
-  const int64_t b0 = (int64_t)blockIdx.x * 32;
-  const int c0 = blockIdx.y * 32;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int64_t b = b0 + r;
-    const int c = c0 + threadIdx.x;
-    tile[r][threadIdx.x] = (b < B && c < C) ? src[b * C + c] : (bf16_t)0;
-  }
-  __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int c = c0 + r;
-    const int64_t b = b0 + threadIdx.x;
-    if (c < C && b < Bp) dst[(int64_t)c * Bp + b] = tile[threadIdx.x][r];
   }
 }
 
@@ -632,17 +659,18 @@ struct xs_mlp {
   float* dout = nullptr;
   float* dzf[2] = {nullptr};
   bf16_t* dzb[2] = {nullptr};
-  bf16_t* dzT = nullptr;
-  bf16_t* aT = nullptr;
+  bf16_t* dzT = nullptr;        // dZ transposed (256 x Bp), for the weight gradient
+  bf16_t* aT[NL - 1] = {nullptr};  // a0 .. a3 transposed (in x Bp), for the weight gradient
 };
 
 static void free_ws(xs_mlp* n) {
   for (int i = 0; i < NL; i++) { cudaFree(n->a[i]); n->a[i] = nullptr; }
   for (int i = 0; i < NL - 1; i++) { cudaFree(n->z[i]); n->z[i] = nullptr; }
   for (int i = 0; i < 2; i++) { cudaFree(n->dzf[i]); cudaFree(n->dzb[i]); n->dzf[i] = nullptr; n->dzb[i] = nullptr; }
-  cudaFree(n->out); cudaFree(n->dout); cudaFree(n->dzT); cudaFree(n->aT);
+  cudaFree(n->out); cudaFree(n->dout); cudaFree(n->dzT);
+  for (int i = 0; i < NL - 1; i++) { cudaFree(n->aT[i]); n->aT[i] = nullptr; }
   n->out = n->dout = nullptr;
-  n->dzT = n->aT = nullptr;
+  n->dzT = nullptr;
   n->cap = 0;
 }
 
@@ -662,7 +690,7 @@ static int ensure_ws(xs_mlp* n, int64_t B) {
   CK(cudaMalloc(&n->out, (size_t)Bp * 2 * sizeof(float)));
   CK(cudaMalloc(&n->dout, (size_t)Bp * 2 * sizeof(float)));
   CK(cudaMalloc(&n->dzT, (size_t)Bp * C * sizeof(bf16_t)));
-  CK(cudaMalloc(&n->aT, (size_t)Bp * C * sizeof(bf16_t)));
+  for (int i = 0; i < NL - 1; i++) CK(cudaMalloc(&n->aT[i], (size_t)Bp * WIDTH[i] * sizeof(bf16_t)));
   n->cap = B;
   return XT_OK;
 }
@@ -685,6 +713,9 @@ static int forward_layers(xs_mlp* n, int64_t B, bool keep_z, bf16_t** acts, floa
     e.bias = n->master + OFF_B[l];
     e.z = keep_z ? n->z[l] : nullptr;
     e.out_b = acts[l + 1];
+    // training: the transposed activations a1 .. a3 for the weight gradients
+    e.out_bt = (keep_z && l + 1 < NL - 1) ? n->aT[l + 1] : nullptr;
+    e.ldt = (int)pad16(B);
     e.ld = 256;
     e.status = (int*)(n->scal + 3);
     const int rc = gemm<EPI_GELU>(acts[l], WIDTH[l], n->wb + OFF_W[l], WIDTH[l], (int)B, 256, WIDTH[l], e, s);
@@ -701,7 +732,8 @@ static int loss_grad(xs_mlp* n, const float* X, const float* y, const float* t, 
                      float lam, cudaStream_t s) {
   int rc = ensure_ws(n, B);
   if (rc) return rc;
-  to_bf16_kernel<<<grid_1d(B * 16, 256), 256, 0, s>>>(X, n->a[0], B * 16);
+  const int64_t Bp = pad16(B);
+  to_bf16_t_kernel<<<grid_1d(B * 16, 256), 256, 0, s>>>(X, n->a[0], n->aT[0], B, Bp);
   CK(cudaGetLastError());
   rc = forward_layers(n, B, true, n->a, n->out, s);
   if (rc) return rc;
@@ -709,27 +741,24 @@ static int loss_grad(xs_mlp* n, const float* X, const float* y, const float* t, 
   mask_count_kernel<<<grid_1d(B, 256), 256, 0, s>>>(mask, B, n->scal + 1);
   loss_kernel<<<grid_1d(B, 256), 256, 0, s>>>(n->out, y, t, mask, B, lam, n->dout, n->scal);
   CK(cudaMemsetAsync(n->grad, 0, NPARAM * sizeof(float), s));
-  const int hb = (int)std::min<int64_t>(B, 1024);
+  const int hb = (int)std::min<int64_t>((B + HB_TILE - 1) / HB_TILE, 1024);
   head_backward_kernel<<<hb, 256, 0, s>>>(n->dout, n->a[NL - 1], n->wb + OFF_W[NL - 1], n->z[NL - 2], B,
                                           n->grad + OFF_W[NL - 1], n->grad + OFF_B[NL - 1], n->dzf[0], n->dzb[0],
-                                          n->grad + OFF_B[NL - 2]);
+                                          n->grad + OFF_B[NL - 2], n->dzT, Bp);
   CK(cudaGetLastError());
-  const int64_t Bp = pad16(B);
   int cur = 0;
   for (int l = NL - 2; l >= 0; l--) {
     const int in = WIDTH[l];
-    // wgrad: dW_l = dZ^T a_{l}  (M = 256 outputs, N = in, K = batch)
-    dim3 tb(32, 8);
-    transpose_kernel<<<dim3((unsigned)((Bp + 31) / 32), 256 / 32), tb, 0, s>>>(n->dzb[cur], B, 256, n->dzT, Bp);
-    transpose_kernel<<<dim3((unsigned)((Bp + 31) / 32), (in + 31) / 32), tb, 0, s>>>(n->a[l], B, in, n->aT, Bp);
-    CK(cudaGetLastError());
+    // wgrad: dW_l = dZ^T a_l (M = 256 outputs, N = in, K = the batch), from
+    // the transposed copies that the producers of dZ and a_l wrote; the
+    // tensor maps end K at B, so the copy engine zero-fills the padding
     Epi e;
     std::memset(&e, 0, sizeof(e));
     e.out_f = n->grad + OFF_W[l];
     e.ld = in;
     e.status = (int*)(n->scal + 3);
     // K (the batch) is split in slices of 256 whose partial sums add up in the gradient
-    rc = gemm<EPI_F32ADD>(n->dzT, (int)Bp, n->aT, (int)Bp, 256, in, (int)Bp, e, s);
+    rc = gemm<EPI_F32ADD>(n->dzT, (int)Bp, n->aT[l], (int)Bp, 256, in, (int)B, e, s);
     if (rc) return rc;
     // the bias gradient of layer l (column sums of its fp32 dZ) was added by
     // the kernel that produced dZ: head_backward_kernel or the dgrad epilogue
@@ -741,6 +770,8 @@ static int loss_grad(xs_mlp* n, const float* X, const float* y, const float* t, 
       d.z = n->dzf[1 - cur];
       d.out_b = n->dzb[1 - cur];
       d.colsum = n->grad + OFF_B[l - 1];
+      d.out_bt = n->dzT;  // read by the next weight gradient, after this one's
+      d.ldt = (int)Bp;
       d.ld = 256;
       d.status = (int*)(n->scal + 3);
       rc = gemm<EPI_DGRAD>(n->dzb[cur], 256, n->wtb + OFF_W[l], 256, (int)B, 256, 256, d, s);
