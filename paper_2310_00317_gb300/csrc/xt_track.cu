@@ -445,12 +445,12 @@ __device__ __forceinline__ double one_minus_exp(double u) {
 }
 
 // w(x + i y), y >= 0: 2 p(Z) q^2 + q / sqrt(pi), q = 1/(L - i z),
-// Z = (L + i z) q.
-__device__ __forceinline__ void faddeeva(double x, double y, double* wr, double* wi) {
+// Z = (L + i z) q, given 1/D, D = |L - i z|^2 = (L + y)^2 + x^2 (so that the
+// two evaluations of a lens share one division).
+__device__ __forceinline__ void faddeeva_id(double x, double y, double iD, double* wr, double* wi) {
   const double L = c_special[0];
   const double cr = L + y;
-  const double D = fma(cr, cr, x * x);
-  const double qr = cr / D, qi = x / D;
+  const double qr = cr * iD, qi = x * iD;
   const double ar = L - y;
   const double Zr = fma(ar, qr, -(x * qi));
   const double Zi = fma(ar, qi, x * qr);
@@ -467,6 +467,18 @@ __device__ __forceinline__ void faddeeva(double x, double y, double* wr, double*
   const double ui = 2.0 * ti;
   *wr = fma(qr, ur, -(qi * ui));
   *wi = fma(qr, ui, qi * ur);
+}
+
+// w at two points with one division: R = 1/(D1 D2), 1/D1 = D2 R, 1/D2 = D1 R
+// (D is at least L^2, about 28, so the product cannot underflow).
+__device__ __forceinline__ void faddeeva2(double x1, double y1, double x2, double y2, double* w1r, double* w1i,
+                                          double* w2r, double* w2i) {
+  const double L = c_special[0];
+  const double c1 = L + y1, c2 = L + y2;
+  const double D1 = fma(c1, c1, x1 * x1), D2 = fma(c2, c2, x2 * x2);
+  const double R = 1.0 / (D1 * D2);
+  faddeeva_id(x1, y1, D2 * R, w1r, w1i);
+  faddeeva_id(x2, y2, D1 * R, w2r, w2i);
 }
 
 // Field shape of the unit bi-Gaussian line charge of record prm (K, x_c, y_c,
@@ -490,8 +502,7 @@ __device__ __forceinline__ void bb_field(double x, double y, const double* prm, 
       fv = v * prm[11];
     } else {
       double w1r, w1i, w2r, w2i;
-      faddeeva(u * prm[8], v * prm[8], &w1r, &w1i);
-      faddeeva((u * prm[6]) * prm[8], (v * prm[7]) * prm[8], &w2r, &w2i);
+      faddeeva2(u * prm[8], v * prm[8], (u * prm[6]) * prm[8], (v * prm[7]) * prm[8], &w1r, &w1i, &w2r, &w2i);
       const double e = exp_cw(-h);
       fu = prm[9] * fma(-e, w2i, w1i);
       fv = prm[9] * fma(-e, w2r, w1r);
