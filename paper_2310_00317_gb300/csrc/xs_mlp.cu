@@ -376,6 +376,207 @@ __global__ void __launch_bounds__(256) tc_gemm_kernel(const __grid_constant__ CU
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS) : "memory");
 }
 
+// Warp-specialised form of the same GEMM, for launches with many tiles per
+// CTA: warp 0 issues the copies, warp 1 the MMAs, warps 2..9 run the
+// epilogue.  mbarriers connect them: full[s] (copies landed) and empty[s]
+// (the MMAs that read stage s are done) for the TC_NST operand stages, and
+// accf[a] (MMAs of a tile done) and acce[a] (its accumulator read) for two
+// accumulators in tensor memory.  The copies of later tiles, the MMAs of the
+// next tile and the epilogue of this one therefore run at the same time.
+// Every wait is clock-limited: a wait that gives up sets the CTA's error
+// flag, every role leaves its loop, the copies and MMAs still in flight are
+// waited for (again bounded), the tensor memory is freed and e.status is set.
+constexpr int WS_THREADS = 320;
+
+template <int EPI, int BN>
+__global__ void __launch_bounds__(WS_THREADS) tc_gemm_ws_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                const __grid_constant__ CUtensorMap tmB, int M,
+                                                                int N, int K, Epi e) {
+  constexpr int A_BYTES = TC_M * TC_BK * 2, B_BYTES = BN * TC_BK * 2, STAGE = A_BYTES + B_BYTES;
+  static_assert(STAGE % 1024 == 0, "stages must keep the 1024-byte alignment of the swizzle atoms");
+  constexpr uint32_t ACC = BN < 32 ? 32 : BN;  // columns per accumulator
+  constexpr uint32_t NCOLS = 2 * ACC;
+  constexpr int CH = BN < 32 ? BN : 32;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + TC_NST * STAGE);
+  uint64_t* empty = full + TC_NST;
+  uint64_t* accf = empty + TC_NST;
+  uint64_t* acce = accf + 2;
+  uint64_t* drain = acce + 2;
+  uint32_t* tslot = (uint32_t*)(drain + 1);
+  volatile int* err = (volatile int*)(tslot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n_mt = (M + TC_M - 1) / TC_M, n_nt = N / BN, n_ks = (K + TC_KSLICE - 1) / TC_KSLICE;
+  const int n_tiles = n_mt * n_nt * n_ks;
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_addr(tslot)),
+                 "r"(NCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int j = 0; j < TC_NST; j++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(full + j)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(empty + j)) : "memory");
+    }
+    for (int a = 0; a < 2; a++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(accf + a)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(sm_addr(acce + a)) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(drain)) : "memory");
+    *err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                         ((uint32_t)(TC_M >> 4) << 24);
+  auto coords = [&](int t, int& m0, int& n0, int& k0, int& k1) {
+    const int nt = t % n_nt, mt = (t / n_nt) % n_mt, ks = t / (n_nt * n_mt);
+    m0 = mt * TC_M;
+    n0 = nt * BN;
+    k0 = ks * TC_KSLICE;
+    k1 = min(K, k0 + TC_KSLICE);
+  };
+  uint32_t armed = 0;  // warp 0, lane 0: stage fills issued
+  int mma_open = 0;    // warp 1, lane 0: MMAs issued since the last commit that was waited for
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int t = blockIdx.x; t < n_tiles && !*err; t += gridDim.x) {
+        int m0, n0, k0, k1;
+        coords(t, m0, n0, k0, k1);
+        for (int j = 0; k0 + j * TC_BK < k1; j++) {
+          const int s = (int)(armed % TC_NST);
+          const uint32_t ph = (armed / TC_NST) & 1u;
+          if (!mbar_wait(sm_addr(empty + s), ph ^ 1u)) {
+            *err = 1;
+            break;
+          }
+          const uint32_t bar = sm_addr(full + s);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(STAGE) : "memory");
+          tma_load_2d(sm_addr(smem + s * STAGE), &tmA, k0 + j * TC_BK, m0, bar);
+          tma_load_2d(sm_addr(smem + s * STAGE + A_BYTES), &tmB, k0 + j * TC_BK, n0, bar);
+          armed++;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t it = 0, i = 0;
+      for (int t = blockIdx.x; t < n_tiles && !*err; t += gridDim.x, i++) {
+        const uint32_t a = i & 1u, aph = (i >> 1) & 1u;
+        if (!mbar_wait(sm_addr(acce + a), aph ^ 1u)) {
+          *err = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        int m0, n0, k0, k1;
+        coords(t, m0, n0, k0, k1);
+        const uint32_t d = tmem + a * ACC;
+        bool ok = true;
+        for (int j = 0; k0 + j * TC_BK < k1; j++, it++) {
+          const int s = (int)(it % TC_NST);
+          if (!mbar_wait(sm_addr(full + s), (it / TC_NST) & 1u)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const int kc = min(TC_BK, k1 - (k0 + j * TC_BK));
+          const uint64_t ad = smem_desc_sw128(sm_addr(smem + s * STAGE));
+          const uint64_t bd = smem_desc_sw128(sm_addr(smem + s * STAGE + A_BYTES));
+          for (int q = 0; q * 16 < kc; q++) {
+            const uint32_t accumulate = (j > 0 || q > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                "l"(ad + 2 * q), "l"(bd + 2 * q), "r"(idesc), "r"(accumulate)
+                : "memory");
+            mma_open = 1;
+          }
+          // the stage is free once these MMAs have read it
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           sm_addr(empty + s))
+                       : "memory");
+        }
+        if (!ok) {
+          *err = 1;
+          break;
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         sm_addr(accf + a))
+                     : "memory");
+      }
+    }
+  } else {
+    const int quad = warp & 3;         // the accumulator lanes (rows) this warp may read
+    const int half = (warp - 2) >> 2;  // 0 or 1: which columns
+    uint32_t i = 0;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, i++) {
+      const uint32_t a = i & 1u, aph = (i >> 1) & 1u;
+      int ok = mbar_wait(sm_addr(accf + a), aph) ? 1 : 0;
+      ok = __all_sync(0xFFFFFFFFu, ok);
+      if (!ok) {
+        *err = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int m0, n0, k0, k1;
+      coords(t, m0, n0, k0, k1);
+      const int row = m0 + quad * 32 + lane;
+      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + a * ACC;
+      bool released = false;
+#pragma unroll 1
+      for (int c0 = half * CH; c0 < BN; c0 += 2 * CH) {
+        uint32_t r[CH];
+        tmem_load<CH>(taddr + (uint32_t)c0, r);
+        if (c0 + 2 * CH >= BN) {  // this warp's last read of the accumulator: hand it back
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_addr(acce + a)) : "memory");
+          released = true;
+        }
+        float v[CH];
+#pragma unroll
+        for (int q = 0; q < CH; q++) v[q] = 0.0f;
+        if (row < M) epilogue<EPI, CH>(e, row, n0 + c0, r, v);
+        if constexpr (EPI == EPI_DGRAD && CH == 32) {
+          if (e.colsum) warp_colsum32(v, lane, e.colsum + n0 + c0);  // rows past M add 0
+        }
+      }
+      if (!released) {
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_addr(acce + a)) : "memory");
+      }
+    }
+  }
+  __syncthreads();
+  if (*err) {
+    if (warp == 0 && lane == 0) {
+      // the last fill of every stage has landed before the shared memory goes
+      for (uint32_t s = 0; s < (uint32_t)TC_NST && s < armed; s++) {
+        const uint32_t last = s + ((armed - 1 - s) / TC_NST) * TC_NST;
+        mbar_wait(sm_addr(full + s), (last / TC_NST) & 1u);
+      }
+    }
+    if (warp == 1 && lane == 0 && mma_open) {
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       sm_addr(drain))
+                   : "memory");
+      mbar_wait(sm_addr(drain), 0);
+    }
+    if (tid == 0 && e.status) atomicExch(e.status, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS) : "memory");
+}
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
 // against the driver library).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -446,6 +647,32 @@ int tc_launch(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K,
   return XT_OK;
 }
 
+// The warp-specialised kernel for the same tiles, when there are more tiles
+// than resident CTAs (each CTA then pipelines several).
+template <int EPI, int BN>
+int tc_launch_ws(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, const Epi& e, cudaStream_t s) {
+  constexpr size_t smem = (size_t)TC_NST * (TC_M * TC_BK * 2 + BN * TC_BK * 2) + 1024 + 256;
+  static int occ = 0;
+  if (!occ) {
+    CK(cudaFuncSetAttribute(tc_gemm_ws_kernel<EPI, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CK(cudaFuncSetAttribute(tc_gemm_ws_kernel<EPI, BN>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                            (int)cudaSharedmemCarveoutMaxShared));
+    int dev = 0, per_sm = 0, reserved = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    CK(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    const int by_smem = per_sm / (int)(smem + (size_t)reserved);
+    occ = std::max(1, std::min(by_smem, 512 / (2 * (BN < 32 ? 32 : BN))));
+  }
+  const int64_t tiles = (int64_t)((M + TC_M - 1) / TC_M) * (N / BN) * ((K + TC_KSLICE - 1) / TC_KSLICE);
+  const int sms = sm_count_of_current_device();
+  if (sms <= 0) return fail(XT_ERR_CUDA, "device attribute");
+  const int grid = (int)std::min<int64_t>(tiles, (int64_t)occ * sms);
+  tc_gemm_ws_kernel<EPI, BN><<<grid, WS_THREADS, smem, s>>>(ta, tb, M, N, K, e);
+  CK(cudaGetLastError());
+  return XT_OK;
+}
+
 // C = A B^T: A (M x K, row stride lda), B (N x K, row stride ldb), N = 256 or
 // 16 (16 only for the split-K weight gradient).  K slices of 256 run in
 // separate CTAs; EPI_F32ADD adds their partial sums into a zeroed output,
@@ -461,6 +688,9 @@ int gemm(const bf16_t* A, int lda, const bf16_t* B, int ldb, int M, int N, int K
   if (N == 256) {
     rc = make_tensor_map(&tb, B, N, K, ldb, 64);
     if (rc) return rc;
+    // more tiles than two per SM: the warp-specialised pipeline
+    const int64_t tiles = (int64_t)((M + TC_M - 1) / TC_M) * (N / 64) * ((K + TC_KSLICE - 1) / TC_KSLICE);
+    if (tiles > 2 * (int64_t)sm_count_of_current_device()) return tc_launch_ws<EPI, 64>(ta, tb, M, N, K, e, s);
     return tc_launch<EPI, 64>(ta, tb, M, N, K, e, s);
   }
   if constexpr (EPI == EPI_F32ADD) {

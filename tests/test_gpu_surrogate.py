@@ -64,8 +64,12 @@ def test_forward_vs_oracle():
     net.close()
 
 
-@pytest.mark.parametrize("B", [64, 777])
+@pytest.mark.parametrize("B", [64, 777, 20011])
 def test_loss_and_gradients_vs_oracle(B):
+    """64 and 777 samples run the GEMM kernel with one tile per CTA; 20,011
+    samples have more tiles than resident CTAs and run the warp-specialised
+    pipeline (two accumulators, copies and MMAs of the next tiles under the
+    epilogue), for the forward, dgrad and weight-gradient epilogues."""
     p = mlp.init_params(11).astype(np.float32).astype(np.float64)
     net = xtgb.Surrogate(1)
     net.set_params(p)
