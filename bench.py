@@ -44,10 +44,10 @@ SM_MAX_MHZ = 2070.0
 NOMINAL_FP64 = FP64_FLOP_PER_CLK_SM * N_SM * SM_MAX_MHZ * 1e6
 # DRAM bytes (read + write) of a tracking launch per particle and turn: ncu
 # capture of the current kernel on a 400,000-particle subset of this workload
-# over one turn (34,758,912 B read, 0 B written; all 152 SMs busy).  The
+# over one turn (34,656,512 B read, 0 B written; all 152 SMs busy).  The
 # per-launch traffic is the particle state, so it scales with the particle
 # count.
-TRACK_DRAM_BYTES_PER_PARTICLE_TURN = 34758912.0 / 400000.0
+TRACK_DRAM_BYTES_PER_PARTICLE_TURN = 34656512.0 / 400000.0
 
 
 def dist_env():
