@@ -704,6 +704,33 @@ def test_batched_seeds_with_quantum_radiation():
         t.close()
 
 
+def test_batched_graph_follows_new_options():
+    """A batch replayed from its CUDA graph after xt_tracker_set_options
+    changed the Philox seed (and the cycle budget) uses the new seed: it
+    equals the plain launch with the new seed bit for bit and differs from
+    the old seed's result."""
+    el, ref, _ = I.lepton_ring(n_cells=4, E0=5e9, v_total=30e6)
+    qs = [I.matched_gaussian(el, ref, n, 1e-3, 1e-3, seed=400 + i) for i, n in enumerate((700, 500))]
+    trs = [xtgb.Tracker(el, ref, radiation=xtgb.RAD_QUANTUM, seed=17) for _ in qs]
+
+    def run(graph):
+        P = [xtgb.Particles.from_numpy(q) for q in qs]
+        xtgb.track_batched(trs, P, 6, 0, graph=graph)
+        assert xtgb.batched_sync_status(trs, P) == xtgb.XT_OK
+        return [p.to_numpy() for p in P]
+
+    old = run(True)
+    for t in trs:
+        t.set_options(seed=99, max_cycles=0)
+    new_graph, new_plain = run(True), run(False)
+    for i in range(len(qs)):
+        assert_same(new_graph[i], new_plain[i], "seed %d: " % i)
+        assert not np.array_equal(new_graph[i]["px"], old[i]["px"])
+    xtgb.batched_release()
+    for t in trs:
+        t.close()
+
+
 @pytest.mark.parametrize("rad", [1, 2])
 def test_radiation_with_thick_elements(rad):
     """A small lepton ring with thick quadrupoles, a full bend between
