@@ -607,18 +607,21 @@ def measure_da_scan(n_turns=300):
     return out
 
 
-def measure_da_scan_full(n_turns=100, base_mult=1.0):
+def measure_da_scan_full(n_turns=100, base_mult=1.0, total_labels=5_000_000, n_test=4):
     """The surrogate-guided DA scan on the LHC-scale ring itself: a family of
-    64 error seeds of the 20,000-element ring, 5e6 labels from one batched
-    launch per segment, the full 999,990-point grid of the test seeds."""
+    64 error seeds of the 20,000-element ring, total_labels labels from one
+    batched launch per segment, the full 999,990-point grid of the first
+    n_test of the test seeds 60, 13, 30, 45."""
     from paper_2310_00317_gb300 import surrogate as S
-    r = S.da_study_full(n_turns=n_turns, base_mult=base_mult)
+    test_seeds = (60, 13, 30, 45)[:n_test]
+    r = S.da_study_full(n_turns=n_turns, base_mult=base_mult, total_labels=int(total_labels), test_seeds=test_seeds)
     out = {k: v for k, v in r.items() if k not in ("loss_history",)}
     out["workload"] = ("family of 64 error seeds of the LHC-scale ring (200 cells, 20,000 elements, orders 2..6 "
                        "scaled log-uniformly in [0.5, 2] x %g): %d random-amplitude labels (momentum deviations "
                        "N(0, 3e-4)) tracked by the batched tracker, band limits from plain scans of 3 validation "
-                       "seeds on 2,222 radii, 4 test seeds each scanned on the full grid of 22,222 radii x 9 angles "
-                       "x 5 momentum offsets (999,990 points), %d turns" % (base_mult, r["n_train"], n_turns))
+                       "seeds on 2,222 radii, %d test seeds each scanned on the full grid of 22,222 radii x 9 "
+                       "angles x 5 momentum offsets (999,990 points), %d turns"
+                       % (base_mult, r["n_train"], len(test_seeds), n_turns))
     return out
 
 
@@ -784,7 +787,9 @@ def run_ours(args):
         extras["twiss"] = measure_twiss()
         extras["batched_seeds"] = measure_batched()
         extras["lepton_quantum"] = measure_lepton()
-        extras["da_scan"] = measure_da_scan()
+        # the LHC-scale ring itself with 1e6 labels (5e6 in --only da_scan_full:
+        # 5 more minutes of labels for a narrower band)
+        extras["da_scan"] = measure_da_scan_full(n_turns=100, total_labels=1_000_000, n_test=4)
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(seed, args.cpu_particles, args.cpu_turns)
@@ -891,7 +896,8 @@ def main():
     ap.add_argument("--only", default="",
                     help="run one extra measurement alone and print its JSON: thick_elements[:n[:turns]], "
                          "beambeam_lens[:n[:turns]], lepton_quantum[:n[:turns]], twiss, steady[:turns[:window]], "
-                         "batched_seeds[:turns_per_step:steps], lepton_equilibrium[:n[:turns]]")
+                         "batched_seeds[:turns_per_step:steps], lepton_equilibrium[:n[:turns]], fodo10[:n[:turns]], "
+                         "da_scan (the reduced ring), da_scan_full[:turns[:error_mult[:labels[:test_seeds]]]]")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -902,27 +908,40 @@ def main():
     return run_ours(args)
 
 
-def run_only(spec: str) -> int:
-    """One extra measurement on its own (for profiling its kernel)."""
+def only_kwargs(spec: str):
+    """Name and keyword arguments of an --only measurement spec."""
     name, *nums = spec.split(":")
     kw = {}
-    if nums:
-        kw["n"] = int(nums[0])
-    if len(nums) > 1:
-        kw["turns"] = int(nums[1])
     if name == "steady":
         kw = {"turns": int(nums[0])} if nums else {}
         if len(nums) > 1:
             kw["window"] = int(nums[1])
     elif name == "batched_seeds":
         kw = {"T": int(nums[0]), "steps": int(nums[1])} if len(nums) > 1 else {}
+    elif name == "da_scan":
+        kw = {"n_turns": int(nums[0])} if nums else {}
     elif name == "da_scan_full":
         kw = {"n_turns": int(nums[0])} if nums else {}
         if len(nums) > 1:
             kw["base_mult"] = float(nums[1])
+        if len(nums) > 2:
+            kw["total_labels"] = int(float(nums[2]))
+        if len(nums) > 3:
+            kw["n_test"] = int(nums[3])
+    else:
+        if nums:
+            kw["n"] = int(nums[0])
+        if len(nums) > 1:
+            kw["turns"] = int(nums[1])
+    return name, kw
+
+
+def run_only(spec: str) -> int:
+    """One extra measurement on its own (for profiling its kernel)."""
+    name, kw = only_kwargs(spec)
     fn = {"thick_elements": measure_thick, "beambeam_lens": measure_beambeam, "twiss": measure_twiss,
           "lepton_quantum": measure_lepton, "steady": measure_steady, "batched_seeds": measure_batched,
-          "lepton_equilibrium": measure_lepton_equilibrium, "da_scan_full": measure_da_scan_full,
+          "lepton_equilibrium": measure_lepton_equilibrium, "da_scan_full": measure_da_scan_full, "da_scan": measure_da_scan,
           "fodo10": measure_fodo}.get(name)
     if fn is None:
         raise SystemExit("--only: unknown measurement %r" % name)
