@@ -467,6 +467,13 @@ def measure_lepton(n=200000, turns=10):
     p = I.matched_gaussian(el, ref, n, 0.0, 1.06e-3, seed=5, emit_x=2 * 3.9e-8, emit_y=2 * 3.9e-10)
     tr = xtgb.Tracker(el, ref, radiation=xtgb.RAD_QUANTUM, seed=1)
     P = xtgb.Particles.from_numpy(p)
+    # block, chunk and segment from the autotuner on these particles (2 turns)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    opt = tr.autotune(P, 2)
+    torch.cuda.synchronize()
+    tune = {"block": int(opt["block"]), "chunk_bytes": int(opt["chunk_bytes"]),
+            "segment_turns": int(opt["segment_turns"]), "seconds": time.perf_counter() - t0}
     tr.track(P, 2, 0)
     before = P.t["state"].cpu().numpy()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -484,7 +491,7 @@ def measure_lepton(n=200000, turns=10):
     tr.close()
     achieved = units * per_pass / (ms * 1e-3)
     return {"workload": "lepton ring 10,000 elements, 45.6 GeV, mean + quantum radiation, %d particles" % n,
-            "turns": turns, "value": units / (ms * 1e-3), "unit": UNIT,
+            "turns": turns, "value": units / (ms * 1e-3), "unit": UNIT, "autotune": tune,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": NOMINAL_FP64 / 1e12,
                          "unit": "TFLOP/s", "frac": achieved / NOMINAL_FP64,
                          "algorithmic_flops_per_pass": per_pass,
