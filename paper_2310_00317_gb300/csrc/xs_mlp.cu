@@ -86,16 +86,60 @@ __device__ __forceinline__ float normal_tail(float z, float* e) {
   *e = ex2_approx(z * (z * -0.72134752044448170f));                 // -log2(e) / 2
   return (q * t) * *e;
 }
-__device__ __forceinline__ float gelu_f(float z) {
-  float e;
-  const float tail = normal_tail(z, &e);
-  return fmaf(-fabsf(z), tail, fmaxf(z, 0.0f));
-}
 __device__ __forceinline__ float gelu_grad_f(float z) {
   float e;
   const float tail = normal_tail(z, &e);
   const float phi = z >= 0.0f ? 1.0f - tail : tail;
   return fmaf(z * 0.39894228040143268f, e, phi);  // 1 / sqrt(2 pi)
+}
+
+// The same on two outputs at once: the packed FP32 pair instructions
+// (fma/mul/add.rn.f32x2) do both lanes' arithmetic in one instruction with
+// the rounding of the single-lane operations.
+union F2 {
+  float2 f;
+  unsigned long long u;
+};
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  F2 A, B, C, D;
+  A.f = a; B.f = b; C.f = c;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(D.u) : "l"(A.u), "l"(B.u), "l"(C.u));
+  return D.f;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  F2 A, B, D;
+  A.f = a; B.f = b;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(D.u) : "l"(A.u), "l"(B.u));
+  return D.f;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  F2 A, B, D;
+  A.f = a; B.f = b;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(D.u) : "l"(A.u), "l"(B.u));
+  return D.f;
+}
+__device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 normal_tail2(float2 z, float2* e) {
+  const float2 d = make_float2(fmaf(0.231641888f, fabsf(z.x), 1.0f), fmaf(0.231641888f, fabsf(z.y), 1.0f));
+  const float2 t = make_float2(rcp_approx(d.x), rcp_approx(d.y));
+  float2 q = fma2(splat2(0.5307027145f), t, splat2(-0.7265760135f));
+  q = fma2(q, t, splat2(0.7107068705f));
+  q = fma2(q, t, splat2(-0.142248368f));
+  q = fma2(q, t, splat2(0.127414796f));
+  const float2 a = mul2(mul2(z, z), splat2(-0.72134752044448170f));
+  *e = make_float2(ex2_approx(a.x), ex2_approx(a.y));
+  return mul2(mul2(q, t), *e);
+}
+__device__ __forceinline__ float2 gelu2(float2 z) {
+  float2 e;
+  const float2 tail = normal_tail2(z, &e);
+  return make_float2(fmaf(-fabsf(z.x), tail.x, fmaxf(z.x, 0.0f)), fmaf(-fabsf(z.y), tail.y, fmaxf(z.y, 0.0f)));
+}
+__device__ __forceinline__ float2 gelu_grad2(float2 z) {
+  float2 e;
+  const float2 tail = normal_tail2(z, &e);
+  const float2 phi = make_float2(z.x >= 0.0f ? 1.0f - tail.x : tail.x, z.y >= 0.0f ? 1.0f - tail.y : tail.y);
+  return fma2(mul2(z, splat2(0.39894228040143268f)), e, phi);
 }
 
 // ---------------------------------------------------------------------------
@@ -216,12 +260,15 @@ __device__ __forceinline__ void epilogue(const Epi& e, int row, int col, const u
       float4 a;
       if (EPI == EPI_GELU) a = __ldg((const float4*)(e.bias + col) + q);
       else a = __ldg((const float4*)(e.zprev + o) + q);
-      const float aa[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-      for (int i = 0; i < 4; i++) {
-        const float acc = __uint_as_float(r[4 * q + i]);
-        v[4 * q + i] = (EPI == EPI_GELU) ? acc + aa[i] : acc * gelu_grad_f(aa[i]);
-      }
+      const float2 acc01 = make_float2(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]));
+      const float2 acc23 = make_float2(__uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+      const float2 a01 = make_float2(a.x, a.y), a23 = make_float2(a.z, a.w);
+      const float2 v01 = (EPI == EPI_GELU) ? add2(acc01, a01) : mul2(acc01, gelu_grad2(a01));
+      const float2 v23 = (EPI == EPI_GELU) ? add2(acc23, a23) : mul2(acc23, gelu_grad2(a23));
+      v[4 * q] = v01.x;
+      v[4 * q + 1] = v01.y;
+      v[4 * q + 2] = v23.x;
+      v[4 * q + 3] = v23.y;
     }
     if (e.z) {
 #pragma unroll
@@ -235,9 +282,9 @@ __device__ __forceinline__ void epilogue(const Epi& e, int row, int col, const u
     uint32_t h[CH / 2];
 #pragma unroll
     for (int i = 0; i < CH / 2; i++) {
-      const float a = (EPI == EPI_GELU) ? gelu_f(v[2 * i]) : v[2 * i];
-      const float b = (EPI == EPI_GELU) ? gelu_f(v[2 * i + 1]) : v[2 * i + 1];
-      h[i] = pack_bf16x2(a, b);
+      const float2 zi = make_float2(v[2 * i], v[2 * i + 1]);
+      const float2 g = (EPI == EPI_GELU) ? gelu2(zi) : zi;
+      h[i] = pack_bf16x2(g.x, g.y);
     }
 #pragma unroll
     for (int q = 0; q < CH / 8; q++)
