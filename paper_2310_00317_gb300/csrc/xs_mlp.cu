@@ -237,6 +237,24 @@ __device__ __forceinline__ void tmem_load<16>(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// A 16-column accumulator read issued without waiting, and the wait that
+// completes it; the wait names the destination registers, so no use of them
+// can be scheduled before it.
+__device__ __forceinline__ void tmem_issue16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait16(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&h);
@@ -244,8 +262,10 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 
 // Epilogue of CH accumulator columns [col, col + CH) of one row; v receives
 // the fp32 values written (EPI_DGRAD: dZ).
-template <int EPI, int CH>
-__device__ __forceinline__ void epilogue(const Epi& e, int row, int col, const uint32_t* r, float* vout) {
+// SBIAS: the layer's bias is read from its copy in shared memory, sbias
+template <int EPI, int CH, bool SBIAS = false>
+__device__ __forceinline__ void epilogue(const Epi& e, int row, int col, const uint32_t* r, float* vout,
+                                         const float* sbias = nullptr) {
   const int64_t o = (int64_t)row * e.ld + col;
   if (EPI == EPI_F32ADD) {
 #pragma unroll
@@ -258,7 +278,7 @@ __device__ __forceinline__ void epilogue(const Epi& e, int row, int col, const u
 #pragma unroll
     for (int q = 0; q < CH / 4; q++) {
       float4 a;
-      if (EPI == EPI_GELU) a = __ldg((const float4*)(e.bias + col) + q);
+      if (EPI == EPI_GELU) a = SBIAS ? *((const float4*)(sbias + col) + q) : __ldg((const float4*)(e.bias + col) + q);
       else a = __ldg((const float4*)(e.zprev + o) + q);
       const float2 acc01 = make_float2(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]));
       const float2 acc23 = make_float2(__uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
@@ -472,6 +492,7 @@ __global__ void __launch_bounds__(256, 2) tc_gemm_kernel(const __grid_constant__
 // flag, every role leaves its loop, the copies and MMAs still in flight are
 // waited for (again bounded), the tensor memory is freed and e.status is set.
 constexpr int WS_THREADS = 320;
+constexpr int WS_BIAS = 256;  // bias floats kept in shared memory
 
 template <int EPI, int BN>
 __global__ void __launch_bounds__(WS_THREADS) tc_gemm_ws_kernel(const __grid_constant__ CUtensorMap tmA,
@@ -491,9 +512,16 @@ __global__ void __launch_bounds__(WS_THREADS) tc_gemm_ws_kernel(const __grid_con
   uint64_t* drain = acce + 2;
   uint32_t* tslot = (uint32_t*)(drain + 1);
   volatile int* err = (volatile int*)(tslot + 1);
+  float* sbias = (float*)(smem + TC_NST * STAGE + 256);  // WS_BIAS floats
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n_mt = (M + TC_M - 1) / TC_M, n_nt = N / BN, n_ks = (K + TC_KSLICE - 1) / TC_KSLICE;
   const int n_tiles = n_mt * n_nt * n_ks;
+  // the bias is read once per CTA into shared memory (N <= WS_BIAS, checked
+  // by the host)
+  if (EPI == EPI_GELU) {
+    for (int j = tid; j < N; j += WS_THREADS) sbias[j] = e.bias[j];
+  }
+  constexpr bool SB = EPI == EPI_GELU;
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_addr(tslot)),
                  "r"(NCOLS)
@@ -618,17 +646,32 @@ __global__ void __launch_bounds__(WS_THREADS) tc_gemm_ws_kernel(const __grid_con
 #pragma unroll 1
       for (int c0 = half * CH; c0 < BN; c0 += 2 * CH) {
         uint32_t r[CH];
-        tmem_load<CH>(taddr + (uint32_t)c0, r);
-        if (c0 + 2 * CH >= BN) {  // this warp's last read of the accumulator: hand it back
+        float v[CH];
+#pragma unroll
+        for (int q = 0; q < CH; q++) v[q] = 0.0f;
+        const bool last = c0 + 2 * CH >= BN;  // this warp's last read of the accumulator
+        if constexpr (CH == 32) {
+          // two 16-column reads: the second lands while the first is processed
+          tmem_issue16(taddr + (uint32_t)c0, r);
+          tmem_wait16(r);
+          tmem_issue16(taddr + (uint32_t)c0 + 16u, r + 16);
+          if (row < M) epilogue<EPI, 16, SB>(e, row, n0 + c0, r, v, sbias);
+          __syncwarp();
+          tmem_wait16(r + 16);
+        } else {
+          tmem_load<CH>(taddr + (uint32_t)c0, r);
+        }
+        if (last) {  // hand the accumulator back
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           __syncwarp();
           if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_addr(acce + a)) : "memory");
           released = true;
         }
-        float v[CH];
-#pragma unroll
-        for (int q = 0; q < CH; q++) v[q] = 0.0f;
-        if (row < M) epilogue<EPI, CH>(e, row, n0 + c0, r, v);
+        if constexpr (CH == 32) {
+          if (row < M) epilogue<EPI, 16, SB>(e, row, n0 + c0 + 16, r + 16, v + 16, sbias);
+        } else {
+          if (row < M) epilogue<EPI, CH, SB>(e, row, n0 + c0, r, v, sbias);
+        }
         if constexpr (EPI == EPI_DGRAD && CH == 32) {
           if (e.colsum) warp_colsum32(v, lane, e.colsum + n0 + c0);  // rows past M add 0
         }
@@ -736,7 +779,8 @@ int tc_launch(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K,
 // than resident CTAs (each CTA then pipelines several).
 template <int EPI, int BN>
 int tc_launch_ws(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, const Epi& e, cudaStream_t s) {
-  constexpr size_t smem = (size_t)TC_NST * (TC_M * TC_BK * 2 + BN * TC_BK * 2) + 1024 + 256;
+  constexpr size_t smem =
+      (size_t)TC_NST * (TC_M * TC_BK * 2 + BN * TC_BK * 2) + 1024 + 256 + WS_BIAS * sizeof(float);
   static int occ = 0;
   if (!occ) {
     CK(cudaFuncSetAttribute(tc_gemm_ws_kernel<EPI, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -775,7 +819,8 @@ int gemm(const bf16_t* A, int lda, const bf16_t* B, int ldb, int M, int N, int K
     if (rc) return rc;
     // more tiles than two per SM: the warp-specialised pipeline
     const int64_t tiles = (int64_t)((M + TC_M - 1) / TC_M) * (N / 64) * ((K + TC_KSLICE - 1) / TC_KSLICE);
-    if (tiles > 2 * (int64_t)sm_count_of_current_device()) return tc_launch_ws<EPI, 64>(ta, tb, M, N, K, e, s);
+    if (tiles > 2 * (int64_t)sm_count_of_current_device() && (EPI != EPI_GELU || N <= WS_BIAS))
+      return tc_launch_ws<EPI, 64>(ta, tb, M, N, K, e, s);
     return tc_launch<EPI, 64>(ta, tb, M, N, K, e, s);
   }
   if constexpr (EPI == EPI_F32ADD) {
