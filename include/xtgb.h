@@ -414,8 +414,10 @@ int xt_refine_losses(xt_tracker* tr, const xt_particles* particles, double ds, i
 /* Dynamic-aperture surrogate network.  The paper lists dynamic-aperture
    estimates based on machine learning among Xsuite's applications (section
    "Lattice modelling and single particle tracking"); the network is this
-   project's: MLP 16 -> 256 -> 256 -> 256 -> 256 -> 2 with exact GELU,
-   inputs = 6 normalised initial coordinates + 10 lattice-error descriptors,
+   project's: MLP 16 -> 256 -> 256 -> 256 -> 256 -> 2 with GELU (erf by
+   Hastings' rational approximation, Abramowitz & Stegun 7.1.26, within
+   1.5e-7), inputs = 6 normalised initial coordinates + 10 lattice-error
+   descriptors,
    outputs = (survival logit, normalised log loss turn).  bfloat16 weights,
    inputs, activations and back-propagated dZ; FP32 accumulation on the
    tensor cores, FP32 bias/GELU/head/loss; FP32 master weights with Adam
